@@ -1,0 +1,112 @@
+"""Textbook Krylov loops on top of the oracle's operators (TEST INFRASTRUCTURE).
+
+* ``cg``   unpreconditioned conjugate gradient (Hestenes-Stiefel) with exactly the vector operations
+           the paper lists per iteration in Table 4: one operator apply, the dot p^T A p, the updates
+           of x and r, the dot r^T r, and the update of p.
+* ``pcg``  the same with a fixed preconditioner z = M(r) (Jacobi when M = diag(A)^-1).
+* ``fcg``  flexible CG for a preconditioner that may change between iterations (a network):
+           beta_k = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k)  (Polak-Ribiere form, Notay 2000).
+* ``iterative_refinement``  x += solve_inner(b - A x) until the FP64 residual meets the tolerance.
+
+Readings: x0 = 0; stop when ||r_k||_2 <= rtol ||b||_2 (the paper gives no stopping norm); the
+iteration count is the number of operator applies inside the loop.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def cg(apply, b, rtol=1e-8, max_iter=100000, x0=None, dot=None):
+    """Returns (x, iterations, residual history ||r_k||/||b||)."""
+    dot = dot or (lambda u, v: float(np.dot(u, v)))
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - apply(x) if x0 is not None else b.copy()
+    p = r.copy()
+    bn = math.sqrt(dot(b, b))
+    if bn == 0.0:
+        return x, 0, [0.0]
+    rr = dot(r, r)
+    hist = [math.sqrt(rr) / bn]
+    k = 0
+    while k < max_iter and math.sqrt(rr) > rtol * bn:
+        Ap = apply(p)
+        pAp = dot(p, Ap)
+        if not pAp > 0.0:
+            raise FloatingPointError("CG breakdown: p^T A p <= 0")
+        alpha = rr / pAp
+        x += alpha * p
+        r -= alpha * Ap
+        rr_new = dot(r, r)
+        beta = rr_new / rr
+        p = r + beta * p
+        rr = rr_new
+        k += 1
+        hist.append(math.sqrt(rr) / bn)
+    return x, k, hist
+
+
+def pcg(apply, b, precond, rtol=1e-8, max_iter=100000):
+    """Preconditioned CG with a fixed symmetric preconditioner z = precond(r)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = precond(r)
+    p = z.copy()
+    bn = float(np.linalg.norm(b))
+    rz = float(np.dot(r, z))
+    k = 0
+    hist = [1.0]
+    while k < max_iter and np.linalg.norm(r) > rtol * bn:
+        Ap = apply(p)
+        alpha = rz / float(np.dot(p, Ap))
+        x += alpha * p
+        r -= alpha * Ap
+        z = precond(r)
+        rz_new = float(np.dot(r, z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        k += 1
+        hist.append(float(np.linalg.norm(r)) / bn)
+    return x, k, hist
+
+
+def fcg(apply, b, precond, rtol=1e-8, max_iter=100000):
+    """Flexible CG (Polak-Ribiere beta).  With precond = identity the iterates are CG's up to rounding."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = precond(r)
+    p = z.copy()
+    bn = float(np.linalg.norm(b))
+    rz = float(np.dot(r, z))
+    k = 0
+    hist = [1.0]
+    while k < max_iter and np.linalg.norm(r) > rtol * bn:
+        Ap = apply(p)
+        alpha = rz / float(np.dot(p, Ap))
+        x += alpha * p
+        r_old = r.copy()
+        r -= alpha * Ap
+        z = precond(r)
+        beta = float(np.dot(z, r - r_old)) / rz
+        rz = float(np.dot(r, z))
+        p = z + beta * p
+        k += 1
+        hist.append(float(np.linalg.norm(r)) / bn)
+    return x, k, hist
+
+
+def iterative_refinement(apply64, inner_solve, b, rtol=1e-10, max_outer=50):
+    """x_{m+1} = x_m + d_m with d_m ~ A^{-1} (b - A x_m) from a lower-precision inner solve.
+    Returns (x, outer iterations, history of the FP64 relative residual)."""
+    x = np.zeros_like(b)
+    bn = float(np.linalg.norm(b))
+    r = b.copy()
+    hist = [1.0]
+    m = 0
+    while m < max_outer and np.linalg.norm(r) > rtol * bn:
+        x = x + inner_solve(r)
+        r = b - apply64(x)
+        m += 1
+        hist.append(float(np.linalg.norm(r)) / bn)
+    return x, m, hist
