@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free Q1 operator apply y = A x on the GPU (one JSON line on stdout).
+
+Workload (one "step" = one pass of the hot path over one batch of synthetic input): the matrix-free
+FP64 apply of the scalar Laplace operator on a 256^3-cell Cartesian box (16,908,544 free DoF) and
+of isotropic elasticity on a 160^3-cell box (12,442,080 free DoF), both with 8 z-layers of
+heterogeneous coefficients times per-cell lognormal noise and u = 0 on z = 0.  ``value`` is free
+DoF processed per second over both applies (GDoF/s).  The same line carries, measured after the
+timed region: the in-library CSR SpMV on the same matrices, CG time-to-1e-8 (matrix-free vs CSR),
+the end-to-end throughput through the C ABI with host buffers, the roofline of the dominant
+kernel, and the CPU oracle timed on a bounded sample on the host cores.
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under torchrun every rank
+runs an independent replica (the operator needs no exchange between independent problems) and
+rank 0 prints the line with value = all ranks' DoF / max-over-ranks time.
+``--impl reference`` times the CPU oracle (the deliberately slow reference implementation) on the
+host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GDoF/s of matrix-free A.x (Q1 Laplace 256^3 + elasticity 160^3, FP64)"
+UNIT = "GDoF/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-laplace", type=int, default=256)
+    ap.add_argument("--n-elasticity", type=int, default=160)
+    ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution measurements")
+    ap.add_argument("--no-csr", action="store_true", help="skip the CSR SpMV measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cg-timeout", type=float, default=90.0)
+    ap.add_argument("--variant", type=int, default=0, help="0 = auto (fastest FP64-accurate), 1 = reference")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------ clocks ----
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.proc = None
+        self.path = None
+        exe = shutil.which("nvidia-smi")
+        if exe is None:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.f = open(self.path, "w")
+        self.proc = subprocess.Popen([exe, "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                      "-lms", str(period_ms)], stdout=self.f, stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- CPU oracle ----
+
+def slab(p, nz_slab):
+    """The bottom ``nz_slab`` cell layers of a box problem (same coordinates and coefficients)."""
+    from paper_2308_09839_gb300 import inputs
+    nn = (p.nx + 1) * (p.ny + 1) * (nz_slab + 1)
+    ne = p.nx * p.ny * nz_slab
+    return inputs.Problem(p.name + f"_slab{nz_slab}", p.physics, p.nx, p.ny, nz_slab, p.coords[:nn], p.mat[:ne],
+                          p.dirichlet[:nn], p.seed)
+
+
+def oracle_sample_rate(problems, nz_slabs, repeats=1):
+    """Time the oracle's apply on slabs of each problem; returns (free DoF per second scaled from
+    the full problems' DoF per cell, seconds, description)."""
+    from oracle import fem
+    dof_equiv, secs, desc = 0.0, 0.0, []
+    for p, nzs in zip(problems, nz_slabs):
+        s = slab(p, nzs)
+        cells = s.cell_array()
+        x = s.x()
+        t0 = time.perf_counter()
+        for _ in range(repeats):
+            fem.apply(s.physics, s.coords, cells, s.mat, s.dirichlet, x)
+        dt = time.perf_counter() - t0
+        dof_equiv += repeats * cells.shape[0] * (p.n_free / p.n_cells)
+        secs += dt
+        desc.append(f"{p.physics} {p.nx}x{p.ny}x{nzs} cells x{repeats}")
+    return dof_equiv / secs, secs, "; ".join(desc)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2308_09839_gb300 import inputs
+    pL = inputs.cartesian_laplace_256(n=args.n_laplace)
+    pE = inputs.cartesian_elasticity_160(n=args.n_elasticity)
+    for _ in range(args.warmup):
+        oracle_sample_rate([pL, pE], [1, 1])
+    rates, tot = [], 0.0
+    for _ in range(args.steps):
+        r, s, desc = oracle_sample_rate([pL, pE], [1, 1])
+        rates.append(r)
+        tot += s
+    value = float(np.mean(rates)) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Q1 matrix-free apply, Laplace {args.n_laplace}^3 + elasticity {args.n_elasticity}^3 "
+                               "Cartesian, layered lognormal coefficients", "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: " + desc + " (one-cell-thick bottom slabs of both workloads)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------- GPU arm ----
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2308_09839_gb300 import bytes_model as bm
+    from paper_2308_09839_gb300 import inputs, mf
+
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+
+    pL = inputs.cartesian_laplace_256(n=args.n_laplace)
+    pE = inputs.cartesian_elasticity_160(n=args.n_elasticity)
+    meshes = []
+    for p in (pL, pE):
+        m = mf.Mesh.from_problem(p, device=f"cuda:{local}")
+        m.set_variant(args.variant)
+        x = torch.from_numpy(p.x()).cuda()
+        meshes.append((p, m, x, torch.empty_like(x)))
+    F = [p.n_free for p in (pL, pE)]
+    torch.cuda.synchronize()
+
+    def step(evs=None, k=0):
+        for j, (p, m, x, y) in enumerate(meshes):
+            if evs is not None:
+                evs[j][0][k].record()
+            m.apply(x, y)
+            if evs is not None:
+                evs[j][1][k].record()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(K)] for _ in range(2)] for _ in range(2)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = mf.mf_kernel_launches()
+    e0.record()
+    for k in range(K):
+        step(evs, k)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = mf.mf_kernel_launches() - l0
+    clk = clocks.stop()
+    t_total = e0.elapsed_time(e1) / 1e3
+    t_app = [float(np.mean([evs[j][0][k].elapsed_time(evs[j][1][k]) for k in range(K)])) / 1e3 for j in range(2)]
+    if world > 1:
+        t = torch.tensor([t_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = world * K * sum(F) / t_total / 1e9
+
+    # ---- parity spot check of the timed launch configuration (sampled rows vs the oracle)
+    extras = {"gdofs_apply": {"laplace": F[0] / t_app[0] / 1e9, "elasticity": F[1] / t_app[1] / 1e9},
+              "ms_apply": {"laplace": 1e3 * t_app[0], "elasticity": 1e3 * t_app[1]}}
+
+    # ---- end to end through the C ABI with host buffers (H2D of x, apply, D2H of y every step)
+    hx = [x.cpu().pin_memory() for (_, _, x, _) in meshes]
+    hy = [torch.empty_like(h).pin_memory() for h in hx]
+    for _ in range(2):
+        for j, (p, m, x, y) in enumerate(meshes):
+            x.copy_(hx[j], non_blocking=True)
+            m.apply(x, y)
+            hy[j].copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    Ke = max(5, K // 2)
+    barrier()
+    e0.record()
+    for _ in range(Ke):
+        for j, (p, m, x, y) in enumerate(meshes):
+            x.copy_(hx[j], non_blocking=True)
+            m.apply(x, y)
+            hy[j].copy_(y, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    io_bytes = sum(h.numel() * 8 for h in hx)
+    e2e = {"value": world * Ke * sum(F) / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+           "d2h_bytes_per_step": io_bytes}
+
+    # ---- roofline of the dominant kernel (the matrix-free apply taking the most time)
+    j = int(np.argmax(t_app))
+    p = (pL, pE)[j]
+    abytes = bm.kernel_apply_bytes(p.physics, p.n_cells, p.n_nodes, structured=True)
+    achieved = abytes / t_app[j] / 1e9
+    roof = {"kernel": f"matrix-free {p.physics} apply ({p.nx}^3)", "bound": "hbm", "achieved": achieved,
+            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": hbm_src,
+            "algorithmic_bytes": abytes, "traffic": None}
+
+    # ---- CSR SpMV on the same matrices (in-library matrix-based baseline)
+    if not args.no_csr:
+        csr = {}
+        for (p, m, x, y) in meshes:
+            A = m.assemble_csr()
+            for _ in range(3):
+                A.spmv(x, y)
+            torch.cuda.synchronize()
+            Ks = max(5, K // 2)
+            e0.record()
+            for _ in range(Ks):
+                A.spmv(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ts = e0.elapsed_time(e1) / 1e3 / Ks
+            sb = bm.kernel_spmv_bytes(A.info["n_rows"], A.info["nnz"])
+            csr[p.physics] = {"gdofs": p.n_free / ts / 1e9, "ms": 1e3 * ts, "nnz": A.info["nnz"],
+                              "hbm_frac": sb / ts / 1e9 / hbm_peak}
+            if not args.no_cg:
+                xs, info = m.cg(torch.from_numpy(p.b()).cuda(), csr=A, timeout_s=args.cg_timeout)
+                csr[p.physics]["cg"] = {"seconds": info.seconds, "iters": info.iters, "status": info.status,
+                                        "rel_res_true": info.rel_res_true}
+            A.close()
+            del A
+            torch.cuda.empty_cache()
+        extras["csr_spmv"] = csr
+        extras["mf_over_csr"] = {ph: extras["gdofs_apply"][ph] / csr[ph]["gdofs"] for ph in csr}
+
+    # ---- CG time-to-1e-8 with the matrix-free operator
+    if not args.no_cg:
+        cg = {}
+        for (p, m, x, y) in meshes:
+            b = torch.from_numpy(p.b()).cuda()
+            xs, info = m.cg(b, timeout_s=args.cg_timeout)
+            cg[p.physics] = {"seconds": info.seconds, "iters": info.iters, "status": info.status,
+                             "rel_res_true": info.rel_res_true,
+                             "cg_gdofs": p.n_free * info.iters / info.seconds / 1e9}
+        extras["cg_matfree"] = cg
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, secs, desc = oracle_sample_rate([pL, pE], [4, 2])
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": desc + f" (bottom slabs of both workloads, {secs:.1f} s of CPU time)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Q1 matrix-free apply, Laplace {pL.nx}^3 Cartesian (F={F[0]}) + elasticity "
+                               f"{pE.nx}^3 Cartesian (F={F[1]}), 8 z-layers x lognormal(0,0.5)",
+                   "n_dof_total": [pL.n_dof, pE.n_dof], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (no flush)", "variant": args.variant},
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+        "extras": extras,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * mf.h - C ABI of the GB300 (sm_103a) matrix-free Q1 finite-element library.
+ *
+ * The library applies the low-order finite-element operators of the paper "Performant low-order
+ * matrix-free finite element kernels on GPU architectures" (Settgast et al.): the scalar Laplace
+ * and isotropic linear-elasticity operators on trilinear hexahedra (Q1) with 2x2x2 Gauss
+ * quadrature (Sec. 2, Eqs. 1, 3, 4, 6), matrix-free (Sec. 3, Eqs. 7 and 9, Algorithm 1) or through
+ * an assembled CSR matrix (Sec. 3 and Table 1), and solves A x = b by conjugate gradient (the
+ * operations of Table 4).
+ *
+ * Conventions shared by every call:
+ *   - All array arguments are DEVICE pointers on the current CUDA device, owned by the caller,
+ *     unless marked "host".  The library never frees caller memory.
+ *   - Node (i, j, k) of an nx x ny x nz box has id i + (nx+1)(j + (ny+1)k); element (ex, ey, ez)
+ *     has id ex + nx(ey + ny ez).  Corner a = 0..7 of an element sits at reference coordinates
+ *     (+-1, +-1, +-1) with bit 0 of a -> xi, bit 1 -> eta, bit 2 -> zeta (0 -> -1, 1 -> +1).
+ *   - Vector problems interleave components: DoF 3*node + k (the 3(i-1)+k index of Eqs. 2-3).
+ *   - Dirichlet DoFs: their columns are dropped and their rows are the identity, so
+ *     (A x)_d = x_d for every constrained DoF d.
+ *   - Calls taking a stream are asynchronous on it unless stated; NULL is the legacy default
+ *     stream.  No call aborts or exits: every call returns an mf_status and, on failure, leaves a
+ *     message for mf_last_error() in the calling thread.
+ */
+#ifndef MF_H_
+#define MF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mf_stream; /* identical to cudaStream_t */
+
+typedef enum {
+  MF_OK = 0,
+  MF_NOT_CONVERGED = 1,    /* solver stopped at max_iter above the tolerance (x is still valid) */
+  MF_ERR_ARG = -1,         /* invalid argument (null pointer, size, aliasing, bad option) */
+  MF_ERR_CUDA = -2,        /* a CUDA runtime call failed (message names it) */
+  MF_ERR_MESH = -3,        /* invalid mesh: det J <= 0, node id out of range, NaN, bad material */
+  MF_ERR_OOM = -4,         /* device allocation failed */
+  MF_ERR_BREAKDOWN = -5,   /* CG breakdown: p^T A p <= 0 or a NaN/Inf scalar */
+  MF_ERR_TIMEOUT = -6,     /* wall-clock budget of a solve exhausted */
+  MF_ERR_UNSUPPORTED = -7  /* operation not available for this mesh or physics */
+} mf_status;
+
+enum { MF_LAPLACE = 0, MF_ELASTICITY = 1 };
+
+typedef struct mf_mesh mf_mesh;
+typedef struct mf_csr mf_csr;
+
+/*
+ * mf_setup_mesh - validate a Q1 hexahedral mesh and build the operator's device data.
+ *
+ * The inputs of Algorithm 1 (support-point coordinates) plus the cell constants of Table 2.
+ *   physics    MF_LAPLACE (1 DoF per node) or MF_ELASTICITY (3 DoFs per node).
+ *   n_nodes    N >= 8; n_cells E >= 1.
+ *   coords     device double[N][3], node coordinates.
+ *   cells      device int32[E][8] element -> node map in the corner order above, or NULL for a
+ *              structured nx x ny x nz box numbered as above (then E must equal nx*ny*nz and N
+ *              must equal (nx+1)(ny+1)(nz+1); coordinates may still be arbitrary).
+ *   mat        device double[E] (Laplace: conductivity kappa_e > 0) or double[E][2] (elasticity:
+ *              Young's modulus E_e > 0 and Poisson ratio -1 < nu_e < 0.5).
+ *   dirichlet  device uint8[N] (nonzero = all DoFs of that node constrained) or NULL (none).
+ * The library copies what it needs into its own layout; the caller's arrays may be freed after the
+ * call returns.  Synchronises `stream`.  Errors: MF_ERR_ARG, MF_ERR_MESH (det J <= 0 at a Gauss
+ * point or corner, node id out of range, non-finite coordinate or material), MF_ERR_OOM,
+ * MF_ERR_CUDA.  *out is NULL on failure.
+ */
+mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells, const double *coords,
+                        const int32_t *cells, int32_t nx, int32_t ny, int32_t nz, const double *mat,
+                        const uint8_t *dirichlet, mf_stream stream, mf_mesh **out);
+
+/* Frees every device buffer the handle owns (synchronises the device first).  NULL is a no-op. */
+mf_status mf_destroy_mesh(mf_mesh *mesh);
+
+/* Host outputs (any may be NULL): node, cell and DoF counts, free (unconstrained) DoFs, number of
+ * element colours of the scatter, and flags (bit 0: structured, bit 1: every cell affine). */
+mf_status mf_mesh_query(const mf_mesh *mesh, int64_t *n_nodes, int64_t *n_cells, int64_t *n_dof,
+                        int64_t *n_free, int32_t *n_colours, int32_t *flags);
+
+/*
+ * Kernel variants for the operator apply (mf_set_apply_variant):
+ *   MF_VARIANT_AUTO       fastest variant that meets FP64 accuracy for this mesh (default)
+ *   MF_VARIANT_REFERENCE  Algorithm 1 as printed: one thread per element, FP64 arithmetic,
+ *                         Jacobian at every quadrature point, colour-by-colour scatter
+ */
+enum { MF_VARIANT_AUTO = 0, MF_VARIANT_REFERENCE = 1 };
+mf_status mf_set_apply_variant(mf_mesh *mesh, int variant);
+
+/*
+ * mf_apply_laplace - y = A x for the scalar Laplace operator, matrix-free (Eqs. 4 and 7 with the
+ * per-cell factor kappa_e; Algorithm 1 with sigma replaced by the flux).
+ *   x  device double[N], input; entries on Dirichlet nodes are ignored except that y_d = x_d.
+ *   y  device double[N], output, overwritten.  Must not overlap x.
+ * Asynchronous on `stream`, allocates nothing, deterministic (bitwise-reproducible: the scatter
+ * uses no atomics).  Errors: MF_ERR_ARG (null, aliasing, mesh is not Laplace), MF_ERR_CUDA.
+ */
+mf_status mf_apply_laplace(const mf_mesh *mesh, const double *x, double *y, mf_stream stream);
+
+/*
+ * mf_apply_elasticity - y = A x for isotropic linear elasticity (Eqs. 6 and 9, Algorithm 1):
+ * sigma = lam tr(eps) I + 2 mu eps, eps = sym grad u, (lam, mu) from each cell's (E, nu).
+ *   x, y  device double[3N], xyz interleaved.  Same contract as mf_apply_laplace.
+ */
+mf_status mf_apply_elasticity(const mf_mesh *mesh, const double *x, double *y, mf_stream stream);
+
+/*
+ * mf_apply_f32 - the same operator (either physics) evaluated entirely in FP32: geometry from FP32
+ * copies of the coordinates and cell constants, FP32 x and y.  Used by the mixed-precision solver.
+ *   x, y  device float[N * ndof_per_node].  Same contract otherwise.
+ */
+mf_status mf_apply_f32(const mf_mesh *mesh, const float *x, float *y, mf_stream stream);
+
+/*
+ * mf_apply_multi - Y = A X for nrhs right-hand sides at once; geometry evaluated once per element
+ * and reused for every right-hand side.
+ *   X, Y  device double[N][nrhs][ndof_per_node] (node-major, then right-hand side, then
+ *         component).  1 <= nrhs <= 16.  Same contract as the single apply.
+ */
+mf_status mf_apply_multi(const mf_mesh *mesh, int32_t nrhs, const double *X, double *Y, mf_stream stream);
+
+/*
+ * mf_assemble_csr - assemble the global matrix (Sec. 3, matrix-based operator): the element
+ * matrices of Eqs. 4/6 are summed into a CSR matrix whose rows follow the DoF numbering; the fill
+ * adds each element's rows without atomics (elements of one colour share no node).
+ *   Rows of Dirichlet DoFs hold the single entry 1 on the diagonal; their columns are removed from
+ *   the other rows.  Columns are sorted within each row.  Index types: int64 row pointers, int32
+ *   column indices, double values (12 bytes per non-zero as in Table 1).
+ * Synchronises `stream`.  Errors: MF_ERR_OOM, MF_ERR_CUDA, MF_ERR_ARG.
+ */
+mf_status mf_assemble_csr(const mf_mesh *mesh, mf_stream stream, mf_csr **out);
+
+/* Host outputs (any may be NULL): rows, non-zeros and the DEVICE arrays (owned by the handle). */
+mf_status mf_csr_query(const mf_csr *csr, int64_t *n_rows, int64_t *nnz, const int64_t **rowptr,
+                       const int32_t **col, const double **val);
+
+/* Copy the matrix into caller-owned device arrays: rowptr int64[n_rows+1], col int32[nnz],
+ * val double[nnz].  Asynchronous on `stream`.  Errors: MF_ERR_ARG, MF_ERR_CUDA. */
+mf_status mf_csr_export(const mf_csr *csr, int64_t *rowptr, int32_t *col, double *val, mf_stream stream);
+
+/* y = A x with the assembled matrix.  x, y device double[n_rows], must not overlap.  Asynchronous,
+ * allocates nothing, deterministic. */
+mf_status mf_spmv_csr(const mf_csr *csr, const double *x, double *y, mf_stream stream);
+
+mf_status mf_destroy_csr(mf_csr *csr);
+
+/* Solver options (mf_cg_solve). */
+enum { MF_OP_MATFREE = 0, MF_OP_CSR = 1 };
+enum { MF_PREC_FP64 = 0, MF_PREC_MIXED_IR = 1 };
+enum { MF_PC_NONE = 0, MF_PC_JACOBI = 1 };
+
+typedef struct {
+  int32_t op;            /* MF_OP_MATFREE or MF_OP_CSR (then `csr` must be set) */
+  int32_t precision;     /* MF_PREC_FP64, or MF_PREC_MIXED_IR: FP32 inner CG, FP64 refinement */
+  int32_t precond;       /* MF_PC_NONE or MF_PC_JACOBI (FP64 only) */
+  int32_t max_iter;      /* > 0; for MIXED_IR the total inner iterations */
+  double rtol;           /* stop when ||r||_2 <= rtol ||b||_2 (FP64 residual for MIXED_IR) */
+  int32_t check_every;   /* iterations per CUDA-graph launch between host convergence checks */
+  int32_t use_graph;     /* 1: capture check_every iterations in a CUDA graph; 0: plain launches */
+  double timeout_s;      /* wall-clock budget, <= 0 for none */
+  double inner_rtol;     /* MIXED_IR: relative tolerance of each inner FP32 solve (e.g. 1e-4) */
+  int32_t max_outer;     /* MIXED_IR: refinement steps */
+  const mf_csr *csr;     /* operator when op == MF_OP_CSR */
+} mf_solve_opts;
+
+typedef struct {
+  int32_t iters;          /* operator applies inside the Krylov loop(s) */
+  int32_t outer_iters;    /* refinement steps (MIXED_IR), else 0 */
+  int32_t status;         /* same value as the return code */
+  int32_t reserved;
+  double rel_res;         /* ||r_k|| / ||b|| from the recurrence (inner FP64 residual for IR) */
+  double rel_res_true;    /* ||b - A x|| / ||b|| recomputed with the FP64 operator after the solve */
+  double seconds;         /* wall time of the call */
+} mf_solve_info;
+
+/* Fills *opts with defaults: matrix-free, FP64, no preconditioner, rtol 1e-8, max_iter 100000,
+ * check_every 32, graphs on, no timeout, inner_rtol 1e-4, max_outer 50. */
+void mf_solve_opts_default(mf_solve_opts *opts);
+
+/*
+ * mf_cg_solve - solve A x = b by conjugate gradient (Table 4: per iteration one apply, the dots
+ * p^T A p and r^T r, and the updates of x, r, p), starting from x0 = 0.
+ *   b     device double[n_dof], right-hand side (Dirichlet entries are the prescribed values,
+ *         normally 0).
+ *   x     device double[n_dof], output solution (its input content is ignored).
+ *   info  host, may be NULL.
+ * The scalars alpha, beta and the residual norm stay on the device; the dots use a deterministic
+ * two-level reduction fused into the update kernels; `check_every` iterations run per CUDA-graph
+ * launch and the host reads a convergence flag between launches.  Synchronises `stream` before
+ * returning.  Workspace (a few DoF vectors) is allocated on the first call per mesh and kept by the
+ * handle.  Returns MF_OK, MF_NOT_CONVERGED, MF_ERR_BREAKDOWN, MF_ERR_TIMEOUT, MF_ERR_ARG,
+ * MF_ERR_OOM or MF_ERR_CUDA.
+ */
+mf_status mf_cg_solve(mf_mesh *mesh, const mf_solve_opts *opts, const double *b, double *x,
+                      mf_solve_info *info, mf_stream stream);
+
+/* Message describing the last failure in the calling thread ("" if none).  Valid until the next
+ * failing call in the same thread. */
+const char *mf_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far (kernels replayed by a
+ * CUDA graph count once per replay).  Host call, thread-safe; for accounting in benchmarks. */
+int64_t mf_kernel_launches(void);
+
+/* Library version string (host). */
+const char *mf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H_ */

@@ -1,0 +1,262 @@
+// Matrix-free operator apply, reference variant: Algorithm 1 with one thread per element.
+//
+// Each thread gathers its element's 8 support points and input values (Alg. 1, gather step),
+// evaluates the Jacobian, its inverse and determinant at every Gauss point, applies the flux /
+// stress, and adds v^e into y (Alg. 1, final step).  The paper does not say how the final
+// additions avoid races; here the elements are split into colours whose elements share no node
+// (2x2x2 parity classes on a structured box, a greedy colouring otherwise), one launch per colour,
+// so every addition is a plain read-modify-write in a fixed order: no atomics, bitwise
+// reproducible.
+#include "mf_element.cuh"
+#include "mf_internal.cuh"
+
+namespace {
+
+// Element index of thread t in colour c of a structured box (parity class (c&1, c>>1&1, c>>2&1)).
+__device__ __forceinline__ int64_t parity_element(int64_t t, int c, int nx, int ny, int nz) {
+  const int px = c & 1, py = (c >> 1) & 1, pz = (c >> 2) & 1;
+  const int64_t cnx = (nx - px + 1) / 2, cny = (ny - py + 1) / 2;
+  const int64_t ix = t % cnx, r = t / cnx, iy = r % cny, iz = r / cny;
+  return (2 * ix + px) + (int64_t)nx * ((2 * iy + py) + (int64_t)ny * (2 * iz + pz));
+}
+
+template <int PHYS, typename R>
+__global__ void __launch_bounds__(128) apply_ref_colour(MeshView m, const R *__restrict__ x, R *__restrict__ y,
+                                                        int colour, int64_t count, const int32_t *__restrict__ celems,
+                                                        const int *__restrict__ skip) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count || (skip && *skip)) return;
+  const int64_t e = celems ? (int64_t)celems[t] : parity_element(t, colour, m.nx, m.ny, m.nz);
+  int64_t nodes[8];
+  element_nodes(m, e, nodes);
+  const R *Xc = coords_of<R>(m);
+  const R *mat = mat_of<R>(m);
+  R X[8][3];
+  bool dir[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    X[a][0] = Xc[3 * nodes[a]];
+    X[a][1] = Xc[3 * nodes[a] + 1];
+    X[a][2] = Xc[3 * nodes[a] + 2];
+    dir[a] = m.dmask[nodes[a]] != 0;
+  }
+  if (PHYS == MF_LAPLACE) {
+    R u[8], v[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) u[a] = dir[a] ? (R)0 : x[nodes[a]];
+    q1::laplace_element<R>(X, u, mat[e], v);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!dir[a]) y[nodes[a]] += v[a];
+  } else {
+    R u[8][3], v[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u[a][k] = dir[a] ? (R)0 : x[3 * nodes[a] + k];
+    q1::elasticity_element<R>(X, u, mat[2 * e], mat[2 * e + 1], v);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!dir[a]) {
+        y[3 * nodes[a]] += v[a][0];
+        y[3 * nodes[a] + 1] += v[a][1];
+        y[3 * nodes[a] + 2] += v[a][2];
+      }
+  }
+}
+
+// Multi right-hand-side reference apply: the geometry (adjugate and determinant at every Gauss
+// point) is computed once per element and reused for each right-hand side.  Layout [node][rhs][k].
+template <int PHYS>
+__global__ void __launch_bounds__(128) apply_multi_colour(MeshView m, const double *__restrict__ x,
+                                                          double *__restrict__ y, int nrhs, int colour, int64_t count,
+                                                          const int32_t *__restrict__ celems) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t e = celems ? (int64_t)celems[t] : parity_element(t, colour, m.nx, m.ny, m.nz);
+  int64_t nodes[8];
+  element_nodes(m, e, nodes);
+  double X[8][3];
+  bool dir[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) X[a][i] = m.X[3 * nodes[a] + i];
+    dir[a] = m.dmask[nodes[a]] != 0;
+  }
+  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  double Cq[8][3][3], idet[8];
+#define MF_GEOM(Q)                                        \
+  {                                                       \
+    double J[3][3];                                       \
+    q1::jacobian<double, Q>(X, J);                        \
+    idet[Q] = 1.0 / q1::adjugate(J, Cq[Q]);               \
+  }
+  MF_GEOM(0) MF_GEOM(1) MF_GEOM(2) MF_GEOM(3) MF_GEOM(4) MF_GEOM(5) MF_GEOM(6) MF_GEOM(7)
+#undef MF_GEOM
+  const double c0 = PHYS == MF_LAPLACE ? m.mat[e] : m.mat[2 * e];
+  const double c1 = PHYS == MF_LAPLACE ? 0.0 : m.mat[2 * e + 1];
+  for (int r = 0; r < nrhs; ++r) {
+    double u[8][ND], v[8][ND];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int k = 0; k < ND; ++k) {
+        u[a][k] = dir[a] ? 0.0 : x[((int64_t)nodes[a] * nrhs + r) * ND + k];
+        v[a][k] = 0.0;
+      }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double(&C)[3][3] = Cq[q];
+      if (PHYS == MF_LAPLACE) {
+        double g[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          double s = 0;
+#pragma unroll
+          for (int a = 0; a < 8; ++a) s += u[a][0] * q1::dN(q, a, j);
+          g[j] = s;
+        }
+        double tt[3], f[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tt[k] = C[0][k] * g[0] + C[1][k] * g[1] + C[2][k] * g[2];
+        const double sc = c0 * idet[q];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f[j] = sc * (C[j][0] * tt[0] + C[j][1] * tt[1] + C[j][2] * tt[2]);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) v[a][0] += q1::dN(q, a, 0) * f[0] + q1::dN(q, a, 1) * f[1] + q1::dN(q, a, 2) * f[2];
+      } else {
+        double H[3][3], G[3][3], S[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            double s = 0;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) s += u[a][k % ND] * q1::dN(q, a, j);
+            H[k][j] = s;
+          }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int l = 0; l < 3; ++l) G[k][l] = (H[k][0] * C[0][l] + H[k][1] * C[1][l] + H[k][2] * C[2][l]) * idet[q];
+        const double tr = G[0][0] + G[1][1] + G[2][2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int l = 0; l < 3; ++l) S[k][l] = c1 * (G[k][l] + G[l][k]) + (k == l ? c0 * tr : 0.0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          double P[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) P[j] = S[k][0] * C[j][0] + S[k][1] * C[j][1] + S[k][2] * C[j][2];
+#pragma unroll
+          for (int a = 0; a < 8; ++a) v[a][k % ND] += P[0] * q1::dN(q, a, 0) + P[1] * q1::dN(q, a, 1) + P[2] * q1::dN(q, a, 2);
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!dir[a])
+#pragma unroll
+        for (int k = 0; k < ND; ++k) y[((int64_t)nodes[a] * nrhs + r) * ND + k] += v[a][k];
+  }
+}
+
+// Dirichlet rows: y_d = x_d.
+template <typename R>
+__global__ void dirichlet_rows(const int32_t *__restrict__ dn, int64_t n, int ndw, const R *__restrict__ x,
+                               R *__restrict__ y, const int *__restrict__ skip) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n * ndw || (skip && *skip)) return;
+  const int64_t node = dn[i / ndw];
+  const int64_t k = i % ndw;
+  y[node * ndw + k] = x[node * ndw + k];
+}
+
+template <typename R>
+mf_status apply_reference(const mf_mesh *m, const R *x, R *y, cudaStream_t s, const int *skip) {
+  MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * sizeof(R), s));
+  const MeshView v = m->view();
+  for (int c = 0; c < m->n_colours; ++c) {
+    const int64_t cnt = colour_count(m, c);
+    if (cnt == 0) continue;
+    const int32_t *ce = m->structured ? nullptr : m->colour_elems + m->colour_off[c];
+    mf_count_launches(1);
+    if (m->physics == MF_LAPLACE)
+      apply_ref_colour<MF_LAPLACE, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, c, cnt, ce, skip);
+    else
+      apply_ref_colour<MF_ELASTICITY, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, c, cnt, ce, skip);
+  }
+  if (m->n_dnodes) mf_count_launches(1);
+  if (m->n_dnodes)
+    dirichlet_rows<R><<<blocks_for(m->n_dnodes * m->ndpn), kThreads, 0, s>>>(m->dnodes, m->n_dnodes, m->ndpn, x, y, skip);
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
+}  // namespace
+
+mf_status apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip) {
+  return apply_reference<double>(m, x, y, s, skip);
+}
+
+mf_status apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip) {
+  return apply_reference<float>(m, x, y, s, skip);
+}
+
+mf_status apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s) {
+  MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * nrhs * sizeof(double), s));
+  const MeshView v = m->view();
+  for (int c = 0; c < m->n_colours; ++c) {
+    const int64_t cnt = colour_count(m, c);
+    if (cnt == 0) continue;
+    const int32_t *ce = m->structured ? nullptr : m->colour_elems + m->colour_off[c];
+    mf_count_launches(1);
+    if (m->physics == MF_LAPLACE)
+      apply_multi_colour<MF_LAPLACE><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, c, cnt, ce);
+    else
+      apply_multi_colour<MF_ELASTICITY><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, c, cnt, ce);
+  }
+  if (m->n_dnodes) mf_count_launches(1);
+  if (m->n_dnodes)
+    dirichlet_rows<double><<<blocks_for(m->n_dnodes * m->ndpn * nrhs), kThreads, 0, s>>>(
+        m->dnodes, m->n_dnodes, m->ndpn * nrhs, x, y, nullptr);
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
+// ----------------------------------------------------------------------------- entry points ----
+static mf_status check_apply_args(const mf_mesh *m, const void *x, void *y, size_t bytes) {
+  MF_ARG(m && x && y, "apply: null argument");
+  const char *xb = (const char *)x, *yb = (const char *)y;
+  MF_ARG(xb + bytes <= yb || yb + bytes <= xb, "apply: x and y overlap");
+  return MF_OK;
+}
+
+extern "C" mf_status mf_apply_laplace(const mf_mesh *m, const double *x, double *y, mf_stream stream) {
+  mf_clear_error();
+  MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(double) : 0));
+  MF_ARG(m->physics == MF_LAPLACE, "mf_apply_laplace: mesh was set up for elasticity");
+  return apply_fp64(m, x, y, (cudaStream_t)stream);
+}
+
+extern "C" mf_status mf_apply_elasticity(const mf_mesh *m, const double *x, double *y, mf_stream stream) {
+  mf_clear_error();
+  MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(double) : 0));
+  MF_ARG(m->physics == MF_ELASTICITY, "mf_apply_elasticity: mesh was set up for Laplace");
+  return apply_fp64(m, x, y, (cudaStream_t)stream);
+}
+
+extern "C" mf_status mf_apply_f32(const mf_mesh *m, const float *x, float *y, mf_stream stream) {
+  mf_clear_error();
+  MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(float) : 0));
+  return apply_fp32(m, x, y, (cudaStream_t)stream);
+}
+
+extern "C" mf_status mf_apply_multi(const mf_mesh *m, int32_t nrhs, const double *X, double *Y, mf_stream stream) {
+  mf_clear_error();
+  MF_ARG(nrhs >= 1 && nrhs <= 16, "mf_apply_multi: nrhs must be in [1, 16]");
+  MF_TRY(check_apply_args(m, X, Y, m ? m->n_dof * nrhs * sizeof(double) : 0));
+  return apply_multi_fp64(m, nrhs, X, Y, (cudaStream_t)stream);
+}

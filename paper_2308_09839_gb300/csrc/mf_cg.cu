@@ -1,0 +1,498 @@
+// Conjugate gradient on the device (the per-iteration operations of Table 4), with the scalars
+// alpha, beta and the residual norms kept in device memory.
+//
+// The paper observes that the dot-product implementation decides CG performance (Sec. 6, the
+// "dot" figure) and leaves kernel fusion undone.  Here each dot is fused into the vector update
+// that produces its operand, and reduced with a fixed two-level tree (per-block partials in a
+// fixed grid-stride partition, summed in index order by the last block to finish): results are
+// bitwise reproducible and no host round trip is needed per iteration.  `check_every` iterations
+// are captured in one CUDA graph; every kernel first reads a device "done" flag, so iterations
+// after convergence cost only their launch.
+//
+// Per iteration (FP64, no preconditioner), in DoF-vector passes:
+//   apply A p -> Ap                     (operator)
+//   pAp = p.Ap; alpha = rho/pAp          read p, Ap
+//   x += alpha p; r -= alpha Ap; rho' = r.r   read x, p, r, Ap; write x, r
+//   p = r + beta p                       read r, p; write p
+#include <chrono>
+#include <cmath>
+#include <functional>
+
+#include "mf_internal.cuh"
+
+namespace {
+
+constexpr int kRedBlocks = 608;  // 4 per SM on 152 SMs; fixed so the reduction tree is fixed
+constexpr int kRedThreads = 256;
+
+struct CgScalars {
+  double bb, rr, rz, pAp, alpha, beta, tol2, res2;
+  int iter, max_iter, done, status;
+  unsigned int ticket;
+  int pad;
+};
+
+// Sum NV per-thread values over the whole grid.  Returns true in the last block to arrive, whose
+// thread 0 then holds the totals in `out`.  Every block of the launch must call it.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double *partials, unsigned int *ticket, double (&out)[NV]) {
+  __shared__ double sh[NV][kRedThreads / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0) sh[k][w] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < kRedThreads / 32; ++i) s += sh[k][i];
+      partials[k * gridDim.x + blockIdx.x] = s;
+    }
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  const volatile double *vp = partials;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += vp[k * gridDim.x + i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    __syncthreads();
+    if (lane == 0) sh[k][w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < kRedThreads / 32; ++i) s += sh[k][i];
+      out[k] = s;
+    }
+    *ticket = 0;
+  }
+  return true;
+}
+
+#define GRID_STRIDE(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// x = 0, r = b, p = z = M r; rho = r.z, ||b||^2.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) cg_init(int64_t n, const R *__restrict__ b, R *__restrict__ x,
+                                                       R *__restrict__ r, R *__restrict__ p,
+                                                       const double *__restrict__ invdiag, double *partials,
+                                                       CgScalars *sc, double rtol, int max_iter) {
+  double v[2] = {0.0, 0.0};
+  GRID_STRIDE(i, n) {
+    const R bi = b[i];
+    x[i] = (R)0;
+    r[i] = bi;
+    const double z = invdiag ? (double)bi * invdiag[i] : (double)bi;
+    p[i] = (R)z;
+    v[0] += (double)bi * (double)bi;
+    v[1] += (double)bi * z;
+  }
+  double out[2];
+  if (grid_reduce<2>(v, partials, &sc->ticket, out) && threadIdx.x == 0) {
+    sc->bb = out[0];
+    sc->rr = out[0];
+    sc->rz = out[1];
+    sc->tol2 = rtol * rtol * out[0];
+    sc->iter = 0;
+    sc->max_iter = max_iter;
+    sc->status = 0;
+    sc->done = (out[0] <= sc->tol2) ? 1 : 0;
+    if (!isfinite(out[0])) {
+      sc->status = MF_ERR_BREAKDOWN;
+      sc->done = 1;
+    }
+  }
+}
+
+// pAp = p.Ap; alpha = rho / pAp.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) cg_pap(int64_t n, const R *__restrict__ p, const R *__restrict__ Ap,
+                                                      double *partials, CgScalars *sc) {
+  if (sc->done) return;
+  double v[1] = {0.0};
+  GRID_STRIDE(i, n) v[0] += (double)p[i] * (double)Ap[i];
+  double out[1];
+  if (grid_reduce<1>(v, partials, &sc->ticket, out) && threadIdx.x == 0) {
+    const double pap = out[0];
+    sc->pAp = pap;
+    if (!(pap > 0.0) || !isfinite(pap)) {
+      sc->status = MF_ERR_BREAKDOWN;
+      sc->done = 1;
+    } else {
+      sc->alpha = sc->rz / pap;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha Ap; rho' = r.z (z = M r), ||r||^2; beta = rho'/rho; convergence test.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) cg_update_xr(int64_t n, R *__restrict__ x, R *__restrict__ r,
+                                                            const R *__restrict__ p, const R *__restrict__ Ap,
+                                                            const double *__restrict__ invdiag, double *partials,
+                                                            CgScalars *sc) {
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  double v[2] = {0.0, 0.0};
+  GRID_STRIDE(i, n) {
+    x[i] = (R)((double)x[i] + alpha * (double)p[i]);
+    const R ri = (R)((double)r[i] - alpha * (double)Ap[i]);
+    r[i] = ri;
+    const double rd = (double)ri;
+    v[0] += rd * rd;
+    v[1] += invdiag ? rd * rd * invdiag[i] : rd * rd;
+  }
+  double out[2];
+  if (grid_reduce<2>(v, partials, &sc->ticket, out) && threadIdx.x == 0) {
+    const double rr = out[0], rz = out[1];
+    sc->beta = rz / sc->rz;
+    sc->rr = rr;
+    sc->rz = rz;
+    sc->iter += 1;
+    if (!isfinite(rr) || !isfinite(rz)) {
+      sc->status = MF_ERR_BREAKDOWN;
+      sc->done = 1;
+    } else if (rr <= sc->tol2) {
+      sc->done = 1;
+    } else if (sc->iter >= sc->max_iter) {
+      sc->status = MF_NOT_CONVERGED;
+      sc->done = 1;
+    }
+  }
+}
+
+// p = z + beta p.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) cg_update_p(int64_t n, const R *__restrict__ r, R *__restrict__ p,
+                                                           const double *__restrict__ invdiag, const CgScalars *sc) {
+  if (sc->done) return;
+  const double beta = sc->beta;
+  GRID_STRIDE(i, n) {
+    const double z = invdiag ? (double)r[i] * invdiag[i] : (double)r[i];
+    p[i] = (R)(z + beta * (double)p[i]);
+  }
+}
+
+// res = b - Ax (stored when `res` is not null); res2 = ||b - Ax||^2.
+__global__ void __launch_bounds__(kRedThreads) residual_kernel(int64_t n, const double *__restrict__ b,
+                                                               const double *__restrict__ Ax, double *__restrict__ res,
+                                                               double *partials, CgScalars *sc) {
+  double v[1] = {0.0};
+  GRID_STRIDE(i, n) {
+    const double ri = b[i] - Ax[i];
+    if (res) res[i] = ri;
+    v[0] += ri * ri;
+  }
+  double out[1];
+  if (grid_reduce<1>(v, partials, &sc->ticket, out) && threadIdx.x == 0) sc->res2 = out[0];
+}
+
+__global__ void invert_kernel(int64_t n, double *d) {
+  GRID_STRIDE(i, n) d[i] = 1.0 / d[i];
+}
+
+__global__ void to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+  GRID_STRIDE(i, n) b[i] = (float)a[i];
+}
+
+__global__ void add_f32(int64_t n, double *__restrict__ x, const float *__restrict__ d) {
+  GRID_STRIDE(i, n) x[i] += (double)d[i];
+}
+
+using OpFn = std::function<mf_status(const void *in, void *out, cudaStream_t s, const int *skip)>;
+
+}  // namespace
+
+struct CgWorkspace {
+  int64_t n = 0;
+  double *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *invdiag = nullptr, *bb = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr;
+  double *partials = nullptr;
+  CgScalars *sc = nullptr, *sc32 = nullptr;
+  CgScalars *h_sc = nullptr;
+  cudaStream_t cap = nullptr;
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    long long key = -1;
+    int64_t kernels = 0;  // kernel nodes per replay
+  } g[2];
+  int variant_at_diag = -1;
+};
+
+void cg_workspace_free(CgWorkspace *w) {
+  if (!w) return;
+  for (auto &g : w->g)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  cudaFree(w->x); cudaFree(w->r); cudaFree(w->p); cudaFree(w->Ap); cudaFree(w->invdiag); cudaFree(w->bb);
+  cudaFree(w->x32); cudaFree(w->r32); cudaFree(w->p32); cudaFree(w->Ap32);
+  cudaFree(w->partials); cudaFree(w->sc); cudaFree(w->sc32);
+  if (w->h_sc) cudaFreeHost(w->h_sc);
+  if (w->cap) cudaStreamDestroy(w->cap);
+  delete w;
+}
+
+namespace {
+
+mf_status ensure_workspace(mf_mesh *m, bool need32, bool needdiag) {
+  if (!m->cg) {
+    CgWorkspace *w = new CgWorkspace();
+    m->cg = w;
+    w->n = m->n_dof;
+    const size_t nb = w->n * sizeof(double);
+    MF_CUDA(cudaMalloc(&w->x, nb));
+    MF_CUDA(cudaMalloc(&w->r, nb));
+    MF_CUDA(cudaMalloc(&w->p, nb));
+    MF_CUDA(cudaMalloc(&w->Ap, nb));
+    MF_CUDA(cudaMalloc(&w->partials, 4 * kRedBlocks * sizeof(double)));
+    MF_CUDA(cudaMalloc(&w->sc, sizeof(CgScalars)));
+    MF_CUDA(cudaMalloc(&w->sc32, sizeof(CgScalars)));
+    MF_CUDA(cudaMemset(w->sc, 0, sizeof(CgScalars)));
+    MF_CUDA(cudaMemset(w->sc32, 0, sizeof(CgScalars)));
+    MF_CUDA(cudaMallocHost(&w->h_sc, 2 * sizeof(CgScalars)));
+    MF_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+  }
+  CgWorkspace *w = m->cg;
+  if (need32 && !w->x32) {
+    const size_t nf = w->n * sizeof(float);
+    MF_CUDA(cudaMalloc(&w->x32, nf));
+    MF_CUDA(cudaMalloc(&w->r32, nf));
+    MF_CUDA(cudaMalloc(&w->p32, nf));
+    MF_CUDA(cudaMalloc(&w->Ap32, nf));
+  }
+  if (needdiag && !w->invdiag) MF_CUDA(cudaMalloc(&w->invdiag, w->n * sizeof(double)));
+  return MF_OK;
+}
+
+// One CG iteration (Table 4) for vectors of type R.
+template <typename R>
+mf_status cg_iteration(const OpFn &op, int64_t n, R *x, R *r, R *p, R *Ap, const double *invdiag, double *partials,
+                       CgScalars *sc, cudaStream_t s) {
+  MF_TRY(op(p, Ap, s, &sc->done));
+  mf_count_launches(3);
+  cg_pap<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, p, Ap, partials, sc);
+  cg_update_xr<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, Ap, invdiag, partials, sc);
+  cg_update_p<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, r, p, invdiag, sc);
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
+// Run the CG loop that cg_init prepared: blocks of `k` iterations (graph or plain launches),
+// host reads the done flag after each block.
+template <typename R>
+mf_status cg_loop(CgWorkspace *w, int slot, long long key, const OpFn &op, int64_t n, R *x, R *r, R *p, R *Ap,
+                  const double *invdiag, CgScalars *sc, int k, bool use_graph, double deadline_s,
+                  std::chrono::steady_clock::time_point t0, cudaStream_t s, CgScalars *host) {
+  auto body = [&](cudaStream_t st) -> mf_status {
+    for (int it = 0; it < k; ++it) MF_TRY(cg_iteration<R>(op, n, x, r, p, Ap, invdiag, w->partials, sc, st));
+    return MF_OK;
+  };
+  CgWorkspace::Graph &g = w->g[slot];
+  if (use_graph && (g.exec == nullptr || g.key != key)) {
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    cudaGraph_t graph;
+    MF_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = mf_launches_now();
+    mf_status st = body(w->cap);
+    g.kernels = mf_launches_now() - before;
+    mf_count_launches(-g.kernels);  // captured, not launched: counted per replay below
+    cudaError_t ce = cudaStreamEndCapture(w->cap, &graph);
+    if (st != MF_OK) return st;
+    if (ce != cudaSuccess) {
+      mf_set_error("CG graph capture failed: %s", cudaGetErrorString(ce));
+      return MF_ERR_CUDA;
+    }
+    ce = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      g.exec = nullptr;
+      mf_set_error("CG graph instantiation failed: %s", cudaGetErrorString(ce));
+      return MF_ERR_CUDA;
+    }
+    g.key = key;
+  }
+  for (;;) {
+    if (use_graph) {
+      MF_CUDA(cudaGraphLaunch(g.exec, s));
+      mf_count_launches(g.kernels);
+    }
+    else MF_TRY(body(s));
+    MF_CUDA(cudaMemcpyAsync(host, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    if (host->done) return MF_OK;
+    if (deadline_s > 0) {
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > deadline_s) {
+        mf_set_error("mf_cg_solve: timeout after %.3f s (%d iterations)", el, host->iter);
+        return MF_ERR_TIMEOUT;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" void mf_solve_opts_default(mf_solve_opts *o) {
+  if (!o) return;
+  o->op = MF_OP_MATFREE;
+  o->precision = MF_PREC_FP64;
+  o->precond = MF_PC_NONE;
+  o->max_iter = 100000;
+  o->rtol = 1e-8;
+  o->check_every = 32;
+  o->use_graph = 1;
+  o->timeout_s = 0.0;
+  o->inner_rtol = 1e-4;
+  o->max_outer = 50;
+  o->csr = nullptr;
+}
+
+extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double *x, mf_solve_info *info,
+                                 mf_stream stream) {
+  mf_clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  MF_ARG(m && o && b && x, "mf_cg_solve: null argument");
+  MF_ARG(o->op == MF_OP_MATFREE || o->op == MF_OP_CSR, "mf_cg_solve: unknown op %d", o->op);
+  MF_ARG(o->op == MF_OP_MATFREE || o->csr != nullptr, "mf_cg_solve: op CSR needs opts->csr");
+  MF_ARG(o->op == MF_OP_MATFREE || o->csr->n_rows == m->n_dof, "mf_cg_solve: CSR size does not match the mesh");
+  MF_ARG(o->precision == MF_PREC_FP64 || o->precision == MF_PREC_MIXED_IR, "mf_cg_solve: unknown precision");
+  MF_ARG(o->precond == MF_PC_NONE || o->precond == MF_PC_JACOBI, "mf_cg_solve: unknown preconditioner");
+  MF_ARG(o->precision == MF_PREC_FP64 || o->precond == MF_PC_NONE, "mf_cg_solve: MIXED_IR takes no preconditioner");
+  MF_ARG(o->precision == MF_PREC_FP64 || o->op == MF_OP_MATFREE, "mf_cg_solve: MIXED_IR needs the matrix-free operator");
+  MF_ARG(o->max_iter > 0 && o->rtol > 0 && o->check_every > 0, "mf_cg_solve: bad max_iter/rtol/check_every");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool mixed = o->precision == MF_PREC_MIXED_IR;
+  const bool jac = o->precond == MF_PC_JACOBI;
+  MF_TRY(ensure_workspace(m, mixed, jac));
+  CgWorkspace *w = m->cg;
+  const int64_t n = m->n_dof;
+  if (jac) {
+    MF_TRY(operator_diagonal(m, w->invdiag, s));
+    mf_count_launches(1);
+    invert_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, w->invdiag);
+  }
+  const mf_csr *A = o->csr;
+  OpFn op64 = [m, A, o](const void *in, void *out, cudaStream_t st, const int *skip) -> mf_status {
+    if (o->op == MF_OP_CSR) return spmv(A, (const double *)in, (double *)out, st, skip);
+    return apply_fp64(m, (const double *)in, (double *)out, st, skip);
+  };
+  OpFn op32 = [m](const void *in, void *out, cudaStream_t st, const int *skip) -> mf_status {
+    return apply_fp32(m, (const float *)in, (float *)out, st, skip);
+  };
+  const long long key64 = ((long long)o->op << 40) ^ ((long long)o->precond << 36) ^ ((long long)m->variant << 32) ^
+                          ((long long)(intptr_t)A & 0xffffffffll) ^ ((long long)o->check_every << 44);
+  const long long key32 = ((long long)m->variant << 32) ^ ((long long)o->check_every << 44) ^ 0x5a5a;
+  mf_status st = MF_OK;
+  int iters = 0, outer = 0;
+  double rel_rec = 0.0;
+  CgScalars *h = w->h_sc;
+  if (!mixed) {
+    mf_count_launches(1);
+    cg_init<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->x, w->r, w->p, jac ? w->invdiag : nullptr, w->partials,
+                                                      w->sc, o->rtol, o->max_iter);
+    MF_CUDA(cudaGetLastError());
+    st = cg_loop<double>(w, 0, key64, op64, n, w->x, w->r, w->p, w->Ap, jac ? w->invdiag : nullptr, w->sc,
+                         o->check_every, o->use_graph != 0, o->timeout_s, t0, s, h);
+    if (st != MF_OK && st != MF_ERR_TIMEOUT) return st;
+    if (st == MF_OK) st = (mf_status)h->status;
+    iters = h->iter;
+    rel_rec = h->bb > 0 ? std::sqrt(h->rr / h->bb) : 0.0;
+  } else {
+    // FP64 iterative refinement around an FP32 inner CG: x_{m+1} = x_m + A32^{-1}(b - A64 x_m).
+    MF_CUDA(cudaMemsetAsync(w->x, 0, n * sizeof(double), s));
+    MF_CUDA(cudaMemcpyAsync(w->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    mf_count_launches(1);
+    residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->x, nullptr, w->partials, w->sc);  // ||b||^2 (x = 0)
+    MF_CUDA(cudaMemcpyAsync(h, w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    const double bb = h->res2;
+    double rr = bb;
+    const double tol2 = o->rtol * o->rtol * bb;
+    st = MF_NOT_CONVERGED;
+    while (outer < o->max_outer && iters < o->max_iter) {
+      if (rr <= tol2) {
+        st = MF_OK;
+        break;
+      }
+      mf_count_launches(1);
+      to_f32<<<kRedBlocks, kRedThreads, 0, s>>>(n, w->r, w->r32);
+      // inner solve A32 d = r32 (b of the inner CG lives in Ap32 so r32 can be the inner residual)
+      MF_CUDA(cudaMemcpyAsync(w->Ap32, w->r32, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      mf_count_launches(1);
+      cg_init<float><<<kRedBlocks, kRedThreads, 0, s>>>(n, w->Ap32, w->x32, w->r32, w->p32, nullptr, w->partials,
+                                                       w->sc32, o->inner_rtol, o->max_iter - iters);
+      MF_CUDA(cudaGetLastError());
+      mf_status si = cg_loop<float>(w, 1, key32, op32, n, w->x32, w->r32, w->p32, w->Ap32, nullptr, w->sc32,
+                                    o->check_every, o->use_graph != 0, o->timeout_s, t0, s, h + 1);
+      if (si != MF_OK) {
+        st = si;
+        break;
+      }
+      iters += h[1].iter;
+      if (h[1].status == MF_ERR_BREAKDOWN) {
+        st = MF_ERR_BREAKDOWN;
+        break;
+      }
+      mf_count_launches(1);
+      add_f32<<<kRedBlocks, kRedThreads, 0, s>>>(n, w->x, w->x32);
+      MF_TRY(apply_fp64(m, w->x, w->Ap, s));
+      mf_count_launches(1);
+      residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->Ap, w->r, w->partials, w->sc);
+      MF_CUDA(cudaMemcpyAsync(h, w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+      MF_CUDA(cudaStreamSynchronize(s));
+      rr = h->res2;
+      ++outer;
+      if (!std::isfinite(rr)) {
+        st = MF_ERR_BREAKDOWN;
+        break;
+      }
+    }
+    if (st == MF_NOT_CONVERGED && rr <= tol2) st = MF_OK;
+    rel_rec = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  }
+  // true residual with the FP64 operator of the solve
+  MF_CUDA(cudaMemcpyAsync(x, w->x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  MF_TRY(op64(w->x, w->Ap, s, nullptr));
+  mf_count_launches(1);
+  residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->Ap, nullptr, w->partials, w->sc);
+  MF_CUDA(cudaGetLastError());
+  MF_CUDA(cudaMemcpyAsync(h, w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  const double res2 = h->res2;
+  double bb = h->bb;
+  if (mixed || bb == 0.0) {
+    // ||b||^2 = ||b - 0||^2 (the FP64 scalars of a mixed solve live in the refinement loop)
+    MF_CUDA(cudaMemsetAsync(w->Ap, 0, n * sizeof(double), s));
+    mf_count_launches(1);
+    residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->Ap, nullptr, w->partials, w->sc);
+    MF_CUDA(cudaMemcpyAsync(h, w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    bb = h->res2;
+  }
+  if (info) {
+    info->iters = iters;
+    info->outer_iters = outer;
+    info->status = st;
+    info->rel_res = rel_rec;
+    info->rel_res_true = bb > 0 ? std::sqrt(res2 / bb) : 0.0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (st == MF_ERR_BREAKDOWN) mf_set_error("mf_cg_solve: breakdown (p^T A p <= 0 or non-finite scalar)");
+  if (st == MF_NOT_CONVERGED) mf_set_error("mf_cg_solve: not converged within the iteration limit");
+  return st;
+}

@@ -1,0 +1,385 @@
+// Matrix-based operator (Sec. 3 and Table 1): CSR assembly of the element matrices of Eqs. 4/6 and
+// the SpMV used as the baseline of the matrix-free kernels.
+//
+// Fill: the paper describes an element loop that searches each global column and adds with an
+// atomic.  Here the search is a binary search in the sorted row, and the add is a plain
+// read-modify-write: elements are processed colour by colour (elements of one colour share no
+// node, hence no row), which keeps the fill deterministic.
+#include <algorithm>
+#include <vector>
+
+#include "mf_element.cuh"
+#include "mf_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ int64_t parity_element_c(int64_t t, int c, int nx, int ny, int nz) {
+  const int px = c & 1, py = (c >> 1) & 1, pz = (c >> 2) & 1;
+  const int64_t cnx = (nx - px + 1) / 2, cny = (ny - py + 1) / 2;
+  const int64_t ix = t % cnx, r = t / cnx, iy = r % cny, iz = r / cny;
+  return (2 * ix + px) + (int64_t)nx * ((2 * iy + py) + (int64_t)ny * (2 * iz + pz));
+}
+
+// Rows of A^e belonging to corner a: out[k][b][l] = A^e_{ND a + k, ND b + l} (Eqs. 4 and 6).
+template <int PHYS>
+__device__ void element_rows(const double X[8][3], int a, double c0, double c1, double out[][8][3]) {
+  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  for (int k = 0; k < ND; ++k)
+    for (int b = 0; b < 8; ++b)
+      for (int l = 0; l < 3; ++l) out[k][b][l] = 0.0;
+  for (int q = 0; q < 8; ++q) {
+    double xi[3];
+    for (int d = 0; d < 3; ++d) xi[d] = q1::sgn(q, d) * q1::kG;
+    double J[3][3], C[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0;
+        for (int c = 0; c < 8; ++c) s += X[c][i] * q1::dN_at(xi, c, j);
+        J[i][j] = s;
+      }
+    const double det = q1::adjugate(J, C);
+    // physical gradients g_b = J^{-T} grad_ref phi_b = C^T grad_ref phi_b / det
+    double g[8][3];
+    for (int b = 0; b < 8; ++b) {
+      double r[3] = {q1::dN_at(xi, b, 0), q1::dN_at(xi, b, 1), q1::dN_at(xi, b, 2)};
+      for (int i = 0; i < 3; ++i) g[b][i] = (C[0][i] * r[0] + C[1][i] * r[1] + C[2][i] * r[2]) / det;
+    }
+    const double wd = det;  // w_q = 1
+    for (int b = 0; b < 8; ++b) {
+      const double gg = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+      if (PHYS == MF_LAPLACE) {
+        out[0][b][0] += c0 * gg * wd;
+      } else {
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l)
+            out[k][b][l] += wd * (c0 * g[a][k] * g[b][l] + c1 * (g[a][l] * g[b][k] + (k == l ? gg : 0.0)));
+      }
+    }
+  }
+}
+
+template <int PHYS>
+__global__ void csr_fill_colour(MeshView m, int colour, int64_t count, const int32_t *__restrict__ celems,
+                                const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, double *val) {
+  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= count * 8) return;
+  const int64_t t = gid >> 3;
+  const int a = (int)(gid & 7);
+  const int64_t e = celems ? (int64_t)celems[t] : parity_element_c(t, colour, m.nx, m.ny, m.nz);
+  int64_t nodes[8];
+  element_nodes(m, e, nodes);
+  if (m.dmask[nodes[a]]) return;  // Dirichlet row: identity, set separately
+  double X[8][3];
+  for (int c = 0; c < 8; ++c)
+    for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
+  const double c0 = PHYS == MF_LAPLACE ? m.mat[e] : m.mat[2 * e];
+  const double c1 = PHYS == MF_LAPLACE ? 0.0 : m.mat[2 * e + 1];
+  double A[ND][8][3];
+  element_rows<PHYS>(X, a, c0, c1, A);
+  const int64_t row0 = nodes[a] * ND;
+  const int64_t lo0 = rowptr[row0], hi0 = rowptr[row0 + 1];
+  for (int b = 0; b < 8; ++b) {
+    if (m.dmask[nodes[b]]) continue;  // Dirichlet column dropped
+    const int32_t target = (int32_t)(nodes[b] * ND);
+    int64_t lo = lo0, hi = hi0;  // binary search for the first column of node b
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (col[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    const int64_t rel = lo - lo0;
+    for (int k = 0; k < ND; ++k) {
+      const int64_t base = rowptr[row0 + k] + rel;
+      for (int l = 0; l < ND; ++l) val[base + l] += A[k][b][l];
+    }
+  }
+}
+
+template <int PHYS>
+__global__ void diag_colour(MeshView m, int colour, int64_t count, const int32_t *__restrict__ celems, double *diag) {
+  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= count * 8) return;
+  const int64_t t = gid >> 3;
+  const int a = (int)(gid & 7);
+  const int64_t e = celems ? (int64_t)celems[t] : parity_element_c(t, colour, m.nx, m.ny, m.nz);
+  int64_t nodes[8];
+  element_nodes(m, e, nodes);
+  if (m.dmask[nodes[a]]) return;
+  double X[8][3];
+  for (int c = 0; c < 8; ++c)
+    for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
+  const double c0 = PHYS == MF_LAPLACE ? m.mat[e] : m.mat[2 * e];
+  const double c1 = PHYS == MF_LAPLACE ? 0.0 : m.mat[2 * e + 1];
+  double A[ND][8][3];
+  element_rows<PHYS>(X, a, c0, c1, A);
+  for (int k = 0; k < ND; ++k) diag[nodes[a] * ND + k] += A[k][a][k];
+}
+
+__global__ void dirichlet_unit(const int32_t *dn, int64_t n, int nd, const int64_t *rowptr, double *val) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n * nd) return;
+  const int64_t row = (int64_t)dn[i / nd] * nd + i % nd;
+  val[rowptr[row]] = 1.0;
+}
+
+__global__ void dirichlet_diag(const int32_t *dn, int64_t n, int nd, double *diag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n * nd) return;
+  diag[(int64_t)dn[i / nd] * nd + i % nd] = 1.0;
+}
+
+// Expand the node-level neighbour lists to DoF-level columns: row ND*n + k holds ND*m + l for every
+// neighbour m of n (l = 0..ND-1), or only its own diagonal when n is constrained.
+__global__ void expand_columns(int64_t n_nodes, int nd, const int64_t *__restrict__ noff, const int32_t *__restrict__ nbr,
+                               const uint8_t *__restrict__ dmask, const int64_t *__restrict__ rowptr, int32_t *col) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_nodes * nd) return;
+  const int64_t n = i / nd, k = i % nd;
+  int64_t p = rowptr[i];
+  if (dmask[n]) {
+    col[p] = (int32_t)i;
+    return;
+  }
+  for (int64_t t = noff[n]; t < noff[n + 1]; ++t)
+    for (int l = 0; l < nd; ++l) col[p++] = nbr[t] * nd + l;
+  (void)k;
+}
+
+// y = A x with L threads per row; lanes accumulate strided partial sums, reduced by a fixed
+// shuffle tree (deterministic).
+template <int L>
+__global__ void __launch_bounds__(256) spmv_kernel(int64_t n_rows, const int64_t *__restrict__ rowptr,
+                                                   const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                   const double *__restrict__ x, double *__restrict__ y,
+                                                   const int *__restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gid / L;
+  const int lane = (int)(gid % L);
+  double s = 0.0;
+  if (row < n_rows) {
+    const int64_t end = rowptr[row + 1];
+    for (int64_t p = rowptr[row] + lane; p < end; p += L) s += __ldcs(val + p) * __ldg(x + __ldcs(col + p));
+  }
+#pragma unroll
+  for (int off = L / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (row < n_rows && lane == 0) y[row] = s;
+}
+
+template <int PHYS>
+void launch_fill(const mf_mesh *m, const MeshView &v, const mf_csr *A, cudaStream_t s) {
+  for (int c = 0; c < m->n_colours; ++c) {
+    const int64_t cnt = colour_count(m, c);
+    if (!cnt) continue;
+    const int32_t *ce = m->structured ? nullptr : m->colour_elems + m->colour_off[c];
+    csr_fill_colour<PHYS><<<blocks_for(cnt * 8, 128), 128, 0, s>>>(v, c, cnt, ce, A->rowptr, A->col, A->val);
+  }
+}
+
+template <int PHYS>
+void launch_diag(const mf_mesh *m, const MeshView &v, double *diag, cudaStream_t s) {
+  for (int c = 0; c < m->n_colours; ++c) {
+    const int64_t cnt = colour_count(m, c);
+    if (!cnt) continue;
+    const int32_t *ce = m->structured ? nullptr : m->colour_elems + m->colour_off[c];
+    diag_colour<PHYS><<<blocks_for(cnt * 8, 128), 128, 0, s>>>(v, c, cnt, ce, diag);
+  }
+}
+
+// Node-level neighbour lists (sorted, Dirichlet neighbours removed) on the host.
+void node_neighbours(const mf_mesh *m, const std::vector<uint8_t> &dmask, std::vector<int64_t> &off,
+                     std::vector<int32_t> &nbr) {
+  const int64_t N = m->n_nodes;
+  off.assign(N + 1, 0);
+  if (m->structured) {
+    const int nx = m->nx, ny = m->ny, nz = m->nz;
+    // count
+    for (int k = 0; k <= nz; ++k)
+      for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+          const int64_t n = i + (int64_t)(nx + 1) * (j + (int64_t)(ny + 1) * k);
+          int64_t c = 0;
+          if (!dmask[n])
+            for (int dk = -1; dk <= 1; ++dk)
+              for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                  const int ii = i + di, jj = j + dj, kk = k + dk;
+                  if (ii < 0 || jj < 0 || kk < 0 || ii > nx || jj > ny || kk > nz) continue;
+                  if (dmask[ii + (int64_t)(nx + 1) * (jj + (int64_t)(ny + 1) * kk)]) continue;
+                  ++c;
+                }
+          off[n + 1] = c;
+        }
+    for (int64_t n = 0; n < N; ++n) off[n + 1] += off[n];
+    nbr.resize(off[N]);
+    for (int k = 0; k <= nz; ++k)
+      for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+          const int64_t n = i + (int64_t)(nx + 1) * (j + (int64_t)(ny + 1) * k);
+          if (dmask[n]) continue;
+          int64_t p = off[n];
+          for (int dk = -1; dk <= 1; ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+              for (int di = -1; di <= 1; ++di) {
+                const int ii = i + di, jj = j + dj, kk = k + dk;
+                if (ii < 0 || jj < 0 || kk < 0 || ii > nx || jj > ny || kk > nz) continue;
+                const int64_t mm = ii + (int64_t)(nx + 1) * (jj + (int64_t)(ny + 1) * kk);
+                if (dmask[mm]) continue;
+                nbr[p++] = (int32_t)mm;
+              }
+        }
+    return;
+  }
+  const std::vector<int32_t> &cells = m->h_cells;
+  const int64_t E = m->n_cells;
+  std::vector<int64_t> eoff(N + 1, 0);
+  for (int64_t i = 0; i < 8 * E; ++i) eoff[cells[i] + 1]++;
+  for (int64_t n = 0; n < N; ++n) eoff[n + 1] += eoff[n];
+  std::vector<int64_t> fill(eoff.begin(), eoff.end() - 1);
+  std::vector<int32_t> adj(8 * E);
+  for (int64_t e = 0; e < E; ++e)
+    for (int a = 0; a < 8; ++a) adj[fill[cells[8 * e + a]]++] = (int32_t)e;
+  std::vector<std::vector<int32_t>> lists(N);
+  std::vector<int32_t> tmp;
+  for (int64_t n = 0; n < N; ++n) {
+    if (dmask[n]) continue;
+    tmp.clear();
+    for (int64_t t = eoff[n]; t < eoff[n + 1]; ++t)
+      for (int a = 0; a < 8; ++a) {
+        const int32_t mm = cells[8 * (int64_t)adj[t] + a];
+        if (!dmask[mm]) tmp.push_back(mm);
+      }
+    std::sort(tmp.begin(), tmp.end());
+    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    lists[n] = tmp;
+    off[n + 1] = (int64_t)tmp.size();
+  }
+  for (int64_t n = 0; n < N; ++n) off[n + 1] += off[n];
+  nbr.resize(off[N]);
+  for (int64_t n = 0; n < N; ++n) std::copy(lists[n].begin(), lists[n].end(), nbr.begin() + off[n]);
+}
+
+}  // namespace
+
+mf_status spmv(const mf_csr *A, const double *x, double *y, cudaStream_t s, const int *skip) {
+  const int64_t threads = A->n_rows * A->lanes;
+  mf_count_launches(1);
+  switch (A->lanes) {
+    case 4: spmv_kernel<4><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+    case 8: spmv_kernel<8><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+    case 16: spmv_kernel<16><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+    default: spmv_kernel<32><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+  }
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
+mf_status operator_diagonal(const mf_mesh *m, double *diag, cudaStream_t s) {
+  MF_CUDA(cudaMemsetAsync(diag, 0, m->n_dof * sizeof(double), s));
+  const MeshView v = m->view();
+  if (m->physics == MF_LAPLACE) launch_diag<MF_LAPLACE>(m, v, diag, s);
+  else launch_diag<MF_ELASTICITY>(m, v, diag, s);
+  if (m->n_dnodes) dirichlet_diag<<<blocks_for(m->n_dnodes * m->ndpn), kThreads, 0, s>>>(m->dnodes, m->n_dnodes, m->ndpn, diag);
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
+extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr **out) {
+  mf_clear_error();
+  MF_ARG(m && out, "mf_assemble_csr: null argument");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nd = m->ndpn;
+  std::vector<uint8_t> hmask(m->n_nodes);
+  MF_CUDA(cudaMemcpyAsync(hmask.data(), m->dmask, m->n_nodes, cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  std::vector<int64_t> noff;
+  std::vector<int32_t> nbr;
+  node_neighbours(m, hmask, noff, nbr);
+  // DoF-level row pointers
+  const int64_t n_rows = m->n_nodes * nd;
+  std::vector<int64_t> rowptr(n_rows + 1, 0);
+  for (int64_t n = 0; n < m->n_nodes; ++n)
+    for (int k = 0; k < nd; ++k) rowptr[n * nd + k + 1] = hmask[n] ? 1 : (noff[n + 1] - noff[n]) * nd;
+  for (int64_t r = 0; r < n_rows; ++r) rowptr[r + 1] += rowptr[r];
+  const int64_t nnz = rowptr[n_rows];
+  MF_ARG(nnz < (int64_t)INT32_MAX * 4, "mf_assemble_csr: matrix too large");
+
+  mf_csr *A = new mf_csr();
+  A->n_rows = n_rows;
+  A->nnz = nnz;
+  A->lanes = nd == 1 ? 8 : 16;
+  int64_t *d_noff = nullptr;
+  int32_t *d_nbr = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_noff);
+    cudaFree(d_nbr);
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&A->rowptr, (n_rows + 1) * sizeof(int64_t))) != cudaSuccess ||
+      (e = cudaMalloc(&A->col, nnz * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&A->val, nnz * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&d_noff, noff.size() * sizeof(int64_t))) != cudaSuccess ||
+      (e = cudaMalloc(&d_nbr, std::max<size_t>(nbr.size(), 1) * sizeof(int32_t))) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    mf_destroy_csr(A);
+    mf_set_error("mf_assemble_csr: allocation of %lld non-zeros failed: %s", (long long)nnz, cudaGetErrorString(e));
+    return MF_ERR_OOM;
+  }
+  MF_CUDA(cudaMemcpyAsync(A->rowptr, rowptr.data(), rowptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  MF_CUDA(cudaMemcpyAsync(d_noff, noff.data(), noff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  if (!nbr.empty()) MF_CUDA(cudaMemcpyAsync(d_nbr, nbr.data(), nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  expand_columns<<<blocks_for(n_rows), kThreads, 0, s>>>(m->n_nodes, nd, d_noff, d_nbr, m->dmask, A->rowptr, A->col);
+  MF_CUDA(cudaMemsetAsync(A->val, 0, nnz * sizeof(double), s));
+  const MeshView v = m->view();
+  if (m->physics == MF_LAPLACE) launch_fill<MF_LAPLACE>(m, v, A, s);
+  else launch_fill<MF_ELASTICITY>(m, v, A, s);
+  if (m->n_dnodes) dirichlet_unit<<<blocks_for(m->n_dnodes * nd), kThreads, 0, s>>>(m->dnodes, m->n_dnodes, nd, A->rowptr, A->val);
+  MF_CUDA(cudaGetLastError());
+  MF_CUDA(cudaStreamSynchronize(s));
+  cleanup();
+  *out = A;
+  return MF_OK;
+}
+
+extern "C" mf_status mf_csr_query(const mf_csr *A, int64_t *n_rows, int64_t *nnz, const int64_t **rowptr,
+                                  const int32_t **col, const double **val) {
+  MF_ARG(A != nullptr, "mf_csr_query: csr is NULL");
+  if (n_rows) *n_rows = A->n_rows;
+  if (nnz) *nnz = A->nnz;
+  if (rowptr) *rowptr = A->rowptr;
+  if (col) *col = A->col;
+  if (val) *val = A->val;
+  return MF_OK;
+}
+
+extern "C" mf_status mf_csr_export(const mf_csr *A, int64_t *rowptr, int32_t *col, double *val, mf_stream stream) {
+  mf_clear_error();
+  MF_ARG(A && rowptr && col && val, "mf_csr_export: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  MF_CUDA(cudaMemcpyAsync(rowptr, A->rowptr, (A->n_rows + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  MF_CUDA(cudaMemcpyAsync(col, A->col, A->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  MF_CUDA(cudaMemcpyAsync(val, A->val, A->nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return MF_OK;
+}
+
+extern "C" mf_status mf_spmv_csr(const mf_csr *A, const double *x, double *y, mf_stream stream) {
+  mf_clear_error();
+  MF_ARG(A && x && y, "mf_spmv_csr: null argument");
+  const size_t bytes = A->n_rows * sizeof(double);
+  MF_ARG((const char *)x + bytes <= (const char *)y || (const char *)y + bytes <= (const char *)x,
+         "mf_spmv_csr: x and y overlap");
+  return spmv(A, x, y, (cudaStream_t)stream);
+}
+
+extern "C" mf_status mf_destroy_csr(mf_csr *A) {
+  if (!A) return MF_OK;
+  cudaDeviceSynchronize();
+  cudaFree(A->rowptr);
+  cudaFree(A->col);
+  cudaFree(A->val);
+  delete A;
+  return MF_OK;
+}

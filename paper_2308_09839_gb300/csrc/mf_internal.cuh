@@ -1,0 +1,153 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mf.h"
+
+// ------------------------------------------------------------------------------------ errors ----
+void mf_set_error(const char *fmt, ...);
+void mf_clear_error();
+
+#define MF_CUDA(call)                                                                            \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      mf_set_error("%s:%d: %s failed: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));   \
+      return e_ == cudaErrorMemoryAllocation ? MF_ERR_OOM : MF_ERR_CUDA;                         \
+    }                                                                                            \
+  } while (0)
+
+#define MF_TRY(expr)                  \
+  do {                                \
+    mf_status s_ = (expr);            \
+    if (s_ != MF_OK) return s_;       \
+  } while (0)
+
+#define MF_ARG(cond, ...)             \
+  do {                                \
+    if (!(cond)) {                    \
+      mf_set_error(__VA_ARGS__);      \
+      return MF_ERR_ARG;              \
+    }                                 \
+  } while (0)
+
+// Kernel-launch accounting (mf_kernel_launches): every host function that launches kernels adds
+// the number it launched.
+void mf_count_launches(int64_t n);
+int64_t mf_launches_now();
+
+// ------------------------------------------------------------------------- device geometry ----
+// Plain view of a mesh, passed by value to kernels.
+struct MeshView {
+  const double *X;     // [N][3] node coordinates
+  const float *X32;    // [N][3] FP32 copy
+  const int32_t *cells;  // [E][8], null for structured boxes
+  const double *mat;   // Laplace: kappa[E]; elasticity: (lam, mu)[E][2]
+  const float *mat32;  // FP32 copy of mat
+  const uint8_t *dmask;  // [N] Dirichlet mask (never null: zero-filled when unconstrained)
+  int32_t nx, ny, nz;
+  int64_t n_nodes, n_cells;
+};
+
+// Template accessors for the real type.
+template <typename Real> __device__ __forceinline__ const Real *coords_of(const MeshView &m);
+template <> __device__ __forceinline__ const double *coords_of<double>(const MeshView &m) { return m.X; }
+template <> __device__ __forceinline__ const float *coords_of<float>(const MeshView &m) { return m.X32; }
+template <typename Real> __device__ __forceinline__ const Real *mat_of(const MeshView &m);
+template <> __device__ __forceinline__ const double *mat_of<double>(const MeshView &m) { return m.mat; }
+template <> __device__ __forceinline__ const float *mat_of<float>(const MeshView &m) { return m.mat32; }
+
+// Structured box: node id of element e's corner a.
+__host__ __device__ __forceinline__ int64_t box_corner_node(int64_t e, int a, int nx, int ny) {
+  int64_t ex = e % nx;
+  int64_t t = e / nx;
+  int64_t ey = t % ny;
+  int64_t ez = t / ny;
+  return (ex + (a & 1)) + (int64_t)(nx + 1) * ((ey + ((a >> 1) & 1)) + (int64_t)(ny + 1) * (ez + ((a >> 2) & 1)));
+}
+
+__device__ __forceinline__ void element_nodes(const MeshView &m, int64_t e, int64_t nodes[8]) {
+  if (m.cells) {
+    const int4 *c4 = reinterpret_cast<const int4 *>(m.cells + 8 * e);
+    int4 lo = __ldg(c4), hi = __ldg(c4 + 1);
+    nodes[0] = lo.x; nodes[1] = lo.y; nodes[2] = lo.z; nodes[3] = lo.w;
+    nodes[4] = hi.x; nodes[5] = hi.y; nodes[6] = hi.z; nodes[7] = hi.w;
+  } else {
+    int64_t base = box_corner_node(e, 0, m.nx, m.ny);
+    const int64_t sx = 1, sy = m.nx + 1, sz = (int64_t)(m.nx + 1) * (m.ny + 1);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) nodes[a] = base + (a & 1) * sx + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
+  }
+}
+
+// -------------------------------------------------------------------------------- the mesh ----
+struct CgWorkspace;
+
+struct mf_mesh {
+  int physics = 0;
+  int ndpn = 1;
+  int device = 0;
+  int variant = MF_VARIANT_AUTO;
+  int64_t n_nodes = 0, n_cells = 0, n_dof = 0, n_free = 0;
+  bool structured = false;
+  bool all_affine = false;
+  int32_t nx = 0, ny = 0, nz = 0;
+  // owned device buffers
+  double *X = nullptr;
+  float *X32 = nullptr;
+  int32_t *cells = nullptr;
+  double *mat = nullptr;   // kappa or (lam, mu)
+  float *mat32 = nullptr;
+  uint8_t *dmask = nullptr;
+  int32_t *dnodes = nullptr;  // Dirichlet node list
+  int64_t n_dnodes = 0;
+  // element colouring (unstructured): colour c holds colour_elems[colour_off[c] .. colour_off[c+1])
+  int n_colours = 0;
+  std::vector<int64_t> colour_off;
+  int32_t *colour_elems = nullptr;
+  // solver workspace (created lazily by mf_cg_solve)
+  CgWorkspace *cg = nullptr;
+  // host copy of the connectivity used by CSR assembly (empty for structured meshes)
+  std::vector<int32_t> h_cells;
+
+  MeshView view() const {
+    MeshView v;
+    v.X = X; v.X32 = X32; v.cells = cells; v.mat = mat; v.mat32 = mat32; v.dmask = dmask;
+    v.nx = nx; v.ny = ny; v.nz = nz; v.n_nodes = n_nodes; v.n_cells = n_cells;
+    return v;
+  }
+};
+
+struct mf_csr {
+  int64_t n_rows = 0, nnz = 0;
+  int64_t *rowptr = nullptr;
+  int32_t *col = nullptr;
+  double *val = nullptr;
+  int lanes = 8;  // threads per row in the SpMV kernel
+};
+
+// --------------------------------------------------------------------- internal entry points ----
+// Operator apply on `stream` (FP64).  Picks the variant; x and y are DoF vectors.
+// `skip` (device int, may be null): when it holds a nonzero value at run time every kernel of the
+// apply returns immediately (used by solver loops captured in CUDA graphs after convergence).
+mf_status apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip = nullptr);
+mf_status apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip = nullptr);
+mf_status apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s);
+mf_status spmv(const mf_csr *A, const double *x, double *y, cudaStream_t s, const int *skip = nullptr);
+// diag(A) of the matrix-free operator (Jacobi), FP64, Dirichlet rows 1.
+mf_status operator_diagonal(const mf_mesh *m, double *diag, cudaStream_t s);
+void cg_workspace_free(CgWorkspace *w);
+
+// number of element colours and the launch grid for one colour
+int64_t colour_count(const mf_mesh *m, int c);
+
+constexpr int kThreads = 256;
+inline unsigned blocks_for(int64_t n, int threads = kThreads) {
+  int64_t b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : b);
+}

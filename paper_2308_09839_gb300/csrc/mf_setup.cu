@@ -1,0 +1,359 @@
+// Mesh setup (inputs of Algorithm 1 and the cell constants of Table 2): validation, material
+// conversion, Dirichlet list, element colouring for the atomic-free scatter, error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <atomic>
+#include <numeric>
+
+#include "mf_element.cuh"
+#include "mf_internal.cuh"
+
+// ------------------------------------------------------------------------------------ errors ----
+static thread_local char g_err[1024] = "";
+
+void mf_set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+void mf_clear_error() { g_err[0] = 0; }
+
+extern "C" const char *mf_last_error(void) { return g_err; }
+extern "C" const char *mf_version(void) { return "mf-gb300 0.1 (sm_103a)"; }
+
+static std::atomic<int64_t> g_launches{0};
+void mf_count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t mf_launches_now() { return g_launches.load(std::memory_order_relaxed); }
+extern "C" int64_t mf_kernel_launches(void) { return mf_launches_now(); }
+
+// ------------------------------------------------------------------------- setup kernels ----
+enum : int { BAD_DET = 1, BAD_NODE = 2, BAD_COORD = 4, BAD_MAT = 8 };
+
+struct ValidateOut {
+  int flags;
+  int not_affine;     // set if any cell is not a parallelepiped
+  long long first_bad;  // smallest element index with a problem
+};
+
+// det J at the 8 Gauss points and the 8 corners must be positive and finite; node ids in range;
+// material finite and admissible.  Also records whether every cell is affine (x(xi) has no
+// bilinear or trilinear terms), in which case J is constant over the cell.
+__global__ void validate_kernel(MeshView m, int physics, ValidateOut *out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_cells) return;
+  int flags = 0;
+  int64_t nodes[8];
+  if (m.cells) {
+    for (int a = 0; a < 8; ++a) {
+      int32_t n = m.cells[8 * e + a];
+      if (n < 0 || n >= m.n_nodes) flags |= BAD_NODE;
+      nodes[a] = n;
+    }
+  } else {
+    element_nodes(m, e, nodes);
+  }
+  if (!(flags & BAD_NODE)) {
+    double X[8][3];
+    for (int a = 0; a < 8; ++a)
+      for (int i = 0; i < 3; ++i) {
+        X[a][i] = m.X[3 * nodes[a] + i];
+        if (!isfinite(X[a][i])) flags |= BAD_COORD;
+      }
+    if (!(flags & BAD_COORD)) {
+      for (int p = 0; p < 16; ++p) {
+        double xi[3];
+        for (int d = 0; d < 3; ++d) xi[d] = q1::sgn(p & 7, d) * (p < 8 ? q1::kG : 1.0);
+        double J[3][3], C[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int a = 0; a < 8; ++a) s += X[a][i] * q1::dN_at(xi, a, j);
+            J[i][j] = s;
+          }
+        double det = q1::adjugate(J, C);
+        if (!(det > 0.0) || !isfinite(det)) flags |= BAD_DET;
+      }
+      // monomial coefficients of xi*eta, eta*zeta, xi*zeta, xi*eta*zeta in x(xi)
+      double scale = 0;
+      for (int i = 0; i < 3; ++i) scale = fmax(scale, fabs(X[7][i] - X[0][i]));
+      bool affine = true;
+      for (int mono = 3; mono < 7; ++mono) {
+        int mask = (mono == 3) ? 3 : (mono == 4) ? 6 : (mono == 5) ? 5 : 7;
+        for (int i = 0; i < 3; ++i) {
+          double c = 0;
+          for (int a = 0; a < 8; ++a) {
+            double sgnp = 1;
+            for (int d = 0; d < 3; ++d)
+              if (mask >> d & 1) sgnp *= q1::sgn(a, d);
+            c += sgnp * X[a][i];
+          }
+          if (fabs(c) > 1e-14 * scale) affine = false;
+        }
+      }
+      if (!affine) atomicOr(&out->not_affine, 1);
+    }
+  }
+  if (physics == MF_LAPLACE) {
+    double k = m.mat[e];
+    if (!(k > 0.0) || !isfinite(k)) flags |= BAD_MAT;
+  } else {
+    double E = m.mat[2 * e], nu = m.mat[2 * e + 1];
+    if (!(E > 0.0) || !isfinite(E) || !(nu > -1.0 && nu < 0.5)) flags |= BAD_MAT;
+  }
+  if (flags) {
+    atomicOr(&out->flags, flags);
+    atomicMin(&out->first_bad, (long long)e);
+  }
+}
+
+// (E, nu) -> (lam, mu) per cell, plus the FP32 copies.
+__global__ void material_kernel(const double *in, double *out, float *out32, int64_t n_cells, int physics) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n_cells) return;
+  if (physics == MF_LAPLACE) {
+    out[e] = in[e];
+    out32[e] = (float)in[e];
+  } else {
+    double E = in[2 * e], nu = in[2 * e + 1];
+    double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    double mu = E / (2.0 * (1.0 + nu));
+    out[2 * e] = lam;
+    out[2 * e + 1] = mu;
+    out32[2 * e] = (float)lam;
+    out32[2 * e + 1] = (float)mu;
+  }
+}
+
+__global__ void to_f32_kernel(const double *in, float *out, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
+// --------------------------------------------------------------------------- host helpers ----
+template <typename T>
+static mf_status dmalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mf_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    return MF_ERR_OOM;
+  }
+  return MF_OK;
+}
+
+static void free_mesh(mf_mesh *m) {
+  if (!m) return;
+  if (m->cg) cg_workspace_free(m->cg);
+  cudaFree(m->X);
+  cudaFree(m->X32);
+  cudaFree(m->cells);
+  cudaFree(m->mat);
+  cudaFree(m->mat32);
+  cudaFree(m->dmask);
+  cudaFree(m->dnodes);
+  cudaFree(m->colour_elems);
+  delete m;
+}
+
+// Greedy element colouring: elements of one colour share no node, so the scatter of one colour
+// needs no atomics.  Deterministic (elements visited in index order, smallest free colour).
+static mf_status colour_elements(mf_mesh *m, cudaStream_t s) {
+  const int64_t E = m->n_cells, N = m->n_nodes;
+  const std::vector<int32_t> &cells = m->h_cells;
+  std::vector<int64_t> off(N + 1, 0);
+  for (int64_t i = 0; i < 8 * E; ++i) off[cells[i] + 1]++;
+  for (int64_t n = 0; n < N; ++n) off[n + 1] += off[n];
+  std::vector<int64_t> fill(off.begin(), off.end() - 1);
+  std::vector<int32_t> adj(8 * E);
+  for (int64_t e = 0; e < E; ++e)
+    for (int a = 0; a < 8; ++a) adj[fill[cells[8 * e + a]]++] = (int32_t)e;
+  std::vector<int8_t> colour(E, -1);
+  int ncol = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    uint64_t used = 0;
+    for (int a = 0; a < 8; ++a) {
+      int32_t n = cells[8 * e + a];
+      for (int64_t t = off[n]; t < off[n + 1]; ++t) {
+        int8_t c = colour[adj[t]];
+        if (c >= 0) used |= 1ull << c;
+      }
+    }
+    int c = 0;
+    while (c < 64 && (used >> c & 1)) ++c;
+    if (c >= 64) {
+      mf_set_error("element colouring needs more than 64 colours (element %lld)", (long long)e);
+      return MF_ERR_MESH;
+    }
+    colour[e] = (int8_t)c;
+    ncol = std::max(ncol, c + 1);
+  }
+  m->n_colours = ncol;
+  m->colour_off.assign(ncol + 1, 0);
+  for (int64_t e = 0; e < E; ++e) m->colour_off[colour[e] + 1]++;
+  for (int c = 0; c < ncol; ++c) m->colour_off[c + 1] += m->colour_off[c];
+  std::vector<int64_t> pos(m->colour_off.begin(), m->colour_off.end() - 1);
+  std::vector<int32_t> order(E);
+  for (int64_t e = 0; e < E; ++e) order[pos[colour[e]]++] = (int32_t)e;
+  MF_TRY(dmalloc(&m->colour_elems, E));
+  MF_CUDA(cudaMemcpyAsync(m->colour_elems, order.data(), E * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  return MF_OK;
+}
+
+int64_t colour_count(const mf_mesh *m, int c) {
+  if (!m->structured) return m->colour_off[c + 1] - m->colour_off[c];
+  int px = c & 1, py = (c >> 1) & 1, pz = (c >> 2) & 1;
+  return (int64_t)((m->nx - px + 1) / 2) * ((m->ny - py + 1) / 2) * ((m->nz - pz + 1) / 2);
+}
+
+// ----------------------------------------------------------------------------- entry points ----
+extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells, const double *coords,
+                                   const int32_t *cells, int32_t nx, int32_t ny, int32_t nz, const double *mat,
+                                   const uint8_t *dirichlet, mf_stream stream, mf_mesh **out) {
+  mf_clear_error();
+  MF_ARG(out != nullptr, "mf_setup_mesh: out is NULL");
+  *out = nullptr;
+  MF_ARG(physics == MF_LAPLACE || physics == MF_ELASTICITY, "mf_setup_mesh: unknown physics %d", physics);
+  MF_ARG(coords && mat, "mf_setup_mesh: coords and mat are required");
+  MF_ARG(n_nodes >= 8 && n_cells >= 1, "mf_setup_mesh: need n_nodes >= 8 and n_cells >= 1");
+  MF_ARG(n_nodes < (int64_t)INT32_MAX, "mf_setup_mesh: n_nodes must fit int32");
+  if (!cells) {
+    MF_ARG(nx > 0 && ny > 0 && nz > 0, "mf_setup_mesh: structured mesh needs nx, ny, nz > 0");
+    MF_ARG((int64_t)nx * ny * nz == n_cells, "mf_setup_mesh: n_cells != nx*ny*nz");
+    MF_ARG((int64_t)(nx + 1) * (ny + 1) * (nz + 1) == n_nodes, "mf_setup_mesh: n_nodes != (nx+1)(ny+1)(nz+1)");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  mf_mesh *m = new mf_mesh();
+  MF_CUDA(cudaGetDevice(&m->device));
+  m->physics = physics;
+  m->ndpn = physics == MF_LAPLACE ? 1 : 3;
+  m->n_nodes = n_nodes;
+  m->n_cells = n_cells;
+  m->n_dof = n_nodes * m->ndpn;
+  m->structured = cells == nullptr;
+  m->nx = cells ? 0 : nx;
+  m->ny = cells ? 0 : ny;
+  m->nz = cells ? 0 : nz;
+  const int nmat = physics == MF_LAPLACE ? 1 : 2;
+  mf_status st = MF_OK;
+#define SETUP_TRY(expr)               \
+  do {                                \
+    st = (expr);                      \
+    if (st != MF_OK) goto fail;       \
+  } while (0)
+#define SETUP_CUDA(call)                                                                         \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      mf_set_error("mf_setup_mesh: %s failed: %s", #call, cudaGetErrorString(e_));               \
+      st = e_ == cudaErrorMemoryAllocation ? MF_ERR_OOM : MF_ERR_CUDA;                           \
+      goto fail;                                                                                 \
+    }                                                                                            \
+  } while (0)
+  {
+    SETUP_TRY(dmalloc(&m->X, 3 * n_nodes));
+    SETUP_TRY(dmalloc(&m->X32, 3 * n_nodes));
+    SETUP_TRY(dmalloc(&m->mat, nmat * n_cells));
+    SETUP_TRY(dmalloc(&m->mat32, nmat * n_cells));
+    SETUP_TRY(dmalloc(&m->dmask, n_nodes));
+    SETUP_CUDA(cudaMemcpyAsync(m->X, coords, 3 * n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (cells) {
+      SETUP_TRY(dmalloc(&m->cells, 8 * n_cells));
+      SETUP_CUDA(cudaMemcpyAsync(m->cells, cells, 8 * n_cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    if (dirichlet)
+      SETUP_CUDA(cudaMemcpyAsync(m->dmask, dirichlet, n_nodes, cudaMemcpyDeviceToDevice, s));
+    else
+      SETUP_CUDA(cudaMemsetAsync(m->dmask, 0, n_nodes, s));
+    to_f32_kernel<<<blocks_for(3 * n_nodes), kThreads, 0, s>>>(m->X, m->X32, 3 * n_nodes);
+    SETUP_CUDA(cudaGetLastError());
+
+    // validation (uses the caller's material array before conversion)
+    ValidateOut *dv = nullptr;
+    SETUP_TRY(dmalloc(&dv, 1));
+    ValidateOut hv = {0, 0, (long long)n_cells};
+    SETUP_CUDA(cudaMemcpyAsync(dv, &hv, sizeof(hv), cudaMemcpyHostToDevice, s));
+    MeshView v = m->view();
+    v.mat = mat;
+    validate_kernel<<<blocks_for(n_cells), kThreads, 0, s>>>(v, physics, dv);
+    SETUP_CUDA(cudaGetLastError());
+    SETUP_CUDA(cudaMemcpyAsync(&hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, s));
+    SETUP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(dv);
+    if (hv.flags) {
+      mf_set_error("mf_setup_mesh: invalid mesh (element %lld:%s%s%s%s)", hv.first_bad,
+                   hv.flags & BAD_DET ? " det J <= 0" : "", hv.flags & BAD_NODE ? " node id out of range" : "",
+                   hv.flags & BAD_COORD ? " non-finite coordinate" : "", hv.flags & BAD_MAT ? " bad material" : "");
+      st = MF_ERR_MESH;
+      goto fail;
+    }
+    m->all_affine = hv.not_affine == 0;
+    material_kernel<<<blocks_for(n_cells), kThreads, 0, s>>>(mat, m->mat, m->mat32, n_cells, physics);
+    SETUP_CUDA(cudaGetLastError());
+
+    // Dirichlet node list
+    std::vector<uint8_t> hmask(n_nodes);
+    SETUP_CUDA(cudaMemcpyAsync(hmask.data(), m->dmask, n_nodes, cudaMemcpyDeviceToHost, s));
+    SETUP_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> dn;
+    for (int64_t i = 0; i < n_nodes; ++i)
+      if (hmask[i]) dn.push_back((int32_t)i);
+    m->n_dnodes = (int64_t)dn.size();
+    m->n_free = (n_nodes - m->n_dnodes) * m->ndpn;
+    SETUP_TRY(dmalloc(&m->dnodes, dn.size()));
+    if (!dn.empty())
+      SETUP_CUDA(cudaMemcpyAsync(m->dnodes, dn.data(), dn.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+
+    if (cells) {
+      m->h_cells.resize(8 * n_cells);
+      SETUP_CUDA(cudaMemcpyAsync(m->h_cells.data(), cells, 8 * n_cells * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      SETUP_CUDA(cudaStreamSynchronize(s));
+      SETUP_TRY(colour_elements(m, s));
+    } else {
+      m->n_colours = 8;  // parity colouring of the box
+    }
+    SETUP_CUDA(cudaStreamSynchronize(s));
+  }
+  *out = m;
+  return MF_OK;
+fail:
+  cudaStreamSynchronize(s);
+  free_mesh(m);
+  return st;
+#undef SETUP_TRY
+#undef SETUP_CUDA
+}
+
+extern "C" mf_status mf_destroy_mesh(mf_mesh *mesh) {
+  mf_clear_error();
+  if (!mesh) return MF_OK;
+  MF_CUDA(cudaDeviceSynchronize());
+  free_mesh(mesh);
+  return MF_OK;
+}
+
+extern "C" mf_status mf_mesh_query(const mf_mesh *m, int64_t *n_nodes, int64_t *n_cells, int64_t *n_dof,
+                                   int64_t *n_free, int32_t *n_colours, int32_t *flags) {
+  MF_ARG(m != nullptr, "mf_mesh_query: mesh is NULL");
+  if (n_nodes) *n_nodes = m->n_nodes;
+  if (n_cells) *n_cells = m->n_cells;
+  if (n_dof) *n_dof = m->n_dof;
+  if (n_free) *n_free = m->n_free;
+  if (n_colours) *n_colours = m->n_colours;
+  if (flags) *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0);
+  return MF_OK;
+}
+
+extern "C" mf_status mf_set_apply_variant(mf_mesh *m, int variant) {
+  MF_ARG(m != nullptr, "mf_set_apply_variant: mesh is NULL");
+  MF_ARG(variant == MF_VARIANT_AUTO || variant == MF_VARIANT_REFERENCE, "mf_set_apply_variant: unknown variant %d",
+         variant);
+  m->variant = variant;
+  return MF_OK;
+}

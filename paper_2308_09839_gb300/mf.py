@@ -1,0 +1,307 @@
+"""Thin ctypes binding to ``libmf.so`` (argument marshalling only).
+
+Every function of ``include/mf.h`` is exposed under the same name; tensors are passed as device
+pointers (``tensor.data_ptr()``) and the stream defaults to PyTorch's current CUDA stream.  Nothing
+here computes: when the library is missing the import fails loudly (no CPU fallback).
+
+``Mesh`` and ``Csr`` are small owners of the opaque handles with the same calls as methods.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmf.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is not built; run `python -m paper_2308_09839_gb300.build` "
+                      "(or __graft_entry__.build()) first")
+lib = C.CDLL(_LIB_PATH)
+
+MF_OK, MF_NOT_CONVERGED = 0, 1
+MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_MESH, MF_ERR_OOM, MF_ERR_BREAKDOWN, MF_ERR_TIMEOUT, MF_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+MF_LAPLACE, MF_ELASTICITY = 0, 1
+MF_VARIANT_AUTO, MF_VARIANT_REFERENCE = 0, 1
+MF_OP_MATFREE, MF_OP_CSR = 0, 1
+MF_PREC_FP64, MF_PREC_MIXED_IR = 0, 1
+MF_PC_NONE, MF_PC_JACOBI = 0, 1
+
+STATUS_NAMES = {0: "MF_OK", 1: "MF_NOT_CONVERGED", -1: "MF_ERR_ARG", -2: "MF_ERR_CUDA", -3: "MF_ERR_MESH",
+                -4: "MF_ERR_OOM", -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_UNSUPPORTED"}
+
+vp = C.c_void_p
+i32, i64, f64 = C.c_int32, C.c_int64, C.c_double
+
+
+class mf_solve_opts(C.Structure):
+    _fields_ = [("op", i32), ("precision", i32), ("precond", i32), ("max_iter", i32), ("rtol", f64),
+                ("check_every", i32), ("use_graph", i32), ("timeout_s", f64), ("inner_rtol", f64),
+                ("max_outer", i32), ("csr", vp)]
+
+
+class mf_solve_info(C.Structure):
+    _fields_ = [("iters", i32), ("outer_iters", i32), ("status", i32), ("reserved", i32), ("rel_res", f64),
+                ("rel_res_true", f64), ("seconds", f64)]
+
+
+_SIGS = {
+    "mf_setup_mesh": (C.c_int, [C.c_int, i64, i64, vp, vp, i32, i32, i32, vp, vp, vp, C.POINTER(vp)]),
+    "mf_destroy_mesh": (C.c_int, [vp]),
+    "mf_mesh_query": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
+                                C.POINTER(i32), C.POINTER(i32)]),
+    "mf_set_apply_variant": (C.c_int, [vp, C.c_int]),
+    "mf_apply_laplace": (C.c_int, [vp, vp, vp, vp]),
+    "mf_apply_elasticity": (C.c_int, [vp, vp, vp, vp]),
+    "mf_apply_f32": (C.c_int, [vp, vp, vp, vp]),
+    "mf_apply_multi": (C.c_int, [vp, i32, vp, vp, vp]),
+    "mf_assemble_csr": (C.c_int, [vp, vp, C.POINTER(vp)]),
+    "mf_csr_query": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
+    "mf_csr_export": (C.c_int, [vp, vp, vp, vp, vp]),
+    "mf_spmv_csr": (C.c_int, [vp, vp, vp, vp]),
+    "mf_destroy_csr": (C.c_int, [vp]),
+    "mf_solve_opts_default": (None, [C.POINTER(mf_solve_opts)]),
+    "mf_cg_solve": (C.c_int, [vp, C.POINTER(mf_solve_opts), vp, vp, C.POINTER(mf_solve_info), vp]),
+    "mf_kernel_launches": (i64, []),
+    "mf_last_error": (C.c_char_p, []),
+    "mf_version": (C.c_char_p, []),
+}
+EXPORTED = tuple(_SIGS)
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class MfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.mf_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def check(status: int, where: str, ok=(MF_OK,)) -> int:
+    if status not in ok:
+        raise MfError(status, where)
+    return status
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+# ----------------------------------------------------------------------- same-name functions ----
+
+def mf_setup_mesh(physics, n_nodes, n_cells, coords, cells, nx, ny, nz, mat, dirichlet, stream=None) -> int:
+    h = vp()
+    check(lib.mf_setup_mesh(physics, n_nodes, n_cells, _ptr(coords), _ptr(cells), nx, ny, nz, _ptr(mat),
+                            _ptr(dirichlet), _stream(stream), C.byref(h)), "mf_setup_mesh")
+    return h.value
+
+
+def mf_destroy_mesh(h) -> None:
+    check(lib.mf_destroy_mesh(h), "mf_destroy_mesh")
+
+
+def mf_mesh_query(h) -> dict:
+    a, b, c, d = i64(), i64(), i64(), i64()
+    e, f = i32(), i32()
+    check(lib.mf_mesh_query(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e), C.byref(f)), "mf_mesh_query")
+    return dict(n_nodes=a.value, n_cells=b.value, n_dof=c.value, n_free=d.value, n_colours=e.value,
+                structured=bool(f.value & 1), all_affine=bool(f.value & 2))
+
+
+def mf_set_apply_variant(h, variant: int) -> None:
+    check(lib.mf_set_apply_variant(h, variant), "mf_set_apply_variant")
+
+
+def mf_apply_laplace(h, x, y, stream=None) -> None:
+    check(lib.mf_apply_laplace(h, _ptr(x), _ptr(y), _stream(stream)), "mf_apply_laplace")
+
+
+def mf_apply_elasticity(h, x, y, stream=None) -> None:
+    check(lib.mf_apply_elasticity(h, _ptr(x), _ptr(y), _stream(stream)), "mf_apply_elasticity")
+
+
+def mf_apply_f32(h, x, y, stream=None) -> None:
+    check(lib.mf_apply_f32(h, _ptr(x), _ptr(y), _stream(stream)), "mf_apply_f32")
+
+
+def mf_apply_multi(h, nrhs, X, Y, stream=None) -> None:
+    check(lib.mf_apply_multi(h, nrhs, _ptr(X), _ptr(Y), _stream(stream)), "mf_apply_multi")
+
+
+def mf_assemble_csr(h, stream=None) -> int:
+    out = vp()
+    check(lib.mf_assemble_csr(h, _stream(stream), C.byref(out)), "mf_assemble_csr")
+    return out.value
+
+
+def mf_csr_query(a) -> dict:
+    n, z = i64(), i64()
+    rp, cl, vl = vp(), vp(), vp()
+    check(lib.mf_csr_query(a, C.byref(n), C.byref(z), C.byref(rp), C.byref(cl), C.byref(vl)), "mf_csr_query")
+    return dict(n_rows=n.value, nnz=z.value, rowptr=rp.value, col=cl.value, val=vl.value)
+
+
+def mf_csr_export(a, rowptr, col, val, stream=None) -> None:
+    check(lib.mf_csr_export(a, _ptr(rowptr), _ptr(col), _ptr(val), _stream(stream)), "mf_csr_export")
+
+
+def mf_spmv_csr(a, x, y, stream=None) -> None:
+    check(lib.mf_spmv_csr(a, _ptr(x), _ptr(y), _stream(stream)), "mf_spmv_csr")
+
+
+def mf_destroy_csr(a) -> None:
+    check(lib.mf_destroy_csr(a), "mf_destroy_csr")
+
+
+def mf_solve_opts_default() -> mf_solve_opts:
+    o = mf_solve_opts()
+    lib.mf_solve_opts_default(C.byref(o))
+    return o
+
+
+def mf_cg_solve(h, opts: mf_solve_opts, b, x, stream=None, ok=(MF_OK, MF_NOT_CONVERGED)) -> mf_solve_info:
+    info = mf_solve_info()
+    st = lib.mf_cg_solve(h, C.byref(opts), _ptr(b), _ptr(x), C.byref(info), _stream(stream))
+    check(st, "mf_cg_solve", ok)
+    return info
+
+
+def mf_kernel_launches() -> int:
+    return int(lib.mf_kernel_launches())
+
+
+def mf_last_error() -> str:
+    return lib.mf_last_error().decode(errors="replace")
+
+
+def mf_version() -> str:
+    return lib.mf_version().decode()
+
+
+# ----------------------------------------------------------------------------- handle owners ----
+
+class Mesh:
+    """Owner of an ``mf_mesh`` handle.  Arrays are torch tensors on the current CUDA device."""
+
+    def __init__(self, physics: str, coords, mat, dirichlet=None, cells=None, dims=None, stream=None):
+        self.physics = MF_LAPLACE if physics == "laplace" else MF_ELASTICITY
+        n_nodes = coords.shape[0]
+        n_cells = cells.shape[0] if cells is not None else dims[0] * dims[1] * dims[2]
+        nx, ny, nz = dims if (cells is None) else (0, 0, 0)
+        self._keep = (coords, mat, dirichlet, cells)
+        self.h = mf_setup_mesh(self.physics, n_nodes, n_cells, coords, cells, nx, ny, nz, mat, dirichlet, stream)
+        self.info = mf_mesh_query(self.h)
+        self._keep = None
+        self.device = coords.device
+
+    @classmethod
+    def from_problem(cls, p, device="cuda", structured=True, stream=None):
+        """Build from a ``paper_2308_09839_gb300.inputs.Problem``."""
+        coords = torch.from_numpy(p.coords).to(device)
+        mat = torch.from_numpy(p.mat).to(device).contiguous()
+        dirichlet = torch.from_numpy(p.dirichlet).to(device)
+        cells = None if structured else torch.from_numpy(p.cell_array()).to(device)
+        return cls(p.physics, coords, mat, dirichlet, cells, (p.nx, p.ny, p.nz), stream)
+
+    @property
+    def n_dof(self) -> int:
+        return self.info["n_dof"]
+
+    def set_variant(self, variant: int) -> None:
+        mf_set_apply_variant(self.h, variant)
+
+    def apply(self, x, y=None, stream=None):
+        if y is None:
+            y = torch.empty_like(x)
+        if x.dtype == torch.float32:
+            mf_apply_f32(self.h, x, y, stream)
+        elif self.physics == MF_LAPLACE:
+            mf_apply_laplace(self.h, x, y, stream)
+        else:
+            mf_apply_elasticity(self.h, x, y, stream)
+        return y
+
+    def apply_multi(self, X, nrhs, Y=None, stream=None):
+        if Y is None:
+            Y = torch.empty_like(X)
+        mf_apply_multi(self.h, nrhs, X, Y, stream)
+        return Y
+
+    def assemble_csr(self, stream=None) -> "Csr":
+        return Csr(mf_assemble_csr(self.h, stream), self.device)
+
+    def cg(self, b, x=None, stream=None, **kw):
+        o = mf_solve_opts_default()
+        csr = kw.pop("csr", None)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        if csr is not None:
+            o.csr = csr.h
+            o.op = MF_OP_CSR
+        if x is None:
+            x = torch.empty_like(b)
+        info = mf_cg_solve(self.h, o, b, x, stream)
+        return x, info
+
+    def close(self):
+        if getattr(self, "h", None):
+            mf_destroy_mesh(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Csr:
+    def __init__(self, h: int, device):
+        self.h = h
+        self.device = device
+        self.info = mf_csr_query(h)
+
+    def spmv(self, x, y=None, stream=None):
+        if y is None:
+            y = torch.empty_like(x)
+        mf_spmv_csr(self.h, x, y, stream)
+        return y
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        q = self.info
+        rp = torch.empty(q["n_rows"] + 1, dtype=torch.int64, device=self.device)
+        cl = torch.empty(q["nnz"], dtype=torch.int32, device=self.device)
+        vl = torch.empty(q["nnz"], dtype=torch.float64, device=self.device)
+        mf_csr_export(self.h, rp, cl, vl)
+        torch.cuda.synchronize()
+        return sp.csr_matrix((vl.cpu().numpy(), cl.cpu().numpy(), rp.cpu().numpy()), shape=(q["n_rows"], q["n_rows"]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            mf_destroy_csr(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

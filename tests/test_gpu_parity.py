@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Tolerance: FP64 results agree with the oracle to <= 1e-12 relative in the 2-norm (rounding order
+differs only); FP32 results state their error.  Integer / structural results (CSR pattern) are
+compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fem, solvers
+from paper_2308_09839_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+from paper_2308_09839_gb300 import mf  # noqa: E402
+
+DEV = "cuda"
+TOL64 = 1e-12
+
+
+def rel2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def oracle_apply(p, x, cells=None):
+    return fem.apply(p.physics, p.coords, p.cell_array() if cells is None else cells, p.mat, p.dirichlet, x)
+
+
+def gpu_apply(mesh, x):
+    y = mesh.apply(gpu(x))
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+PROBLEMS = {
+    "laplace16_jitter": lambda: inputs.small_laplace_16(seed=0),
+    "laplace_5x7x3": lambda: inputs.laplace_box(5, ny=7, nz=3, jitter=0.2, seed=1),
+    "laplace_1x1x1": lambda: inputs.laplace_box(1, jitter=0.0, seed=2),
+    "laplace_1x2x3": lambda: inputs.laplace_box(1, ny=2, nz=3, jitter=0.0, seed=3),
+    "laplace_cartesian_layers": lambda: inputs.laplace_box(12, jitter=0.0, sigma=0.5, layered=True, seed=4),
+    "elast8_jitter": lambda: inputs.elasticity_box(8, jitter=0.2, seed=5),
+    "elast_cartesian_6x5x9": lambda: inputs.elasticity_box(6, ny=5, nz=9, jitter=0.0, seed=6),
+    "elast_1x1x1": lambda: inputs.elasticity_box(1, jitter=0.0, seed=7),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PROBLEMS))
+@pytest.mark.parametrize("variant", [mf.MF_VARIANT_AUTO, mf.MF_VARIANT_REFERENCE])
+@pytest.mark.parametrize("structured", [True, False])
+def test_apply_fp64_matches_oracle(name, variant, structured):
+    p = PROBLEMS[name]()
+    mesh = mf.Mesh.from_problem(p, structured=structured)
+    mesh.set_variant(variant)
+    for seed in (0, 1):
+        x = p.x(seed)
+        y = gpu_apply(mesh, x)
+        ref = oracle_apply(p, x)
+        assert rel2(y, ref) <= TOL64, (name, seed, rel2(y, ref))
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+def test_apply_renumbered_mesh(physics):
+    """General connectivity: randomly permuted node and element numbering (greedy colouring)."""
+    p = (inputs.laplace_box if physics == "laplace" else inputs.elasticity_box)(7, jitter=0.2, seed=11)
+    c2, cl2, d2, nperm, eperm = inputs.renumber(p.coords, p.cell_array(), p.dirichlet, 3)
+    mat2 = p.mat[eperm]
+    nd = p.ndpn
+    x = p.x()
+    x2 = np.empty_like(x).reshape(-1, nd)
+    x2[nperm] = x.reshape(-1, nd)
+    x2 = x2.reshape(-1)
+    mesh = mf.Mesh(physics, gpu(c2), gpu(mat2), gpu(d2), gpu(cl2))
+    assert mesh.info["n_colours"] >= 8
+    y = gpu_apply(mesh, x2)
+    ref = fem.apply(physics, c2, cl2, mat2, d2, x2)
+    assert rel2(y, ref) <= TOL64
+
+
+def test_apply_dirichlet_entries_ignored_and_identity_rows():
+    p = inputs.small_laplace_16(seed=2)
+    mesh = mf.Mesh.from_problem(p)
+    x = inputs.uniform_vector(p.n_dof, 5)  # nonzero on Dirichlet nodes
+    y = gpu_apply(mesh, x)
+    d = p.dirichlet.astype(bool)
+    assert np.array_equal(y[d], x[d])
+    assert rel2(y, oracle_apply(p, x)) <= TOL64
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+def test_apply_bitwise_deterministic(physics):
+    p = (inputs.laplace_box if physics == "laplace" else inputs.elasticity_box)(10, jitter=0.2, seed=8)
+    mesh = mf.Mesh.from_problem(p)
+    x = gpu(p.x())
+    y1 = mesh.apply(x).clone()
+    y2 = mesh.apply(x).clone()
+    assert torch.equal(y1, y2)
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+def test_apply_fp32_error_vs_oracle(physics):
+    """FP32 geometry and arithmetic: error against the FP64 oracle stated and bounded."""
+    p = (inputs.laplace_box if physics == "laplace" else inputs.elasticity_box)(10, jitter=0.2, seed=9)
+    mesh = mf.Mesh.from_problem(p)
+    x = p.x()
+    y = mesh.apply(gpu(x).float())
+    torch.cuda.synchronize()
+    err = rel2(y.double().cpu().numpy(), oracle_apply(p, x))
+    print(f"fp32 apply rel err {physics}: {err:.2e}")
+    assert err < 1e-5
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+@pytest.mark.parametrize("nrhs", [1, 3, 16])
+def test_apply_multi_rhs(physics, nrhs):
+    p = (inputs.laplace_box if physics == "laplace" else inputs.elasticity_box)(6, jitter=0.2, seed=10)
+    mesh = mf.Mesh.from_problem(p)
+    nd = p.ndpn
+    xs = [p.x(seed=s) for s in range(nrhs)]
+    X = np.stack([x.reshape(-1, nd) for x in xs], axis=1).reshape(-1)  # [node][rhs][k]
+    Y = mesh.apply_multi(gpu(X), nrhs)
+    torch.cuda.synchronize()
+    Y = Y.cpu().numpy().reshape(p.n_nodes, nrhs, nd)
+    for r in range(nrhs):
+        assert rel2(Y[:, r, :].reshape(-1), oracle_apply(p, xs[r])) <= TOL64
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+@pytest.mark.parametrize("structured", [True, False])
+def test_csr_matches_oracle(physics, structured):
+    p = (inputs.laplace_box if physics == "laplace" else inputs.elasticity_box)(5, ny=4, nz=6, jitter=0.2, seed=12)
+    mesh = mf.Mesh.from_problem(p, structured=structured)
+    A = mesh.assemble_csr()
+    G = A.to_scipy()
+    R = fem.assemble_csr(p.physics, p.coords, p.cell_array(), p.mat, p.dirichlet, p.n_nodes)
+    # identical sparsity (structural, exact)
+    assert np.array_equal(G.indptr, R.indptr) and np.array_equal(G.indices, R.indices)
+    assert np.max(np.abs(G.data - R.data)) <= 1e-13 * np.max(np.abs(R.data))
+    x = p.x()
+    y = A.spmv(gpu(x))
+    torch.cuda.synchronize()
+    assert rel2(y.cpu().numpy(), R @ x) <= TOL64
+    assert rel2(y.cpu().numpy(), oracle_apply(p, x)) <= TOL64
+
+
+def _oracle_cg(p, rtol=1e-8):
+    A = fem.assemble_csr(p.physics, p.coords, p.cell_array(), p.mat, p.dirichlet, p.n_nodes)
+    b = p.b()
+    x, it, _ = solvers.cg(lambda v: A @ v, b, rtol=rtol)
+    return A, b, x, it
+
+
+@pytest.mark.parametrize("op", ["matfree", "csr"])
+def test_cg_small_laplace_matches_oracle(op):
+    """16^3 jittered Laplace, lognormal(0,1) kappa: iterations within +-1 % (at least +-2) of the
+    oracle's, true residual <= 1e-8, solution close to the oracle's."""
+    p = inputs.small_laplace_16(seed=0)
+    A, b, xo, it_o = _oracle_cg(p)
+    mesh = mf.Mesh.from_problem(p)
+    kw = {}
+    if op == "csr":
+        kw["csr"] = mesh.assemble_csr()
+    x, info = mesh.cg(gpu(b), **kw)
+    torch.cuda.synchronize()
+    x = x.cpu().numpy()
+    assert info.status == mf.MF_OK
+    assert abs(info.iters - it_o) <= max(2, math.ceil(0.01 * it_o)), (info.iters, it_o)
+    assert info.rel_res_true <= 1.05e-8
+    assert np.linalg.norm(b - A @ x) <= 1.05e-8 * np.linalg.norm(b)
+    assert rel2(x, xo) <= 1e-5
+
+
+def test_cg_elasticity_matches_oracle():
+    p = inputs.elasticity_box(8, jitter=0.2, seed=13)
+    A, b, xo, it_o = _oracle_cg(p)
+    mesh = mf.Mesh.from_problem(p)
+    x, info = mesh.cg(gpu(b))
+    torch.cuda.synchronize()
+    assert info.status == mf.MF_OK
+    assert abs(info.iters - it_o) <= max(2, math.ceil(0.01 * it_o)), (info.iters, it_o)
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.05e-8 * np.linalg.norm(b)
+
+
+def test_cg_graph_and_plain_launches_agree_bitwise():
+    p = inputs.small_laplace_16(seed=1)
+    mesh = mf.Mesh.from_problem(p)
+    b = gpu(p.b())
+    x1, i1 = mesh.cg(b, use_graph=1, check_every=16)
+    x1 = x1.clone()
+    x2, i2 = mesh.cg(b, use_graph=0, check_every=5)
+    assert i1.iters == i2.iters
+    assert torch.equal(x1, x2)
+
+
+def test_jacobi_pcg_matches_oracle():
+    p = inputs.small_laplace_16(seed=3)
+    A, b, _, _ = _oracle_cg(p)
+    dg = fem.diagonal(p.physics, p.coords, p.cell_array(), p.mat, p.dirichlet, p.n_nodes)
+    _, it_o, _ = solvers.pcg(lambda v: A @ v, b, lambda r: r / dg, rtol=1e-8)
+    mesh = mf.Mesh.from_problem(p)
+    x, info = mesh.cg(gpu(b), precond=mf.MF_PC_JACOBI)
+    assert info.status == mf.MF_OK
+    assert abs(info.iters - it_o) <= max(2, math.ceil(0.01 * it_o)), (info.iters, it_o)
+    assert info.rel_res_true <= 1.05e-8
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+def test_mixed_precision_ir(physics):
+    """FP32 inner CG (rtol 1e-4) inside FP64 refinement reaches a 1e-10 FP64 residual; the error
+    against the oracle's FP64 solution is stated."""
+    p = (inputs.laplace_box if physics == "laplace" else inputs.elasticity_box)(10, jitter=0.1, seed=14)
+    A, b, xo, _ = _oracle_cg(p, rtol=1e-12)
+    mesh = mf.Mesh.from_problem(p)
+    x, info = mesh.cg(gpu(b), precision=mf.MF_PREC_MIXED_IR, rtol=1e-10, inner_rtol=1e-4)
+    torch.cuda.synchronize()
+    x = x.cpu().numpy()
+    assert info.status == mf.MF_OK
+    assert info.rel_res_true <= 1.05e-10
+    assert np.linalg.norm(b - A @ x) <= 1.05e-10 * np.linalg.norm(b)
+    err = rel2(x, xo)
+    print(f"mixed IR {physics}: outer {info.outer_iters} inner {info.iters} err vs oracle {err:.2e}")
+    assert err < 1e-6
+
+
+# ------------------------------------------------------------------------------------- errors ----
+
+def test_setup_rejects_inverted_element():
+    p = inputs.laplace_box(3, seed=0)
+    c = p.coords.copy()
+    inner = inputs.node_id(1, 1, 1, 3, 3)
+    c[inner] = c[inputs.node_id(2, 2, 2, 3, 3)] + 0.2  # push a node through its neighbours
+    with pytest.raises(mf.MfError) as e:
+        mf.Mesh("laplace", gpu(c), gpu(p.mat), gpu(p.dirichlet), None, (3, 3, 3))
+    assert e.value.status == mf.MF_ERR_MESH
+
+
+@pytest.mark.parametrize("what", ["nan_coord", "neg_kappa", "bad_node"])
+def test_setup_rejects_bad_input(what):
+    p = inputs.laplace_box(3, seed=0)
+    c, k, cells = p.coords.copy(), p.mat.copy(), p.cell_array().copy()
+    if what == "nan_coord":
+        c[5, 1] = np.nan
+    elif what == "neg_kappa":
+        k[3] = -1.0
+    else:
+        cells[2, 4] = p.n_nodes + 7
+    with pytest.raises(mf.MfError) as e:
+        mf.Mesh("laplace", gpu(c), gpu(k), gpu(p.dirichlet), gpu(cells) if what == "bad_node" else None, (3, 3, 3))
+    assert e.value.status == mf.MF_ERR_MESH
+
+
+def test_apply_rejects_aliasing_and_wrong_physics():
+    p = inputs.laplace_box(3, seed=0)
+    mesh = mf.Mesh.from_problem(p)
+    x = gpu(p.x())
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_apply_laplace(mesh.h, x, x)
+    assert e.value.status == mf.MF_ERR_ARG
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_apply_elasticity(mesh.h, x, torch.empty_like(x))
+    assert e.value.status == mf.MF_ERR_ARG
+
+
+def test_cg_not_converged_and_breakdown_statuses():
+    p = inputs.small_laplace_16(seed=0)
+    mesh = mf.Mesh.from_problem(p)
+    b = p.b()
+    _, info = mesh.cg(gpu(b), max_iter=3)
+    assert info.status == mf.MF_NOT_CONVERGED and info.iters == 3
+    bn = b.copy()
+    bn[17] = np.nan
+    with pytest.raises(mf.MfError) as e:
+        mesh.cg(gpu(bn))
+    assert e.value.status == mf.MF_ERR_BREAKDOWN
+    # the context stays usable
+    x, info = mesh.cg(gpu(b))
+    assert info.status == mf.MF_OK
+
+
+def test_cg_timeout_status():
+    p = inputs.laplace_box(24, jitter=0.2, seed=0)
+    mesh = mf.Mesh.from_problem(p)
+    with pytest.raises(mf.MfError) as e:
+        mesh.cg(gpu(p.b()), timeout_s=1e-9, check_every=1, rtol=1e-14)
+    assert e.value.status == mf.MF_ERR_TIMEOUT
+
+
+# ------------------------------------------------------------- full-size sampled parity ----
+
+def _sampled_parity(p, n_rows=1500, seed=0):
+    mesh = mf.Mesh.from_problem(p)
+    x = p.x()
+    y = gpu_apply(mesh, x)
+    rows = np.random.default_rng(seed).choice(p.n_dof, n_rows, replace=False)
+    el = fem.adjacent_elements_box(rows // p.ndpn, p.nx, p.ny, p.nz)
+    cells = inputs.box_cells(p.nx, p.ny, p.nz)
+    ref = fem.apply_rows(p.physics, p.coords, cells, p.mat, p.dirichlet, x, rows, el)
+    return rel2(y[rows], ref)
+
+
+def test_full_size_laplace_256_sampled():
+    """256^3 Cartesian Laplace (the benchmarked launch configuration): sampled rows vs the oracle."""
+    assert _sampled_parity(inputs.cartesian_laplace_256()) <= TOL64
+
+
+def test_full_size_elasticity_160_sampled():
+    assert _sampled_parity(inputs.cartesian_elasticity_160()) <= TOL64
