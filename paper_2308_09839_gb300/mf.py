@@ -248,7 +248,7 @@ class Mesh:
     def assemble_csr(self, stream=None) -> "Csr":
         return Csr(mf_assemble_csr(self.h, stream), self.device)
 
-    def cg(self, b, x=None, stream=None, **kw):
+    def cg(self, b, x=None, stream=None, ok=(MF_OK, MF_NOT_CONVERGED), **kw):
         o = mf_solve_opts_default()
         csr = kw.pop("csr", None)
         for k, v in kw.items():
@@ -258,7 +258,7 @@ class Mesh:
             o.op = MF_OP_CSR
         if x is None:
             x = torch.empty_like(b)
-        info = mf_cg_solve(self.h, o, b, x, stream)
+        info = mf_cg_solve(self.h, o, b, x, stream, ok=ok)
         return x, info
 
     def close(self):
