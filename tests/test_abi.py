@@ -16,7 +16,7 @@ def declared_functions():
         if fn.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names += re.findall(r"^\s*(?:mf_status|void|const char \*)\s*\*?\s*(mf_\w+)\s*\(", txt, flags=re.M)
+            names += re.findall(r"^\s*(?:mf_status|void|int64_t|const char \*)\s*\*?\s*(mf_\w+)\s*\(", txt, flags=re.M)
     return names
 
 
