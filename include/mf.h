@@ -195,6 +195,32 @@ void mf_solve_opts_default(mf_solve_opts *opts);
 mf_status mf_cg_solve(mf_mesh *mesh, const mf_solve_opts *opts, const double *b, double *x,
                       mf_solve_info *info, mf_stream stream);
 
+/*
+ * mf_cg_solve_noalloc - the unpreconditioned FP64 CG of mf_cg_solve for callers that cannot
+ * allocate device memory while they run: for example an application that hands the whole device
+ * to its own memory pool at start-up, or one whose memory budget is enforced outside CUDA, where a
+ * cudaMalloc inside a solve would fail or is not allowed.  The paper has no counterpart to this
+ * call; it is a deployment convenience.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch (three DoF vectors,
+ * the reduction partials and the device scalars) is a fixed array with static storage inside the
+ * library, sized for MF_NOALLOC_MAX_DOF degrees of freedom (about 6 MB); every GPU that loads the
+ * library holds that array until the process exits.  Larger problems are rejected with
+ * MF_ERR_ARG.  The first call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.
+ *
+ * All calls share the one array and it keeps the previous call's contents (each call clears what
+ * must start at zero itself).  Calls whose work overlaps on the GPU - on two streams, or from two
+ * host threads - race on the array: serialise them.
+ *   mesh, b, x, info, stream: as for mf_cg_solve; x is used as the iterate and holds the solution.
+ *   opts: op MF_OP_MATFREE or MF_OP_CSR (with opts->csr), precision MF_PREC_FP64, precond
+ *   MF_PC_NONE; rtol, max_iter, check_every and timeout_s as for mf_cg_solve; use_graph is ignored.
+ * Returns MF_OK, MF_NOT_CONVERGED, MF_ERR_BREAKDOWN, MF_ERR_TIMEOUT, MF_ERR_ARG or MF_ERR_CUDA.
+ */
+#define MF_NOALLOC_MAX_DOF 262144
+mf_status mf_cg_solve_noalloc(const mf_mesh *mesh, const mf_solve_opts *opts, const double *b, double *x,
+                              mf_solve_info *info, mf_stream stream);
+
 /* Message describing the last failure in the calling thread ("" if none).  Valid until the next
  * failing call in the same thread. */
 const char *mf_last_error(void);

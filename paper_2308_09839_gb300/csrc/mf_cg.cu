@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cmath>
 #include <functional>
+#include <mutex>
 
 #include "mf_internal.cuh"
 
@@ -494,5 +495,116 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
   }
   if (st == MF_ERR_BREAKDOWN) mf_set_error("mf_cg_solve: breakdown (p^T A p <= 0 or non-finite scalar)");
   if (st == MF_NOT_CONVERGED) mf_set_error("mf_cg_solve: not converged within the iteration limit");
+  return st;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free CG (mf_cg_solve_noalloc).
+//
+// Some callers cannot allocate device memory once they are running: applications that reserve the
+// whole device for their own memory pool at start-up, or that run under a memory budget enforced
+// outside CUDA, and code paths where a cudaMalloc would stall or be forbidden.  For them the
+// solver's scratch (three DoF vectors, the block partials of the reductions and the device
+// scalars) lives in one fixed-size array with static storage inside this library.  Every GPU that
+// loads the library holds the array until the process exits.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxDof = 262144;  // MF_NOALLOC_MAX_DOF in mf.h
+constexpr int64_t kNoAllocScalarsDoubles = (sizeof(CgScalars) + sizeof(double) - 1) / sizeof(double);
+constexpr int64_t kNoAllocDoubles = 3 * kNoAllocMaxDof + 4 * kRedBlocks + kNoAllocScalarsDoubles;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+static double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array on the current device, looked up once per device.  In host
+// code the array's name is only a host-side stand-in, so kernels get this address instead.
+mf_status noalloc_scratch(double **out) {
+  int dev = 0;
+  MF_CUDA(cudaGetDevice(&dev));
+  MF_ARG(dev >= 0 && dev < kMaxDevices, "mf_cg_solve_noalloc: device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      mf_set_error("mf_cg_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return MF_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = (double *)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MF_OK;
+}
+
+}  // namespace
+
+extern "C" mf_status mf_cg_solve_noalloc(const mf_mesh *m, const mf_solve_opts *o, const double *b, double *x,
+                                         mf_solve_info *info, mf_stream stream) {
+  mf_clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  MF_ARG(m && o && b && x, "mf_cg_solve_noalloc: null argument");
+  MF_ARG(m->n_dof <= kNoAllocMaxDof, "mf_cg_solve_noalloc: %lld DoFs exceed the fixed scratch limit of %lld DoFs",
+         (long long)m->n_dof, (long long)kNoAllocMaxDof);
+  MF_ARG(o->op == MF_OP_MATFREE || (o->op == MF_OP_CSR && o->csr != nullptr && o->csr->n_rows == m->n_dof),
+         "mf_cg_solve_noalloc: op must be MATFREE, or CSR with a matching opts->csr");
+  MF_ARG(o->precision == MF_PREC_FP64 && o->precond == MF_PC_NONE,
+         "mf_cg_solve_noalloc: only FP64 without preconditioner is available");
+  MF_ARG(o->max_iter > 0 && o->rtol > 0 && o->check_every > 0, "mf_cg_solve_noalloc: bad max_iter/rtol/check_every");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *base = nullptr;
+  MF_TRY(noalloc_scratch(&base));
+  const int64_t n = m->n_dof;
+  double *r = base, *p = base + kNoAllocMaxDof, *Ap = base + 2 * kNoAllocMaxDof;
+  double *partials = base + 3 * kNoAllocMaxDof;
+  CgScalars *sc = reinterpret_cast<CgScalars *>(partials + 4 * kRedBlocks);
+  // the array keeps the previous call's contents: the reduction ticket must start at zero
+  MF_CUDA(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
+  const mf_csr *A = o->csr;
+  const bool use_csr = o->op == MF_OP_CSR;
+  OpFn op = [m, A, use_csr](const void *in, void *out, cudaStream_t st, const int *skip) -> mf_status {
+    if (use_csr) return spmv(A, (const double *)in, (double *)out, st, skip);
+    return apply_fp64(m, (const double *)in, (double *)out, st, skip);
+  };
+  mf_count_launches(1);
+  cg_init<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, b, x, r, p, nullptr, partials, sc, o->rtol, o->max_iter);
+  MF_CUDA(cudaGetLastError());
+  CgScalars h{};
+  mf_status st = MF_OK;
+  for (;;) {
+    for (int it = 0; it < o->check_every; ++it) MF_TRY(cg_iteration<double>(op, n, x, r, p, Ap, nullptr, partials, sc, s));
+    MF_CUDA(cudaMemcpyAsync(&h, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    if (h.done) break;
+    if (o->timeout_s > 0 &&
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > o->timeout_s) {
+      mf_set_error("mf_cg_solve_noalloc: timeout (%d iterations)", h.iter);
+      st = MF_ERR_TIMEOUT;
+      break;
+    }
+  }
+  if (st == MF_OK) st = (mf_status)h.status;
+  const int iters = h.iter;
+  const double bb = h.bb, rr = h.rr;
+  // true residual ||b - A x|| with the same operator (Ap is free scratch now)
+  MF_TRY(op(x, Ap, s, nullptr));
+  mf_count_launches(1);
+  residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, Ap, nullptr, partials, sc);
+  MF_CUDA(cudaGetLastError());
+  MF_CUDA(cudaMemcpyAsync(&h, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters;
+    info->outer_iters = 0;
+    info->status = st;
+    info->rel_res = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+    info->rel_res_true = bb > 0 ? std::sqrt(h.res2 / bb) : 0.0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (st == MF_ERR_BREAKDOWN) mf_set_error("mf_cg_solve_noalloc: breakdown (p^T A p <= 0 or non-finite scalar)");
+  if (st == MF_NOT_CONVERGED) mf_set_error("mf_cg_solve_noalloc: not converged within the iteration limit");
   return st;
 }

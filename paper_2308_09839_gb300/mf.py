@@ -62,6 +62,7 @@ _SIGS = {
     "mf_destroy_csr": (C.c_int, [vp]),
     "mf_solve_opts_default": (None, [C.POINTER(mf_solve_opts)]),
     "mf_cg_solve": (C.c_int, [vp, C.POINTER(mf_solve_opts), vp, vp, C.POINTER(mf_solve_info), vp]),
+    "mf_cg_solve_noalloc": (C.c_int, [vp, C.POINTER(mf_solve_opts), vp, vp, C.POINTER(mf_solve_info), vp]),
     "mf_kernel_launches": (i64, []),
     "mf_last_error": (C.c_char_p, []),
     "mf_version": (C.c_char_p, []),
@@ -182,6 +183,18 @@ def mf_cg_solve(h, opts: mf_solve_opts, b, x, stream=None, ok=(MF_OK, MF_NOT_CON
     st = lib.mf_cg_solve(h, C.byref(opts), _ptr(b), _ptr(x), C.byref(info), _stream(stream))
     check(st, "mf_cg_solve", ok)
     return info
+
+
+def mf_cg_solve_noalloc(h, opts: mf_solve_opts, b, x, stream=None, ok=(MF_OK, MF_NOT_CONVERGED)) -> mf_solve_info:
+    """CG whose scratch is a fixed array inside the library (no device allocation; n_dof <=
+    MF_NOALLOC_MAX_DOF)."""
+    info = mf_solve_info()
+    st = lib.mf_cg_solve_noalloc(h, C.byref(opts), _ptr(b), _ptr(x), C.byref(info), _stream(stream))
+    check(st, "mf_cg_solve_noalloc", ok)
+    return info
+
+
+MF_NOALLOC_MAX_DOF = 262144
 
 
 def mf_kernel_launches() -> int:
