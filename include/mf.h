@@ -75,13 +75,17 @@ mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells, const dou
 mf_status mf_destroy_mesh(mf_mesh *mesh);
 
 /* Host outputs (any may be NULL): node, cell and DoF counts, free (unconstrained) DoFs, number of
- * element colours of the scatter, and flags (bit 0: structured, bit 1: every cell affine). */
+ * element colours of the scatter, and flags (bit 0: structured, bit 1: every cell affine, bit 2:
+ * tensor-product grid of axis-aligned cells, which enables the FP64-accurate tile kernels). */
 mf_status mf_mesh_query(const mf_mesh *mesh, int64_t *n_nodes, int64_t *n_cells, int64_t *n_dof,
                         int64_t *n_free, int32_t *n_colours, int32_t *flags);
 
 /*
  * Kernel variants for the operator apply (mf_set_apply_variant):
- *   MF_VARIANT_AUTO       fastest variant that meets FP64 accuracy for this mesh (default)
+ *   MF_VARIANT_AUTO       fastest variant that meets FP64 accuracy for this mesh (default): on a
+ *                         structured tensor-product grid the tile kernel (Walsh-Hadamard form of
+ *                         the 2x2x2 Gauss sums, double-word FP32 arithmetic, owner-computes
+ *                         z-marching tiles); otherwise the reference kernel
  *   MF_VARIANT_REFERENCE  Algorithm 1 as printed: one thread per element, FP64 arithmetic,
  *                         Jacobian at every quadrature point, colour-by-colour scatter
  */

@@ -146,9 +146,11 @@ __global__ void expand_columns(int64_t n_nodes, int nd, const int64_t *__restric
   (void)k;
 }
 
-// y = A x with L threads per row; lanes accumulate strided partial sums, reduced by a fixed
-// shuffle tree (deterministic).
-template <int L>
+// y = A x with L threads per row.  Each lane first issues U independent (value, column) loads,
+// then the U gathers of x, so every thread keeps several memory requests in flight; rows longer
+// than L*U continue in a plain strided loop.  Lanes are reduced by a fixed shuffle tree
+// (deterministic).
+template <int L, int U>
 __global__ void __launch_bounds__(256) spmv_kernel(int64_t n_rows, const int64_t *__restrict__ rowptr,
                                                    const int32_t *__restrict__ col, const double *__restrict__ val,
                                                    const double *__restrict__ x, double *__restrict__ y,
@@ -159,8 +161,20 @@ __global__ void __launch_bounds__(256) spmv_kernel(int64_t n_rows, const int64_t
   const int lane = (int)(gid % L);
   double s = 0.0;
   if (row < n_rows) {
-    const int64_t end = rowptr[row + 1];
-    for (int64_t p = rowptr[row] + lane; p < end; p += L) s += __ldcs(val + p) * __ldg(x + __ldcs(col + p));
+    const int64_t beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
+    double v[U];
+    int32_t c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = beg + lane + (int64_t)u * L;
+      const bool ok = p < end;
+      v[u] = ok ? __ldcs(val + p) : 0.0;
+      c[u] = ok ? __ldcs(col + p) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (c[u] >= 0) s += v[u] * __ldg(x + c[u]);
+    for (int64_t p = beg + lane + (int64_t)U * L; p < end; p += L) s += __ldcs(val + p) * __ldg(x + __ldcs(col + p));
   }
 #pragma unroll
   for (int off = L / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -266,10 +280,9 @@ mf_status spmv(const mf_csr *A, const double *x, double *y, cudaStream_t s, cons
   const int64_t threads = A->n_rows * A->lanes;
   mf_count_launches(1);
   switch (A->lanes) {
-    case 4: spmv_kernel<4><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
-    case 8: spmv_kernel<8><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
-    case 16: spmv_kernel<16><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
-    default: spmv_kernel<32><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+    case 8: spmv_kernel<8, 4><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+    case 16: spmv_kernel<16, 6><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+    default: spmv_kernel<32, 4><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
   }
   MF_CUDA(cudaGetLastError());
   return MF_OK;
@@ -309,7 +322,9 @@ extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr 
   mf_csr *A = new mf_csr();
   A->n_rows = n_rows;
   A->nnz = nnz;
-  A->lanes = nd == 1 ? 8 : 16;
+  int64_t maxrow = 0;
+  for (int64_t r = 0; r < n_rows; ++r) maxrow = std::max(maxrow, rowptr[r + 1] - rowptr[r]);
+  A->lanes = maxrow <= 32 ? 8 : maxrow <= 96 ? 16 : 32;
   int64_t *d_noff = nullptr;
   int32_t *d_nbr = nullptr;
   auto cleanup = [&]() {

@@ -1,0 +1,114 @@
+// Double-word ("double-FP32") arithmetic: a value is the unevaluated sum hi + lo of two floats.
+//
+// GB300 runs FP32 FMAs about 60x faster than FP64 FMAs, so the FP64-accurate operator kernels do
+// their arithmetic on pairs of floats.  The building blocks are the error-free transformations
+// TwoSum (Knuth, TAOCP vol. 2; Moller 1965), Fast2Sum (Dekker 1971) and the FMA-based TwoProd, as
+// analysed for double-word arithmetic by Joldes, Muller and Popescu ("Tight and rigorous error
+// bounds for basic building blocks of double-word arithmetic", ACM TOMS 44(2), 2017).
+//
+// The operators here are "lazy": the sum of the high parts is exact (TwoSum) and the low parts
+// are added in FP32 without renormalising the pair afterwards.  The absolute error of each
+// operation is then O(u^2 (|x| + |y|)) with u = 2^-24, which is what a sum of element
+// contributions needs (the FP64 tolerance is relative to the norm of the whole result, not to
+// each cancelled intermediate).  Pairs are renormalised only where they leave the kernel.
+//
+// All operations use the explicitly rounded intrinsics so the compiler cannot contract or
+// reassociate them.
+#pragma once
+
+#include <stdint.h>
+
+namespace dwa {
+
+struct dw {
+  float h, l;
+};
+
+__device__ __forceinline__ dw make(float h, float l = 0.0f) { return dw{h, l}; }
+
+// TwoSum: s + t == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
+  s = __fadd_rn(a, b);
+  const float ap = __fsub_rn(s, b);
+  const float bp = __fsub_rn(s, ap);
+  t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// Fast2Sum (requires |a| >= |b| or a == 0): s + t == a + b exactly.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &t) {
+  s = __fadd_rn(a, b);
+  t = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ dw add(dw x, dw y) {
+  float s, t;
+  two_sum(x.h, y.h, s, t);
+  return dw{s, __fadd_rn(__fadd_rn(x.l, y.l), t)};
+}
+
+__device__ __forceinline__ dw sub(dw x, dw y) {
+  float s, t;
+  two_sum(x.h, -y.h, s, t);
+  return dw{s, __fadd_rn(__fsub_rn(x.l, y.l), t)};
+}
+
+__device__ __forceinline__ dw neg(dw x) { return dw{-x.h, -x.l}; }
+
+// x * y; the lo*lo term (relative size u^2) is dropped.
+__device__ __forceinline__ dw mul(dw x, dw y) {
+  const float p = __fmul_rn(x.h, y.h);
+  const float e = __fmaf_rn(x.h, y.h, -p);
+  return dw{p, __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, e))};
+}
+
+// x * 2^k (exact for both parts in the normal range).
+__device__ __forceinline__ dw scale(dw x, float pow2) { return dw{__fmul_rn(x.h, pow2), __fmul_rn(x.l, pow2)}; }
+
+// Renormalise so that |lo| <= ulp(hi)/2.
+__device__ __forceinline__ dw norm(dw x) {
+  float s, t;
+  two_sum(x.h, x.l, s, t);
+  return dw{s, t};
+}
+
+// --------------------------------------------------------------------------- conversions ----
+
+// double -> (hi, lo) with integer operations only (the FP64 pipe of GB300 is the scarce unit):
+// hi keeps the leading 24 significand bits (truncated), lo is the remaining 29 bits rounded to a
+// float; |x - (hi + lo)| <= 2^-48 |x|.  Values outside [2^-74, 2^127) and non-finite values take
+// the FP64 conversion path instead.
+__device__ __forceinline__ dw split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  const int e = (int)((bh >> 20) & 0x7ffu);
+  if (e < 949 || e > 1150) {
+    const float h = __double2float_rz(x);
+    return dw{h, __double2float_rn(x - (double)h)};
+  }
+  const unsigned sign = bh & 0x80000000u;
+  const unsigned mhi = ((bh & 0x000fffffu) << 3) | (bl >> 29);
+  const float h = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | mhi);
+  const unsigned rem = bl & 0x1fffffffu;
+  const float lo = __fmul_rn(__uint2float_rn(rem), __uint_as_float((unsigned)(e - 1075 + 127) << 23));
+  return dw{h, __uint_as_float(__float_as_uint(lo) | sign)};
+}
+
+// float -> double exactly by bit manipulation (normal floats; others convert on the FP64 unit).
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// (hi, lo) -> nearest double: one FP64 add.
+__device__ __forceinline__ double to_double(dw x) { return __dadd_rn(f2d(x.h), f2d(x.l)); }
+
+// Host/device-agnostic split of a double constant (setup and constants, not hot paths).
+__host__ __device__ inline dw from_double_slow(double x) {
+  const float h = (float)x;
+  return dw{h, (float)(x - (double)h)};
+}
+
+}  // namespace dwa

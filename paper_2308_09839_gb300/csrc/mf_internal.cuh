@@ -114,6 +114,12 @@ struct mf_mesh {
   CgWorkspace *cg = nullptr;
   // host copy of the connectivity used by CSR assembly (empty for structured meshes)
   std::vector<int32_t> h_cells;
+  // tensor-product geometry (structured boxes of axis-aligned cells): per-axis spacings and their
+  // inverses as (hi, lo) float pairs [hx | hy | hz | 1/hx | 1/hy | 1/hz], and the cell constants
+  // as pairs; enables the FP64-accurate tile kernels of mf_tile.cu
+  bool tp = false;
+  float2 *tp_axis = nullptr;
+  float2 *mat_pairs = nullptr;
 
   MeshView view() const {
     MeshView v;
@@ -139,6 +145,10 @@ mf_status apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t 
 mf_status apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip = nullptr);
 mf_status apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s);
 mf_status spmv(const mf_csr *A, const double *x, double *y, cudaStream_t s, const int *skip = nullptr);
+// tensor-product tile kernels (mf_tile.cu)
+mf_status tile_setup(mf_mesh *m, cudaStream_t s);
+mf_status tile_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip);
+mf_status tile_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip);
 // diag(A) of the matrix-free operator (Jacobi), FP64, Dirichlet rows 1.
 mf_status operator_diagonal(const mf_mesh *m, double *diag, cudaStream_t s);
 void cg_workspace_free(CgWorkspace *w);

@@ -158,6 +158,8 @@ static void free_mesh(mf_mesh *m) {
   cudaFree(m->dmask);
   cudaFree(m->dnodes);
   cudaFree(m->colour_elems);
+  cudaFree(m->tp_axis);
+  cudaFree(m->mat_pairs);
   delete m;
 }
 
@@ -317,6 +319,7 @@ extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells
       SETUP_TRY(colour_elements(m, s));
     } else {
       m->n_colours = 8;  // parity colouring of the box
+      SETUP_TRY(tile_setup(m, s));
     }
     SETUP_CUDA(cudaStreamSynchronize(s));
   }
@@ -346,7 +349,7 @@ extern "C" mf_status mf_mesh_query(const mf_mesh *m, int64_t *n_nodes, int64_t *
   if (n_dof) *n_dof = m->n_dof;
   if (n_free) *n_free = m->n_free;
   if (n_colours) *n_colours = m->n_colours;
-  if (flags) *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0);
+  if (flags) *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0);
   return MF_OK;
 }
 

@@ -69,6 +69,25 @@ def box_coords(nx: int, ny: int, nz: int, jitter: float = 0.0, seed: int = 0) ->
     return X
 
 
+def tensor_coords(nx: int, ny: int, nz: int, seed: int = 0, spread: float = 0.5) -> np.ndarray:
+    """Node coordinates of a non-uniform tensor-product grid of the unit cube: along each axis the
+    cell widths are (1 + U[-spread, spread]) times uniform, renormalised to sum to one."""
+    rng = _rng(seed, _S_JITTER)
+    axes = []
+    for n in (nx, ny, nz):
+        w = 1.0 + rng.uniform(-spread, spread, size=n)
+        t = np.concatenate([[0.0], np.cumsum(w)])
+        t /= t[-1]
+        t[-1] = 1.0
+        axes.append(t)
+    X = np.empty(((nx + 1) * (ny + 1) * (nz + 1), 3))
+    Xv = X.reshape(nz + 1, ny + 1, nx + 1, 3)
+    Xv[..., 0] = axes[0][None, None, :]
+    Xv[..., 1] = axes[1][None, :, None]
+    Xv[..., 2] = axes[2][:, None, None]
+    return X
+
+
 def box_cells(nx: int, ny: int, nz: int) -> np.ndarray:
     """Element -> node map of the box mesh, int32 [E][8], corners in the lexicographic order above."""
     ex = np.arange(nx, dtype=np.int64)
@@ -232,10 +251,11 @@ class Problem:
         return uniform_vector(self.n_dof, s, _S_B, self.dirichlet_dofs())
 
 
-def laplace_box(n, jitter=0.0, sigma=1.0, layered=False, seed=0, name=None, ny=None, nz=None) -> Problem:
+def laplace_box(n, jitter=0.0, sigma=1.0, layered=False, seed=0, name=None, ny=None, nz=None, graded=0.0) -> Problem:
+    """Laplace on an n x ny x nz box; ``graded > 0`` gives a non-uniform tensor-product grid."""
     ny = n if ny is None else ny
     nz = n if nz is None else nz
-    coords = box_coords(n, ny, nz, jitter, seed)
+    coords = tensor_coords(n, ny, nz, seed, graded) if graded > 0 else box_coords(n, ny, nz, jitter, seed)
     if layered:
         kappa = layered_lognormal(n, ny, nz, sigma, seed)
     else:
@@ -244,10 +264,11 @@ def laplace_box(n, jitter=0.0, sigma=1.0, layered=False, seed=0, name=None, ny=N
                    dirichlet_z0(n, ny, nz), seed, meta=dict(jitter=jitter, sigma=sigma, layered=layered))
 
 
-def elasticity_box(n, jitter=0.0, sigma=0.5, layered=True, seed=0, name=None, ny=None, nz=None) -> Problem:
+def elasticity_box(n, jitter=0.0, sigma=0.5, layered=True, seed=0, name=None, ny=None, nz=None,
+                   graded=0.0) -> Problem:
     ny = n if ny is None else ny
     nz = n if nz is None else nz
-    coords = box_coords(n, ny, nz, jitter, seed)
+    coords = tensor_coords(n, ny, nz, seed, graded) if graded > 0 else box_coords(n, ny, nz, jitter, seed)
     E = layered_lognormal(n, ny, nz, sigma, seed) if layered else lognormal_cells(n * ny * nz, sigma, seed)
     nu = poisson_ratio(n * ny * nz, seed)
     mat = np.stack([E, nu], axis=1)

@@ -124,7 +124,7 @@ def mf_mesh_query(h) -> dict:
     e, f = i32(), i32()
     check(lib.mf_mesh_query(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e), C.byref(f)), "mf_mesh_query")
     return dict(n_nodes=a.value, n_cells=b.value, n_dof=c.value, n_free=d.value, n_colours=e.value,
-                structured=bool(f.value & 1), all_affine=bool(f.value & 2))
+                structured=bool(f.value & 1), all_affine=bool(f.value & 2), tensor_product=bool(f.value & 4))
 
 
 def mf_set_apply_variant(h, variant: int) -> None:

@@ -313,3 +313,80 @@ def test_full_size_laplace_256_sampled():
 
 def test_full_size_elasticity_160_sampled():
     assert _sampled_parity(inputs.cartesian_elasticity_160()) <= TOL64
+
+
+# ------------------------------------------------------- tensor-product tile kernels (auto) ----
+
+TILE_SHAPES = [(1, 1, 1), (2, 3, 1), (31, 7, 5), (32, 8, 3), (45, 19, 23), (62, 14, 9), (5, 70, 4)]
+
+
+@pytest.mark.parametrize("shape", TILE_SHAPES)
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+def test_tile_apply_matches_oracle(shape, physics):
+    """Graded (non-uniform) tensor-product grids with ragged tiles in x, y and z segments."""
+    nx, ny, nz = shape
+    mk = inputs.laplace_box if physics == "laplace" else inputs.elasticity_box
+    p = mk(nx, ny=ny, nz=nz, graded=0.5, seed=nx + ny + nz, sigma=1.0)
+    mesh = mf.Mesh.from_problem(p)
+    assert mesh.info["tensor_product"]
+    for seed in (0, 3):
+        x = p.x(seed)
+        y = gpu_apply(mesh, x)
+        ref = oracle_apply(p, x)
+        assert rel2(y, ref) <= TOL64, (shape, rel2(y, ref))
+    # FP32 tile path: error stated and bounded
+    y32 = mesh.apply(gpu(x).float())
+    torch.cuda.synchronize()
+    e32 = rel2(y32.double().cpu().numpy(), ref)
+    assert e32 < 2e-6, e32
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+def test_tile_and_reference_variants_agree(physics):
+    mk = inputs.laplace_box if physics == "laplace" else inputs.elasticity_box
+    p = mk(20, ny=17, nz=13, graded=0.3, seed=5)
+    mesh = mf.Mesh.from_problem(p)
+    x = gpu(p.x())
+    ya = mesh.apply(x).clone()
+    mesh.set_variant(mf.MF_VARIANT_REFERENCE)
+    yr = mesh.apply(x).clone()
+    torch.cuda.synchronize()
+    assert rel2(ya.cpu().numpy(), yr.cpu().numpy()) <= TOL64
+    mesh.set_variant(mf.MF_VARIANT_AUTO)
+    yb = mesh.apply(x).clone()
+    assert torch.equal(ya, yb)  # bitwise reproducible
+
+
+def test_tile_dirichlet_rows_and_large_values():
+    """Dirichlet rows copy x; inputs spanning many binades stay FP64-accurate."""
+    p = inputs.laplace_box(12, ny=9, nz=11, graded=0.4, seed=6)
+    mesh = mf.Mesh.from_problem(p)
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-1, 1, p.n_dof) * 10.0 ** rng.uniform(-20, 20, p.n_dof)
+    y = gpu_apply(mesh, x)
+    d = p.dirichlet.astype(bool)
+    assert np.array_equal(y[d], x[d])
+    ref = oracle_apply(p, x)
+    assert rel2(y, ref) <= TOL64
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+def test_cg_auto_variant_matches_oracle(physics):
+    mk = inputs.laplace_box if physics == "laplace" else inputs.elasticity_box
+    p = mk(12, ny=10, nz=14, graded=0.3, seed=7, layered=True, sigma=0.5)
+    A, b, xo, it_o = _oracle_cg(p)
+    mesh = mf.Mesh.from_problem(p)
+    x, info = mesh.cg(gpu(b))
+    torch.cuda.synchronize()
+    assert info.status == mf.MF_OK
+    assert abs(info.iters - it_o) <= max(2, math.ceil(0.01 * it_o)), (info.iters, it_o)
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.05e-8 * np.linalg.norm(b)
+
+
+def test_mixed_ir_auto_variant():
+    p = inputs.elasticity_box(14, ny=12, nz=10, graded=0.3, seed=8)
+    A, b, xo, _ = _oracle_cg(p, rtol=1e-12)
+    mesh = mf.Mesh.from_problem(p)
+    x, info = mesh.cg(gpu(b), precision=mf.MF_PREC_MIXED_IR, rtol=1e-10)
+    assert info.status == mf.MF_OK and info.rel_res_true <= 1.05e-10
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.05e-10 * np.linalg.norm(b)
