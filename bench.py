@@ -40,7 +40,7 @@ UNIT = "GDoF/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-laplace", type=int, default=256)
@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution measurements")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR SpMV measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solver measurement")
     ap.add_argument("--cg-timeout", type=float, default=90.0)
     ap.add_argument("--variant", type=int, default=0, help="0 = auto (fastest FP64-accurate), 1 = reference")
     return ap.parse_args()
@@ -206,20 +207,15 @@ def main():
     F = [p.n_free for p in (pL, pE)]
     torch.cuda.synchronize()
 
-    def step(evs=None, k=0):
-        for j, (p, m, x, y) in enumerate(meshes):
-            if evs is not None:
-                evs[j][0][k].record()
+    def step():
+        for (p, m, x, y) in meshes:
             m.apply(x, y)
-            if evs is not None:
-                evs[j][1][k].record()
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
 
     K = args.steps
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(K)] for _ in range(2)] for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     barrier()
@@ -227,14 +223,24 @@ def main():
     l0 = mf.mf_kernel_launches()
     e0.record()
     for k in range(K):
-        step(evs, k)
+        step()
     e1.record()
     torch.cuda.synchronize()
     barrier()
     launches = mf.mf_kernel_launches() - l0
     clk = clocks.stop()
     t_total = e0.elapsed_time(e1) / 1e3
-    t_app = [float(np.mean([evs[j][0][k].elapsed_time(evs[j][1][k]) for k in range(K)])) / 1e3 for j in range(2)]
+    # per-operator kernel time: K back-to-back applies of one operator between two events (the
+    # per-step events above include host launch gaps when a kernel is shorter than the launch path)
+    t_app = []
+    for (p, m, x, y) in meshes:
+        m.apply(x, y)
+        e0.record()
+        for _ in range(K):
+            m.apply(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        t_app.append(e0.elapsed_time(e1) / 1e3 / K)
     if world > 1:
         t = torch.tensor([t_total], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -276,7 +282,8 @@ def main():
     # ---- roofline of the dominant kernel (the matrix-free apply taking the most time)
     j = int(np.argmax(t_app))
     p = (pL, pE)[j]
-    abytes = bm.kernel_apply_bytes(p.physics, p.n_cells, p.n_nodes, structured=True)
+    tp = meshes[j][1].info["tensor_product"] and args.variant == 0
+    abytes = bm.kernel_apply_bytes(p.physics, p.n_cells, p.n_nodes, structured=True, tensor_product=tp)
     achieved = abytes / t_app[j] / 1e9
     roof = {"kernel": f"matrix-free {p.physics} apply ({p.nx}^3)", "bound": "hbm", "achieved": achieved,
             "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": hbm_src,
@@ -320,6 +327,42 @@ def main():
                              "rel_res_true": info.rel_res_true,
                              "cg_gdofs": p.n_free * info.iters / info.seconds / 1e9}
         extras["cg_matfree"] = cg
+
+    # ---- batched persistent CG: 64 independent Laplace problems, n ~ log-uniform [8, 96]
+    if not args.no_batch:
+        from paper_2308_09839_gb300 import autotune
+        sizes = inputs.batch_sizes(64, 8, 96, seed=0)
+        probs = [inputs.laplace_box(int(n), jitter=0.0, sigma=1.0, layered=False, seed=1000 + i)
+                 for i, n in enumerate(sizes)]
+        bm_meshes = [mf.Mesh.from_problem(q, device=f"cuda:{local}") for q in probs]
+        bs = [torch.from_numpy(q.b()).cuda() for q in probs]
+        xs = [torch.zeros_like(v) for v in bs]
+        choice = autotune.tune(bm_meshes, [q.nz + 1 for q in probs], bs, xs, iters=10)
+        o = mf.mf_solve_opts_default()
+        batch = mf.mf_batch_create(bm_meshes, o)
+        mf.mf_batch_solve(batch, bs, xs)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = mf.mf_batch_solve(batch, bs, xs)
+        t_batch = time.perf_counter() - t0
+        mf.mf_batch_destroy(batch)
+        dof_it = sum(q.n_free * i.iters for q, i in zip(probs, infos))
+        for mm, v in zip(bm_meshes, bs):  # warm-up: graphs and workspaces
+            mm.cg(v)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        single = [mm.cg(v)[1] for mm, v in zip(bm_meshes, bs)]
+        torch.cuda.synchronize()
+        t_single = time.perf_counter() - t0
+        dof_it1 = sum(q.n_free * i.iters for q, i in zip(probs, single))
+        extras["batched_cg"] = {
+            "problems": len(probs), "sizes": [int(v) for v in sizes], "total_free_dof": int(sum(q.n_free for q in probs)),
+            "seconds_batched": t_batch, "seconds_one_at_a_time": t_single,
+            "gdofs_batched": dof_it / t_batch / 1e9, "gdofs_one_at_a_time": dof_it1 / t_single / 1e9,
+            "speedup": t_single / t_batch, "all_converged": all(i.status == 0 for i in infos),
+            "iters_total": int(sum(i.iters for i in infos)), "segments": {str(k): v for k, v in choice.items()}}
+        for mm in bm_meshes:
+            mm.close()
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None

@@ -225,6 +225,33 @@ mf_status mf_cg_solve(mf_mesh *mesh, const mf_solve_opts *opts, const double *b,
 mf_status mf_cg_solve_noalloc(const mf_mesh *mesh, const mf_solve_opts *opts, const double *b, double *x,
                               mf_solve_info *info, mf_stream stream);
 
+/*
+ * Batched solves (no counterpart in the paper, which solves one problem at a time): n independent
+ * problems A_i x_i = b_i, one mesh each, solved by unpreconditioned FP64 CG in ONE persistent
+ * cooperative kernel launch captured in a CUDA graph.  Every CTA of a co-resident grid loops over
+ * the CG phases (tile apply, p.Ap, x/r update with r.r, p update) of all still-active problems,
+ * separated by grid barriers whose waits are bounded (MF_ERR_TIMEOUT instead of a hang).  Each
+ * problem has its own scalars and stops at its own tolerance.  Meshes must be Laplace on
+ * tensor-product grids (MF_ERR_UNSUPPORTED otherwise); opts: MATFREE, FP64, no preconditioner;
+ * rtol and max_iter apply per problem; timeout_s, when > 0, bounds each barrier wait instead of
+ * the whole solve.
+ *   mf_batch_create   allocates the batch workspace and captures the graph (synchronous).
+ *   mf_batch_solve    b, x: HOST arrays of n DEVICE pointers (double[n_dof_i]); infos: host
+ *                     array of n (rel_res_true is not recomputed: -1).  Synchronises `stream`.
+ *   mf_cg_solve_batched  create + solve + destroy in one call.
+ */
+typedef struct mf_batch mf_batch;
+mf_status mf_batch_create(mf_mesh *const *meshes, int32_t n, const mf_solve_opts *opts, mf_batch **out);
+mf_status mf_batch_solve(mf_batch *batch, const double *const *b, double *const *x, mf_solve_info *infos,
+                         mf_stream stream);
+mf_status mf_batch_destroy(mf_batch *batch);
+mf_status mf_cg_solve_batched(mf_mesh *const *meshes, int32_t n, const mf_solve_opts *opts,
+                              const double *const *b, double *const *x, mf_solve_info *infos, mf_stream stream);
+
+/* z-segment length (node planes per tile work item) of the tile kernels for this mesh; 0 restores
+ * the built-in choice.  Used by the autotuner of the batched solver; results do not depend on it. */
+mf_status mf_set_tile_segment(mf_mesh *mesh, int32_t seg);
+
 /* Message describing the last failure in the calling thread ("" if none).  Valid until the next
  * failing call in the same thread. */
 const char *mf_last_error(void);

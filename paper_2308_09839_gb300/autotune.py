@@ -1,0 +1,109 @@
+"""Autotuner for the batched persistent CG solver: picks the z-segment length of the tile work
+items (node planes per item) for each problem-size bucket by timing short batched solves.
+
+The choice changes only how work is split among CTAs, never the arithmetic (the tile kernel's
+per-node summation order does not depend on it), so results stay bitwise identical.  Choices are
+cached in a JSON file keyed by GPU name, SM count and bucket.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import torch
+
+from . import mf
+
+BUCKETS = ((0, 16), (17, 32), (33, 64), (65, 1 << 30))
+CANDIDATES = (4, 8, 16, 32, 64)
+
+
+def _bucket(n: int) -> int:
+    for i, (lo, hi) in enumerate(BUCKETS):
+        if lo <= n <= hi:
+            return i
+    return len(BUCKETS) - 1
+
+
+def cache_path() -> str:
+    base = os.environ.get("MF_AUTOTUNE_CACHE")
+    if base:
+        return base
+    root = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+    return os.path.join(root, "mf_gb300", "autotune.json")
+
+
+def _device_key() -> str:
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|{p.multi_processor_count}"
+
+
+def _load() -> dict:
+    try:
+        return json.load(open(cache_path()))
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d: dict) -> None:
+    path = cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path + ".tmp", "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(path + ".tmp", path)
+    except OSError:
+        pass
+
+
+def _time_batch(meshes, bs, xs, iters: int, reps: int = 2) -> float:
+    o = mf.mf_solve_opts_default()
+    o.max_iter = iters
+    o.rtol = 1e-30  # run exactly `iters` iterations
+    batch = mf.mf_batch_create(meshes, o)
+    try:
+        mf.mf_batch_solve(batch, bs, xs)
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mf.mf_batch_solve(batch, bs, xs)
+            best = min(best, time.perf_counter() - t0)
+        return best
+    finally:
+        mf.mf_batch_destroy(batch)
+
+
+def tune(meshes, dims, bs, xs, iters: int = 20, use_cache: bool = True) -> dict:
+    """Choose a segment length per size bucket (coordinate descent over buckets), apply it to the
+    meshes with mf_set_tile_segment and return {bucket: seg}.  ``dims`` are the per-mesh node counts
+    along z (the axis the tiles march along)."""
+    key = _device_key()
+    cache = _load() if use_cache else {}
+    buckets = sorted({_bucket(d) for d in dims})
+    choice = {b: 16 for b in buckets}
+    cached = {b: cache.get(f"{key}|bucket{b}") for b in buckets}
+    if use_cache and all(v is not None for v in cached.values()):
+        choice = {b: int(v) for b, v in cached.items()}
+    else:
+        def apply_choice(ch):
+            for m, d in zip(meshes, dims):
+                mf.mf_set_tile_segment(m, ch[_bucket(d)])
+        for b in buckets:
+            best_t, best_s = float("inf"), choice[b]
+            for s in CANDIDATES:
+                trial = dict(choice)
+                trial[b] = s
+                apply_choice(trial)
+                t = _time_batch(meshes, bs, xs, iters)
+                if t < best_t:
+                    best_t, best_s = t, s
+            choice[b] = best_s
+        if use_cache:
+            for b in buckets:
+                cache[f"{key}|bucket{b}"] = choice[b]
+            _store(cache)
+    for m, d in zip(meshes, dims):
+        mf.mf_set_tile_segment(m, choice[_bucket(d)])
+    return choice

@@ -59,15 +59,16 @@ def sol_throughput(n_dof: int, bytes_: float, bandwidth_Bps: float) -> float:
 # ------------------------------------------------------------------- this library's kernels ----
 
 def kernel_apply_bytes(physics: str, n_elem: int, n_nodes: int, structured: bool, real_bytes: int = F64,
-                       nrhs: int = 1) -> int:
+                       nrhs: int = 1, tensor_product: bool = False) -> int:
     """Algorithmic (read-once) bytes of one operator apply y = A x.
 
-    Reads: connectivity (unless implicit on a structured box), node coordinates (FP64), one cell
-    constant (Laplace kappa) or two (elasticity), x, the Dirichlet mask (1 byte per node); writes y.
-    ``real_bytes`` is the width of x and y (8 for FP64, 4 for FP32)."""
+    Reads: connectivity (unless implicit on a structured box), node coordinates (FP64; on a
+    tensor-product grid only the per-axis spacings, which are negligible), one cell constant
+    (Laplace kappa) or two (elasticity) stored as 8-byte values, x, the Dirichlet mask (1 byte per
+    node); writes y.  ``real_bytes`` is the width of x and y (8 for FP64, 4 for FP32)."""
     ndpn = 1 if physics == "laplace" else 3
     conn = 0 if structured else n_elem * 8 * I32
-    coords = n_nodes * 3 * F64
+    coords = 0 if tensor_product else n_nodes * 3 * F64
     cells = n_elem * (1 if physics == "laplace" else 2) * F64
     mask = n_nodes
     vec = 2 * nrhs * n_nodes * ndpn * real_bytes

@@ -118,6 +118,7 @@ struct mf_mesh {
   // inverses as (hi, lo) float pairs [hx | hy | hz | 1/hx | 1/hy | 1/hz], and the cell constants
   // as pairs; enables the FP64-accurate tile kernels of mf_tile.cu
   bool tp = false;
+  int tile_seg = 0;  // z-segment length of the tile kernels (0: heuristic; set by the autotuner)
   float2 *tp_axis = nullptr;
   float2 *mat_pairs = nullptr;
 

@@ -1,329 +1,13 @@
-// Matrix-free apply for structured boxes whose cells are axis-aligned (tensor-product geometry),
-// FP64-accurate on the FP32 pipes ("auto" variant).
-//
-// What it computes is Eq. 7 (Laplace) / Eq. 9 and Algorithm 1 (elasticity) with 2x2x2 Gauss; what
-// differs from the reference kernel is how:
-//
-// 1. Geometry on the fly from per-axis spacings.  A cell of a tensor-product grid is the box
-//    [x_i, x_i+1] x [y_j, y_j+1] x [z_k, z_k+1], so J = diag(hx, hy, hz)/2 is constant on the cell
-//    and is computed per element from three spacings (kept, with their inverses, in tiny per-axis
-//    arrays built at setup from the coordinates).  Coordinates are not re-read per apply.
-//
-// 2. Exact rewriting of the quadrature in the monomial (Walsh-Hadamard) basis.  Writing the
-//    element field as u = sum_m c_m M_m(xi) with M in {1, xi, eta, zeta, xi eta, xi zeta,
-//    eta zeta, xi eta zeta}, the coefficients are c = H u / 8 with H the 8x8 Hadamard matrix, and
-//    with J constant the 2-point Gauss sums of Eqs. 4/6 are the exact integrals of products of
-//    those monomials (degree <= 2 per variable).  They are diagonal or nearly so in this basis:
-//    scalar Laplace:   v = H^T D H u,  D = diag(0, g1, g2, (g1+g2)/3, g3, (g1+g3)/3, (g2+g3)/3,
-//                      (g1+g2+g3)/9) / 16 with g1 = kappa hy hz / hx (cyclic);
-//    elasticity: the same per component plus 24 couplings between components through lam and mu
-//                (see elasticity_box below).  Each apply is two 8-point fast Walsh-Hadamard
-//    transforms per component and a few products instead of a Jacobian per Gauss point.
-//
-// 3. Double-word arithmetic (mf_dw.cuh) for FP64 accuracy; the GB300 FP64 pipe is ~60x slower
-//    than FP32.  x is split into float pairs with integer operations; y leaves through one FP64 add.
-//
-// 4. Atomic-free scatter by owner computes: a CTA owns a TX x TY column of nodes over a z-segment
-//    and evaluates every element touching them (one halo element ring, recomputed by the
-//    neighbour), marching up in z with the input node planes staged in shared memory and the
-//    output planes accumulated there in a fixed order.  Every y entry is written exactly once,
-//    without a memset or read-modify-write, and the result is bitwise reproducible.
+// Setup of the tensor-product geometry and launch of the standalone tile apply (the kernels live in
+// mf_tile.cuh; see there for what they compute and how).
 #include <algorithm>
 
-#include "mf_dw.cuh"
-#include "mf_internal.cuh"
+#include "mf_tile.cuh"
 
-namespace {
-
+using namespace tile;
 using dwa::dw;
 
-// ------------------------------------------------------------------ number types (traits) ----
-struct NumDW {  // FP64-accurate double-word
-  using T = dw;
-  using S = float2;
-  using IO = double;
-  static __device__ __forceinline__ T zero() { return dw{0.f, 0.f}; }
-  static __device__ __forceinline__ T add(T a, T b) { return dwa::add(a, b); }
-  static __device__ __forceinline__ T sub(T a, T b) { return dwa::sub(a, b); }
-  static __device__ __forceinline__ T mul(T a, T b) { return dwa::mul(a, b); }
-  static __device__ __forceinline__ T scale(T a, float p) { return dwa::scale(a, p); }
-  static __device__ __forceinline__ T from2(float2 v) { return dw{v.x, v.y}; }
-  static __device__ __forceinline__ T ld(const S &s) { return dw{s.x, s.y}; }
-  static __device__ __forceinline__ void st(S &s, T v) { s = make_float2(v.h, v.l); }
-  static __device__ __forceinline__ T in(IO v) { return dwa::split(v); }
-  static __device__ __forceinline__ IO out(T v) { return dwa::to_double(v); }
-  static __device__ __forceinline__ T c(float h, float l) { return dw{h, l}; }
-};
-
-struct NumF32 {  // plain FP32 (mixed-precision inner solves)
-  using T = float;
-  using S = float;
-  using IO = float;
-  static __device__ __forceinline__ T zero() { return 0.f; }
-  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
-  static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
-  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
-  static __device__ __forceinline__ T scale(T a, float p) { return a * p; }
-  static __device__ __forceinline__ T from2(float2 v) { return v.x; }
-  static __device__ __forceinline__ T ld(const S &s) { return s; }
-  static __device__ __forceinline__ void st(S &s, T v) { s = v; }
-  static __device__ __forceinline__ T in(IO v) { return v; }
-  static __device__ __forceinline__ IO out(T v) { return v; }
-  static __device__ __forceinline__ T c(float h, float) { return h; }
-};
-
-// 1/3, 1/9, 1/48, 1/144 as (hi, lo) pairs: hi = nearest float, lo = nearest float to the rest.
-#define C_THIRD 0x1.555556p-2f, -0x1.555556p-27f
-#define C_NINTH 0x1.c71c72p-4f, -0x1.c71c72p-31f
-#define C_48TH 0x1.555556p-6f, -0x1.555556p-31f
-#define C_144TH 0x1.c71c72p-8f, -0x1.c71c72p-35f
-
-// Forward transform c = H u in place: butterflies (lo, hi) -> (lo + hi, hi - lo) along each bit.
-template <class N>
-__device__ __forceinline__ void fwht_fwd(typename N::T u[8]) {
-#pragma unroll
-  for (int d = 1; d < 8; d <<= 1)
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-      if (!(a & d)) {
-        const typename N::T lo = u[a], hi = u[a | d];
-        u[a] = N::add(lo, hi);
-        u[a | d] = N::sub(hi, lo);
-      }
-}
-
-// Transposed transform y = H^T v in place: (lo, hi) -> (lo - hi, lo + hi).
-template <class N>
-__device__ __forceinline__ void fwht_inv(typename N::T v[8]) {
-#pragma unroll
-  for (int d = 1; d < 8; d <<= 1)
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-      if (!(a & d)) {
-        const typename N::T lo = v[a], hi = v[a | d];
-        v[a] = N::sub(lo, hi);
-        v[a | d] = N::add(lo, hi);
-      }
-}
-
-// Scalar Laplace on an axis-aligned box, in place: u (nodal values) -> v = A^e u.
-// Modes are indexed by the bit set of the monomial: 1 xi, 2 eta, 4 zeta, 3 xi eta, 5 xi zeta,
-// 6 eta zeta, 7 xi eta zeta.
-template <class N>
-__device__ __forceinline__ void laplace_box(typename N::T u[8], typename N::T k, typename N::T hx,
-                                            typename N::T hy, typename N::T hz, typename N::T ihx,
-                                            typename N::T ihy, typename N::T ihz) {
-  using T = typename N::T;
-  const T kz = N::mul(k, hz);
-  const T g1 = N::mul(N::mul(kz, hy), ihx);                  // kappa hy hz / hx
-  const T g2 = N::mul(N::mul(kz, hx), ihy);                  // kappa hx hz / hy
-  const T g3 = N::mul(N::mul(N::mul(k, hx), hy), ihz);       // kappa hx hy / hz
-  const T g12 = N::add(g1, g2), g13 = N::add(g1, g3), g23 = N::add(g2, g3);
-  const T g123 = N::add(g12, g3);
-  fwht_fwd<N>(u);
-  u[0] = N::zero();
-  u[1] = N::scale(N::mul(g1, u[1]), 0.0625f);
-  u[2] = N::scale(N::mul(g2, u[2]), 0.0625f);
-  u[4] = N::scale(N::mul(g3, u[4]), 0.0625f);
-  u[3] = N::mul(N::mul(g12, N::c(C_48TH)), u[3]);
-  u[5] = N::mul(N::mul(g13, N::c(C_48TH)), u[5]);
-  u[6] = N::mul(N::mul(g23, N::c(C_48TH)), u[6]);
-  u[7] = N::mul(N::mul(g123, N::c(C_144TH)), u[7]);
-  fwht_inv<N>(u);
-}
-
-// Isotropic elasticity on an axis-aligned box, in place on c[k][a] (component k, corner a).
-// With r_k = h_{k+1} h_{k+2} / h_k and the mode coefficients c^k = H u^k:
-//   same-component terms:  W^l_k = (k == l ? lam + 2 mu : mu) r_k / 16 weighted like the Laplace D;
-//   cross-component terms: lam h_m / 16 and mu h_m / 16 (m the third axis) between the linear and
-//   bilinear modes of components k != l, as derived from Eq. 6 with J diagonal.
-template <class N>
-__device__ __forceinline__ void elasticity_box(typename N::T c[3][8], typename N::T lam, typename N::T mu,
-                                               const typename N::T h[3], const typename N::T ih[3]) {
-  using T = typename N::T;
-  const T h01 = N::mul(h[0], h[1]), h02 = N::mul(h[0], h[2]), h12 = N::mul(h[1], h[2]);
-  const T r[3] = {N::mul(h12, ih[0]), N::mul(h02, ih[1]), N::mul(h01, ih[2])};
-  const T l2m = N::add(lam, N::scale(mu, 2.0f));
-  T mr[3], lr[3], L[3], M[3], L3[3], M3[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    mr[k] = N::scale(N::mul(mu, r[k]), 0.0625f);
-    lr[k] = N::scale(N::mul(l2m, r[k]), 0.0625f);
-    L[k] = N::scale(N::mul(lam, h[k]), 0.0625f);
-    M[k] = N::scale(N::mul(mu, h[k]), 0.0625f);
-    L3[k] = N::mul(L[k], N::c(C_THIRD));
-    M3[k] = N::mul(M[k], N::c(C_THIRD));
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) fwht_fwd<N>(c[k]);
-  T o[3][8];
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    const T W1 = l == 0 ? lr[0] : mr[0];
-    const T W2 = l == 1 ? lr[1] : mr[1];
-    const T W3 = l == 2 ? lr[2] : mr[2];
-    const T W12 = N::add(W1, W2), W13 = N::add(W1, W3), W23 = N::add(W2, W3);
-    o[l][0] = N::zero();
-    o[l][1] = N::mul(W1, c[l][1]);
-    o[l][2] = N::mul(W2, c[l][2]);
-    o[l][4] = N::mul(W3, c[l][4]);
-    o[l][3] = N::mul(N::mul(W12, N::c(C_THIRD)), c[l][3]);
-    o[l][5] = N::mul(N::mul(W13, N::c(C_THIRD)), c[l][5]);
-    o[l][6] = N::mul(N::mul(W23, N::c(C_THIRD)), c[l][6]);
-    o[l][7] = N::mul(N::mul(N::add(W12, W3), N::c(C_NINTH)), c[l][7]);
-  }
-#define ACC(l, m, coef, k, mm) o[l][m] = N::add(o[l][m], N::mul(coef, c[k][mm]))
-  // components 0 <-> 1 (third axis 2)
-  ACC(1, 2, L[2], 0, 1); ACC(1, 6, L3[2], 0, 5); ACC(1, 1, M[2], 0, 2); ACC(1, 5, M3[2], 0, 6);
-  ACC(0, 1, L[2], 1, 2); ACC(0, 5, L3[2], 1, 6); ACC(0, 2, M[2], 1, 1); ACC(0, 6, M3[2], 1, 5);
-  // components 0 <-> 2 (third axis 1)
-  ACC(2, 4, L[1], 0, 1); ACC(2, 6, L3[1], 0, 3); ACC(2, 1, M[1], 0, 4); ACC(2, 3, M3[1], 0, 6);
-  ACC(0, 1, L[1], 2, 4); ACC(0, 3, L3[1], 2, 6); ACC(0, 4, M[1], 2, 1); ACC(0, 6, M3[1], 2, 3);
-  // components 1 <-> 2 (third axis 0)
-  ACC(2, 4, L[0], 1, 2); ACC(2, 5, L3[0], 1, 3); ACC(2, 2, M[0], 1, 4); ACC(2, 3, M3[0], 1, 5);
-  ACC(1, 2, L[0], 2, 4); ACC(1, 3, L3[0], 2, 5); ACC(1, 4, M[0], 2, 2); ACC(1, 5, M3[0], 2, 3);
-#undef ACC
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    fwht_inv<N>(o[l]);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) c[l][a] = o[l][a];
-  }
-}
-
-struct TileArgs {
-  int nx, ny, nz;
-  int tiles_x, tiles_y, seg;
-  const float2 *hx, *hy, *hz, *ihx, *ihy, *ihz;  // per-axis spacings and inverses (pairs)
-  const float2 *mat;                             // kappa[E] or (lam, mu)[E] as pairs
-  const uint8_t *dmask;
-};
-
-// One CTA: owned nodes [i0, i0+TX) x [j0, j0+TY) x [k0, k1); one thread per element of an
-// (EX = TX+1) x (EY = TY+1) slab of elements; marches slab by slab in z.
-template <int PHYS, class N, int EX, int EY>
-__global__ void __launch_bounds__(EX *EY) tile_apply(TileArgs g, const typename N::IO *__restrict__ x,
-                                                     typename N::IO *__restrict__ y, const int *__restrict__ skip) {
-  using T = typename N::T;
-  using S = typename N::S;
-  using IO = typename N::IO;
-  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
-  constexpr int NT = EX * EY, TX = EX - 1, TY = EY - 1, PX = EX + 1, PY = EY + 1, NP = PX * PY;
-  constexpr int LOADS = (NP + NT - 1) / NT;
-  constexpr int NACC = TX * TY * ND;
-  __shared__ S up[2][NP * ND];
-  __shared__ S acc[2][NACC];
-  if (skip && *skip) return;
-
-  const int tid = threadIdx.x;
-  const int bx = blockIdx.x % g.tiles_x;
-  const int by = (blockIdx.x / g.tiles_x) % g.tiles_y;
-  const int bz = blockIdx.x / (g.tiles_x * g.tiles_y);
-  const int i0 = bx * TX, j0 = by * TY;
-  const int NXP = g.nx + 1, NYP = g.ny + 1;
-  const int k0 = bz * g.seg, k1 = min(k0 + g.seg, g.nz + 1);
-  const int tx = tid % EX, ty = tid / EX;
-  const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;
-  const bool ein = ex >= 0 && ex < g.nx && ey >= 0 && ey < g.ny;
-  const int ownx = min(TX, NXP - i0), owny = min(TY, NYP - j0);
-
-  T hx = N::zero(), hy = N::zero(), ihx = N::zero(), ihy = N::zero();
-  if (ein) {
-    hx = N::from2(__ldg(g.hx + ex));
-    ihx = N::from2(__ldg(g.ihx + ex));
-    hy = N::from2(__ldg(g.hy + ey));
-    ihy = N::from2(__ldg(g.ihy + ey));
-  }
-  for (int t = tid; t < 2 * NACC; t += NT) N::st(acc[t / NACC][t % NACC], N::zero());
-
-  IO xr[LOADS][ND];
-  bool dr[LOADS];
-  auto fetch = [&](int k) {
-#pragma unroll
-    for (int l = 0; l < LOADS; ++l) {
-      const int p = tid + l * NT;
-      const int ix = i0 - 1 + p % PX, iy = j0 - 1 + p / PX;
-      const bool ok = p < NP && ix >= 0 && ix < NXP && iy >= 0 && iy < NYP;
-      const int64_t node = ix + (int64_t)NXP * (iy + (int64_t)NYP * k);
-      dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
-#pragma unroll
-      for (int c = 0; c < ND; ++c) xr[l][c] = ok ? __ldg(x + node * ND + c) : (IO)0;
-    }
-  };
-  auto stage = [&](int k) {
-    S *u = up[k & 1];
-#pragma unroll
-    for (int l = 0; l < LOADS; ++l) {
-      const int p = tid + l * NT;
-      if (p < NP)
-#pragma unroll
-        for (int c = 0; c < ND; ++c) N::st(u[p * ND + c], dr[l] ? N::zero() : N::in(xr[l][c]));
-    }
-  };
-  auto write_plane = [&](int k) {
-    S *a = acc[k & 1];
-    for (int t = tid; t < NACC; t += NT) {
-      const int idx = t / ND, c = t % ND;
-      const int lx = idx % TX, ly = idx / TX;
-      if (lx < ownx && ly < owny) {
-        const int64_t node = (i0 + lx) + (int64_t)NXP * ((j0 + ly) + (int64_t)NYP * k);
-        y[node * ND + c] = __ldg(g.dmask + node) ? x[node * ND + c] : N::out(N::ld(a[t]));
-      }
-      N::st(a[t], N::zero());
-    }
-  };
-
-  const int s_lo = max(k0 - 1, 0), s_hi = min(k1 - 1, g.nz - 1);
-  fetch(s_lo);
-  stage(s_lo);
-  fetch(s_lo + 1);
-  for (int ez = s_lo; ez <= s_hi; ++ez) {
-    stage(ez + 1);
-    __syncthreads();
-    if (ez + 2 <= g.nz) fetch(ez + 2);
-    T v[ND][8];
-    if (ein) {
-      const S *ub = up[ez & 1];
-      const S *ut = up[(ez + 1) & 1];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int p = (tx + (a & 1)) + PX * (ty + ((a >> 1) & 1));
-        const S *u = (a & 4) ? ut : ub;
-#pragma unroll
-        for (int c = 0; c < ND; ++c) v[c][a] = N::ld(u[p * ND + c]);
-      }
-      const int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
-      const T hz = N::from2(__ldg(g.hz + ez)), ihz = N::from2(__ldg(g.ihz + ez));
-      if constexpr (PHYS == MF_LAPLACE) {
-        laplace_box<N>(v[0], N::from2(__ldg(g.mat + e)), hx, hy, hz, ihx, ihy, ihz);
-      } else {
-        const T h[3] = {hx, hy, hz}, ih[3] = {ihx, ihy, ihz};
-        elasticity_box<N>(v, N::from2(__ldg(g.mat + 2 * e)), N::from2(__ldg(g.mat + 2 * e + 1)), h, ih);
-      }
-    }
-    const bool bot = ez >= k0, top = ez + 1 < k1;
-#pragma unroll
-    for (int ay = 0; ay < 2; ++ay) {
-#pragma unroll
-      for (int ax = 0; ax < 2; ++ax) {
-        const int lx = tx - 1 + ax, ly = ty - 1 + ay;
-        if (ein && lx >= 0 && lx < ownx && ly >= 0 && ly < owny) {
-          const int idx = (lx + TX * ly) * ND;
-          const int a = ax + 2 * ay;
-#pragma unroll
-          for (int c = 0; c < ND; ++c) {
-            if (bot) N::st(acc[ez & 1][idx + c], N::add(N::ld(acc[ez & 1][idx + c]), v[c][a]));
-            if (top) N::st(acc[(ez + 1) & 1][idx + c], N::add(N::ld(acc[(ez + 1) & 1][idx + c]), v[c][a + 4]));
-          }
-        }
-        __syncwarp();
-      }
-      __syncthreads();
-    }
-    if (ez >= k0) write_plane(ez);
-  }
-  if (s_hi + 1 == g.nz && g.nz >= k0 && g.nz < k1) write_plane(g.nz);
-}
+namespace {
 
 // ------------------------------------------------------------------------------------ setup ----
 // Tensor-product check: every node's x depends on i only, y on j only, z on k only.
@@ -371,37 +55,6 @@ __global__ void mat_pairs(const double *m, int64_t n, float2 *out) {
   out[i] = make_float2(v.h, v.l);
 }
 
-constexpr int kEX = 32, kEY = 8;
-
-TileArgs tile_args(const mf_mesh *m) {
-  TileArgs g;
-  g.nx = m->nx;
-  g.ny = m->ny;
-  g.nz = m->nz;
-  const int TX = kEX - 1, TY = kEY - 1;
-  g.tiles_x = (m->nx + 1 + TX - 1) / TX;
-  g.tiles_y = (m->ny + 1 + TY - 1) / TY;
-  const int cols = g.tiles_x * g.tiles_y;
-  const int target = 152 * 4;
-  int nseg = std::max(1, std::min(m->nz + 1, (target + cols - 1) / cols));
-  g.seg = (m->nz + 1 + nseg - 1) / nseg;
-  const int n = m->nx + m->ny + m->nz;
-  g.hx = m->tp_axis;
-  g.hy = m->tp_axis + m->nx;
-  g.hz = m->tp_axis + m->nx + m->ny;
-  g.ihx = m->tp_axis + n;
-  g.ihy = m->tp_axis + n + m->nx;
-  g.ihz = m->tp_axis + n + m->nx + m->ny;
-  g.mat = m->mat_pairs;
-  g.dmask = m->dmask;
-  return g;
-}
-
-unsigned tile_grid(const TileArgs &g) {
-  const int nseg = (g.nz + 1 + g.seg - 1) / g.seg;
-  return (unsigned)(g.tiles_x * g.tiles_y * nseg);
-}
-
 }  // namespace
 
 mf_status tile_setup(mf_mesh *m, cudaStream_t s) {
@@ -428,15 +81,20 @@ mf_status tile_setup(mf_mesh *m, cudaStream_t s) {
   return MF_OK;
 }
 
+template <int PHYS, class N>
+static void tile_launch_one(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
+                            const int *skip) {
+  using TS = TileShape<PHYS, N>;
+  const TileArgs g = make_tile_args(m, TS::EX, TS::EY, m->tile_seg);
+  tile_apply<PHYS, N, TS::EX, TS::EY, TS::MINB><<<tile_items(g), TS::EX * TS::EY, 0, s>>>(g, x, y, skip);
+}
+
 template <class N>
 static mf_status tile_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
                              const int *skip) {
-  const TileArgs g = tile_args(m);
   mf_count_launches(1);
-  if (m->physics == MF_LAPLACE)
-    tile_apply<MF_LAPLACE, N, kEX, kEY><<<tile_grid(g), kEX * kEY, 0, s>>>(g, x, y, skip);
-  else
-    tile_apply<MF_ELASTICITY, N, kEX, kEY><<<tile_grid(g), kEX * kEY, 0, s>>>(g, x, y, skip);
+  if (m->physics == MF_LAPLACE) tile_launch_one<MF_LAPLACE, N>(m, x, y, s, skip);
+  else tile_launch_one<MF_ELASTICITY, N>(m, x, y, s, skip);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }

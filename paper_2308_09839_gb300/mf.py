@@ -63,6 +63,12 @@ _SIGS = {
     "mf_solve_opts_default": (None, [C.POINTER(mf_solve_opts)]),
     "mf_cg_solve": (C.c_int, [vp, C.POINTER(mf_solve_opts), vp, vp, C.POINTER(mf_solve_info), vp]),
     "mf_cg_solve_noalloc": (C.c_int, [vp, C.POINTER(mf_solve_opts), vp, vp, C.POINTER(mf_solve_info), vp]),
+    "mf_batch_create": (C.c_int, [C.POINTER(vp), i32, C.POINTER(mf_solve_opts), C.POINTER(vp)]),
+    "mf_batch_solve": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(mf_solve_info), vp]),
+    "mf_batch_destroy": (C.c_int, [vp]),
+    "mf_cg_solve_batched": (C.c_int, [C.POINTER(vp), i32, C.POINTER(mf_solve_opts), C.POINTER(vp), C.POINTER(vp),
+                                      C.POINTER(mf_solve_info), vp]),
+    "mf_set_tile_segment": (C.c_int, [vp, i32]),
     "mf_kernel_launches": (i64, []),
     "mf_last_error": (C.c_char_p, []),
     "mf_version": (C.c_char_p, []),
@@ -195,6 +201,44 @@ def mf_cg_solve_noalloc(h, opts: mf_solve_opts, b, x, stream=None, ok=(MF_OK, MF
 
 
 MF_NOALLOC_MAX_DOF = 262144
+
+
+def _ptr_array(ts):
+    arr = (vp * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _ptr(t)
+    return arr
+
+
+def mf_batch_create(meshes, opts: mf_solve_opts) -> int:
+    hs = (vp * len(meshes))(*[m.h if isinstance(m, Mesh) else m for m in meshes])
+    out = vp()
+    check(lib.mf_batch_create(hs, len(meshes), C.byref(opts), C.byref(out)), "mf_batch_create")
+    return out.value
+
+
+def mf_batch_solve(batch, bs, xs, stream=None, ok=(MF_OK, MF_NOT_CONVERGED)):
+    infos = (mf_solve_info * len(bs))()
+    st = lib.mf_batch_solve(batch, _ptr_array(bs), _ptr_array(xs), infos, _stream(stream))
+    check(st, "mf_batch_solve", ok)
+    return list(infos)
+
+
+def mf_batch_destroy(batch) -> None:
+    check(lib.mf_batch_destroy(batch), "mf_batch_destroy")
+
+
+def mf_cg_solve_batched(meshes, opts: mf_solve_opts, bs, xs, stream=None, ok=(MF_OK, MF_NOT_CONVERGED)):
+    hs = (vp * len(meshes))(*[m.h if isinstance(m, Mesh) else m for m in meshes])
+    infos = (mf_solve_info * len(bs))()
+    st = lib.mf_cg_solve_batched(hs, len(meshes), C.byref(opts), _ptr_array(bs), _ptr_array(xs), infos,
+                                 _stream(stream))
+    check(st, "mf_cg_solve_batched", ok)
+    return list(infos)
+
+
+def mf_set_tile_segment(h, seg: int) -> None:
+    check(lib.mf_set_tile_segment(h.h if isinstance(h, Mesh) else h, seg), "mf_set_tile_segment")
 
 
 def mf_kernel_launches() -> int:

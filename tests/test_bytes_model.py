@@ -73,3 +73,9 @@ def test_kernel_bytes_config_sizes():
     n = 256
     b = bm.kernel_apply_bytes("laplace", n ** 3, (n + 1) ** 3, structured=True)
     assert b == (n + 1) ** 3 * (24 + 1 + 16) + n ** 3 * 8
+
+
+def test_kernel_bytes_tensor_product():
+    n = 256
+    b = bm.kernel_apply_bytes("laplace", n ** 3, (n + 1) ** 3, structured=True, tensor_product=True)
+    assert b == (n + 1) ** 3 * (1 + 16) + n ** 3 * 8
