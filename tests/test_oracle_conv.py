@@ -79,3 +79,24 @@ def test_bf16_rounding():
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -7  # ties to even
     assert abs(r[3] - 3.140625) < 1e-7
     assert np.all(np.abs(r - v) <= np.abs(v) * 2 ** -8)
+
+
+def test_network_oracle_gradient_matches_finite_differences():
+    """The exact (no rounding) network oracle's backward equals central differences of its forward."""
+    from oracle import net
+    rng = np.random.default_rng(20)
+    p = rng.normal(size=net.num_params()) * 0.2
+    inp = rng.normal(size=(5, 5, 9, 2))
+    tgt = rng.normal(size=(5, 5, 9))
+    loss, g, _ = net.loss_and_grad(p, inp, tgt, bf16=False)
+    idx = rng.choice(p.size, 40, replace=False)
+    # include weights of every layer and the biases of the output layer
+    idx = np.concatenate([idx, [p.size - 1, 5, 27 * 32 + 3]])
+    eps = 1e-6
+    for i in idx:
+        dp = np.zeros_like(p)
+        dp[i] = eps
+        lp = net.loss_and_grad(p + dp, inp, tgt, bf16=False)[0]
+        lm = net.loss_and_grad(p - dp, inp, tgt, bf16=False)[0]
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
