@@ -89,6 +89,19 @@ def laplace_element_matrices(X: np.ndarray, kappa: np.ndarray) -> np.ndarray:
     return np.einsum("e,q,eq,eqai,eqbi->eab", kappa, w, det, g, g)
 
 
+def vector_laplace_element_matrices(X: np.ndarray, kappa: np.ndarray) -> np.ndarray:
+    """Eq. 5 times kappa_e: A^e_{3a+k, 3b+l} = kappa_e delta_kl sum_q (J^{-T} grad_ref phi_a).(J^{-T}
+    grad_ref phi_b) w_q det J  (each displacement component sees the scalar operator)."""
+    pts, w = gauss_points()
+    dN = shape_ref_grads(pts)
+    g, det = physical_grads(jacobians(X, dN), dN)
+    gg = np.einsum("e,q,eq,eqai,eqbi->eab", kappa, w, det, g, g)
+    A = np.zeros((X.shape[0], 8, 3, 8, 3))
+    for k in range(3):
+        A[:, :, k, :, k] = gg
+    return A.reshape(X.shape[0], 24, 24)
+
+
 def elasticity_element_matrices(X: np.ndarray, lam: np.ndarray, mu: np.ndarray) -> np.ndarray:
     """Eq. 6 with Hooke's law:
     A^e_{3a+k, 3b+l} = sum_q w_q det J [lam d_k phi_a d_l phi_b + mu (d_l phi_a d_k phi_b + delta_kl grad phi_a . grad phi_b)].
@@ -126,12 +139,14 @@ def element_matrices(physics: str, coords: np.ndarray, cells: np.ndarray, mat: n
     X = coords[cells[elems]]
     if physics == "laplace":
         return laplace_element_matrices(X, mat[elems])
+    if physics == "vector_laplace":
+        return vector_laplace_element_matrices(X, mat[elems])
     lam, mu = lame(mat[elems, 0], mat[elems, 1])
     return elasticity_element_matrices(X, lam, mu)
 
 
 def _ndpn(physics: str) -> int:
-    return 1 if physics == "laplace" else 3
+    return 1 if physics == "laplace" else 3  # elasticity and vector_laplace: 3 components
 
 
 def apply(physics, coords, cells, mat, dirichlet, x) -> np.ndarray:

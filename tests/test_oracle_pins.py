@@ -352,3 +352,25 @@ def test_iterative_refinement_fp32_inner():
 
     x, m, hist = solvers.iterative_refinement(lambda v: A @ v, inner, b, 1e-10)
     assert hist[-1] <= 1e-10 and m <= 6
+
+
+def test_vector_laplace_is_componentwise_scalar_laplace():
+    """Eq. 5: the vector Laplace element matrix equals the scalar one on each component, exactly
+    (checked against exact rational integration on a parallelepiped)."""
+    Jq = [[Fraction(2), Fraction(1, 8), Fraction(-3, 8)],
+          [Fraction(-1, 4), Fraction(17, 8), Fraction(1, 4)],
+          [Fraction(3, 8), Fraction(-1, 8), Fraction(15, 8)]]
+    ex = np.array(_exact.affine_laplace_exact(Jq, Fraction(5, 3)), dtype=float)
+    X = fem.corner_signs() @ np.array(Jq, dtype=float).T
+    A = fem.vector_laplace_element_matrices(X[None], np.array([5.0 / 3.0]))[0].reshape(8, 3, 8, 3)
+    for k in range(3):
+        for l in range(3):
+            blk = A[:, k, :, l]
+            assert np.max(np.abs(blk - (ex if k == l else 0))) <= 1e-13 * np.abs(ex).max()
+    # constants per component are in the null space without Dirichlet rows
+    p = inputs.elasticity_box(3, jitter=0.2, seed=2)
+    cells = p.cell_array()
+    for k in range(3):
+        u = np.zeros((p.n_nodes, 3)); u[:, k] = 1.0
+        y = fem.apply("vector_laplace", p.coords, cells, p.mat[:, 0], np.zeros(p.n_nodes, np.uint8), u.reshape(-1))
+        assert np.abs(y).max() < 1e-13
