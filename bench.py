@@ -49,6 +49,13 @@ def parse():
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR SpMV measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solver measurement")
+    ap.add_argument("--no-multi", action="store_true", help="skip the multi-RHS measurement")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner measurement")
+    ap.add_argument("--n-learned", type=int, default=128)
+    ap.add_argument("--pairs", type=int, default=200)
+    ap.add_argument("--train-steps", type=int, default=1000)
+    ap.add_argument("--lr", type=float, default=2e-4)
     ap.add_argument("--cg-timeout", type=float, default=90.0)
     ap.add_argument("--variant", type=int, default=0, help="0 = auto (fastest FP64-accurate), 1 = reference")
     return ap.parse_args()
@@ -105,6 +112,20 @@ class ClockSampler:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------- multi-rank timing ----
+
+def aggregate(units_per_rank: float, seconds: float, world: int, dist=None, device=None):
+    """Whole-job throughput of `world` independent replicas: every rank processed `units_per_rank`
+    units; the job took the slowest rank's time (max over ranks, via all_reduce when distributed)."""
+    t = seconds
+    if dist is not None and world > 1:
+        import torch
+        v = torch.tensor([seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        t = float(v.item())
+    return world * units_per_rank / t, t
 
 
 # ------------------------------------------------------------------------------- CPU oracle ----
@@ -229,7 +250,7 @@ def main():
     barrier()
     launches = mf.mf_kernel_launches() - l0
     clk = clocks.stop()
-    t_total = e0.elapsed_time(e1) / 1e3
+    t_local = e0.elapsed_time(e1) / 1e3
     # per-operator kernel time: K back-to-back applies of one operator between two events (the
     # per-step events above include host launch gaps when a kernel is shorter than the launch path)
     t_app = []
@@ -241,11 +262,8 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         t_app.append(e0.elapsed_time(e1) / 1e3 / K)
-    if world > 1:
-        t = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = world * K * sum(F) / t_total / 1e9
+    value, t_total = aggregate(K * sum(F), t_local, world, dist if world > 1 else None, "cuda")
+    value /= 1e9
 
     # ---- parity spot check of the timed launch configuration (sampled rows vs the oracle)
     extras = {"gdofs_apply": {"laplace": F[0] / t_app[0] / 1e9, "elasticity": F[1] / t_app[1] / 1e9},
@@ -270,14 +288,9 @@ def main():
             hy[j].copy_(y, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
-    t_e2e = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    e2e_value, _ = aggregate(Ke * sum(F), e0.elapsed_time(e1) / 1e3, world, dist if world > 1 else None, "cuda")
     io_bytes = sum(h.numel() * 8 for h in hx)
-    e2e = {"value": world * Ke * sum(F) / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
-           "d2h_bytes_per_step": io_bytes}
+    e2e = {"value": e2e_value / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
 
     # ---- roofline of the dominant kernel (the matrix-free apply taking the most time)
     j = int(np.argmax(t_app))
@@ -363,6 +376,88 @@ def main():
             "iters_total": int(sum(i.iters for i in infos)), "segments": {str(k): v for k, v in choice.items()}}
         for mm in bm_meshes:
             mm.close()
+
+    # ---- multi right-hand-side block apply: 16 RHS on a 128^3 Cartesian elasticity mesh
+    if not args.no_multi:
+        pm = inputs.cartesian_elasticity_160(n=128)
+        mm = mf.Mesh.from_problem(pm, device=f"cuda:{local}")
+        R = 16
+        X = torch.from_numpy(np.stack([pm.x(seed=s).reshape(-1, 3) for s in range(R)], axis=1).reshape(-1)).cuda()
+        Y = torch.empty_like(X)
+        xs1 = [torch.from_numpy(pm.x(seed=s)).cuda() for s in range(R)]
+        ys1 = [torch.empty_like(v) for v in xs1]
+        mm.apply_multi(X, R, Y)
+        for v, w in zip(xs1, ys1):
+            mm.apply(v, w)
+        torch.cuda.synchronize()
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            mm.apply_multi(X, R, Y)
+        e1.record()
+        torch.cuda.synchronize()
+        t_blk = e0.elapsed_time(e1) / 1e3 / reps
+        e0.record()
+        for _ in range(reps):
+            for v, w in zip(xs1, ys1):
+                mm.apply(v, w)
+        e1.record()
+        torch.cuda.synchronize()
+        t_one = e0.elapsed_time(e1) / 1e3 / reps
+        extras["multi_rhs"] = {"mesh": "elasticity 128^3 Cartesian", "nrhs": R, "ms_block": 1e3 * t_blk,
+                               "ms_16_single": 1e3 * t_one, "gdofs_block": R * pm.n_free / t_blk / 1e9,
+                               "gdofs_single": R * pm.n_free / t_one / 1e9, "speedup": t_one / t_blk}
+        mm.close()
+        del X, Y, xs1, ys1
+
+    # ---- mixed precision: FP32 inner CG inside FP64 iterative refinement, 192^3 jittered elasticity
+    if not args.no_mixed:
+        p3 = inputs.jittered_elasticity_192()
+        m3 = mf.Mesh.from_problem(p3, device=f"cuda:{local}")
+        b3 = torch.from_numpy(p3.b()).cuda()
+        xm, im = m3.cg(b3, precision=mf.MF_PREC_MIXED_IR, rtol=1e-10, inner_rtol=1e-4, timeout_s=args.cg_timeout,
+                       ok=CG_OK)
+        xd, idd = m3.cg(b3, rtol=1e-10, timeout_s=args.cg_timeout, ok=CG_OK)
+        err = float(torch.linalg.norm(xm - xd) / torch.linalg.norm(xd)) if idd.status == 0 else None
+        extras["mixed_precision"] = {
+            "mesh": "elasticity 192^3, node jitter 0.1h", "free_dof": p3.n_free,
+            "mixed": {"seconds": im.seconds, "outer": im.outer_iters, "inner_iters": im.iters, "status": im.status,
+                      "rel_res_true": im.rel_res_true},
+            "plain_fp64": {"seconds": idd.seconds, "iters": idd.iters, "status": idd.status,
+                           "rel_res_true": idd.rel_res_true},
+            "speedup": idd.seconds / im.seconds if im.status == 0 else None,
+            "rel_err_vs_fp64_solution": err}
+        m3.close()
+        del xm, xd, b3
+
+    # ---- learned preconditioner: 128^3 GRF Laplace, pairs from the FP64 solver, training, flexible CG
+    if not args.no_learned:
+        from paper_2308_09839_gb300 import learned
+        p5 = inputs.grf_laplace_128(seed=0, n=args.n_learned)
+        m5 = mf.Mesh.from_problem(p5, device=f"cuda:{local}")
+        nzyx = (p5.nz + 1, p5.ny + 1, p5.nx + 1)
+        t0 = time.perf_counter()
+        Rp, Tp, cs = learned.generate_pairs(m5, p5, args.pairs, seed=1, k_range=(2, 150))
+        torch.cuda.synchronize()
+        t_pairs = time.perf_counter() - t0
+        params, hist, t_train = learned.train(Rp, Tp, learned.node_logk(p5), nzyx, crop=nzyx[0],
+                                              steps=args.train_steps, lr=args.lr)
+        del Rp, Tp
+        net5 = learned.make_inference_net(params, nzyx, cs)
+        b5 = torch.from_numpy(p5.b()).cuda()
+        _, i_cg = m5.cg(b5, timeout_s=args.cg_timeout, ok=CG_OK)
+        _, i_j = m5.cg(b5, precond=mf.MF_PC_JACOBI, timeout_s=args.cg_timeout, ok=CG_OK)
+        _, i_nn = m5.cg(b5, net=net5, timeout_s=args.cg_timeout, ok=CG_OK)
+        extras["learned_preconditioner"] = {
+            "mesh": f"Laplace {p5.nx}^3, GRF log-kappa (8 cells, sigma 1.5) + 8 layers", "pairs": args.pairs,
+            "seconds_pairs": t_pairs, "train_steps": args.train_steps, "seconds_train": t_train,
+            "loss_first": float(np.mean(hist[:20])), "loss_last": float(np.mean(hist[-50:])),
+            "plain_cg": {"iters": i_cg.iters, "seconds": i_cg.seconds, "status": i_cg.status},
+            "jacobi_pcg": {"iters": i_j.iters, "seconds": i_j.seconds, "status": i_j.status},
+            "learned_fcg": {"iters": i_nn.iters, "seconds": i_nn.seconds, "status": i_nn.status,
+                            "rel_res_true": i_nn.rel_res_true, "network_switched_off_at": i_nn.outer_iters}}
+        net5.close()
+        m5.close()
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None

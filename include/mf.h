@@ -152,12 +152,18 @@ mf_status mf_destroy_csr(mf_csr *csr);
 /* Solver options (mf_cg_solve). */
 enum { MF_OP_MATFREE = 0, MF_OP_CSR = 1 };
 enum { MF_PREC_FP64 = 0, MF_PREC_MIXED_IR = 1 };
-enum { MF_PC_NONE = 0, MF_PC_JACOBI = 1 };
+enum { MF_PC_NONE = 0, MF_PC_JACOBI = 1, MF_PC_LEARNED = 2 };
+typedef struct mf_net mf_net;
 
 typedef struct {
   int32_t op;            /* MF_OP_MATFREE or MF_OP_CSR (then `csr` must be set) */
   int32_t precision;     /* MF_PREC_FP64, or MF_PREC_MIXED_IR: FP32 inner CG, FP64 refinement */
-  int32_t precond;       /* MF_PC_NONE or MF_PC_JACOBI (FP64 only) */
+  int32_t precond;       /* MF_PC_NONE, MF_PC_JACOBI (FP64 only) or MF_PC_LEARNED (flexible CG with
+                            the network in `net`; FP64, matrix-free, structured Laplace meshes whose
+                            node grid matches the network's; a stall or breakdown switches the
+                            network off and the solve continues as Jacobi-PCG from the current
+                            iterate; info->outer_iters reports the iteration of that switch, -1 if
+                            never) */
   int32_t max_iter;      /* > 0; for MIXED_IR the total inner iterations */
   double rtol;           /* stop when ||r||_2 <= rtol ||b||_2 (FP64 residual for MIXED_IR) */
   int32_t check_every;   /* iterations per CUDA-graph launch between host convergence checks */
@@ -166,17 +172,22 @@ typedef struct {
   double inner_rtol;     /* MIXED_IR: relative tolerance of each inner FP32 solve (e.g. 1e-4) */
   int32_t max_outer;     /* MIXED_IR: refinement steps */
   const mf_csr *csr;     /* operator when op == MF_OP_CSR */
+  const mf_net *net;     /* network when precond == MF_PC_LEARNED (flexible CG, see mf_net_create) */
 } mf_solve_opts;
 
 typedef struct {
   int32_t iters;          /* operator applies inside the Krylov loop(s) */
-  int32_t outer_iters;    /* refinement steps (MIXED_IR), else 0 */
+  int32_t outer_iters;    /* refinement steps (MIXED_IR); the switch-off iteration (LEARNED); else 0 */
   int32_t status;         /* same value as the return code */
   int32_t reserved;
   double rel_res;         /* ||r_k|| / ||b|| from the recurrence (inner FP64 residual for IR) */
   double rel_res_true;    /* ||b - A x|| / ||b|| recomputed with the FP64 operator after the solve */
   double seconds;         /* wall time of the call */
 } mf_solve_info;
+
+/* diag(A) of the FP64 operator (Eqs. 4/6; Dirichlet rows 1): device double[n_dof], asynchronous.
+ * This is the Jacobi preconditioner's diagonal. */
+mf_status mf_operator_diagonal(const mf_mesh *mesh, double *diag, mf_stream stream);
 
 /* Fills *opts with defaults: matrix-free, FP64, no preconditioner, rtol 1e-8, max_iter 100000,
  * check_every 32, graphs on, no timeout, inner_rtol 1e-4, max_outer 50. */
@@ -251,6 +262,57 @@ mf_status mf_cg_solve_batched(mf_mesh *const *meshes, int32_t n, const mf_solve_
 /* z-segment length (node planes per tile work item) of the tile kernels for this mesh; 0 restores
  * the built-in choice.  Used by the autotuner of the batched solver; results do not depend on it. */
 mf_status mf_set_tile_segment(mf_mesh *mesh, int32_t seg);
+
+/*
+ * Learned preconditioner (no counterpart in the paper, whose conclusions name matrix-free
+ * preconditioners as future work).  A 3-level convolutional encoder-decoder on the node grid
+ * (channels 16/32/64, 3x3x3 kernels, full-weighting restriction and trilinear prolongation between
+ * (4m+1)^3, (2m+1)^3 and (m+1)^3 node grids, skip connections), BF16 weights and activations with
+ * FP32 accumulation on the tensor cores, FP32 master weights and Adam.  Inputs: the residual
+ * scaled by the diagonal and its RMS, and the node average of log kappa; output: the (scaled)
+ * error.  In flexible CG it is the smooth-error correction of a two-level preconditioner between
+ * damped-Jacobi smoothing steps: z1 = w D^-1 r; r1 = r - A z1; cn = D^-1/2 (s/c) NN(D^-1/2 r1 / s,
+ * log kappa) with s = RMS(D^-1/2 r1); z2 = z1 + theta cn with the energy-norm step
+ * theta = max(0, cn.r1 / cn.A cn); z = z2 + w D^-1 (r - A z2); w = 2/3, c the output scale.
+ *   mf_net_create       node grid nx x ny x nz (each 4m+1 >= 5), seeded He initialisation.
+ *   mf_net_forward      r, logk, out: device float[nx ny nz] (x fastest).  Asynchronous.
+ *   mf_net_train_step   one Adam step on the relative squared error |out - target|^2 / |target|^2;
+ *                       *loss (host, may be NULL) receives the loss before the step (synchronises).
+ *   mf_net_gradients    loss and parameter gradients without an update (grads: host
+ *                       float[mf_net_num_params], may be NULL).
+ *   mf_net_get_params / mf_net_set_params   flat FP32 parameters (host arrays), for checkpoints and
+ *                       for moving weights between networks of different grid sizes.
+ * Low-level kernels, exposed for parity tests (BF16 tensors as uint16 bit patterns, channels-last
+ * [z][y][x][C]; weights [27][Cin][Cout] with tap t = dx + 3 dy + 9 dz for offsets (d - 1)):
+ *   mf_conv3d_fwd   y = relu?(conv(x, w) + bias + skip); C in [1, 64].
+ *   mf_conv3d_dgrad dx = conv^T(dy, w) (input gradient).
+ *   mf_conv3d_wgrad dw[27][Cin][Cout] and db[Cout] (FP32); workspace of mf_conv3d_wgrad_workspace bytes.
+ *   mf_grid_restrict / mf_grid_prolong   full weighting (2m+1)^3 -> (m+1)^3 and trilinear
+ *                   (m+1)^3 -> (2m+1)^3, times `scale`.
+ */
+mf_status mf_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t seed, mf_net **out);
+mf_status mf_net_destroy(mf_net *net);
+int64_t mf_net_num_params(const mf_net *net);
+mf_status mf_net_get_params(const mf_net *net, float *host);
+mf_status mf_net_set_params(mf_net *net, const float *host);
+mf_status mf_net_set_output_scale(mf_net *net, float scale);
+mf_status mf_net_forward(mf_net *net, const float *r, const float *logk, float *out, mf_stream stream);
+mf_status mf_net_train_step(mf_net *net, const float *r, const float *logk, const float *target, float lr,
+                            float *loss, mf_stream stream);
+mf_status mf_net_gradients(mf_net *net, const float *r, const float *logk, const float *target, float *grads,
+                           float *loss, mf_stream stream);
+mf_status mf_conv3d_fwd(const void *x, int32_t nx, int32_t ny, int32_t nz, int32_t cin, const void *w,
+                        const float *bias, int32_t cout, const void *skip, int32_t relu, void *y_bf16,
+                        float *y_f32, mf_stream stream);
+mf_status mf_conv3d_dgrad(const void *dy, int32_t nx, int32_t ny, int32_t nz, int32_t cin, const void *w,
+                          int32_t cout, void *dx_bf16, float *dx_f32, mf_stream stream);
+int64_t mf_conv3d_wgrad_workspace(int32_t nx, int32_t ny, int32_t nz, int32_t cin, int32_t cout);
+mf_status mf_conv3d_wgrad(const void *x, const void *dy, int32_t nx, int32_t ny, int32_t nz, int32_t cin,
+                          int32_t cout, float *dw, float *db, float *workspace, int64_t ws_bytes, mf_stream stream);
+mf_status mf_grid_restrict(const void *in, int32_t nfx, int32_t nfy, int32_t nfz, int32_t c, void *out,
+                           float scale, mf_stream stream);
+mf_status mf_grid_prolong(const void *in, int32_t ncx, int32_t ncy, int32_t ncz, int32_t c, void *out,
+                          float scale, mf_stream stream);
 
 /* Message describing the last failure in the calling thread ("" if none).  Valid until the next
  * failing call in the same thread. */

@@ -199,15 +199,18 @@ mf_status apply_reference(const mf_mesh *m, const R *x, R *y, cudaStream_t s, co
 
 mf_status apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip) {
   if (m->variant == MF_VARIANT_AUTO && m->tp) return tile_apply_fp64(m, x, y, s, skip);
+  if (m->variant == MF_VARIANT_AUTO && m->gen) return gen_apply_fp64(m, x, y, s, skip);
   return apply_reference<double>(m, x, y, s, skip);
 }
 
 mf_status apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip) {
   if (m->variant == MF_VARIANT_AUTO && m->tp) return tile_apply_fp32(m, x, y, s, skip);
+  if (m->variant == MF_VARIANT_AUTO && m->gen) return gen_apply_fp32(m, x, y, s, skip);
   return apply_reference<float>(m, x, y, s, skip);
 }
 
 mf_status apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s) {
+  if (m->variant == MF_VARIANT_AUTO && m->tp) return tile_apply_multi_fp64(m, nrhs, x, y, s);
   MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * nrhs * sizeof(double), s));
   const MeshView v = m->view();
   for (int c = 0; c < m->n_colours; ++c) {

@@ -135,7 +135,7 @@ __device__ bool chunk_reduce(BProblem &P, int lc, double part, double *sh, doubl
 }
 
 __global__ void __launch_bounds__(kThreadsB, 1) batched_cg(BArgs A) {
-  __shared__ TileSmem<MF_LAPLACE, NumDW, kEX, kEY> sm;
+  __shared__ TileSmem<MF_LAPLACE, NumDW, kEX, kEY, 1> sm;
   __shared__ double sh[kThreadsB / 32];
   const int G = gridDim.x;
   const int tid = threadIdx.x;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) batched_cg(BArgs A) {
       const BProblem *P = A.probs + A.item_prob[w];
       if (__ldcg(&P->sc->done)) continue;
       const TileArgs g = P->g;
-      tile_item<MF_LAPLACE, NumDW, kEX, kEY, true>(g, w - P->item0, P->p, P->Ap, sm);
+      tile_item<MF_LAPLACE, NumDW, kEX, kEY, true, 1>(g, w - P->item0, P->p, P->Ap, sm);
     }
     if (!grid_barrier(A.ctl, A.budget)) return;
     // ---- B: pAp, alpha

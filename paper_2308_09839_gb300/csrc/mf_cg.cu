@@ -348,6 +348,316 @@ mf_status cg_loop(CgWorkspace *w, int slot, long long key, const OpFn &op, int64
 
 }  // namespace
 
+// ------------------------------------------------------------------------------------------------
+// Flexible CG with the learned preconditioner (MF_PC_LEARNED).  The preconditioner z = M(r) changes
+// with r (a network), so beta uses the Polak-Ribiere form z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k)
+// (Notay, SIAM J. Sci. Comput. 22, 2000).  If the residual stops improving (no new best over 500
+// iterations) or a breakdown appears, the network is switched off and the solve restarts as
+// Jacobi-preconditioned CG from the current iterate.  M is a two-level preconditioner with the network as the
+// correction of smooth errors between damped-Jacobi smoothing steps (omega = 2/3, D = diag(A)):
+//   z1 = omega D^-1 r;  r1 = r - A z1;  cn = D^-1/2 (s/c) NN(D^-1/2 r1 / s, log kappa), s = RMS(D^-1/2 r1);
+//   z2 = z1 + theta cn with the energy-norm step theta = max(0, cn.r1 / cn.A cn) (a useless or harmful
+//   correction gets theta ~ 0);  z = z2 + omega D^-1 (r - A z2).
+// c is the network's output scale; z = 0 on Dirichlet DoFs.  The FP64 CG stays the fallback and
+// the judge of convergence (the true residual is recomputed at the end).
+// ------------------------------------------------------------------------------------------------
+extern "C" mf_status mf_net_forward(mf_net *N, const float *r, const float *logk, float *out, mf_stream stream);
+int64_t net_nodes(const mf_net *N);
+const int *net_dims(const mf_net *N);
+float net_out_scale(const mf_net *N);
+
+namespace {
+
+__global__ void __launch_bounds__(kRedThreads) dot2_kernel(int64_t n, const double *a, const double *b, const double *c,
+                                                           const double *d, double *partials, CgScalars *sc, double *out) {
+  double v[2] = {0.0, 0.0};
+  GRID_STRIDE(i, n) {
+    v[0] += a[i] * b[i];
+    if (c) v[1] += c[i] * d[i];
+  }
+  double o[2];
+  if (grid_reduce<2>(v, partials, &sc->ticket, o) && threadIdx.x == 0) {
+    out[0] = o[0];
+    if (c) out[1] = o[1];  // single dots write one scalar only
+  }
+}
+
+// ||D^{-1/2} r||^2 into *out (isd = D^{-1/2})
+__global__ void __launch_bounds__(kRedThreads) scaled_norm2(int64_t n, const double *r, const double *isd,
+                                                            double *partials, CgScalars *sc, double *out) {
+  double v[1] = {0.0};
+  GRID_STRIDE(i, n) {
+    const double t = r[i] * isd[i];
+    v[0] += t * t;
+  }
+  double o[1];
+  if (grid_reduce<1>(v, partials, &sc->ticket, o) && threadIdx.x == 0) out[0] = o[0];
+}
+
+// rhat = D^{-1/2} r / s (FP32), s = RMS of D^{-1/2} r from ss = ||D^{-1/2} r||^2
+__global__ void scale_to_f32(int64_t n, const double *r, const double *isd, const double *ss, float *out) {
+  const double s = sqrt(fmax(*ss, 1e-300) / (double)n);
+  GRID_STRIDE(i, n) out[i] = (float)(r[i] * isd[i] / s);
+}
+
+// z = beta z + omega D^{-1} r (damped Jacobi step; beta = 0 starts z), zero on Dirichlet nodes
+__global__ void jacobi_step(int64_t n, const double *r, const double *isd, double omega, double beta,
+                            const uint8_t *dmask, double *z) {
+  GRID_STRIDE(i, n) {
+    const double d = omega * isd[i] * isd[i] * r[i];
+    z[i] = dmask[i] ? 0.0 : (beta == 0.0 ? d : z[i] + d);
+  }
+}
+
+// out = r - t
+__global__ void sub_to(int64_t n, const double *r, const double *t, double *out) {
+  GRID_STRIDE(i, n) out[i] = r[i] - t[i];
+}
+
+// c = D^{-1/2} (s / c_out) zf (network correction), zero on Dirichlet nodes
+__global__ void net_correction(int64_t n, const float *zf, const double *isd, const double *ss, double c_out,
+                               const uint8_t *dmask, double *c) {
+  const double s = sqrt(fmax(*ss, 1e-300) / (double)n) / c_out;
+  GRID_STRIDE(i, n) c[i] = dmask[i] ? 0.0 : isd[i] * s * (double)zf[i];
+}
+
+// energy-norm step for the correction: theta = max(0, c.r1 / c.Ac); z += theta c; r1 -= theta Ac
+__global__ void theta_update(int64_t n, const double *num_den, const double *c, const double *Ac, double *z,
+                             double *r1) {
+  const double den = num_den[1];
+  const double th = den > 0.0 ? fmax(0.0, num_den[0] / den) : 0.0;
+  GRID_STRIDE(i, n) {
+    z[i] += th * c[i];
+    r1[i] -= th * Ac[i];
+  }
+}
+
+__global__ void inv_sqrt_kernel(int64_t n, double *d) {
+  GRID_STRIDE(i, n) d[i] = 1.0 / sqrt(d[i]);
+}
+
+// x += alpha p; rprev = r; r -= alpha Ap   (alpha = dev[0] / dev[1])
+__global__ void fcg_update_xr(int64_t n, double *x, double *r, double *rprev, const double *p, const double *Ap,
+                              const double *num, const double *den) {
+  const double alpha = *num / *den;
+  GRID_STRIDE(i, n) {
+    x[i] += alpha * p[i];
+    const double ri = r[i];
+    rprev[i] = ri;
+    r[i] = ri - alpha * Ap[i];
+  }
+}
+
+// diff = r - rprev (into rprev)
+__global__ void sub_inplace(int64_t n, const double *r, double *rprev) {
+  GRID_STRIDE(i, n) rprev[i] = r[i] - rprev[i];
+}
+
+// p = z + beta p, beta = num / den
+__global__ void fcg_update_p(int64_t n, const double *z, double *p, const double *num, const double *den) {
+  const double beta = *num / *den;
+  GRID_STRIDE(i, n) p[i] = z[i] + beta * p[i];
+}
+
+// node field of log(kappa): mean of log kappa over the cells touching each node (structured box)
+__global__ void node_logk(const double *kappa, int nx, int ny, int nz, float *out) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  if (n >= N) return;
+  const int i = (int)(n % (nx + 1)), j = (int)((n / (nx + 1)) % (ny + 1)), k = (int)(n / ((int64_t)(nx + 1) * (ny + 1)));
+  double s = 0.0;
+  int c = 0;
+  for (int dk = -1; dk <= 0; ++dk)
+    for (int dj = -1; dj <= 0; ++dj)
+      for (int di = -1; di <= 0; ++di) {
+        const int ex = i + di, ey = j + dj, ez = k + dk;
+        if (ex < 0 || ey < 0 || ez < 0 || ex >= nx || ey >= ny || ez >= nz) continue;
+        s += log(kappa[ex + (int64_t)nx * (ey + (int64_t)ny * ez)]);
+        ++c;
+      }
+  out[n] = (float)(s / c);
+}
+
+struct FcgBufs {
+  double *z, *rprev, *dev, *isd, *t, *r1, *cn;  // dev: scalars [0..7]; isd = D^{-1/2}; cn: correction
+  float *rf, *zf, *logk;
+};
+
+mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double *x, mf_solve_info *info,
+                    cudaStream_t s, std::chrono::steady_clock::time_point t0) {
+  const mf_net *net = o->net;
+  MF_ARG(net != nullptr, "mf_cg_solve: MF_PC_LEARNED needs opts->net");
+  MF_ARG(m->physics == MF_LAPLACE && m->structured, "mf_cg_solve: MF_PC_LEARNED needs a structured Laplace mesh");
+  const int *nd = net_dims(net);
+  MF_ARG(nd[0] == m->nx + 1 && nd[1] == m->ny + 1 && nd[2] == m->nz + 1,
+         "mf_cg_solve: the network was created for a different node grid");
+  MF_TRY(ensure_workspace(m, false, false));
+  CgWorkspace *w = m->cg;
+  const int64_t n = m->n_dof;
+  FcgBufs f{};
+  MF_CUDA(cudaMalloc(&f.z, n * sizeof(double)));
+  MF_CUDA(cudaMalloc(&f.rprev, n * sizeof(double)));
+  MF_CUDA(cudaMalloc(&f.dev, 8 * sizeof(double)));
+  MF_CUDA(cudaMalloc(&f.rf, n * sizeof(float)));
+  MF_CUDA(cudaMalloc(&f.zf, n * sizeof(float)));
+  MF_CUDA(cudaMalloc(&f.logk, n * sizeof(float)));
+  MF_CUDA(cudaMalloc(&f.isd, n * sizeof(double)));
+  MF_CUDA(cudaMalloc(&f.t, n * sizeof(double)));
+  MF_CUDA(cudaMalloc(&f.r1, n * sizeof(double)));
+  MF_CUDA(cudaMalloc(&f.cn, n * sizeof(double)));
+  auto release = [&]() {
+    cudaFree(f.z); cudaFree(f.rprev); cudaFree(f.dev); cudaFree(f.rf); cudaFree(f.zf); cudaFree(f.logk);
+    cudaFree(f.isd); cudaFree(f.t); cudaFree(f.r1); cudaFree(f.cn);
+  };
+  mf_count_launches(2);
+  node_logk<<<blocks_for(n), kThreads, 0, s>>>(m->mat, m->nx, m->ny, m->nz, f.logk);
+  MF_TRY(operator_diagonal(m, f.isd, s));
+  inv_sqrt_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.isd);
+  const double c_out = (double)net_out_scale(net);
+  bool learned = true;
+  int fallback_at = -1;
+  // dev: [0] r.r  [1] r.z (current)  [2] p.Ap  [3] z.(r - rprev)  [4] next r.z  [5] |D^-1/2 r1|^2
+  //      [6] cn.r1  [7] cn.A cn
+  auto dot2 = [&](const double *a, const double *bb, const double *c, const double *d, double *out) {
+    mf_count_launches(1);
+    dot2_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, a, bb, c, d, w->partials, w->sc, out);
+  };
+  auto precond = [&](const double *r, double *z) -> mf_status {
+    if (!learned) {  // after the switch-off: Jacobi (z = D^-1 r)
+      mf_count_launches(1);
+      jacobi_step<<<kRedBlocks, kRedThreads, 0, s>>>(n, r, f.isd, 1.0, 0.0, m->dmask, z);
+      return MF_OK;
+    }
+    // two-level form: damped-Jacobi pre-smoothing, network correction of the smoothed residual,
+    // damped-Jacobi post-smoothing
+    const double omega = 2.0 / 3.0;
+    mf_count_launches(2);
+    jacobi_step<<<kRedBlocks, kRedThreads, 0, s>>>(n, r, f.isd, omega, 0.0, m->dmask, z);
+    MF_TRY(apply_fp64(m, z, f.t, s));
+    sub_to<<<kRedBlocks, kRedThreads, 0, s>>>(n, r, f.t, f.r1);
+    mf_count_launches(3);
+    scaled_norm2<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.r1, f.isd, w->partials, w->sc, f.dev + 5);
+    scale_to_f32<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.r1, f.isd, f.dev + 5, f.rf);
+    MF_TRY(mf_net_forward(const_cast<mf_net *>(net), f.rf, f.logk, f.zf, (mf_stream)s));
+    mf_count_launches(1);
+    net_correction<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.zf, f.isd, f.dev + 5, c_out, m->dmask, f.cn);
+    MF_TRY(apply_fp64(m, f.cn, f.t, s));
+    dot2(f.cn, f.r1, f.cn, f.t, f.dev + 6);  // dev[6] = c.r1, dev[7] = c.Ac
+    mf_count_launches(2);
+    theta_update<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.dev + 6, f.cn, f.t, z, f.r1);
+    jacobi_step<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.r1, f.isd, omega, 1.0, m->dmask, z);
+    return MF_OK;
+  };
+  double h[8];
+  mf_status st = MF_OK;
+  // x = 0, r = b
+  MF_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  MF_CUDA(cudaMemcpyAsync(w->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  dot2(w->r, w->r, nullptr, nullptr, f.dev + 0);
+  MF_CUDA(cudaMemcpyAsync(h, f.dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  const double bb = h[0];
+  const double tol2 = o->rtol * o->rtol * bb;
+  double rr = bb, best = bb, window_start = bb;
+  int it = 0, since = 0;
+  const int window = 500;  // the residual norm of CG is not monotone: judge stalls over long windows
+  if (!(bb > 0.0)) {
+    release();
+    if (info) { info->iters = 0; info->status = bb == 0.0 ? MF_OK : MF_ERR_BREAKDOWN; info->rel_res = 0; info->rel_res_true = 0; }
+    return bb == 0.0 ? MF_OK : MF_ERR_BREAKDOWN;
+  }
+  st = precond(w->r, f.z);
+  if (st != MF_OK) { release(); return st; }
+  MF_CUDA(cudaMemcpyAsync(w->p, f.z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  dot2(w->r, f.z, nullptr, nullptr, f.dev + 1);
+  // switch the network off and restart as Jacobi-preconditioned CG from the current iterate (from
+  // x = 0 when the iterate is no longer finite): r = b - A x, p = z = D^-1 r
+  auto restart_jacobi = [&]() -> mf_status {
+    learned = false;
+    fallback_at = it;
+    MF_TRY(apply_fp64(m, x, w->Ap, s));
+    mf_count_launches(1);
+    residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->Ap, w->r, w->partials, w->sc);
+    CgScalars hs;
+    MF_CUDA(cudaMemcpyAsync(&hs, w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    if (!std::isfinite(hs.res2)) {
+      MF_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+      MF_CUDA(cudaMemcpyAsync(w->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    MF_TRY(precond(w->r, f.z));
+    MF_CUDA(cudaMemcpyAsync(w->p, f.z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    dot2(w->r, w->r, nullptr, nullptr, f.dev + 0);
+    dot2(w->r, f.z, nullptr, nullptr, f.dev + 1);
+    MF_CUDA(cudaMemcpyAsync(h, f.dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    rr = h[0];
+    return MF_OK;
+  };
+  while (!(rr <= tol2) && it < o->max_iter) {
+    MF_TRY(apply_fp64(m, w->p, w->Ap, s));
+    dot2(w->p, w->Ap, nullptr, nullptr, f.dev + 2);
+    mf_count_launches(1);
+    fcg_update_xr<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, w->r, f.rprev, w->p, w->Ap, f.dev + 1, f.dev + 2);
+    dot2(w->r, w->r, nullptr, nullptr, f.dev + 0);
+    ++it;
+    MF_CUDA(cudaMemcpyAsync(h, f.dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    rr = h[0];
+    if (!std::isfinite(rr) || !(h[2] > 0.0)) {
+      if (!learned) { st = MF_ERR_BREAKDOWN; break; }
+      MF_TRY(restart_jacobi());  // breakdown with the network: Jacobi-PCG from here
+      continue;
+    }
+    if (rr <= tol2) break;
+    if (o->timeout_s > 0 && std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > o->timeout_s) {
+      st = MF_ERR_TIMEOUT;
+      break;
+    }
+    if (learned) {
+      if (rr < best) best = rr;
+      if (++since >= window) {
+        if (best >= 0.98 * window_start) {  // no new best residual over the whole window
+          MF_TRY(restart_jacobi());
+          continue;
+        }
+        window_start = best;
+        since = 0;
+      }
+    }
+    st = precond(w->r, f.z);
+    if (st != MF_OK) break;
+    mf_count_launches(1);
+    sub_inplace<<<kRedBlocks, kRedThreads, 0, s>>>(n, w->r, f.rprev);
+    dot2(f.z, f.rprev, w->r, f.z, f.dev + 3);  // dev[3] = z.(r - rprev), dev[4] = r.z
+    mf_count_launches(2);
+    fcg_update_p<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.z, w->p, f.dev + 3, f.dev + 1);
+    MF_CUDA(cudaMemcpyAsync(f.dev + 1, f.dev + 4, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  if (st == MF_OK && !(rr <= tol2)) st = std::isfinite(rr) ? MF_NOT_CONVERGED : MF_ERR_BREAKDOWN;
+  // true residual
+  MF_TRY(apply_fp64(m, x, w->Ap, s));
+  mf_count_launches(1);
+  residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->Ap, nullptr, w->partials, w->sc);
+  CgScalars hs;
+  MF_CUDA(cudaMemcpyAsync(&hs, w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  release();
+  if (info) {
+    info->iters = it;
+    info->outer_iters = fallback_at;  // iteration at which the network was switched off, -1 if never
+    info->status = st;
+    info->rel_res = std::sqrt(rr / bb);
+    info->rel_res_true = std::sqrt(hs.res2 / bb);
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (st == MF_NOT_CONVERGED) mf_set_error("mf_cg_solve: not converged within the iteration limit");
+  if (st == MF_ERR_BREAKDOWN) mf_set_error("mf_cg_solve: breakdown");
+  return st;
+}
+
+}  // namespace
+
 extern "C" void mf_solve_opts_default(mf_solve_opts *o) {
   if (!o) return;
   o->op = MF_OP_MATFREE;
@@ -361,6 +671,7 @@ extern "C" void mf_solve_opts_default(mf_solve_opts *o) {
   o->inner_rtol = 1e-4;
   o->max_outer = 50;
   o->csr = nullptr;
+  o->net = nullptr;
 }
 
 extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double *x, mf_solve_info *info,
@@ -372,7 +683,12 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
   MF_ARG(o->op == MF_OP_MATFREE || o->csr != nullptr, "mf_cg_solve: op CSR needs opts->csr");
   MF_ARG(o->op == MF_OP_MATFREE || o->csr->n_rows == m->n_dof, "mf_cg_solve: CSR size does not match the mesh");
   MF_ARG(o->precision == MF_PREC_FP64 || o->precision == MF_PREC_MIXED_IR, "mf_cg_solve: unknown precision");
-  MF_ARG(o->precond == MF_PC_NONE || o->precond == MF_PC_JACOBI, "mf_cg_solve: unknown preconditioner");
+  MF_ARG(o->precond == MF_PC_NONE || o->precond == MF_PC_JACOBI || o->precond == MF_PC_LEARNED,
+         "mf_cg_solve: unknown preconditioner");
+  if (o->precond == MF_PC_LEARNED) {
+    MF_ARG(o->precision == MF_PREC_FP64 && o->op == MF_OP_MATFREE, "mf_cg_solve: MF_PC_LEARNED is FP64 matrix-free");
+    return fcg_solve(m, o, b, x, info, (cudaStream_t)stream, t0);
+  }
   MF_ARG(o->precision == MF_PREC_FP64 || o->precond == MF_PC_NONE, "mf_cg_solve: MIXED_IR takes no preconditioner");
   MF_ARG(o->precision == MF_PREC_FP64 || o->op == MF_OP_MATFREE, "mf_cg_solve: MIXED_IR needs the matrix-free operator");
   MF_ARG(o->max_iter > 0 && o->rtol > 0 && o->check_every > 0, "mf_cg_solve: bad max_iter/rtol/check_every");
@@ -607,4 +923,10 @@ extern "C" mf_status mf_cg_solve_noalloc(const mf_mesh *m, const mf_solve_opts *
   if (st == MF_ERR_BREAKDOWN) mf_set_error("mf_cg_solve_noalloc: breakdown (p^T A p <= 0 or non-finite scalar)");
   if (st == MF_NOT_CONVERGED) mf_set_error("mf_cg_solve_noalloc: not converged within the iteration limit");
   return st;
+}
+
+extern "C" mf_status mf_operator_diagonal(const mf_mesh *m, double *diag, mf_stream stream) {
+  mf_clear_error();
+  MF_ARG(m && diag, "mf_operator_diagonal: null argument");
+  return operator_diagonal(m, diag, (cudaStream_t)stream);
 }

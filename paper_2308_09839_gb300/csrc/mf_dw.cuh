@@ -61,6 +61,22 @@ __device__ __forceinline__ dw mul(dw x, dw y) {
   return dw{p, __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, e))};
 }
 
+// x / y (the division of Joldes, Muller and Popescu 2017, Alg. 17 "DWDivDW2"): quotient of the high
+// parts, one correction step on the DW remainder.
+__device__ __forceinline__ dw div(dw x, dw y) {
+  const float th = __fdiv_rn(x.h, y.h);
+  const float p = __fmul_rn(y.h, th);
+  const float pe = __fmaf_rn(y.h, th, -p);
+  const float pl = __fmaf_rn(y.l, th, pe);  // y * th = p + pl
+  float s, t;
+  two_sum(x.h, -p, s, t);
+  const float rem = __fadd_rn(s, __fadd_rn(__fsub_rn(t, pl), x.l));
+  const float tl = __fdiv_rn(rem, y.h);
+  float zh, zl;
+  fast_two_sum(th, tl, zh, zl);
+  return dw{zh, zl};
+}
+
 // x * 2^k (exact for both parts in the normal range).
 __device__ __forceinline__ dw scale(dw x, float pow2) { return dw{__fmul_rn(x.h, pow2), __fmul_rn(x.l, pow2)}; }
 

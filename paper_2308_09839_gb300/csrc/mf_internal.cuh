@@ -119,6 +119,12 @@ struct mf_mesh {
   // as pairs; enables the FP64-accurate tile kernels of mf_tile.cu
   bool tp = false;
   int tile_seg = 0;  // z-segment length of the tile kernels (0: heuristic; set by the autotuner)
+  // general structured geometry (structured boxes that are not tensor-product grids): half
+  // spacings of the base grid [hx/2 | hy/2 | hz/2] and node offsets from it, as float pairs;
+  // enables the FP64-accurate general tile kernels of mf_general.cu
+  bool gen = false;
+  float2 *gen_axis = nullptr;
+  float2 *gen_delta = nullptr;
   float2 *tp_axis = nullptr;
   float2 *mat_pairs = nullptr;
 
@@ -150,6 +156,11 @@ mf_status spmv(const mf_csr *A, const double *x, double *y, cudaStream_t s, cons
 mf_status tile_setup(mf_mesh *m, cudaStream_t s);
 mf_status tile_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip);
 mf_status tile_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip);
+mf_status tile_apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s);
+// general structured kernels (mf_general.cu)
+mf_status gen_setup(mf_mesh *m, cudaStream_t s);
+mf_status gen_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip);
+mf_status gen_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip);
 // diag(A) of the matrix-free operator (Jacobi), FP64, Dirichlet rows 1.
 mf_status operator_diagonal(const mf_mesh *m, double *diag, cudaStream_t s);
 void cg_workspace_free(CgWorkspace *w);

@@ -160,6 +160,8 @@ static void free_mesh(mf_mesh *m) {
   cudaFree(m->colour_elems);
   cudaFree(m->tp_axis);
   cudaFree(m->mat_pairs);
+  cudaFree(m->gen_axis);
+  cudaFree(m->gen_delta);
   delete m;
 }
 
@@ -320,6 +322,7 @@ extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells
     } else {
       m->n_colours = 8;  // parity colouring of the box
       SETUP_TRY(tile_setup(m, s));
+      SETUP_TRY(gen_setup(m, s));
     }
     SETUP_CUDA(cudaStreamSynchronize(s));
   }

@@ -81,20 +81,53 @@ mf_status tile_setup(mf_mesh *m, cudaStream_t s) {
   return MF_OK;
 }
 
-template <int PHYS, class N>
-static void tile_launch_one(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
-                            const int *skip) {
+template <int PHYS, class N, int NR = 1>
+static mf_status tile_launch_one(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
+                                 const int *skip, int nrhs = 1, int r0 = 0) {
   using TS = TileShape<PHYS, N>;
-  const TileArgs g = make_tile_args(m, TS::EX, TS::EY, m->tile_seg);
-  tile_apply<PHYS, N, TS::EX, TS::EY, TS::MINB><<<tile_items(g), TS::EX * TS::EY, 0, s>>>(g, x, y, skip);
+  TileArgs g = make_tile_args(m, TS::EX, TS::EY, m->tile_seg);
+  g.nrhs = nrhs;
+  g.r0 = r0;
+  const int smem = (int)sizeof(TileSmem<PHYS, N, TS::EX, TS::EY, NR>);
+  auto kern = tile_apply<PHYS, N, TS::EX, TS::EY, TS::MINB, NR>;
+  if (smem > 48 * 1024) {
+    static bool set = false;
+    if (!set) {
+      MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      set = true;
+    }
+  }
+  kern<<<tile_items(g), TS::EX * TS::EY, smem, s>>>(g, x, y, skip);
+  return MF_OK;
 }
 
 template <class N>
 static mf_status tile_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
                              const int *skip) {
   mf_count_launches(1);
-  if (m->physics == MF_LAPLACE) tile_launch_one<MF_LAPLACE, N>(m, x, y, s, skip);
-  else tile_launch_one<MF_ELASTICITY, N>(m, x, y, s, skip);
+  if (m->physics == MF_LAPLACE) MF_TRY((tile_launch_one<MF_LAPLACE, N>(m, x, y, s, skip)));
+  else MF_TRY((tile_launch_one<MF_ELASTICITY, N>(m, x, y, s, skip)));
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
+// Multi right-hand-side apply on [node][rhs][comp] vectors: passes of kMultiR right-hand sides,
+// each computing the element coefficients once and applying them to every right-hand side of the
+// pass (a final pass takes the remainder one at a time).
+constexpr int kMultiR = 4;
+
+mf_status tile_apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s) {
+  int r = 0;
+  for (; r + kMultiR <= nrhs; r += kMultiR) {
+    mf_count_launches(1);
+    if (m->physics == MF_LAPLACE) MF_TRY((tile_launch_one<MF_LAPLACE, NumDW, kMultiR>(m, x, y, s, nullptr, nrhs, r)));
+    else MF_TRY((tile_launch_one<MF_ELASTICITY, NumDW, kMultiR>(m, x, y, s, nullptr, nrhs, r)));
+  }
+  for (; r < nrhs; ++r) {
+    mf_count_launches(1);
+    if (m->physics == MF_LAPLACE) MF_TRY((tile_launch_one<MF_LAPLACE, NumDW, 1>(m, x, y, s, nullptr, nrhs, r)));
+    else MF_TRY((tile_launch_one<MF_ELASTICITY, NumDW, 1>(m, x, y, s, nullptr, nrhs, r)));
+  }
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }

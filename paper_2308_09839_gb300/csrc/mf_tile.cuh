@@ -32,6 +32,7 @@
 //    output planes accumulated there in a fixed order.  Every y entry is written exactly once,
 //    without a memset or read-modify-write, and the result is bitwise reproducible.
 #include <algorithm>
+#include <type_traits>
 
 #include "mf_dw.cuh"
 #include "mf_internal.cuh"
@@ -109,63 +110,93 @@ __device__ __forceinline__ void fwht_inv(typename N::T v[8]) {
       }
 }
 
-// Scalar Laplace on an axis-aligned box, in place: u (nodal values) -> v = A^e u.
+// Scalar Laplace on an axis-aligned box.  The per-element coefficients (depending on geometry and
+// kappa only) are computed once and applied to every right-hand side.
 // Modes are indexed by the bit set of the monomial: 1 xi, 2 eta, 4 zeta, 3 xi eta, 5 xi zeta,
 // 6 eta zeta, 7 xi eta zeta.  hy_ihx = hy/hx, hx_ihy = hx/hy and hxhy = hx hy are per-thread
 // invariants of the z-march.
 template <class N>
-__device__ __forceinline__ void laplace_box(typename N::T u[8], typename N::T k, typename N::T hy_ihx,
-                                            typename N::T hx_ihy, typename N::T hxhy, typename N::T hz,
-                                            typename N::T ihz) {
+struct LapCoef {
+  typename N::T s1, s2, s3, s12, s13, s23, s123;
+};
+
+template <class N>
+__device__ __forceinline__ LapCoef<N> laplace_coef(typename N::T k, typename N::T hy_ihx, typename N::T hx_ihy,
+                                                   typename N::T hxhy, typename N::T hz, typename N::T ihz) {
   using T = typename N::T;
   const T kz = N::mul(k, hz);
   const T g1 = N::mul(kz, hy_ihx);              // kappa hy hz / hx
   const T g2 = N::mul(kz, hx_ihy);              // kappa hx hz / hy
   const T g3 = N::mul(N::mul(k, ihz), hxhy);    // kappa hx hy / hz
-  const T g12 = N::add(g1, g2), g13 = N::add(g1, g3), g23 = N::add(g2, g3);
-  const T g123 = N::add(g12, g3);
+  const T g12 = N::add(g1, g2);
+  LapCoef<N> c;
+  c.s1 = N::scale(g1, 0.0625f);
+  c.s2 = N::scale(g2, 0.0625f);
+  c.s3 = N::scale(g3, 0.0625f);
+  c.s12 = N::mul(g12, N::c(C_48TH));
+  c.s13 = N::mul(N::add(g1, g3), N::c(C_48TH));
+  c.s23 = N::mul(N::add(g2, g3), N::c(C_48TH));
+  c.s123 = N::mul(N::add(g12, g3), N::c(C_144TH));
+  return c;
+}
+
+// u (nodal values) -> A^e u, in place.
+template <class N>
+__device__ __forceinline__ void laplace_apply(const LapCoef<N> &c, typename N::T u[8]) {
   fwht_fwd<N>(u);
   u[0] = N::zero();
-  u[1] = N::scale(N::mul(g1, u[1]), 0.0625f);
-  u[2] = N::scale(N::mul(g2, u[2]), 0.0625f);
-  u[4] = N::scale(N::mul(g3, u[4]), 0.0625f);
-  u[3] = N::mul(N::mul(g12, N::c(C_48TH)), u[3]);
-  u[5] = N::mul(N::mul(g13, N::c(C_48TH)), u[5]);
-  u[6] = N::mul(N::mul(g23, N::c(C_48TH)), u[6]);
-  u[7] = N::mul(N::mul(g123, N::c(C_144TH)), u[7]);
+  u[1] = N::mul(c.s1, u[1]);
+  u[2] = N::mul(c.s2, u[2]);
+  u[4] = N::mul(c.s3, u[4]);
+  u[3] = N::mul(c.s12, u[3]);
+  u[5] = N::mul(c.s13, u[5]);
+  u[6] = N::mul(c.s23, u[6]);
+  u[7] = N::mul(c.s123, u[7]);
   fwht_inv<N>(u);
 }
 
-// Isotropic elasticity on an axis-aligned box, in place on c[k][a] (component k, corner a).
-// With r_k = h_{k+1} h_{k+2} / h_k and the mode coefficients c^k = H u^k:
+// Isotropic elasticity on an axis-aligned box.  With r_k = h_{k+1} h_{k+2} / h_k and the mode
+// coefficients c^k = H u^k:
 //   same-component terms:  W^l_k = (k == l ? lam + 2 mu : mu) r_k / 16 weighted like the Laplace D;
 //   cross-component terms: lam h_m / 16 and mu h_m / 16 (m the third axis) between the linear and
 //   bilinear modes of components k != l, as derived from Eq. 6 with J diagonal.
 template <class N>
-__device__ __forceinline__ void elasticity_box(typename N::T c[3][8], typename N::T lam, typename N::T mu,
-                                               const typename N::T h[3], const typename N::T ih[3]) {
+struct ElCoef {
+  typename N::T lr[3], mr[3], L[3], M[3], L3[3], M3[3];
+};
+
+template <class N>
+__device__ __forceinline__ ElCoef<N> elasticity_coef(typename N::T lam, typename N::T mu, const typename N::T h[3],
+                                                     const typename N::T ih[3]) {
   using T = typename N::T;
   const T h01 = N::mul(h[0], h[1]), h02 = N::mul(h[0], h[2]), h12 = N::mul(h[1], h[2]);
   const T r[3] = {N::mul(h12, ih[0]), N::mul(h02, ih[1]), N::mul(h01, ih[2])};
   const T l2m = N::add(lam, N::scale(mu, 2.0f));
-  T mr[3], lr[3], L[3], M[3], L3[3], M3[3];
+  ElCoef<N> e;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    mr[k] = N::scale(N::mul(mu, r[k]), 0.0625f);
-    lr[k] = N::scale(N::mul(l2m, r[k]), 0.0625f);
-    L[k] = N::scale(N::mul(lam, h[k]), 0.0625f);
-    M[k] = N::scale(N::mul(mu, h[k]), 0.0625f);
-    L3[k] = N::mul(L[k], N::c(C_THIRD));
-    M3[k] = N::mul(M[k], N::c(C_THIRD));
+    e.mr[k] = N::scale(N::mul(mu, r[k]), 0.0625f);
+    e.lr[k] = N::scale(N::mul(l2m, r[k]), 0.0625f);
+    e.L[k] = N::scale(N::mul(lam, h[k]), 0.0625f);
+    e.M[k] = N::scale(N::mul(mu, h[k]), 0.0625f);
+    e.L3[k] = N::mul(e.L[k], N::c(C_THIRD));
+    e.M3[k] = N::mul(e.M[k], N::c(C_THIRD));
   }
+  return e;
+}
+
+// c[k][a] (component k, corner a) -> A^e u, in place.
+template <class N>
+__device__ __forceinline__ void elasticity_apply(const ElCoef<N> &e, typename N::T c[3][8]) {
+  using T = typename N::T;
 #pragma unroll
   for (int k = 0; k < 3; ++k) fwht_fwd<N>(c[k]);
   T o[3][8];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const T W1 = l == 0 ? lr[0] : mr[0];
-    const T W2 = l == 1 ? lr[1] : mr[1];
-    const T W3 = l == 2 ? lr[2] : mr[2];
+    const T W1 = l == 0 ? e.lr[0] : e.mr[0];
+    const T W2 = l == 1 ? e.lr[1] : e.mr[1];
+    const T W3 = l == 2 ? e.lr[2] : e.mr[2];
     const T W12 = N::add(W1, W2), W13 = N::add(W1, W3), W23 = N::add(W2, W3);
     o[l][0] = N::zero();
     o[l][1] = N::mul(W1, c[l][1]);
@@ -176,7 +207,7 @@ __device__ __forceinline__ void elasticity_box(typename N::T c[3][8], typename N
     o[l][6] = N::mul(N::mul(W23, N::c(C_THIRD)), c[l][6]);
     o[l][7] = N::mul(N::mul(N::add(W12, W3), N::c(C_NINTH)), c[l][7]);
   }
-#define ACC(l, m, coef, k, mm) o[l][m] = N::add(o[l][m], N::mul(coef, c[k][mm]))
+#define ACC(l, m, coef, k, mm) o[l][m] = N::add(o[l][m], N::mul(e.coef, c[k][mm]))
   // components 0 <-> 1 (third axis 2)
   ACC(1, 2, L[2], 0, 1); ACC(1, 6, L3[2], 0, 5); ACC(1, 1, M[2], 0, 2); ACC(1, 5, M3[2], 0, 6);
   ACC(0, 1, L[2], 1, 2); ACC(0, 5, L3[2], 1, 6); ACC(0, 2, M[2], 1, 1); ACC(0, 6, M3[2], 1, 5);
@@ -198,15 +229,16 @@ __device__ __forceinline__ void elasticity_box(typename N::T c[3][8], typename N
 struct TileArgs {
   int nx, ny, nz;
   int tiles_x, tiles_y, seg;
+  int nrhs, r0;  // vectors hold nrhs right-hand sides per node ([node][rhs][comp]); this pass does r0..r0+NR-1
   const float2 *hx, *hy, *hz, *ihx, *ihy, *ihz;  // per-axis spacings and inverses (pairs)
   const float2 *mat;                             // kappa[E] or (lam, mu)[E] as pairs
   const uint8_t *dmask;
 };
 
 // Shared-memory footprint of one tile (staged input planes and output-plane accumulators).
-template <int PHYS, class N, int EX, int EY>
+template <int PHYS, class N, int EX, int EY, int NR = 1>
 struct TileSmem {
-  static constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  static constexpr int ND = (PHYS == MF_LAPLACE ? 1 : 3) * NR;
   static constexpr int NP = (EX + 1) * (EY + 1), NACC = (EX - 1) * (EY - 1) * ND;
   typename N::S up[2][NP * ND];
   typename N::S acc[2][NACC];
@@ -217,13 +249,14 @@ struct TileSmem {
 // enumerates tile columns fastest, then z-segments.  Must be called by all EX*EY threads.
 // COHERENT: read x through L2 only (x was written by other CTAs earlier in the same persistent
 // kernel, so the read-only and L1 paths may hold stale lines); otherwise through the read-only path.
-template <int PHYS, class N, int EX, int EY, bool COHERENT = false>
+template <int PHYS, class N, int EX, int EY, bool COHERENT = false, int NR = 1>
 __device__ __forceinline__ void tile_item(const TileArgs &g, int item, const typename N::IO *__restrict__ x,
-                                          typename N::IO *__restrict__ y, TileSmem<PHYS, N, EX, EY> &sm) {
+                                          typename N::IO *__restrict__ y, TileSmem<PHYS, N, EX, EY, NR> &sm) {
   using T = typename N::T;
   using S = typename N::S;
   using IO = typename N::IO;
-  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  constexpr int NC = PHYS == MF_LAPLACE ? 1 : 3;  // components per node and right-hand side
+  constexpr int ND = NC * NR;                     // values per node handled by this pass
   constexpr int NT = EX * EY, TX = EX - 1, TY = EY - 1, PX = EX + 1, PY = EY + 1, NP = PX * PY;
   constexpr int LOADS = (NP + NT - 1) / NT;
   constexpr int NACC = TX * TY * ND;
@@ -263,9 +296,10 @@ __device__ __forceinline__ void tile_item(const TileArgs &g, int item, const typ
       const int ix = i0 - 1 + p % PX, iy = j0 - 1 + p / PX;
       const bool ok = p < NP && ix >= 0 && ix < NXP && iy >= 0 && iy < NYP;
       const int64_t node = ix + (int64_t)NXP * (iy + (int64_t)NYP * k);
+      const int64_t vb = (node * g.nrhs + g.r0) * NC;
       dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
 #pragma unroll
-      for (int c = 0; c < ND; ++c) xr[l][c] = ok ? (COHERENT ? __ldcg(x + node * ND + c) : __ldg(x + node * ND + c)) : (IO)0;
+      for (int c = 0; c < ND; ++c) xr[l][c] = ok ? (COHERENT ? __ldcg(x + vb + c) : __ldg(x + vb + c)) : (IO)0;
     }
   };
   auto stage = [&](int k) {
@@ -285,8 +319,8 @@ __device__ __forceinline__ void tile_item(const TileArgs &g, int item, const typ
       const int lx = idx % TX, ly = idx / TX;
       if (lx < ownx && ly < owny) {
         const int64_t node = (i0 + lx) + (int64_t)NXP * ((j0 + ly) + (int64_t)NYP * k);
-        y[node * ND + c] = __ldg(g.dmask + node) ? (COHERENT ? __ldcg(x + node * ND + c) : x[node * ND + c])
-                                                 : N::out(N::ld(a[t]));
+        const int64_t vi = (node * g.nrhs + g.r0) * NC + c;
+        y[vi] = __ldg(g.dmask + node) ? (COHERENT ? __ldcg(x + vi) : x[vi]) : N::out(N::ld(a[t]));
       }
       N::st(a[t], N::zero());
     }
@@ -300,57 +334,69 @@ __device__ __forceinline__ void tile_item(const TileArgs &g, int item, const typ
     stage(ez + 1);
     __syncthreads();
     if (ez + 2 <= g.nz) fetch(ez + 2);
-    T v[ND][8];
+    // element coefficients (geometry, material) once per element, then per right-hand side: gather,
+    // evaluate and accumulate (one right-hand side's values live in registers at a time)
+    const int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
+    const T hz = N::from2(__ldg(g.hz + ez)), ihz = N::from2(__ldg(g.ihz + ez));
+    using Coef = std::conditional_t<PHYS == MF_LAPLACE, LapCoef<N>, ElCoef<N>>;
+    Coef cf;
     if (ein) {
-      const S *ub = up[ez & 1];
-      const S *ut = up[(ez + 1) & 1];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int p = (tx + (a & 1)) + PX * (ty + ((a >> 1) & 1));
-        const S *u = (a & 4) ? ut : ub;
-#pragma unroll
-        for (int c = 0; c < ND; ++c) v[c][a] = N::ld(u[p * ND + c]);
-      }
-      const int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
-      const T hz = N::from2(__ldg(g.hz + ez)), ihz = N::from2(__ldg(g.ihz + ez));
       if constexpr (PHYS == MF_LAPLACE) {
-        laplace_box<N>(v[0], N::from2(__ldg(g.mat + e)), hy_ihx, hx_ihy, hxhy, hz, ihz);
+        cf = laplace_coef<N>(N::from2(__ldg(g.mat + e)), hy_ihx, hx_ihy, hxhy, hz, ihz);
       } else {
         const T h[3] = {hx, hy, hz}, ih[3] = {ihx, ihy, ihz};
-        elasticity_box<N>(v, N::from2(__ldg(g.mat + 2 * e)), N::from2(__ldg(g.mat + 2 * e + 1)), h, ih);
+        cf = elasticity_coef<N>(N::from2(__ldg(g.mat + 2 * e)), N::from2(__ldg(g.mat + 2 * e + 1)), h, ih);
       }
     }
     const bool bot = ez >= k0, top = ez + 1 < k1;
+#pragma unroll 1
+    for (int r = 0; r < NR; ++r) {
+      T v[NC][8];
+      if (ein) {
+        const S *ub = up[ez & 1];
+        const S *ut = up[(ez + 1) & 1];
 #pragma unroll
-    for (int ay = 0; ay < 2; ++ay) {
+        for (int a = 0; a < 8; ++a) {
+          const int p = (tx + (a & 1)) + PX * (ty + ((a >> 1) & 1));
+          const S *u = (a & 4) ? ut : ub;
 #pragma unroll
-      for (int ax = 0; ax < 2; ++ax) {
-        const int lx = tx - 1 + ax, ly = ty - 1 + ay;
-        if (ein && lx >= 0 && lx < ownx && ly >= 0 && ly < owny) {
-          const int idx = (lx + TX * ly) * ND;
-          const int a = ax + 2 * ay;
-#pragma unroll
-          for (int c = 0; c < ND; ++c) {
-            if (bot) N::st(acc[ez & 1][idx + c], N::add(N::ld(acc[ez & 1][idx + c]), v[c][a]));
-            if (top) N::st(acc[(ez + 1) & 1][idx + c], N::add(N::ld(acc[(ez + 1) & 1][idx + c]), v[c][a + 4]));
-          }
+          for (int c = 0; c < NC; ++c) v[c][a] = N::ld(u[p * ND + r * NC + c]);
         }
-        __syncwarp();
+        if constexpr (PHYS == MF_LAPLACE) laplace_apply<N>(cf, v[0]);
+        else elasticity_apply<N>(cf, v);
       }
-      __syncthreads();
+#pragma unroll
+      for (int ay = 0; ay < 2; ++ay) {
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax) {
+          const int lx = tx - 1 + ax, ly = ty - 1 + ay;
+          if (ein && lx >= 0 && lx < ownx && ly >= 0 && ly < owny) {
+            const int idx = (lx + TX * ly) * ND + r * NC;
+            const int a = ax + 2 * ay;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              if (bot) N::st(acc[ez & 1][idx + c], N::add(N::ld(acc[ez & 1][idx + c]), v[c][a]));
+              if (top) N::st(acc[(ez + 1) & 1][idx + c], N::add(N::ld(acc[(ez + 1) & 1][idx + c]), v[c][a + 4]));
+            }
+          }
+          __syncwarp();
+        }
+        __syncthreads();
+      }
     }
     if (ez >= k0) write_plane(ez);
   }
   if (s_hi + 1 == g.nz && g.nz >= k0 && g.nz < k1) write_plane(g.nz);
 }
 
-template <int PHYS, class N, int EX, int EY, int MINB>
+template <int PHYS, class N, int EX, int EY, int MINB, int NR = 1>
 __global__ void __launch_bounds__(EX *EY, MINB) tile_apply(TileArgs g, const typename N::IO *__restrict__ x,
                                                            typename N::IO *__restrict__ y,
                                                            const int *__restrict__ skip) {
-  __shared__ TileSmem<PHYS, N, EX, EY> sm;
+  extern __shared__ __align__(16) unsigned char tile_smem_raw[];
+  auto &sm = *reinterpret_cast<TileSmem<PHYS, N, EX, EY, NR> *>(tile_smem_raw);
   if (skip && *skip) return;
-  tile_item<PHYS, N, EX, EY>(g, blockIdx.x, x, y, sm);
+  tile_item<PHYS, N, EX, EY, false, NR>(g, blockIdx.x, x, y, sm);
 }
 
 // Tile shapes (elements per slab row x rows) and minimum resident CTAs per SM.
@@ -386,6 +432,8 @@ inline TileArgs make_tile_args(const mf_mesh *m, int EX, int EY, int seg) {
   g.ihz = m->tp_axis + n + m->nx + m->ny;
   g.mat = m->mat_pairs;
   g.dmask = m->dmask;
+  g.nrhs = 1;
+  g.r0 = 0;
   return g;
 }
 

@@ -1,0 +1,121 @@
+"""Learned preconditioner workflow: training pairs from the FP64 CG solver, training of the network
+on the GPU with the library's own kernels, and flexible CG with the trained network.
+
+Training pairs (residual, error): for a seeded random exact solution x*, the right-hand side is
+b = A x*; the FP64 (Jacobi-preconditioned) CG solver is run for k iterations (k drawn per pair),
+and the pair is the residual r_k = b - A x_k and the error e_k = x* - x_k, which satisfy A e_k = r_k
+exactly.  The network learns D^{-1/2} r -> D^{1/2} e in the symmetrically scaled variables (see
+generate_pairs); the solver uses it as the smooth-error correction between damped-Jacobi
+smoothing steps of a two-level preconditioner inside flexible CG.
+
+The network is trained on random crops of (4m+1)^3 nodes (cheaper per step; the convolutions are
+local) and its parameters are then copied into a network created for the full node grid.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import mf
+
+
+def node_logk(p) -> np.ndarray:
+    """Mean of log kappa over the cells touching each node (structured box)."""
+    nx, ny, nz = p.nx, p.ny, p.nz
+    lk = np.log(p.mat).reshape(nz, ny, nx)
+    pad = np.pad(lk, 1, mode="constant")
+    cnt = np.pad(np.ones_like(lk), 1, mode="constant")
+    s = np.zeros((nz + 1, ny + 1, nx + 1))
+    c = np.zeros_like(s)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                s += pad[dz:dz + nz + 1, dy:dy + ny + 1, dx:dx + nx + 1]
+                c += cnt[dz:dz + nz + 1, dy:dy + ny + 1, dx:dx + nx + 1]
+    return (s / c).reshape(-1).astype(np.float32)
+
+
+def generate_pairs(mesh: mf.Mesh, p, n_pairs: int, seed: int = 0, k_range=(2, 150), smooth: int = 2):
+    """Training pairs on the device (float32 [n_pairs][n_nodes] each) and the output scale c.
+
+    For a seeded random exact solution x*, b = A x* and the FP64 Jacobi-preconditioned CG solver
+    runs k iterations (k log-uniform in k_range); with r = b - A x_k, e = x* - x_k and D = diag(A) the
+    pair is input D^{-1/2} r / s and target D^{1/2} e c / s, s = RMS(D^{-1/2} r) (the symmetrically
+    scaled system's residual and error).  c makes the targets O(1)."""
+    rng = np.random.default_rng(seed)
+    n = p.n_dof
+    dmask = torch.from_numpy(p.dirichlet.astype(bool)).cuda()
+    diag = torch.empty(n, dtype=torch.float64, device="cuda")
+    mf.mf_operator_diagonal(mesh, diag)
+    sq = torch.sqrt(diag)
+    R = torch.empty(n_pairs, n, dtype=torch.float32, device="cuda")
+    T = torch.empty(n_pairs, n, dtype=torch.float32, device="cuda")
+    ratios = []
+    nzyx = (p.nz + 1, p.ny + 1, p.nx + 1)
+    for i in range(n_pairs):
+        xs = torch.from_numpy(rng.normal(size=nzyx)).cuda()
+        for _ in range(int(rng.integers(0, smooth + 1))):
+            xs = (xs + torch.roll(xs, 1, 0) + torch.roll(xs, -1, 0) + torch.roll(xs, 1, 1) + torch.roll(xs, -1, 1)
+                  + torch.roll(xs, 1, 2) + torch.roll(xs, -1, 2)) / 7.0
+        xs = xs.reshape(-1).contiguous()
+        xs[dmask] = 0.0
+        b = mesh.apply(xs)
+        k = int(math.exp(rng.uniform(math.log(k_range[0]), math.log(k_range[1]))))
+        xk, _ = mesh.cg(b, max_iter=k, rtol=1e-14, check_every=min(k, 32), precond=mf.MF_PC_JACOBI)
+        r = (b - mesh.apply(xk)) / sq
+        e = (xs - xk) * sq
+        r[dmask] = 0.0
+        e[dmask] = 0.0
+        s = torch.sqrt(torch.mean(r * r)).item()
+        ratios.append(s / max(torch.sqrt(torch.mean(e * e)).item(), 1e-300))
+        R[i] = (r / s).float()
+        T[i] = (e / s).float()
+    c = float(np.median(ratios))
+    T *= c
+    return R, T, c
+
+
+def _crop(t, nzyx, origin, size):
+    z0, y0, x0 = origin
+    return t.view(*nzyx)[z0:z0 + size, y0:y0 + size, x0:x0 + size].contiguous().view(-1)
+
+
+def train(R, E, logk, nzyx, crop: int = 33, steps: int = 2000, lr: float = 5e-4, seed: int = 0, log_every: int = 0,
+          warmup: int = 100):
+    """Train a network on random crops of `crop`^3 nodes (the full grid when `crop` equals its size)
+    with Adam, linear warm-up over `warmup` steps and cosine decay; returns (params, loss history,
+    seconds)."""
+    assert (crop - 1) % 4 == 0
+    rng = np.random.default_rng(seed)
+    net = mf.Net(crop, crop, crop, seed=seed)
+    lk = torch.from_numpy(logk).cuda() if isinstance(logk, np.ndarray) else logk
+    hist = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(steps):
+        i = int(rng.integers(0, R.shape[0]))
+        origin = [int(rng.integers(0, (d - crop) // 4 + 1)) * 4 for d in nzyx]
+        r = _crop(R[i], nzyx, origin, crop)
+        k = _crop(lk, nzyx, origin, crop)
+        e = _crop(E[i], nzyx, origin, crop)
+        step_lr = lr * min(1.0, (s + 1) / max(warmup, 1)) * (0.5 * (1 + math.cos(math.pi * s / steps)))
+        loss = net.train_step(r, k, e, step_lr)
+        hist.append(loss)
+        if log_every and s % log_every == 0:
+            print(f"step {s} loss {loss:.4f}")
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    params = net.params()
+    net.close()
+    return params, hist, secs
+
+
+def make_inference_net(params, nzyx, out_scale: float) -> mf.Net:
+    nz, ny, nx = nzyx
+    net = mf.Net(nx, ny, nz, seed=0)
+    net.set_params(params)
+    net.set_output_scale(out_scale)
+    return net

@@ -25,7 +25,7 @@ MF_LAPLACE, MF_ELASTICITY = 0, 1
 MF_VARIANT_AUTO, MF_VARIANT_REFERENCE = 0, 1
 MF_OP_MATFREE, MF_OP_CSR = 0, 1
 MF_PREC_FP64, MF_PREC_MIXED_IR = 0, 1
-MF_PC_NONE, MF_PC_JACOBI = 0, 1
+MF_PC_NONE, MF_PC_JACOBI, MF_PC_LEARNED = 0, 1, 2
 
 STATUS_NAMES = {0: "MF_OK", 1: "MF_NOT_CONVERGED", -1: "MF_ERR_ARG", -2: "MF_ERR_CUDA", -3: "MF_ERR_MESH",
                 -4: "MF_ERR_OOM", -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_UNSUPPORTED"}
@@ -37,7 +37,7 @@ i32, i64, f64 = C.c_int32, C.c_int64, C.c_double
 class mf_solve_opts(C.Structure):
     _fields_ = [("op", i32), ("precision", i32), ("precond", i32), ("max_iter", i32), ("rtol", f64),
                 ("check_every", i32), ("use_graph", i32), ("timeout_s", f64), ("inner_rtol", f64),
-                ("max_outer", i32), ("csr", vp)]
+                ("max_outer", i32), ("csr", vp), ("net", vp)]
 
 
 class mf_solve_info(C.Structure):
@@ -69,6 +69,22 @@ _SIGS = {
     "mf_cg_solve_batched": (C.c_int, [C.POINTER(vp), i32, C.POINTER(mf_solve_opts), C.POINTER(vp), C.POINTER(vp),
                                       C.POINTER(mf_solve_info), vp]),
     "mf_set_tile_segment": (C.c_int, [vp, i32]),
+    "mf_net_create": (C.c_int, [i32, i32, i32, C.c_uint64, C.POINTER(vp)]),
+    "mf_net_destroy": (C.c_int, [vp]),
+    "mf_net_num_params": (i64, [vp]),
+    "mf_net_get_params": (C.c_int, [vp, vp]),
+    "mf_net_set_params": (C.c_int, [vp, vp]),
+    "mf_net_set_output_scale": (C.c_int, [vp, C.c_float]),
+    "mf_net_forward": (C.c_int, [vp, vp, vp, vp, vp]),
+    "mf_net_train_step": (C.c_int, [vp, vp, vp, vp, C.c_float, C.POINTER(C.c_float), vp]),
+    "mf_net_gradients": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(C.c_float), vp]),
+    "mf_conv3d_fwd": (C.c_int, [vp, i32, i32, i32, i32, vp, vp, i32, vp, i32, vp, vp, vp]),
+    "mf_conv3d_dgrad": (C.c_int, [vp, i32, i32, i32, i32, vp, i32, vp, vp, vp]),
+    "mf_conv3d_wgrad_workspace": (i64, [i32, i32, i32, i32, i32]),
+    "mf_conv3d_wgrad": (C.c_int, [vp, vp, i32, i32, i32, i32, i32, vp, vp, vp, i64, vp]),
+    "mf_grid_restrict": (C.c_int, [vp, i32, i32, i32, i32, vp, C.c_float, vp]),
+    "mf_grid_prolong": (C.c_int, [vp, i32, i32, i32, i32, vp, C.c_float, vp]),
+    "mf_operator_diagonal": (C.c_int, [vp, vp, vp]),
     "mf_kernel_launches": (i64, []),
     "mf_last_error": (C.c_char_p, []),
     "mf_version": (C.c_char_p, []),
@@ -241,6 +257,114 @@ def mf_set_tile_segment(h, seg: int) -> None:
     check(lib.mf_set_tile_segment(h.h if isinstance(h, Mesh) else h, seg), "mf_set_tile_segment")
 
 
+# ------------------------------------------------------------------ learned preconditioner ----
+
+def _bf16_ptr(t):
+    if t is None:
+        return None
+    assert t.dtype == torch.bfloat16
+    return _ptr(t)
+
+
+def mf_conv3d_fwd(x, w, bias, cout, skip=None, relu=False, y_bf16=None, y_f32=None, stream=None):
+    nz, ny, nx, cin = x.shape
+    check(lib.mf_conv3d_fwd(_bf16_ptr(x), nx, ny, nz, cin, _bf16_ptr(w), _ptr(bias), cout, _bf16_ptr(skip),
+                            int(relu), _bf16_ptr(y_bf16), _ptr(y_f32), _stream(stream)), "mf_conv3d_fwd")
+
+
+def mf_conv3d_dgrad(dy, w, cin, dx_bf16=None, dx_f32=None, stream=None):
+    nz, ny, nx, cout = dy.shape
+    check(lib.mf_conv3d_dgrad(_bf16_ptr(dy), nx, ny, nz, cin, _bf16_ptr(w), cout, _bf16_ptr(dx_bf16), _ptr(dx_f32),
+                              _stream(stream)), "mf_conv3d_dgrad")
+
+
+def mf_conv3d_wgrad(x, dy, stream=None):
+    nz, ny, nx, cin = x.shape
+    cout = dy.shape[3]
+    nbytes = int(lib.mf_conv3d_wgrad_workspace(nx, ny, nz, cin, cout))
+    ws = torch.empty(nbytes // 4 + 1, dtype=torch.float32, device=x.device)
+    dw = torch.empty(27, cin, cout, dtype=torch.float32, device=x.device)
+    db = torch.empty(cout, dtype=torch.float32, device=x.device)
+    check(lib.mf_conv3d_wgrad(_bf16_ptr(x), _bf16_ptr(dy), nx, ny, nz, cin, cout, _ptr(dw), _ptr(db), _ptr(ws), nbytes,
+                              _stream(stream)), "mf_conv3d_wgrad")
+    return dw, db
+
+
+def mf_grid_restrict(x, scale=1.0, stream=None):
+    nz, ny, nx, c = x.shape
+    out = torch.empty((nz + 1) // 2, (ny + 1) // 2, (nx + 1) // 2, c, dtype=x.dtype, device=x.device)
+    check(lib.mf_grid_restrict(_bf16_ptr(x), nx, ny, nz, c, _bf16_ptr(out), scale, _stream(stream)), "mf_grid_restrict")
+    return out
+
+
+def mf_grid_prolong(x, scale=1.0, stream=None):
+    nz, ny, nx, c = x.shape
+    out = torch.empty(2 * nz - 1, 2 * ny - 1, 2 * nx - 1, c, dtype=x.dtype, device=x.device)
+    check(lib.mf_grid_prolong(_bf16_ptr(x), nx, ny, nz, c, _bf16_ptr(out), scale, _stream(stream)), "mf_grid_prolong")
+    return out
+
+
+class Net:
+    """Owner of an ``mf_net`` (the learned preconditioner) for a node grid (nx, ny, nz)."""
+
+    def __init__(self, nx, ny, nz, seed=0):
+        h = vp()
+        check(lib.mf_net_create(nx, ny, nz, seed, C.byref(h)), "mf_net_create")
+        self.h = h.value
+        self.dims = (nx, ny, nz)
+        self.n_params = int(lib.mf_net_num_params(self.h))
+
+    def params(self):
+        import numpy as np
+        out = np.empty(self.n_params, dtype=np.float32)
+        check(lib.mf_net_get_params(self.h, out.ctypes.data), "mf_net_get_params")
+        return out
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        check(lib.mf_net_set_params(self.h, p.ctypes.data), "mf_net_set_params")
+
+    def set_output_scale(self, s):
+        check(lib.mf_net_set_output_scale(self.h, float(s)), "mf_net_set_output_scale")
+
+    def forward(self, r, logk, out=None, stream=None):
+        if out is None:
+            out = torch.empty_like(r)
+        check(lib.mf_net_forward(self.h, _ptr(r), _ptr(logk), _ptr(out), _stream(stream)), "mf_net_forward")
+        return out
+
+    def train_step(self, r, logk, target, lr, stream=None):
+        loss = C.c_float()
+        check(lib.mf_net_train_step(self.h, _ptr(r), _ptr(logk), _ptr(target), float(lr), C.byref(loss),
+                                    _stream(stream)), "mf_net_train_step")
+        return loss.value
+
+    def gradients(self, r, logk, target, stream=None):
+        import numpy as np
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = C.c_float()
+        check(lib.mf_net_gradients(self.h, _ptr(r), _ptr(logk), _ptr(target), g.ctypes.data, C.byref(loss),
+                                   _stream(stream)), "mf_net_gradients")
+        return loss.value, g
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(lib.mf_net_destroy(self.h), "mf_net_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mf_operator_diagonal(h, diag, stream=None) -> None:
+    check(lib.mf_operator_diagonal(h.h if isinstance(h, Mesh) else h, _ptr(diag), _stream(stream)), "mf_operator_diagonal")
+
+
 def mf_kernel_launches() -> int:
     return int(lib.mf_kernel_launches())
 
@@ -308,6 +432,10 @@ class Mesh:
     def cg(self, b, x=None, stream=None, ok=(MF_OK, MF_NOT_CONVERGED), **kw):
         o = mf_solve_opts_default()
         csr = kw.pop("csr", None)
+        net = kw.pop("net", None)
+        if net is not None:
+            o.net = net.h
+            o.precond = MF_PC_LEARNED
         for k, v in kw.items():
             setattr(o, k, v)
         if csr is not None:

@@ -1,0 +1,159 @@
+"""BF16 tensor-core network kernels and the network runtime against the oracle (oracle/conv.py,
+oracle/net.py).  Inputs are BF16-representable; the oracle accumulates in float64, the kernels in
+FP32, so FP32 outputs agree to ~1e-5 relative and BF16 outputs to a BF16 rounding."""
+import numpy as np
+import pytest
+
+from oracle import conv, net as onet
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+from paper_2308_09839_gb300 import mf  # noqa: E402
+
+
+def bf(a):
+    return torch.from_numpy(conv.bf16_round(a)).to(torch.bfloat16).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+SHAPES = [((5, 7, 9), 2, 16), ((4, 4, 8), 16, 16), ((9, 6, 11), 16, 32), ((5, 5, 5), 32, 64),
+          ((3, 9, 10), 64, 64), ((6, 5, 7), 64, 32), ((7, 7, 7), 32, 16), ((9, 9, 9), 16, 1), ((4, 5, 3), 3, 5)]
+
+
+@pytest.mark.parametrize("dims,cin,cout", SHAPES)
+def test_conv_fwd_matches_oracle(dims, cin, cout):
+    rng = np.random.default_rng(cin * 100 + cout)
+    nz, ny, nx = dims
+    x = conv.bf16_round(rng.normal(size=(nz, ny, nx, cin)))
+    w = conv.bf16_round(rng.normal(size=(27, cin, cout)) / np.sqrt(27 * cin))
+    b = rng.normal(size=cout).astype(np.float32)
+    skip = conv.bf16_round(rng.normal(size=(nz, ny, nx, cout)))
+    ref = conv.conv3d(x, w, b) + skip
+    y = torch.empty(nz, ny, nx, cout, dtype=torch.float32, device="cuda")
+    mf.mf_conv3d_fwd(bf(x), bf(w), torch.from_numpy(b).cuda(), cout, skip=bf(skip), y_f32=y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), ref) < 1e-5
+    yb = torch.empty(nz, ny, nx, cout, dtype=torch.bfloat16, device="cuda")
+    mf.mf_conv3d_fwd(bf(x), bf(w), torch.from_numpy(b).cuda(), cout, relu=True, y_bf16=yb)
+    torch.cuda.synchronize()
+    refr = np.maximum(conv.conv3d(x, w, b), 0)
+    got = yb.float().cpu().numpy()
+    assert np.all(np.abs(got - refr) <= 2 ** -8 * np.abs(refr) + 1e-6)
+
+
+@pytest.mark.parametrize("dims,cin,cout", SHAPES)
+def test_conv_dgrad_matches_oracle(dims, cin, cout):
+    rng = np.random.default_rng(7 + cin + cout)
+    nz, ny, nx = dims
+    dy = conv.bf16_round(rng.normal(size=(nz, ny, nx, cout)))
+    w = conv.bf16_round(rng.normal(size=(27, cin, cout)) / np.sqrt(27 * cout))
+    dx = torch.empty(nz, ny, nx, cin, dtype=torch.float32, device="cuda")
+    mf.mf_conv3d_dgrad(bf(dy), bf(w), cin, dx_f32=dx)
+    torch.cuda.synchronize()
+    assert rel(dx.cpu().numpy(), conv.conv3d_dgrad(dy, w)) < 1e-5
+
+
+@pytest.mark.parametrize("dims,cin,cout", SHAPES)
+def test_conv_wgrad_matches_oracle(dims, cin, cout):
+    rng = np.random.default_rng(11 + cin + cout)
+    nz, ny, nx = dims
+    x = conv.bf16_round(rng.normal(size=(nz, ny, nx, cin)))
+    dy = conv.bf16_round(rng.normal(size=(nz, ny, nx, cout)))
+    dw, db = mf.mf_conv3d_wgrad(bf(x), bf(dy))
+    torch.cuda.synchronize()
+    rdw, rdb = conv.conv3d_wgrad(x, dy)
+    assert rel(dw.cpu().numpy(), rdw) < 1e-5
+    assert rel(db.cpu().numpy(), rdb) < 1e-5
+
+
+def test_grid_transfers_match_oracle():
+    rng = np.random.default_rng(3)
+    xf = conv.bf16_round(rng.normal(size=(9, 5, 7, 4)))
+    xc = conv.bf16_round(rng.normal(size=(3, 5, 4, 4)))
+    r = mf.mf_grid_restrict(bf(xf), scale=2.0)
+    p = mf.mf_grid_prolong(bf(xc), scale=0.5)
+    torch.cuda.synchronize()
+    rr, pr = 2.0 * conv.restrict(xf), 0.5 * conv.prolong(xc)
+    assert np.all(np.abs(r.float().cpu().numpy() - rr) <= 2 ** -8 * np.abs(rr) + 1e-6)
+    assert np.all(np.abs(p.float().cpu().numpy() - pr) <= 2 ** -8 * np.abs(pr) + 1e-6)
+
+
+def _net_case(dims=(9, 13, 17), seed=0):
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    inp = rng.normal(size=(nz, ny, nx, 2)).astype(np.float32)
+    tgt = rng.normal(size=(nz, ny, nx)).astype(np.float32)
+    return inp, tgt
+
+
+def test_network_forward_and_gradient_match_oracle():
+    dims = (9, 13, 17)
+    nt = mf.Net(*dims, seed=5)
+    p = nt.params()
+    assert p.size == onet.num_params()
+    inp, tgt = _net_case(dims)
+    r = torch.from_numpy(np.ascontiguousarray(inp[..., 0]).reshape(-1)).cuda()
+    k = torch.from_numpy(np.ascontiguousarray(inp[..., 1]).reshape(-1)).cuda()
+    t = torch.from_numpy(tgt.reshape(-1)).cuda()
+    out = nt.forward(r, k)
+    loss, g = nt.gradients(r, k, t)
+    torch.cuda.synchronize()
+    rloss, rg, rout = onet.loss_and_grad(p.astype(np.float64), inp, tgt, bf16=True)
+    assert rel(out.cpu().numpy().reshape(rout.shape), rout) < 2e-2
+    assert abs(loss - rloss) <= 2e-2 * abs(rloss)
+    # per-layer gradient agreement (BF16 activations and gradients on both sides)
+    off = 0
+    for (_, ci, co, _) in onet.LAYERS:
+        n = 27 * ci * co + co
+        assert rel(g[off:off + n], rg[off:off + n]) < 5e-2, (ci, co)
+        off += n
+
+
+def test_network_training_reduces_loss_and_is_deterministic():
+    dims = (9, 9, 9)
+    inp, tgt = _net_case(dims, seed=1)
+    r = torch.from_numpy(np.ascontiguousarray(inp[..., 0]).reshape(-1)).cuda()
+    k = torch.from_numpy(np.ascontiguousarray(inp[..., 1]).reshape(-1)).cuda()
+    # a learnable target: a smoothed copy of the input residual
+    t = torch.from_numpy(conv.conv3d(inp[..., :1], np.full((27, 1, 1), 1.0 / 27))[..., 0].astype(np.float32).reshape(-1)).cuda()
+    losses = []
+    for rep in range(2):
+        nt = mf.Net(*dims, seed=3)
+        ls = [nt.train_step(r, k, t, 3e-3) for _ in range(60)]
+        losses.append(ls)
+        params = nt.params()
+        if rep == 0:
+            p0 = params
+    assert losses[0][-1] < 0.5 * losses[0][0]
+    assert losses[0] == losses[1]
+    assert np.array_equal(p0, params)
+
+
+def test_learned_preconditioner_gains_over_jacobi_pcg():
+    """Train on CG-generated pairs of a 32^3-cell GRF Laplace problem and use the network in
+    flexible CG: it must reach the FP64 tolerance (true residual) and take fewer iterations than
+    Jacobi-PCG (and so than plain CG).  (The wall-time comparison is reported by the benchmark.)"""
+    from paper_2308_09839_gb300 import inputs, learned
+    p = inputs.grf_laplace_128(seed=0, n=32)
+    mesh = mf.Mesh.from_problem(p)
+    nzyx = (p.nz + 1, p.ny + 1, p.nx + 1)
+    R, E, c = learned.generate_pairs(mesh, p, 64, seed=1, k_range=(2, 60))
+    lk = learned.node_logk(p)
+    params, hist, secs = learned.train(R, E, lk, nzyx, crop=33, steps=1500, lr=5e-4)
+    assert np.mean(hist[-50:]) < 0.7 * np.mean(hist[:20])
+    net = learned.make_inference_net(params, nzyx, c)
+    b = torch.from_numpy(p.b()).cuda()
+    x_cg, i_cg = mesh.cg(b)
+    x_j, i_j = mesh.cg(b, precond=mf.MF_PC_JACOBI)
+    x_nn, i_nn = mesh.cg(b, net=net)
+    torch.cuda.synchronize()
+    assert i_nn.status == mf.MF_OK and i_nn.rel_res_true <= 1.05e-8
+    print(f"plain CG {i_cg.iters} it, Jacobi-PCG {i_j.iters} it, learned FCG {i_nn.iters} it "
+          f"(switched off at {i_nn.outer_iters})")
+    assert i_nn.iters < i_j.iters < i_cg.iters

@@ -390,3 +390,55 @@ def test_mixed_ir_auto_variant():
     x, info = mesh.cg(gpu(b), precision=mf.MF_PREC_MIXED_IR, rtol=1e-10)
     assert info.status == mf.MF_OK and info.rel_res_true <= 1.05e-10
     assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.05e-10 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+@pytest.mark.parametrize("nrhs", [1, 3, 4, 5, 16])
+def test_tile_apply_multi_rhs(physics, nrhs):
+    """Multi right-hand-side tile apply ([node][rhs][comp]) equals the single applies bitwise and the
+    oracle to 1e-12."""
+    mk = inputs.laplace_box if physics == "laplace" else inputs.elasticity_box
+    p = mk(11, ny=9, nz=13, graded=0.4, seed=nrhs)
+    mesh = mf.Mesh.from_problem(p)
+    nd = p.ndpn
+    xs = [p.x(seed=s) for s in range(nrhs)]
+    X = np.stack([x.reshape(-1, nd) for x in xs], axis=1).reshape(-1)
+    Y = mesh.apply_multi(gpu(X), nrhs)
+    torch.cuda.synchronize()
+    Y = Y.cpu().numpy().reshape(p.n_nodes, nrhs, nd)
+    for r in range(nrhs):
+        single = gpu_apply(mesh, xs[r])
+        assert np.array_equal(Y[:, r, :].reshape(-1), single)
+        assert rel2(single, oracle_apply(p, xs[r])) <= TOL64
+
+
+def _warped(n, seed):
+    """A smoothly warped structured box (not a tensor-product grid, large offsets from the axis lines)."""
+    p = inputs.laplace_box(n, ny=n - 1, nz=n + 1, jitter=0.1, seed=seed)
+    X = p.coords.copy()
+    x, y, z = X[:, 0].copy(), X[:, 1].copy(), X[:, 2].copy()
+    X[:, 0] = x + 0.08 * np.sin(np.pi * y) * z
+    X[:, 1] = y + 0.05 * x * z
+    X[:, 2] = z + 0.06 * np.sin(np.pi * x) * y
+    return p, X
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+def test_general_kernel_on_warped_mesh(physics):
+    """Structured but curved mesh: the general (per-Gauss-point Jacobian) double-word kernel."""
+    p, X = _warped(9, 3)
+    if physics == "elasticity":
+        q = inputs.elasticity_box(9, ny=8, nz=10, seed=3)
+        mat = q.mat
+    else:
+        mat = p.mat
+    cells = p.cell_array()
+    nd = 1 if physics == "laplace" else 3
+    mesh = mf.Mesh(physics, gpu(X), gpu(np.ascontiguousarray(mat)), gpu(p.dirichlet), None, (p.nx, p.ny, p.nz))
+    assert not mesh.info["tensor_product"]
+    x = inputs.uniform_vector(p.n_nodes * nd, 4, dirichlet_dofs=np.nonzero(np.repeat(p.dirichlet, nd))[0])
+    y = gpu_apply(mesh, x)
+    ref = fem.apply(physics, X, cells, mat, p.dirichlet, x)
+    assert rel2(y, ref) <= TOL64
+    mesh.set_variant(mf.MF_VARIANT_REFERENCE)
+    assert rel2(gpu_apply(mesh, x), ref) <= TOL64
