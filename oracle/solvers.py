@@ -6,6 +6,8 @@
 * ``pcg``  the same with a fixed preconditioner z = M(r) (Jacobi when M = diag(A)^-1).
 * ``fcg``  flexible CG for a preconditioner that may change between iterations (a network):
            beta_k = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k)  (Polak-Ribiere form, Notay 2000).
+* ``fcg_m``  truncated flexible CG, FCG(m) (Notay 2000): each new direction is the preconditioned
+           residual A-orthogonalised against the last m directions.
 * ``iterative_refinement``  x += solve_inner(b - A x) until the FP64 residual meets the tolerance.
 
 Readings: x0 = 0; stop when ||r_k||_2 <= rtol ||b||_2 (the paper gives no stopping norm); the
@@ -94,6 +96,37 @@ def fcg(apply, b, precond, rtol=1e-8, max_iter=100000):
         k += 1
         hist.append(float(np.linalg.norm(r)) / bn)
     return x, k, hist
+
+
+def fcg_m(apply, b, precond, m=8, rtol=1e-8, max_iter=100000, keep_directions=False):
+    """Truncated flexible CG, FCG(m): z_k = M(r_k); p_k = z_k - sum over the last m directions j of
+    (z_k . A p_j) / (p_j . A p_j) p_j; alpha_k = (p_k . r_k) / (p_k . A p_k); x += alpha_k p_k and
+    r -= alpha_k A p_k.  Returns (x, iterations, residual history[, all (p, Ap) pairs])."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    bn = float(np.linalg.norm(b))
+    stored = []  # (p_j, A p_j, p_j . A p_j), oldest first
+    allpairs = []
+    k = 0
+    hist = [1.0]
+    while k < max_iter and np.linalg.norm(r) > rtol * bn:
+        z = precond(r)
+        p = z.copy()
+        for pj, apj, dj in stored:
+            p -= float(np.dot(z, apj)) / dj * pj
+        Ap = apply(p)
+        pAp = float(np.dot(p, Ap))
+        alpha = float(np.dot(p, r)) / pAp
+        x += alpha * p
+        r -= alpha * Ap
+        stored.append((p, Ap, pAp))
+        if len(stored) > m:
+            stored.pop(0)
+        if keep_directions:
+            allpairs.append((p, Ap))
+        k += 1
+        hist.append(float(np.linalg.norm(r)) / bn)
+    return (x, k, hist, allpairs) if keep_directions else (x, k, hist)
 
 
 def iterative_refinement(apply64, inner_solve, b, rtol=1e-10, max_outer=50):

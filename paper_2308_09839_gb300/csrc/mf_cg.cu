@@ -436,27 +436,55 @@ __global__ void inv_sqrt_kernel(int64_t n, double *d) {
   GRID_STRIDE(i, n) d[i] = 1.0 / sqrt(d[i]);
 }
 
-// x += alpha p; rprev = r; r -= alpha Ap   (alpha = dev[0] / dev[1])
-__global__ void fcg_update_xr(int64_t n, double *x, double *r, double *rprev, const double *p, const double *Ap,
-                              const double *num, const double *den) {
-  const double alpha = *num / *den;
+// Truncated flexible CG keeps the last kFcgM search directions and their images under A.
+constexpr int kFcgM = 8;
+
+struct DirSet {
+  const double *v[kFcgM];  // the stored directions (or their images) taking part, cnt of them
+  int idx[kFcgM];          // their ring slots (for the stored p.Ap)
+  int cnt;
+};
+
+// out[j] = z . v_j for the cnt vectors of `vs` (one pass over z)
+__global__ void __launch_bounds__(kRedThreads) multi_dot(int64_t n, const double *z, DirSet vs, double *partials,
+                                                         CgScalars *sc, double *out) {
+  double v[kFcgM];
+#pragma unroll
+  for (int j = 0; j < kFcgM; ++j) v[j] = 0.0;
   GRID_STRIDE(i, n) {
-    x[i] += alpha * p[i];
-    const double ri = r[i];
-    rprev[i] = ri;
-    r[i] = ri - alpha * Ap[i];
+    const double zi = z[i];
+#pragma unroll
+    for (int j = 0; j < kFcgM; ++j)
+      if (j < vs.cnt) v[j] += zi * vs.v[j][i];
+  }
+  double o[kFcgM];
+  if (grid_reduce<kFcgM>(v, partials, &sc->ticket, o) && threadIdx.x == 0)
+    for (int j = 0; j < vs.cnt; ++j) out[j] = o[j];
+}
+
+// p = z - sum_j (zAp_j / pAp_j) p_j   (A-orthogonalisation against the stored directions)
+__global__ void orthogonalise(int64_t n, const double *z, DirSet ps, const double *zAp, const double *pAp, double *p) {
+  double c[kFcgM];
+#pragma unroll
+  for (int j = 0; j < kFcgM; ++j) c[j] = j < ps.cnt ? zAp[j] / pAp[ps.idx[j]] : 0.0;
+  GRID_STRIDE(i, n) {
+    double s = z[i];
+#pragma unroll
+    for (int j = 0; j < kFcgM; ++j)
+      if (j < ps.cnt) s -= c[j] * ps.v[j][i];
+    p[i] = s;
   }
 }
 
-// diff = r - rprev (into rprev)
-__global__ void sub_inplace(int64_t n, const double *r, double *rprev) {
-  GRID_STRIDE(i, n) rprev[i] = r[i] - rprev[i];
-}
-
-// p = z + beta p, beta = num / den
-__global__ void fcg_update_p(int64_t n, const double *z, double *p, const double *num, const double *den) {
-  const double beta = *num / *den;
-  GRID_STRIDE(i, n) p[i] = z[i] + beta * p[i];
+// alpha = (p.r) / (p.Ap); x += alpha p; r -= alpha Ap; pAp is kept for later orthogonalisations
+__global__ void fcg_update_xr(int64_t n, double *x, double *r, const double *p, const double *Ap,
+                              const double *pAp_pr, double *pAp_keep) {
+  const double alpha = pAp_pr[1] / pAp_pr[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *pAp_keep = pAp_pr[0];
+  GRID_STRIDE(i, n) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * Ap[i];
+  }
 }
 
 // node field of log(kappa): mean of log kappa over the cells touching each node (structured box)
@@ -479,7 +507,7 @@ __global__ void node_logk(const double *kappa, int nx, int ny, int nz, float *ou
 }
 
 struct FcgBufs {
-  double *z, *rprev, *dev, *isd, *t, *r1, *cn;  // dev: scalars [0..7]; isd = D^{-1/2}; cn: correction
+  double *z, *dev, *isd, *t, *r1, *cn, *P, *AP, *pAp, *part;  // P, AP: kFcgM stored directions and images
   float *rf, *zf, *logk;
 };
 
@@ -495,20 +523,35 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
   CgWorkspace *w = m->cg;
   const int64_t n = m->n_dof;
   FcgBufs f{};
-  MF_CUDA(cudaMalloc(&f.z, n * sizeof(double)));
-  MF_CUDA(cudaMalloc(&f.rprev, n * sizeof(double)));
-  MF_CUDA(cudaMalloc(&f.dev, 8 * sizeof(double)));
-  MF_CUDA(cudaMalloc(&f.rf, n * sizeof(float)));
-  MF_CUDA(cudaMalloc(&f.zf, n * sizeof(float)));
-  MF_CUDA(cudaMalloc(&f.logk, n * sizeof(float)));
-  MF_CUDA(cudaMalloc(&f.isd, n * sizeof(double)));
-  MF_CUDA(cudaMalloc(&f.t, n * sizeof(double)));
-  MF_CUDA(cudaMalloc(&f.r1, n * sizeof(double)));
-  MF_CUDA(cudaMalloc(&f.cn, n * sizeof(double)));
   auto release = [&]() {
-    cudaFree(f.z); cudaFree(f.rprev); cudaFree(f.dev); cudaFree(f.rf); cudaFree(f.zf); cudaFree(f.logk);
-    cudaFree(f.isd); cudaFree(f.t); cudaFree(f.r1); cudaFree(f.cn);
+    cudaFree(f.z); cudaFree(f.dev); cudaFree(f.rf); cudaFree(f.zf); cudaFree(f.logk); cudaFree(f.isd);
+    cudaFree(f.t); cudaFree(f.r1); cudaFree(f.cn); cudaFree(f.P); cudaFree(f.AP); cudaFree(f.pAp); cudaFree(f.part);
   };
+  {
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](auto **ptr, size_t bytes) {
+      if (e == cudaSuccess) e = cudaMalloc((void **)ptr, bytes);
+    };
+    alloc(&f.z, n * sizeof(double));
+    alloc(&f.dev, 32 * sizeof(double));
+    alloc(&f.rf, n * sizeof(float));
+    alloc(&f.zf, n * sizeof(float));
+    alloc(&f.logk, n * sizeof(float));
+    alloc(&f.isd, n * sizeof(double));
+    alloc(&f.t, n * sizeof(double));
+    alloc(&f.r1, n * sizeof(double));
+    alloc(&f.cn, n * sizeof(double));
+    alloc(&f.P, (size_t)kFcgM * n * sizeof(double));
+    alloc(&f.AP, (size_t)kFcgM * n * sizeof(double));
+    alloc(&f.pAp, kFcgM * sizeof(double));
+    alloc(&f.part, (size_t)kFcgM * kRedBlocks * sizeof(double));
+    if (e != cudaSuccess) {
+      release();
+      cudaGetLastError();
+      mf_set_error("mf_cg_solve: out of device memory for the flexible CG workspace");
+      return MF_ERR_OOM;
+    }
+  }
   mf_count_launches(2);
   node_logk<<<blocks_for(n), kThreads, 0, s>>>(m->mat, m->nx, m->ny, m->nz, f.logk);
   MF_TRY(operator_diagonal(m, f.isd, s));
@@ -516,13 +559,13 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
   const double c_out = (double)net_out_scale(net);
   bool learned = true;
   int fallback_at = -1;
-  // dev: [0] r.r  [1] r.z (current)  [2] p.Ap  [3] z.(r - rprev)  [4] next r.z  [5] |D^-1/2 r1|^2
-  //      [6] cn.r1  [7] cn.A cn
+  // dev: [0] r.r  [2] p.Ap  [3] p.r  [5] |D^-1/2 r1|^2  [6] cn.r1  [7] cn.A cn  [8..8+kFcgM) z.Ap_j
   auto dot2 = [&](const double *a, const double *bb, const double *c, const double *d, double *out) {
     mf_count_launches(1);
     dot2_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, a, bb, c, d, w->partials, w->sc, out);
   };
   auto precond = [&](const double *r, double *z) -> mf_status {
+    const double omega = 2.0 / 3.0;
     if (!learned) {  // after the switch-off: Jacobi (z = D^-1 r)
       mf_count_launches(1);
       jacobi_step<<<kRedBlocks, kRedThreads, 0, s>>>(n, r, f.isd, 1.0, 0.0, m->dmask, z);
@@ -530,7 +573,6 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
     }
     // two-level form: damped-Jacobi pre-smoothing, network correction of the smoothed residual,
     // damped-Jacobi post-smoothing
-    const double omega = 2.0 / 3.0;
     mf_count_launches(2);
     jacobi_step<<<kRedBlocks, kRedThreads, 0, s>>>(n, r, f.isd, omega, 0.0, m->dmask, z);
     MF_TRY(apply_fp64(m, z, f.t, s));
@@ -548,7 +590,7 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
     jacobi_step<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.r1, f.isd, omega, 1.0, m->dmask, z);
     return MF_OK;
   };
-  double h[8];
+  double h[4];
   mf_status st = MF_OK;
   // x = 0, r = b
   MF_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
@@ -559,22 +601,21 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
   const double bb = h[0];
   const double tol2 = o->rtol * o->rtol * bb;
   double rr = bb, best = bb, window_start = bb;
-  int it = 0, since = 0;
+  int it = 0, since = 0, cnt = 0, slot = 0;  // cnt stored directions, the next goes to `slot`
   const int window = 500;  // the residual norm of CG is not monotone: judge stalls over long windows
   if (!(bb > 0.0)) {
     release();
     if (info) { info->iters = 0; info->status = bb == 0.0 ? MF_OK : MF_ERR_BREAKDOWN; info->rel_res = 0; info->rel_res_true = 0; }
     return bb == 0.0 ? MF_OK : MF_ERR_BREAKDOWN;
   }
-  st = precond(w->r, f.z);
-  if (st != MF_OK) { release(); return st; }
-  MF_CUDA(cudaMemcpyAsync(w->p, f.z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  dot2(w->r, f.z, nullptr, nullptr, f.dev + 1);
+  auto Pv = [&](int j) { return f.P + (size_t)j * n; };
+  auto APv = [&](int j) { return f.AP + (size_t)j * n; };
   // switch the network off and restart as Jacobi-preconditioned CG from the current iterate (from
-  // x = 0 when the iterate is no longer finite): r = b - A x, p = z = D^-1 r
+  // x = 0 when the iterate is no longer finite): r = b - A x, no stored directions
   auto restart_jacobi = [&]() -> mf_status {
     learned = false;
     fallback_at = it;
+    cnt = 0;
     MF_TRY(apply_fp64(m, x, w->Ap, s));
     mf_count_launches(1);
     residual_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->Ap, w->r, w->partials, w->sc);
@@ -584,24 +625,39 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
     if (!std::isfinite(hs.res2)) {
       MF_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
       MF_CUDA(cudaMemcpyAsync(w->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      rr = bb;
+    } else {
+      rr = hs.res2;
     }
-    MF_TRY(precond(w->r, f.z));
-    MF_CUDA(cudaMemcpyAsync(w->p, f.z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    dot2(w->r, w->r, nullptr, nullptr, f.dev + 0);
-    dot2(w->r, f.z, nullptr, nullptr, f.dev + 1);
-    MF_CUDA(cudaMemcpyAsync(h, f.dev, sizeof(double), cudaMemcpyDeviceToHost, s));
-    MF_CUDA(cudaStreamSynchronize(s));
-    rr = h[0];
     return MF_OK;
   };
   while (!(rr <= tol2) && it < o->max_iter) {
-    MF_TRY(apply_fp64(m, w->p, w->Ap, s));
-    dot2(w->p, w->Ap, nullptr, nullptr, f.dev + 2);
+    st = precond(w->r, f.z);
+    if (st != MF_OK) break;
+    // new direction: z A-orthogonalised against the last cnt directions
+    double *p = Pv(slot), *Ap = APv(slot);
+    if (cnt == 0) {
+      MF_CUDA(cudaMemcpyAsync(p, f.z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      DirSet aps{}, ps{};
+      for (int j = 0; j < cnt; ++j) {
+        const int sj = (slot - 1 - j + kFcgM) % kFcgM;
+        aps.v[j] = APv(sj);
+        ps.v[j] = Pv(sj);
+        aps.idx[j] = ps.idx[j] = sj;
+      }
+      aps.cnt = ps.cnt = cnt;
+      mf_count_launches(2);
+      multi_dot<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.z, aps, f.part, w->sc, f.dev + 8);
+      orthogonalise<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.z, ps, f.dev + 8, f.pAp, p);
+    }
+    MF_TRY(apply_fp64(m, p, Ap, s));
+    dot2(p, Ap, p, w->r, f.dev + 2);  // dev[2] = p.Ap, dev[3] = p.r
     mf_count_launches(1);
-    fcg_update_xr<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, w->r, f.rprev, w->p, w->Ap, f.dev + 1, f.dev + 2);
+    fcg_update_xr<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, w->r, p, Ap, f.dev + 2, f.pAp + slot);
     dot2(w->r, w->r, nullptr, nullptr, f.dev + 0);
     ++it;
-    MF_CUDA(cudaMemcpyAsync(h, f.dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaMemcpyAsync(h, f.dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     MF_CUDA(cudaStreamSynchronize(s));
     rr = h[0];
     if (!std::isfinite(rr) || !(h[2] > 0.0)) {
@@ -609,6 +665,8 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
       MF_TRY(restart_jacobi());  // breakdown with the network: Jacobi-PCG from here
       continue;
     }
+    slot = (slot + 1) % kFcgM;
+    cnt = cnt < kFcgM ? cnt + 1 : kFcgM;
     if (rr <= tol2) break;
     if (o->timeout_s > 0 && std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > o->timeout_s) {
       st = MF_ERR_TIMEOUT;
@@ -625,14 +683,6 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
         since = 0;
       }
     }
-    st = precond(w->r, f.z);
-    if (st != MF_OK) break;
-    mf_count_launches(1);
-    sub_inplace<<<kRedBlocks, kRedThreads, 0, s>>>(n, w->r, f.rprev);
-    dot2(f.z, f.rprev, w->r, f.z, f.dev + 3);  // dev[3] = z.(r - rprev), dev[4] = r.z
-    mf_count_launches(2);
-    fcg_update_p<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.z, w->p, f.dev + 3, f.dev + 1);
-    MF_CUDA(cudaMemcpyAsync(f.dev + 1, f.dev + 4, sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   if (st == MF_OK && !(rr <= tol2)) st = std::isfinite(rr) ? MF_NOT_CONVERGED : MF_ERR_BREAKDOWN;
   // true residual

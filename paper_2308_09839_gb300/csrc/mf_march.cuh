@@ -1,0 +1,255 @@
+// Face-marching apply on tensor-product boxes (auto variant, one right-hand side), scalar Laplace
+// and isotropic elasticity.
+//
+// The arithmetic is that of tile::laplace_apply / tile::elasticity_apply (Eqs. 7 and 9 with 2x2x2
+// Gauss, rewritten exactly in the Walsh-Hadamard monomial basis: A^e = H^T D_e H with D_e diagonal
+// for Laplace and diagonal plus 24 couplings between components for elasticity), in double-word
+// FP32 for FP64 accuracy or in plain FP32.  What changes is the organisation, which shares work
+// between neighbouring elements:
+//
+//  * H = Hz (Hy Hx): the 8-point transform of an element is the 2D transform of its bottom and of
+//    its top face of 4 nodes, followed by one butterfly along z.  The face transform of node plane
+//    k is shared by the elements below and above it: a thread owns a column of elements, marches
+//    up in z and carries the top-face transform of one element over as the bottom-face transform
+//    of the next.  Forward cost per element: 8 + 8 adds instead of 24.
+//  * H^T = (Hy Hx)^T Hz^T likewise: after the z butterfly the bottom-face part of an element and
+//    the top-face part of the element below belong to the same face, so they are added first and
+//    transposed once (4 + 8 adds), then the element's top-face part is carried up.
+//  * The four faces around a node are summed in the plane: along x by a warp shuffle (a warp is a
+//    row of 32 element columns), along y by one shared-memory exchange per plane.  Every owned
+//    node is then complete and written once (coalesced along x), without atomics, memset or
+//    read-modify-write; the summation order is fixed, so the result is bitwise reproducible.
+//
+// A CTA covers EX x EY element columns = an (EX-1) x (EY-1) block of owned nodes plus one halo
+// ring of elements on the low sides (recomputed by the neighbouring CTA), over a z-segment of
+// node planes [k0, k1) (plus the element layer below k0).  One __syncthreads per plane.
+#pragma once
+
+#include "mf_tile.cuh"
+
+namespace march {
+
+using tile::TileArgs;
+
+template <class N>
+__device__ __forceinline__ typename N::T shfl_up1(typename N::T v);
+template <>
+__device__ __forceinline__ tile::NumDW::T shfl_up1<tile::NumDW>(tile::NumDW::T v) {
+  return dwa::dw{__shfl_up_sync(0xffffffffu, v.h, 1), __shfl_up_sync(0xffffffffu, v.l, 1)};
+}
+template <>
+__device__ __forceinline__ tile::NumF32::T shfl_up1<tile::NumF32>(tile::NumF32::T v) {
+  return __shfl_up_sync(0xffffffffu, v, 1);
+}
+
+template <int NC, class N, int EX, int EY>
+struct MarchSmem {
+  typename N::S up[2][(EX + 1) * (EY + 1) * NC];  // staged node planes (double buffered)
+  typename N::S xrow[2][NC * EX * EY];            // partial sums of the top node row of each face
+};
+
+// PHYS = MF_LAPLACE (Eq. 7) or MF_ELASTICITY (Eq. 9, Algorithm 1); vectors hold NC values per
+// node (x, y, z components interleaved for elasticity).
+template <int PHYS, class N, int EX, int EY, int MINB>
+__global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const typename N::IO *__restrict__ x,
+                                                            typename N::IO *__restrict__ y,
+                                                            const int *__restrict__ skip) {
+  static_assert(EX == 32, "a warp is one row of element columns");
+  using T = typename N::T;
+  using IO = typename N::IO;
+  constexpr int NC = PHYS == MF_LAPLACE ? 1 : 3;
+  constexpr int NT = EX * EY, PX = EX + 1, NP = (EX + 1) * (EY + 1), TX = EX - 1, TY = EY - 1;
+  constexpr int LOADS = (NP + NT - 1) / NT;
+  __shared__ MarchSmem<NC, N, EX, EY> sm;
+  if (skip && *skip) return;
+  (void)TX;
+  (void)TY;
+
+  const int tid = threadIdx.x;
+  const int item = blockIdx.x;
+  const int bx = item % g.tiles_x;
+  const int by = (item / g.tiles_x) % g.tiles_y;
+  const int bz = item / (g.tiles_x * g.tiles_y);
+  const int i0 = bx * (EX - 1), j0 = by * (EY - 1);
+  const int NXP = g.nx + 1, NYP = g.ny + 1;
+  const int k0 = bz * g.seg, k1 = min(k0 + g.seg, g.nz + 1);
+  const int tx = tid % EX, ty = tid / EX;
+  const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;
+  const bool ein = ex >= 0 && ex < g.nx && ey >= 0 && ey < g.ny;
+  // this thread's lower-left node (ex, ey) is owned by the CTA
+  const bool own = tx >= 1 && ty >= 1 && ex < NXP && ey < NYP;
+
+  // per-column geometry invariants
+  T hx = N::zero(), hy = N::zero(), ihx = N::zero(), ihy = N::zero();
+  if (ein) {
+    hx = N::from2(__ldg(g.hx + ex));
+    ihx = N::from2(__ldg(g.ihx + ex));
+    hy = N::from2(__ldg(g.hy + ey));
+    ihy = N::from2(__ldg(g.ihy + ey));
+  }
+  T hy_ihx = N::zero(), hx_ihy = N::zero(), hxhy = N::zero();
+  if constexpr (PHYS == MF_LAPLACE) {
+    hy_ihx = N::mul(hy, ihx);
+    hx_ihy = N::mul(hx, ihy);
+    hxhy = N::mul(hx, hy);
+  }
+
+  // plane staging: global -> registers (one plane ahead) -> shared memory
+  IO xr[LOADS][NC];
+  bool dr[LOADS];
+  auto fetch = [&](int k) {
+#pragma unroll
+    for (int l = 0; l < LOADS; ++l) {
+      const int p = tid + l * NT;
+      const int ix = i0 - 1 + p % PX, iy = j0 - 1 + p / PX;
+      const bool ok = p < NP && ix >= 0 && ix < NXP && iy >= 0 && iy < NYP;
+      const int64_t node = ix + (int64_t)NXP * (iy + (int64_t)NYP * k);
+      dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) xr[l][c] = ok ? __ldg(x + node * NC + c) : (IO)0;
+    }
+  };
+  auto stage = [&](int k) {
+    auto *u = sm.up[k & 1];
+#pragma unroll
+    for (int l = 0; l < LOADS; ++l) {
+      const int p = tid + l * NT;
+      if (p < NP)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) N::st(u[p * NC + c], dr[l] ? N::zero() : N::in(xr[l][c]));
+    }
+  };
+  // 2D forward transform of this thread's face in plane k (modes: bit 0 x, bit 1 y)
+  auto face_fwd = [&](int k, T F[NC][4]) {
+    const auto *u = sm.up[k & 1];
+    const int p = tx + PX * ty;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T u0 = N::ld(u[p * NC + c]), u1 = N::ld(u[(p + 1) * NC + c]);
+      const T u2 = N::ld(u[(p + PX) * NC + c]), u3 = N::ld(u[(p + PX + 1) * NC + c]);
+      const T a0 = N::add(u0, u1), a1 = N::sub(u1, u0), a2 = N::add(u2, u3), a3 = N::sub(u3, u2);
+      F[c][0] = N::add(a0, a2);
+      F[c][1] = N::add(a1, a3);
+      F[c][2] = N::sub(a2, a0);
+      F[c][3] = N::sub(a3, a1);
+    }
+  };
+
+  const int s_lo = max(k0 - 1, 0);      // first element layer (the one below the segment)
+  const int s_hi = min(k1 - 1, g.nz);   // last step; step nz only completes the top plane
+  const int plim = min(k1, g.nz);       // highest node plane read
+  fetch(s_lo);
+  stage(s_lo);
+  if (s_lo + 1 <= plim) {
+    fetch(s_lo + 1);
+    stage(s_lo + 1);
+  }
+  if (s_lo + 2 <= plim) fetch(s_lo + 2);
+  __syncthreads();
+  T Fb[NC][4], Gc[NC][4];  // bottom-face transform of the current element; top-face part from below
+  face_fwd(s_lo, Fb);
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Gc[c][m] = N::zero();
+  __syncthreads();  // everyone has read plane s_lo before its buffer is reused
+
+  for (int ez = s_lo; ez <= s_hi; ++ez) {
+    const bool elem = ein && ez < g.nz;
+    T Ft[NC][4], S[NC][4];
+    if (ez < g.nz) face_fwd(ez + 1, Ft);
+    else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Ft[c][m] = N::zero();
+    }
+    if (elem) {
+      const int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
+      const T hz = N::from2(__ldg(g.hz + ez)), ihz = N::from2(__ldg(g.ihz + ez));
+      // o[l][m]: D times the 8 modes; the z butterfly gives mode m (m < 4) as Fb + Ft and mode
+      // m + 4 as Ft - Fb; mode 0 has D = 0
+      T o[NC][8];
+      if constexpr (PHYS == MF_LAPLACE) {
+        const tile::LapCoef<N> cf = tile::laplace_coef<N>(N::from2(__ldg(g.mat + e)), hy_ihx, hx_ihy, hxhy, hz, ihz);
+        o[0][1] = N::mul(cf.s1, N::add(Fb[0][1], Ft[0][1]));
+        o[0][2] = N::mul(cf.s2, N::add(Fb[0][2], Ft[0][2]));
+        o[0][3] = N::mul(cf.s12, N::add(Fb[0][3], Ft[0][3]));
+        o[0][4] = N::mul(cf.s3, N::sub(Ft[0][0], Fb[0][0]));
+        o[0][5] = N::mul(cf.s13, N::sub(Ft[0][1], Fb[0][1]));
+        o[0][6] = N::mul(cf.s23, N::sub(Ft[0][2], Fb[0][2]));
+        o[0][7] = N::mul(cf.s123, N::sub(Ft[0][3], Fb[0][3]));
+      } else {
+        const T h[3] = {hx, hy, hz}, ih[3] = {ihx, ihy, ihz};
+        const tile::ElCoef<N> cf =
+            tile::elasticity_coef<N>(N::from2(__ldg(g.mat + 2 * e)), N::from2(__ldg(g.mat + 2 * e + 1)), h, ih);
+        T c[3][8];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          c[k][0] = N::zero();
+#pragma unroll
+          for (int m = 1; m < 4; ++m) c[k][m] = N::add(Fb[k][m], Ft[k][m]);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) c[k][m + 4] = N::sub(Ft[k][m], Fb[k][m]);
+        }
+        tile::elasticity_modes<N>(cf, c, o);
+      }
+      // transposed z butterfly: bottom part o[m] - o[m+4] (summed with the carried top part of the
+      // element below), top part o[m] + o[m+4] (carried up)
+#pragma unroll
+      for (int l = 0; l < NC; ++l) {
+        S[l][0] = N::sub(Gc[l][0], o[l][4]);
+        Gc[l][0] = o[l][4];
+#pragma unroll
+        for (int m = 1; m < 4; ++m) {
+          S[l][m] = N::add(Gc[l][m], N::sub(o[l][m], o[l][m + 4]));
+          Gc[l][m] = N::add(o[l][m], o[l][m + 4]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < NC; ++l)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          S[l][m] = Gc[l][m];
+          Gc[l][m] = N::zero();
+        }
+    }
+    // transposed 2D transform of the face sums -> contributions to the face's 4 corner nodes; along
+    // x node (ex, .) gets this face's left corners and the left neighbour face's right corners
+    T rb[NC];
+#pragma unroll
+    for (int l = 0; l < NC; ++l) {
+      const T t0 = N::sub(S[l][0], S[l][1]), t1 = N::add(S[l][0], S[l][1]);
+      const T t2 = N::sub(S[l][2], S[l][3]), t3 = N::add(S[l][2], S[l][3]);
+      const T v00 = N::sub(t0, t2), v01 = N::add(t0, t2), v10 = N::sub(t1, t3), v11 = N::add(t1, t3);
+      rb[l] = N::add(v00, shfl_up1<N>(v10));
+      N::st(sm.xrow[ez & 1][l * NT + tid], N::add(v01, shfl_up1<N>(v11)));
+    }
+    if (ez + 2 <= plim) {
+      stage(ez + 2);  // plane ez's buffer: its last reader finished before the previous barrier
+      if (ez + 3 <= plim) fetch(ez + 3);
+    }
+    __syncthreads();
+    // y: node (ex, ey) gets the bottom row of this thread's faces and the top row of the row below
+    if (own && ez >= k0) {
+      const int64_t node = ex + (int64_t)NXP * (ey + (int64_t)NYP * ez);
+      const bool dir = __ldg(g.dmask + node) != 0;
+#pragma unroll
+      for (int l = 0; l < NC; ++l) {
+        const T tot = N::add(rb[l], N::ld(sm.xrow[ez & 1][l * NT + tid - EX]));
+        y[node * NC + l] = dir ? x[node * NC + l] : N::out(tot);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Fb[c][m] = Ft[c][m];
+  }
+}
+
+// Launch shapes: EX = 32 element columns per warp row, EY rows, MINB resident CTAs per SM.
+template <int PHYS, class N> struct MarchShape { static constexpr int EX = 32, EY = 16, MINB = 2; };
+template <class N> struct MarchShape<MF_ELASTICITY, N> { static constexpr int EX = 32, EY = 8, MINB = 1; };
+
+}  // namespace march

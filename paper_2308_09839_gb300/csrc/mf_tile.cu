@@ -2,6 +2,7 @@
 // mf_tile.cuh; see there for what they compute and how).
 #include <algorithm>
 
+#include "mf_march.cuh"
 #include "mf_tile.cuh"
 
 using namespace tile;
@@ -101,12 +102,22 @@ static mf_status tile_launch_one(const mf_mesh *m, const typename N::IO *x, type
   return MF_OK;
 }
 
+// One right-hand side: the face-marching kernels (mf_march.cuh).
+template <int PHYS, class N>
+static mf_status march_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
+                              const int *skip) {
+  using MS = march::MarchShape<PHYS, N>;
+  TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg);
+  march::march_apply<PHYS, N, MS::EX, MS::EY, MS::MINB><<<tile_items(g), MS::EX * MS::EY, 0, s>>>(g, x, y, skip);
+  return MF_OK;
+}
+
 template <class N>
 static mf_status tile_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
                              const int *skip) {
   mf_count_launches(1);
-  if (m->physics == MF_LAPLACE) MF_TRY((tile_launch_one<MF_LAPLACE, N>(m, x, y, s, skip)));
-  else MF_TRY((tile_launch_one<MF_ELASTICITY, N>(m, x, y, s, skip)));
+  if (m->physics == MF_LAPLACE) MF_TRY((march_launch<MF_LAPLACE, N>(m, x, y, s, skip)));
+  else MF_TRY((march_launch<MF_ELASTICITY, N>(m, x, y, s, skip)));
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }

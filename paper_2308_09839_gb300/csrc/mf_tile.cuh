@@ -185,13 +185,11 @@ __device__ __forceinline__ ElCoef<N> elasticity_coef(typename N::T lam, typename
   return e;
 }
 
-// c[k][a] (component k, corner a) -> A^e u, in place.
+// Mode coefficients c[k][m] = (H u^k)_m -> o[l][m] = (D c)_l,m (modes 1..6 are coupled between
+// components; modes 0 and 7 of c are not read, o[l][0] = 0).
 template <class N>
-__device__ __forceinline__ void elasticity_apply(const ElCoef<N> &e, typename N::T c[3][8]) {
+__device__ __forceinline__ void elasticity_modes(const ElCoef<N> &e, const typename N::T c[3][8], typename N::T o[3][8]) {
   using T = typename N::T;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) fwht_fwd<N>(c[k]);
-  T o[3][8];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const T W1 = l == 0 ? e.lr[0] : e.mr[0];
@@ -218,6 +216,16 @@ __device__ __forceinline__ void elasticity_apply(const ElCoef<N> &e, typename N:
   ACC(2, 4, L[0], 1, 2); ACC(2, 5, L3[0], 1, 3); ACC(2, 2, M[0], 1, 4); ACC(2, 3, M3[0], 1, 5);
   ACC(1, 2, L[0], 2, 4); ACC(1, 3, L3[0], 2, 5); ACC(1, 4, M[0], 2, 2); ACC(1, 5, M3[0], 2, 3);
 #undef ACC
+}
+
+// c[k][a] (component k, corner a) -> A^e u, in place.
+template <class N>
+__device__ __forceinline__ void elasticity_apply(const ElCoef<N> &e, typename N::T c[3][8]) {
+  using T = typename N::T;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) fwht_fwd<N>(c[k]);
+  T o[3][8];
+  elasticity_modes<N>(e, c, o);
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     fwht_inv<N>(o[l]);

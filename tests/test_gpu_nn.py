@@ -157,3 +157,34 @@ def test_learned_preconditioner_gains_over_jacobi_pcg():
     print(f"plain CG {i_cg.iters} it, Jacobi-PCG {i_j.iters} it, learned FCG {i_nn.iters} it "
           f"(switched off at {i_nn.outer_iters})")
     assert i_nn.iters < i_j.iters < i_cg.iters
+
+
+def test_fcg_with_zero_network_matches_oracle_fcg_m():
+    """With every network parameter zero the correction vanishes (theta = 0) and the learned
+    preconditioner is two damped-Jacobi sweeps (omega = 2/3), a fixed linear map; the GPU's
+    truncated flexible CG (8 stored directions) must then follow the oracle's FCG(8) with that
+    preconditioner: same iteration count (+-1) and the same solution."""
+    from oracle import fem, solvers
+    from paper_2308_09839_gb300 import inputs
+    p = inputs.laplace_box(12, jitter=0.0, sigma=1.0, seed=4)
+    mesh = mf.Mesh.from_problem(p)
+    net = mf.Net(p.nx + 1, p.ny + 1, p.nz + 1, seed=0)
+    net.set_params(np.zeros(net.n_params, np.float32))
+    net.set_output_scale(1.0)
+    b = p.b()
+    x, info = mesh.cg(torch.from_numpy(b).cuda(), net=net, rtol=1e-8)
+    torch.cuda.synchronize()
+    A = fem.assemble_csr("laplace", p.coords, p.cell_array(), p.mat, p.dirichlet, p.n_nodes)
+    d = A.diagonal()
+    w = 2.0 / 3.0
+
+    def two_sweeps(r):
+        z1 = w * r / d
+        return z1 + w * (r - A @ z1) / d
+
+    xo, it_o, h_o = solvers.fcg_m(lambda v: A @ v, b, two_sweeps, m=8, rtol=1e-8)
+    assert info.status == mf.MF_OK and info.outer_iters == -1
+    assert abs(info.iters - it_o) <= 1, (info.iters, it_o)
+    assert info.rel_res_true <= 1.05e-8 and h_o[-1] <= 1e-8
+    assert rel(x.cpu().numpy(), xo) <= 1e-6
+    net.close()

@@ -337,6 +337,32 @@ def test_fcg_identity_equals_cg_and_pcg_jacobi():
     assert it_j < it_cg  # lognormal(0, 1) coefficients: diagonal scaling helps
 
 
+def test_fcg_m_special_cases_and_orthogonality():
+    """FCG(m) with a fixed preconditioner is PCG (identity: CG); with a preconditioner that changes
+    every iteration its directions are still A-orthogonal within the window."""
+    p = inputs.laplace_box(5, jitter=0.2, sigma=1.0, seed=2)
+    cells = p.cell_array()
+    A = fem.assemble_csr("laplace", p.coords, cells, p.mat, p.dirichlet, p.n_nodes)
+    b = p.b()
+    _, it_cg, h_cg = solvers.cg(lambda v: A @ v, b, rtol=1e-8)
+    _, it_m, h_m = solvers.fcg_m(lambda v: A @ v, b, lambda r: r.copy(), m=4, rtol=1e-8)
+    assert abs(it_m - it_cg) <= 1 and np.allclose(h_m[:20], h_cg[:20], rtol=1e-8)
+    dg = A.diagonal()
+    _, it_j, h_j = solvers.pcg(lambda v: A @ v, b, lambda r: r / dg, rtol=1e-8)
+    _, it_mj, h_mj = solvers.fcg_m(lambda v: A @ v, b, lambda r: r / dg, m=1, rtol=1e-8)
+    assert abs(it_mj - it_j) <= 1 and np.allclose(h_mj[:20], h_j[:20], rtol=1e-8)
+    # a preconditioner that varies from call to call (random positive diagonal scalings)
+    rng = np.random.default_rng(5)
+    var = lambda r: r / dg * rng.uniform(0.5, 2.0, size=r.size)
+    x, it_v, _, pairs = solvers.fcg_m(lambda v: A @ v, b, var, m=3, rtol=1e-8, keep_directions=True)
+    assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+    for k in range(len(pairs)):
+        for j in range(max(0, k - 3), k):
+            pk, apk = pairs[k]
+            pj, apj = pairs[j]
+            assert abs(pk @ apj) <= 1e-9 * np.sqrt((pk @ apk) * (pj @ apj))
+
+
 def test_iterative_refinement_fp32_inner():
     """FP64 IR around an FP32 inner CG (rtol 1e-4) reaches a 1e-10 FP64 residual."""
     p = inputs.laplace_box(6, jitter=0.1, sigma=0.5, seed=3)
