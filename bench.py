@@ -35,6 +35,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GDoF/s of matrix-free A.x (Q1 Laplace 256^3 + elasticity 160^3, FP64)"
 UNIT = "GDoF/s"
+# DRAM bytes (read + write) per launch of the face-marching FP64 kernels at the benchmarked sizes:
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 192^3 Laplace and 128^3
+# elasticity meshes, scaled by the node count (the traffic is proportional to it).  Part of y is
+# still dirty in L2 when a launch ends, so the write share is below the bytes written.
+TRAFFIC = {"laplace": round(152346880 * 16974593 / 7189057), "elasticity": round(103310592 * 4173281 / 2146689)}
 
 
 def parse():
@@ -50,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solver measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-RHS measurement")
+    ap.add_argument("--no-vector", action="store_true", help="skip the vector Laplace measurement")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner measurement")
     ap.add_argument("--n-learned", type=int, default=128)
@@ -58,6 +64,7 @@ def parse():
     ap.add_argument("--lr", type=float, default=2e-4)
     ap.add_argument("--cg-timeout", type=float, default=90.0)
     ap.add_argument("--variant", type=int, default=0, help="0 = auto (fastest FP64-accurate), 1 = reference")
+    ap.add_argument("--no-tune", action="store_true", help="keep the library's default z-segment length")
     return ap.parse_args()
 
 
@@ -219,10 +226,13 @@ def main():
 
     pL = inputs.cartesian_laplace_256(n=args.n_laplace)
     pE = inputs.cartesian_elasticity_160(n=args.n_elasticity)
-    meshes = []
+    meshes, segs = [], []
     for p in (pL, pE):
         m = mf.Mesh.from_problem(p, device=f"cuda:{local}")
         m.set_variant(args.variant)
+        if args.variant == 0 and not args.no_tune:
+            from paper_2308_09839_gb300 import autotune
+            segs.append(autotune.tune_apply(m, use_cache=False))  # setup, not timed
         x = torch.from_numpy(p.x()).cuda()
         meshes.append((p, m, x, torch.empty_like(x)))
     F = [p.n_free for p in (pL, pE)]
@@ -292,15 +302,36 @@ def main():
     io_bytes = sum(h.numel() * 8 for h in hx)
     e2e = {"value": e2e_value / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
 
-    # ---- roofline of the dominant kernel (the matrix-free apply taking the most time)
+    # ---- roofline of the dominant kernel (the matrix-free apply taking the most time).  The FP64-
+    # accurate apply runs in double-word FP32 arithmetic and is bound by the FP32 pipe: achieved =
+    # algorithmic FP32-pipe operations per launch / kernel time against SMs x lanes x max clock.
+    # The HBM view is reported beside it: the paper's read-once bytes of a matrix-free apply on a
+    # general hex mesh (node map, coordinates, cell constants, x, y) and the bytes this kernel must
+    # move on a tensor-product grid (cell constants, mask, x, y).
     j = int(np.argmax(t_app))
     p = (pL, pE)[j]
     tp = meshes[j][1].info["tensor_product"] and args.variant == 0
-    abytes = bm.kernel_apply_bytes(p.physics, p.n_cells, p.n_nodes, structured=True, tensor_product=tp)
-    achieved = abytes / t_app[j] / 1e9
-    roof = {"kernel": f"matrix-free {p.physics} apply ({p.nx}^3)", "bound": "hbm", "achieved": achieved,
-            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": hbm_src,
-            "algorithmic_bytes": abytes, "traffic": None}
+    paper_bytes = bm.kernel_apply_bytes(p.physics, p.n_cells, p.n_nodes, structured=False) - p.n_nodes
+    kern_bytes = bm.kernel_apply_bytes(p.physics, p.n_cells, p.n_nodes, structured=True, tensor_product=tp)
+    hbm = {"peak": hbm_peak, "unit": "GB/s", "peak_source": hbm_src,
+           "paper_model_bytes": paper_bytes, "paper_model_achieved": paper_bytes / t_app[j] / 1e9,
+           "paper_model_frac": paper_bytes / t_app[j] / 1e9 / hbm_peak,
+           "kernel_bytes": kern_bytes, "kernel_bytes_achieved": kern_bytes / t_app[j] / 1e9,
+           "kernel_bytes_frac": kern_bytes / t_app[j] / 1e9 / hbm_peak}
+    if tp:
+        ops = bm.kernel_apply_ops(p.physics)["total"] * p.n_cells
+        peak = bm.fp32_lane_peak() / 1e12
+        achieved = ops / t_app[j] / 1e12
+        roof = {"kernel": f"matrix-free {p.physics} apply ({p.nx}^3, face-marching DW)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                "algorithmic_ops": ops, "ops_per_element": bm.kernel_apply_ops(p.physics)["total"],
+                "traffic": TRAFFIC.get(p.physics), "hbm": hbm}
+    else:
+        achieved = kern_bytes / t_app[j] / 1e9
+        roof = {"kernel": f"matrix-free {p.physics} apply ({p.nx}^3)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": hbm_src,
+                "algorithmic_bytes": kern_bytes, "traffic": None}
 
     # ---- CSR SpMV on the same matrices (in-library matrix-based baseline)
     if not args.no_csr:
@@ -340,6 +371,42 @@ def main():
                              "rel_res_true": info.rel_res_true,
                              "cg_gdofs": p.n_free * info.iters / info.seconds / 1e9}
         extras["cg_matfree"] = cg
+
+    # ---- vector Laplace (Eq. 5) on the elasticity workload's 160^3 mesh: matrix-free vs CSR
+    if not args.no_vector:
+        pv = inputs.vector_laplace_box(args.n_elasticity, sigma=0.5, layered=True, seed=0)
+        mv = mf.Mesh.from_problem(pv, device=f"cuda:{local}")
+        if args.variant == 0 and not args.no_tune:
+            from paper_2308_09839_gb300 import autotune
+            autotune.tune_apply(mv, use_cache=False)
+        xv = torch.from_numpy(pv.x()).cuda()
+        yv = torch.empty_like(xv)
+
+        def timed(fn, reps):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / 1e3 / reps
+
+        tv = timed(lambda: mv.apply(xv, yv), max(10, K // 4))
+        vec = {"mesh": f"vector Laplace {pv.nx}^3 Cartesian", "free_dof": pv.n_free, "ms_apply": 1e3 * tv,
+               "gdofs_apply": pv.n_free / tv / 1e9}
+        if not args.no_csr:
+            Av = mv.assemble_csr()
+            ts = timed(lambda: Av.spmv(xv, yv), max(10, K // 4))
+            vec.update({"ms_csr": 1e3 * ts, "gdofs_csr": pv.n_free / ts / 1e9, "nnz": Av.info["nnz"],
+                        "mf_over_csr": ts / tv})
+            Av.close()
+            del Av
+        extras["vector_laplace"] = vec
+        mv.close()
+        del xv, yv
+        torch.cuda.empty_cache()
 
     # ---- batched persistent CG: 64 independent Laplace problems, n ~ log-uniform [8, 96]
     if not args.no_batch:
@@ -469,11 +536,15 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f32x2" if args.variant == 0 else "f64",
+        "dtype_note": ("double-word FP32 arithmetic (pairs of floats), FP64 inputs and outputs, parity <= 1e-12 "
+                       "relative 2-norm against the FP64 oracle" if args.variant == 0 else "FP64 arithmetic"),
+        "data": "synthetic",
         "config": {"workload": f"Q1 matrix-free apply, Laplace {pL.nx}^3 Cartesian (F={F[0]}) + elasticity "
                                f"{pE.nx}^3 Cartesian (F={F[1]}), 8 z-layers x lognormal(0,0.5)",
                    "n_dof_total": [pL.n_dof, pE.n_dof], "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (no flush)", "variant": args.variant},
+                   "l2": "inputs larger than L2 (no flush)", "variant": args.variant,
+                   "tile_segments": segs or None},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
         "extras": extras,
     }

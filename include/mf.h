@@ -44,7 +44,7 @@ typedef enum {
   MF_ERR_UNSUPPORTED = -7  /* operation not available for this mesh or physics */
 } mf_status;
 
-enum { MF_LAPLACE = 0, MF_ELASTICITY = 1 };
+enum { MF_LAPLACE = 0, MF_ELASTICITY = 1, MF_VECTOR_LAPLACE = 2 };
 
 typedef struct mf_mesh mf_mesh;
 typedef struct mf_csr mf_csr;
@@ -53,14 +53,17 @@ typedef struct mf_csr mf_csr;
  * mf_setup_mesh - validate a Q1 hexahedral mesh and build the operator's device data.
  *
  * The inputs of Algorithm 1 (support-point coordinates) plus the cell constants of Table 2.
- *   physics    MF_LAPLACE (1 DoF per node) or MF_ELASTICITY (3 DoFs per node).
+ *   physics    MF_LAPLACE (1 DoF per node), MF_ELASTICITY (3 DoFs per node) or MF_VECTOR_LAPLACE
+ *              (3 DoFs per node: the vector Laplacian of Eqs. 2 and 5, the scalar operator acting
+ *              on each component).
  *   n_nodes    N >= 8; n_cells E >= 1.
  *   coords     device double[N][3], node coordinates.
  *   cells      device int32[E][8] element -> node map in the corner order above, or NULL for a
  *              structured nx x ny x nz box numbered as above (then E must equal nx*ny*nz and N
  *              must equal (nx+1)(ny+1)(nz+1); coordinates may still be arbitrary).
- *   mat        device double[E] (Laplace: conductivity kappa_e > 0) or double[E][2] (elasticity:
- *              Young's modulus E_e > 0 and Poisson ratio -1 < nu_e < 0.5).
+ *   mat        device double[E] (Laplace and vector Laplace: coefficient kappa_e > 0) or
+ *              double[E][2] (elasticity: Young's modulus E_e > 0 and Poisson ratio
+ *              -1 < nu_e < 0.5).
  *   dirichlet  device uint8[N] (nonzero = all DoFs of that node constrained) or NULL (none).
  * The library copies what it needs into its own layout; the caller's arrays may be freed after the
  * call returns.  Synchronises `stream`.  Errors: MF_ERR_ARG, MF_ERR_MESH (det J <= 0 at a Gauss
@@ -110,15 +113,27 @@ mf_status mf_apply_laplace(const mf_mesh *mesh, const double *x, double *y, mf_s
 mf_status mf_apply_elasticity(const mf_mesh *mesh, const double *x, double *y, mf_stream stream);
 
 /*
- * mf_apply_f32 - the same operator (either physics) evaluated entirely in FP32: geometry from FP32
+ * mf_apply_vector_laplace - y = A x for the vector Laplace operator (Eq. 5: the element matrix is
+ * the scalar one of Eq. 4, with the per-cell factor kappa_e, acting on each of the three components;
+ * the vector form of Eq. 7).
+ *   x, y  device double[3N], xyz interleaved.  Same contract as mf_apply_laplace; MF_ERR_ARG if
+ *         the mesh was set up for another physics.
+ */
+mf_status mf_apply_vector_laplace(const mf_mesh *mesh, const double *x, double *y, mf_stream stream);
+
+/*
+ * mf_apply_f32 - the same operator (any physics) evaluated entirely in FP32: geometry from FP32
  * copies of the coordinates and cell constants, FP32 x and y.  Used by the mixed-precision solver.
  *   x, y  device float[N * ndof_per_node].  Same contract otherwise.
  */
 mf_status mf_apply_f32(const mf_mesh *mesh, const float *x, float *y, mf_stream stream);
 
 /*
- * mf_apply_multi - Y = A X for nrhs right-hand sides at once; geometry evaluated once per element
- * and reused for every right-hand side.
+ * mf_apply_multi - Y = A X for nrhs right-hand sides at once.  On tensor-product meshes one launch
+ * of the face-marching kernel covers all right-hand sides (each column bitwise equal to the single
+ * apply; the element coefficients are cheap there and are recomputed per right-hand side); on other
+ * meshes the reference kernel evaluates the geometry (J, adj J, det J at every Gauss point) once per
+ * element and reuses it for every right-hand side.
  *   X, Y  device double[N][nrhs][ndof_per_node] (node-major, then right-hand side, then
  *         component).  1 <= nrhs <= 16.  Same contract as the single apply.
  */

@@ -1,5 +1,6 @@
-"""Autotuner for the batched persistent CG solver: picks the z-segment length of the tile work
-items (node planes per item) for each problem-size bucket by timing short batched solves.
+"""Autotuners for the z-segment length of the tile work items (node planes per CTA): ``tune`` for
+the batched persistent CG solver (one choice per problem-size bucket, timed on short batched
+solves) and ``tune_apply`` for the single operator apply of one mesh (timed applies).
 
 The choice changes only how work is split among CTAs, never the arithmetic (the tile kernel's
 per-node summation order does not depend on it), so results stay bitwise identical.  Choices are
@@ -107,3 +108,42 @@ def tune(meshes, dims, bs, xs, iters: int = 20, use_cache: bool = True) -> dict:
     for m, d in zip(meshes, dims):
         mf.mf_set_tile_segment(m, choice[_bucket(d)])
     return choice
+
+
+APPLY_CANDIDATES = (0, 8, 12, 16, 20, 24, 32, 48, 64, 96, 128)
+
+
+def tune_apply(mesh, reps: int = 20, use_cache: bool = True) -> int:
+    """Time ``mesh.apply`` for each segment length in APPLY_CANDIDATES (0 = the library's wave-model
+    default) on a random vector, keep the fastest with mf_set_tile_segment and return it.  Cached per
+    GPU, physics and mesh dimensions.  The choice never changes the result bits."""
+    key = f"{_device_key()}|apply|{mesh.physics}|{mesh.dims}"
+    cache = _load() if use_cache else {}
+    if use_cache and key in cache:
+        seg = int(cache[key])
+        mf.mf_set_tile_segment(mesh, seg)
+        return seg
+    n = mesh.info["n_dof"]
+    x = torch.rand(n, dtype=torch.float64, device=mesh.device)
+    y = torch.empty_like(x)
+    best_t, best_s = float("inf"), 0
+    for s in APPLY_CANDIDATES:
+        if s > 0 and s > mesh.dims[2] + 1:
+            continue
+        mf.mf_set_tile_segment(mesh, s)
+        for _ in range(3):
+            mesh.apply(x, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            mesh.apply(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        if t < best_t:
+            best_t, best_s = t, s
+    mf.mf_set_tile_segment(mesh, best_s)
+    if use_cache:
+        cache[key] = best_s
+        _store(cache)
+    return best_s

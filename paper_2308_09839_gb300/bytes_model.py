@@ -78,3 +78,40 @@ def kernel_apply_bytes(physics: str, n_elem: int, n_nodes: int, structured: bool
 def kernel_spmv_bytes(n_rows: int, nnz: int) -> int:
     """Algorithmic bytes of one CSR SpMV: values + column indices + row pointers + x (read once) + y."""
     return nnz * (F64 + I32) + (n_rows + 1) * I32 + 2 * n_rows * F64
+
+
+# ------------------------------------------------------ arithmetic of the double-word kernels ----
+
+# FP32-pipe lane operations of the double-word (DW) building blocks (add, sub, mul, fma or integer op
+# = one operation each): lazy DW add/sub = TwoSum (6) + 2 adds of the low parts; DW mul = product,
+# its FMA error term and two cross FMAs; split of a double into a pair (integer path) and the
+# conversion back (exact float-to-double by bits for both parts, one FP64 add).
+DW_ADD, DW_MUL, DW_SPLIT, DW_OUT = 8, 4, 12, 13
+
+
+def kernel_apply_ops(physics: str) -> dict:
+    """Algorithmic FP32-pipe operations per element of the face-marching DW apply (one right-hand
+    side, tensor-product mesh), counted from the algorithm, not from the compiled code.
+
+    Laplace (one component): 2D transform of the new top face (8 DW adds), z butterfly of the 7
+    non-constant modes (7 adds), element coefficients from kappa and the spacings (9 DW muls + 4 DW
+    adds + 6 FP32 scalings), diagonal scaling (7 muls), transposed z butterfly with the carried face
+    (10 adds), transposed face transform (8 adds), in-plane sums (3 adds), one split in and one
+    conversion out per node.
+    Elasticity (three components): 3 x (8 + 7) transform adds, coefficients (24 DW muls + 1 DW add +
+    26 FP32 scalings), diagonal blocks (12 adds + 33 muls), 24 cross-component multiply-adds,
+    3 x (10 + 8 + 3) transposed-transform adds, three splits and three conversions per node."""
+    if physics == "laplace":
+        parts = {"face_transform": 8 * DW_ADD, "z_butterfly": 7 * DW_ADD, "coefficients": 9 * DW_MUL + 4 * DW_ADD + 6,
+                 "scaling": 7 * DW_MUL, "transposed": (10 + 8 + 3) * DW_ADD, "conversions": DW_SPLIT + DW_OUT}
+    else:
+        parts = {"face_transform": 3 * 8 * DW_ADD, "z_butterfly": 3 * 7 * DW_ADD,
+                 "coefficients": 24 * DW_MUL + DW_ADD + 26, "diagonal": 12 * DW_ADD + 33 * DW_MUL,
+                 "cross": 24 * (DW_MUL + DW_ADD), "transposed": 3 * (10 + 8 + 3) * DW_ADD,
+                 "conversions": 3 * (DW_SPLIT + DW_OUT)}
+    return dict(parts=parts, total=sum(parts.values()))
+
+
+def fp32_lane_peak(sms: int = 152, lanes: int = 128, clock_hz: float = 2.07e9) -> float:
+    """FP32-pipe lane operations per second: SMs x FP32 lanes per SM x maximum SM clock."""
+    return sms * lanes * clock_hz

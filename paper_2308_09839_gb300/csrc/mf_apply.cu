@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(128) apply_ref_colour(MeshView m, const R *__r
     for (int a = 0; a < 8; ++a)
 #pragma unroll
       for (int k = 0; k < 3; ++k) u[a][k] = dir[a] ? (R)0 : x[3 * nodes[a] + k];
-    q1::elasticity_element<R>(X, u, mat[2 * e], mat[2 * e + 1], v);
+    if (PHYS == MF_VECTOR_LAPLACE) q1::vector_laplace_element<R>(X, u, mat[e], v);
+    else q1::elasticity_element<R>(X, u, mat[2 * e], mat[2 * e + 1], v);
 #pragma unroll
     for (int a = 0; a < 8; ++a)
       if (!dir[a]) {
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(128) apply_multi_colour(MeshView m, const doub
     for (int i = 0; i < 3; ++i) X[a][i] = m.X[3 * nodes[a] + i];
     dir[a] = m.dmask[nodes[a]] != 0;
   }
-  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  constexpr int ND = phys_ndpn(PHYS);
   double Cq[8][3][3], idet[8];
 #define MF_GEOM(Q)                                        \
   {                                                       \
@@ -94,8 +95,8 @@ __global__ void __launch_bounds__(128) apply_multi_colour(MeshView m, const doub
   }
   MF_GEOM(0) MF_GEOM(1) MF_GEOM(2) MF_GEOM(3) MF_GEOM(4) MF_GEOM(5) MF_GEOM(6) MF_GEOM(7)
 #undef MF_GEOM
-  const double c0 = PHYS == MF_LAPLACE ? m.mat[e] : m.mat[2 * e];
-  const double c1 = PHYS == MF_LAPLACE ? 0.0 : m.mat[2 * e + 1];
+  const double c0 = phys_is_laplace(PHYS) ? m.mat[e] : m.mat[2 * e];
+  const double c1 = phys_is_laplace(PHYS) ? 0.0 : m.mat[2 * e + 1];
   for (int r = 0; r < nrhs; ++r) {
     double u[8][ND], v[8][ND];
 #pragma unroll
@@ -108,23 +109,27 @@ __global__ void __launch_bounds__(128) apply_multi_colour(MeshView m, const doub
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const double(&C)[3][3] = Cq[q];
-      if (PHYS == MF_LAPLACE) {
-        double g[3];
+      if (phys_is_laplace(PHYS)) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          double s = 0;
+        for (int kc = 0; kc < ND; ++kc) {  // the scalar flux for each component (Eq. 5)
+          double g[3];
 #pragma unroll
-          for (int a = 0; a < 8; ++a) s += u[a][0] * q1::dN(q, a, j);
-          g[j] = s;
+          for (int j = 0; j < 3; ++j) {
+            double s = 0;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) s += u[a][kc] * q1::dN(q, a, j);
+            g[j] = s;
+          }
+          double tt[3], f[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) tt[k] = C[0][k] * g[0] + C[1][k] * g[1] + C[2][k] * g[2];
+          const double sc = c0 * idet[q];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) f[j] = sc * (C[j][0] * tt[0] + C[j][1] * tt[1] + C[j][2] * tt[2]);
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+            v[a][kc] += q1::dN(q, a, 0) * f[0] + q1::dN(q, a, 1) * f[1] + q1::dN(q, a, 2) * f[2];
         }
-        double tt[3], f[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) tt[k] = C[0][k] * g[0] + C[1][k] * g[1] + C[2][k] * g[2];
-        const double sc = c0 * idet[q];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) f[j] = sc * (C[j][0] * tt[0] + C[j][1] * tt[1] + C[j][2] * tt[2]);
-#pragma unroll
-        for (int a = 0; a < 8; ++a) v[a][0] += q1::dN(q, a, 0) * f[0] + q1::dN(q, a, 1) * f[1] + q1::dN(q, a, 2) * f[2];
       } else {
         double H[3][3], G[3][3], S[3][3];
 #pragma unroll
@@ -185,6 +190,8 @@ mf_status apply_reference(const mf_mesh *m, const R *x, R *y, cudaStream_t s, co
     mf_count_launches(1);
     if (m->physics == MF_LAPLACE)
       apply_ref_colour<MF_LAPLACE, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, c, cnt, ce, skip);
+    else if (m->physics == MF_VECTOR_LAPLACE)
+      apply_ref_colour<MF_VECTOR_LAPLACE, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, c, cnt, ce, skip);
     else
       apply_ref_colour<MF_ELASTICITY, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, c, cnt, ce, skip);
   }
@@ -220,6 +227,8 @@ mf_status apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *
     mf_count_launches(1);
     if (m->physics == MF_LAPLACE)
       apply_multi_colour<MF_LAPLACE><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, c, cnt, ce);
+    else if (m->physics == MF_VECTOR_LAPLACE)
+      apply_multi_colour<MF_VECTOR_LAPLACE><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, c, cnt, ce);
     else
       apply_multi_colour<MF_ELASTICITY><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, c, cnt, ce);
   }
@@ -242,14 +251,21 @@ static mf_status check_apply_args(const mf_mesh *m, const void *x, void *y, size
 extern "C" mf_status mf_apply_laplace(const mf_mesh *m, const double *x, double *y, mf_stream stream) {
   mf_clear_error();
   MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(double) : 0));
-  MF_ARG(m->physics == MF_LAPLACE, "mf_apply_laplace: mesh was set up for elasticity");
+  MF_ARG(m->physics == MF_LAPLACE, "mf_apply_laplace: mesh was set up for another physics");
+  return apply_fp64(m, x, y, (cudaStream_t)stream);
+}
+
+extern "C" mf_status mf_apply_vector_laplace(const mf_mesh *m, const double *x, double *y, mf_stream stream) {
+  mf_clear_error();
+  MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(double) : 0));
+  MF_ARG(m->physics == MF_VECTOR_LAPLACE, "mf_apply_vector_laplace: mesh was set up for another physics");
   return apply_fp64(m, x, y, (cudaStream_t)stream);
 }
 
 extern "C" mf_status mf_apply_elasticity(const mf_mesh *m, const double *x, double *y, mf_stream stream) {
   mf_clear_error();
   MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(double) : 0));
-  MF_ARG(m->physics == MF_ELASTICITY, "mf_apply_elasticity: mesh was set up for Laplace");
+  MF_ARG(m->physics == MF_ELASTICITY, "mf_apply_elasticity: mesh was set up for another physics");
   return apply_fp64(m, x, y, (cudaStream_t)stream);
 }
 

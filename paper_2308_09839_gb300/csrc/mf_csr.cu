@@ -1,5 +1,6 @@
-// Matrix-based operator (Sec. 3 and Table 1): CSR assembly of the element matrices of Eqs. 4/6 and
-// the SpMV used as the baseline of the matrix-free kernels.
+// Matrix-based operator (Sec. 3 and Table 1): CSR assembly of the element matrices of Eqs. 4/5/6
+// and the SpMV used as the baseline of the matrix-free kernels.  The vector Laplacian is stored
+// block-diagonally (27 entries per row: its components do not couple).
 //
 // Fill: the paper describes an element loop that searches each global column and adds with an
 // atomic.  Here the search is a binary search in the sorted row, and the add is a plain
@@ -23,7 +24,7 @@ __device__ __forceinline__ int64_t parity_element_c(int64_t t, int c, int nx, in
 // Rows of A^e belonging to corner a: out[k][b][l] = A^e_{ND a + k, ND b + l} (Eqs. 4 and 6).
 template <int PHYS>
 __device__ void element_rows(const double X[8][3], int a, double c0, double c1, double out[][8][3]) {
-  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  constexpr int ND = phys_ndpn(PHYS);
   for (int k = 0; k < ND; ++k)
     for (int b = 0; b < 8; ++b)
       for (int l = 0; l < 3; ++l) out[k][b][l] = 0.0;
@@ -61,7 +62,9 @@ __device__ void element_rows(const double X[8][3], int a, double c0, double c1, 
 template <int PHYS>
 __global__ void csr_fill_colour(MeshView m, int colour, int64_t count, const int32_t *__restrict__ celems,
                                 const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, double *val) {
-  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  constexpr int ND = phys_ndpn(PHYS);
+  constexpr int EP = PHYS == MF_VECTOR_LAPLACE ? MF_LAPLACE : PHYS;  // element matrix computed
+  constexpr int NE = phys_ndpn(EP);
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= count * 8) return;
   const int64_t t = gid >> 3;
@@ -73,10 +76,27 @@ __global__ void csr_fill_colour(MeshView m, int colour, int64_t count, const int
   double X[8][3];
   for (int c = 0; c < 8; ++c)
     for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
-  const double c0 = PHYS == MF_LAPLACE ? m.mat[e] : m.mat[2 * e];
-  const double c1 = PHYS == MF_LAPLACE ? 0.0 : m.mat[2 * e + 1];
-  double A[ND][8][3];
-  element_rows<PHYS>(X, a, c0, c1, A);
+  const double c0 = phys_is_laplace(PHYS) ? m.mat[e] : m.mat[2 * e];
+  const double c1 = phys_is_laplace(PHYS) ? 0.0 : m.mat[2 * e + 1];
+  double A[NE][8][3];
+  element_rows<EP>(X, a, c0, c1, A);
+  if constexpr (PHYS == MF_VECTOR_LAPLACE) {
+    // block-diagonal: row 3 n + k couples only to columns 3 m + k, with the scalar entries
+    for (int k = 0; k < 3; ++k) {
+      const int64_t row = nodes[a] * 3 + k;
+      for (int b = 0; b < 8; ++b) {
+        if (m.dmask[nodes[b]]) continue;
+        const int32_t target = (int32_t)(nodes[b] * 3 + k);
+        int64_t lo = rowptr[row], hi = rowptr[row + 1];
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (col[mid] < target) lo = mid + 1; else hi = mid;
+        }
+        val[lo] += A[0][b][0];
+      }
+    }
+    return;
+  }
   const int64_t row0 = nodes[a] * ND;
   const int64_t lo0 = rowptr[row0], hi0 = rowptr[row0 + 1];
   for (int b = 0; b < 8; ++b) {
@@ -97,7 +117,9 @@ __global__ void csr_fill_colour(MeshView m, int colour, int64_t count, const int
 
 template <int PHYS>
 __global__ void diag_colour(MeshView m, int colour, int64_t count, const int32_t *__restrict__ celems, double *diag) {
-  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  constexpr int ND = phys_ndpn(PHYS);
+  constexpr int EP = PHYS == MF_VECTOR_LAPLACE ? MF_LAPLACE : PHYS;
+  constexpr int NE = phys_ndpn(EP);
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= count * 8) return;
   const int64_t t = gid >> 3;
@@ -109,11 +131,11 @@ __global__ void diag_colour(MeshView m, int colour, int64_t count, const int32_t
   double X[8][3];
   for (int c = 0; c < 8; ++c)
     for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
-  const double c0 = PHYS == MF_LAPLACE ? m.mat[e] : m.mat[2 * e];
-  const double c1 = PHYS == MF_LAPLACE ? 0.0 : m.mat[2 * e + 1];
-  double A[ND][8][3];
-  element_rows<PHYS>(X, a, c0, c1, A);
-  for (int k = 0; k < ND; ++k) diag[nodes[a] * ND + k] += A[k][a][k];
+  const double c0 = phys_is_laplace(PHYS) ? m.mat[e] : m.mat[2 * e];
+  const double c1 = phys_is_laplace(PHYS) ? 0.0 : m.mat[2 * e + 1];
+  double A[NE][8][3];
+  element_rows<EP>(X, a, c0, c1, A);
+  for (int k = 0; k < ND; ++k) diag[nodes[a] * ND + k] += NE == 1 ? A[0][a][0] : A[k][a][k];
 }
 
 __global__ void dirichlet_unit(const int32_t *dn, int64_t n, int nd, const int64_t *rowptr, double *val) {
@@ -131,8 +153,9 @@ __global__ void dirichlet_diag(const int32_t *dn, int64_t n, int nd, double *dia
 
 // Expand the node-level neighbour lists to DoF-level columns: row ND*n + k holds ND*m + l for every
 // neighbour m of n (l = 0..ND-1), or only its own diagonal when n is constrained.
-__global__ void expand_columns(int64_t n_nodes, int nd, const int64_t *__restrict__ noff, const int32_t *__restrict__ nbr,
-                               const uint8_t *__restrict__ dmask, const int64_t *__restrict__ rowptr, int32_t *col) {
+__global__ void expand_columns(int64_t n_nodes, int nd, bool blockdiag, const int64_t *__restrict__ noff,
+                               const int32_t *__restrict__ nbr, const uint8_t *__restrict__ dmask,
+                               const int64_t *__restrict__ rowptr, int32_t *col) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n_nodes * nd) return;
   const int64_t n = i / nd, k = i % nd;
@@ -141,9 +164,13 @@ __global__ void expand_columns(int64_t n_nodes, int nd, const int64_t *__restric
     col[p] = (int32_t)i;
     return;
   }
-  for (int64_t t = noff[n]; t < noff[n + 1]; ++t)
-    for (int l = 0; l < nd; ++l) col[p++] = nbr[t] * nd + l;
-  (void)k;
+  for (int64_t t = noff[n]; t < noff[n + 1]; ++t) {
+    if (blockdiag) {
+      col[p++] = (int32_t)(nbr[t] * nd + k);  // component k couples to component k only
+    } else {
+      for (int l = 0; l < nd; ++l) col[p++] = nbr[t] * nd + l;
+    }
+  }
 }
 
 // y = A x with L threads per row.  Each lane first issues U independent (value, column) loads,
@@ -292,6 +319,7 @@ mf_status operator_diagonal(const mf_mesh *m, double *diag, cudaStream_t s) {
   MF_CUDA(cudaMemsetAsync(diag, 0, m->n_dof * sizeof(double), s));
   const MeshView v = m->view();
   if (m->physics == MF_LAPLACE) launch_diag<MF_LAPLACE>(m, v, diag, s);
+  else if (m->physics == MF_VECTOR_LAPLACE) launch_diag<MF_VECTOR_LAPLACE>(m, v, diag, s);
   else launch_diag<MF_ELASTICITY>(m, v, diag, s);
   if (m->n_dnodes) dirichlet_diag<<<blocks_for(m->n_dnodes * m->ndpn), kThreads, 0, s>>>(m->dnodes, m->n_dnodes, m->ndpn, diag);
   MF_CUDA(cudaGetLastError());
@@ -304,6 +332,7 @@ extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr 
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   const int nd = m->ndpn;
+  const bool blockdiag = m->physics == MF_VECTOR_LAPLACE;  // components do not couple
   std::vector<uint8_t> hmask(m->n_nodes);
   MF_CUDA(cudaMemcpyAsync(hmask.data(), m->dmask, m->n_nodes, cudaMemcpyDeviceToHost, s));
   MF_CUDA(cudaStreamSynchronize(s));
@@ -314,7 +343,7 @@ extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr 
   const int64_t n_rows = m->n_nodes * nd;
   std::vector<int64_t> rowptr(n_rows + 1, 0);
   for (int64_t n = 0; n < m->n_nodes; ++n)
-    for (int k = 0; k < nd; ++k) rowptr[n * nd + k + 1] = hmask[n] ? 1 : (noff[n + 1] - noff[n]) * nd;
+    for (int k = 0; k < nd; ++k) rowptr[n * nd + k + 1] = hmask[n] ? 1 : (noff[n + 1] - noff[n]) * (blockdiag ? 1 : nd);
   for (int64_t r = 0; r < n_rows; ++r) rowptr[r + 1] += rowptr[r];
   const int64_t nnz = rowptr[n_rows];
   MF_ARG(nnz < (int64_t)INT32_MAX * 4, "mf_assemble_csr: matrix too large");
@@ -346,10 +375,12 @@ extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr 
   MF_CUDA(cudaMemcpyAsync(A->rowptr, rowptr.data(), rowptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   MF_CUDA(cudaMemcpyAsync(d_noff, noff.data(), noff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   if (!nbr.empty()) MF_CUDA(cudaMemcpyAsync(d_nbr, nbr.data(), nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-  expand_columns<<<blocks_for(n_rows), kThreads, 0, s>>>(m->n_nodes, nd, d_noff, d_nbr, m->dmask, A->rowptr, A->col);
+  expand_columns<<<blocks_for(n_rows), kThreads, 0, s>>>(m->n_nodes, nd, blockdiag, d_noff, d_nbr, m->dmask, A->rowptr,
+                                                          A->col);
   MF_CUDA(cudaMemsetAsync(A->val, 0, nnz * sizeof(double), s));
   const MeshView v = m->view();
   if (m->physics == MF_LAPLACE) launch_fill<MF_LAPLACE>(m, v, A, s);
+  else if (m->physics == MF_VECTOR_LAPLACE) launch_fill<MF_VECTOR_LAPLACE>(m, v, A, s);
   else launch_fill<MF_ELASTICITY>(m, v, A, s);
   if (m->n_dnodes) dirichlet_unit<<<blocks_for(m->n_dnodes * nd), kThreads, 0, s>>>(m->dnodes, m->n_dnodes, nd, A->rowptr, A->val);
   MF_CUDA(cudaGetLastError());

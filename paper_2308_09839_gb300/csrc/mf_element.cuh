@@ -98,6 +98,50 @@ __device__ __forceinline__ void laplace_element(const R X[8][3], const R u[8], R
   laplace_qp<R, 7>(X, u, kappa, v);
 }
 
+// Vector Laplace (Eq. 5) at one quadrature point: the flux of Eq. 7 for each of the three
+// components, with the geometry (J, adj J, det J) shared between them.
+template <typename R, int Q>
+__device__ __forceinline__ void vector_laplace_qp(const R X[8][3], const R u[8][3], R kappa, R v[8][3]) {
+  R J[3][3], C[3][3];
+  jacobian<R, Q>(X, J);
+  const R det = adjugate(J, C);
+  const R scale = kappa / det;  // w_q = 1
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    R g[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R s = 0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) s += u[a][k] * (R)dN(Q, a, j);
+      g[j] = s;
+    }
+    R t[3], f[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[i] = C[0][i] * g[0] + C[1][i] * g[1] + C[2][i] * g[2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) f[j] = scale * (C[j][0] * t[0] + C[j][1] * t[1] + C[j][2] * t[2]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) v[a][k] += (R)dN(Q, a, 0) * f[0] + (R)dN(Q, a, 1) * f[1] + (R)dN(Q, a, 2) * f[2];
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void vector_laplace_element(const R X[8][3], const R u[8][3], R kappa, R v[8][3]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[a][k] = 0;
+  vector_laplace_qp<R, 0>(X, u, kappa, v);
+  vector_laplace_qp<R, 1>(X, u, kappa, v);
+  vector_laplace_qp<R, 2>(X, u, kappa, v);
+  vector_laplace_qp<R, 3>(X, u, kappa, v);
+  vector_laplace_qp<R, 4>(X, u, kappa, v);
+  vector_laplace_qp<R, 5>(X, u, kappa, v);
+  vector_laplace_qp<R, 6>(X, u, kappa, v);
+  vector_laplace_qp<R, 7>(X, u, kappa, v);
+}
+
 // Isotropic elasticity, Algorithm 1 at one quadrature point:
 //   grad u = (sum_a u_a (x) grad_ref phi_a) J^{-1};  sigma = lam tr(eps) I + 2 mu eps, eps = sym grad u;
 //   sigma *= w |J|;  P = sigma J^{-T};  v_a += P grad_ref phi_a.

@@ -170,6 +170,60 @@ __device__ void laplace_general(typename N::T u[8], const typename N::T del[8][3
   unmodes<N>(A, u);
 }
 
+// Vector Laplace element (Eq. 5: the flux of Eq. 7 for each component, geometry shared), in place
+// on u[component][corner]; slot accumulators in shared memory as for elasticity.
+template <class N>
+__device__ void vector_laplace_general(typename N::T u[3][8], const typename N::T del[8][3], const typename N::T hh[3],
+                                       typename N::T kappa, typename N::S *Ash, int stride) {
+  using T = typename N::T;
+  T cd[3][8];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) cd[i][a] = del[a][i];
+    modes<N>(cd[i]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) modes<N>(u[c]);
+  for (int t = 0; t < 36; ++t) N::st(Ash[t * stride], N::zero());
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    const int s[3] = {(q & 1) ? 1 : -1, (q & 2) ? 1 : -1, (q & 4) ? 1 : -1};
+    T J[3][3], C[3][3];
+    jac<N>(cd, hh, s, J);
+    const T det = adj<N>(J, C);
+    const T sc = ndiv<N>(kappa, det);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T gu[3], t[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gu[j] = dref<N>(u[c], j, s);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        t[k] = N::add(N::add(N::mul(C[0][k], gu[0]), N::mul(C[1][k], gu[1])), N::mul(C[2][k], gu[2]));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const T f = N::mul(sc, N::add(N::add(N::mul(C[j][0], t[0]), N::mul(C[j][1], t[1])), N::mul(C[j][2], t[2])));
+        T A4[4];
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) A4[tt] = N::ld(Ash[((c * 3 + j) * 4 + tt) * stride]);
+        accum<N>(A4, f, j, s);
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) N::st(Ash[((c * 3 + j) * 4 + tt) * stride], A4[tt]);
+      }
+    }
+  }
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    T A[3][4];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) A[j][t] = N::ld(Ash[((c * 3 + j) * 4 + t) * stride]);
+    unmodes<N>(A, u[c]);
+  }
+}
+
 // Elasticity element (Algorithm 1), in place on u[component][corner].  The slot accumulators of
 // the three output components live in shared memory (per-thread slice `Ash`) to bound registers.
 template <class N>
@@ -240,7 +294,7 @@ __device__ void elasticity_general(typename N::T u[3][8], const typename N::T de
 
 template <int PHYS, class N, int EX, int EY>
 struct GenSmem {
-  static constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  static constexpr int ND = phys_ndpn(PHYS);
   static constexpr int NP = (EX + 1) * (EY + 1), NACC = (EX - 1) * (EY - 1) * ND;
   typename N::S up[2][NP * ND];
   typename N::S dp[2][NP * 3];
@@ -256,7 +310,7 @@ __global__ void __launch_bounds__(EX *EY, 1) gen_apply(GenArgs g, const typename
   using T = typename N::T;
   using S = typename N::S;
   using IO = typename N::IO;
-  constexpr int ND = PHYS == MF_LAPLACE ? 1 : 3;
+  constexpr int ND = phys_ndpn(PHYS);
   constexpr int NT = EX * EY, TX = EX - 1, TY = EY - 1, PX = EX + 1, PY = EY + 1, NP = PX * PY;
   constexpr int LOADS = (NP + NT - 1) / NT;
   constexpr int NACC = TX * TY * ND;
@@ -348,6 +402,8 @@ __global__ void __launch_bounds__(EX *EY, 1) gen_apply(GenArgs g, const typename
       const T hh[3] = {hxh, hyh, N::from2(__ldg(g.hh + g.nx + g.ny + ez))};
       if constexpr (PHYS == MF_LAPLACE) {
         laplace_general<N>(v[0], del, hh, N::from2(__ldg(g.mat + e)));
+      } else if constexpr (PHYS == MF_VECTOR_LAPLACE) {
+        vector_laplace_general<N>(v, del, hh, N::from2(__ldg(g.mat + e)), sm.ash + tid, NT);
       } else {
         elasticity_general<N>(v, del, hh, N::from2(__ldg(g.mat + 2 * e)), N::from2(__ldg(g.mat + 2 * e + 1)),
                               sm.ash + tid, NT);
@@ -422,6 +478,7 @@ __global__ void gen_mat_pairs(const double *m, int64_t n, float2 *out) {
 template <int PHYS, class N> struct GenShape;
 template <class N> struct GenShape<MF_LAPLACE, N> { static constexpr int EX = 32, EY = 8; };
 template <class N> struct GenShape<MF_ELASTICITY, N> { static constexpr int EX = 32, EY = 8; };
+template <class N> struct GenShape<MF_VECTOR_LAPLACE, N> { static constexpr int EX = 32, EY = 8; };
 
 template <int PHYS, class N>
 mf_status gen_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s, const int *skip) {
@@ -463,7 +520,7 @@ mf_status gen_setup(mf_mesh *m, cudaStream_t s) {
   gen_axes<<<blocks_for(n), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->gen_axis);
   gen_delta<<<blocks_for(m->n_nodes), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->gen_delta);
   if (!m->mat_pairs) {
-    const int64_t nm = m->n_cells * (m->physics == MF_LAPLACE ? 1 : 2);
+    const int64_t nm = m->n_cells * phys_nmat(m->physics);
     MF_CUDA(cudaMalloc(&m->mat_pairs, nm * sizeof(float2)));
     gen_mat_pairs<<<blocks_for(nm), kThreads, 0, s>>>(m->mat, nm, m->mat_pairs);
   }
@@ -475,10 +532,12 @@ mf_status gen_setup(mf_mesh *m, cudaStream_t s) {
 
 mf_status gen_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip) {
   if (m->physics == MF_LAPLACE) return gen_launch<MF_LAPLACE, NumDW>(m, x, y, s, skip);
+  if (m->physics == MF_VECTOR_LAPLACE) return gen_launch<MF_VECTOR_LAPLACE, NumDW>(m, x, y, s, skip);
   return gen_launch<MF_ELASTICITY, NumDW>(m, x, y, s, skip);
 }
 
 mf_status gen_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip) {
   if (m->physics == MF_LAPLACE) return gen_launch<MF_LAPLACE, NumF32>(m, x, y, s, skip);
+  if (m->physics == MF_VECTOR_LAPLACE) return gen_launch<MF_VECTOR_LAPLACE, NumF32>(m, x, y, s, skip);
   return gen_launch<MF_ELASTICITY, NumF32>(m, x, y, s, skip);
 }

@@ -9,6 +9,12 @@
 
 #include "mf.h"
 
+// Physics traits: DoFs per node, cell constants per cell, and whether the element arithmetic is the
+// scalar Laplace one (applied to each component for the vector Laplacian of Eq. 5).
+__host__ __device__ constexpr int phys_ndpn(int p) { return p == MF_LAPLACE ? 1 : 3; }
+__host__ __device__ constexpr int phys_nmat(int p) { return p == MF_ELASTICITY ? 2 : 1; }
+__host__ __device__ constexpr bool phys_is_laplace(int p) { return p != MF_ELASTICITY; }
+
 // ------------------------------------------------------------------------------------ errors ----
 void mf_set_error(const char *fmt, ...);
 void mf_clear_error();

@@ -1,5 +1,5 @@
-// Face-marching apply on tensor-product boxes (auto variant, one right-hand side), scalar Laplace
-// and isotropic elasticity.
+// Face-marching apply on tensor-product boxes (auto variant): scalar Laplace,
+// vector Laplace (the scalar element operator on each component, Eq. 5) and isotropic elasticity.
 //
 // The arithmetic is that of tile::laplace_apply / tile::elasticity_apply (Eqs. 7 and 9 with 2x2x2
 // Gauss, rewritten exactly in the Walsh-Hadamard monomial basis: A^e = H^T D_e H with D_e diagonal
@@ -22,7 +22,8 @@
 //
 // A CTA covers EX x EY element columns = an (EX-1) x (EY-1) block of owned nodes plus one halo
 // ring of elements on the low sides (recomputed by the neighbouring CTA), over a z-segment of
-// node planes [k0, k1) (plus the element layer below k0).  One __syncthreads per plane.
+// node planes [k0, k1) (plus the element layer below k0), for one right-hand side (blockIdx.y; the
+// vectors of a multi-RHS apply are [node][rhs][comp]).  One __syncthreads per plane.
 #pragma once
 
 #include "mf_tile.cuh"
@@ -48,8 +49,8 @@ struct MarchSmem {
   typename N::S xrow[2][NC * EX * EY];            // partial sums of the top node row of each face
 };
 
-// PHYS = MF_LAPLACE (Eq. 7) or MF_ELASTICITY (Eq. 9, Algorithm 1); vectors hold NC values per
-// node (x, y, z components interleaved for elasticity).
+// PHYS = MF_LAPLACE (Eq. 7), MF_VECTOR_LAPLACE (Eq. 5) or MF_ELASTICITY (Eq. 9, Algorithm 1);
+// vectors hold NC values per node (x, y, z components interleaved for the vector operators).
 template <int PHYS, class N, int EX, int EY, int MINB>
 __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const typename N::IO *__restrict__ x,
                                                             typename N::IO *__restrict__ y,
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
   static_assert(EX == 32, "a warp is one row of element columns");
   using T = typename N::T;
   using IO = typename N::IO;
-  constexpr int NC = PHYS == MF_LAPLACE ? 1 : 3;
+  constexpr int NC = phys_ndpn(PHYS);
   constexpr int NT = EX * EY, PX = EX + 1, NP = (EX + 1) * (EY + 1), TX = EX - 1, TY = EY - 1;
   constexpr int LOADS = (NP + NT - 1) / NT;
   __shared__ MarchSmem<NC, N, EX, EY> sm;
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
 
   const int tid = threadIdx.x;
   const int item = blockIdx.x;
+  const int64_t rr = g.r0 + blockIdx.y;  // right-hand side of this CTA ([node][rhs][comp] vectors)
   const int bx = item % g.tiles_x;
   const int by = (item / g.tiles_x) % g.tiles_y;
   const int bz = item / (g.tiles_x * g.tiles_y);
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
     ihy = N::from2(__ldg(g.ihy + ey));
   }
   T hy_ihx = N::zero(), hx_ihy = N::zero(), hxhy = N::zero();
-  if constexpr (PHYS == MF_LAPLACE) {
+  if constexpr (phys_is_laplace(PHYS)) {
     hy_ihx = N::mul(hy, ihx);
     hx_ihy = N::mul(hx, ihy);
     hxhy = N::mul(hx, hy);
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
       const int64_t node = ix + (int64_t)NXP * (iy + (int64_t)NYP * k);
       dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) xr[l][c] = ok ? __ldg(x + node * NC + c) : (IO)0;
+      for (int c = 0; c < NC; ++c) xr[l][c] = ok ? __ldg(x + (node * g.nrhs + rr) * NC + c) : (IO)0;
     }
   };
   auto stage = [&](int k) {
@@ -154,8 +156,32 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
     for (int m = 0; m < 4; ++m) Gc[c][m] = N::zero();
   __syncthreads();  // everyone has read plane s_lo before its buffer is reused
 
+  // material of the element: loaded one step ahead for elasticity; for Laplace (64 registers at
+  // two 512-thread CTAs per SM) at the top of the step, ahead of the face transform
+  constexpr int NM = phys_nmat(PHYS);
+  constexpr bool PREFETCH = PHYS != MF_LAPLACE;
+  const int e_step = g.nx * g.ny * NM;
+  const float2 *matp = g.mat + NM * (ex + (int64_t)g.nx * (ey + (int64_t)g.ny * s_lo));
+  float2 mat_next[NM];
+#pragma unroll
+  for (int q = 0; q < NM; ++q)
+    mat_next[q] = (PREFETCH && ein && s_lo < g.nz) ? __ldg(matp + q) : make_float2(0.f, 0.f);
+
   for (int ez = s_lo; ez <= s_hi; ++ez) {
     const bool elem = ein && ez < g.nz;
+    float2 mat_cur[NM];
+    if constexpr (PREFETCH) {
+      matp += e_step;
+#pragma unroll
+      for (int q = 0; q < NM; ++q) {
+        mat_cur[q] = mat_next[q];
+        mat_next[q] = (ein && ez + 1 < g.nz) ? __ldg(matp + q) : make_float2(0.f, 0.f);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NM; ++q) mat_cur[q] = elem ? __ldg(matp + q) : make_float2(0.f, 0.f);
+      matp += e_step;
+    }
     T Ft[NC][4], S[NC][4];
     if (ez < g.nz) face_fwd(ez + 1, Ft);
     else {
@@ -165,24 +191,26 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
         for (int m = 0; m < 4; ++m) Ft[c][m] = N::zero();
     }
     if (elem) {
-      const int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
       const T hz = N::from2(__ldg(g.hz + ez)), ihz = N::from2(__ldg(g.ihz + ez));
       // o[l][m]: D times the 8 modes; the z butterfly gives mode m (m < 4) as Fb + Ft and mode
       // m + 4 as Ft - Fb; mode 0 has D = 0
       T o[NC][8];
-      if constexpr (PHYS == MF_LAPLACE) {
-        const tile::LapCoef<N> cf = tile::laplace_coef<N>(N::from2(__ldg(g.mat + e)), hy_ihx, hx_ihy, hxhy, hz, ihz);
-        o[0][1] = N::mul(cf.s1, N::add(Fb[0][1], Ft[0][1]));
-        o[0][2] = N::mul(cf.s2, N::add(Fb[0][2], Ft[0][2]));
-        o[0][3] = N::mul(cf.s12, N::add(Fb[0][3], Ft[0][3]));
-        o[0][4] = N::mul(cf.s3, N::sub(Ft[0][0], Fb[0][0]));
-        o[0][5] = N::mul(cf.s13, N::sub(Ft[0][1], Fb[0][1]));
-        o[0][6] = N::mul(cf.s23, N::sub(Ft[0][2], Fb[0][2]));
-        o[0][7] = N::mul(cf.s123, N::sub(Ft[0][3], Fb[0][3]));
+      if constexpr (phys_is_laplace(PHYS)) {  // Laplace; vector Laplace: the same D per component
+        const tile::LapCoef<N> cf = tile::laplace_coef<N>(N::from2(mat_cur[0]), hy_ihx, hx_ihy, hxhy, hz, ihz);
+#pragma unroll
+        for (int l = 0; l < NC; ++l) {
+          o[l][1] = N::mul(cf.s1, N::add(Fb[l][1], Ft[l][1]));
+          o[l][2] = N::mul(cf.s2, N::add(Fb[l][2], Ft[l][2]));
+          o[l][3] = N::mul(cf.s12, N::add(Fb[l][3], Ft[l][3]));
+          o[l][4] = N::mul(cf.s3, N::sub(Ft[l][0], Fb[l][0]));
+          o[l][5] = N::mul(cf.s13, N::sub(Ft[l][1], Fb[l][1]));
+          o[l][6] = N::mul(cf.s23, N::sub(Ft[l][2], Fb[l][2]));
+          o[l][7] = N::mul(cf.s123, N::sub(Ft[l][3], Fb[l][3]));
+        }
       } else {
         const T h[3] = {hx, hy, hz}, ih[3] = {ihx, ihy, ihz};
         const tile::ElCoef<N> cf =
-            tile::elasticity_coef<N>(N::from2(__ldg(g.mat + 2 * e)), N::from2(__ldg(g.mat + 2 * e + 1)), h, ih);
+            tile::elasticity_coef<N>(N::from2(mat_cur[0]), N::from2(mat_cur[NM - 1]), h, ih);
         T c[3][8];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -226,19 +254,21 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
       rb[l] = N::add(v00, shfl_up1<N>(v10));
       N::st(sm.xrow[ez & 1][l * NT + tid], N::add(v01, shfl_up1<N>(v11)));
     }
+    const bool wr = own && ez >= k0;
+    const int64_t node = ex + (int64_t)NXP * (ey + (int64_t)NYP * ez);
+    const bool dir = wr && __ldg(g.dmask + node) != 0;  // issued before the barrier
     if (ez + 2 <= plim) {
       stage(ez + 2);  // plane ez's buffer: its last reader finished before the previous barrier
       if (ez + 3 <= plim) fetch(ez + 3);
     }
     __syncthreads();
     // y: node (ex, ey) gets the bottom row of this thread's faces and the top row of the row below
-    if (own && ez >= k0) {
-      const int64_t node = ex + (int64_t)NXP * (ey + (int64_t)NYP * ez);
-      const bool dir = __ldg(g.dmask + node) != 0;
+    if (wr) {
 #pragma unroll
       for (int l = 0; l < NC; ++l) {
         const T tot = N::add(rb[l], N::ld(sm.xrow[ez & 1][l * NT + tid - EX]));
-        y[node * NC + l] = dir ? x[node * NC + l] : N::out(tot);
+        const int64_t vi = (node * g.nrhs + rr) * NC + l;
+        y[vi] = dir ? x[vi] : N::out(tot);
       }
     }
 #pragma unroll
@@ -251,5 +281,6 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
 // Launch shapes: EX = 32 element columns per warp row, EY rows, MINB resident CTAs per SM.
 template <int PHYS, class N> struct MarchShape { static constexpr int EX = 32, EY = 16, MINB = 2; };
 template <class N> struct MarchShape<MF_ELASTICITY, N> { static constexpr int EX = 32, EY = 8, MINB = 1; };
+template <class N> struct MarchShape<MF_VECTOR_LAPLACE, N> { static constexpr int EX = 32, EY = 8, MINB = 2; };
 
 }  // namespace march

@@ -97,7 +97,7 @@ __global__ void validate_kernel(MeshView m, int physics, ValidateOut *out) {
       if (!affine) atomicOr(&out->not_affine, 1);
     }
   }
-  if (physics == MF_LAPLACE) {
+  if (phys_is_laplace(physics)) {
     double k = m.mat[e];
     if (!(k > 0.0) || !isfinite(k)) flags |= BAD_MAT;
   } else {
@@ -114,7 +114,7 @@ __global__ void validate_kernel(MeshView m, int physics, ValidateOut *out) {
 __global__ void material_kernel(const double *in, double *out, float *out32, int64_t n_cells, int physics) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n_cells) return;
-  if (physics == MF_LAPLACE) {
+  if (phys_is_laplace(physics)) {
     out[e] = in[e];
     out32[e] = (float)in[e];
   } else {
@@ -223,7 +223,8 @@ extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells
   mf_clear_error();
   MF_ARG(out != nullptr, "mf_setup_mesh: out is NULL");
   *out = nullptr;
-  MF_ARG(physics == MF_LAPLACE || physics == MF_ELASTICITY, "mf_setup_mesh: unknown physics %d", physics);
+  MF_ARG(physics == MF_LAPLACE || physics == MF_ELASTICITY || physics == MF_VECTOR_LAPLACE,
+         "mf_setup_mesh: unknown physics %d", physics);
   MF_ARG(coords && mat, "mf_setup_mesh: coords and mat are required");
   MF_ARG(n_nodes >= 8 && n_cells >= 1, "mf_setup_mesh: need n_nodes >= 8 and n_cells >= 1");
   MF_ARG(n_nodes < (int64_t)INT32_MAX, "mf_setup_mesh: n_nodes must fit int32");
@@ -236,7 +237,7 @@ extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells
   mf_mesh *m = new mf_mesh();
   MF_CUDA(cudaGetDevice(&m->device));
   m->physics = physics;
-  m->ndpn = physics == MF_LAPLACE ? 1 : 3;
+  m->ndpn = phys_ndpn(physics);
   m->n_nodes = n_nodes;
   m->n_cells = n_cells;
   m->n_dof = n_nodes * m->ndpn;
@@ -244,7 +245,7 @@ extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells
   m->nx = cells ? 0 : nx;
   m->ny = cells ? 0 : ny;
   m->nz = cells ? 0 : nz;
-  const int nmat = physics == MF_LAPLACE ? 1 : 2;
+  const int nmat = phys_nmat(physics);
   mf_status st = MF_OK;
 #define SETUP_TRY(expr)               \
   do {                                \

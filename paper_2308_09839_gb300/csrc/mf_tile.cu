@@ -1,6 +1,7 @@
-// Setup of the tensor-product geometry and launch of the standalone tile apply (the kernels live in
-// mf_tile.cuh; see there for what they compute and how).
+// Setup of the tensor-product geometry and launch of the face-marching apply (single and
+// multi-RHS; the kernels live in mf_march.cuh and mf_tile.cuh).
 #include <algorithm>
+#include <atomic>
 
 #include "mf_march.cuh"
 #include "mf_tile.cuh"
@@ -73,7 +74,7 @@ mf_status tile_setup(mf_mesh *m, cudaStream_t s) {
   const int n = m->nx + m->ny + m->nz;
   MF_CUDA(cudaMalloc(&m->tp_axis, 2 * n * sizeof(float2)));
   tp_axes<<<blocks_for(n), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->tp_axis);
-  const int64_t nm = m->n_cells * (m->physics == MF_LAPLACE ? 1 : 2);
+  const int64_t nm = m->n_cells * phys_nmat(m->physics);
   MF_CUDA(cudaMalloc(&m->mat_pairs, nm * sizeof(float2)));
   mat_pairs<<<blocks_for(nm), kThreads, 0, s>>>(m->mat, nm, m->mat_pairs);
   MF_CUDA(cudaGetLastError());
@@ -82,33 +83,23 @@ mf_status tile_setup(mf_mesh *m, cudaStream_t s) {
   return MF_OK;
 }
 
-template <int PHYS, class N, int NR = 1>
-static mf_status tile_launch_one(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
-                                 const int *skip, int nrhs = 1, int r0 = 0) {
-  using TS = TileShape<PHYS, N>;
-  TileArgs g = make_tile_args(m, TS::EX, TS::EY, m->tile_seg);
-  g.nrhs = nrhs;
-  g.r0 = r0;
-  const int smem = (int)sizeof(TileSmem<PHYS, N, TS::EX, TS::EY, NR>);
-  auto kern = tile_apply<PHYS, N, TS::EX, TS::EY, TS::MINB, NR>;
-  if (smem > 48 * 1024) {
-    static bool set = false;
-    if (!set) {
-      MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      set = true;
-    }
-  }
-  kern<<<tile_items(g), TS::EX * TS::EY, smem, s>>>(g, x, y, skip);
-  return MF_OK;
-}
-
-// One right-hand side: the face-marching kernels (mf_march.cuh).
+// The face-marching kernels (mf_march.cuh): one launch for `nrhs` right-hand sides of
+// [node][rhs][comp] vectors (grid.y = right-hand side).
 template <int PHYS, class N>
 static mf_status march_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
-                              const int *skip) {
+                              const int *skip, int nrhs = 1) {
   using MS = march::MarchShape<PHYS, N>;
-  TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg);
-  march::march_apply<PHYS, N, MS::EX, MS::EY, MS::MINB><<<tile_items(g), MS::EX * MS::EY, 0, s>>>(g, x, y, skip);
+  auto kern = march::march_apply<PHYS, N, MS::EX, MS::EY, MS::MINB>;
+  static std::atomic<int> resident{0};  // CTAs per SM: a property of the kernel, same for every caller
+  if (resident.load() == 0) {
+    int r = 0;
+    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, MS::EX * MS::EY, 0));
+    resident.store(std::max(r, 1));
+  }
+  TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident.load(), nrhs);
+  g.nrhs = nrhs;
+  g.r0 = 0;
+  kern<<<dim3(tile_items(g), nrhs), MS::EX * MS::EY, 0, s>>>(g, x, y, skip);
   return MF_OK;
 }
 
@@ -117,28 +108,19 @@ static mf_status tile_launch(const mf_mesh *m, const typename N::IO *x, typename
                              const int *skip) {
   mf_count_launches(1);
   if (m->physics == MF_LAPLACE) MF_TRY((march_launch<MF_LAPLACE, N>(m, x, y, s, skip)));
+  else if (m->physics == MF_VECTOR_LAPLACE) MF_TRY((march_launch<MF_VECTOR_LAPLACE, N>(m, x, y, s, skip)));
   else MF_TRY((march_launch<MF_ELASTICITY, N>(m, x, y, s, skip)));
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }
 
-// Multi right-hand-side apply on [node][rhs][comp] vectors: passes of kMultiR right-hand sides,
-// each computing the element coefficients once and applying them to every right-hand side of the
-// pass (a final pass takes the remainder one at a time).
-constexpr int kMultiR = 4;
-
+// Multi right-hand-side apply on [node][rhs][comp] vectors: one face-marching launch over all
+// right-hand sides; every column is computed exactly as by the single apply.
 mf_status tile_apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s) {
-  int r = 0;
-  for (; r + kMultiR <= nrhs; r += kMultiR) {
-    mf_count_launches(1);
-    if (m->physics == MF_LAPLACE) MF_TRY((tile_launch_one<MF_LAPLACE, NumDW, kMultiR>(m, x, y, s, nullptr, nrhs, r)));
-    else MF_TRY((tile_launch_one<MF_ELASTICITY, NumDW, kMultiR>(m, x, y, s, nullptr, nrhs, r)));
-  }
-  for (; r < nrhs; ++r) {
-    mf_count_launches(1);
-    if (m->physics == MF_LAPLACE) MF_TRY((tile_launch_one<MF_LAPLACE, NumDW, 1>(m, x, y, s, nullptr, nrhs, r)));
-    else MF_TRY((tile_launch_one<MF_ELASTICITY, NumDW, 1>(m, x, y, s, nullptr, nrhs, r)));
-  }
+  mf_count_launches(1);
+  if (m->physics == MF_LAPLACE) MF_TRY((march_launch<MF_LAPLACE, NumDW>(m, x, y, s, nullptr, nrhs)));
+  else if (m->physics == MF_VECTOR_LAPLACE) MF_TRY((march_launch<MF_VECTOR_LAPLACE, NumDW>(m, x, y, s, nullptr, nrhs)));
+  else MF_TRY((march_launch<MF_ELASTICITY, NumDW>(m, x, y, s, nullptr, nrhs)));
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }

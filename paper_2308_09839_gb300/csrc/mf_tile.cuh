@@ -1,5 +1,6 @@
-// Tile machinery shared by the standalone apply (mf_tile.cu) and the batched persistent solver
-// (mf_batched.cu).
+// Tensor-product element arithmetic (number types, Walsh-Hadamard transforms, Laplace and elasticity
+// coefficients) shared by the face-marching kernels (mf_march.cuh), and the tile work items of the
+// batched persistent solver (mf_batched.cu).
 #pragma once
 // Matrix-free apply for structured boxes whose cells are axis-aligned (tensor-product geometry),
 // FP64-accurate on the FP32 pipes ("auto" variant).
@@ -246,7 +247,7 @@ struct TileArgs {
 // Shared-memory footprint of one tile (staged input planes and output-plane accumulators).
 template <int PHYS, class N, int EX, int EY, int NR = 1>
 struct TileSmem {
-  static constexpr int ND = (PHYS == MF_LAPLACE ? 1 : 3) * NR;
+  static constexpr int ND = phys_ndpn(PHYS) * NR;
   static constexpr int NP = (EX + 1) * (EY + 1), NACC = (EX - 1) * (EY - 1) * ND;
   typename N::S up[2][NP * ND];
   typename N::S acc[2][NACC];
@@ -263,7 +264,7 @@ __device__ __forceinline__ void tile_item(const TileArgs &g, int item, const typ
   using T = typename N::T;
   using S = typename N::S;
   using IO = typename N::IO;
-  constexpr int NC = PHYS == MF_LAPLACE ? 1 : 3;  // components per node and right-hand side
+  constexpr int NC = phys_ndpn(PHYS);  // components per node and right-hand side
   constexpr int ND = NC * NR;                     // values per node handled by this pass
   constexpr int NT = EX * EY, TX = EX - 1, TY = EY - 1, PX = EX + 1, PY = EY + 1, NP = PX * PY;
   constexpr int LOADS = (NP + NT - 1) / NT;
@@ -346,10 +347,10 @@ __device__ __forceinline__ void tile_item(const TileArgs &g, int item, const typ
     // evaluate and accumulate (one right-hand side's values live in registers at a time)
     const int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
     const T hz = N::from2(__ldg(g.hz + ez)), ihz = N::from2(__ldg(g.ihz + ez));
-    using Coef = std::conditional_t<PHYS == MF_LAPLACE, LapCoef<N>, ElCoef<N>>;
+    using Coef = std::conditional_t<phys_is_laplace(PHYS), LapCoef<N>, ElCoef<N>>;
     Coef cf;
     if (ein) {
-      if constexpr (PHYS == MF_LAPLACE) {
+      if constexpr (phys_is_laplace(PHYS)) {
         cf = laplace_coef<N>(N::from2(__ldg(g.mat + e)), hy_ihx, hx_ihy, hxhy, hz, ihz);
       } else {
         const T h[3] = {hx, hy, hz}, ih[3] = {ihx, ihy, ihz};
@@ -370,8 +371,12 @@ __device__ __forceinline__ void tile_item(const TileArgs &g, int item, const typ
 #pragma unroll
           for (int c = 0; c < NC; ++c) v[c][a] = N::ld(u[p * ND + r * NC + c]);
         }
-        if constexpr (PHYS == MF_LAPLACE) laplace_apply<N>(cf, v[0]);
-        else elasticity_apply<N>(cf, v);
+        if constexpr (phys_is_laplace(PHYS)) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) laplace_apply<N>(cf, v[c]);
+        } else {
+          elasticity_apply<N>(cf, v);
+        }
       }
 #pragma unroll
       for (int ay = 0; ay < 2; ++ay) {
@@ -397,26 +402,38 @@ __device__ __forceinline__ void tile_item(const TileArgs &g, int item, const typ
   if (s_hi + 1 == g.nz && g.nz >= k0 && g.nz < k1) write_plane(g.nz);
 }
 
-template <int PHYS, class N, int EX, int EY, int MINB, int NR = 1>
-__global__ void __launch_bounds__(EX *EY, MINB) tile_apply(TileArgs g, const typename N::IO *__restrict__ x,
-                                                           typename N::IO *__restrict__ y,
-                                                           const int *__restrict__ skip) {
-  extern __shared__ __align__(16) unsigned char tile_smem_raw[];
-  auto &sm = *reinterpret_cast<TileSmem<PHYS, N, EX, EY, NR> *>(tile_smem_raw);
-  if (skip && *skip) return;
-  tile_item<PHYS, N, EX, EY, false, NR>(g, blockIdx.x, x, y, sm);
-}
-
 // Tile shapes (elements per slab row x rows) and minimum resident CTAs per SM.
 template <int PHYS, class N> struct TileShape;
 template <> struct TileShape<MF_LAPLACE, NumDW> { static constexpr int EX = 32, EY = 16, MINB = 2; };
 template <> struct TileShape<MF_LAPLACE, NumF32> { static constexpr int EX = 32, EY = 16, MINB = 2; };
 template <> struct TileShape<MF_ELASTICITY, NumDW> { static constexpr int EX = 32, EY = 8, MINB = 2; };
 template <> struct TileShape<MF_ELASTICITY, NumF32> { static constexpr int EX = 32, EY = 8, MINB = 2; };
+template <class N> struct TileShape<MF_VECTOR_LAPLACE, N> { static constexpr int EX = 32, EY = 8, MINB = 2; };
+
+// Segment length from a wave model: with R CTAs resident at a time, nseg segments of seg = ceil((nz
+// + 1) / nseg) planes take about ceil(cols * nseg / R) waves of (seg + 1) element layers each (the
+// +1 is the recomputed layer below a segment); the smallest estimate wins, ties to fewer segments.
+inline int wave_segment(int cols, int nzp1, int resident_total) {
+  int best_seg = nzp1;
+  long long best = -1;
+  for (int nseg = 1; nseg <= nzp1; ++nseg) {
+    const int seg = (nzp1 + nseg - 1) / nseg;
+    if (nseg > 1 && seg == (nzp1 + nseg - 2) / (nseg - 1)) continue;  // same segment length as before
+    const long long waves = ((long long)cols * nseg + resident_total - 1) / resident_total;
+    const long long cost = waves * (seg + 1);
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_seg = seg;
+    }
+  }
+  return best_seg;
+}
 
 // Grid decomposition of a structured mesh into tile columns and z-segments of `seg` node planes
-// (seg <= 0: enough segments for about four CTAs per SM).
-inline TileArgs make_tile_args(const mf_mesh *m, int EX, int EY, int seg) {
+// (seg <= 0: by the wave model for `resident` CTAs per SM on 152 SMs and `batch` launches' worth
+// of columns (right-hand sides), or, without an occupancy figure, enough segments for about four
+// CTAs per SM).
+inline TileArgs make_tile_args(const mf_mesh *m, int EX, int EY, int seg, int resident = 0, int batch = 1) {
   TileArgs g;
   g.nx = m->nx;
   g.ny = m->ny;
@@ -426,9 +443,13 @@ inline TileArgs make_tile_args(const mf_mesh *m, int EX, int EY, int seg) {
   g.tiles_y = (m->ny + 1 + TY - 1) / TY;
   if (seg <= 0) {
     const int cols = g.tiles_x * g.tiles_y;
-    const int target = 152 * 4;
-    const int nseg = std::max(1, std::min(m->nz + 1, (target + cols - 1) / cols));
-    seg = (m->nz + 1 + nseg - 1) / nseg;
+    if (resident > 0) {
+      seg = wave_segment(cols * batch, m->nz + 1, 152 * resident);
+    } else {
+      const int target = 152 * 4;
+      const int nseg = std::max(1, std::min(m->nz + 1, (target + cols - 1) / cols));
+      seg = (m->nz + 1 + nseg - 1) / nseg;
+    }
   }
   g.seg = std::max(1, std::min(seg, m->nz + 1));
   const int n = m->nx + m->ny + m->nz;

@@ -276,6 +276,17 @@ def elasticity_box(n, jitter=0.0, sigma=0.5, layered=True, seed=0, name=None, ny
                    dirichlet_z0(n, ny, nz), seed, meta=dict(jitter=jitter, sigma=sigma, layered=layered))
 
 
+def vector_laplace_box(n, jitter=0.0, sigma=1.0, layered=False, seed=0, name=None, ny=None, nz=None,
+                       graded=0.0) -> Problem:
+    """Vector Laplace (three components, one coefficient kappa per cell) on the same boxes as
+    ``laplace_box``."""
+    p = laplace_box(n, jitter=jitter, sigma=sigma, layered=layered, seed=seed, ny=ny, nz=nz, graded=graded)
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    return Problem(name or f"vector_laplace_{n}x{ny}x{nz}", "vector_laplace", n, ny, nz, p.coords, p.mat,
+                   p.dirichlet, seed, meta=p.meta)
+
+
 def small_laplace_16(seed=0) -> Problem:
     """16^3 cells, interior nodes jittered by U[-0.2h, 0.2h], kappa ~ lognormal(0, 1) per cell,
     Dirichlet u = 0 on z = 0."""

@@ -21,7 +21,8 @@ lib = C.CDLL(_LIB_PATH)
 
 MF_OK, MF_NOT_CONVERGED = 0, 1
 MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_MESH, MF_ERR_OOM, MF_ERR_BREAKDOWN, MF_ERR_TIMEOUT, MF_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
-MF_LAPLACE, MF_ELASTICITY = 0, 1
+MF_LAPLACE, MF_ELASTICITY, MF_VECTOR_LAPLACE = 0, 1, 2
+PHYSICS = {"laplace": MF_LAPLACE, "elasticity": MF_ELASTICITY, "vector_laplace": MF_VECTOR_LAPLACE}
 MF_VARIANT_AUTO, MF_VARIANT_REFERENCE = 0, 1
 MF_OP_MATFREE, MF_OP_CSR = 0, 1
 MF_PREC_FP64, MF_PREC_MIXED_IR = 0, 1
@@ -53,6 +54,7 @@ _SIGS = {
     "mf_set_apply_variant": (C.c_int, [vp, C.c_int]),
     "mf_apply_laplace": (C.c_int, [vp, vp, vp, vp]),
     "mf_apply_elasticity": (C.c_int, [vp, vp, vp, vp]),
+    "mf_apply_vector_laplace": (C.c_int, [vp, vp, vp, vp]),
     "mf_apply_f32": (C.c_int, [vp, vp, vp, vp]),
     "mf_apply_multi": (C.c_int, [vp, i32, vp, vp, vp]),
     "mf_assemble_csr": (C.c_int, [vp, vp, C.POINTER(vp)]),
@@ -159,6 +161,10 @@ def mf_apply_laplace(h, x, y, stream=None) -> None:
 
 def mf_apply_elasticity(h, x, y, stream=None) -> None:
     check(lib.mf_apply_elasticity(h, _ptr(x), _ptr(y), _stream(stream)), "mf_apply_elasticity")
+
+
+def mf_apply_vector_laplace(h, x, y, stream=None) -> None:
+    check(lib.mf_apply_vector_laplace(h, _ptr(x), _ptr(y), _stream(stream)), "mf_apply_vector_laplace")
 
 
 def mf_apply_f32(h, x, y, stream=None) -> None:
@@ -383,10 +389,11 @@ class Mesh:
     """Owner of an ``mf_mesh`` handle.  Arrays are torch tensors on the current CUDA device."""
 
     def __init__(self, physics: str, coords, mat, dirichlet=None, cells=None, dims=None, stream=None):
-        self.physics = MF_LAPLACE if physics == "laplace" else MF_ELASTICITY
+        self.physics = PHYSICS[physics]
         n_nodes = coords.shape[0]
         n_cells = cells.shape[0] if cells is not None else dims[0] * dims[1] * dims[2]
         nx, ny, nz = dims if (cells is None) else (0, 0, 0)
+        self.dims = (nx, ny, nz)
         self._keep = (coords, mat, dirichlet, cells)
         self.h = mf_setup_mesh(self.physics, n_nodes, n_cells, coords, cells, nx, ny, nz, mat, dirichlet, stream)
         self.info = mf_mesh_query(self.h)
@@ -416,6 +423,8 @@ class Mesh:
             mf_apply_f32(self.h, x, y, stream)
         elif self.physics == MF_LAPLACE:
             mf_apply_laplace(self.h, x, y, stream)
+        elif self.physics == MF_VECTOR_LAPLACE:
+            mf_apply_vector_laplace(self.h, x, y, stream)
         else:
             mf_apply_elasticity(self.h, x, y, stream)
         return y
