@@ -12,16 +12,19 @@
 // geometric multigrid), all convolutions 3x3x3, zero padding, with bias.
 //
 // Kernels:
-//  * conv_mma: implicit-GEMM convolution, M = 128 output voxels per CTA (an 8x4x4 block), N =
-//    output channels, K = 27 taps x input channels.  The CTA stages its (10x6x6) input halo once in
-//    shared memory (channels-last, padded rows against bank conflicts), then for each tap stages
-//    that tap's weights and issues mma.sync m16n8k16 BF16 x BF16 -> FP32.  The same kernel computes
-//    the input gradient (MODE 1) with the mirrored, transposed weights.
+//  * conv_mma: implicit-GEMM convolution, persistent CTAs over work items of 16x4x4 output voxels
+//    (M = 256 per item, N = output channels, K = 27 taps x input channels).  Each item's 18x6x6
+//    input halo is staged in shared memory (channels-last, rows padded by 16 bytes); the weights of
+//    all taps are staged once per CTA when they fit (else in groups of 9 taps); ldmatrix feeds
+//    mma.sync m16n8k16 BF16 x BF16 -> FP32.  The same kernel computes the input gradient (MODE 1)
+//    with the mirrored, transposed weights.
 //  * conv_wgrad: weight and bias gradients, FP32 on the CUDA cores, split over voxel partitions
 //    and reduced in fixed order (deterministic).
 //  * restrict / prolong (and their adjoints as scaled prolong / restrict), relu masks, loss, Adam.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -33,8 +36,10 @@ typedef __nv_bfloat16 bf16;
 
 namespace {
 
-constexpr int TXc = 8, TYc = 4, TZc = 4, HXc = TXc + 2, HYc = TYc + 2, HZc = TZc + 2, NHc = HXc * HYc * HZc;
-constexpr int kConvThreads = 128;
+// Work item: 16 x 4 x 4 output voxels (8 warps; warp w computes the two x-rows of 16 voxels
+// m16 = 2w, 2w+1 as m16n8k16 row tiles); input halo 18 x 6 x 6 voxels.
+constexpr int TXc = 16, TYc = 4, TZc = 4, HXc = TXc + 2, HYc = TYc + 2, HZc = TZc + 2, NHc = HXc * HYc * HZc;
+constexpr int kConvThreads = 256;
 
 struct ConvArgs {
   const bf16 *in;
@@ -46,7 +51,7 @@ struct ConvArgs {
   int cn;                 // output channels actually stored (<= CN)
   bf16 *out_bf;           // [..][cn] or null
   float *out_f;           // [..][cn] or null
-  int tiles_x, tiles_y;
+  int tiles_x, tiles_y, tiles;
 };
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
@@ -58,118 +63,166 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// ldmatrix: four (two) 8x8 b16 matrices; lane L supplies the address of row L % 8 of matrix L / 8.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16 *p) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t (&r)[2], const bf16 *p) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(s));
+}
+
 // CKP: input channels padded to a multiple of 16; CN: output channels padded to a multiple of 8.
+// SK: shared row length (16 bytes of padding keep the ldmatrix rows on distinct banks); G: taps whose
+// weights are staged at once (all 27 when they fit, which then stay resident for the CTA's life).
+template <int CKP, int CN>
+struct ConvCfg {
+  static constexpr int SK = CKP + 8;
+  static constexpr int G = ((NHc + 27 * CN) * SK * 2 <= 220 * 1024) ? 27 : 9;
+  static constexpr int SMEM = (NHc + G * CN) * SK * 2;
+};
+
+// Implicit-GEMM 3x3x3 convolution, persistent: each CTA loops over work items.  Per item the input
+// halo is staged in shared memory (16-byte loads when the channel count is the padded one), then
+// for each tap and 16-channel chunk the A fragments (rows = the tap-shifted halo rows) and B
+// fragments (the tap's weights) are read with ldmatrix and issued as mma.sync m16n8k16 BF16 x BF16
+// -> FP32.  MODE 1 computes the input gradient with the mirrored, transposed weights.
 template <int CKP, int CN, int MODE>
 __global__ void __launch_bounds__(kConvThreads) conv_mma(ConvArgs a) {
-  constexpr int SK = CKP + 8;  // padded smem row (bf16 elements)
+  using Cfg = ConvCfg<CKP, CN>;
+  constexpr int SK = Cfg::SK, G = Cfg::G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   bf16 *in_s = reinterpret_cast<bf16 *>(smem_raw);
   bf16 *w_s = in_s + NHc * SK;
-  const int tid = threadIdx.x;
-  const int bx = blockIdx.x % a.tiles_x;
-  const int by = (blockIdx.x / a.tiles_x) % a.tiles_y;
-  const int bz = blockIdx.x / (a.tiles_x * a.tiles_y);
-  const int x0 = bx * TXc, y0 = by * TYc, z0 = bz * TZc;
-
-  // stage the input halo (zero outside the grid and for padded channels)
-  for (int idx = tid; idx < NHc * CKP; idx += kConvThreads) {
-    const int hv = idx / CKP, c = idx % CKP;
-    const int hx = hv % HXc, hy = (hv / HXc) % HYc, hz = hv / (HXc * HYc);
-    const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
-    bf16 v = __float2bfloat16(0.0f);
-    if (c < a.ck && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
-      v = a.in[(((int64_t)gz * a.ny + gy) * a.nx + gx) * a.ck + c];
-    in_s[hv * SK + c] = v;
-  }
-
-  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  float acc[2][CN / 8][4];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < CN / 8; ++nt)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[mt][nt][j] = 0.0f;
-
-  for (int tap = 0; tap < 27; ++tap) {
-    __syncthreads();
-    for (int idx = tid; idx < CN * CKP; idx += kConvThreads) {
-      const int n = idx / CKP, k = idx % CKP;
-      bf16 v = __float2bfloat16(0.0f);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const bf16 zero = __float2bfloat16(0.0f);
+  auto stage_w = [&](int t0) {  // weights of taps [t0, t0 + G) as w_s[tap - t0][n][k], zero padded
+    for (int idx = tid; idx < G * CN * CKP; idx += kConvThreads) {
+      const int k = idx % CKP, n = (idx / CKP) % CN, tl = idx / (CKP * CN), tap = t0 + tl;
+      bf16 v = zero;
       if (k < a.ck && n < a.cn) {
         if (MODE == 0) v = a.w[((int64_t)tap * a.ck + k) * a.cn + n];
         else v = a.w[((int64_t)(26 - tap) * a.cn + n) * a.ck + k];
       }
-      w_s[n * SK + k] = v;
+      w_s[(tl * CN + n) * SK + k] = v;
     }
-    __syncthreads();
-    const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
-    int hv[2][2];
+  };
+  const bool vec = a.ck == CKP && ((uintptr_t)a.in & 15) == 0;
+  if (G == 27) stage_w(0);  // published by the first barrier of the loop
+  if (!vec)  // channels [ck, CKP) of the halo stay zero: only [0, ck) is rewritten per item
+    for (int idx = tid; idx < NHc * SK; idx += kConvThreads) in_s[idx] = zero;
+
+  for (int item = blockIdx.x; item < a.tiles; item += gridDim.x) {
+    const int bx = item % a.tiles_x, by = (item / a.tiles_x) % a.tiles_y, bz = item / (a.tiles_x * a.tiles_y);
+    const int x0 = bx * TXc, y0 = by * TYc, z0 = bz * TZc;
+    __syncthreads();  // the previous item's reads of in_s are done
+    if (vec) {
+      constexpr int CH = CKP / 8;  // 16-byte chunks per voxel
+      for (int idx = tid; idx < NHc * CH; idx += kConvThreads) {
+        const int hv = idx / CH, ch = idx % CH;
+        const int hx = hv % HXc, hy = (hv / HXc) % HYc, hz = hv / (HXc * HYc);
+        const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
+          v = __ldg(reinterpret_cast<const uint4 *>(a.in + (((int64_t)gz * a.ny + gy) * a.nx + gx) * CKP) + ch);
+        *reinterpret_cast<uint4 *>(in_s + hv * SK + ch * 8) = v;
+      }
+    } else {
+      for (int idx = tid; idx < NHc * a.ck; idx += kConvThreads) {
+        const int hv = idx / a.ck, c = idx % a.ck;
+        const int hx = hv % HXc, hy = (hv / HXc) % HYc, hz = hv / (HXc * HYc);
+        const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+        bf16 v = zero;
+        if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
+          v = a.in[(((int64_t)gz * a.ny + gy) * a.nx + gx) * a.ck + c];
+        in_s[hv * SK + c] = v;
+      }
+    }
+    float acc[2][CN / 8][4];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
+      for (int nt = 0; nt < CN / 8; ++nt)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[mt][nt][j] = 0.0f;
+    for (int t0 = 0; t0 < 27; t0 += G) {
+      if (G < 27) {
+        __syncthreads();  // the previous group's weights are no longer read
+        stage_w(t0);
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int tl = 0; tl < G; ++tl) {
+        const int tap = t0 + tl, dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+        const bf16 *arow[2];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const int m16 = 2 * warp + mt, ty = m16 & 3, tz = m16 >> 2;
+          arow[mt] = in_s + ((tz + dz) * (HXc * HYc) + (ty + dy) * HXc + (lane & 15) + dx) * SK + 8 * (lane >> 4);
+        }
+        const bf16 *brow = w_s + (tl * CN + (lane & 7)) * SK + 8 * ((lane >> 3) & 1);
+#pragma unroll
+        for (int k0 = 0; k0 < CKP; k0 += 16) {
+          uint32_t af[2][4];
+          ldsm_x4(af[0], arow[0] + k0);
+          ldsm_x4(af[1], arow[1] + k0);
+#pragma unroll
+          for (int nt = 0; nt < CN / 8; ++nt) {
+            uint32_t bfr[2];
+            ldsm_x2(bfr, brow + nt * 8 * SK + k0);
+            mma_bf16(acc[0][nt], af[0][0], af[0][1], af[0][2], af[0][3], bfr[0], bfr[1]);
+            mma_bf16(acc[1][nt], af[1][0], af[1][1], af[1][2], af[1][3], bfr[0], bfr[1]);
+          }
+        }
+      }
+    }
+    // epilogue: rows g and g + 8 of each m16 tile are the voxels x0 + g (+8) of that x-row
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int m16 = 2 * warp + mt;
+      const int gy = y0 + (m16 & 3), gz = z0 + (m16 >> 2);
+#pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int r = 32 * warp + 16 * mt + g + 8 * h;
-        const int tx = r & 7, ty = (r >> 3) & 3, tz = r >> 5;
-        hv[mt][h] = (tz + dz) * (HXc * HYc) + (ty + dy) * HXc + (tx + dx);
-      }
+        const int gx = x0 + g + 8 * h;
+        if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
+        const int64_t vox = ((int64_t)gz * a.ny + gy) * a.nx + gx;
 #pragma unroll
-    for (int k0 = 0; k0 < CKP; k0 += 16) {
-      uint32_t af[2][4];
+        for (int nt = 0; nt < CN / 8; ++nt)
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        af[mt][0] = *reinterpret_cast<const uint32_t *>(in_s + hv[mt][0] * SK + k0 + 2 * t);
-        af[mt][1] = *reinterpret_cast<const uint32_t *>(in_s + hv[mt][1] * SK + k0 + 2 * t);
-        af[mt][2] = *reinterpret_cast<const uint32_t *>(in_s + hv[mt][0] * SK + k0 + 8 + 2 * t);
-        af[mt][3] = *reinterpret_cast<const uint32_t *>(in_s + hv[mt][1] * SK + k0 + 8 + 2 * t);
-      }
-#pragma unroll
-      for (int nt = 0; nt < CN / 8; ++nt) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(w_s + (nt * 8 + g) * SK + k0 + 2 * t);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(w_s + (nt * 8 + g) * SK + k0 + 8 + 2 * t);
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b0, b1);
+          for (int j = 0; j < 2; ++j) {
+            const int n = nt * 8 + 2 * t + j;
+            if (n >= a.cn) continue;
+            float v = acc[mt][nt][2 * h + j];
+            if (MODE == 0) {
+              if (a.bias) v += a.bias[n];
+              if (a.skip) v += __bfloat162float(a.skip[vox * a.cn + n]);
+              if (a.relu) v = fmaxf(v, 0.0f);
+            }
+            if (a.out_bf) a.out_bf[vox * a.cn + n] = __float2bfloat16(v);
+            if (a.out_f) a.out_f[vox * a.cn + n] = v;
+          }
       }
     }
   }
-  // epilogue
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int r = 32 * warp + 16 * mt + g + 8 * h;
-      const int gx = x0 + (r & 7), gy = y0 + ((r >> 3) & 3), gz = z0 + (r >> 5);
-      if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
-      const int64_t vox = ((int64_t)gz * a.ny + gy) * a.nx + gx;
-#pragma unroll
-      for (int nt = 0; nt < CN / 8; ++nt)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int n = nt * 8 + 2 * t + j;
-          if (n >= a.cn) continue;
-          float v = acc[mt][nt][2 * h + j];
-          if (MODE == 0) {
-            if (a.bias) v += a.bias[n];
-            if (a.skip) v += __bfloat162float(a.skip[vox * a.cn + n]);
-            if (a.relu) v = fmaxf(v, 0.0f);
-          }
-          if (a.out_bf) a.out_bf[vox * a.cn + n] = __float2bfloat16(v);
-          if (a.out_f) a.out_f[vox * a.cn + n] = v;
-        }
-    }
 }
 
 template <int CKP, int CN, int MODE>
-mf_status launch_conv_t(const ConvArgs &a, cudaStream_t s) {
-  const int smem = (NHc + CN) * (CKP + 8) * (int)sizeof(bf16);
-  static bool attr_set = false;
-  if (!attr_set) {
+mf_status launch_conv_t(ConvArgs a, cudaStream_t s) {
+  constexpr int smem = ConvCfg<CKP, CN>::SMEM;
+  static std::atomic<int> resident{0};  // CTAs per SM: a property of the kernel
+  if (resident.load() == 0) {
     MF_CUDA(cudaFuncSetAttribute(conv_mma<CKP, CN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr_set = true;
+    int r = 0;
+    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, conv_mma<CKP, CN, MODE>, kConvThreads, smem));
+    resident.store(std::max(r, 1));
   }
-  const int tz = (a.nz + TZc - 1) / TZc;
+  a.tiles = a.tiles_x * a.tiles_y * ((a.nz + TZc - 1) / TZc);
+  const int grid = std::min(a.tiles, 152 * resident.load());
   mf_count_launches(1);
-  conv_mma<CKP, CN, MODE><<<a.tiles_x * a.tiles_y * tz, kConvThreads, smem, s>>>(a);
+  conv_mma<CKP, CN, MODE><<<grid, kConvThreads, smem, s>>>(a);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }
@@ -266,17 +319,52 @@ __global__ void bias_grad(const bf16 *__restrict__ dy, int64_t nvox, int co, flo
 }
 
 // ------------------------------------------------------------------- grid transfer ops ----
+// Grid transfers on channels-last BF16 tensors: one thread per output voxel and group of 8
+// channels (16-byte loads and stores when the channel count is a multiple of 8, else per channel),
+// FP32 sums.
+template <int V>
+__device__ __forceinline__ void ld_ch(const bf16 *p, float (&f)[V]) {
+  if constexpr (V == 8) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 t = __bfloat1622float2(h[i]);
+      f[2 * i] = t.x;
+      f[2 * i + 1] = t.y;
+    }
+  } else {
+    f[0] = __bfloat162float(*p);
+  }
+}
+template <int V>
+__device__ __forceinline__ void st_ch(bf16 *p, const float (&f)[V]) {
+  if constexpr (V == 8) {
+    uint4 u;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    *reinterpret_cast<uint4 *>(p) = u;
+  } else {
+    *p = __float2bfloat16(f[0]);
+  }
+}
+
 // Full weighting (m+1)^3 <- (2m+1)^3, scaled by `scale`; weights 1/4, 1/2, 1/4 per axis.
+template <int V>
 __global__ void restrict_k(const bf16 *__restrict__ in, int nfx, int nfy, int nfz, int c, bf16 *__restrict__ out,
                            float scale) {
   const int ncx = (nfx + 1) / 2, ncy = (nfy + 1) / 2, ncz = (nfz + 1) / 2;
+  const int cg = c / V;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t n = (int64_t)ncx * ncy * ncz * c;
+  const int64_t n = (int64_t)ncx * ncy * ncz * cg;
   if (i >= n) return;
-  const int ch = (int)(i % c);
-  const int64_t v = i / c;
+  const int ch = (int)(i % cg) * V;
+  const int64_t v = i / cg;
   const int cx = (int)(v % ncx), cy = (int)((v / ncx) % ncy), cz = (int)(v / ((int64_t)ncx * ncy));
-  float s = 0.0f;
+  float s[V], t[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) s[q] = 0.0f;
   for (int dz = -1; dz <= 1; ++dz) {
     const int fz = 2 * cz + dz;
     if (fz < 0 || fz >= nfz) continue;
@@ -288,33 +376,46 @@ __global__ void restrict_k(const bf16 *__restrict__ in, int nfx, int nfy, int nf
       for (int dx = -1; dx <= 1; ++dx) {
         const int fx = 2 * cx + dx;
         if (fx < 0 || fx >= nfx) continue;
-        const float wx = dx == 0 ? 0.5f : 0.25f;
-        s += wx * wy * wz * __bfloat162float(in[(((int64_t)fz * nfy + fy) * nfx + fx) * c + ch]);
+        const float w = (dx == 0 ? 0.5f : 0.25f) * wy * wz;
+        ld_ch<V>(in + (((int64_t)fz * nfy + fy) * nfx + fx) * c + ch, t);
+#pragma unroll
+        for (int q = 0; q < V; ++q) s[q] += w * t[q];
       }
     }
   }
-  out[i] = __float2bfloat16(s * scale);
+#pragma unroll
+  for (int q = 0; q < V; ++q) s[q] *= scale;
+  st_ch<V>(out + v * c + ch, s);
 }
 
 // Trilinear prolongation (2m+1)^3 <- (m+1)^3, scaled by `scale`.
+template <int V>
 __global__ void prolong_k(const bf16 *__restrict__ in, int ncx, int ncy, int ncz, int c, bf16 *__restrict__ out,
                           float scale) {
   const int nfx = 2 * ncx - 1, nfy = 2 * ncy - 1, nfz = 2 * ncz - 1;
+  const int cg = c / V;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t n = (int64_t)nfx * nfy * nfz * c;
+  const int64_t n = (int64_t)nfx * nfy * nfz * cg;
   if (i >= n) return;
-  const int ch = (int)(i % c);
-  const int64_t v = i / c;
+  const int ch = (int)(i % cg) * V;
+  const int64_t v = i / cg;
   const int fx = (int)(v % nfx), fy = (int)((v / nfx) % nfy), fz = (int)(v / ((int64_t)nfx * nfy));
-  float s = 0.0f;
   const int xs[2] = {fx / 2, (fx + 1) / 2}, ys[2] = {fy / 2, (fy + 1) / 2}, zs[2] = {fz / 2, (fz + 1) / 2};
   const int nxp = (fx & 1) ? 2 : 1, nyp = (fy & 1) ? 2 : 1, nzp = (fz & 1) ? 2 : 1;
-  const float w = 1.0f / (float)(nxp * nyp * nzp);
+  const float w = scale / (float)(nxp * nyp * nzp);
+  float s[V], t[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) s[q] = 0.0f;
   for (int a = 0; a < nzp; ++a)
     for (int b = 0; b < nyp; ++b)
-      for (int d = 0; d < nxp; ++d)
-        s += __bfloat162float(in[(((int64_t)zs[a] * ncy + ys[b]) * ncx + xs[d]) * c + ch]);
-  out[i] = __float2bfloat16(s * w * scale);
+      for (int d = 0; d < nxp; ++d) {
+        ld_ch<V>(in + (((int64_t)zs[a] * ncy + ys[b]) * ncx + xs[d]) * c + ch, t);
+#pragma unroll
+        for (int q = 0; q < V; ++q) s[q] += t[q];
+      }
+#pragma unroll
+  for (int q = 0; q < V; ++q) s[q] *= w;
+  st_ch<V>(out + v * c + ch, s);
 }
 
 // d = d_out * (act > 0)
@@ -397,13 +498,23 @@ extern "C" mf_status mf_conv3d_wgrad(const void *x, const void *dy, int32_t nx, 
   return MF_OK;
 }
 
+// 16-byte channel groups: channel count a multiple of 8 and both tensors 16-byte aligned
+static bool vec8(const void *in, const void *out, int c) {
+  return c % 8 == 0 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0;
+}
+
 extern "C" mf_status mf_grid_restrict(const void *in, int32_t nfx, int32_t nfy, int32_t nfz, int32_t c, void *out,
                                       float scale, mf_stream stream) {
   mf_clear_error();
   MF_ARG(in && out && nfx % 2 == 1 && nfy % 2 == 1 && nfz % 2 == 1 && c > 0, "mf_grid_restrict: bad argument");
   const int64_t n = (int64_t)((nfx + 1) / 2) * ((nfy + 1) / 2) * ((nfz + 1) / 2) * c;
   mf_count_launches(1);
-  restrict_k<<<blocks_for(n), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, nfx, nfy, nfz, c, (bf16 *)out, scale);
+  if (vec8(in, out, c))
+    restrict_k<8><<<blocks_for(n / 8), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, nfx, nfy, nfz, c,
+                                                                             (bf16 *)out, scale);
+  else
+    restrict_k<1><<<blocks_for(n), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, nfx, nfy, nfz, c,
+                                                                        (bf16 *)out, scale);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }
@@ -414,7 +525,12 @@ extern "C" mf_status mf_grid_prolong(const void *in, int32_t ncx, int32_t ncy, i
   MF_ARG(in && out && ncx > 0 && ncy > 0 && ncz > 0 && c > 0, "mf_grid_prolong: bad argument");
   const int64_t n = (int64_t)(2 * ncx - 1) * (2 * ncy - 1) * (2 * ncz - 1) * c;
   mf_count_launches(1);
-  prolong_k<<<blocks_for(n), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, ncx, ncy, ncz, c, (bf16 *)out, scale);
+  if (vec8(in, out, c))
+    prolong_k<8><<<blocks_for(n / 8), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, ncx, ncy, ncz, c,
+                                                                            (bf16 *)out, scale);
+  else
+    prolong_k<1><<<blocks_for(n), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, ncx, ncy, ncz, c,
+                                                                       (bf16 *)out, scale);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }
