@@ -99,13 +99,20 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
   // plane staging: global -> registers (one plane ahead) -> shared memory
   IO xr[LOADS][NC];
   bool dr[LOADS];
+  // in-plane node index of each load slot (-1: outside the mesh or the tile's plane)
+  const int64_t NPL = (int64_t)NXP * NYP;
+  int nib[LOADS];
+#pragma unroll
+  for (int l = 0; l < LOADS; ++l) {
+    const int p = tid + l * NT;
+    const int ix = i0 - 1 + p % PX, iy = j0 - 1 + p / PX;
+    nib[l] = (p < NP && ix >= 0 && ix < NXP && iy >= 0 && iy < NYP) ? ix + NXP * iy : -1;
+  }
   auto fetch = [&](int k) {
 #pragma unroll
     for (int l = 0; l < LOADS; ++l) {
-      const int p = tid + l * NT;
-      const int ix = i0 - 1 + p % PX, iy = j0 - 1 + p / PX;
-      const bool ok = p < NP && ix >= 0 && ix < NXP && iy >= 0 && iy < NYP;
-      const int64_t node = ix + (int64_t)NXP * (iy + (int64_t)NYP * k);
+      const bool ok = nib[l] >= 0;
+      const int64_t node = nib[l] + (int64_t)k * NPL;
       dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
 #pragma unroll
       for (int c = 0; c < NC; ++c) xr[l][c] = ok ? __ldg(x + (node * g.nrhs + rr) * NC + c) : (IO)0;
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
       N::st(sm.xrow[ez & 1][l * NT + tid], N::add(v01, shfl_up1<N>(v11)));
     }
     const bool wr = own && ez >= k0;
-    const int64_t node = ex + (int64_t)NXP * (ey + (int64_t)NYP * ez);
+    const int64_t node = (ex + NXP * ey) + (int64_t)ez * NPL;
     const bool dir = wr && __ldg(g.dmask + node) != 0;  // issued before the barrier
     if (ez + 2 <= plim) {
       stage(ez + 2);  // plane ez's buffer: its last reader finished before the previous barrier
