@@ -291,7 +291,8 @@ mf_status mf_set_tile_segment(mf_mesh *mesh, int32_t seg);
  * theta = max(0, cn.r1 / cn.A cn); z = z2 + w D^-1 (r - A z2); w = 2/3, c the output scale.
  *   mf_net_create       node grid nx x ny x nz (each 4m+1 >= 5), seeded He initialisation.
  *   mf_net_forward      r, logk, out: device float[nx ny nz] (x fastest).  Asynchronous.
- *   mf_net_train_step   one Adam step on the relative squared error |out - target|^2 / |target|^2;
+ *   mf_net_train_step   one Adam step on the relative squared error |out - target|^2 / |target|^2
+ *                       (gradient norm clipped to 5x its moving average over earlier steps);
  *                       *loss (host, may be NULL) receives the loss before the step (synchronises).
  *   mf_net_gradients    loss and parameter gradients without an update (grads: host
  *                       float[mf_net_num_params], may be NULL).

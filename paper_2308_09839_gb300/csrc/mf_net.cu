@@ -49,10 +49,15 @@ __global__ void make_input(const float *__restrict__ r, const float *__restrict_
 }
 
 // Relative squared error L = sum (o - t)^2 / sum t^2 and its gradient 2 (o - t) / sum t^2 (bf16).
-__global__ void loss_reduce(const float *__restrict__ o, const float *__restrict__ t, int64_t n, float *__restrict__ out2) {
-  __shared__ float s1[1024], s2[1024];
+// Relative squared error: per-block partials of sum (o - t)^2 and sum t^2 over a grid-stride range
+// (kLossBlocks blocks), then one block sums the partials in order (deterministic).
+constexpr int kLossBlocks = 256;
+
+__global__ void __launch_bounds__(256) loss_part(const float *__restrict__ o, const float *__restrict__ t, int64_t n,
+                                                 float *__restrict__ part) {
+  __shared__ float s1[256], s2[256];
   float a = 0.f, b = 0.f;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
     const float d = o[i] - t[i];
     a += d * d;
     b += t[i] * t[i];
@@ -60,7 +65,7 @@ __global__ void loss_reduce(const float *__restrict__ o, const float *__restrict
   s1[threadIdx.x] = a;
   s2[threadIdx.x] = b;
   __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+  for (int off = 128; off > 0; off >>= 1) {
     if ((int)threadIdx.x < off) {
       s1[threadIdx.x] += s1[threadIdx.x + off];
       s2[threadIdx.x] += s2[threadIdx.x + off];
@@ -68,9 +73,16 @@ __global__ void loss_reduce(const float *__restrict__ o, const float *__restrict
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out2[0] = s1[0];
-    out2[1] = s2[0];
+    part[2 * blockIdx.x] = s1[0];
+    part[2 * blockIdx.x + 1] = s2[0];
   }
+}
+
+__global__ void loss_final(const float *__restrict__ part, int nparts, float *__restrict__ out2) {
+  if (threadIdx.x > 1) return;
+  float s = 0.f;
+  for (int p = 0; p < nparts; ++p) s += part[2 * p + threadIdx.x];
+  out2[threadIdx.x] = s;
 }
 
 __global__ void loss_grad(const float *__restrict__ o, const float *__restrict__ t, int64_t n,
@@ -81,12 +93,46 @@ __global__ void loss_grad(const float *__restrict__ o, const float *__restrict__
   g[i] = __float2bfloat16(2.0f * (o[i] - t[i]) / den);
 }
 
-// Adam (Kingma & Ba 2015) with bias correction; writes the BF16 copy of the weights.
+// Gradient-norm clipping against loss spikes: partial sums of g^2 (fixed grid, fixed order), then
+// one thread forms ||g|| and the scale min(1, kClipRatio * ema / ||g||) against an exponential
+// moving average of the (clipped) norms of earlier steps; state = {ema, scale}.
+constexpr int kClipBlocks = 256;
+constexpr float kClipRatio = 5.0f;
+
+__global__ void __launch_bounds__(256) grad_sq_part(const float *__restrict__ g, int64_t n, float *__restrict__ part) {
+  __shared__ float sh[256];
+  float s = 0.f;
+  for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) s += g[i] * g[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void clip_scale(const float *__restrict__ part, int nparts, float *__restrict__ state) {
+  if (threadIdx.x != 0) return;
+  float s = 0.f;
+  for (int p = 0; p < nparts; ++p) s += part[p];
+  const float norm = sqrtf(s), ema = state[0];
+  float scale = 1.0f;
+  if (ema > 0.f && norm > kClipRatio * ema) scale = kClipRatio * ema / norm;
+  if (!isfinite(norm)) scale = 0.0f;  // skip a non-finite step
+  const float used = isfinite(norm) ? norm * scale : ema;
+  state[0] = ema > 0.f ? 0.9f * ema + 0.1f * used : used;
+  state[1] = scale;
+}
+
+// Adam (Kingma & Ba 2015) with bias correction on the clipped gradient gscale[0] * g; writes the
+// BF16 copy of the weights.
 __global__ void adam_k(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
-                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, bf16 *__restrict__ pb) {
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, bf16 *__restrict__ pb,
+                       const float *__restrict__ gscale) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float gi = g[i];
+  const float gi = g[i] * gscale[0];
   const float mi = b1 * m[i] + (1.f - b1) * gi;
   const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
   m[i] = mi;
@@ -114,6 +160,9 @@ struct mf_net {
   float *ws = nullptr;
   int64_t ws_bytes = 0;
   float *sums = nullptr;
+  float *lpart = nullptr;  // loss partials [kLossBlocks][2]
+  float *cpart = nullptr;  // squared-gradient partials [kClipBlocks]
+  float *clip = nullptr;   // {moving average of the gradient norm, scale of this step}
   float out_scale = 1.0f;
   std::vector<void *> allocs;
 };
@@ -178,8 +227,9 @@ mf_status conv_back(mf_net *N, int l, const bf16 *in, const bf16 *gpre, bf16 *gi
 mf_status backward(mf_net *N, const float *target, float *loss_host, cudaStream_t s) {
   const int64_t V0 = N->V[0], V1 = N->V[1], V2 = N->V[2];
   const int *n0 = N->n[0], *n1 = N->n[1], *n2 = N->n[2];
-  mf_count_launches(2);
-  loss_reduce<<<1, 1024, 0, s>>>(N->out, target, V0, N->sums);
+  mf_count_launches(3);
+  loss_part<<<kLossBlocks, 256, 0, s>>>(N->out, target, V0, N->lpart);
+  loss_final<<<1, 32, 0, s>>>(N->lpart, kLossBlocks, N->sums);
   loss_grad<<<blocks_for(V0), kThreads, 0, s>>>(N->out, target, V0, N->sums, N->g_out);
   MF_CUDA(cudaGetLastError());
   // out = conv7(d0), linear
@@ -270,7 +320,7 @@ extern "C" mf_status mf_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t 
   NA(N->m2, V2 * 64) NA(N->p1, V1 * 64) NA(N->d1, V1 * 32) NA(N->q1, V1 * 16) NA(N->p0, V0 * 16) NA(N->d0, V0 * 16)
   NA(N->out, V0) NA(N->g_out, V0)
   const int64_t gmax = std::max(std::max(V0 * 16, V1 * 64), V2 * 64);
-  NA(N->g_a, gmax) NA(N->g_b, gmax) NA(N->g_c, gmax) NA(N->g_e1, V1 * 32) NA(N->g_e0, V0 * 16) NA(N->sums, 2)
+  NA(N->g_a, gmax) NA(N->g_b, gmax) NA(N->g_c, gmax) NA(N->g_e1, V1 * 32) NA(N->g_e0, V0 * 16) NA(N->sums, 2) NA(N->lpart, 2 * kLossBlocks) NA(N->cpart, kClipBlocks) NA(N->clip, 2)
   int64_t wsb = 0;
   for (auto &L : N->layers) {
     const int *dd = N->n[L.level];
@@ -290,6 +340,7 @@ extern "C" mf_status mf_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t 
   cudaError_t e = cudaMemcpy(N->p, h.data(), off * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(N->m, 0, off * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(N->v, 0, off * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(N->clip, 0, 2 * sizeof(float));  // no norm history yet
   if (e != cudaSuccess) {
     mf_set_error("mf_net_create: %s", cudaGetErrorString(e));
     net_free(N);
@@ -370,9 +421,11 @@ extern "C" mf_status mf_net_train_step(mf_net *N, const float *r, const float *l
   N->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.0f - std::pow(b1, (float)N->step), c2 = 1.0f - std::pow(b2, (float)N->step);
-  mf_count_launches(1);
+  mf_count_launches(3);
+  grad_sq_part<<<kClipBlocks, 256, 0, s>>>(N->g, N->n_params, N->cpart);
+  clip_scale<<<1, 32, 0, s>>>(N->cpart, kClipBlocks, N->clip);
   adam_k<<<blocks_for(N->n_params), kThreads, 0, s>>>(N->p, N->g, N->m, N->v, N->n_params, lr, b1, b2, 1e-8f, c1, c2,
-                                                      N->pb);
+                                                      N->pb, N->clip + 1);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }

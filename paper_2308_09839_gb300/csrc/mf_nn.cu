@@ -18,8 +18,9 @@
 //    all taps are staged once per CTA when they fit (else in groups of 9 taps); ldmatrix feeds
 //    mma.sync m16n8k16 BF16 x BF16 -> FP32.  The same kernel computes the input gradient (MODE 1)
 //    with the mirrored, transposed weights.
-//  * conv_wgrad: weight and bias gradients, FP32 on the CUDA cores, split over voxel partitions
-//    and reduced in fixed order (deterministic).
+//  * conv_wgrad_mma: weight and bias gradients on the tensor cores (per tap a GEMM contracting over
+//    voxels, ldmatrix.trans fragments, FP32 accumulation), partial sums per CTA reduced in fixed
+//    order (deterministic).
 //  * restrict / prolong (and their adjoints as scaled prolong / restrict), relu masks, loss, Adam.
 #include <cuda_bf16.h>
 
@@ -244,78 +245,167 @@ mf_status launch_conv(ConvArgs a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------ weight gradient ----
-// dw[t][ci][co] = sum_v x[v + off_t][ci] dy[v][co]; partials over P voxel partitions, FP32.
-constexpr int kWgThreads = 256, kWgChunk = 64;
+// dw[t][ci][co] = sum_v x[v + off_t][ci] dy[v][co] and db[co] = sum_v dy[v][co] on the tensor
+// cores: for each tap a GEMM with M = input channels, N = output channels and K = voxels.  A CTA
+// takes 8 taps (one per warp; blockIdx.y picks the group) and loops over the same 16x4x4-voxel
+// work items as the convolution: it stages the item's input halo and output gradient in shared
+// memory, and each warp accumulates its tap's Cin x Cout block over the item's 256 voxels with
+// ldmatrix.trans fragments (the voxel index is the contraction index) and mma.sync m16n8k16 BF16 ->
+// FP32.  Every CTA writes its partial sums; a fixed-order reduction over the CTAs gives dw and db
+// (deterministic: the partition does not depend on the GPU).
+constexpr int kWgParts = 256;  // CTAs along the voxel items (the partition of the partial sums)
 
-__global__ void __launch_bounds__(kWgThreads) conv_wgrad_part(const bf16 *__restrict__ x, const bf16 *__restrict__ dy,
-                                                              int nx, int ny, int nz, int ci, int co, int nparts,
-                                                              float *__restrict__ part) {
-  // blockIdx.x = tap + 27 * partition
-  const int tap = blockIdx.x % 27, pidx = blockIdx.x / 27;
-  const int ox = tap % 3 - 1, oy = (tap / 3) % 3 - 1, oz = tap / 9 - 1;
-  const int64_t nvox = (int64_t)nx * ny * nz;
-  const int64_t v0 = nvox * pidx / nparts, v1 = nvox * (pidx + 1) / nparts;
-  __shared__ float xs[kWgChunk][65], ds[kWgChunk][65];
-  const int npair = ci * co;
-  float accv[16];
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const bf16 *p) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t (&r)[2], const bf16 *p) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(s));
+}
+
+template <int CKP, int CNP>
+struct WgCfg {
+  static constexpr int SKX = CKP + 8, SKD = CNP + 8;
+  static constexpr int NV = TXc * TYc * TZc;  // voxels per item
+  static constexpr int SMEM = (NHc * SKX + NV * SKD) * 2;
+};
+
+template <int CKP, int CNP>
+__global__ void __launch_bounds__(kConvThreads) conv_wgrad_mma(const bf16 *__restrict__ x, const bf16 *__restrict__ dy,
+                                                               int nx, int ny, int nz, int ci, int co, int tiles_x,
+                                                               int tiles_y, int tiles, float *__restrict__ part) {
+  using Cfg = WgCfg<CKP, CNP>;
+  constexpr int SKX = Cfg::SKX, SKD = Cfg::SKD, NV = Cfg::NV;
+  extern __shared__ __align__(16) unsigned char wg_smem_raw[];
+  bf16 *x_s = reinterpret_cast<bf16 *>(wg_smem_raw);
+  bf16 *d_s = x_s + NHc * SKX;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int tap = 8 * blockIdx.y + warp;
+  const bool active = tap < 27;
+  const int dx = tap % 3, dyo = (tap / 3) % 3, dz = tap / 9;
+  const bf16 zero = __float2bfloat16(0.0f);
+  const bool vx = ci == CKP && ((uintptr_t)x & 15) == 0, vd = co == CNP && ((uintptr_t)dy & 15) == 0;
+  (void)t;
+  // padded channels stay zero from this initial clear; only the real ones are rewritten per item
+  for (int idx = tid; idx < NHc * SKX + NV * SKD; idx += kConvThreads) x_s[idx] = zero;
+  float acc[CKP / 16][CNP / 8][4];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) accv[i] = 0.0f;
-  for (int64_t base = v0; base < v1; base += kWgChunk) {
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < kWgChunk * 64; idx += kWgThreads) {
-      const int j = idx / 64, c = idx % 64;
-      const int64_t v = base + j;
-      float xv = 0.0f, dv = 0.0f;
-      if (v < v1) {
-        const int gx = (int)(v % nx), gy = (int)((v / nx) % ny), gz = (int)(v / ((int64_t)nx * ny));
-        const int sx = gx + ox, sy = gy + oy, sz = gz + oz;
-        if (c < ci && sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz)
-          xv = __bfloat162float(x[(((int64_t)sz * ny + sy) * nx + sx) * ci + c]);
-        if (c < co) dv = __bfloat162float(dy[v * co + c]);
+  for (int mi = 0; mi < CKP / 16; ++mi)
+#pragma unroll
+    for (int nj = 0; nj < CNP / 8; ++nj)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[mi][nj][j] = 0.0f;
+
+  for (int item = blockIdx.x; item < tiles; item += gridDim.x) {
+    const int bx = item % tiles_x, by = (item / tiles_x) % tiles_y, bz = item / (tiles_x * tiles_y);
+    const int x0 = bx * TXc, y0 = by * TYc, z0 = bz * TZc;
+    __syncthreads();  // the previous item's reads are done
+    if (vx) {
+      constexpr int CH = CKP / 8;
+      for (int idx = tid; idx < NHc * CH; idx += kConvThreads) {
+        const int hv = idx / CH, ch = idx % CH;
+        const int gx = x0 - 1 + hv % HXc, gy = y0 - 1 + (hv / HXc) % HYc, gz = z0 - 1 + hv / (HXc * HYc);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+          v = __ldg(reinterpret_cast<const uint4 *>(x + (((int64_t)gz * ny + gy) * nx + gx) * CKP) + ch);
+        *reinterpret_cast<uint4 *>(x_s + hv * SKX + ch * 8) = v;
       }
-      xs[j][c] = xv;
-      ds[j][c] = dv;
+    } else {
+      for (int idx = tid; idx < NHc * ci; idx += kConvThreads) {
+        const int hv = idx / ci, c = idx % ci;
+        const int gx = x0 - 1 + hv % HXc, gy = y0 - 1 + (hv / HXc) % HYc, gz = z0 - 1 + hv / (HXc * HYc);
+        bf16 v = zero;
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+          v = x[(((int64_t)gz * ny + gy) * nx + gx) * ci + c];
+        x_s[hv * SKX + c] = v;
+      }
+    }
+    // output gradient of the item's voxels; row r = x offset + 16 (y offset + 4 z offset)
+    if (vd) {
+      constexpr int CH = CNP / 8;
+      for (int idx = tid; idx < NV * CH; idx += kConvThreads) {
+        const int r = idx / CH, ch = idx % CH;
+        const int gx = x0 + (r & 15), gy = y0 + ((r >> 4) & 3), gz = z0 + (r >> 6);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gx < nx && gy < ny && gz < nz)
+          v = __ldg(reinterpret_cast<const uint4 *>(dy + (((int64_t)gz * ny + gy) * nx + gx) * CNP) + ch);
+        *reinterpret_cast<uint4 *>(d_s + r * SKD + ch * 8) = v;
+      }
+    } else {
+      for (int idx = tid; idx < NV * co; idx += kConvThreads) {
+        const int r = idx / co, c = idx % co;
+        const int gx = x0 + (r & 15), gy = y0 + ((r >> 4) & 3), gz = z0 + (r >> 6);
+        bf16 v = zero;
+        if (gx < nx && gy < ny && gz < nz) v = dy[(((int64_t)gz * ny + gy) * nx + gx) * co + c];
+        d_s[r * SKD + c] = v;
+      }
     }
     __syncthreads();
+    if (active) {
+#pragma unroll 1
+      for (int kc = 0; kc < NV / 16; ++kc) {  // 16 voxels: one x-row of the item
+        const int ty = kc & 3, tz = kc >> 2;
+        const int v = (lane & 7) + 8 * (lane >> 4);  // voxel of the row addressed by this lane
+        const bf16 *arow = x_s + ((tz + dz) * (HXc * HYc) + (ty + dyo) * HXc + v + dx) * SKX + 8 * ((lane >> 3) & 1);
+        const bf16 *brow = d_s + (kc * 16 + (lane & 15)) * SKD;
+        uint32_t bfr[CNP / 8][2];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int pair = threadIdx.x + i * kWgThreads;
-      if (pair < npair) {
-        const int a = pair / co, b = pair % co;
-        float s = accv[i];
-        for (int j = 0; j < kWgChunk; ++j) s = fmaf(xs[j][a], ds[j][b], s);
-        accv[i] = s;
+        for (int nj = 0; nj < CNP / 8; ++nj) ldsm_x2_t(bfr[nj], brow + 8 * nj);
+#pragma unroll
+        for (int mi = 0; mi < CKP / 16; ++mi) {
+          uint32_t af[4];
+          ldsm_x4_t(af, arow + 16 * mi);
+#pragma unroll
+          for (int nj = 0; nj < CNP / 8; ++nj)
+            mma_bf16(acc[mi][nj], af[0], af[1], af[2], af[3], bfr[nj][0], bfr[nj][1]);
+        }
       }
     }
   }
+  // partial sums of this CTA: part[p][27 ci co] with p = blockIdx.x
+  float *pp = part + (int64_t)blockIdx.x * (27 * (int64_t)ci * co);
+  if (active) {
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int pair = threadIdx.x + i * kWgThreads;
-    if (pair < npair) part[((int64_t)pidx * 27 + tap) * npair + pair] = accv[i];
+    for (int mi = 0; mi < CKP / 16; ++mi)
+#pragma unroll
+      for (int nj = 0; nj < CNP / 8; ++nj)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int a = 16 * mi + g + 8 * (j >> 1), b = 8 * nj + 2 * t + (j & 1);
+          if (a < ci && b < co) pp[((int64_t)tap * ci + a) * co + b] = acc[mi][nj][j];
+        }
   }
 }
 
-__global__ void conv_wgrad_reduce(const float *__restrict__ part, int nparts, int n, float *__restrict__ dw) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Bias gradient partials: block b sums voxels [nvox b / parts, nvox (b + 1) / parts) of every
+// channel (thread = channel + co * lane, coalesced), lanes combined in fixed order.
+__global__ void __launch_bounds__(256) bias_grad_part(const bf16 *__restrict__ dy, int64_t nvox, int co, int parts,
+                                                      float *__restrict__ part) {
+  __shared__ float sh[256];
+  const int lanes = 256 / co, c = threadIdx.x % co, l = threadIdx.x / co;
+  const int64_t v0 = nvox * blockIdx.x / parts, v1 = nvox * (blockIdx.x + 1) / parts;
+  float s = 0.0f;
+  if (l < lanes)
+    for (int64_t v = v0 + l; v < v1; v += lanes) s += __bfloat162float(dy[v * co + c]);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  if ((int)threadIdx.x < co) {
+    float tot = 0.0f;
+    for (int q = 0; q < lanes; ++q) tot += sh[q * co + threadIdx.x];
+    part[(int64_t)blockIdx.x * co + threadIdx.x] = tot;
+  }
+}
+
+// out[i] = sum_p part[p][i], p in order (deterministic); i < n
+__global__ void conv_wgrad_reduce(const float *__restrict__ part, int nparts, int64_t n, float *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   float s = 0.0f;
   for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * n + i];
-  dw[i] = s;
-}
-
-// db[co] = sum_v dy[v][co] (fixed-order two-level sum)
-__global__ void bias_grad(const bf16 *__restrict__ dy, int64_t nvox, int co, float *__restrict__ db) {
-  const int c = blockIdx.x;
-  __shared__ float sh[256];
-  float s = 0.0f;
-  for (int64_t v = threadIdx.x; v < nvox; v += blockDim.x) s += __bfloat162float(dy[v * co + c]);
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-    if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) db[c] = sh[0];
+  out[i] = s;
 }
 
 // ------------------------------------------------------------------- grid transfer ops ----
@@ -470,30 +560,63 @@ extern "C" mf_status mf_conv3d_dgrad(const void *dy, int32_t nx, int32_t ny, int
   return launch_conv<1>(a, (cudaStream_t)stream);
 }
 
-static int64_t wgrad_parts(int64_t nvox) {
-  int64_t p = (nvox + 4095) / 4096;
-  return p < 1 ? 1 : p > 64 ? 64 : p;
+static int wgrad_tiles(int nx, int ny, int nz) {
+  return ((nx + TXc - 1) / TXc) * ((ny + TYc - 1) / TYc) * ((nz + TZc - 1) / TZc);
+}
+
+// Number of partial sums (CTAs along the voxel items): at most one per item and kWgParts, and few
+// enough that the partials (parts x 27 cin cout floats) stay near 2^22 values for the reduction.
+static int wgrad_parts(int nx, int ny, int nz, int cin, int cout) {
+  const int by_size = std::max(32, (int)((1 << 22) / (27 * (int64_t)cin * cout)));
+  return std::min(std::min(wgrad_tiles(nx, ny, nz), kWgParts), by_size);
 }
 
 extern "C" int64_t mf_conv3d_wgrad_workspace(int32_t nx, int32_t ny, int32_t nz, int32_t cin, int32_t cout) {
-  return wgrad_parts((int64_t)nx * ny * nz) * 27 * cin * cout * (int64_t)sizeof(float);
+  const int64_t parts = wgrad_parts(nx, ny, nz, cin, cout);
+  return (parts * 27 * (int64_t)cin * cout + (int64_t)kWgParts * cout) * (int64_t)sizeof(float);
+}
+
+template <int CKP, int CNP>
+static mf_status launch_wgrad_t(const bf16 *x, const bf16 *dy, int nx, int ny, int nz, int ci, int co, int parts,
+                                float *ws, cudaStream_t s) {
+  constexpr int smem = WgCfg<CKP, CNP>::SMEM;
+  static std::atomic<int> attr{0};
+  if (attr.load() == 0) {
+    MF_CUDA(cudaFuncSetAttribute(conv_wgrad_mma<CKP, CNP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr.store(1);
+  }
+  const int tx = (nx + TXc - 1) / TXc, ty = (ny + TYc - 1) / TYc;
+  conv_wgrad_mma<CKP, CNP><<<dim3(parts, 4), kConvThreads, smem, s>>>(x, dy, nx, ny, nz, ci, co, tx, ty,
+                                                                      wgrad_tiles(nx, ny, nz), ws);
+  return MF_OK;
 }
 
 extern "C" mf_status mf_conv3d_wgrad(const void *x, const void *dy, int32_t nx, int32_t ny, int32_t nz, int32_t cin,
                                      int32_t cout, float *dw, float *db, float *workspace, int64_t ws_bytes,
                                      mf_stream stream) {
   mf_clear_error();
-  MF_ARG(x && dy && dw && workspace && cin > 0 && cout > 0 && cin <= 64 && cout <= 64, "mf_conv3d_wgrad: bad argument");
-  const int64_t nvox = (int64_t)nx * ny * nz;
-  const int64_t parts = wgrad_parts(nvox);
+  MF_ARG(x && dy && dw && workspace && cin > 0 && cout > 0 && cin <= 64 && cout <= 64 && nx > 0 && ny > 0 && nz > 0,
+         "mf_conv3d_wgrad: bad argument");
   MF_ARG(ws_bytes >= mf_conv3d_wgrad_workspace(nx, ny, nz, cin, cout), "mf_conv3d_wgrad: workspace too small");
   cudaStream_t s = (cudaStream_t)stream;
-  mf_count_launches(db ? 3 : 2);
-  conv_wgrad_part<<<(unsigned)(27 * parts), kWgThreads, 0, s>>>((const bf16 *)x, (const bf16 *)dy, nx, ny, nz, cin,
-                                                                cout, (int)parts, workspace);
-  const int n = 27 * cin * cout;
-  conv_wgrad_reduce<<<(n + 255) / 256, 256, 0, s>>>(workspace, (int)parts, n, dw);
-  if (db) bias_grad<<<cout, 256, 0, s>>>((const bf16 *)dy, nvox, cout, db);
+  const int parts = wgrad_parts(nx, ny, nz, cin, cout);
+  const int ckp = cin <= 16 ? 16 : cin <= 32 ? 32 : 64;
+  const int cnp = cout <= 8 ? 8 : cout <= 16 ? 16 : cout <= 32 ? 32 : 64;
+  const bf16 *xb = (const bf16 *)x, *db16 = (const bf16 *)dy;
+  mf_count_launches(db ? 4 : 2);
+#define WG(K, N) \
+  if (ckp == K && cnp == N) MF_TRY((launch_wgrad_t<K, N>(xb, db16, nx, ny, nz, cin, cout, parts, workspace, s)));
+  WG(16, 8) WG(16, 16) WG(16, 32) WG(16, 64)
+  WG(32, 8) WG(32, 16) WG(32, 32) WG(32, 64)
+  WG(64, 8) WG(64, 16) WG(64, 32) WG(64, 64)
+#undef WG
+  const int64_t nw = 27 * (int64_t)cin * cout;
+  conv_wgrad_reduce<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(workspace, parts, nw, dw);
+  if (db) {
+    float *bp = workspace + parts * nw;
+    bias_grad_part<<<kWgParts, 256, 0, s>>>((const bf16 *)dy, (int64_t)nx * ny * nz, cout, kWgParts, bp);
+    conv_wgrad_reduce<<<1, 256, 0, s>>>(bp, kWgParts, cout, db);
+  }
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }

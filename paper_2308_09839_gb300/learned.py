@@ -83,7 +83,7 @@ def _crop(t, nzyx, origin, size):
     return t.view(*nzyx)[z0:z0 + size, y0:y0 + size, x0:x0 + size].contiguous().view(-1)
 
 
-def train(R, E, logk, nzyx, crop: int = 33, steps: int = 2000, lr: float = 5e-4, seed: int = 0, log_every: int = 0,
+def train(R, E, logk, nzyx, crop: int = 33, steps: int = 2000, lr: float = 2e-4, seed: int = 0, log_every: int = 0,
           warmup: int = 100):
     """Train a network on random crops of `crop`^3 nodes (the full grid when `crop` equals its size)
     with Adam, linear warm-up over `warmup` steps and cosine decay; returns (params, loss history,

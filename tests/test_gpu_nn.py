@@ -145,7 +145,7 @@ def test_learned_preconditioner_gains_over_jacobi_pcg():
     nzyx = (p.nz + 1, p.ny + 1, p.nx + 1)
     R, E, c = learned.generate_pairs(mesh, p, 64, seed=1, k_range=(2, 60))
     lk = learned.node_logk(p)
-    params, hist, secs = learned.train(R, E, lk, nzyx, crop=33, steps=1500, lr=5e-4)
+    params, hist, secs = learned.train(R, E, lk, nzyx, crop=33, steps=1500, lr=2e-4)
     assert np.mean(hist[-50:]) < 0.7 * np.mean(hist[:20])
     net = learned.make_inference_net(params, nzyx, c)
     b = torch.from_numpy(p.b()).cuda()
