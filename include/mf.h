@@ -86,13 +86,21 @@ mf_status mf_mesh_query(const mf_mesh *mesh, int64_t *n_nodes, int64_t *n_cells,
 /*
  * Kernel variants for the operator apply (mf_set_apply_variant):
  *   MF_VARIANT_AUTO       fastest variant that meets FP64 accuracy for this mesh (default): on a
- *                         structured tensor-product grid the tile kernel (Walsh-Hadamard form of
- *                         the 2x2x2 Gauss sums, double-word FP32 arithmetic, owner-computes
- *                         z-marching tiles); otherwise the reference kernel
+ *                         structured tensor-product grid the face-marching kernel (Walsh-Hadamard
+ *                         form of the 2x2x2 Gauss sums, double-word FP32 arithmetic); on another
+ *                         structured box the partial-assembly kernel when its data fit (flag bit 3
+ *                         of mf_mesh_query), else the general kernel; otherwise the reference kernel
  *   MF_VARIANT_REFERENCE  Algorithm 1 as printed: one thread per element, FP64 arithmetic,
  *                         Jacobian at every quadrature point, colour-by-colour scatter
+ *   MF_VARIANT_GENERAL    structured boxes that are not tensor-product grids: Jacobian, adjugate
+ *                         and determinant at every quadrature point in double-word arithmetic
+ *                         (MF_ERR_UNSUPPORTED on other meshes)
+ *   MF_VARIANT_PARTIAL    the same meshes: partial assembly (Table 3), the quadrature-point data
+ *                         computed once in FP64 and stored as float pairs (6 values per point for
+ *                         Laplace, 10 for elasticity); built on first selection (MF_ERR_OOM if it
+ *                         does not fit; synchronises the device)
  */
-enum { MF_VARIANT_AUTO = 0, MF_VARIANT_REFERENCE = 1 };
+enum { MF_VARIANT_AUTO = 0, MF_VARIANT_REFERENCE = 1, MF_VARIANT_GENERAL = 2, MF_VARIANT_PARTIAL = 3 };
 mf_status mf_set_apply_variant(mf_mesh *mesh, int variant);
 
 /*

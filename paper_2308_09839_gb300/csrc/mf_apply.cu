@@ -206,13 +206,13 @@ mf_status apply_reference(const mf_mesh *m, const R *x, R *y, cudaStream_t s, co
 
 mf_status apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip) {
   if (m->variant == MF_VARIANT_AUTO && m->tp) return tile_apply_fp64(m, x, y, s, skip);
-  if (m->variant == MF_VARIANT_AUTO && m->gen) return gen_apply_fp64(m, x, y, s, skip);
+  if (m->variant != MF_VARIANT_REFERENCE && m->gen) return gen_apply_fp64(m, x, y, s, skip);
   return apply_reference<double>(m, x, y, s, skip);
 }
 
 mf_status apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip) {
   if (m->variant == MF_VARIANT_AUTO && m->tp) return tile_apply_fp32(m, x, y, s, skip);
-  if (m->variant == MF_VARIANT_AUTO && m->gen) return gen_apply_fp32(m, x, y, s, skip);
+  if (m->variant != MF_VARIANT_REFERENCE && m->gen) return gen_apply_fp32(m, x, y, s, skip);
   return apply_reference<float>(m, x, y, s, skip);
 }
 

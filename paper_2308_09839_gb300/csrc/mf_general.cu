@@ -18,7 +18,9 @@
 // Laplace: flux f = kappa adj(J) adj(J)^T grad_ref u / det J (Eq. 7).  Elasticity: grad u =
 // H adj(J) / det J, sigma = lam tr(eps) I + 2 mu eps, P = sigma adj(J)^T (Algorithm 1).
 #include <algorithm>
+#include <type_traits>
 
+#include "mf_element.cuh"
 #include "mf_tile.cuh"
 
 using namespace tile;
@@ -37,11 +39,14 @@ struct GenArgs {
   const float2 *delta;  // [N][3] offsets from the base grid
   const float2 *mat;    // kappa[E] or (lam, mu)[E]
   const uint8_t *dmask;
+  const void *pa;       // partial-assembly data (float2 or float, see PaView), or null
+  int64_t n_cells;
 };
 
+// v or -v (negation of a float pair is exact: both parts change sign)
 template <class N>
 __device__ __forceinline__ typename N::T sgn(typename N::T v, int s) {
-  return s > 0 ? v : typename N::T(N::sub(N::zero(), v));
+  return s > 0 ? v : N::neg(v);
 }
 
 // Hadamard coefficients of 8 nodal values, scaled by 1/8, bilinear modes times g, trilinear
@@ -129,17 +134,67 @@ __device__ __forceinline__ dw ndiv<NumDW>(dw a, dw b) { return dwa::div(a, b); }
 template <>
 __device__ __forceinline__ float ndiv<NumF32>(float a, float b) { return a / b; }
 
-// Laplace element (Eq. 7), in place on u.
+// Stored quadrature-point data of partial assembly (Table 3), as pairs (DW) or floats (FP32):
+// pa[(q * K + k) * n_cells + e].  Laplace and vector Laplace: K = 6, the symmetric flux matrix
+// D_q = kappa w adj(J) adj(J)^T / det J (entries 00 01 02 11 12 22); elasticity: K = 10, adj(J)
+// row-major and 1/det J.
+// With pairs (DW) the data of the next Gauss point are copied asynchronously (cp.async, no
+// registers) into this thread's two shared-memory slot sets while the current point is computed.
+struct PaView {
+  const void *pa;
+  int64_t n_cells;
+  int64_t e;
+  void *buf;   // per-thread slots in shared memory: buf[(b * K + k) * stride], b = q & 1 (DW only)
+  int stride;
+};
+
 template <class N>
+__device__ __forceinline__ typename N::T pa_load(const PaView &P, int q, int K, int k) {
+  const typename N::S *p = static_cast<const typename N::S *>(P.pa);
+  if constexpr (std::is_same<N, NumDW>::value) {
+    const float2 *b = static_cast<const float2 *>(P.buf);
+    return N::ld(b[((q & 1) * K + k) * P.stride]);
+  } else {
+    return N::ld(p[((int64_t)q * K + k) * P.n_cells + P.e]);
+  }
+}
+
+// issue the asynchronous copies of Gauss point q's K pairs (DW) into slot set q & 1
+template <class N>
+__device__ __forceinline__ void pa_issue(const PaView &P, int q, int K) {
+  if constexpr (std::is_same<N, NumDW>::value) {
+    const float2 *p = static_cast<const float2 *>(P.pa);
+    float2 *b = static_cast<float2 *>(P.buf);
+    for (int k = 0; k < K; ++k) {
+      const unsigned s = (unsigned)__cvta_generic_to_shared(b + ((q & 1) * K + k) * P.stride);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(p + ((int64_t)q * K + k) * P.n_cells + P.e));
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  }
+}
+
+// before reading point q: point q's copies are complete (point q + 1's may still be in flight)
+template <class N>
+__device__ __forceinline__ void pa_wait(int q) {
+  if constexpr (std::is_same<N, NumDW>::value) {
+    if (q < 7) asm volatile("cp.async.wait_group 1;\n" ::);
+    else asm volatile("cp.async.wait_group 0;\n" ::);
+  }
+}
+
+// Laplace element (Eq. 7), in place on u; with PA the flux matrix is loaded instead of computed.
+template <class N, bool PA = false>
 __device__ void laplace_general(typename N::T u[8], const typename N::T del[8][3], const typename N::T hh[3],
-                                typename N::T kappa) {
+                                typename N::T kappa, const PaView &P = PaView{}) {
   using T = typename N::T;
   T cd[3][8];
+  if constexpr (!PA) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 3; ++i) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a) cd[i][a] = del[a][i];
-    modes<N>(cd[i]);
+      for (int a = 0; a < 8; ++a) cd[i][a] = del[a][i];
+      modes<N>(cd[i]);
+    }
   }
   modes<N>(u);
   T A[3][4];
@@ -147,24 +202,39 @@ __device__ void laplace_general(typename N::T u[8], const typename N::T del[8][3
   for (int j = 0; j < 3; ++j)
 #pragma unroll
     for (int t = 0; t < 4; ++t) A[j][t] = N::zero();
-#pragma unroll 1
+  if constexpr (PA) pa_issue<N>(P, 0, 6);
+#pragma unroll ((PA && std::is_same<N, NumF32>::value) ? 8 : 1)
   for (int q = 0; q < 8; ++q) {
     const int s[3] = {(q & 1) ? 1 : -1, (q & 2) ? 1 : -1, (q & 4) ? 1 : -1};
-    T J[3][3], C[3][3];
-    jac<N>(cd, hh, s, J);
-    const T det = adj<N>(J, C);
-    const T sc = ndiv<N>(kappa, det);
     T gu[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) gu[j] = dref<N>(u, j, s);
-    T t[3];
+    if constexpr (PA) {
+      if (q < 7) pa_issue<N>(P, q + 1, 6);
+      pa_wait<N>(q);
+      T D[6];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      t[k] = N::add(N::add(N::mul(C[0][k], gu[0]), N::mul(C[1][k], gu[1])), N::mul(C[2][k], gu[2]));
+      for (int k = 0; k < 6; ++k) D[k] = pa_load<N>(P, q, 6, k);
+      const T f0 = N::add(N::add(N::mul(D[0], gu[0]), N::mul(D[1], gu[1])), N::mul(D[2], gu[2]));
+      const T f1 = N::add(N::add(N::mul(D[1], gu[0]), N::mul(D[3], gu[1])), N::mul(D[4], gu[2]));
+      const T f2 = N::add(N::add(N::mul(D[2], gu[0]), N::mul(D[4], gu[1])), N::mul(D[5], gu[2]));
+      accum<N>(A[0], f0, 0, s);
+      accum<N>(A[1], f1, 1, s);
+      accum<N>(A[2], f2, 2, s);
+    } else {
+      T J[3][3], C[3][3];
+      jac<N>(cd, hh, s, J);
+      const T det = adj<N>(J, C);
+      const T sc = ndiv<N>(kappa, det);
+      T t[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const T f = N::mul(sc, N::add(N::add(N::mul(C[j][0], t[0]), N::mul(C[j][1], t[1])), N::mul(C[j][2], t[2])));
-      accum<N>(A[j], f, j, s);
+      for (int k = 0; k < 3; ++k)
+        t[k] = N::add(N::add(N::mul(C[0][k], gu[0]), N::mul(C[1][k], gu[1])), N::mul(C[2][k], gu[2]));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const T f = N::mul(sc, N::add(N::add(N::mul(C[j][0], t[0]), N::mul(C[j][1], t[1])), N::mul(C[j][2], t[2])));
+        accum<N>(A[j], f, j, s);
+      }
     }
   }
   unmodes<N>(A, u);
@@ -172,38 +242,55 @@ __device__ void laplace_general(typename N::T u[8], const typename N::T del[8][3
 
 // Vector Laplace element (Eq. 5: the flux of Eq. 7 for each component, geometry shared), in place
 // on u[component][corner]; slot accumulators in shared memory as for elasticity.
-template <class N>
+template <class N, bool PA = false>
 __device__ void vector_laplace_general(typename N::T u[3][8], const typename N::T del[8][3], const typename N::T hh[3],
-                                       typename N::T kappa, typename N::S *Ash, int stride) {
+                                       typename N::T kappa, typename N::S *Ash, int stride, const PaView &P = PaView{}) {
   using T = typename N::T;
   T cd[3][8];
+  if constexpr (!PA) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 3; ++i) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a) cd[i][a] = del[a][i];
-    modes<N>(cd[i]);
+      for (int a = 0; a < 8; ++a) cd[i][a] = del[a][i];
+      modes<N>(cd[i]);
+    }
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) modes<N>(u[c]);
   for (int t = 0; t < 36; ++t) N::st(Ash[t * stride], N::zero());
-#pragma unroll 1
+  if constexpr (PA) pa_issue<N>(P, 0, 6);
+#pragma unroll ((PA && std::is_same<N, NumF32>::value) ? 8 : 1)
   for (int q = 0; q < 8; ++q) {
     const int s[3] = {(q & 1) ? 1 : -1, (q & 2) ? 1 : -1, (q & 4) ? 1 : -1};
-    T J[3][3], C[3][3];
-    jac<N>(cd, hh, s, J);
-    const T det = adj<N>(J, C);
-    const T sc = ndiv<N>(kappa, det);
+    // flux matrix D = kappa adj(J) adj(J)^T / det (stored, or formed from J)
+    T D[6];
+    if constexpr (PA) {
+      if (q < 7) pa_issue<N>(P, q + 1, 6);
+      pa_wait<N>(q);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) D[k] = pa_load<N>(P, q, 6, k);
+    } else {
+      T J[3][3], C[3][3];
+      jac<N>(cd, hh, s, J);
+      const T det = adj<N>(J, C);
+      const T sc = ndiv<N>(kappa, det);
+      const int r[6] = {0, 0, 0, 1, 1, 2}, cc[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        D[k] = N::mul(sc, N::add(N::add(N::mul(C[r[k]][0], C[cc[k]][0]), N::mul(C[r[k]][1], C[cc[k]][1])),
+                                 N::mul(C[r[k]][2], C[cc[k]][2])));
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      T gu[3], t[3];
+      T gu[3];
 #pragma unroll
       for (int j = 0; j < 3; ++j) gu[j] = dref<N>(u[c], j, s);
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        t[k] = N::add(N::add(N::mul(C[0][k], gu[0]), N::mul(C[1][k], gu[1])), N::mul(C[2][k], gu[2]));
+      const T fv[3] = {N::add(N::add(N::mul(D[0], gu[0]), N::mul(D[1], gu[1])), N::mul(D[2], gu[2])),
+                       N::add(N::add(N::mul(D[1], gu[0]), N::mul(D[3], gu[1])), N::mul(D[4], gu[2])),
+                       N::add(N::add(N::mul(D[2], gu[0]), N::mul(D[4], gu[1])), N::mul(D[5], gu[2]))};
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        const T f = N::mul(sc, N::add(N::add(N::mul(C[j][0], t[0]), N::mul(C[j][1], t[1])), N::mul(C[j][2], t[2])));
+        const T f = fv[j];
         T A4[4];
 #pragma unroll
         for (int tt = 0; tt < 4; ++tt) A4[tt] = N::ld(Ash[((c * 3 + j) * 4 + tt) * stride]);
@@ -226,27 +313,40 @@ __device__ void vector_laplace_general(typename N::T u[3][8], const typename N::
 
 // Elasticity element (Algorithm 1), in place on u[component][corner].  The slot accumulators of
 // the three output components live in shared memory (per-thread slice `Ash`) to bound registers.
-template <class N>
+template <class N, bool PA = false>
 __device__ void elasticity_general(typename N::T u[3][8], const typename N::T del[8][3], const typename N::T hh[3],
-                                   typename N::T lam, typename N::T mu, typename N::S *Ash, int stride) {
+                                   typename N::T lam, typename N::T mu, typename N::S *Ash, int stride,
+                                   const PaView &P = PaView{}) {
   using T = typename N::T;
   T cd[3][8];
+  if constexpr (!PA) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 3; ++i) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a) cd[i][a] = del[a][i];
-    modes<N>(cd[i]);
+      for (int a = 0; a < 8; ++a) cd[i][a] = del[a][i];
+      modes<N>(cd[i]);
+    }
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) modes<N>(u[c]);
   for (int t = 0; t < 36; ++t) N::st(Ash[t * stride], N::zero());
-#pragma unroll 1
+  if constexpr (PA) pa_issue<N>(P, 0, 10);
+#pragma unroll ((PA && std::is_same<N, NumF32>::value) ? 8 : 1)
   for (int q = 0; q < 8; ++q) {
     const int s[3] = {(q & 1) ? 1 : -1, (q & 2) ? 1 : -1, (q & 4) ? 1 : -1};
-    T J[3][3], C[3][3];
-    jac<N>(cd, hh, s, J);
-    const T det = adj<N>(J, C);
-    const T idet = ndiv<N>(N::c(1.0f, 0.0f), det);
+    T C[3][3], idet;
+    if constexpr (PA) {
+      if (q < 7) pa_issue<N>(P, q + 1, 10);
+      pa_wait<N>(q);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) C[k / 3][k % 3] = pa_load<N>(P, q, 10, k);
+      idet = pa_load<N>(P, q, 10, 9);
+    } else {
+      T J[3][3];
+      jac<N>(cd, hh, s, J);
+      const T det = adj<N>(J, C);
+      idet = ndiv<N>(N::c(1.0f, 0.0f), det);
+    }
     T G[3][3];  // grad u = H C / det, H_cj = d_j u_c
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -300,12 +400,13 @@ struct GenSmem {
   typename N::S dp[2][NP * 3];
   typename N::S acc[2][NACC];
   typename N::S ash[PHYS == MF_LAPLACE ? 1 : 36 * EX * EY];
+  typename N::S pbuf[std::is_same<N, NumDW>::value ? 20 * EX * EY : 1];  // partial-assembly prefetch slots
 };
 
 // Same tile traversal as tile_item (owner computes, z-march, fixed accumulation order), with the
 // node offsets staged next to the input values.
-template <int PHYS, class N, int EX, int EY>
-__global__ void __launch_bounds__(EX *EY, 1) gen_apply(GenArgs g, const typename N::IO *__restrict__ x,
+template <int PHYS, class N, int EX, int EY, bool PA>
+__global__ void __launch_bounds__(EX *EY, (PA && std::is_same<N, NumF32>::value) ? 2 : 1) gen_apply(GenArgs g, const typename N::IO *__restrict__ x,
                                                        typename N::IO *__restrict__ y, const int *__restrict__ skip) {
   using T = typename N::T;
   using S = typename N::S;
@@ -349,8 +450,10 @@ __global__ void __launch_bounds__(EX *EY, 1) gen_apply(GenArgs g, const typename
       dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
 #pragma unroll
       for (int c = 0; c < ND; ++c) xr[l][c] = ok ? __ldg(x + node * ND + c) : (IO)0;
+      if constexpr (!PA) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) dl[l][c] = ok ? __ldg(g.delta + node * 3 + c) : make_float2(0.f, 0.f);
+        for (int c = 0; c < 3; ++c) dl[l][c] = ok ? __ldg(g.delta + node * 3 + c) : make_float2(0.f, 0.f);
+      }
     }
   };
   auto stage = [&](int k) {
@@ -360,8 +463,10 @@ __global__ void __launch_bounds__(EX *EY, 1) gen_apply(GenArgs g, const typename
       if (p < NP) {
 #pragma unroll
         for (int c = 0; c < ND; ++c) N::st(sm.up[k & 1][p * ND + c], dr[l] ? N::zero() : N::in(xr[l][c]));
+        if constexpr (!PA) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) N::st(sm.dp[k & 1][p * 3 + c], N::from2(dl[l][c]));
+          for (int c = 0; c < 3; ++c) N::st(sm.dp[k & 1][p * 3 + c], N::from2(dl[l][c]));
+        }
       }
     }
   };
@@ -396,17 +501,18 @@ __global__ void __launch_bounds__(EX *EY, 1) gen_apply(GenArgs g, const typename
 #pragma unroll
         for (int c = 0; c < ND; ++c) v[c][a] = N::ld(sm.up[pl][p * ND + c]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) del[a][c] = N::ld(sm.dp[pl][p * 3 + c]);
+        for (int c = 0; c < 3; ++c) del[a][c] = PA ? N::zero() : N::ld(sm.dp[pl][p * 3 + c]);
       }
       const int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
       const T hh[3] = {hxh, hyh, N::from2(__ldg(g.hh + g.nx + g.ny + ez))};
+      const PaView P{g.pa, g.n_cells, e, sm.pbuf + tid, NT};
       if constexpr (PHYS == MF_LAPLACE) {
-        laplace_general<N>(v[0], del, hh, N::from2(__ldg(g.mat + e)));
+        laplace_general<N, PA>(v[0], del, hh, N::from2(__ldg(g.mat + e)), P);
       } else if constexpr (PHYS == MF_VECTOR_LAPLACE) {
-        vector_laplace_general<N>(v, del, hh, N::from2(__ldg(g.mat + e)), sm.ash + tid, NT);
+        vector_laplace_general<N, PA>(v, del, hh, N::from2(__ldg(g.mat + e)), sm.ash + tid, NT, P);
       } else {
-        elasticity_general<N>(v, del, hh, N::from2(__ldg(g.mat + 2 * e)), N::from2(__ldg(g.mat + 2 * e + 1)),
-                              sm.ash + tid, NT);
+        elasticity_general<N, PA>(v, del, hh, N::from2(__ldg(g.mat + 2 * e)), N::from2(__ldg(g.mat + 2 * e + 1)),
+                                  sm.ash + tid, NT, P);
       }
     }
     const bool bot = ez >= k0, top = ez + 1 < k1;
@@ -480,7 +586,7 @@ template <class N> struct GenShape<MF_LAPLACE, N> { static constexpr int EX = 32
 template <class N> struct GenShape<MF_ELASTICITY, N> { static constexpr int EX = 32, EY = 8; };
 template <class N> struct GenShape<MF_VECTOR_LAPLACE, N> { static constexpr int EX = 32, EY = 8; };
 
-template <int PHYS, class N>
+template <int PHYS, class N, bool PA>
 mf_status gen_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s, const int *skip) {
   constexpr int EX = GenShape<PHYS, N>::EX, EY = GenShape<PHYS, N>::EY;
   GenArgs g;
@@ -496,8 +602,10 @@ mf_status gen_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *
   g.delta = m->gen_delta;
   g.mat = m->mat_pairs;
   g.dmask = m->dmask;
+  g.pa = std::is_same<N, NumDW>::value ? (const void *)m->pa : (const void *)m->pa32;
+  g.n_cells = m->n_cells;
   const int smem = (int)sizeof(GenSmem<PHYS, N, EX, EY>);
-  auto kern = gen_apply<PHYS, N, EX, EY>;
+  auto kern = gen_apply<PHYS, N, EX, EY, PA>;
   static bool set = false;
   if (!set) {
     MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -511,6 +619,9 @@ mf_status gen_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *
 }
 
 }  // namespace
+
+// values stored by partial assembly: 8 Gauss points x (10 elasticity, 6 Laplace) per cell
+static int64_t pa_values(const mf_mesh *m) { return 8LL * (m->physics == MF_ELASTICITY ? 10 : 6) * m->n_cells; }
 
 mf_status gen_setup(mf_mesh *m, cudaStream_t s) {
   if (!m->structured || m->tp) return MF_OK;
@@ -527,17 +638,107 @@ mf_status gen_setup(mf_mesh *m, cudaStream_t s) {
   MF_CUDA(cudaGetLastError());
   MF_CUDA(cudaStreamSynchronize(s));
   m->gen = true;
+  // the auto variant uses partial assembly when its data take at most a quarter of the free memory
+  size_t free_b = 0, total_b = 0;
+  MF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  if ((double)pa_values(m) * (sizeof(float2) + sizeof(float)) <= 0.25 * (double)free_b) MF_TRY(pa_setup(m, s));
+  return MF_OK;
+}
+
+namespace {
+
+// Quadrature-point data of partial assembly, computed in FP64 from the node coordinates (J, adj J,
+// det J at the 2x2x2 Gauss points, Algorithm 1) and stored as pairs and floats: one thread per cell.
+template <int PHYS>
+__global__ void pa_build(const double *__restrict__ X, int nx, int ny, int nz, const double *__restrict__ mat,
+                         float2 *__restrict__ pa, float *__restrict__ pa32) {
+  constexpr int K = PHYS == MF_ELASTICITY ? 10 : 6;
+  const int64_t E = (int64_t)nx * ny * nz;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((int64_t)nx * ny));
+  double Xe[8][3];
+  for (int a = 0; a < 8; ++a) {
+    const int64_t node = (i + (a & 1)) + (int64_t)(nx + 1) * ((j + ((a >> 1) & 1)) + (int64_t)(ny + 1) * (k + (a >> 2)));
+    for (int c = 0; c < 3; ++c) Xe[a][c] = X[3 * node + c];
+  }
+  for (int q = 0; q < 8; ++q) {
+    double xi[3];
+    for (int d = 0; d < 3; ++d) xi[d] = q1::sgn(q, d) * q1::kG;
+    double J[3][3], C[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        double sum = 0.0;
+        for (int a = 0; a < 8; ++a) sum += Xe[a][r] * q1::dN_at(xi, a, c);
+        J[r][c] = sum;
+      }
+    const double det = q1::adjugate(J, C);
+    double v[K];
+    if (PHYS == MF_ELASTICITY) {
+      for (int t = 0; t < 9; ++t) v[t] = C[t / 3][t % 3];
+      v[9] = 1.0 / det;
+    } else {
+      const int r[6] = {0, 0, 0, 1, 1, 2}, c[6] = {0, 1, 2, 1, 2, 2};
+      for (int t = 0; t < 6; ++t)
+        v[t] = mat[e] * (C[r[t]][0] * C[c[t]][0] + C[r[t]][1] * C[c[t]][1] + C[r[t]][2] * C[c[t]][2]) / det;
+    }
+    for (int t = 0; t < K; ++t) {
+      const dw d = dwa::from_double_slow(v[t]);
+      const int64_t idx = ((int64_t)q * K + t) * E + e;
+      pa[idx] = make_float2(d.h, d.l);
+      pa32[idx] = (float)v[t];
+    }
+  }
+}
+
+template <class N>
+mf_status gen_dispatch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
+                       const int *skip) {
+  const bool pa = m->pa && m->variant != MF_VARIANT_GENERAL;
+  if (m->physics == MF_LAPLACE)
+    return pa ? gen_launch<MF_LAPLACE, N, true>(m, x, y, s, skip) : gen_launch<MF_LAPLACE, N, false>(m, x, y, s, skip);
+  if (m->physics == MF_VECTOR_LAPLACE)
+    return pa ? gen_launch<MF_VECTOR_LAPLACE, N, true>(m, x, y, s, skip)
+              : gen_launch<MF_VECTOR_LAPLACE, N, false>(m, x, y, s, skip);
+  return pa ? gen_launch<MF_ELASTICITY, N, true>(m, x, y, s, skip)
+            : gen_launch<MF_ELASTICITY, N, false>(m, x, y, s, skip);
+}
+
+}  // namespace
+
+mf_status pa_setup(mf_mesh *m, cudaStream_t s) {
+  if (m->pa) return MF_OK;
+  if (!m->gen) {
+    mf_set_error("partial assembly needs a structured mesh that is not a tensor-product grid");
+    return MF_ERR_UNSUPPORTED;
+  }
+  const int64_t n = pa_values(m);
+  cudaError_t e = cudaMalloc(&m->pa, n * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&m->pa32, n * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(m->pa);
+    cudaFree(m->pa32);
+    m->pa = nullptr;
+    m->pa32 = nullptr;
+    mf_set_error("partial assembly: no room for %lld quadrature-point values", (long long)n);
+    return MF_ERR_OOM;
+  }
+  if (m->physics == MF_ELASTICITY)
+    pa_build<MF_ELASTICITY><<<blocks_for(m->n_cells), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->mat, m->pa,
+                                                                          m->pa32);
+  else
+    pa_build<MF_LAPLACE><<<blocks_for(m->n_cells), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->mat, m->pa,
+                                                                       m->pa32);
+  MF_CUDA(cudaGetLastError());
+  MF_CUDA(cudaStreamSynchronize(s));
   return MF_OK;
 }
 
 mf_status gen_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip) {
-  if (m->physics == MF_LAPLACE) return gen_launch<MF_LAPLACE, NumDW>(m, x, y, s, skip);
-  if (m->physics == MF_VECTOR_LAPLACE) return gen_launch<MF_VECTOR_LAPLACE, NumDW>(m, x, y, s, skip);
-  return gen_launch<MF_ELASTICITY, NumDW>(m, x, y, s, skip);
+  return gen_dispatch<NumDW>(m, x, y, s, skip);
 }
 
 mf_status gen_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip) {
-  if (m->physics == MF_LAPLACE) return gen_launch<MF_LAPLACE, NumF32>(m, x, y, s, skip);
-  if (m->physics == MF_VECTOR_LAPLACE) return gen_launch<MF_VECTOR_LAPLACE, NumF32>(m, x, y, s, skip);
-  return gen_launch<MF_ELASTICITY, NumF32>(m, x, y, s, skip);
+  return gen_dispatch<NumF32>(m, x, y, s, skip);
 }

@@ -133,6 +133,11 @@ struct mf_mesh {
   float2 *gen_delta = nullptr;
   float2 *tp_axis = nullptr;
   float2 *mat_pairs = nullptr;
+  // partial assembly of the general structured geometry (Table 3): per quadrature point the flux
+  // matrix (Laplace, 6 values) or adj(J) and 1/det J (elasticity, 10 values), as float pairs and as
+  // floats, [q][k][cell]; built when it fits the device (auto variant) or on request
+  float2 *pa = nullptr;
+  float *pa32 = nullptr;
 
   MeshView view() const {
     MeshView v;
@@ -165,6 +170,7 @@ mf_status tile_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream
 mf_status tile_apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s);
 // general structured kernels (mf_general.cu)
 mf_status gen_setup(mf_mesh *m, cudaStream_t s);
+mf_status pa_setup(mf_mesh *m, cudaStream_t s);
 mf_status gen_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip);
 mf_status gen_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip);
 // diag(A) of the matrix-free operator (Jacobi), FP64, Dirichlet rows 1.

@@ -162,6 +162,8 @@ static void free_mesh(mf_mesh *m) {
   cudaFree(m->mat_pairs);
   cudaFree(m->gen_axis);
   cudaFree(m->gen_delta);
+  cudaFree(m->pa);
+  cudaFree(m->pa32);
   delete m;
 }
 
@@ -353,14 +355,23 @@ extern "C" mf_status mf_mesh_query(const mf_mesh *m, int64_t *n_nodes, int64_t *
   if (n_dof) *n_dof = m->n_dof;
   if (n_free) *n_free = m->n_free;
   if (n_colours) *n_colours = m->n_colours;
-  if (flags) *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0);
+  if (flags) *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0) | (m->pa ? 8 : 0);
   return MF_OK;
 }
 
 extern "C" mf_status mf_set_apply_variant(mf_mesh *m, int variant) {
   MF_ARG(m != nullptr, "mf_set_apply_variant: mesh is NULL");
-  MF_ARG(variant == MF_VARIANT_AUTO || variant == MF_VARIANT_REFERENCE, "mf_set_apply_variant: unknown variant %d",
-         variant);
+  MF_ARG(variant == MF_VARIANT_AUTO || variant == MF_VARIANT_REFERENCE || variant == MF_VARIANT_GENERAL ||
+             variant == MF_VARIANT_PARTIAL,
+         "mf_set_apply_variant: unknown variant %d", variant);
+  if (variant == MF_VARIANT_GENERAL || variant == MF_VARIANT_PARTIAL) {
+    if (!m->gen) {
+      mf_set_error("mf_set_apply_variant: the general and partial-assembly variants need a structured mesh that is "
+                   "not a tensor-product grid");
+      return MF_ERR_UNSUPPORTED;
+    }
+  }
+  if (variant == MF_VARIANT_PARTIAL && !m->pa) MF_TRY(pa_setup(m, 0));
   m->variant = variant;
   return MF_OK;
 }

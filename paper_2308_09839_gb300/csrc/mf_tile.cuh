@@ -50,6 +50,7 @@ struct NumDW {  // FP64-accurate double-word
   static __device__ __forceinline__ T zero() { return dw{0.f, 0.f}; }
   static __device__ __forceinline__ T add(T a, T b) { return dwa::add(a, b); }
   static __device__ __forceinline__ T sub(T a, T b) { return dwa::sub(a, b); }
+  static __device__ __forceinline__ T neg(T a) { return dwa::neg(a); }  // exact
   static __device__ __forceinline__ T mul(T a, T b) { return dwa::mul(a, b); }
   static __device__ __forceinline__ T scale(T a, float p) { return dwa::scale(a, p); }
   static __device__ __forceinline__ T from2(float2 v) { return dw{v.x, v.y}; }
@@ -67,6 +68,7 @@ struct NumF32 {  // plain FP32 (mixed-precision inner solves)
   static __device__ __forceinline__ T zero() { return 0.f; }
   static __device__ __forceinline__ T add(T a, T b) { return a + b; }
   static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+  static __device__ __forceinline__ T neg(T a) { return -a; }
   static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
   static __device__ __forceinline__ T scale(T a, float p) { return a * p; }
   static __device__ __forceinline__ T from2(float2 v) { return v.x; }

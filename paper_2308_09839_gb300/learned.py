@@ -41,11 +41,14 @@ def node_logk(p) -> np.ndarray:
 def generate_pairs(mesh: mf.Mesh, p, n_pairs: int, seed: int = 0, k_range=(2, 150), smooth: int = 2):
     """Training pairs on the device (float32 [n_pairs][n_nodes] each) and the output scale c.
 
-    For a seeded random exact solution x*, b = A x* and the FP64 Jacobi-preconditioned CG solver
+    For a seeded random exact solution x* (white noise from a seeded device generator, smoothed 0 to
+    `smooth` times by a 7-point average), b = A x* and the FP64 Jacobi-preconditioned CG solver
     runs k iterations (k log-uniform in k_range); with r = b - A x_k, e = x* - x_k and D = diag(A) the
     pair is input D^{-1/2} r / s and target D^{1/2} e c / s, s = RMS(D^{-1/2} r) (the symmetrically
     scaled system's residual and error).  c makes the targets O(1)."""
     rng = np.random.default_rng(seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
     n = p.n_dof
     dmask = torch.from_numpy(p.dirichlet.astype(bool)).cuda()
     diag = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -56,7 +59,7 @@ def generate_pairs(mesh: mf.Mesh, p, n_pairs: int, seed: int = 0, k_range=(2, 15
     ratios = []
     nzyx = (p.nz + 1, p.ny + 1, p.nx + 1)
     for i in range(n_pairs):
-        xs = torch.from_numpy(rng.normal(size=nzyx)).cuda()
+        xs = torch.randn(nzyx, dtype=torch.float64, device="cuda", generator=gen)
         for _ in range(int(rng.integers(0, smooth + 1))):
             xs = (xs + torch.roll(xs, 1, 0) + torch.roll(xs, -1, 0) + torch.roll(xs, 1, 1) + torch.roll(xs, -1, 1)
                   + torch.roll(xs, 1, 2) + torch.roll(xs, -1, 2)) / 7.0

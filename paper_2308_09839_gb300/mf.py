@@ -23,7 +23,7 @@ MF_OK, MF_NOT_CONVERGED = 0, 1
 MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_MESH, MF_ERR_OOM, MF_ERR_BREAKDOWN, MF_ERR_TIMEOUT, MF_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
 MF_LAPLACE, MF_ELASTICITY, MF_VECTOR_LAPLACE = 0, 1, 2
 PHYSICS = {"laplace": MF_LAPLACE, "elasticity": MF_ELASTICITY, "vector_laplace": MF_VECTOR_LAPLACE}
-MF_VARIANT_AUTO, MF_VARIANT_REFERENCE = 0, 1
+MF_VARIANT_AUTO, MF_VARIANT_REFERENCE, MF_VARIANT_GENERAL, MF_VARIANT_PARTIAL = 0, 1, 2, 3
 MF_OP_MATFREE, MF_OP_CSR = 0, 1
 MF_PREC_FP64, MF_PREC_MIXED_IR = 0, 1
 MF_PC_NONE, MF_PC_JACOBI, MF_PC_LEARNED = 0, 1, 2
@@ -148,7 +148,8 @@ def mf_mesh_query(h) -> dict:
     e, f = i32(), i32()
     check(lib.mf_mesh_query(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e), C.byref(f)), "mf_mesh_query")
     return dict(n_nodes=a.value, n_cells=b.value, n_dof=c.value, n_free=d.value, n_colours=e.value,
-                structured=bool(f.value & 1), all_affine=bool(f.value & 2), tensor_product=bool(f.value & 4))
+                structured=bool(f.value & 1), all_affine=bool(f.value & 2), tensor_product=bool(f.value & 4),
+                partial_assembly=bool(f.value & 8))
 
 
 def mf_set_apply_variant(h, variant: int) -> None:

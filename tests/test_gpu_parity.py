@@ -465,3 +465,43 @@ def test_general_kernel_on_warped_mesh(physics):
     assert rel2(y, ref) <= TOL64
     mesh.set_variant(mf.MF_VARIANT_REFERENCE)
     assert rel2(gpu_apply(mesh, x), ref) <= TOL64
+
+
+# ------------------------------------------ general structured kernel and partial assembly ----
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity", "vector_laplace"])
+@pytest.mark.parametrize("variant", ["general", "partial"])
+def test_general_and_partial_assembly_variants(physics, variant):
+    """Jittered and warped structured boxes: the general kernel (geometry at every Gauss point in
+    double-word arithmetic) and partial assembly (quadrature-point data computed once in FP64 and
+    stored as float pairs) both match the oracle to 1e-12; their FP32 forms state their error."""
+    mk = {"laplace": inputs.laplace_box, "elasticity": inputs.elasticity_box,
+          "vector_laplace": inputs.vector_laplace_box}[physics]
+    p = mk(23, ny=9, nz=14, jitter=0.2, seed=31, sigma=1.0)
+    mesh = mf.Mesh.from_problem(p)
+    assert not mesh.info["tensor_product"]
+    mesh.set_variant(mf.MF_VARIANT_GENERAL if variant == "general" else mf.MF_VARIANT_PARTIAL)
+    if variant == "partial":
+        assert mf.mf_mesh_query(mesh.h)["partial_assembly"]
+    for seed in (0, 1):
+        x = p.x(seed)
+        y = gpu_apply(mesh, x)
+        ref = oracle_apply(p, x)
+        assert rel2(y, ref) <= TOL64, (physics, variant, rel2(y, ref))
+    y32 = mesh.apply(gpu(x).float())
+    torch.cuda.synchronize()
+    assert rel2(y32.double().cpu().numpy(), ref) < 2e-6
+
+
+def test_partial_assembly_is_the_auto_choice_and_rejected_on_tensor_grids():
+    p = inputs.elasticity_box(10, jitter=0.1, seed=32)
+    mesh = mf.Mesh.from_problem(p)
+    assert mesh.info["partial_assembly"]  # small mesh: the data fit, so the auto variant uses it
+    x = p.x()
+    ya = gpu_apply(mesh, x)
+    mesh.set_variant(mf.MF_VARIANT_PARTIAL)
+    assert np.array_equal(gpu_apply(mesh, x), ya)
+    q = inputs.laplace_box(6, graded=0.3, seed=33)  # tensor-product grid: face-marching kernel only
+    mq = mf.Mesh.from_problem(q)
+    with pytest.raises(mf.MfError):
+        mq.set_variant(mf.MF_VARIANT_PARTIAL)
