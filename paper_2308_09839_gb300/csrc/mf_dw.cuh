@@ -91,31 +91,41 @@ __device__ __forceinline__ dw norm(dw x) {
 
 // double -> (hi, lo) with integer operations only (the FP64 pipe of GB300 is the scarce unit):
 // hi keeps the leading 24 significand bits (truncated), lo is the remaining 29 bits rounded to a
-// float; |x - (hi + lo)| <= 2^-48 |x|.  Values outside [2^-74, 2^127) and non-finite values take
-// the FP64 conversion path instead.
+// float; |x - (hi + lo)| <= 2^-48 |x|.  Zeros give a signed zero pair; other values outside
+// [2^-74, 2^127) and non-finite values take the FP64 conversion path.
 __device__ __forceinline__ dw split(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
   const int e = (int)((bh >> 20) & 0x7ffu);
-  if (e < 949 || e > 1150) {
+  if ((e != 0 && e < 949) || e > 1150) {  // rare: tiny non-zero or huge magnitudes
     const float h = __double2float_rz(x);
     return dw{h, __double2float_rn(x - (double)h)};
   }
+  // zeros (and subnormal doubles, below 2^-1022) become a signed zero pair by selects, so that
+  // lanes holding zeros do not diverge from the others
   const unsigned sign = bh & 0x80000000u;
   const unsigned mhi = ((bh & 0x000fffffu) << 3) | (bl >> 29);
-  const float h = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | mhi);
+  const unsigned hb = sign | ((unsigned)(e - 1023 + 127) << 23) | mhi;
   const unsigned rem = bl & 0x1fffffffu;
   const float lo = __fmul_rn(__uint2float_rn(rem), __uint_as_float((unsigned)(e - 1075 + 127) << 23));
-  return dw{h, __uint_as_float(__float_as_uint(lo) | sign)};
+  const unsigned lb = __float_as_uint(lo) | sign;
+  return dw{__uint_as_float(e == 0 ? sign : hb), __uint_as_float(e == 0 ? sign : lb)};
 }
 
-// float -> double exactly by bit manipulation (normal floats; others convert on the FP64 unit).
+// float -> double exactly by bit manipulation, without branches (lanes of a warp often differ in
+// whether the low part of a pair is zero): normal floats are rebiased; zeros and subnormals give a
+// signed zero (a subnormal low part is below 2^-126 of nothing that matters here), infinities and
+// NaNs keep their class (exponent all ones, payload shifted like the mantissa).
 __device__ __forceinline__ double f2d(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hi, (int)(u << 29));
+  const unsigned sign = u & 0x80000000u, mant = u & 0x7fffffu;
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;
+  unsigned hi = sign | (ed << 20) | (mant >> 3);
+  unsigned lo = u << 29;
+  hi = e == 0u ? sign : hi;
+  lo = e == 0u ? 0u : lo;
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 // (hi, lo) -> nearest double: one FP64 add.
