@@ -279,28 +279,50 @@ def main():
     extras = {"gdofs_apply": {"laplace": F[0] / t_app[0] / 1e9, "elasticity": F[1] / t_app[1] / 1e9},
               "ms_apply": {"laplace": 1e3 * t_app[0], "elasticity": 1e3 * t_app[1]}}
 
-    # ---- end to end through the C ABI with host buffers (H2D of x, apply, D2H of y every step)
+    # ---- end to end through the C ABI with host buffers (H2D of x, apply, D2H of y every step).
+    # Each mesh alternates between two device buffer sets, each on its own stream, so the copies
+    # of one step overlap the applies of the other mesh and of the neighbouring step (the copy
+    # engines and the SMs work at the same time); every step still moves its full input and output.
     hx = [x.cpu().pin_memory() for (_, _, x, _) in meshes]
-    hy = [torch.empty_like(h).pin_memory() for h in hx]
-    for _ in range(2):
-        for j, (p, m, x, y) in enumerate(meshes):
-            x.copy_(hx[j], non_blocking=True)
-            m.apply(x, y)
-            hy[j].copy_(y, non_blocking=True)
+    hy = [[torch.empty_like(h).pin_memory() for _ in range(2)] for h in hx]
+    dx = [[x, x.clone()] for (_, _, x, _) in meshes]
+    dy = [[y, torch.empty_like(y)] for (_, _, _, y) in meshes]
+    streams = [[torch.cuda.Stream() for _ in range(2)] for _ in meshes]
+
+    def e2e_step(k):
+        b = k & 1
+        for j, (p, m, _, _) in enumerate(meshes):
+            st = streams[j][b]
+            with torch.cuda.stream(st):
+                dx[j][b].copy_(hx[j], non_blocking=True)
+                m.apply(dx[j][b], dy[j][b], stream=st)
+                hy[j][b].copy_(dy[j][b], non_blocking=True)
+
+    for k in range(4):
+        e2e_step(k)
     torch.cuda.synchronize()
-    Ke = max(5, K // 2)
+    Ke = max(6, K // 2) // 2 * 2
     barrier()
-    e0.record()
-    for _ in range(Ke):
-        for j, (p, m, x, y) in enumerate(meshes):
-            x.copy_(hx[j], non_blocking=True)
-            m.apply(x, y)
-            hy[j].copy_(y, non_blocking=True)
-    e1.record()
+    torch.cuda.synchronize()
+    main = torch.cuda.current_stream()
+    e0.record(main)
+    for sl in streams:
+        for st in sl:
+            st.wait_event(e0)
+    for k in range(Ke):
+        e2e_step(k)
+    for sl in streams:
+        for st in sl:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            main.wait_event(ev)
+    e1.record(main)
     torch.cuda.synchronize()
     e2e_value, _ = aggregate(Ke * sum(F), e0.elapsed_time(e1) / 1e3, world, dist if world > 1 else None, "cuda")
     io_bytes = sum(h.numel() * 8 for h in hx)
-    e2e = {"value": e2e_value / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
+    e2e = {"value": e2e_value / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+           "overlap": "2 streams per mesh, copies overlap applies"}
+    del dx, dy
 
     # ---- roofline of the dominant kernel (the matrix-free apply taking the most time).  The FP64-
     # accurate apply runs in double-word FP32 arithmetic and is bound by the FP32 pipe: achieved =
