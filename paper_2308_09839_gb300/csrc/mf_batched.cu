@@ -9,8 +9,8 @@
 // are separated by a grid-wide barrier.  Every problem keeps its own scalars, iteration count and
 // convergence flag; a converged problem drops out of the work lists.
 //
-// Work items: the operator is the tensor-product tile kernel of mf_tile.cuh, one item per
-// (tile column, z-segment) of each problem; the z-segment length per problem is a tunable (set by
+// Work items: the operator is the face-marching kernel of mf_march.cuh, one item per (tile column,
+// z-segment) of each problem; the z-segment length per problem is a tunable (set by
 // mf_set_tile_segment, e.g. from an autotuner).  Vector phases use chunks of kChunk DoFs.
 // Reductions: each chunk writes a partial, the last chunk of a problem to finish (per-problem
 // ticket) sums the partials in chunk order, so results do not depend on scheduling.
@@ -21,6 +21,7 @@
 #include <cmath>
 #include <vector>
 
+#include "mf_march.cuh"
 #include "mf_tile.cuh"
 
 using namespace tile;
@@ -28,7 +29,7 @@ using namespace tile;
 namespace {
 
 constexpr int kChunk = 4096;
-using Shape = TileShape<MF_LAPLACE, NumDW>;
+using Shape = march::MarchShape<MF_LAPLACE, NumDW>;
 constexpr int kEX = Shape::EX, kEY = Shape::EY, kThreadsB = kEX * kEY;
 
 struct BScalars {
@@ -135,7 +136,7 @@ __device__ bool chunk_reduce(BProblem &P, int lc, double part, double *sh, doubl
 }
 
 __global__ void __launch_bounds__(kThreadsB, 1) batched_cg(BArgs A) {
-  __shared__ TileSmem<MF_LAPLACE, NumDW, kEX, kEY, 1> sm;
+  __shared__ march::MarchSmem<1, NumDW, kEX, kEY> sm;
   __shared__ double sh[kThreadsB / 32];
   const int G = gridDim.x;
   const int tid = threadIdx.x;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) batched_cg(BArgs A) {
       const BProblem *P = A.probs + A.item_prob[w];
       if (__ldcg(&P->sc->done)) continue;
       const TileArgs g = P->g;
-      tile_item<MF_LAPLACE, NumDW, kEX, kEY, true, 1>(g, w - P->item0, P->p, P->Ap, sm);
+      march::march_item<MF_LAPLACE, NumDW, kEX, kEY, true>(g, w - P->item0, 0, P->p, P->Ap, sm);
     }
     if (!grid_barrier(A.ctl, A.budget)) return;
     // ---- B: pAp, alpha

@@ -403,10 +403,11 @@ struct GenSmem {
   typename N::S pbuf[std::is_same<N, NumDW>::value ? 20 * EX * EY : 1];  // partial-assembly prefetch slots
 };
 
-// Same tile traversal as tile_item (owner computes, z-march, fixed accumulation order), with the
-// node offsets staged next to the input values.
+// Owner-computes tile traversal marching up in z (output-plane accumulators in shared memory,
+// summed in a fixed order), with the node offsets staged next to the input values.
 template <int PHYS, class N, int EX, int EY, bool PA>
-__global__ void __launch_bounds__(EX *EY, (PA && std::is_same<N, NumF32>::value) ? 2 : 1) gen_apply(GenArgs g, const typename N::IO *__restrict__ x,
+__global__ void __launch_bounds__(EX *EY, (PA && std::is_same<N, NumF32>::value) ? 2 : 1)
+    gen_apply(GenArgs g, const typename N::IO *__restrict__ x,
                                                        typename N::IO *__restrict__ y, const int *__restrict__ skip) {
   using T = typename N::T;
   using S = typename N::S;

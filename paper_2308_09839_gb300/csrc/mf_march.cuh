@@ -1,7 +1,7 @@
 // Face-marching apply on tensor-product boxes (auto variant): scalar Laplace,
 // vector Laplace (the scalar element operator on each component, Eq. 5) and isotropic elasticity.
 //
-// The arithmetic is that of tile::laplace_apply / tile::elasticity_apply (Eqs. 7 and 9 with 2x2x2
+// The arithmetic is that of the Walsh-Hadamard form in mf_tile.cuh (Eqs. 7 and 9 with 2x2x2
 // Gauss, rewritten exactly in the Walsh-Hadamard monomial basis: A^e = H^T D_e H with D_e diagonal
 // for Laplace and diagonal plus 24 couplings between components for elasticity), in double-word
 // FP32 for FP64 accuracy or in plain FP32.  What changes is the organisation, which shares work
@@ -51,24 +51,25 @@ struct MarchSmem {
 
 // PHYS = MF_LAPLACE (Eq. 7), MF_VECTOR_LAPLACE (Eq. 5) or MF_ELASTICITY (Eq. 9, Algorithm 1);
 // vectors hold NC values per node (x, y, z components interleaved for the vector operators).
-template <int PHYS, class N, int EX, int EY, int MINB>
-__global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const typename N::IO *__restrict__ x,
-                                                            typename N::IO *__restrict__ y,
-                                                            const int *__restrict__ skip) {
+// One work item (tile column x z-segment `item`, right-hand side `rr`); must be called by all EX*EY
+// threads of the CTA.  COHERENT: read x through L2 only (x was written by other CTAs earlier in the
+// same persistent kernel, so the read-only and L1 paths may hold stale lines).
+template <int PHYS, class N, int EX, int EY, bool COHERENT>
+__device__ __forceinline__ void march_item(const TileArgs &g, int item, int64_t rr, const typename N::IO *__restrict__ x,
+                                           typename N::IO *__restrict__ y,
+                                           MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm) {
   static_assert(EX == 32, "a warp is one row of element columns");
   using T = typename N::T;
   using IO = typename N::IO;
   constexpr int NC = phys_ndpn(PHYS);
   constexpr int NT = EX * EY, PX = EX + 1, NP = (EX + 1) * (EY + 1), TX = EX - 1, TY = EY - 1;
   constexpr int LOADS = (NP + NT - 1) / NT;
-  __shared__ MarchSmem<NC, N, EX, EY> sm;
-  if (skip && *skip) return;
   (void)TX;
   (void)TY;
+  auto ldx = [](const IO *p) -> IO { return COHERENT ? __ldcg(p) : __ldg(p); };
+  __syncthreads();  // the previous item of a persistent CTA may still be reading sm
 
   const int tid = threadIdx.x;
-  const int item = blockIdx.x;
-  const int64_t rr = g.r0 + blockIdx.y;  // right-hand side of this CTA ([node][rhs][comp] vectors)
   const int bx = item % g.tiles_x;
   const int by = (item / g.tiles_x) % g.tiles_y;
   const int bz = item / (g.tiles_x * g.tiles_y);
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
       const int64_t node = nib[l] + (int64_t)k * NPL;
       dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) xr[l][c] = ok ? __ldg(x + (node * g.nrhs + rr) * NC + c) : (IO)0;
+      for (int c = 0; c < NC; ++c) xr[l][c] = ok ? ldx(x + (node * g.nrhs + rr) * NC + c) : (IO)0;
     }
   };
   auto stage = [&](int k) {
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
       for (int l = 0; l < NC; ++l) {
         const T tot = N::add(rb[l], N::ld(sm.xrow[ez & 1][l * NT + tid - EX]));
         const int64_t vi = (node * g.nrhs + rr) * NC + l;
-        y[vi] = dir ? x[vi] : N::out(tot);
+        y[vi] = dir ? ldx(x + vi) : N::out(tot);
       }
     }
 #pragma unroll
@@ -283,6 +284,15 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
 #pragma unroll
       for (int m = 0; m < 4; ++m) Fb[c][m] = Ft[c][m];
   }
+}
+
+template <int PHYS, class N, int EX, int EY, int MINB>
+__global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const typename N::IO *__restrict__ x,
+                                                            typename N::IO *__restrict__ y,
+                                                            const int *__restrict__ skip) {
+  __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
+  if (skip && *skip) return;
+  march_item<PHYS, N, EX, EY, false>(g, blockIdx.x, g.r0 + blockIdx.y, x, y, sm);
 }
 
 // Launch shapes: EX = 32 element columns per warp row, EY rows, MINB resident CTAs per SM.

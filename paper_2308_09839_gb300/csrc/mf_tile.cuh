@@ -1,14 +1,12 @@
-// Tensor-product element arithmetic (number types, Walsh-Hadamard transforms, Laplace and elasticity
-// coefficients) shared by the face-marching kernels (mf_march.cuh), and the tile work items of the
-// batched persistent solver (mf_batched.cu).
+// Tensor-product element arithmetic shared by the face-marching kernels (mf_march.cuh, which also
+// serve the batched persistent solver): number types, Walsh-Hadamard transforms, the Laplace and
+// elasticity coefficients, the work decomposition.
 #pragma once
-// Matrix-free apply for structured boxes whose cells are axis-aligned (tensor-product geometry),
-// FP64-accurate on the FP32 pipes ("auto" variant).
 //
-// What it computes is Eq. 7 (Laplace) / Eq. 9 and Algorithm 1 (elasticity) with 2x2x2 Gauss; what
-// differs from the reference kernel is how:
+// What it computes is Eq. 7 (Laplace) / Eq. 9 and Algorithm 1 (elasticity) with 2x2x2 Gauss on
+// structured boxes whose cells are axis-aligned (tensor-product geometry):
 //
-// 1. Geometry on the fly from per-axis spacings.  A cell of a tensor-product grid is the box
+// 1. Geometry from per-axis spacings.  A cell of a tensor-product grid is the box
 //    [x_i, x_i+1] x [y_j, y_j+1] x [z_k, z_k+1], so J = diag(hx, hy, hz)/2 is constant on the cell
 //    and is computed per element from three spacings (kept, with their inverses, in tiny per-axis
 //    arrays built at setup from the coordinates).  Coordinates are not re-read per apply.
@@ -21,17 +19,10 @@
 //    scalar Laplace:   v = H^T D H u,  D = diag(0, g1, g2, (g1+g2)/3, g3, (g1+g3)/3, (g2+g3)/3,
 //                      (g1+g2+g3)/9) / 16 with g1 = kappa hy hz / hx (cyclic);
 //    elasticity: the same per component plus 24 couplings between components through lam and mu
-//                (see elasticity_box below).  Each apply is two 8-point fast Walsh-Hadamard
-//    transforms per component and a few products instead of a Jacobian per Gauss point.
+//                (see elasticity_modes below).
 //
 // 3. Double-word arithmetic (mf_dw.cuh) for FP64 accuracy; the GB300 FP64 pipe is ~60x slower
 //    than FP32.  x is split into float pairs with integer operations; y leaves through one FP64 add.
-//
-// 4. Atomic-free scatter by owner computes: a CTA owns a TX x TY column of nodes over a z-segment
-//    and evaluates every element touching them (one halo element ring, recomputed by the
-//    neighbour), marching up in z with the input node planes staged in shared memory and the
-//    output planes accumulated there in a fixed order.  Every y entry is written exactly once,
-//    without a memset or read-modify-write, and the result is bitwise reproducible.
 #include <algorithm>
 #include <type_traits>
 
@@ -143,21 +134,6 @@ __device__ __forceinline__ LapCoef<N> laplace_coef(typename N::T k, typename N::
   return c;
 }
 
-// u (nodal values) -> A^e u, in place.
-template <class N>
-__device__ __forceinline__ void laplace_apply(const LapCoef<N> &c, typename N::T u[8]) {
-  fwht_fwd<N>(u);
-  u[0] = N::zero();
-  u[1] = N::mul(c.s1, u[1]);
-  u[2] = N::mul(c.s2, u[2]);
-  u[4] = N::mul(c.s3, u[4]);
-  u[3] = N::mul(c.s12, u[3]);
-  u[5] = N::mul(c.s13, u[5]);
-  u[6] = N::mul(c.s23, u[6]);
-  u[7] = N::mul(c.s123, u[7]);
-  fwht_inv<N>(u);
-}
-
 // Isotropic elasticity on an axis-aligned box.  With r_k = h_{k+1} h_{k+2} / h_k and the mode
 // coefficients c^k = H u^k:
 //   same-component terms:  W^l_k = (k == l ? lam + 2 mu : mu) r_k / 16 weighted like the Laplace D;
@@ -221,196 +197,14 @@ __device__ __forceinline__ void elasticity_modes(const ElCoef<N> &e, const typen
 #undef ACC
 }
 
-// c[k][a] (component k, corner a) -> A^e u, in place.
-template <class N>
-__device__ __forceinline__ void elasticity_apply(const ElCoef<N> &e, typename N::T c[3][8]) {
-  using T = typename N::T;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) fwht_fwd<N>(c[k]);
-  T o[3][8];
-  elasticity_modes<N>(e, c, o);
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    fwht_inv<N>(o[l]);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) c[l][a] = o[l][a];
-  }
-}
-
 struct TileArgs {
   int nx, ny, nz;
   int tiles_x, tiles_y, seg;
-  int nrhs, r0;  // vectors hold nrhs right-hand sides per node ([node][rhs][comp]); this pass does r0..r0+NR-1
+  int nrhs, r0;  // vectors hold nrhs right-hand sides per node ([node][rhs][comp]); first one of the launch
   const float2 *hx, *hy, *hz, *ihx, *ihy, *ihz;  // per-axis spacings and inverses (pairs)
   const float2 *mat;                             // kappa[E] or (lam, mu)[E] as pairs
   const uint8_t *dmask;
 };
-
-// Shared-memory footprint of one tile (staged input planes and output-plane accumulators).
-template <int PHYS, class N, int EX, int EY, int NR = 1>
-struct TileSmem {
-  static constexpr int ND = phys_ndpn(PHYS) * NR;
-  static constexpr int NP = (EX + 1) * (EY + 1), NACC = (EX - 1) * (EY - 1) * ND;
-  typename N::S up[2][NP * ND];
-  typename N::S acc[2][NACC];
-};
-
-// One work item = one CTA's tile: owned nodes [i0, i0+TX) x [j0, j0+TY) x [k0, k1); one thread per
-// element of an (EX = TX+1) x (EY = TY+1) slab of elements; marches slab by slab in z.  `item`
-// enumerates tile columns fastest, then z-segments.  Must be called by all EX*EY threads.
-// COHERENT: read x through L2 only (x was written by other CTAs earlier in the same persistent
-// kernel, so the read-only and L1 paths may hold stale lines); otherwise through the read-only path.
-template <int PHYS, class N, int EX, int EY, bool COHERENT = false, int NR = 1>
-__device__ __forceinline__ void tile_item(const TileArgs &g, int item, const typename N::IO *__restrict__ x,
-                                          typename N::IO *__restrict__ y, TileSmem<PHYS, N, EX, EY, NR> &sm) {
-  using T = typename N::T;
-  using S = typename N::S;
-  using IO = typename N::IO;
-  constexpr int NC = phys_ndpn(PHYS);  // components per node and right-hand side
-  constexpr int ND = NC * NR;                     // values per node handled by this pass
-  constexpr int NT = EX * EY, TX = EX - 1, TY = EY - 1, PX = EX + 1, PY = EY + 1, NP = PX * PY;
-  constexpr int LOADS = (NP + NT - 1) / NT;
-  constexpr int NACC = TX * TY * ND;
-  auto &up = sm.up;
-  auto &acc = sm.acc;
-  (void)PY;
-
-  __syncthreads();  // the previous item of a persistent CTA may still be reading sm
-  const int tid = threadIdx.x;
-  const int bx = item % g.tiles_x;
-  const int by = (item / g.tiles_x) % g.tiles_y;
-  const int bz = item / (g.tiles_x * g.tiles_y);
-  const int i0 = bx * TX, j0 = by * TY;
-  const int NXP = g.nx + 1, NYP = g.ny + 1;
-  const int k0 = bz * g.seg, k1 = min(k0 + g.seg, g.nz + 1);
-  const int tx = tid % EX, ty = tid / EX;
-  const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;
-  const bool ein = ex >= 0 && ex < g.nx && ey >= 0 && ey < g.ny;
-  const int ownx = min(TX, NXP - i0), owny = min(TY, NYP - j0);
-
-  T hx = N::zero(), hy = N::zero(), ihx = N::zero(), ihy = N::zero();
-  if (ein) {
-    hx = N::from2(__ldg(g.hx + ex));
-    ihx = N::from2(__ldg(g.ihx + ex));
-    hy = N::from2(__ldg(g.hy + ey));
-    ihy = N::from2(__ldg(g.ihy + ey));
-  }
-  const T hy_ihx = N::mul(hy, ihx), hx_ihy = N::mul(hx, ihy), hxhy = N::mul(hx, hy);
-  for (int t = tid; t < 2 * NACC; t += NT) N::st(acc[t / NACC][t % NACC], N::zero());
-
-  IO xr[LOADS][ND];
-  bool dr[LOADS];
-  auto fetch = [&](int k) {
-#pragma unroll
-    for (int l = 0; l < LOADS; ++l) {
-      const int p = tid + l * NT;
-      const int ix = i0 - 1 + p % PX, iy = j0 - 1 + p / PX;
-      const bool ok = p < NP && ix >= 0 && ix < NXP && iy >= 0 && iy < NYP;
-      const int64_t node = ix + (int64_t)NXP * (iy + (int64_t)NYP * k);
-      const int64_t vb = (node * g.nrhs + g.r0) * NC;
-      dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
-#pragma unroll
-      for (int c = 0; c < ND; ++c) xr[l][c] = ok ? (COHERENT ? __ldcg(x + vb + c) : __ldg(x + vb + c)) : (IO)0;
-    }
-  };
-  auto stage = [&](int k) {
-    S *u = up[k & 1];
-#pragma unroll
-    for (int l = 0; l < LOADS; ++l) {
-      const int p = tid + l * NT;
-      if (p < NP)
-#pragma unroll
-        for (int c = 0; c < ND; ++c) N::st(u[p * ND + c], dr[l] ? N::zero() : N::in(xr[l][c]));
-    }
-  };
-  auto write_plane = [&](int k) {
-    S *a = acc[k & 1];
-    for (int t = tid; t < NACC; t += NT) {
-      const int idx = t / ND, c = t % ND;
-      const int lx = idx % TX, ly = idx / TX;
-      if (lx < ownx && ly < owny) {
-        const int64_t node = (i0 + lx) + (int64_t)NXP * ((j0 + ly) + (int64_t)NYP * k);
-        const int64_t vi = (node * g.nrhs + g.r0) * NC + c;
-        y[vi] = __ldg(g.dmask + node) ? (COHERENT ? __ldcg(x + vi) : x[vi]) : N::out(N::ld(a[t]));
-      }
-      N::st(a[t], N::zero());
-    }
-  };
-
-  const int s_lo = max(k0 - 1, 0), s_hi = min(k1 - 1, g.nz - 1);
-  fetch(s_lo);
-  stage(s_lo);
-  fetch(s_lo + 1);
-  for (int ez = s_lo; ez <= s_hi; ++ez) {
-    stage(ez + 1);
-    __syncthreads();
-    if (ez + 2 <= g.nz) fetch(ez + 2);
-    // element coefficients (geometry, material) once per element, then per right-hand side: gather,
-    // evaluate and accumulate (one right-hand side's values live in registers at a time)
-    const int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
-    const T hz = N::from2(__ldg(g.hz + ez)), ihz = N::from2(__ldg(g.ihz + ez));
-    using Coef = std::conditional_t<phys_is_laplace(PHYS), LapCoef<N>, ElCoef<N>>;
-    Coef cf;
-    if (ein) {
-      if constexpr (phys_is_laplace(PHYS)) {
-        cf = laplace_coef<N>(N::from2(__ldg(g.mat + e)), hy_ihx, hx_ihy, hxhy, hz, ihz);
-      } else {
-        const T h[3] = {hx, hy, hz}, ih[3] = {ihx, ihy, ihz};
-        cf = elasticity_coef<N>(N::from2(__ldg(g.mat + 2 * e)), N::from2(__ldg(g.mat + 2 * e + 1)), h, ih);
-      }
-    }
-    const bool bot = ez >= k0, top = ez + 1 < k1;
-#pragma unroll 1
-    for (int r = 0; r < NR; ++r) {
-      T v[NC][8];
-      if (ein) {
-        const S *ub = up[ez & 1];
-        const S *ut = up[(ez + 1) & 1];
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const int p = (tx + (a & 1)) + PX * (ty + ((a >> 1) & 1));
-          const S *u = (a & 4) ? ut : ub;
-#pragma unroll
-          for (int c = 0; c < NC; ++c) v[c][a] = N::ld(u[p * ND + r * NC + c]);
-        }
-        if constexpr (phys_is_laplace(PHYS)) {
-#pragma unroll
-          for (int c = 0; c < NC; ++c) laplace_apply<N>(cf, v[c]);
-        } else {
-          elasticity_apply<N>(cf, v);
-        }
-      }
-#pragma unroll
-      for (int ay = 0; ay < 2; ++ay) {
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax) {
-          const int lx = tx - 1 + ax, ly = ty - 1 + ay;
-          if (ein && lx >= 0 && lx < ownx && ly >= 0 && ly < owny) {
-            const int idx = (lx + TX * ly) * ND + r * NC;
-            const int a = ax + 2 * ay;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              if (bot) N::st(acc[ez & 1][idx + c], N::add(N::ld(acc[ez & 1][idx + c]), v[c][a]));
-              if (top) N::st(acc[(ez + 1) & 1][idx + c], N::add(N::ld(acc[(ez + 1) & 1][idx + c]), v[c][a + 4]));
-            }
-          }
-          __syncwarp();
-        }
-        __syncthreads();
-      }
-    }
-    if (ez >= k0) write_plane(ez);
-  }
-  if (s_hi + 1 == g.nz && g.nz >= k0 && g.nz < k1) write_plane(g.nz);
-}
-
-// Tile shapes (elements per slab row x rows) and minimum resident CTAs per SM.
-template <int PHYS, class N> struct TileShape;
-template <> struct TileShape<MF_LAPLACE, NumDW> { static constexpr int EX = 32, EY = 16, MINB = 2; };
-template <> struct TileShape<MF_LAPLACE, NumF32> { static constexpr int EX = 32, EY = 16, MINB = 2; };
-template <> struct TileShape<MF_ELASTICITY, NumDW> { static constexpr int EX = 32, EY = 8, MINB = 2; };
-template <> struct TileShape<MF_ELASTICITY, NumF32> { static constexpr int EX = 32, EY = 8, MINB = 2; };
-template <class N> struct TileShape<MF_VECTOR_LAPLACE, N> { static constexpr int EX = 32, EY = 8, MINB = 2; };
 
 // Segment length from a wave model: with R CTAs resident at a time, nseg segments of seg = ceil((nz
 // + 1) / nseg) planes take about ceil(cols * nseg / R) waves of (seg + 1) element layers each (the
