@@ -135,7 +135,7 @@ __device__ bool chunk_reduce(BProblem &P, int lc, double part, double *sh, doubl
   return true;
 }
 
-__global__ void __launch_bounds__(kThreadsB, 1) batched_cg(BArgs A) {
+__global__ void __launch_bounds__(kThreadsB, 4) batched_cg(BArgs A) {
   __shared__ march::MarchSmem<1, NumDW, kEX, kEY> sm;
   __shared__ double sh[kThreadsB / 32];
   const int G = gridDim.x;

@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
 }
 
 // Launch shapes: EX = 32 element columns per warp row, EY rows, MINB resident CTAs per SM.
-template <int PHYS, class N> struct MarchShape { static constexpr int EX = 32, EY = 16, MINB = 2; };
+template <int PHYS, class N> struct MarchShape { static constexpr int EX = 32, EY = 8, MINB = 4; };
 template <class N> struct MarchShape<MF_ELASTICITY, N> { static constexpr int EX = 32, EY = 8, MINB = 1; };
 template <class N> struct MarchShape<MF_VECTOR_LAPLACE, N> { static constexpr int EX = 32, EY = 8, MINB = 2; };
 
