@@ -146,6 +146,27 @@ def slab(p, nz_slab):
                           p.dirichlet[:nn], p.seed)
 
 
+def bind_to_gpu_numa(device: int):
+    """Bind this process to the CPUs of the NUMA node of `device` (read from sysfs through the GPU's
+    PCI address); returns the node, or None when the topology cannot be read (then nothing changes)."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(device)
+        addr = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        node = int(open(f"/sys/bus/pci/devices/{addr}/numa_node").read().strip())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        return node
+    except (AttributeError, OSError, ValueError):
+        return None
+
+
 def oracle_sample_rate(problems, nz_slabs, repeats=1):
     """Time the oracle's apply on slabs of each problem; returns (free DoF per second scaled from
     the full problems' DoF per cell, seconds, description)."""
@@ -280,6 +301,9 @@ def main():
               "ms_apply": {"laplace": 1e3 * t_app[0], "elasticity": 1e3 * t_app[1]}}
 
     # ---- end to end through the C ABI with host buffers (H2D of x, apply, D2H of y every step).
+    # The host buffers are allocated (first touch) by a thread bound to the CPUs of the NUMA node
+    # the GPU is attached to, so the copies do not cross the link between the host's sockets.
+    numa_node = bind_to_gpu_numa(local)
     # Each mesh alternates between two device buffer sets, each on its own stream, so the copies
     # of one step overlap the applies of the other mesh and of the neighbouring step (the copy
     # engines and the SMs work at the same time); every step still moves its full input and output.
@@ -321,7 +345,7 @@ def main():
     e2e_value, _ = aggregate(Ke * sum(F), e0.elapsed_time(e1) / 1e3, world, dist if world > 1 else None, "cuda")
     io_bytes = sum(h.numel() * 8 for h in hx)
     e2e = {"value": e2e_value / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
-           "overlap": "2 streams per mesh, copies overlap applies"}
+           "overlap": "2 streams per mesh, copies overlap applies", "host_numa_node": numa_node}
     del dx, dy
 
     # ---- roofline of the dominant kernel (the matrix-free apply taking the most time).  The FP64-
