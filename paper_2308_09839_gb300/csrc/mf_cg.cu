@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kRedThreads) cg_init(int64_t n, const R *__res
   }
 }
 
-// pAp = p.Ap; alpha = rho / pAp.
+// pAp = p.Ap (when the operator does not fuse it into its own write phase).
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) cg_pap(int64_t n, const R *__restrict__ p, const R *__restrict__ Ap,
                                                       double *partials, CgScalars *sc) {
@@ -127,16 +127,7 @@ __global__ void __launch_bounds__(kRedThreads) cg_pap(int64_t n, const R *__rest
   double v[1] = {0.0};
   GRID_STRIDE(i, n) v[0] += (double)p[i] * (double)Ap[i];
   double out[1];
-  if (grid_reduce<1>(v, partials, &sc->ticket, out) && threadIdx.x == 0) {
-    const double pap = out[0];
-    sc->pAp = pap;
-    if (!(pap > 0.0) || !isfinite(pap)) {
-      sc->status = MF_ERR_BREAKDOWN;
-      sc->done = 1;
-    } else {
-      sc->alpha = sc->rz / pap;
-    }
-  }
+  if (grid_reduce<1>(v, partials, &sc->ticket, out) && threadIdx.x == 0) sc->pAp = out[0];
 }
 
 // x += alpha p; r -= alpha Ap; rho' = r.z (z = M r), ||r||^2; beta = rho'/rho; convergence test.
@@ -146,7 +137,17 @@ __global__ void __launch_bounds__(kRedThreads) cg_update_xr(int64_t n, R *__rest
                                                             const double *__restrict__ invdiag, double *partials,
                                                             CgScalars *sc) {
   if (sc->done) return;
-  const double alpha = sc->alpha;
+  // alpha = rho / pAp (every block forms it from the same scalars; block 0 records it)
+  const double pap = sc->pAp;
+  if (!(pap > 0.0) || !isfinite(pap)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc->status = MF_ERR_BREAKDOWN;
+      sc->done = 1;
+    }
+    return;
+  }
+  const double alpha = sc->rz / pap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->alpha = alpha;
   double v[2] = {0.0, 0.0};
   GRID_STRIDE(i, n) {
     x[i] = (R)((double)x[i] + alpha * (double)p[i]);
@@ -214,6 +215,8 @@ __global__ void add_f32(int64_t n, double *__restrict__ x, const float *__restri
 }
 
 using OpFn = std::function<mf_status(const void *in, void *out, cudaStream_t s, const int *skip)>;
+// operator with in . out fused: writes the dot product to *dot (null function when not available)
+using OpDotFn = std::function<mf_status(const void *in, void *out, cudaStream_t s, const int *skip, double *dot)>;
 
 }  // namespace
 
@@ -222,6 +225,8 @@ struct CgWorkspace {
   double *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *invdiag = nullptr, *bb = nullptr;
   float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr;
   double *partials = nullptr;
+  double *dotp = nullptr;       // per-CTA parts of the dot product fused into the apply
+  unsigned int *dticket = nullptr;
   CgScalars *sc = nullptr, *sc32 = nullptr;
   CgScalars *h_sc = nullptr;
   cudaStream_t cap = nullptr;
@@ -239,7 +244,7 @@ void cg_workspace_free(CgWorkspace *w) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
   cudaFree(w->x); cudaFree(w->r); cudaFree(w->p); cudaFree(w->Ap); cudaFree(w->invdiag); cudaFree(w->bb);
   cudaFree(w->x32); cudaFree(w->r32); cudaFree(w->p32); cudaFree(w->Ap32);
-  cudaFree(w->partials); cudaFree(w->sc); cudaFree(w->sc32);
+  cudaFree(w->partials); cudaFree(w->sc); cudaFree(w->sc32); cudaFree(w->dotp); cudaFree(w->dticket);
   if (w->h_sc) cudaFreeHost(w->h_sc);
   if (w->cap) cudaStreamDestroy(w->cap);
   delete w;
@@ -264,6 +269,11 @@ mf_status ensure_workspace(mf_mesh *m, bool need32, bool needdiag) {
     MF_CUDA(cudaMemset(w->sc32, 0, sizeof(CgScalars)));
     MF_CUDA(cudaMallocHost(&w->h_sc, 2 * sizeof(CgScalars)));
     MF_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+    if (m->tp) {
+      MF_CUDA(cudaMalloc(&w->dotp, tile_dot_slots(m) * sizeof(double)));
+      MF_CUDA(cudaMalloc(&w->dticket, sizeof(unsigned int)));
+      MF_CUDA(cudaMemset(w->dticket, 0, sizeof(unsigned int)));
+    }
   }
   CgWorkspace *w = m->cg;
   if (need32 && !w->x32) {
@@ -279,11 +289,16 @@ mf_status ensure_workspace(mf_mesh *m, bool need32, bool needdiag) {
 
 // One CG iteration (Table 4) for vectors of type R.
 template <typename R>
-mf_status cg_iteration(const OpFn &op, int64_t n, R *x, R *r, R *p, R *Ap, const double *invdiag, double *partials,
-                       CgScalars *sc, cudaStream_t s) {
-  MF_TRY(op(p, Ap, s, &sc->done));
-  mf_count_launches(3);
-  cg_pap<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, p, Ap, partials, sc);
+mf_status cg_iteration(const OpFn &op, const OpDotFn &opdot, int64_t n, R *x, R *r, R *p, R *Ap,
+                       const double *invdiag, double *partials, CgScalars *sc, cudaStream_t s) {
+  if (opdot) {
+    MF_TRY(opdot(p, Ap, s, &sc->done, &sc->pAp));  // Ap = A p and pAp in one kernel
+    mf_count_launches(2);
+  } else {
+    MF_TRY(op(p, Ap, s, &sc->done));
+    mf_count_launches(3);
+    cg_pap<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, p, Ap, partials, sc);
+  }
   cg_update_xr<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, Ap, invdiag, partials, sc);
   cg_update_p<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, r, p, invdiag, sc);
   MF_CUDA(cudaGetLastError());
@@ -293,11 +308,12 @@ mf_status cg_iteration(const OpFn &op, int64_t n, R *x, R *r, R *p, R *Ap, const
 // Run the CG loop that cg_init prepared: blocks of `k` iterations (graph or plain launches),
 // host reads the done flag after each block.
 template <typename R>
-mf_status cg_loop(CgWorkspace *w, int slot, long long key, const OpFn &op, int64_t n, R *x, R *r, R *p, R *Ap,
+mf_status cg_loop(CgWorkspace *w, int slot, long long key, const OpFn &op, const OpDotFn &opdot, int64_t n, R *x,
+                  R *r, R *p, R *Ap,
                   const double *invdiag, CgScalars *sc, int k, bool use_graph, double deadline_s,
                   std::chrono::steady_clock::time_point t0, cudaStream_t s, CgScalars *host) {
   auto body = [&](cudaStream_t st) -> mf_status {
-    for (int it = 0; it < k; ++it) MF_TRY(cg_iteration<R>(op, n, x, r, p, Ap, invdiag, w->partials, sc, st));
+    for (int it = 0; it < k; ++it) MF_TRY(cg_iteration<R>(op, opdot, n, x, r, p, Ap, invdiag, w->partials, sc, st));
     return MF_OK;
   };
   CgWorkspace::Graph &g = w->g[slot];
@@ -761,6 +777,17 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
   OpFn op32 = [m](const void *in, void *out, cudaStream_t st, const int *skip) -> mf_status {
     return apply_fp32(m, (const float *)in, (float *)out, st, skip);
   };
+  // tensor-product meshes with the auto variant: p . Ap fused into the face-marching apply
+  const bool fuse = m->tp && m->variant == MF_VARIANT_AUTO && w->dotp != nullptr;
+  OpDotFn opdot64, opdot32;
+  if (fuse && o->op == MF_OP_MATFREE)
+    opdot64 = [m, w](const void *in, void *out, cudaStream_t st, const int *skip, double *dot) -> mf_status {
+      return tile_apply_dot_fp64(m, (const double *)in, (double *)out, st, skip, w->dotp, w->dticket, dot);
+    };
+  if (fuse)
+    opdot32 = [m, w](const void *in, void *out, cudaStream_t st, const int *skip, double *dot) -> mf_status {
+      return tile_apply_dot_fp32(m, (const float *)in, (float *)out, st, skip, w->dotp, w->dticket, dot);
+    };
   const long long key64 = ((long long)o->op << 40) ^ ((long long)o->precond << 36) ^ ((long long)m->variant << 32) ^
                           ((long long)(intptr_t)A & 0xffffffffll) ^ ((long long)o->check_every << 44);
   const long long key32 = ((long long)m->variant << 32) ^ ((long long)o->check_every << 44) ^ 0x5a5a;
@@ -773,7 +800,7 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
     cg_init<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->x, w->r, w->p, jac ? w->invdiag : nullptr, w->partials,
                                                       w->sc, o->rtol, o->max_iter);
     MF_CUDA(cudaGetLastError());
-    st = cg_loop<double>(w, 0, key64, op64, n, w->x, w->r, w->p, w->Ap, jac ? w->invdiag : nullptr, w->sc,
+    st = cg_loop<double>(w, 0, key64, op64, opdot64, n, w->x, w->r, w->p, w->Ap, jac ? w->invdiag : nullptr, w->sc,
                          o->check_every, o->use_graph != 0, o->timeout_s, t0, s, h);
     if (st != MF_OK && st != MF_ERR_TIMEOUT) return st;
     if (st == MF_OK) st = (mf_status)h->status;
@@ -804,7 +831,7 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
       cg_init<float><<<kRedBlocks, kRedThreads, 0, s>>>(n, w->Ap32, w->x32, w->r32, w->p32, nullptr, w->partials,
                                                        w->sc32, o->inner_rtol, o->max_iter - iters);
       MF_CUDA(cudaGetLastError());
-      mf_status si = cg_loop<float>(w, 1, key32, op32, n, w->x32, w->r32, w->p32, w->Ap32, nullptr, w->sc32,
+      mf_status si = cg_loop<float>(w, 1, key32, op32, opdot32, n, w->x32, w->r32, w->p32, w->Ap32, nullptr, w->sc32,
                                     o->check_every, o->use_graph != 0, o->timeout_s, t0, s, h + 1);
       if (si != MF_OK) {
         st = si;
@@ -941,7 +968,8 @@ extern "C" mf_status mf_cg_solve_noalloc(const mf_mesh *m, const mf_solve_opts *
   CgScalars h{};
   mf_status st = MF_OK;
   for (;;) {
-    for (int it = 0; it < o->check_every; ++it) MF_TRY(cg_iteration<double>(op, n, x, r, p, Ap, nullptr, partials, sc, s));
+    for (int it = 0; it < o->check_every; ++it)
+      MF_TRY(cg_iteration<double>(op, OpDotFn(), n, x, r, p, Ap, nullptr, partials, sc, s));
     MF_CUDA(cudaMemcpyAsync(&h, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     MF_CUDA(cudaStreamSynchronize(s));
     if (h.done) break;

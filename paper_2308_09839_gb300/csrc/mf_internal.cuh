@@ -167,6 +167,13 @@ mf_status spmv(const mf_csr *A, const double *x, double *y, cudaStream_t s, cons
 mf_status tile_setup(mf_mesh *m, cudaStream_t s);
 mf_status tile_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip);
 mf_status tile_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip);
+// tensor-product apply with x . y fused into its write phase (*out, deterministic); partials needs
+// tile_dot_slots(m) entries, ticket a zeroed counter
+int64_t tile_dot_slots(const mf_mesh *m);
+mf_status tile_apply_dot_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip,
+                              double *partials, unsigned int *ticket, double *out);
+mf_status tile_apply_dot_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip,
+                              double *partials, unsigned int *ticket, double *out);
 mf_status tile_apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s);
 // general structured kernels (mf_general.cu)
 mf_status gen_setup(mf_mesh *m, cudaStream_t s);

@@ -54,10 +54,13 @@ struct MarchSmem {
 // One work item (tile column x z-segment `item`, right-hand side `rr`); must be called by all EX*EY
 // threads of the CTA.  COHERENT: read x through L2 only (x was written by other CTAs earlier in the
 // same persistent kernel, so the read-only and L1 paths may hold stale lines).
-template <int PHYS, class N, int EX, int EY, bool COHERENT>
-__device__ __forceinline__ void march_item(const TileArgs &g, int item, int64_t rr, const typename N::IO *__restrict__ x,
-                                           typename N::IO *__restrict__ y,
-                                           MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm) {
+// DOT: also return this thread's part of x . y over the nodes it writes (the dot product a CG
+// iteration needs next, p . Ap, formed while the result is written; FP64 products and sums).
+template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT = false>
+__device__ __forceinline__ double march_item(const TileArgs &g, int item, int64_t rr,
+                                             const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
+                                             MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm) {
+  double dacc = 0.0;
   static_assert(EX == 32, "a warp is one row of element columns");
   using T = typename N::T;
   using IO = typename N::IO;
@@ -276,7 +279,14 @@ __device__ __forceinline__ void march_item(const TileArgs &g, int item, int64_t 
       for (int l = 0; l < NC; ++l) {
         const T tot = N::add(rb[l], N::ld(sm.xrow[ez & 1][l * NT + tid - EX]));
         const int64_t vi = (node * g.nrhs + rr) * NC + l;
-        y[vi] = dir ? ldx(x + vi) : N::out(tot);
+        if constexpr (DOT) {
+          const IO xv = ldx(x + vi);
+          const IO yv = dir ? xv : N::out(tot);
+          y[vi] = yv;
+          dacc += (double)xv * (double)yv;
+        } else {
+          y[vi] = dir ? ldx(x + vi) : N::out(tot);
+        }
       }
     }
 #pragma unroll
@@ -284,6 +294,7 @@ __device__ __forceinline__ void march_item(const TileArgs &g, int item, int64_t 
 #pragma unroll
       for (int m = 0; m < 4; ++m) Fb[c][m] = Ft[c][m];
   }
+  return dacc;
 }
 
 template <int PHYS, class N, int EX, int EY, int MINB>
@@ -293,6 +304,49 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
   __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
   if (skip && *skip) return;
   march_item<PHYS, N, EX, EY, false>(g, blockIdx.x, g.r0 + blockIdx.y, x, y, sm);
+}
+
+// Apply with the dot product x . y fused in (one right-hand side): each CTA stores its part, the
+// last CTA to finish (ticket) sums the parts in CTA order into *out and resets the ticket, so the
+// result does not depend on scheduling.  partials: one slot per CTA.
+template <int PHYS, class N, int EX, int EY, int MINB>
+__global__ void __launch_bounds__(EX *EY, MINB)
+    march_apply_dot(TileArgs g, const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
+                    const int *__restrict__ skip, double *__restrict__ partials, unsigned int *ticket,
+                    double *out) {
+  __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
+  __shared__ double red[EX * EY / 32];
+  __shared__ bool last;
+  if (skip && *skip) return;
+  double d = march_item<PHYS, N, EX, EY, false, true>(g, blockIdx.x, g.r0, x, y, sm);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+  if (lane == 0) red[w] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < EX * EY / 32; ++i) s += red[i];
+    partials[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += EX * EY) s += __ldcg(partials + i);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  __syncthreads();
+  if (lane == 0) red[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < EX * EY / 32; ++i) t += red[i];
+    *out = t;
+    *ticket = 0u;
+  }
 }
 
 // Launch shapes: EX = 32 element columns per warp row, EY rows, MINB resident CTAs per SM.

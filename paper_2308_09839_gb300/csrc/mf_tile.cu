@@ -114,6 +114,50 @@ static mf_status tile_launch(const mf_mesh *m, const typename N::IO *x, typename
   return MF_OK;
 }
 
+// Apply with x . y fused (CG: p . Ap); partials needs one slot per CTA (tile_dot_slots).
+template <int PHYS, class N>
+static mf_status march_dot_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
+                                  const int *skip, double *partials, unsigned int *ticket, double *out) {
+  using MS = march::MarchShape<PHYS, N>;
+  auto kern = march::march_apply_dot<PHYS, N, MS::EX, MS::EY, MS::MINB>;
+  static std::atomic<int> resident{0};
+  if (resident.load() == 0) {
+    int r = 0;
+    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, MS::EX * MS::EY, 0));
+    resident.store(std::max(r, 1));
+  }
+  TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident.load());
+  mf_count_launches(1);
+  kern<<<tile_items(g), MS::EX * MS::EY, 0, s>>>(g, x, y, skip, partials, ticket, out);
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
+int64_t tile_dot_slots(const mf_mesh *m) {
+  // at most one CTA per tile column and node plane (z-segments of one plane)
+  const int64_t tx = (m->nx + 1 + 30) / 31, ty = (m->ny + 1 + 6) / 7;
+  return tx * ty * (int64_t)(m->nz + 1);
+}
+
+template <class N>
+static mf_status tile_apply_dot(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
+                                const int *skip, double *partials, unsigned int *ticket, double *out) {
+  if (m->physics == MF_LAPLACE) return march_dot_launch<MF_LAPLACE, N>(m, x, y, s, skip, partials, ticket, out);
+  if (m->physics == MF_VECTOR_LAPLACE)
+    return march_dot_launch<MF_VECTOR_LAPLACE, N>(m, x, y, s, skip, partials, ticket, out);
+  return march_dot_launch<MF_ELASTICITY, N>(m, x, y, s, skip, partials, ticket, out);
+}
+
+mf_status tile_apply_dot_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip,
+                              double *partials, unsigned int *ticket, double *out) {
+  return tile_apply_dot<NumDW>(m, x, y, s, skip, partials, ticket, out);
+}
+
+mf_status tile_apply_dot_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip,
+                              double *partials, unsigned int *ticket, double *out) {
+  return tile_apply_dot<NumF32>(m, x, y, s, skip, partials, ticket, out);
+}
+
 // Multi right-hand-side apply on [node][rhs][comp] vectors: one face-marching launch over all
 // right-hand sides; every column is computed exactly as by the single apply.
 mf_status tile_apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s) {
