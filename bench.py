@@ -59,8 +59,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner measurement")
     ap.add_argument("--n-learned", type=int, default=128)
-    ap.add_argument("--pairs", type=int, default=200)
-    ap.add_argument("--train-steps", type=int, default=1000)
+    ap.add_argument("--pairs", type=int, default=1000)
+    ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--lr", type=float, default=2e-4)
     ap.add_argument("--cg-timeout", type=float, default=90.0)
     ap.add_argument("--variant", type=int, default=0, help="0 = auto (fastest FP64-accurate), 1 = reference")

@@ -235,7 +235,7 @@ struct CgWorkspace {
     long long key = -1;
     int64_t kernels = 0;  // kernel nodes per replay
   } g[2];
-  int variant_at_diag = -1;
+  bool invdiag_ready = false;  // invdiag holds 1 / diag(A) of this mesh
 };
 
 void cg_workspace_free(CgWorkspace *w) {
@@ -284,6 +284,20 @@ mf_status ensure_workspace(mf_mesh *m, bool need32, bool needdiag) {
     MF_CUDA(cudaMalloc(&w->Ap32, nf));
   }
   if (needdiag && !w->invdiag) MF_CUDA(cudaMalloc(&w->invdiag, w->n * sizeof(double)));
+  return MF_OK;
+}
+
+// 1 / diag(A) in the workspace.  The diagonal depends on the mesh alone, so it is computed by the
+// first solve that needs it and kept for the later ones.
+mf_status ensure_invdiag(mf_mesh *m, cudaStream_t s) {
+  MF_TRY(ensure_workspace(m, false, true));
+  CgWorkspace *w = m->cg;
+  if (w->invdiag_ready) return MF_OK;
+  MF_TRY(operator_diagonal(m, w->invdiag, s));
+  mf_count_launches(1);
+  invert_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(w->n, w->invdiag);
+  MF_CUDA(cudaGetLastError());
+  w->invdiag_ready = true;
   return MF_OK;
 }
 
@@ -448,8 +462,8 @@ __global__ void theta_update(int64_t n, const double *num_den, const double *c, 
   }
 }
 
-__global__ void inv_sqrt_kernel(int64_t n, double *d) {
-  GRID_STRIDE(i, n) d[i] = 1.0 / sqrt(d[i]);
+__global__ void sqrt_to(int64_t n, const double *__restrict__ a, double *__restrict__ b) {
+  GRID_STRIDE(i, n) b[i] = sqrt(a[i]);
 }
 
 // Truncated flexible CG keeps the last kFcgM search directions and their images under A.
@@ -535,7 +549,7 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
   const int *nd = net_dims(net);
   MF_ARG(nd[0] == m->nx + 1 && nd[1] == m->ny + 1 && nd[2] == m->nz + 1,
          "mf_cg_solve: the network was created for a different node grid");
-  MF_TRY(ensure_workspace(m, false, false));
+  MF_TRY(ensure_invdiag(m, s));
   CgWorkspace *w = m->cg;
   const int64_t n = m->n_dof;
   FcgBufs f{};
@@ -570,8 +584,7 @@ mf_status fcg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double 
   }
   mf_count_launches(2);
   node_logk<<<blocks_for(n), kThreads, 0, s>>>(m->mat, m->nx, m->ny, m->nz, f.logk);
-  MF_TRY(operator_diagonal(m, f.isd, s));
-  inv_sqrt_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, f.isd);
+  sqrt_to<<<kRedBlocks, kRedThreads, 0, s>>>(n, w->invdiag, f.isd);  // D^-1/2
   const double c_out = (double)net_out_scale(net);
   bool learned = true;
   int fallback_at = -1;
@@ -764,11 +777,7 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
   MF_TRY(ensure_workspace(m, mixed, jac));
   CgWorkspace *w = m->cg;
   const int64_t n = m->n_dof;
-  if (jac) {
-    MF_TRY(operator_diagonal(m, w->invdiag, s));
-    mf_count_launches(1);
-    invert_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, w->invdiag);
-  }
+  if (jac) MF_TRY(ensure_invdiag(m, s));
   const mf_csr *A = o->csr;
   OpFn op64 = [m, A, o](const void *in, void *out, cudaStream_t st, const int *skip) -> mf_status {
     if (o->op == MF_OP_CSR) return spmv(A, (const double *)in, (double *)out, st, skip);

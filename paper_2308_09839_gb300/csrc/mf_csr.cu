@@ -59,6 +59,38 @@ __device__ void element_rows(const double X[8][3], int a, double c0, double c1, 
   }
 }
 
+// Diagonal of A^e for all corners: out[a][k] = A^e_{ND a + k, ND a + k}, summed over the Gauss
+// points in the same order and with the same expressions as element_rows.
+template <int PHYS>
+__device__ void element_diag(const double X[8][3], double c0, double c1, double out[8][3]) {
+  for (int a = 0; a < 8; ++a)
+    for (int k = 0; k < 3; ++k) out[a][k] = 0.0;
+  for (int q = 0; q < 8; ++q) {
+    double xi[3];
+    for (int d = 0; d < 3; ++d) xi[d] = q1::sgn(q, d) * q1::kG;
+    double J[3][3], C[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0;
+        for (int c = 0; c < 8; ++c) s += X[c][i] * q1::dN_at(xi, c, j);
+        J[i][j] = s;
+      }
+    const double det = q1::adjugate(J, C);
+    const double wd = det;
+    for (int a = 0; a < 8; ++a) {
+      const double r[3] = {q1::dN_at(xi, a, 0), q1::dN_at(xi, a, 1), q1::dN_at(xi, a, 2)};
+      double ga[3];
+      for (int i = 0; i < 3; ++i) ga[i] = (C[0][i] * r[0] + C[1][i] * r[1] + C[2][i] * r[2]) / det;
+      const double gg = ga[0] * ga[0] + ga[1] * ga[1] + ga[2] * ga[2];
+      if (PHYS == MF_LAPLACE) {
+        out[a][0] += c0 * gg * wd;
+      } else {
+        for (int k = 0; k < 3; ++k) out[a][k] += wd * (c0 * ga[k] * ga[k] + c1 * (ga[k] * ga[k] + gg));
+      }
+    }
+  }
+}
+
 template <int PHYS>
 __global__ void csr_fill_colour(MeshView m, int colour, int64_t count, const int32_t *__restrict__ celems,
                                 const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, double *val) {
@@ -120,22 +152,23 @@ __global__ void diag_colour(MeshView m, int colour, int64_t count, const int32_t
   constexpr int ND = phys_ndpn(PHYS);
   constexpr int EP = PHYS == MF_VECTOR_LAPLACE ? MF_LAPLACE : PHYS;
   constexpr int NE = phys_ndpn(EP);
-  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= count * 8) return;
-  const int64_t t = gid >> 3;
-  const int a = (int)(gid & 7);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // one element per thread
+  if (t >= count) return;
   const int64_t e = celems ? (int64_t)celems[t] : parity_element_c(t, colour, m.nx, m.ny, m.nz);
   int64_t nodes[8];
   element_nodes(m, e, nodes);
-  if (m.dmask[nodes[a]]) return;
   double X[8][3];
   for (int c = 0; c < 8; ++c)
     for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
   const double c0 = phys_is_laplace(PHYS) ? m.mat[e] : m.mat[2 * e];
   const double c1 = phys_is_laplace(PHYS) ? 0.0 : m.mat[2 * e + 1];
-  double A[NE][8][3];
-  element_rows<EP>(X, a, c0, c1, A);
-  for (int k = 0; k < ND; ++k) diag[nodes[a] * ND + k] += NE == 1 ? A[0][a][0] : A[k][a][k];
+  double D[8][3];
+  element_diag<EP>(X, c0, c1, D);
+  // elements of one colour share no node: plain adds
+  for (int a = 0; a < 8; ++a) {
+    if (m.dmask[nodes[a]]) continue;
+    for (int k = 0; k < ND; ++k) diag[nodes[a] * ND + k] += NE == 1 ? D[a][0] : D[a][k];
+  }
 }
 
 __global__ void dirichlet_unit(const int32_t *dn, int64_t n, int nd, const int64_t *rowptr, double *val) {
@@ -224,7 +257,7 @@ void launch_diag(const mf_mesh *m, const MeshView &v, double *diag, cudaStream_t
     const int64_t cnt = colour_count(m, c);
     if (!cnt) continue;
     const int32_t *ce = m->structured ? nullptr : m->colour_elems + m->colour_off[c];
-    diag_colour<PHYS><<<blocks_for(cnt * 8, 128), 128, 0, s>>>(v, c, cnt, ce, diag);
+    diag_colour<PHYS><<<blocks_for(cnt, 128), 128, 0, s>>>(v, c, cnt, ce, diag);
   }
 }
 

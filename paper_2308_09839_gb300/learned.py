@@ -67,7 +67,9 @@ def generate_pairs(mesh: mf.Mesh, p, n_pairs: int, seed: int = 0, k_range=(2, 15
         xs[dmask] = 0.0
         b = mesh.apply(xs)
         k = int(math.exp(rng.uniform(math.log(k_range[0]), math.log(k_range[1]))))
-        xk, _ = mesh.cg(b, max_iter=k, rtol=1e-14, check_every=min(k, 32), precond=mf.MF_PC_JACOBI)
+        # a fixed graph block of 16 iterations (the device-side iteration limit stops at k), so one
+        # captured graph serves every pair
+        xk, _ = mesh.cg(b, max_iter=k, rtol=1e-14, check_every=16, precond=mf.MF_PC_JACOBI)
         r = (b - mesh.apply(xk)) / sq
         e = (xs - xk) * sq
         r[dmask] = 0.0
