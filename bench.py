@@ -38,8 +38,9 @@ UNIT = "GDoF/s"
 # DRAM bytes (read + write) per launch of the face-marching FP64 kernels at the benchmarked sizes:
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 192^3 Laplace and 128^3
 # elasticity meshes, scaled by the node count (the traffic is proportional to it).  Part of y is
-# still dirty in L2 when a launch ends, so the write share is below the bytes written.
-TRAFFIC = {"laplace": round(152346880 * 16974593 / 7189057), "elasticity": round(103310592 * 4173281 / 2146689)}
+# still dirty in L2 when a launch ends, so the write share is below the bytes written.  None: no
+# capture of the current kernel yet.
+TRAFFIC = {"laplace": round(152346880 * 16974593 / 7189057), "elasticity": None}
 
 
 def parse():
@@ -59,7 +60,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner measurement")
     ap.add_argument("--n-learned", type=int, default=128)
-    ap.add_argument("--pairs", type=int, default=1000)
+    ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--lr", type=float, default=2e-4)
     ap.add_argument("--cg-timeout", type=float, default=90.0)

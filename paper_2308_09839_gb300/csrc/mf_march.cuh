@@ -350,8 +350,12 @@ __global__ void __launch_bounds__(EX *EY, MINB)
 }
 
 // Launch shapes: EX = 32 element columns per warp row, EY rows, MINB resident CTAs per SM.
+// Double-word elasticity takes 12 rows at 168 registers (12 warps per SM, halo factor 1.13): at 8
+// rows it needed 241 registers and ran 8 warps per SM, 17 % slower at 160^3.  FP32 elasticity keeps
+// 8 rows, where it is fastest.
 template <int PHYS, class N> struct MarchShape { static constexpr int EX = 32, EY = 8, MINB = 4; };
 template <class N> struct MarchShape<MF_ELASTICITY, N> { static constexpr int EX = 32, EY = 8, MINB = 1; };
+template <> struct MarchShape<MF_ELASTICITY, tile::NumDW> { static constexpr int EX = 32, EY = 12, MINB = 1; };
 template <class N> struct MarchShape<MF_VECTOR_LAPLACE, N> { static constexpr int EX = 32, EY = 8, MINB = 2; };
 
 }  // namespace march

@@ -133,10 +133,22 @@ static mf_status march_dot_launch(const mf_mesh *m, const typename N::IO *x, typ
   return MF_OK;
 }
 
+// At most one CTA per tile column and node plane (z-segments of one plane), for the FP64 and the
+// FP32 launch shapes of the mesh's physics.
+template <int PHYS>
+static int64_t dot_slots(const mf_mesh *m) {
+  auto tiles = [m](int EX, int EY) {
+    return (int64_t)((m->nx + EX - 1) / (EX - 1)) * ((m->ny + EY - 1) / (EY - 1)) * (m->nz + 1);
+  };
+  using S64 = march::MarchShape<PHYS, NumDW>;
+  using S32 = march::MarchShape<PHYS, NumF32>;
+  return std::max(tiles(S64::EX, S64::EY), tiles(S32::EX, S32::EY));
+}
+
 int64_t tile_dot_slots(const mf_mesh *m) {
-  // at most one CTA per tile column and node plane (z-segments of one plane)
-  const int64_t tx = (m->nx + 1 + 30) / 31, ty = (m->ny + 1 + 6) / 7;
-  return tx * ty * (int64_t)(m->nz + 1);
+  if (m->physics == MF_LAPLACE) return dot_slots<MF_LAPLACE>(m);
+  if (m->physics == MF_VECTOR_LAPLACE) return dot_slots<MF_VECTOR_LAPLACE>(m);
+  return dot_slots<MF_ELASTICITY>(m);
 }
 
 template <class N>
