@@ -38,9 +38,8 @@ UNIT = "GDoF/s"
 # DRAM bytes (read + write) per launch of the face-marching FP64 kernels at the benchmarked sizes:
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 192^3 Laplace and 128^3
 # elasticity meshes, scaled by the node count (the traffic is proportional to it).  Part of y is
-# still dirty in L2 when a launch ends, so the write share is below the bytes written.  None: no
-# capture of the current kernel yet.
-TRAFFIC = {"laplace": round(152346880 * 16974593 / 7189057), "elasticity": None}
+# still dirty in L2 when a launch ends, so the write share is below the bytes written.
+TRAFFIC = {"laplace": round(152346880 * 16974593 / 7189057), "elasticity": round(103899904 * 4173281 / 2146689)}
 
 
 def parse():
@@ -66,6 +65,9 @@ def parse():
     ap.add_argument("--cg-timeout", type=float, default=90.0)
     ap.add_argument("--variant", type=int, default=0, help="0 = auto (fastest FP64-accurate), 1 = reference")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default z-segment length")
+    ap.add_argument("--tile-segments", default="",
+                    help="z-segment lengths 'laplace,elasticity' to use instead of tuning (e.g. the ones a "
+                         "tuned run reported), so that a profiled run launches the same grids")
     return ap.parse_args()
 
 
@@ -249,10 +251,14 @@ def main():
     pL = inputs.cartesian_laplace_256(n=args.n_laplace)
     pE = inputs.cartesian_elasticity_160(n=args.n_elasticity)
     meshes, segs = [], []
-    for p in (pL, pE):
+    fixed = [int(s) for s in args.tile_segments.split(",")] if args.tile_segments else None
+    for j, p in enumerate((pL, pE)):
         m = mf.Mesh.from_problem(p, device=f"cuda:{local}")
         m.set_variant(args.variant)
-        if args.variant == 0 and not args.no_tune:
+        if fixed is not None:
+            mf.mf_set_tile_segment(m, fixed[j])
+            segs.append(fixed[j])
+        elif args.variant == 0 and not args.no_tune:
             from paper_2308_09839_gb300 import autotune
             segs.append(autotune.tune_apply(m, use_cache=False))  # setup, not timed
         x = torch.from_numpy(p.x()).cuda()

@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const ty
                                                             const int *__restrict__ skip) {
   __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
   if (skip && *skip) return;
-  march_item<PHYS, N, EX, EY, false>(g, blockIdx.x, g.r0 + blockIdx.y, x, y, sm);
+  // right-hand side fastest: CTAs that run together read the same x lines ([node][rhs][comp])
+  march_item<PHYS, N, EX, EY, false>(g, blockIdx.x / g.nrhs, g.r0 + blockIdx.x % g.nrhs, x, y, sm);
 }
 
 // Apply with the dot product x . y fused in (one right-hand side): each CTA stores its part, the

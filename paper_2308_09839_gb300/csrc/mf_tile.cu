@@ -84,7 +84,7 @@ mf_status tile_setup(mf_mesh *m, cudaStream_t s) {
 }
 
 // The face-marching kernels (mf_march.cuh): one launch for `nrhs` right-hand sides of
-// [node][rhs][comp] vectors (grid.y = right-hand side).
+// [node][rhs][comp] vectors (CTA = work item x nrhs + right-hand side).
 template <int PHYS, class N>
 static mf_status march_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
                               const int *skip, int nrhs = 1) {
@@ -99,7 +99,7 @@ static mf_status march_launch(const mf_mesh *m, const typename N::IO *x, typenam
   TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident.load(), nrhs);
   g.nrhs = nrhs;
   g.r0 = 0;
-  kern<<<dim3(tile_items(g), nrhs), MS::EX * MS::EY, 0, s>>>(g, x, y, skip);
+  kern<<<tile_items(g) * nrhs, MS::EX * MS::EY, 0, s>>>(g, x, y, skip);
   return MF_OK;
 }
 
