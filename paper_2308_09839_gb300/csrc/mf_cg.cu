@@ -389,7 +389,7 @@ mf_status cg_loop(CgWorkspace *w, int slot, long long key, const OpFn &op, const
 //   z2 = z1 + theta cn with the energy-norm step theta = max(0, cn.r1 / cn.A cn) (a useless or harmful
 //   correction gets theta ~ 0);  z = z2 + omega D^-1 (r - A z2).
 // c is the network's output scale; z = 0 on Dirichlet DoFs.  The FP64 CG stays the fallback and
-// the judge of convergence (the true residual is recomputed at the end).
+// what decides convergence (the true residual is recomputed at the end).
 // ------------------------------------------------------------------------------------------------
 extern "C" mf_status mf_net_forward(mf_net *N, const float *r, const float *logk, float *out, mf_stream stream);
 int64_t net_nodes(const mf_net *N);
