@@ -17,6 +17,12 @@ grad phi = J^{-T} grad_ref phi.  Readings taken where the paper is silent:
 * Dirichlet degrees of freedom: their columns are dropped and their rows are the identity, so
   (A x)_d = x_d.  For b_d = 0 and x0_d = 0 this is the reduced system on the free DoFs.
 
+Linear tetrahedra (P1, 4 nodes), the simplex elements that Sec. 7 names as future work, use the
+same element integrals (Eqs. 1-3) with the reference tetrahedron {xi, eta, zeta >= 0, xi + eta +
+zeta <= 1}: phi_0 = 1 - xi - eta - zeta, phi_k = xi_k; the gradients are constant, so one point
+with weight 1/6 (the reference volume) integrates the element matrices exactly.  Every helper below
+takes the element type from the connectivity's width (8: Q1 hexahedron, 4: P1 tetrahedron).
+
 Parity pins live in ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
@@ -59,6 +65,23 @@ def shape_ref_grads(pts: np.ndarray) -> np.ndarray:
     return out
 
 
+def tet_ref_grads() -> np.ndarray:
+    """(4, 3) reference gradients of the P1 tetrahedron's shape functions (constant)."""
+    return np.array([[-1.0, -1.0, -1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+
+
+def reference_rule(npe: int) -> tuple[np.ndarray, np.ndarray]:
+    """Quadrature weights (nq,) and reference gradients (nq, npe, 3) of the element with npe nodes:
+    the 2x2x2 Gauss rule for the Q1 hexahedron, the one-point rule (weight 1/6) for the P1
+    tetrahedron."""
+    if npe == 8:
+        pts, w = gauss_points()
+        return w, shape_ref_grads(pts)
+    if npe == 4:
+        return np.array([1.0 / 6.0]), tet_ref_grads()[None]
+    raise ValueError(f"no element with {npe} nodes")
+
+
 def jacobians(X: np.ndarray, dN: np.ndarray) -> np.ndarray:
     """J[e, q, i, j] = sum_a X[e, a, i] dN[q, a, j]   (Algorithm 1: J = sum_j x_j (x) grad_ref phi_j)."""
     return np.einsum("eai,qaj->eqij", X, dN)
@@ -82,9 +105,8 @@ def lame(E: np.ndarray, nu: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
 def laplace_element_matrices(X: np.ndarray, kappa: np.ndarray) -> np.ndarray:
     """Eq. 4 times kappa_e:  A^e_ab = kappa_e sum_q (J^{-T} grad_ref phi_a).(J^{-T} grad_ref phi_b) w_q det J.
 
-    X: (E, 8, 3) element corner coordinates, kappa: (E,).  Returns (E, 8, 8)."""
-    pts, w = gauss_points()
-    dN = shape_ref_grads(pts)
+    X: (E, npe, 3) element node coordinates, kappa: (E,).  Returns (E, npe, npe)."""
+    w, dN = reference_rule(X.shape[1])
     g, det = physical_grads(jacobians(X, dN), dN)
     return np.einsum("e,q,eq,eqai,eqbi->eab", kappa, w, det, g, g)
 
@@ -92,23 +114,23 @@ def laplace_element_matrices(X: np.ndarray, kappa: np.ndarray) -> np.ndarray:
 def vector_laplace_element_matrices(X: np.ndarray, kappa: np.ndarray) -> np.ndarray:
     """Eq. 5 times kappa_e: A^e_{3a+k, 3b+l} = kappa_e delta_kl sum_q (J^{-T} grad_ref phi_a).(J^{-T}
     grad_ref phi_b) w_q det J  (each displacement component sees the scalar operator)."""
-    pts, w = gauss_points()
-    dN = shape_ref_grads(pts)
+    npe = X.shape[1]
+    w, dN = reference_rule(npe)
     g, det = physical_grads(jacobians(X, dN), dN)
     gg = np.einsum("e,q,eq,eqai,eqbi->eab", kappa, w, det, g, g)
-    A = np.zeros((X.shape[0], 8, 3, 8, 3))
+    A = np.zeros((X.shape[0], npe, 3, npe, 3))
     for k in range(3):
         A[:, :, k, :, k] = gg
-    return A.reshape(X.shape[0], 24, 24)
+    return A.reshape(X.shape[0], 3 * npe, 3 * npe)
 
 
 def elasticity_element_matrices(X: np.ndarray, lam: np.ndarray, mu: np.ndarray) -> np.ndarray:
     """Eq. 6 with Hooke's law:
     A^e_{3a+k, 3b+l} = sum_q w_q det J [lam d_k phi_a d_l phi_b + mu (d_l phi_a d_k phi_b + delta_kl grad phi_a . grad phi_b)].
 
-    X: (E, 8, 3), lam, mu: (E,).  Returns (E, 24, 24) in the xyz-interleaved DoF order 3a + k."""
-    pts, w = gauss_points()
-    dN = shape_ref_grads(pts)
+    X: (E, npe, 3), lam, mu: (E,).  Returns (E, 3 npe, 3 npe) in the xyz-interleaved DoF order 3a + k."""
+    npe = X.shape[1]
+    w, dN = reference_rule(npe)
     g, det = physical_grads(jacobians(X, dN), dN)
     wd = det * w[None, :]
     t_lam = np.einsum("e,eq,eqak,eqbl->eakbl", lam, wd, g, g)
@@ -117,7 +139,7 @@ def elasticity_element_matrices(X: np.ndarray, lam: np.ndarray, mu: np.ndarray) 
     A = t_lam + t_mu1
     for k in range(3):
         A[:, :, k, :, k] += dot
-    return A.reshape(X.shape[0], 24, 24)
+    return A.reshape(X.shape[0], 3 * npe, 3 * npe)
 
 
 # --------------------------------------------------------------------------------------------------
@@ -125,11 +147,11 @@ def elasticity_element_matrices(X: np.ndarray, lam: np.ndarray, mu: np.ndarray) 
 # --------------------------------------------------------------------------------------------------
 
 def element_dofs(cells: np.ndarray, ndpn: int) -> np.ndarray:
-    """(E, 8*ndpn) global DoF indices, xyz interleaved (DoF 3*node + k)."""
+    """(E, npe*ndpn) global DoF indices, xyz interleaved (DoF 3*node + k)."""
     cells = cells.astype(np.int64)
     if ndpn == 1:
         return cells
-    return (cells[:, :, None] * ndpn + np.arange(ndpn)[None, None, :]).reshape(cells.shape[0], 8 * ndpn)
+    return (cells[:, :, None] * ndpn + np.arange(ndpn)[None, None, :]).reshape(cells.shape[0], cells.shape[1] * ndpn)
 
 
 def element_matrices(physics: str, coords: np.ndarray, cells: np.ndarray, mat: np.ndarray, elems=None) -> np.ndarray:

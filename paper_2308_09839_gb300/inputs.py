@@ -104,6 +104,26 @@ def box_cells(nx: int, ny: int, nz: int) -> np.ndarray:
     return cells.astype(np.int32)
 
 
+# The 6 tetrahedra of a hexahedron that share its diagonal from corner 0 to corner 7 (Kuhn's
+# subdivision): one per order in which a path from corner 0 to corner 7 steps along x (corner bit
+# 1), y (bit 2) and z (bit 4), with the parity of that order.
+_KUHN = ((1, 2, 4, 0), (1, 4, 2, 1), (2, 1, 4, 1), (2, 4, 1, 0), (4, 1, 2, 0), (4, 2, 1, 1))
+
+
+def tet_cells(nx: int, ny: int, nz: int) -> np.ndarray:
+    """Tetrahedral connectivity of the box, int32 [6E][4]: hexahedron e of ``box_cells`` becomes
+    tetrahedra 6e..6e+5 with nodes (c0, c_a, c_{a+b}, c7).  Every hexahedron face is cut along its
+    diagonal through the face's lowest corner, so neighbouring hexahedra cut a shared face the same
+    way (the mesh is conforming).  Paths of odd parity swap their two middle nodes, which makes every
+    tetrahedron positively oriented on the undistorted box."""
+    hexes = box_cells(nx, ny, nz)
+    out = np.empty((hexes.shape[0], 6, 4), dtype=np.int32)
+    for t, (a, b, _c, odd) in enumerate(_KUHN):
+        mid = [a + b, a] if odd else [a, a + b]
+        out[:, t] = hexes[:, [0, mid[0], mid[1], 7]]
+    return out.reshape(-1, 4)
+
+
 def dirichlet_z0(nx: int, ny: int, nz: int) -> np.ndarray:
     """uint8 [N] mask, 1 on the nodes of the face z = 0."""
     m = np.zeros((nz + 1, ny + 1, nx + 1), dtype=np.uint8)
@@ -211,6 +231,7 @@ class Problem:
     seed: int = 0
     cells: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
+    element: str = "hex8"   # "hex8" (Q1 hexahedra) | "tet4" (P1 tetrahedra, explicit cells)
 
     @property
     def n_nodes(self) -> int:
@@ -218,7 +239,7 @@ class Problem:
 
     @property
     def n_cells(self) -> int:
-        return self.nx * self.ny * self.nz
+        return self.cells.shape[0] if self.cells is not None else self.nx * self.ny * self.nz
 
     @property
     def ndpn(self) -> int:
@@ -285,6 +306,21 @@ def vector_laplace_box(n, jitter=0.0, sigma=1.0, layered=False, seed=0, name=Non
     nz = n if nz is None else nz
     return Problem(name or f"vector_laplace_{n}x{ny}x{nz}", "vector_laplace", n, ny, nz, p.coords, p.mat,
                    p.dirichlet, seed, meta=p.meta)
+
+
+def tet_box(physics: str, n, jitter=0.0, sigma=0.5, layered=True, seed=0, name=None, ny=None,
+            nz=None) -> Problem:
+    """P1 tetrahedra: the n x ny x nz box (node jitter as ``box_coords``) with every hexahedron split
+    into 6 tetrahedra (``tet_cells``).  Each tetrahedron takes the cell constants of its hexahedron:
+    the recipe of ``laplace_box`` / ``elasticity_box`` / ``vector_laplace_box``, repeated 6 times.
+    Dirichlet on z = 0."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    maker = {"laplace": laplace_box, "elasticity": elasticity_box, "vector_laplace": vector_laplace_box}[physics]
+    h = maker(n, jitter=jitter, sigma=sigma, layered=layered, seed=seed, ny=ny, nz=nz)
+    mat = np.repeat(h.mat, 6, axis=0)
+    return Problem(name or f"tet_{physics}_{n}x{ny}x{nz}", physics, n, ny, nz, h.coords, mat, h.dirichlet, seed,
+                   cells=tet_cells(n, ny, nz), meta=dict(h.meta, element="tet4"), element="tet4")
 
 
 def small_laplace_16(seed=0) -> Problem:
