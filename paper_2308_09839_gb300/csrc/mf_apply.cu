@@ -1,4 +1,5 @@
-// Matrix-free operator apply, reference variant: Algorithm 1 with one thread per element.
+// Matrix-free operator apply, reference variant: Algorithm 1 with one thread per element (Q1
+// hexahedra; the same scheme runs the P1 tetrahedra of mf_tet.cuh).
 //
 // Each thread gathers its element's 8 support points and input values (Alg. 1, gather step),
 // evaluates the Jacobian, its inverse and determinant at every Gauss point, applies the flux /
@@ -9,6 +10,7 @@
 // reproducible.
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
+#include "mf_tet.cuh"
 
 namespace {
 
@@ -168,6 +170,58 @@ __global__ void __launch_bounds__(128) apply_multi_colour(MeshView m, const doub
   }
 }
 
+// P1 tetrahedra, one thread per element of a colour: gather the 4 vertices and values, apply the
+// element operator of mf_tet.cuh, add into y.  Layout [node][rhs][comp] with `nrhs` right-hand
+// sides per node (the geometry is computed once per element for all of them).
+template <int PHYS, typename R>
+__global__ void __launch_bounds__(128) tet_apply_colour(MeshView m, const R *__restrict__ x, R *__restrict__ y,
+                                                        int nrhs, int64_t count, const int32_t *__restrict__ celems,
+                                                        const int *__restrict__ skip) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count || (skip && *skip)) return;
+  constexpr int ND = phys_ndpn(PHYS);
+  const int64_t e = celems[t];
+  int64_t nodes[4];
+  p1::nodes_of(m.cells, e, nodes);
+  const R *Xc = coords_of<R>(m);
+  const R *mat = mat_of<R>(m);
+  R X[4][3], n[4][3];
+  bool dir[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) X[a][i] = Xc[3 * nodes[a] + i];
+    dir[a] = m.dmask[nodes[a]] != 0;
+  }
+  const R D = p1::geometry<R>(X, n);
+  for (int r = 0; r < nrhs; ++r) {
+    if (PHYS == MF_ELASTICITY) {
+      R u[4][3], v[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u[a][k] = dir[a] ? (R)0 : x[(nodes[a] * nrhs + r) * 3 + k];
+      p1::elasticity<R>(n, D, mat[2 * e], mat[2 * e + 1], u, v);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        if (!dir[a])
+#pragma unroll
+          for (int k = 0; k < 3; ++k) y[(nodes[a] * nrhs + r) * 3 + k] += v[a][k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < ND; ++k) {  // the scalar operator on each component (Eq. 5)
+        R u[4], v[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) u[a] = dir[a] ? (R)0 : x[(nodes[a] * nrhs + r) * ND + k];
+        p1::laplace<R>(n, D, mat[e], u, v);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+          if (!dir[a]) y[(nodes[a] * nrhs + r) * ND + k] += v[a];
+      }
+    }
+  }
+}
+
 // Dirichlet rows: y_d = x_d.
 template <typename R>
 __global__ void dirichlet_rows(const int32_t *__restrict__ dn, int64_t n, int ndw, const R *__restrict__ x,
@@ -180,7 +234,32 @@ __global__ void dirichlet_rows(const int32_t *__restrict__ dn, int64_t n, int nd
 }
 
 template <typename R>
+mf_status tet_apply(const mf_mesh *m, const R *x, R *y, int nrhs, cudaStream_t s, const int *skip) {
+  MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * nrhs * sizeof(R), s));
+  const MeshView v = m->view();
+  for (int c = 0; c < m->n_colours; ++c) {
+    const int64_t cnt = colour_count(m, c);
+    if (cnt == 0) continue;
+    const int32_t *ce = m->colour_elems + m->colour_off[c];
+    mf_count_launches(1);
+    if (m->physics == MF_LAPLACE)
+      tet_apply_colour<MF_LAPLACE, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
+    else if (m->physics == MF_VECTOR_LAPLACE)
+      tet_apply_colour<MF_VECTOR_LAPLACE, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
+    else
+      tet_apply_colour<MF_ELASTICITY, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
+  }
+  if (m->n_dnodes) mf_count_launches(1);
+  if (m->n_dnodes)
+    dirichlet_rows<R><<<blocks_for(m->n_dnodes * m->ndpn * nrhs), kThreads, 0, s>>>(m->dnodes, m->n_dnodes,
+                                                                                  m->ndpn * nrhs, x, y, skip);
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
+template <typename R>
 mf_status apply_reference(const mf_mesh *m, const R *x, R *y, cudaStream_t s, const int *skip) {
+  if (m->npe == 4) return tet_apply<R>(m, x, y, 1, s, skip);
   MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * sizeof(R), s));
   const MeshView v = m->view();
   for (int c = 0; c < m->n_colours; ++c) {
@@ -218,6 +297,7 @@ mf_status apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s,
 
 mf_status apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s) {
   if (m->variant == MF_VARIANT_AUTO && m->tp) return tile_apply_multi_fp64(m, nrhs, x, y, s);
+  if (m->npe == 4) return tet_apply<double>(m, x, y, nrhs, s, nullptr);
   MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * nrhs * sizeof(double), s));
   const MeshView v = m->view();
   for (int c = 0; c < m->n_colours; ++c) {

@@ -11,6 +11,7 @@
 
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
+#include "mf_tet.cuh"
 
 namespace {
 
@@ -171,6 +172,79 @@ __global__ void diag_colour(MeshView m, int colour, int64_t count, const int32_t
   }
 }
 
+// P1 tetrahedra: rows of node a of A^e (mf_tet.cuh) added into the CSR values, one thread per
+// (element, node) of a colour.  Same search as csr_fill_colour: the three rows of a node share
+// their column pattern, so the offset found in the first row serves all three.
+template <int PHYS>
+__global__ void tet_fill_colour(MeshView m, int64_t count, const int32_t *__restrict__ celems,
+                                const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, double *val) {
+  constexpr int ND = phys_ndpn(PHYS);
+  constexpr int EP = PHYS == MF_VECTOR_LAPLACE ? MF_LAPLACE : PHYS;
+  constexpr int NE = phys_ndpn(EP);
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= count * 4) return;
+  const int64_t e = celems[gid >> 2];
+  const int a = (int)(gid & 3);
+  int64_t nodes[4];
+  p1::nodes_of(m.cells, e, nodes);
+  if (m.dmask[nodes[a]]) return;  // Dirichlet row: identity, set separately
+  double X[4][3], n[4][3];
+  for (int c = 0; c < 4; ++c)
+    for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
+  const double D = p1::geometry<double>(X, n);
+  const double c0 = phys_is_laplace(PHYS) ? m.mat[e] : m.mat[2 * e];
+  const double c1 = phys_is_laplace(PHYS) ? 0.0 : m.mat[2 * e + 1];
+  double A[NE][4][3];
+  p1::element_rows<EP>(n, D, a, c0, c1, A);
+  for (int b = 0; b < 4; ++b) {
+    if (m.dmask[nodes[b]]) continue;  // Dirichlet column dropped
+    for (int k = 0; k < (PHYS == MF_VECTOR_LAPLACE ? 3 : 1); ++k) {
+      // vector Laplace: row 3 n + k holds only the columns 3 m + k (block-diagonal pattern)
+      const int64_t row = nodes[a] * ND + k;
+      const int32_t target = (int32_t)(nodes[b] * ND + (PHYS == MF_VECTOR_LAPLACE ? k : 0));
+      int64_t lo = rowptr[row], hi = rowptr[row + 1];
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < target) lo = mid + 1; else hi = mid;
+      }
+      if (PHYS == MF_VECTOR_LAPLACE) {
+        val[lo] += A[0][b][0];
+      } else {
+        const int64_t rel = lo - rowptr[row];
+        for (int kk = 0; kk < ND; ++kk) {
+          const int64_t base = rowptr[nodes[a] * ND + kk] + rel;
+          for (int l = 0; l < ND; ++l) val[base + l] += NE == 1 ? A[0][b][0] : A[kk][b][l];
+        }
+      }
+    }
+  }
+}
+
+// diag(A) of P1 tetrahedra, one thread per element of a colour.
+template <int PHYS>
+__global__ void tet_diag_colour(MeshView m, int64_t count, const int32_t *__restrict__ celems, double *diag) {
+  constexpr int ND = phys_ndpn(PHYS);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t e = celems[t];
+  int64_t nodes[4];
+  p1::nodes_of(m.cells, e, nodes);
+  double X[4][3], n[4][3];
+  for (int c = 0; c < 4; ++c)
+    for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
+  const double D = p1::geometry<double>(X, n);
+  const double c0 = phys_is_laplace(PHYS) ? m.mat[e] : m.mat[2 * e];
+  const double c1 = phys_is_laplace(PHYS) ? 0.0 : m.mat[2 * e + 1];
+  const double c = 1.0 / (6.0 * D);
+  for (int a = 0; a < 4; ++a) {
+    if (m.dmask[nodes[a]]) continue;
+    const double nn = n[a][0] * n[a][0] + n[a][1] * n[a][1] + n[a][2] * n[a][2];
+    for (int k = 0; k < ND; ++k)
+      diag[nodes[a] * ND + k] +=
+          phys_is_laplace(PHYS) ? c0 * nn * c : c * (c0 * n[a][k] * n[a][k] + c1 * (n[a][k] * n[a][k] + nn));
+  }
+}
+
 __global__ void dirichlet_unit(const int32_t *dn, int64_t n, int nd, const int64_t *rowptr, double *val) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n * nd) return;
@@ -247,7 +321,10 @@ void launch_fill(const mf_mesh *m, const MeshView &v, const mf_csr *A, cudaStrea
     const int64_t cnt = colour_count(m, c);
     if (!cnt) continue;
     const int32_t *ce = m->structured ? nullptr : m->colour_elems + m->colour_off[c];
-    csr_fill_colour<PHYS><<<blocks_for(cnt * 8, 128), 128, 0, s>>>(v, c, cnt, ce, A->rowptr, A->col, A->val);
+    if (m->npe == 4)
+      tet_fill_colour<PHYS><<<blocks_for(cnt * 4, 128), 128, 0, s>>>(v, cnt, ce, A->rowptr, A->col, A->val);
+    else
+      csr_fill_colour<PHYS><<<blocks_for(cnt * 8, 128), 128, 0, s>>>(v, c, cnt, ce, A->rowptr, A->col, A->val);
   }
 }
 
@@ -257,7 +334,8 @@ void launch_diag(const mf_mesh *m, const MeshView &v, double *diag, cudaStream_t
     const int64_t cnt = colour_count(m, c);
     if (!cnt) continue;
     const int32_t *ce = m->structured ? nullptr : m->colour_elems + m->colour_off[c];
-    diag_colour<PHYS><<<blocks_for(cnt, 128), 128, 0, s>>>(v, c, cnt, ce, diag);
+    if (m->npe == 4) tet_diag_colour<PHYS><<<blocks_for(cnt, 128), 128, 0, s>>>(v, cnt, ce, diag);
+    else diag_colour<PHYS><<<blocks_for(cnt, 128), 128, 0, s>>>(v, c, cnt, ce, diag);
   }
 }
 
@@ -307,21 +385,22 @@ void node_neighbours(const mf_mesh *m, const std::vector<uint8_t> &dmask, std::v
   }
   const std::vector<int32_t> &cells = m->h_cells;
   const int64_t E = m->n_cells;
+  const int npe = m->npe;
   std::vector<int64_t> eoff(N + 1, 0);
-  for (int64_t i = 0; i < 8 * E; ++i) eoff[cells[i] + 1]++;
+  for (int64_t i = 0; i < npe * E; ++i) eoff[cells[i] + 1]++;
   for (int64_t n = 0; n < N; ++n) eoff[n + 1] += eoff[n];
   std::vector<int64_t> fill(eoff.begin(), eoff.end() - 1);
-  std::vector<int32_t> adj(8 * E);
+  std::vector<int32_t> adj(npe * E);
   for (int64_t e = 0; e < E; ++e)
-    for (int a = 0; a < 8; ++a) adj[fill[cells[8 * e + a]]++] = (int32_t)e;
+    for (int a = 0; a < npe; ++a) adj[fill[cells[npe * e + a]]++] = (int32_t)e;
   std::vector<std::vector<int32_t>> lists(N);
   std::vector<int32_t> tmp;
   for (int64_t n = 0; n < N; ++n) {
     if (dmask[n]) continue;
     tmp.clear();
     for (int64_t t = eoff[n]; t < eoff[n + 1]; ++t)
-      for (int a = 0; a < 8; ++a) {
-        const int32_t mm = cells[8 * (int64_t)adj[t] + a];
+      for (int a = 0; a < npe; ++a) {
+        const int32_t mm = cells[npe * (int64_t)adj[t] + a];
         if (!dmask[mm]) tmp.push_back(mm);
       }
     std::sort(tmp.begin(), tmp.end());

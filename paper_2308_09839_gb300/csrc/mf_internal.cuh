@@ -52,7 +52,7 @@ int64_t mf_launches_now();
 struct MeshView {
   const double *X;     // [N][3] node coordinates
   const float *X32;    // [N][3] FP32 copy
-  const int32_t *cells;  // [E][8], null for structured boxes
+  const int32_t *cells;  // [E][8] ([E][4] for tetrahedra), null for structured boxes
   const double *mat;   // Laplace: kappa[E]; elasticity: (lam, mu)[E][2]
   const float *mat32;  // FP32 copy of mat
   const uint8_t *dmask;  // [N] Dirichlet mask (never null: zero-filled when unconstrained)
@@ -100,6 +100,7 @@ struct mf_mesh {
   int device = 0;
   int variant = MF_VARIANT_AUTO;
   int64_t n_nodes = 0, n_cells = 0, n_dof = 0, n_free = 0;
+  int npe = 8;  // nodes per element: 8 (Q1 hexahedron) or 4 (P1 tetrahedron, explicit cells only)
   bool structured = false;
   bool all_affine = false;
   int32_t nx = 0, ny = 0, nz = 0;

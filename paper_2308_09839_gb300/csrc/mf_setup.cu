@@ -10,6 +10,7 @@
 
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
+#include "mf_tet.cuh"
 
 // ------------------------------------------------------------------------------------ errors ----
 static thread_local char g_err[1024] = "";
@@ -110,6 +111,43 @@ __global__ void validate_kernel(MeshView m, int physics, ValidateOut *out) {
   }
 }
 
+// Tetrahedra: node ids in range, finite coordinates, positive orientation (D = 6 |T| > 0), material
+// admissible.
+__global__ void validate_tet_kernel(MeshView m, int physics, ValidateOut *out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_cells) return;
+  int flags = 0;
+  int64_t nodes[4];
+  for (int a = 0; a < 4; ++a) {
+    const int32_t n = m.cells[4 * e + a];
+    if (n < 0 || n >= m.n_nodes) flags |= BAD_NODE;
+    nodes[a] = n;
+  }
+  if (!(flags & BAD_NODE)) {
+    double X[4][3], n[4][3];
+    for (int a = 0; a < 4; ++a)
+      for (int i = 0; i < 3; ++i) {
+        X[a][i] = m.X[3 * nodes[a] + i];
+        if (!isfinite(X[a][i])) flags |= BAD_COORD;
+      }
+    if (!(flags & BAD_COORD)) {
+      const double D = p1::geometry<double>(X, n);
+      if (!(D > 0.0) || !isfinite(D)) flags |= BAD_DET;
+    }
+  }
+  if (phys_is_laplace(physics)) {
+    double k = m.mat[e];
+    if (!(k > 0.0) || !isfinite(k)) flags |= BAD_MAT;
+  } else {
+    double E = m.mat[2 * e], nu = m.mat[2 * e + 1];
+    if (!(E > 0.0) || !isfinite(E) || !(nu > -1.0 && nu < 0.5)) flags |= BAD_MAT;
+  }
+  if (flags) {
+    atomicOr(&out->flags, flags);
+    atomicMin(&out->first_bad, (long long)e);
+  }
+}
+
 // (E, nu) -> (lam, mu) per cell, plus the FP32 copies.
 __global__ void material_kernel(const double *in, double *out, float *out32, int64_t n_cells, int physics) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -171,20 +209,21 @@ static void free_mesh(mf_mesh *m) {
 // needs no atomics.  Deterministic (elements visited in index order, smallest free colour).
 static mf_status colour_elements(mf_mesh *m, cudaStream_t s) {
   const int64_t E = m->n_cells, N = m->n_nodes;
+  const int npe = m->npe;
   const std::vector<int32_t> &cells = m->h_cells;
   std::vector<int64_t> off(N + 1, 0);
-  for (int64_t i = 0; i < 8 * E; ++i) off[cells[i] + 1]++;
+  for (int64_t i = 0; i < npe * E; ++i) off[cells[i] + 1]++;
   for (int64_t n = 0; n < N; ++n) off[n + 1] += off[n];
   std::vector<int64_t> fill(off.begin(), off.end() - 1);
-  std::vector<int32_t> adj(8 * E);
+  std::vector<int32_t> adj(npe * E);
   for (int64_t e = 0; e < E; ++e)
-    for (int a = 0; a < 8; ++a) adj[fill[cells[8 * e + a]]++] = (int32_t)e;
+    for (int a = 0; a < npe; ++a) adj[fill[cells[npe * e + a]]++] = (int32_t)e;
   std::vector<int8_t> colour(E, -1);
   int ncol = 0;
   for (int64_t e = 0; e < E; ++e) {
     uint64_t used = 0;
-    for (int a = 0; a < 8; ++a) {
-      int32_t n = cells[8 * e + a];
+    for (int a = 0; a < npe; ++a) {
+      int32_t n = cells[npe * e + a];
       for (int64_t t = off[n]; t < off[n + 1]; ++t) {
         int8_t c = colour[adj[t]];
         if (c >= 0) used |= 1ull << c;
@@ -219,16 +258,17 @@ int64_t colour_count(const mf_mesh *m, int c) {
 }
 
 // ----------------------------------------------------------------------------- entry points ----
-extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells, const double *coords,
-                                   const int32_t *cells, int32_t nx, int32_t ny, int32_t nz, const double *mat,
-                                   const uint8_t *dirichlet, mf_stream stream, mf_mesh **out) {
+static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cells, const double *coords,
+                            const int32_t *cells, int32_t nx, int32_t ny, int32_t nz, const double *mat,
+                            const uint8_t *dirichlet, mf_stream stream, mf_mesh **out) {
   mf_clear_error();
   MF_ARG(out != nullptr, "mf_setup_mesh: out is NULL");
   *out = nullptr;
   MF_ARG(physics == MF_LAPLACE || physics == MF_ELASTICITY || physics == MF_VECTOR_LAPLACE,
          "mf_setup_mesh: unknown physics %d", physics);
   MF_ARG(coords && mat, "mf_setup_mesh: coords and mat are required");
-  MF_ARG(n_nodes >= 8 && n_cells >= 1, "mf_setup_mesh: need n_nodes >= 8 and n_cells >= 1");
+  MF_ARG(npe == 8 || cells != nullptr, "mf_setup_mesh: tetrahedral meshes need an explicit connectivity");
+  MF_ARG(n_nodes >= npe && n_cells >= 1, "mf_setup_mesh: need n_nodes >= %d and n_cells >= 1", npe);
   MF_ARG(n_nodes < (int64_t)INT32_MAX, "mf_setup_mesh: n_nodes must fit int32");
   if (!cells) {
     MF_ARG(nx > 0 && ny > 0 && nz > 0, "mf_setup_mesh: structured mesh needs nx, ny, nz > 0");
@@ -242,6 +282,7 @@ extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells
   m->ndpn = phys_ndpn(physics);
   m->n_nodes = n_nodes;
   m->n_cells = n_cells;
+  m->npe = npe;
   m->n_dof = n_nodes * m->ndpn;
   m->structured = cells == nullptr;
   m->nx = cells ? 0 : nx;
@@ -271,8 +312,8 @@ extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells
     SETUP_TRY(dmalloc(&m->dmask, n_nodes));
     SETUP_CUDA(cudaMemcpyAsync(m->X, coords, 3 * n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (cells) {
-      SETUP_TRY(dmalloc(&m->cells, 8 * n_cells));
-      SETUP_CUDA(cudaMemcpyAsync(m->cells, cells, 8 * n_cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      SETUP_TRY(dmalloc(&m->cells, npe * n_cells));
+      SETUP_CUDA(cudaMemcpyAsync(m->cells, cells, npe * n_cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
     if (dirichlet)
       SETUP_CUDA(cudaMemcpyAsync(m->dmask, dirichlet, n_nodes, cudaMemcpyDeviceToDevice, s));
@@ -288,7 +329,8 @@ extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells
     SETUP_CUDA(cudaMemcpyAsync(dv, &hv, sizeof(hv), cudaMemcpyHostToDevice, s));
     MeshView v = m->view();
     v.mat = mat;
-    validate_kernel<<<blocks_for(n_cells), kThreads, 0, s>>>(v, physics, dv);
+    if (npe == 4) validate_tet_kernel<<<blocks_for(n_cells), kThreads, 0, s>>>(v, physics, dv);
+    else validate_kernel<<<blocks_for(n_cells), kThreads, 0, s>>>(v, physics, dv);
     SETUP_CUDA(cudaGetLastError());
     SETUP_CUDA(cudaMemcpyAsync(&hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, s));
     SETUP_CUDA(cudaStreamSynchronize(s));
@@ -318,8 +360,8 @@ extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells
       SETUP_CUDA(cudaMemcpyAsync(m->dnodes, dn.data(), dn.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
 
     if (cells) {
-      m->h_cells.resize(8 * n_cells);
-      SETUP_CUDA(cudaMemcpyAsync(m->h_cells.data(), cells, 8 * n_cells * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      m->h_cells.resize(npe * n_cells);
+      SETUP_CUDA(cudaMemcpyAsync(m->h_cells.data(), cells, npe * n_cells * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       SETUP_CUDA(cudaStreamSynchronize(s));
       SETUP_TRY(colour_elements(m, s));
     } else {
@@ -339,6 +381,22 @@ fail:
 #undef SETUP_CUDA
 }
 
+extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells, const double *coords,
+                                   const int32_t *cells, int32_t nx, int32_t ny, int32_t nz, const double *mat,
+                                   const uint8_t *dirichlet, mf_stream stream, mf_mesh **out) {
+  return setup_mesh(8, physics, n_nodes, n_cells, coords, cells, nx, ny, nz, mat, dirichlet, stream, out);
+}
+
+extern "C" mf_status mf_setup_mesh_elem(int element, int physics, int64_t n_nodes, int64_t n_cells,
+                                        const double *coords, const int32_t *cells, const double *mat,
+                                        const uint8_t *dirichlet, mf_stream stream, mf_mesh **out) {
+  mf_clear_error();
+  MF_ARG(element == MF_ELEM_HEX8 || element == MF_ELEM_TET4, "mf_setup_mesh_elem: unknown element %d", element);
+  MF_ARG(cells != nullptr, "mf_setup_mesh_elem: cells is required");
+  return setup_mesh(element == MF_ELEM_TET4 ? 4 : 8, physics, n_nodes, n_cells, coords, cells, 0, 0, 0, mat,
+                    dirichlet, stream, out);
+}
+
 extern "C" mf_status mf_destroy_mesh(mf_mesh *mesh) {
   mf_clear_error();
   if (!mesh) return MF_OK;
@@ -355,7 +413,9 @@ extern "C" mf_status mf_mesh_query(const mf_mesh *m, int64_t *n_nodes, int64_t *
   if (n_dof) *n_dof = m->n_dof;
   if (n_free) *n_free = m->n_free;
   if (n_colours) *n_colours = m->n_colours;
-  if (flags) *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0) | (m->pa ? 8 : 0);
+  if (flags)
+    *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0) | (m->pa ? 8 : 0) |
+             (m->npe == 4 ? 16 : 0);
   return MF_OK;
 }
 

@@ -24,6 +24,8 @@ MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_MESH, MF_ERR_OOM, MF_ERR_BREAKDOWN, MF_ERR_TIMEO
 MF_LAPLACE, MF_ELASTICITY, MF_VECTOR_LAPLACE = 0, 1, 2
 PHYSICS = {"laplace": MF_LAPLACE, "elasticity": MF_ELASTICITY, "vector_laplace": MF_VECTOR_LAPLACE}
 MF_VARIANT_AUTO, MF_VARIANT_REFERENCE, MF_VARIANT_GENERAL, MF_VARIANT_PARTIAL = 0, 1, 2, 3
+MF_ELEM_HEX8, MF_ELEM_TET4 = 0, 1
+ELEMENTS = {"hex8": MF_ELEM_HEX8, "tet4": MF_ELEM_TET4}
 MF_OP_MATFREE, MF_OP_CSR = 0, 1
 MF_PREC_FP64, MF_PREC_MIXED_IR = 0, 1
 MF_PC_NONE, MF_PC_JACOBI, MF_PC_LEARNED = 0, 1, 2
@@ -48,6 +50,7 @@ class mf_solve_info(C.Structure):
 
 _SIGS = {
     "mf_setup_mesh": (C.c_int, [C.c_int, i64, i64, vp, vp, i32, i32, i32, vp, vp, vp, C.POINTER(vp)]),
+    "mf_setup_mesh_elem": (C.c_int, [C.c_int, C.c_int, i64, i64, vp, vp, vp, vp, vp, C.POINTER(vp)]),
     "mf_destroy_mesh": (C.c_int, [vp]),
     "mf_mesh_query": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
                                 C.POINTER(i32), C.POINTER(i32)]),
@@ -139,6 +142,13 @@ def mf_setup_mesh(physics, n_nodes, n_cells, coords, cells, nx, ny, nz, mat, dir
     return h.value
 
 
+def mf_setup_mesh_elem(element, physics, n_nodes, n_cells, coords, cells, mat, dirichlet, stream=None) -> int:
+    h = vp()
+    check(lib.mf_setup_mesh_elem(element, physics, n_nodes, n_cells, _ptr(coords), _ptr(cells), _ptr(mat),
+                                 _ptr(dirichlet), _stream(stream), C.byref(h)), "mf_setup_mesh_elem")
+    return h.value
+
+
 def mf_destroy_mesh(h) -> None:
     check(lib.mf_destroy_mesh(h), "mf_destroy_mesh")
 
@@ -149,7 +159,7 @@ def mf_mesh_query(h) -> dict:
     check(lib.mf_mesh_query(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e), C.byref(f)), "mf_mesh_query")
     return dict(n_nodes=a.value, n_cells=b.value, n_dof=c.value, n_free=d.value, n_colours=e.value,
                 structured=bool(f.value & 1), all_affine=bool(f.value & 2), tensor_product=bool(f.value & 4),
-                partial_assembly=bool(f.value & 8))
+                partial_assembly=bool(f.value & 8), tetrahedral=bool(f.value & 16))
 
 
 def mf_set_apply_variant(h, variant: int) -> None:
@@ -389,14 +399,19 @@ def mf_version() -> str:
 class Mesh:
     """Owner of an ``mf_mesh`` handle.  Arrays are torch tensors on the current CUDA device."""
 
-    def __init__(self, physics: str, coords, mat, dirichlet=None, cells=None, dims=None, stream=None):
+    def __init__(self, physics: str, coords, mat, dirichlet=None, cells=None, dims=None, stream=None,
+                 element: str = "hex8"):
         self.physics = PHYSICS[physics]
         n_nodes = coords.shape[0]
         n_cells = cells.shape[0] if cells is not None else dims[0] * dims[1] * dims[2]
         nx, ny, nz = dims if (cells is None) else (0, 0, 0)
         self.dims = (nx, ny, nz)
         self._keep = (coords, mat, dirichlet, cells)
-        self.h = mf_setup_mesh(self.physics, n_nodes, n_cells, coords, cells, nx, ny, nz, mat, dirichlet, stream)
+        if element == "hex8":
+            self.h = mf_setup_mesh(self.physics, n_nodes, n_cells, coords, cells, nx, ny, nz, mat, dirichlet, stream)
+        else:
+            self.h = mf_setup_mesh_elem(ELEMENTS[element], self.physics, n_nodes, n_cells, coords, cells, mat,
+                                        dirichlet, stream)
         self.info = mf_mesh_query(self.h)
         self._keep = None
         self.device = coords.device
@@ -407,8 +422,10 @@ class Mesh:
         coords = torch.from_numpy(p.coords).to(device)
         mat = torch.from_numpy(p.mat).to(device).contiguous()
         dirichlet = torch.from_numpy(p.dirichlet).to(device)
-        cells = None if structured else torch.from_numpy(p.cell_array()).to(device)
-        return cls(p.physics, coords, mat, dirichlet, cells, (p.nx, p.ny, p.nz), stream)
+        element = getattr(p, "element", "hex8")
+        explicit = not structured or element != "hex8"
+        cells = torch.from_numpy(p.cell_array()).to(device) if explicit else None
+        return cls(p.physics, coords, mat, dirichlet, cells, (p.nx, p.ny, p.nz), stream, element=element)
 
     @property
     def n_dof(self) -> int:
