@@ -425,6 +425,12 @@ def main():
             cg[p.physics] = {"seconds": info.seconds, "iters": info.iters, "status": info.status,
                              "rel_res_true": info.rel_res_true,
                              "cg_gdofs": p.n_free * info.iters / info.seconds / 1e9}
+            # single-synchronisation recurrence (Chronopoulos-Gear): one kernel fewer per iteration
+            _, ip = m.cg(b, timeout_s=args.cg_timeout, ok=CG_OK, recurrence=mf.MF_CG_PIPELINED)
+            cg[p.physics]["pipelined"] = {"seconds": ip.seconds, "iters": ip.iters, "status": ip.status,
+                                          "rel_res_true": ip.rel_res_true,
+                                          "ms_per_iter": 1e3 * ip.seconds / max(ip.iters, 1),
+                                          "ms_per_iter_classic": 1e3 * info.seconds / max(info.iters, 1)}
         extras["cg_matfree"] = cg
 
     # ---- vector Laplace (Eq. 5) on the elasticity workload's 160^3 mesh: matrix-free vs CSR

@@ -198,6 +198,15 @@ mf_status mf_destroy_csr(mf_csr *csr);
 enum { MF_OP_MATFREE = 0, MF_OP_CSR = 1 };
 enum { MF_PREC_FP64 = 0, MF_PREC_MIXED_IR = 1 };
 enum { MF_PC_NONE = 0, MF_PC_JACOBI = 1, MF_PC_LEARNED = 2 };
+/* CG recurrence (FP64 solves with MF_PC_NONE or MF_PC_JACOBI):
+ *   MF_CG_CLASSIC    Hestenes-Stiefel as in Table 4: per iteration the apply (with p^T A p fused on
+ *                    tensor-product meshes), the x/r update with r^T z, and the p update
+ *   MF_CG_PIPELINED  single-synchronisation recurrence of Chronopoulos and Gear (1989): w = A u
+ *                    (u = M^-1 r) with u^T w fused into the apply, then one pass that updates p, s = A p,
+ *                    x, r and u and forms r^T u; one kernel fewer per iteration, the same iterates
+ *                    in exact arithmetic.  Not available for MIXED_IR, the learned preconditioner,
+ *                    mf_cg_solve_noalloc or the batched solver (MF_ERR_ARG). */
+enum { MF_CG_CLASSIC = 0, MF_CG_PIPELINED = 1 };
 typedef struct mf_net mf_net;
 
 typedef struct {
@@ -218,6 +227,7 @@ typedef struct {
   int32_t max_outer;     /* MIXED_IR: refinement steps */
   const mf_csr *csr;     /* operator when op == MF_OP_CSR */
   const mf_net *net;     /* network when precond == MF_PC_LEARNED (flexible CG, see mf_net_create) */
+  int32_t recurrence;    /* MF_CG_CLASSIC (default) or MF_CG_PIPELINED */
 } mf_solve_opts;
 
 typedef struct {
@@ -235,7 +245,7 @@ typedef struct {
 mf_status mf_operator_diagonal(const mf_mesh *mesh, double *diag, mf_stream stream);
 
 /* Fills *opts with defaults: matrix-free, FP64, no preconditioner, rtol 1e-8, max_iter 100000,
- * check_every 32, graphs on, no timeout, inner_rtol 1e-4, max_outer 50. */
+ * check_every 32, graphs on, no timeout, inner_rtol 1e-4, max_outer 50, classic recurrence. */
 void mf_solve_opts_default(mf_solve_opts *opts);
 
 /*

@@ -9,6 +9,10 @@
 * ``fcg_m``  truncated flexible CG, FCG(m) (Notay 2000): each new direction is the preconditioned
            residual A-orthogonalised against the last m directions.
 * ``iterative_refinement``  x += solve_inner(b - A x) until the FP64 residual meets the tolerance.
+* ``cg_single_sync``  the single-synchronisation CG of Chronopoulos and Gear (1989): both inner
+           products of an iteration, gamma = r^T u and delta = w^T u with u = M r and w = A u, are
+           taken together, and s = A p is carried by a recurrence.  In exact arithmetic it produces
+           the iterates of ``pcg``.
 
 Readings: x0 = 0; stop when ||r_k||_2 <= rtol ||b||_2 (the paper gives no stopping norm); the
 iteration count is the number of operator applies inside the loop.
@@ -143,3 +147,44 @@ def iterative_refinement(apply64, inner_solve, b, rtol=1e-10, max_outer=50):
         m += 1
         hist.append(float(np.linalg.norm(r)) / bn)
     return x, m, hist
+
+
+def cg_single_sync(apply, b, precond=None, rtol=1e-8, max_iter=100000):
+    """Chronopoulos-Gear CG, x0 = 0; precond(r) = M r (None: identity).  Returns (x, iterations,
+    residual history).  Iteration k: u_k = M r_k, w_k = A u_k, gamma_k = r_k.u_k, delta_k = w_k.u_k;
+    beta_k = gamma_k / gamma_{k-1} (beta_0 = 0), alpha_k = gamma_k / (delta_k - beta_k gamma_k /
+    alpha_{k-1}) (alpha_0 = gamma_0 / delta_0); p_k = u_k + beta_k p_{k-1}, s_k = w_k + beta_k
+    s_{k-1}; x_{k+1} = x_k + alpha_k p_k, r_{k+1} = r_k - alpha_k s_k."""
+    M = precond or (lambda v: v.copy())
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = np.zeros_like(b)
+    s = np.zeros_like(b)
+    bn = float(np.linalg.norm(b))
+    if bn == 0.0:
+        return x, 0, [0.0]
+    u = M(r)
+    gamma_prev = alpha_prev = None
+    k = 0
+    hist = [1.0]
+    while k < max_iter and np.linalg.norm(r) > rtol * bn:
+        w = apply(u)
+        gamma = float(np.dot(r, u))
+        delta = float(np.dot(w, u))
+        if k == 0:
+            beta, alpha = 0.0, gamma / delta
+        else:
+            beta = gamma / gamma_prev
+            alpha = gamma / (delta - beta * gamma / alpha_prev)
+        if not alpha > 0.0:
+            raise FloatingPointError("single-synchronisation CG breakdown")
+        p = u + beta * p
+        s = w + beta * s
+        x += alpha * p
+        r -= alpha * s
+        u = M(r)
+        gamma_prev, alpha_prev = gamma, alpha
+        k += 1
+        hist.append(float(np.linalg.norm(r)) / bn)
+    return x, k, hist
+

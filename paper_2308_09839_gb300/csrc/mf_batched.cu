@@ -299,6 +299,7 @@ extern "C" mf_status mf_batch_create(mf_mesh *const *meshes, int32_t n, const mf
   MF_ARG(o->precision == MF_PREC_FP64 && o->precond == MF_PC_NONE && o->op == MF_OP_MATFREE,
          "mf_batch_create: the batched solver is matrix-free FP64 CG without preconditioner");
   MF_ARG(o->max_iter > 0 && o->rtol > 0, "mf_batch_create: bad max_iter/rtol");
+  MF_ARG(o->recurrence == MF_CG_CLASSIC, "mf_batch_create: the batched solver uses the classic recurrence");
   for (int i = 0; i < n; ++i) {
     MF_ARG(meshes[i] != nullptr, "mf_batch_create: mesh %d is NULL", i);
     if (meshes[i]->physics != MF_LAPLACE || !meshes[i]->tp) {

@@ -188,6 +188,106 @@ __global__ void __launch_bounds__(kRedThreads) cg_update_p(int64_t n, const R *_
   }
 }
 
+// ---- single-synchronisation CG (Chronopoulos and Gear 1989), the pipelined recurrence.  With
+// u = M^-1 r and w = A u, both dot products of an iteration, gamma = r.u and delta = u.w, are
+// formed where their operands are produced (gamma in the update, delta in the apply), and
+//   beta_i = gamma_i / gamma_{i-1},  alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1}),
+//   p = u + beta p,  s = w + beta s (= A p),  x += alpha p,  r -= alpha s,  u = M^-1 r
+// run in one pass: per iteration the apply and one update kernel (the classic recurrence needs a
+// second vector kernel, because its p update waits for the reduced r.r).
+
+// x = 0, r = b, u = M^-1 b (u is r without a preconditioner), p = s = 0; gamma = r.u, ||b||^2,
+// beta = 0, alpha = 1 (so that the first alpha is gamma / delta).
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) cgp_init(int64_t n, const R *__restrict__ b, R *__restrict__ x,
+                                                        R *__restrict__ r, R *__restrict__ u, R *__restrict__ p,
+                                                        R *__restrict__ s, const double *__restrict__ invdiag,
+                                                        double *partials, CgScalars *sc, double rtol, int max_iter) {
+  double v[2] = {0.0, 0.0};
+  GRID_STRIDE(i, n) {
+    const R bi = b[i];
+    x[i] = (R)0;
+    r[i] = bi;
+    p[i] = (R)0;
+    s[i] = (R)0;
+    const double z = invdiag ? (double)bi * invdiag[i] : (double)bi;
+    if (u) u[i] = (R)z;
+    v[0] += (double)bi * (double)bi;
+    v[1] += (double)bi * z;
+  }
+  double out[2];
+  if (grid_reduce<2>(v, partials, &sc->ticket, out) && threadIdx.x == 0) {
+    sc->bb = out[0];
+    sc->rr = out[0];
+    sc->rz = out[1];
+    sc->beta = 0.0;
+    sc->alpha = 1.0;
+    sc->tol2 = rtol * rtol * out[0];
+    sc->iter = 0;
+    sc->max_iter = max_iter;
+    sc->status = 0;
+    sc->done = (out[0] <= sc->tol2) ? 1 : 0;
+    if (!isfinite(out[0])) {
+      sc->status = MF_ERR_BREAKDOWN;
+      sc->done = 1;
+    }
+  }
+}
+
+// The update pass of an iteration: alpha from gamma (sc->rz), delta (sc->pAp), beta and the previous
+// alpha; p, s, x, r and u; then gamma' = r.u and ||r||^2, beta' = gamma'/gamma, convergence test.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) cgp_update(int64_t n, R *__restrict__ x, R *__restrict__ r,
+                                                          R *__restrict__ u, R *__restrict__ p, R *__restrict__ s,
+                                                          const R *__restrict__ w, const double *__restrict__ invdiag,
+                                                          double *partials, CgScalars *sc) {
+  if (sc->done) return;
+  const double gamma = sc->rz, beta = sc->beta;
+  const double denom = sc->pAp - beta * gamma / sc->alpha;
+  if (!(denom > 0.0) || !isfinite(denom)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc->status = MF_ERR_BREAKDOWN;
+      sc->done = 1;
+    }
+    return;
+  }
+  const double alpha = gamma / denom;
+  const R *uu = u ? u : r;
+  double v[2] = {0.0, 0.0};
+  GRID_STRIDE(i, n) {
+    const double pi = (double)uu[i] + beta * (double)p[i];
+    const double si = (double)w[i] + beta * (double)s[i];
+    p[i] = (R)pi;
+    s[i] = (R)si;
+    x[i] = (R)((double)x[i] + alpha * pi);
+    const R ri = (R)((double)r[i] - alpha * si);
+    r[i] = ri;
+    const double rd = (double)ri;
+    const double z = invdiag ? rd * invdiag[i] : rd;
+    if (u) u[i] = (R)z;
+    v[0] += rd * rd;
+    v[1] += rd * z;
+  }
+  double out[2];
+  if (grid_reduce<2>(v, partials, &sc->ticket, out) && threadIdx.x == 0) {
+    const double rr = out[0], rz = out[1];
+    sc->beta = rz / gamma;
+    sc->alpha = alpha;
+    sc->rr = rr;
+    sc->rz = rz;
+    sc->iter += 1;
+    if (!isfinite(rr) || !isfinite(rz)) {
+      sc->status = MF_ERR_BREAKDOWN;
+      sc->done = 1;
+    } else if (rr <= sc->tol2) {
+      sc->done = 1;
+    } else if (sc->iter >= sc->max_iter) {
+      sc->status = MF_NOT_CONVERGED;
+      sc->done = 1;
+    }
+  }
+}
+
 // res = b - Ax (stored when `res` is not null); res2 = ||b - Ax||^2.
 __global__ void __launch_bounds__(kRedThreads) residual_kernel(int64_t n, const double *__restrict__ b,
                                                                const double *__restrict__ Ax, double *__restrict__ res,
@@ -223,6 +323,7 @@ using OpDotFn = std::function<mf_status(const void *in, void *out, cudaStream_t 
 struct CgWorkspace {
   int64_t n = 0;
   double *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *invdiag = nullptr, *bb = nullptr;
+  double *s = nullptr, *u = nullptr;  // pipelined recurrence: s = A p, u = M^-1 r (Jacobi only)
   float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr;
   double *partials = nullptr;
   double *dotp = nullptr;       // per-CTA parts of the dot product fused into the apply
@@ -243,6 +344,7 @@ void cg_workspace_free(CgWorkspace *w) {
   for (auto &g : w->g)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   cudaFree(w->x); cudaFree(w->r); cudaFree(w->p); cudaFree(w->Ap); cudaFree(w->invdiag); cudaFree(w->bb);
+  cudaFree(w->s); cudaFree(w->u);
   cudaFree(w->x32); cudaFree(w->r32); cudaFree(w->p32); cudaFree(w->Ap32);
   cudaFree(w->partials); cudaFree(w->sc); cudaFree(w->sc32); cudaFree(w->dotp); cudaFree(w->dticket);
   if (w->h_sc) cudaFreeHost(w->h_sc);
@@ -319,15 +421,39 @@ mf_status cg_iteration(const OpFn &op, const OpDotFn &opdot, int64_t n, R *x, R 
   return MF_OK;
 }
 
+// One iteration of the single-synchronisation recurrence: w = A u with delta = u.w, then the update.
+mf_status cgp_iteration(const OpFn &op, const OpDotFn &opdot, int64_t n, double *x, double *r, double *u, double *p,
+                        double *sv, double *wv, const double *invdiag, double *partials, CgScalars *sc,
+                        cudaStream_t s) {
+  double *in = u ? u : r;
+  if (opdot) {
+    MF_TRY(opdot(in, wv, s, &sc->done, &sc->pAp));  // w = A u and u.w in one kernel
+    mf_count_launches(1);
+  } else {
+    MF_TRY(op(in, wv, s, &sc->done));
+    mf_count_launches(2);
+    cg_pap<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, in, wv, partials, sc);
+  }
+  cgp_update<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, u, p, sv, wv, invdiag, partials, sc);
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
 // Run the CG loop that cg_init prepared: blocks of `k` iterations (graph or plain launches),
 // host reads the done flag after each block.
+using IterFn = std::function<mf_status(cudaStream_t)>;
+
 template <typename R>
 mf_status cg_loop(CgWorkspace *w, int slot, long long key, const OpFn &op, const OpDotFn &opdot, int64_t n, R *x,
                   R *r, R *p, R *Ap,
                   const double *invdiag, CgScalars *sc, int k, bool use_graph, double deadline_s,
-                  std::chrono::steady_clock::time_point t0, cudaStream_t s, CgScalars *host) {
+                  std::chrono::steady_clock::time_point t0, cudaStream_t s, CgScalars *host,
+                  const IterFn &iter = IterFn()) {
   auto body = [&](cudaStream_t st) -> mf_status {
-    for (int it = 0; it < k; ++it) MF_TRY(cg_iteration<R>(op, opdot, n, x, r, p, Ap, invdiag, w->partials, sc, st));
+    for (int it = 0; it < k; ++it) {
+      if (iter) MF_TRY(iter(st));
+      else MF_TRY(cg_iteration<R>(op, opdot, n, x, r, p, Ap, invdiag, w->partials, sc, st));
+    }
     return MF_OK;
   };
   CgWorkspace::Graph &g = w->g[slot];
@@ -751,6 +877,7 @@ extern "C" void mf_solve_opts_default(mf_solve_opts *o) {
   o->max_outer = 50;
   o->csr = nullptr;
   o->net = nullptr;
+  o->recurrence = MF_CG_CLASSIC;
 }
 
 extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double *x, mf_solve_info *info,
@@ -766,8 +893,13 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
          "mf_cg_solve: unknown preconditioner");
   if (o->precond == MF_PC_LEARNED) {
     MF_ARG(o->precision == MF_PREC_FP64 && o->op == MF_OP_MATFREE, "mf_cg_solve: MF_PC_LEARNED is FP64 matrix-free");
+    MF_ARG(o->recurrence == MF_CG_CLASSIC, "mf_cg_solve: MF_PC_LEARNED runs flexible CG (classic recurrence only)");
     return fcg_solve(m, o, b, x, info, (cudaStream_t)stream, t0);
   }
+  MF_ARG(o->recurrence == MF_CG_CLASSIC || o->recurrence == MF_CG_PIPELINED, "mf_cg_solve: unknown recurrence %d",
+         o->recurrence);
+  MF_ARG(o->recurrence == MF_CG_CLASSIC || o->precision == MF_PREC_FP64,
+         "mf_cg_solve: the pipelined recurrence is FP64 (MIXED_IR uses the classic one)");
   MF_ARG(o->precision == MF_PREC_FP64 || o->precond == MF_PC_NONE, "mf_cg_solve: MIXED_IR takes no preconditioner");
   MF_ARG(o->precision == MF_PREC_FP64 || o->op == MF_OP_MATFREE, "mf_cg_solve: MIXED_IR needs the matrix-free operator");
   MF_ARG(o->max_iter > 0 && o->rtol > 0 && o->check_every > 0, "mf_cg_solve: bad max_iter/rtol/check_every");
@@ -798,13 +930,32 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
       return tile_apply_dot_fp32(m, (const float *)in, (float *)out, st, skip, w->dotp, w->dticket, dot);
     };
   const long long key64 = ((long long)o->op << 40) ^ ((long long)o->precond << 36) ^ ((long long)m->variant << 32) ^
-                          ((long long)(intptr_t)A & 0xffffffffll) ^ ((long long)o->check_every << 44);
+                          ((long long)(intptr_t)A & 0xffffffffll) ^ ((long long)o->check_every << 44) ^
+                          ((long long)o->recurrence << 60);
   const long long key32 = ((long long)m->variant << 32) ^ ((long long)o->check_every << 44) ^ 0x5a5a;
   mf_status st = MF_OK;
   int iters = 0, outer = 0;
   double rel_rec = 0.0;
   CgScalars *h = w->h_sc;
-  if (!mixed) {
+  if (!mixed && o->recurrence == MF_CG_PIPELINED) {
+    if (!w->s) MF_CUDA(cudaMalloc(&w->s, n * sizeof(double)));
+    if (jac && !w->u) MF_CUDA(cudaMalloc(&w->u, n * sizeof(double)));
+    double *u = jac ? w->u : nullptr;
+    const double *idg = jac ? w->invdiag : nullptr;
+    mf_count_launches(1);
+    cgp_init<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->x, w->r, u, w->p, w->s, idg, w->partials, w->sc,
+                                                       o->rtol, o->max_iter);
+    MF_CUDA(cudaGetLastError());
+    IterFn iter = [&](cudaStream_t st) {
+      return cgp_iteration(op64, opdot64, n, w->x, w->r, u, w->p, w->s, w->Ap, idg, w->partials, w->sc, st);
+    };
+    st = cg_loop<double>(w, 0, key64, op64, opdot64, n, w->x, w->r, w->p, w->Ap, idg, w->sc, o->check_every,
+                         o->use_graph != 0, o->timeout_s, t0, s, h, iter);
+    if (st != MF_OK && st != MF_ERR_TIMEOUT) return st;
+    if (st == MF_OK) st = (mf_status)h->status;
+    iters = h->iter;
+    rel_rec = h->bb > 0 ? std::sqrt(h->rr / h->bb) : 0.0;
+  } else if (!mixed) {
     mf_count_launches(1);
     cg_init<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->x, w->r, w->p, jac ? w->invdiag : nullptr, w->partials,
                                                       w->sc, o->rtol, o->max_iter);
@@ -956,6 +1107,7 @@ extern "C" mf_status mf_cg_solve_noalloc(const mf_mesh *m, const mf_solve_opts *
   MF_ARG(o->precision == MF_PREC_FP64 && o->precond == MF_PC_NONE,
          "mf_cg_solve_noalloc: only FP64 without preconditioner is available");
   MF_ARG(o->max_iter > 0 && o->rtol > 0 && o->check_every > 0, "mf_cg_solve_noalloc: bad max_iter/rtol/check_every");
+  MF_ARG(o->recurrence == MF_CG_CLASSIC, "mf_cg_solve_noalloc: only the classic recurrence");
   cudaStream_t s = (cudaStream_t)stream;
   double *base = nullptr;
   MF_TRY(noalloc_scratch(&base));

@@ -26,6 +26,7 @@ PHYSICS = {"laplace": MF_LAPLACE, "elasticity": MF_ELASTICITY, "vector_laplace":
 MF_VARIANT_AUTO, MF_VARIANT_REFERENCE, MF_VARIANT_GENERAL, MF_VARIANT_PARTIAL = 0, 1, 2, 3
 MF_ELEM_HEX8, MF_ELEM_TET4 = 0, 1
 ELEMENTS = {"hex8": MF_ELEM_HEX8, "tet4": MF_ELEM_TET4}
+MF_CG_CLASSIC, MF_CG_PIPELINED = 0, 1
 MF_OP_MATFREE, MF_OP_CSR = 0, 1
 MF_PREC_FP64, MF_PREC_MIXED_IR = 0, 1
 MF_PC_NONE, MF_PC_JACOBI, MF_PC_LEARNED = 0, 1, 2
@@ -40,7 +41,7 @@ i32, i64, f64 = C.c_int32, C.c_int64, C.c_double
 class mf_solve_opts(C.Structure):
     _fields_ = [("op", i32), ("precision", i32), ("precond", i32), ("max_iter", i32), ("rtol", f64),
                 ("check_every", i32), ("use_graph", i32), ("timeout_s", f64), ("inner_rtol", f64),
-                ("max_outer", i32), ("csr", vp), ("net", vp)]
+                ("max_outer", i32), ("csr", vp), ("net", vp), ("recurrence", i32)]
 
 
 class mf_solve_info(C.Structure):

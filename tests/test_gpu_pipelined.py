@@ -1,0 +1,93 @@
+"""Single-synchronisation (pipelined) CG recurrence of Chronopoulos and Gear through the C ABI,
+against the oracle's ``cg_single_sync``: iteration counts within 1 % (at least 2), true residual at
+the tolerance, on every operator path (face-marching with the fused u.w, general structured,
+reference kernel on an unstructured mesh, CSR, tetrahedra), with and without Jacobi; graph and plain
+launches bitwise equal; the option checks."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fem, solvers
+from paper_2308_09839_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+from paper_2308_09839_gb300 import mf  # noqa: E402
+
+CASES = {
+    "laplace_tensor_product": (lambda: inputs.laplace_box(14, ny=11, nz=9, graded=0.4, seed=71), {}),
+    "elasticity_tensor_product": (lambda: inputs.elasticity_box(9, ny=8, nz=10, seed=72), {}),
+    "laplace_jittered": (lambda: inputs.laplace_box(10, jitter=0.2, seed=73), {}),
+    "elasticity_unstructured": (lambda: inputs.elasticity_box(6, jitter=0.1, seed=74), {"structured": False}),
+    "laplace_tet": (lambda: inputs.tet_box("laplace", 6, jitter=0.1, seed=75), {}),
+}
+
+
+def _close(a, b):
+    return abs(a - b) <= max(2, math.ceil(0.01 * b))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("jacobi", [False, True])
+def test_pipelined_cg_matches_oracle(name, jacobi):
+    make, kw = CASES[name]
+    p = make()
+    cells = p.cell_array()
+    A = fem.assemble_csr(p.physics, p.coords, cells, p.mat, p.dirichlet, p.n_nodes)
+    b = p.b()
+    dg = A.diagonal()
+    _, it_o, _ = solvers.cg_single_sync(lambda v: A @ v, b, (lambda r: r / dg) if jacobi else None, rtol=1e-8)
+    mesh = mf.Mesh.from_problem(p, **kw)
+    pc = mf.MF_PC_JACOBI if jacobi else mf.MF_PC_NONE
+    x, info = mesh.cg(torch.from_numpy(b).cuda(), recurrence=mf.MF_CG_PIPELINED, precond=pc)
+    torch.cuda.synchronize()
+    assert info.status == mf.MF_OK
+    assert _close(info.iters, it_o), (info.iters, it_o)
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.05e-8 * np.linalg.norm(b)
+    assert info.rel_res_true <= 1.05e-8
+    # the classic recurrence takes the same number of iterations up to rounding
+    _, ic = mesh.cg(torch.from_numpy(b).cuda(), precond=pc)
+    assert _close(ic.iters, info.iters), (ic.iters, info.iters)
+
+
+def test_pipelined_cg_csr_operator():
+    p = inputs.elasticity_box(7, jitter=0.15, seed=76)
+    mesh = mf.Mesh.from_problem(p)
+    csr = mesh.assemble_csr()
+    A = fem.assemble_csr(p.physics, p.coords, p.cell_array(), p.mat, p.dirichlet, p.n_nodes)
+    b = p.b()
+    _, it_o, _ = solvers.cg_single_sync(lambda v: A @ v, b, rtol=1e-8)
+    x, info = mesh.cg(torch.from_numpy(b).cuda(), csr=csr, recurrence=mf.MF_CG_PIPELINED)
+    torch.cuda.synchronize()
+    assert info.status == mf.MF_OK and _close(info.iters, it_o), (info.iters, it_o)
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.05e-8 * np.linalg.norm(b)
+
+
+def test_pipelined_graph_and_plain_launches_bitwise_equal():
+    p = inputs.laplace_box(16, ny=12, nz=20, graded=0.3, seed=77)
+    mesh = mf.Mesh.from_problem(p)
+    b = torch.from_numpy(p.b()).cuda()
+    x1, i1 = mesh.cg(b, recurrence=mf.MF_CG_PIPELINED, use_graph=1, check_every=16)
+    x1 = x1.clone()
+    x2, i2 = mesh.cg(b, recurrence=mf.MF_CG_PIPELINED, use_graph=0, check_every=7)
+    assert i1.iters == i2.iters
+    assert torch.equal(x1, x2)
+
+
+def test_pipelined_option_checks():
+    p = inputs.laplace_box(4, seed=78)
+    mesh = mf.Mesh.from_problem(p)
+    b = torch.from_numpy(p.b()).cuda()
+    with pytest.raises(mf.MfError):
+        mesh.cg(b, recurrence=mf.MF_CG_PIPELINED, precision=mf.MF_PREC_MIXED_IR)
+    with pytest.raises(mf.MfError):
+        mesh.cg(b, recurrence=7)
+    o = mf.mf_solve_opts_default()
+    o.recurrence = mf.MF_CG_PIPELINED
+    x = torch.empty_like(b)
+    with pytest.raises(mf.MfError):
+        mf.mf_cg_solve_noalloc(mesh.h, o, b, x)

@@ -400,3 +400,29 @@ def test_vector_laplace_is_componentwise_scalar_laplace():
         u = np.zeros((p.n_nodes, 3)); u[:, k] = 1.0
         y = fem.apply("vector_laplace", p.coords, cells, p.mat[:, 0], np.zeros(p.n_nodes, np.uint8), u.reshape(-1))
         assert np.abs(y).max() < 1e-13
+
+
+def test_single_sync_cg_pins():
+    """Chronopoulos-Gear CG: finite termination on a small SPD system, the exact solution of a
+    direct solve, the same residual history as CG (identity preconditioner) and as Jacobi-PCG in its
+    first iterations (equal in exact arithmetic), and its residual recurrence equal to b - A x."""
+    rng = np.random.default_rng(5)
+    Q = np.linalg.qr(rng.normal(size=(10, 10)))[0]
+    A = Q @ np.diag(np.linspace(1, 3, 10)) @ Q.T
+    b = rng.normal(size=10)
+    x, it, _ = solvers.cg_single_sync(lambda v: A @ v, b, rtol=1e-12)
+    assert it <= 12 and np.allclose(x, np.linalg.solve(A, b), atol=1e-10)
+    p = inputs.laplace_box(5, jitter=0.2, sigma=1.0, seed=3)
+    cells = p.cell_array()
+    A = fem.assemble_csr("laplace", p.coords, cells, p.mat, p.dirichlet, p.n_nodes)
+    b = p.b()
+    _, it_cg, h_cg = solvers.cg(lambda v: A @ v, b, rtol=1e-8)
+    x1, it_s, h_s = solvers.cg_single_sync(lambda v: A @ v, b, rtol=1e-8)
+    assert abs(it_s - it_cg) <= 1
+    assert np.allclose(h_s[:20], h_cg[:20], rtol=1e-8)
+    assert np.linalg.norm(b - A @ x1) <= 1.01e-8 * np.linalg.norm(b)
+    dg = A.diagonal()
+    _, it_j, h_j = solvers.pcg(lambda v: A @ v, b, lambda r: r / dg, rtol=1e-8)
+    _, it_sj, h_sj = solvers.cg_single_sync(lambda v: A @ v, b, lambda r: r / dg, rtol=1e-8)
+    assert abs(it_sj - it_j) <= 1
+    assert np.allclose(h_sj[:20], h_j[:20], rtol=1e-8)
