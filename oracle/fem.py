@@ -17,11 +17,19 @@ grad phi = J^{-T} grad_ref phi.  Readings taken where the paper is silent:
 * Dirichlet degrees of freedom: their columns are dropped and their rows are the identity, so
   (A x)_d = x_d.  For b_d = 0 and x0_d = 0 this is the reduced system on the free DoFs.
 
+Triquadratic hexahedra (Q2, 27 nodes), the higher-order elements that Sec. 7 names as future work:
+node a = i + 3 j + 9 k (i, j, k in {0, 1, 2}) sits at reference coordinates (i - 1, j - 1, k - 1) and
+phi_a = L_i(xi) L_j(eta) L_k(zeta) with the quadratic Lagrange polynomials L_0(t) = t (t - 1) / 2,
+L_1(t) = 1 - t^2, L_2(t) = t (t + 1) / 2; quadrature is the 3 x 3 x 3 Gauss rule (points 0 and
++-sqrt(3/5), weights 8/9 and 5/9; point q = i + 3 j + 9 k), exact for the stiffness integrand of
+an affine Q2 element.
+
 Linear tetrahedra (P1, 4 nodes), the simplex elements that Sec. 7 names as future work, use the
 same element integrals (Eqs. 1-3) with the reference tetrahedron {xi, eta, zeta >= 0, xi + eta +
 zeta <= 1}: phi_0 = 1 - xi - eta - zeta, phi_k = xi_k; the gradients are constant, so one point
 with weight 1/6 (the reference volume) integrates the element matrices exactly.  Every helper below
-takes the element type from the connectivity's width (8: Q1 hexahedron, 4: P1 tetrahedron).
+takes the element type from the connectivity's width (8: Q1 hexahedron, 4: P1 tetrahedron, 27: Q2
+hexahedron).
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
@@ -35,6 +43,11 @@ import scipy.sparse as sp
 G = 1.0 / math.sqrt(3.0)
 
 CHUNK = 1 << 16  # elements per vectorised block (bounds the memory of the (E, 8, 24, 24) temporaries)
+
+
+def _chunk(npe: int) -> int:
+    """Elements per block for elements with npe nodes (the temporaries grow as npe^2)."""
+    return max(1, CHUNK * 64 // (npe * npe))
 
 
 def corner_signs() -> np.ndarray:
@@ -65,6 +78,46 @@ def shape_ref_grads(pts: np.ndarray) -> np.ndarray:
     return out
 
 
+def q2_nodes() -> np.ndarray:
+    """(27, 3) reference coordinates of the Q2 nodes, a = i + 3 j + 9 k at (i - 1, j - 1, k - 1)."""
+    a = np.arange(27)
+    return np.stack([a % 3, (a // 3) % 3, a // 9], axis=1).astype(np.float64) - 1.0
+
+
+def _lagrange2(t: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Quadratic Lagrange polynomials on the nodes -1, 0, 1 and their derivatives: (n, 3) each."""
+    L = np.stack([0.5 * t * (t - 1.0), 1.0 - t * t, 0.5 * t * (t + 1.0)], axis=-1)
+    dL = np.stack([t - 0.5, -2.0 * t, t + 0.5], axis=-1)
+    return L, dL
+
+
+def gauss3_points() -> tuple[np.ndarray, np.ndarray]:
+    """Tensor 3-point Gauss rule on [-1, 1]^3: points (27, 3), weights (27,), q = i + 3 j + 9 k."""
+    g1 = np.array([-math.sqrt(0.6), 0.0, math.sqrt(0.6)])
+    w1 = np.array([5.0, 8.0, 5.0]) / 9.0
+    q = np.arange(27)
+    idx = np.stack([q % 3, (q // 3) % 3, q // 9], axis=1)
+    return g1[idx], w1[idx[:, 0]] * w1[idx[:, 1]] * w1[idx[:, 2]]
+
+
+def q2_shape_values(pts: np.ndarray) -> np.ndarray:
+    """phi_a at points: (nq, 27)."""
+    n = q2_nodes().astype(int) + 1
+    Ls = [_lagrange2(pts[:, d])[0] for d in range(3)]
+    return Ls[0][:, n[:, 0]] * Ls[1][:, n[:, 1]] * Ls[2][:, n[:, 2]]
+
+
+def q2_shape_ref_grads(pts: np.ndarray) -> np.ndarray:
+    """Reference gradients d phi_a / d xi_d at points: (nq, 27, 3)."""
+    n = q2_nodes().astype(int) + 1
+    LL = [_lagrange2(pts[:, d]) for d in range(3)]
+    out = np.empty((pts.shape[0], 27, 3))
+    for d in range(3):
+        f = [LL[e][1 if e == d else 0][:, n[:, e]] for e in range(3)]
+        out[:, :, d] = f[0] * f[1] * f[2]
+    return out
+
+
 def tet_ref_grads() -> np.ndarray:
     """(4, 3) reference gradients of the P1 tetrahedron's shape functions (constant)."""
     return np.array([[-1.0, -1.0, -1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
@@ -79,6 +132,9 @@ def reference_rule(npe: int) -> tuple[np.ndarray, np.ndarray]:
         return w, shape_ref_grads(pts)
     if npe == 4:
         return np.array([1.0 / 6.0]), tet_ref_grads()[None]
+    if npe == 27:
+        pts, w = gauss3_points()
+        return w, q2_shape_ref_grads(pts)
     raise ValueError(f"no element with {npe} nodes")
 
 
@@ -180,8 +236,9 @@ def apply(physics, coords, cells, mat, dirichlet, x) -> np.ndarray:
     dmask = np.repeat(dirichlet.astype(bool), ndpn)
     xm = np.where(dmask, 0.0, x)
     y = np.zeros(x.shape[0])
-    for s in range(0, cells.shape[0], CHUNK):
-        el = np.arange(s, min(s + CHUNK, cells.shape[0]))
+    ch = _chunk(cells.shape[1])
+    for s in range(0, cells.shape[0], ch):
+        el = np.arange(s, min(s + ch, cells.shape[0]))
         Ae = element_matrices(physics, coords, cells, mat, el)
         dofs = element_dofs(cells[el], ndpn)
         ve = np.einsum("eij,ej->ei", Ae, xm[dofs])
@@ -234,8 +291,9 @@ def assemble_csr(physics, coords, cells, mat, dirichlet, n_nodes) -> sp.csr_matr
     n = n_nodes * ndpn
     dmask = np.repeat(dirichlet.astype(bool), ndpn)
     rows_l, cols_l, vals_l = [], [], []
-    for s in range(0, cells.shape[0], CHUNK):
-        el = np.arange(s, min(s + CHUNK, cells.shape[0]))
+    ch = _chunk(cells.shape[1])
+    for s in range(0, cells.shape[0], ch):
+        el = np.arange(s, min(s + ch, cells.shape[0]))
         Ae = element_matrices(physics, coords, cells, mat, el)
         dofs = element_dofs(cells[el], ndpn)
         r = np.broadcast_to(dofs[:, :, None], Ae.shape).reshape(-1)
@@ -257,8 +315,9 @@ def diagonal(physics, coords, cells, mat, dirichlet, n_nodes) -> np.ndarray:
     ndpn = _ndpn(physics)
     dmask = np.repeat(dirichlet.astype(bool), ndpn)
     dg = np.zeros(n_nodes * ndpn)
-    for s in range(0, cells.shape[0], CHUNK):
-        el = np.arange(s, min(s + CHUNK, cells.shape[0]))
+    ch = _chunk(cells.shape[1])
+    for s in range(0, cells.shape[0], ch):
+        el = np.arange(s, min(s + ch, cells.shape[0]))
         Ae = element_matrices(physics, coords, cells, mat, el)
         dofs = element_dofs(cells[el], ndpn)
         dg += np.bincount(dofs.reshape(-1), weights=np.einsum("eii->ei", Ae).reshape(-1), minlength=dg.shape[0])
@@ -276,8 +335,9 @@ def load_vector(coords, cells, dirichlet, f) -> np.ndarray:
     N = shape_values(pts)
     dN = shape_ref_grads(pts)
     b = np.zeros(coords.shape[0])
-    for s in range(0, cells.shape[0], CHUNK):
-        el = np.arange(s, min(s + CHUNK, cells.shape[0]))
+    ch = _chunk(cells.shape[1])
+    for s in range(0, cells.shape[0], ch):
+        el = np.arange(s, min(s + ch, cells.shape[0]))
         X = coords[cells[el]]
         det = np.linalg.det(jacobians(X, dN))
         xq = np.einsum("qa,eai->eqi", N, X)
@@ -294,8 +354,9 @@ def error_norms(coords, cells, uh, u, grad_u) -> tuple[float, float]:
     N = shape_values(pts)
     dN = shape_ref_grads(pts)
     e0 = e1 = 0.0
-    for s in range(0, cells.shape[0], CHUNK):
-        el = np.arange(s, min(s + CHUNK, cells.shape[0]))
+    ch = _chunk(cells.shape[1])
+    for s in range(0, cells.shape[0], ch):
+        el = np.arange(s, min(s + ch, cells.shape[0]))
         X = coords[cells[el]]
         g, det = physical_grads(jacobians(X, dN), dN)
         xq = np.einsum("qa,eai->eqi", N, X)
@@ -315,8 +376,9 @@ def volumes(coords, cells) -> np.ndarray:
     pts, w = gauss_points()
     dN = shape_ref_grads(pts)
     out = np.empty(cells.shape[0])
-    for s in range(0, cells.shape[0], CHUNK):
-        el = np.arange(s, min(s + CHUNK, cells.shape[0]))
+    ch = _chunk(cells.shape[1])
+    for s in range(0, cells.shape[0], ch):
+        el = np.arange(s, min(s + ch, cells.shape[0]))
         out[el] = np.linalg.det(jacobians(coords[cells[el]], dN)) @ w
     return out
 
@@ -327,7 +389,8 @@ def min_det(coords, cells) -> float:
     allp = np.concatenate([pts, corner_signs()])
     dN = shape_ref_grads(allp)
     m = math.inf
-    for s in range(0, cells.shape[0], CHUNK):
-        el = np.arange(s, min(s + CHUNK, cells.shape[0]))
+    ch = _chunk(cells.shape[1])
+    for s in range(0, cells.shape[0], ch):
+        el = np.arange(s, min(s + ch, cells.shape[0]))
         m = min(m, float(np.linalg.det(jacobians(coords[cells[el]], dN)).min()))
     return m

@@ -231,7 +231,7 @@ class Problem:
     seed: int = 0
     cells: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
-    element: str = "hex8"   # "hex8" (Q1 hexahedra) | "tet4" (P1 tetrahedra, explicit cells)
+    element: str = "hex8"   # "hex8" (Q1) | "tet4" (P1 tetrahedra) | "hex27" (Q2); the last two with explicit cells
 
     @property
     def n_nodes(self) -> int:
@@ -321,6 +321,64 @@ def tet_box(physics: str, n, jitter=0.0, sigma=0.5, layered=True, seed=0, name=N
     mat = np.repeat(h.mat, 6, axis=0)
     return Problem(name or f"tet_{physics}_{n}x{ny}x{nz}", physics, n, ny, nz, h.coords, mat, h.dirichlet, seed,
                    cells=tet_cells(n, ny, nz), meta=dict(h.meta, element="tet4"), element="tet4")
+
+
+def q2_cells(nx: int, ny: int, nz: int) -> np.ndarray:
+    """Triquadratic (27-node) connectivity of the box, int32 [E][27].  Nodes form the
+    (2nx+1) x (2ny+1) x (2nz+1) lattice with id I + (2nx+1)(J + (2ny+1)K); node a = i + 3j + 9k of
+    element (ex, ey, ez) is lattice node (2ex + i, 2ey + j, 2ez + k)."""
+    NX, NY = 2 * nx + 1, 2 * ny + 1
+    ex, ey, ez = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ex, ey, ez = (v.transpose(2, 1, 0).reshape(-1) for v in (ex, ey, ez))  # element id runs ex fastest
+    a = np.arange(27)
+    I = 2 * ex[:, None] + (a % 3)[None]
+    J = 2 * ey[:, None] + ((a // 3) % 3)[None]
+    K = 2 * ez[:, None] + (a // 9)[None]
+    ids = I + NX * (J + NY * K)
+    if ids.max(initial=0) >= 2**31:
+        raise ValueError("mesh too large for int32 node ids")
+    return ids.astype(np.int32)
+
+
+def q2_coords(nx: int, ny: int, nz: int, jitter: float = 0.0, curve: float = 0.0, seed: int = 0) -> np.ndarray:
+    """Lattice coordinates of the triquadratic box mesh, float64 [(2nx+1)(2ny+1)(2nz+1)][3].  The
+    element vertices are the nodes of ``box_coords(nx, ny, nz, jitter, seed)``; every other lattice
+    node is the mean of the vertices around it (the trilinear midpoint, so edges stay straight).
+    ``curve = c > 0`` then moves every non-vertex node strictly inside the cube by U[-c h, c h] per
+    coordinate (curved elements)."""
+    V = box_coords(nx, ny, nz, jitter, seed).reshape(nz + 1, ny + 1, nx + 1, 3)
+    L = np.empty((2 * nz + 1, 2 * ny + 1, 2 * nx + 1, 3))
+    L[::2, ::2, ::2] = V
+    L[::2, ::2, 1::2] = 0.5 * (V[:, :, :-1] + V[:, :, 1:])
+    L[::2, 1::2, :] = 0.5 * (L[::2, :-1:2, :] + L[::2, 2::2, :])
+    L[1::2] = 0.5 * (L[:-1:2] + L[2::2])
+    X = L.reshape(-1, 3)
+    if curve > 0.0:
+        NX, NY, NZ = 2 * nx + 1, 2 * ny + 1, 2 * nz + 1
+        K, J, I = np.meshgrid(np.arange(NZ), np.arange(NY), np.arange(NX), indexing="ij")
+        I, J, K = I.reshape(-1), J.reshape(-1), K.reshape(-1)
+        vertex = (I % 2 == 0) & (J % 2 == 0) & (K % 2 == 0)
+        inner = (I > 0) & (I < NX - 1) & (J > 0) & (J < NY - 1) & (K > 0) & (K < NZ - 1)
+        sel = inner & ~vertex
+        h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+        X[sel] += _rng(seed, _S_JITTER + 100).uniform(-curve, curve, size=(int(sel.sum()), 3)) * h
+    return X
+
+
+def q2_box(physics: str, n, jitter=0.0, curve=0.0, sigma=0.5, layered=True, seed=0, name=None, ny=None,
+           nz=None) -> Problem:
+    """Q2 hexahedra on the n x ny x nz box (``q2_coords``, ``q2_cells``); cell constants as the Q1
+    recipe of the same physics; Dirichlet on z = 0 (lattice plane K = 0)."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    maker = {"laplace": laplace_box, "elasticity": elasticity_box, "vector_laplace": vector_laplace_box}[physics]
+    h = maker(n, jitter=jitter, sigma=sigma, layered=layered, seed=seed, ny=ny, nz=nz)
+    coords = q2_coords(n, ny, nz, jitter, curve, seed)
+    NX, NY = 2 * n + 1, 2 * ny + 1
+    dirichlet = np.zeros(coords.shape[0], dtype=np.uint8)
+    dirichlet[: NX * NY] = 1
+    return Problem(name or f"q2_{physics}_{n}x{ny}x{nz}", physics, n, ny, nz, coords, h.mat, dirichlet, seed,
+                   cells=q2_cells(n, ny, nz), meta=dict(h.meta, element="hex27", curve=curve), element="hex27")
 
 
 def small_laplace_16(seed=0) -> Problem:
