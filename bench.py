@@ -57,8 +57,9 @@ def parse():
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-RHS measurement")
     ap.add_argument("--no-vector", action="store_true", help="skip the vector Laplace measurement")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
-    ap.add_argument("--no-tet", action="store_true", help="skip the P1 tetrahedra measurement")
+    ap.add_argument("--no-tet", action="store_true", help="skip the P1 tetrahedra and Q2 hexahedra measurements")
     ap.add_argument("--n-tet", type=int, default=96, help="boxes per side of the tetrahedral meshes (6 tets each)")
+    ap.add_argument("--n-q2", type=int, default=48, help="Q2 hexahedra per side")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner measurement")
     ap.add_argument("--n-learned", type=int, default=128)
     ap.add_argument("--pairs", type=int, default=2000)
@@ -469,56 +470,63 @@ def main():
         del xv, yv
         torch.cuda.empty_cache()
 
-    # ---- P1 tetrahedra (Kuhn split of an n^3 box, 6 tets per box, jitter 0.1h): matrix-free apply
-    # (reference kernel, FP64 and FP32) against the CSR SpMV, and CG to 1e-8 both ways (Laplace).
-    # The FP64 kernel is bound by the FP64 pipe: FP64 operations per element of the formulation in
-    # csrc/mf_tet.cuh (geometry 47, Laplace 44 + 4 adds, elasticity 164 + 12 adds) against the
+    # ---- elements beyond Q1 (Sec. 7): P1 tetrahedra (Kuhn split of an n^3 box, 6 per box) and Q2
+    # hexahedra (27 nodes, 3x3x3 Gauss), jitter 0.1h: matrix-free apply (reference kernel, FP64 and
+    # FP32) against the CSR SpMV, and CG to 1e-8 both ways (Laplace).  The FP64 kernels are bound by
+    # the FP64 pipe: FP64 operations per element of the formulations in csrc/mf_tet.cuh (geometry
+    # 47, Laplace 44 + 4 adds, elasticity 164 + 12 adds) and csrc/mf_q2.cuh (per Gauss point: J 648,
+    # adj J 32, gradient 324 / 648, flux 40 / stress 150, scatter 324 / 648; times 27) against the
     # measured 1.20 TFLOP/s of FP64 FMA.
     if not args.no_tet:
-        tet = {}
-        for phys, flops_el in (("laplace", 95), ("elasticity", 211)):
-            pt = inputs.tet_box(phys, args.n_tet, jitter=0.1, sigma=0.5, layered=True, seed=0)
-            mt = mf.Mesh.from_problem(pt, device=f"cuda:{local}")
-            xt = torch.from_numpy(pt.x()).cuda()
-            yt = torch.empty_like(xt)
-            x32, y32 = xt.float(), torch.empty_like(xt, dtype=torch.float32)
+        cases = (("tetrahedra", inputs.tet_box, args.n_tet, {"laplace": 95, "elasticity": 211}, "x 6 tetrahedra"),
+                 ("q2_hexahedra", inputs.q2_box, args.n_q2, {"laplace": 36936, "elasticity": 57402},
+                  "Q2 hexahedra"))
+        for key, make, nb, flops, what in cases:
+            res = {}
+            for phys in ("laplace", "elasticity"):
+                pt = make(phys, nb, jitter=0.1, sigma=0.5, layered=True, seed=0)
+                mt = mf.Mesh.from_problem(pt, device=f"cuda:{local}")
+                xt = torch.from_numpy(pt.x()).cuda()
+                yt = torch.empty_like(xt)
+                x32, y32 = xt.float(), torch.empty_like(xt, dtype=torch.float32)
 
-            def timed_t(fn, reps):
-                for _ in range(3):
-                    fn()
-                torch.cuda.synchronize()
-                e0.record()
-                for _ in range(reps):
-                    fn()
-                e1.record()
-                torch.cuda.synchronize()
-                return e0.elapsed_time(e1) / 1e3 / reps
+                def timed_t(fn, reps):
+                    for _ in range(3):
+                        fn()
+                    torch.cuda.synchronize()
+                    e0.record()
+                    for _ in range(reps):
+                        fn()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    return e0.elapsed_time(e1) / 1e3 / reps
 
-            ta = timed_t(lambda: mt.apply(xt, yt), 20)
-            t32 = timed_t(lambda: mt.apply(x32, y32), 20)
-            r = {"mesh": f"{args.n_tet}^3 boxes x 6 tetrahedra, jitter 0.1h", "cells": pt.n_cells,
-                 "free_dof": pt.n_free, "colours": mt.info["n_colours"], "ms_apply": 1e3 * ta,
-                 "gdofs_apply": pt.n_free / ta / 1e9, "ms_apply_f32": 1e3 * t32,
-                 "fp64_tflops": flops_el * pt.n_cells / ta / 1e12,
-                 "fp64_frac": flops_el * pt.n_cells / ta / 1e12 / 1.20, "fp64_peak_note": "of measured 1.20 TFLOP/s"}
-            if not args.no_csr:
-                At = mt.assemble_csr()
-                ts = timed_t(lambda: At.spmv(xt, yt), 20)
-                r.update({"ms_csr": 1e3 * ts, "gdofs_csr": pt.n_free / ts / 1e9, "nnz": At.info["nnz"],
-                          "mf_over_csr": ts / ta})
-                if phys == "laplace" and not args.no_cg:
-                    bt = torch.from_numpy(pt.b()).cuda()
-                    _, im = mt.cg(bt, timeout_s=args.cg_timeout)
-                    _, ic = mt.cg(bt, csr=At, timeout_s=args.cg_timeout)
-                    r["cg"] = {"iters": im.iters, "seconds_matfree": im.seconds, "seconds_csr": ic.seconds,
-                               "status": [im.status, ic.status]}
-                At.close()
-                del At
-            tet[phys] = r
-            mt.close()
-            del xt, yt, x32, y32
-            torch.cuda.empty_cache()
-        extras["tetrahedra"] = tet
+                reps = 20 if key == "tetrahedra" else 5
+                ta = timed_t(lambda: mt.apply(xt, yt), reps)
+                t32 = timed_t(lambda: mt.apply(x32, y32), reps)
+                tf = flops[phys] * pt.n_cells / ta / 1e12
+                r = {"mesh": f"{nb}^3 boxes, {what}, jitter 0.1h", "cells": pt.n_cells, "free_dof": pt.n_free,
+                     "colours": mt.info["n_colours"], "ms_apply": 1e3 * ta, "gdofs_apply": pt.n_free / ta / 1e9,
+                     "ms_apply_f32": 1e3 * t32, "fp64_tflops": tf, "fp64_frac": tf / 1.20,
+                     "fp64_peak_note": "of measured 1.20 TFLOP/s"}
+                if not args.no_csr:
+                    At = mt.assemble_csr()
+                    ts = timed_t(lambda: At.spmv(xt, yt), reps)
+                    r.update({"ms_csr": 1e3 * ts, "gdofs_csr": pt.n_free / ts / 1e9, "nnz": At.info["nnz"],
+                              "mf_over_csr": ts / ta})
+                    if phys == "laplace" and not args.no_cg:
+                        bt = torch.from_numpy(pt.b()).cuda()
+                        _, im = mt.cg(bt, timeout_s=args.cg_timeout, ok=CG_OK)
+                        _, ic = mt.cg(bt, csr=At, timeout_s=args.cg_timeout, ok=CG_OK)
+                        r["cg"] = {"iters": im.iters, "seconds_matfree": im.seconds, "seconds_csr": ic.seconds,
+                                   "status": [im.status, ic.status]}
+                    At.close()
+                    del At
+                res[phys] = r
+                mt.close()
+                del xt, yt, x32, y32
+                torch.cuda.empty_cache()
+            extras[key] = res
 
     # ---- batched persistent CG: 64 independent Laplace problems, n ~ log-uniform [8, 96]
     if not args.no_batch:

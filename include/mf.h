@@ -83,14 +83,18 @@ mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells, const dou
  *            vertices 1..3 follow xi, eta, zeta of the reference tetrahedron; the vertices must be
  *            positively oriented, det[x1 - x0, x2 - x0, x3 - x0] > 0.  The element integrals of
  *            Eqs. 1-3 have constant integrands and are evaluated exactly (one point, weight 1/6).
+ *            MF_ELEM_HEX27: the triquadratic hexahedron (Q2), the higher-order element of Sec. 7.
+ *            cells int32[E][27]; node a = i + 3j + 9k (i, j, k in {0, 1, 2}) at reference
+ *            coordinates (i - 1, j - 1, k - 1); 3x3x3 Gauss quadrature; det J must be positive at
+ *            the 27 Gauss points and the 8 vertices.
  *   Other arguments as mf_setup_mesh (cells is required).
- * Tetrahedral meshes run the reference kernel (one thread per element, colour-by-colour scatter,
- * FP64 or FP32) for every apply, the multi-RHS apply, CSR assembly, the operator diagonal and CG;
- * MF_VARIANT_GENERAL / MF_VARIANT_PARTIAL, the batched solver and the learned preconditioner
- * return MF_ERR_UNSUPPORTED or MF_ERR_ARG for them.  Errors as mf_setup_mesh (MF_ERR_MESH for a
- * tetrahedron with det <= 0).
+ * Tetrahedral and Q2 meshes run the reference kernel (one thread per element, colour-by-colour
+ * scatter, FP64 or FP32) for every apply, the multi-RHS apply, CSR assembly, the operator diagonal
+ * and CG; MF_VARIANT_GENERAL / MF_VARIANT_PARTIAL, the batched solver and the learned
+ * preconditioner return MF_ERR_UNSUPPORTED or MF_ERR_ARG for them.  Errors as mf_setup_mesh
+ * (MF_ERR_MESH for an element with det <= 0).
  */
-enum { MF_ELEM_HEX8 = 0, MF_ELEM_TET4 = 1 };
+enum { MF_ELEM_HEX8 = 0, MF_ELEM_TET4 = 1, MF_ELEM_HEX27 = 2 };
 mf_status mf_setup_mesh_elem(int element, int physics, int64_t n_nodes, int64_t n_cells, const double *coords,
                              const int32_t *cells, const double *mat, const uint8_t *dirichlet, mf_stream stream,
                              mf_mesh **out);
@@ -101,7 +105,7 @@ mf_status mf_destroy_mesh(mf_mesh *mesh);
 /* Host outputs (any may be NULL): node, cell and DoF counts, free (unconstrained) DoFs, number of
  * element colours of the scatter, and flags (bit 0: structured, bit 1: every cell affine, bit 2:
  * tensor-product grid of axis-aligned cells, which enables the FP64-accurate tile kernels, bit 3:
- * partial-assembly data built, bit 4: tetrahedral mesh). */
+ * partial-assembly data built, bit 4: tetrahedral mesh, bit 5: Q2 mesh). */
 mf_status mf_mesh_query(const mf_mesh *mesh, int64_t *n_nodes, int64_t *n_cells, int64_t *n_dof,
                         int64_t *n_free, int32_t *n_colours, int32_t *flags);
 

@@ -10,6 +10,7 @@
 // reproducible.
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
+#include "mf_q2.cuh"
 #include "mf_tet.cuh"
 
 namespace {
@@ -222,6 +223,39 @@ __global__ void __launch_bounds__(128) tet_apply_colour(MeshView m, const R *__r
   }
 }
 
+// Q2 hexahedra, one thread per element of a colour (mf_q2.cuh); `nrhs` right-hand sides per node,
+// [node][rhs][comp], one after the other (the geometry is recomputed for each).
+template <int PHYS, typename R>
+__global__ void __launch_bounds__(64) q2_apply_colour(MeshView m, const R *__restrict__ x, R *__restrict__ y, int nrhs,
+                                                      int64_t count, const int32_t *__restrict__ celems,
+                                                      const int *__restrict__ skip) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count || (skip && *skip)) return;
+  constexpr int ND = phys_ndpn(PHYS);
+  const int64_t e = celems[t];
+  const R *Xc = coords_of<R>(m);
+  const R *mat = mat_of<R>(m);
+  int64_t nodes[27];
+  R X[27][3];
+  bool dir[27];
+  for (int a = 0; a < 27; ++a) {
+    nodes[a] = m.cells[27 * e + a];
+    for (int i = 0; i < 3; ++i) X[a][i] = Xc[3 * nodes[a] + i];
+    dir[a] = m.dmask[nodes[a]] != 0;
+  }
+  const R c0 = phys_is_laplace(PHYS) ? mat[e] : mat[2 * e];
+  const R c1 = phys_is_laplace(PHYS) ? (R)0 : mat[2 * e + 1];
+  for (int r = 0; r < nrhs; ++r) {
+    R u[27][ND], v[27][ND];
+    for (int a = 0; a < 27; ++a)
+      for (int k = 0; k < ND; ++k) u[a][k] = dir[a] ? (R)0 : x[(nodes[a] * nrhs + r) * ND + k];
+    q2::element_apply<R, ND, PHYS == MF_ELASTICITY>(X, u, c0, c1, v);
+    for (int a = 0; a < 27; ++a)
+      if (!dir[a])
+        for (int k = 0; k < ND; ++k) y[(nodes[a] * nrhs + r) * ND + k] += v[a][k];
+  }
+}
+
 // Dirichlet rows: y_d = x_d.
 template <typename R>
 __global__ void dirichlet_rows(const int32_t *__restrict__ dn, int64_t n, int ndw, const R *__restrict__ x,
@@ -233,8 +267,10 @@ __global__ void dirichlet_rows(const int32_t *__restrict__ dn, int64_t n, int nd
   y[node * ndw + k] = x[node * ndw + k];
 }
 
+// Apply for the elements other than Q1 (P1 tetrahedra, Q2 hexahedra): colour by colour, then the
+// Dirichlet rows.
 template <typename R>
-mf_status tet_apply(const mf_mesh *m, const R *x, R *y, int nrhs, cudaStream_t s, const int *skip) {
+mf_status explicit_apply(const mf_mesh *m, const R *x, R *y, int nrhs, cudaStream_t s, const int *skip) {
   MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * nrhs * sizeof(R), s));
   const MeshView v = m->view();
   for (int c = 0; c < m->n_colours; ++c) {
@@ -242,7 +278,14 @@ mf_status tet_apply(const mf_mesh *m, const R *x, R *y, int nrhs, cudaStream_t s
     if (cnt == 0) continue;
     const int32_t *ce = m->colour_elems + m->colour_off[c];
     mf_count_launches(1);
-    if (m->physics == MF_LAPLACE)
+    if (m->npe == 27) {
+      if (m->physics == MF_LAPLACE)
+        q2_apply_colour<MF_LAPLACE, R><<<blocks_for(cnt, 64), 64, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
+      else if (m->physics == MF_VECTOR_LAPLACE)
+        q2_apply_colour<MF_VECTOR_LAPLACE, R><<<blocks_for(cnt, 64), 64, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
+      else
+        q2_apply_colour<MF_ELASTICITY, R><<<blocks_for(cnt, 64), 64, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
+    } else if (m->physics == MF_LAPLACE)
       tet_apply_colour<MF_LAPLACE, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
     else if (m->physics == MF_VECTOR_LAPLACE)
       tet_apply_colour<MF_VECTOR_LAPLACE, R><<<blocks_for(cnt, 128), 128, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
@@ -259,7 +302,7 @@ mf_status tet_apply(const mf_mesh *m, const R *x, R *y, int nrhs, cudaStream_t s
 
 template <typename R>
 mf_status apply_reference(const mf_mesh *m, const R *x, R *y, cudaStream_t s, const int *skip) {
-  if (m->npe == 4) return tet_apply<R>(m, x, y, 1, s, skip);
+  if (m->npe != 8) return explicit_apply<R>(m, x, y, 1, s, skip);  // P1 tetrahedra, Q2 hexahedra
   MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * sizeof(R), s));
   const MeshView v = m->view();
   for (int c = 0; c < m->n_colours; ++c) {
@@ -297,7 +340,7 @@ mf_status apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s,
 
 mf_status apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s) {
   if (m->variant == MF_VARIANT_AUTO && m->tp) return tile_apply_multi_fp64(m, nrhs, x, y, s);
-  if (m->npe == 4) return tet_apply<double>(m, x, y, nrhs, s, nullptr);
+  if (m->npe != 8) return explicit_apply<double>(m, x, y, nrhs, s, nullptr);
   MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * nrhs * sizeof(double), s));
   const MeshView v = m->view();
   for (int c = 0; c < m->n_colours; ++c) {

@@ -11,6 +11,7 @@
 
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
+#include "mf_q2.cuh"
 #include "mf_tet.cuh"
 
 namespace {
@@ -220,6 +221,77 @@ __global__ void tet_fill_colour(MeshView m, int64_t count, const int32_t *__rest
   }
 }
 
+// Q2 hexahedra: rows of node a of A^e (mf_q2.cuh), one thread per (element, node) of a colour.
+template <int PHYS>
+__global__ void __launch_bounds__(64) q2_fill_colour(MeshView m, int64_t count, const int32_t *__restrict__ celems,
+                                                     const int64_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ col, double *val) {
+  constexpr int ND = phys_ndpn(PHYS);
+  constexpr int EP = PHYS == MF_VECTOR_LAPLACE ? MF_LAPLACE : PHYS;
+  constexpr int NE = phys_ndpn(EP);
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= count * 27) return;
+  const int64_t e = celems[gid / 27];
+  const int a = (int)(gid % 27);
+  int64_t nodes[27];
+  for (int c = 0; c < 27; ++c) nodes[c] = m.cells[27 * e + c];
+  if (m.dmask[nodes[a]]) return;  // Dirichlet row: identity, set separately
+  double X[27][3];
+  for (int c = 0; c < 27; ++c)
+    for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
+  const double c0 = phys_is_laplace(PHYS) ? m.mat[e] : m.mat[2 * e];
+  const double c1 = phys_is_laplace(PHYS) ? 0.0 : m.mat[2 * e + 1];
+  double A[NE][27][3];
+  q2::element_rows<EP>(X, a, c0, c1, A);
+  for (int b = 0; b < 27; ++b) {
+    if (m.dmask[nodes[b]]) continue;  // Dirichlet column dropped
+    for (int k = 0; k < (PHYS == MF_VECTOR_LAPLACE ? 3 : 1); ++k) {
+      const int64_t row = nodes[a] * ND + k;
+      const int32_t target = (int32_t)(nodes[b] * ND + (PHYS == MF_VECTOR_LAPLACE ? k : 0));
+      int64_t lo = rowptr[row], hi = rowptr[row + 1];
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < target) lo = mid + 1; else hi = mid;
+      }
+      if (PHYS == MF_VECTOR_LAPLACE) {
+        val[lo] += A[0][b][0];
+      } else {
+        const int64_t rel = lo - rowptr[row];
+        for (int kk = 0; kk < ND; ++kk) {
+          const int64_t base = rowptr[nodes[a] * ND + kk] + rel;
+          for (int l = 0; l < ND; ++l) val[base + l] += NE == 1 ? A[0][b][0] : A[kk][b][l];
+        }
+      }
+    }
+  }
+}
+
+// diag(A) of Q2 hexahedra, one thread per element of a colour.
+template <int PHYS>
+__global__ void __launch_bounds__(64) q2_diag_colour(MeshView m, int64_t count, const int32_t *__restrict__ celems,
+                                                     double *diag) {
+  constexpr int ND = phys_ndpn(PHYS);
+  constexpr int EP = PHYS == MF_VECTOR_LAPLACE ? MF_LAPLACE : PHYS;
+  constexpr int NE = phys_ndpn(EP);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t e = celems[t];
+  int64_t nodes[27];
+  double X[27][3];
+  for (int c = 0; c < 27; ++c) {
+    nodes[c] = m.cells[27 * e + c];
+    for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
+  }
+  const double c0 = phys_is_laplace(PHYS) ? m.mat[e] : m.mat[2 * e];
+  const double c1 = phys_is_laplace(PHYS) ? 0.0 : m.mat[2 * e + 1];
+  double D[27][3];
+  q2::element_diag<EP>(X, c0, c1, D);
+  for (int a = 0; a < 27; ++a) {
+    if (m.dmask[nodes[a]]) continue;
+    for (int k = 0; k < ND; ++k) diag[nodes[a] * ND + k] += NE == 1 ? D[a][0] : D[a][k];
+  }
+}
+
 // diag(A) of P1 tetrahedra, one thread per element of a colour.
 template <int PHYS>
 __global__ void tet_diag_colour(MeshView m, int64_t count, const int32_t *__restrict__ celems, double *diag) {
@@ -323,6 +395,8 @@ void launch_fill(const mf_mesh *m, const MeshView &v, const mf_csr *A, cudaStrea
     const int32_t *ce = m->structured ? nullptr : m->colour_elems + m->colour_off[c];
     if (m->npe == 4)
       tet_fill_colour<PHYS><<<blocks_for(cnt * 4, 128), 128, 0, s>>>(v, cnt, ce, A->rowptr, A->col, A->val);
+    else if (m->npe == 27)
+      q2_fill_colour<PHYS><<<blocks_for(cnt * 27, 64), 64, 0, s>>>(v, cnt, ce, A->rowptr, A->col, A->val);
     else
       csr_fill_colour<PHYS><<<blocks_for(cnt * 8, 128), 128, 0, s>>>(v, c, cnt, ce, A->rowptr, A->col, A->val);
   }
@@ -335,6 +409,7 @@ void launch_diag(const mf_mesh *m, const MeshView &v, double *diag, cudaStream_t
     if (!cnt) continue;
     const int32_t *ce = m->structured ? nullptr : m->colour_elems + m->colour_off[c];
     if (m->npe == 4) tet_diag_colour<PHYS><<<blocks_for(cnt, 128), 128, 0, s>>>(v, cnt, ce, diag);
+    else if (m->npe == 27) q2_diag_colour<PHYS><<<blocks_for(cnt, 64), 64, 0, s>>>(v, cnt, ce, diag);
     else diag_colour<PHYS><<<blocks_for(cnt, 128), 128, 0, s>>>(v, c, cnt, ce, diag);
   }
 }

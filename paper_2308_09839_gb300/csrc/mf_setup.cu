@@ -10,6 +10,7 @@
 
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
+#include "mf_q2.cuh"
 #include "mf_tet.cuh"
 
 // ------------------------------------------------------------------------------------ errors ----
@@ -148,6 +149,40 @@ __global__ void validate_tet_kernel(MeshView m, int physics, ValidateOut *out) {
   }
 }
 
+// Q2 hexahedra: node ids in range, finite coordinates, det J > 0 at the 27 Gauss points and the 8
+// vertices, material admissible.
+__global__ void validate_q2_kernel(MeshView m, int physics, ValidateOut *out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_cells) return;
+  int flags = 0;
+  int64_t nodes[27];
+  for (int a = 0; a < 27; ++a) {
+    const int32_t n = m.cells[27 * e + a];
+    if (n < 0 || n >= m.n_nodes) flags |= BAD_NODE;
+    nodes[a] = n;
+  }
+  if (!(flags & BAD_NODE)) {
+    double X[27][3];
+    for (int a = 0; a < 27; ++a)
+      for (int i = 0; i < 3; ++i) {
+        X[a][i] = m.X[3 * nodes[a] + i];
+        if (!isfinite(X[a][i])) flags |= BAD_COORD;
+      }
+    if (!(flags & BAD_COORD) && !q2::dets_positive(X)) flags |= BAD_DET;
+  }
+  if (phys_is_laplace(physics)) {
+    double k = m.mat[e];
+    if (!(k > 0.0) || !isfinite(k)) flags |= BAD_MAT;
+  } else {
+    double E = m.mat[2 * e], nu = m.mat[2 * e + 1];
+    if (!(E > 0.0) || !isfinite(E) || !(nu > -1.0 && nu < 0.5)) flags |= BAD_MAT;
+  }
+  if (flags) {
+    atomicOr(&out->flags, flags);
+    atomicMin(&out->first_bad, (long long)e);
+  }
+}
+
 // (E, nu) -> (lam, mu) per cell, plus the FP32 copies.
 __global__ void material_kernel(const double *in, double *out, float *out32, int64_t n_cells, int physics) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -267,7 +302,7 @@ static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cel
   MF_ARG(physics == MF_LAPLACE || physics == MF_ELASTICITY || physics == MF_VECTOR_LAPLACE,
          "mf_setup_mesh: unknown physics %d", physics);
   MF_ARG(coords && mat, "mf_setup_mesh: coords and mat are required");
-  MF_ARG(npe == 8 || cells != nullptr, "mf_setup_mesh: tetrahedral meshes need an explicit connectivity");
+  MF_ARG(npe == 8 || cells != nullptr, "mf_setup_mesh: tetrahedral and Q2 meshes need an explicit connectivity");
   MF_ARG(n_nodes >= npe && n_cells >= 1, "mf_setup_mesh: need n_nodes >= %d and n_cells >= 1", npe);
   MF_ARG(n_nodes < (int64_t)INT32_MAX, "mf_setup_mesh: n_nodes must fit int32");
   if (!cells) {
@@ -330,6 +365,7 @@ static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cel
     MeshView v = m->view();
     v.mat = mat;
     if (npe == 4) validate_tet_kernel<<<blocks_for(n_cells), kThreads, 0, s>>>(v, physics, dv);
+    else if (npe == 27) validate_q2_kernel<<<blocks_for(n_cells, 64), 64, 0, s>>>(v, physics, dv);
     else validate_kernel<<<blocks_for(n_cells), kThreads, 0, s>>>(v, physics, dv);
     SETUP_CUDA(cudaGetLastError());
     SETUP_CUDA(cudaMemcpyAsync(&hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, s));
@@ -342,7 +378,7 @@ static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cel
       st = MF_ERR_MESH;
       goto fail;
     }
-    m->all_affine = hv.not_affine == 0;
+    m->all_affine = hv.not_affine == 0 && npe != 27;  // Q2 cells are not checked for affinity
     material_kernel<<<blocks_for(n_cells), kThreads, 0, s>>>(mat, m->mat, m->mat32, n_cells, physics);
     SETUP_CUDA(cudaGetLastError());
 
@@ -391,10 +427,11 @@ extern "C" mf_status mf_setup_mesh_elem(int element, int physics, int64_t n_node
                                         const double *coords, const int32_t *cells, const double *mat,
                                         const uint8_t *dirichlet, mf_stream stream, mf_mesh **out) {
   mf_clear_error();
-  MF_ARG(element == MF_ELEM_HEX8 || element == MF_ELEM_TET4, "mf_setup_mesh_elem: unknown element %d", element);
+  MF_ARG(element == MF_ELEM_HEX8 || element == MF_ELEM_TET4 || element == MF_ELEM_HEX27,
+         "mf_setup_mesh_elem: unknown element %d", element);
   MF_ARG(cells != nullptr, "mf_setup_mesh_elem: cells is required");
-  return setup_mesh(element == MF_ELEM_TET4 ? 4 : 8, physics, n_nodes, n_cells, coords, cells, 0, 0, 0, mat,
-                    dirichlet, stream, out);
+  const int npe = element == MF_ELEM_TET4 ? 4 : element == MF_ELEM_HEX27 ? 27 : 8;
+  return setup_mesh(npe, physics, n_nodes, n_cells, coords, cells, 0, 0, 0, mat, dirichlet, stream, out);
 }
 
 extern "C" mf_status mf_destroy_mesh(mf_mesh *mesh) {
@@ -415,7 +452,7 @@ extern "C" mf_status mf_mesh_query(const mf_mesh *m, int64_t *n_nodes, int64_t *
   if (n_colours) *n_colours = m->n_colours;
   if (flags)
     *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0) | (m->pa ? 8 : 0) |
-             (m->npe == 4 ? 16 : 0);
+             (m->npe == 4 ? 16 : 0) | (m->npe == 27 ? 32 : 0);
   return MF_OK;
 }
 

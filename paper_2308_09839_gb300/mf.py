@@ -24,8 +24,8 @@ MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_MESH, MF_ERR_OOM, MF_ERR_BREAKDOWN, MF_ERR_TIMEO
 MF_LAPLACE, MF_ELASTICITY, MF_VECTOR_LAPLACE = 0, 1, 2
 PHYSICS = {"laplace": MF_LAPLACE, "elasticity": MF_ELASTICITY, "vector_laplace": MF_VECTOR_LAPLACE}
 MF_VARIANT_AUTO, MF_VARIANT_REFERENCE, MF_VARIANT_GENERAL, MF_VARIANT_PARTIAL = 0, 1, 2, 3
-MF_ELEM_HEX8, MF_ELEM_TET4 = 0, 1
-ELEMENTS = {"hex8": MF_ELEM_HEX8, "tet4": MF_ELEM_TET4}
+MF_ELEM_HEX8, MF_ELEM_TET4, MF_ELEM_HEX27 = 0, 1, 2
+ELEMENTS = {"hex8": MF_ELEM_HEX8, "tet4": MF_ELEM_TET4, "hex27": MF_ELEM_HEX27}
 MF_CG_CLASSIC, MF_CG_PIPELINED = 0, 1
 MF_OP_MATFREE, MF_OP_CSR = 0, 1
 MF_PREC_FP64, MF_PREC_MIXED_IR = 0, 1
@@ -160,7 +160,7 @@ def mf_mesh_query(h) -> dict:
     check(lib.mf_mesh_query(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e), C.byref(f)), "mf_mesh_query")
     return dict(n_nodes=a.value, n_cells=b.value, n_dof=c.value, n_free=d.value, n_colours=e.value,
                 structured=bool(f.value & 1), all_affine=bool(f.value & 2), tensor_product=bool(f.value & 4),
-                partial_assembly=bool(f.value & 8), tetrahedral=bool(f.value & 16))
+                partial_assembly=bool(f.value & 8), tetrahedral=bool(f.value & 16), q2=bool(f.value & 32))
 
 
 def mf_set_apply_variant(h, variant: int) -> None:
