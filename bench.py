@@ -472,7 +472,7 @@ def main():
 
     # ---- elements beyond Q1 (Sec. 7): P1 tetrahedra (Kuhn split of an n^3 box, 6 per box) and Q2
     # hexahedra (27 nodes, 3x3x3 Gauss), jitter 0.1h: matrix-free apply (reference kernel, FP64 and
-    # FP32) against the CSR SpMV, and CG to 1e-8 both ways (Laplace).  The FP64 kernels are bound by
+    # FP32) against the CSR SpMV, and CG to 1e-8 both ways (tetrahedra, Laplace).  The FP64 kernels are bound by
     # the FP64 pipe: FP64 operations per element of the formulations in csrc/mf_tet.cuh (geometry
     # 47, Laplace 44 + 4 adds, elasticity 164 + 12 adds) and csrc/mf_q2.cuh (per Gauss point: J 648,
     # adj J 32, gradient 324 / 648, flux 40 / stress 150, scatter 324 / 648; times 27) against the
@@ -514,7 +514,7 @@ def main():
                     ts = timed_t(lambda: At.spmv(xt, yt), reps)
                     r.update({"ms_csr": 1e3 * ts, "gdofs_csr": pt.n_free / ts / 1e9, "nnz": At.info["nnz"],
                               "mf_over_csr": ts / ta})
-                    if phys == "laplace" and not args.no_cg:
+                    if phys == "laplace" and key == "tetrahedra" and not args.no_cg:
                         bt = torch.from_numpy(pt.b()).cuda()
                         _, im = mt.cg(bt, timeout_s=args.cg_timeout, ok=CG_OK)
                         _, ic = mt.cg(bt, csr=At, timeout_s=args.cg_timeout, ok=CG_OK)
