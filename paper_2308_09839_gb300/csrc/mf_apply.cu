@@ -256,6 +256,63 @@ __global__ void __launch_bounds__(64) q2_apply_colour(MeshView m, const R *__res
   }
 }
 
+// Q2 partial assembly: D_q = (w_q kappa / det J) adj J adj J^T at the 27 Gauss points, [q][6][e].
+__global__ void __launch_bounds__(64) q2pa_build(MeshView m, double *__restrict__ D) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_cells) return;
+  const int64_t E = m.n_cells;
+  double X[27][3];
+  for (int a = 0; a < 27; ++a) {
+    const int64_t n = m.cells[27 * e + a];
+    for (int i = 0; i < 3; ++i) X[a][i] = m.X[3 * n + i];
+  }
+  const double kappa = m.mat[e];
+  for (int q = 0; q < 27; ++q) {
+    double xi[3];
+    q2::point_q(q, xi);
+    q2::Tab<double> t;
+    q2::tables_at<double>(xi, t);
+    double J[3][3], C[3][3];
+    q2::jacobian(X, t, J);
+    const double det = q1::adjugate(J, C);
+    const double s = q2::weight_q(q) * kappa / det;
+    double d[6];
+    int k = 0;
+    for (int r = 0; r < 3; ++r)
+      for (int c = r; c < 3; ++c) d[k++] = s * (C[r][0] * C[c][0] + C[r][1] * C[c][1] + C[r][2] * C[c][2]);
+    for (int j = 0; j < 6; ++j) D[((int64_t)q * 6 + j) * E + e] = d[j];
+  }
+}
+
+// Q2 Laplace / vector Laplace apply from the partial assembly, one thread per element of a colour.
+template <int ND>
+__global__ void __launch_bounds__(64) q2pa_apply_colour(MeshView m, const double *__restrict__ D,
+                                                        const double *__restrict__ x, double *__restrict__ y, int nrhs,
+                                                        int64_t count, const int32_t *__restrict__ celems,
+                                                        const int *__restrict__ skip) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count || (skip && *skip)) return;
+  const int64_t e = celems[t];
+  const q2::SF tab = q2::sf_tables();
+  int32_t nodes[27];
+  bool dir[27];
+#pragma unroll
+  for (int a = 0; a < 27; ++a) {
+    nodes[a] = __ldg(m.cells + 27 * e + a);
+    dir[a] = m.dmask[nodes[a]] != 0;
+  }
+  for (int r = 0; r < nrhs; ++r)
+    for (int k = 0; k < ND; ++k) {
+      double u[27], v[27];
+#pragma unroll
+      for (int a = 0; a < 27; ++a) u[a] = dir[a] ? 0.0 : x[((int64_t)nodes[a] * nrhs + r) * ND + k];
+      q2::pa_laplace(tab, D + e, m.n_cells, u, v);
+#pragma unroll
+      for (int a = 0; a < 27; ++a)
+        if (!dir[a]) y[((int64_t)nodes[a] * nrhs + r) * ND + k] += v[a];
+    }
+}
+
 // Dirichlet rows: y_d = x_d.
 template <typename R>
 __global__ void dirichlet_rows(const int32_t *__restrict__ dn, int64_t n, int ndw, const R *__restrict__ x,
@@ -278,7 +335,14 @@ mf_status explicit_apply(const mf_mesh *m, const R *x, R *y, int nrhs, cudaStrea
     if (cnt == 0) continue;
     const int32_t *ce = m->colour_elems + m->colour_off[c];
     mf_count_launches(1);
-    if (m->npe == 27) {
+    if (m->npe == 27 && m->q2pa && m->variant != MF_VARIANT_REFERENCE && sizeof(R) == 8) {
+      const double *xd = reinterpret_cast<const double *>(x);
+      double *yd = reinterpret_cast<double *>(y);
+      if (m->physics == MF_LAPLACE)
+        q2pa_apply_colour<1><<<blocks_for(cnt, 64), 64, 0, s>>>(v, m->q2pa, xd, yd, nrhs, cnt, ce, skip);
+      else
+        q2pa_apply_colour<3><<<blocks_for(cnt, 64), 64, 0, s>>>(v, m->q2pa, xd, yd, nrhs, cnt, ce, skip);
+    } else if (m->npe == 27) {
       if (m->physics == MF_LAPLACE)
         q2_apply_colour<MF_LAPLACE, R><<<blocks_for(cnt, 64), 64, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
       else if (m->physics == MF_VECTOR_LAPLACE)
@@ -325,6 +389,27 @@ mf_status apply_reference(const mf_mesh *m, const R *x, R *y, cudaStream_t s, co
 }
 
 }  // namespace
+
+mf_status q2_pa_setup(mf_mesh *m, cudaStream_t s) {
+  if (m->q2pa) return MF_OK;
+  if (m->npe != 27 || !phys_is_laplace(m->physics)) {
+    mf_set_error("partial assembly of Q2 meshes is built for Laplace and vector Laplace");
+    return MF_ERR_UNSUPPORTED;
+  }
+  const size_t bytes = (size_t)m->n_cells * 27 * 6 * sizeof(double);
+  cudaError_t e = cudaMalloc(&m->q2pa, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    m->q2pa = nullptr;
+    mf_set_error("Q2 partial assembly: allocation of %zu bytes failed", bytes);
+    return MF_ERR_OOM;
+  }
+  mf_count_launches(1);
+  q2pa_build<<<blocks_for(m->n_cells, 64), 64, 0, s>>>(m->view(), m->q2pa);
+  MF_CUDA(cudaGetLastError());
+  MF_CUDA(cudaStreamSynchronize(s));
+  return MF_OK;
+}
 
 mf_status apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip) {
   if (m->variant == MF_VARIANT_AUTO && m->tp) return tile_apply_fp64(m, x, y, s, skip);

@@ -139,6 +139,9 @@ struct mf_mesh {
   // floats, [q][k][cell]; built when it fits the device (auto variant) or on request
   float2 *pa = nullptr;
   float *pa32 = nullptr;
+  // partial assembly of Q2 Laplace meshes: the flux matrix (6 values) per Gauss point, FP64,
+  // [q][k][cell]; used by the sum-factorised Q2 kernel
+  double *q2pa = nullptr;
 
   MeshView view() const {
     MeshView v;
@@ -179,6 +182,7 @@ mf_status tile_apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, dou
 // general structured kernels (mf_general.cu)
 mf_status gen_setup(mf_mesh *m, cudaStream_t s);
 mf_status pa_setup(mf_mesh *m, cudaStream_t s);
+mf_status q2_pa_setup(mf_mesh *m, cudaStream_t s);  // mf_apply.cu
 mf_status gen_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip);
 mf_status gen_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip);
 // diag(A) of the matrix-free operator (Jacobi), FP64, Dirichlet rows 1.

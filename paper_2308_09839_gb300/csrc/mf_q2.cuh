@@ -231,4 +231,80 @@ __device__ inline bool dets_positive(const double X[27][3]) {
   return ok;
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// Partial assembly with sum factorisation (Laplace and vector Laplace on Q2 meshes).  Per element and
+// Gauss point the symmetric flux matrix D_q = (w_q kappa / det J) adj(J) adj(J)^T (6 values) is
+// computed once in FP64 and stored ([q][6][element], element fastest).  The apply then needs no
+// geometry: with the 1D tables B_qi = L_i(x_q) and G_qi = L_i'(x_q), the reference gradient at all
+// 27 points is (G x B x B) u, (B x G x B) u, (B x B x G) u, formed by one-dimensional contractions
+// (8 passes of 27 x 3 multiply-adds instead of 27 x 27 x 3); the transposed contractions scatter
+// D_q g_q back to the nodes.  Arrays are indexed [z][y][x] = 9 z + 3 y + x for nodes and points.
+// ------------------------------------------------------------------------------------------------
+struct SF {
+  double B[3][3], G[3][3];  // [point][node]
+};
+
+__device__ __forceinline__ SF sf_tables() {
+  SF t;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const double s = gauss_point(q);
+    t.B[q][0] = 0.5 * s * (s - 1.0);
+    t.B[q][1] = 1.0 - s * s;
+    t.B[q][2] = 0.5 * s * (s + 1.0);
+    t.G[q][0] = s - 0.5;
+    t.G[q][1] = -2.0 * s;
+    t.G[q][2] = s + 0.5;
+  }
+  return t;
+}
+
+// out = M along axis AX (0 x, 1 y, 2 z) applied to in: out[.., q, ..] = sum_i M[q][i] in[.., i, ..].
+template <int AX, bool TRANS, bool ACC>
+__device__ __forceinline__ void contract(const double M[3][3], const double in[27], double out[27]) {
+  constexpr int st = AX == 0 ? 1 : AX == 1 ? 3 : 9;
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    const int q = (o / st) % 3, base = o - q * st;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s += (TRANS ? M[i][q] : M[q][i]) * in[base + i * st];
+    out[o] = ACC ? out[o] + s : s;
+  }
+}
+
+// v = A^e u for one component with the partially assembled D (pointer to D[0][0][e], stride E).
+__device__ __forceinline__ void pa_laplace(const SF &t, const double *__restrict__ D, int64_t E, const double u[27],
+                                           double v[27]) {
+  double a[27], b[27], gx[27], gy[27], gz[27];
+  contract<2, false, false>(t.B, u, a);   // Bz u
+  contract<1, false, false>(t.B, a, b);   // By Bz u
+  contract<0, false, false>(t.G, b, gx);  // Gx By Bz u
+  contract<1, false, false>(t.G, a, b);   // Gy Bz u
+  contract<0, false, false>(t.B, b, gy);  // Bx Gy Bz u
+  contract<2, false, false>(t.G, u, a);   // Gz u
+  contract<1, false, false>(t.B, a, b);   // By Gz u
+  contract<0, false, false>(t.B, b, gz);  // Bx By Gz u
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const double *d = D + (int64_t)q * 6 * E;
+    const double d00 = __ldg(d), d01 = __ldg(d + E), d02 = __ldg(d + 2 * E);
+    const double d11 = __ldg(d + 3 * E), d12 = __ldg(d + 4 * E), d22 = __ldg(d + 5 * E);
+    const double x = gx[q], y = gy[q], z = gz[q];
+    gx[q] = d00 * x + d01 * y + d02 * z;
+    gy[q] = d01 * x + d11 * y + d12 * z;
+    gz[q] = d02 * x + d12 * y + d22 * z;
+  }
+  // v = Bz^T (By^T Gx^T fx + Gy^T Bx^T fy) + Gz^T By^T Bx^T fz
+  contract<0, true, false>(t.G, gx, a);   // Gx^T fx
+  contract<1, true, false>(t.B, a, b);    // By^T Gx^T fx
+  contract<0, true, false>(t.B, gy, a);   // Bx^T fy
+  contract<1, true, true>(t.G, a, b);     // + Gy^T Bx^T fy
+  contract<2, true, false>(t.B, b, v);    // Bz^T (...)
+  contract<0, true, false>(t.B, gz, a);   // Bx^T fz
+  contract<1, true, false>(t.B, a, b);    // By^T Bx^T fz
+  contract<2, true, true>(t.G, b, v);     // + Gz^T By^T Bx^T fz
+}
+
 }  // namespace q2

@@ -237,6 +237,7 @@ static void free_mesh(mf_mesh *m) {
   cudaFree(m->gen_delta);
   cudaFree(m->pa);
   cudaFree(m->pa32);
+  cudaFree(m->q2pa);
   delete m;
 }
 
@@ -400,6 +401,13 @@ static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cel
       SETUP_CUDA(cudaMemcpyAsync(m->h_cells.data(), cells, npe * n_cells * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       SETUP_CUDA(cudaStreamSynchronize(s));
       SETUP_TRY(colour_elements(m, s));
+      if (npe == 27 && phys_is_laplace(physics)) {
+        // the auto variant uses the Q2 partial assembly when it takes at most a quarter of the
+        // free memory
+        size_t free_b = 0, total_b = 0;
+        SETUP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        if ((double)n_cells * 27 * 6 * sizeof(double) <= 0.25 * (double)free_b) SETUP_TRY(q2_pa_setup(m, s));
+      }
     } else {
       m->n_colours = 8;  // parity colouring of the box
       SETUP_TRY(tile_setup(m, s));
@@ -451,7 +459,7 @@ extern "C" mf_status mf_mesh_query(const mf_mesh *m, int64_t *n_nodes, int64_t *
   if (n_free) *n_free = m->n_free;
   if (n_colours) *n_colours = m->n_colours;
   if (flags)
-    *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0) | (m->pa ? 8 : 0) |
+    *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0) | (m->pa || m->q2pa ? 8 : 0) |
              (m->npe == 4 ? 16 : 0) | (m->npe == 27 ? 32 : 0);
   return MF_OK;
 }
@@ -461,6 +469,11 @@ extern "C" mf_status mf_set_apply_variant(mf_mesh *m, int variant) {
   MF_ARG(variant == MF_VARIANT_AUTO || variant == MF_VARIANT_REFERENCE || variant == MF_VARIANT_GENERAL ||
              variant == MF_VARIANT_PARTIAL,
          "mf_set_apply_variant: unknown variant %d", variant);
+  if (variant == MF_VARIANT_PARTIAL && m->npe == 27) {  // Q2 Laplace: sum-factorised partial assembly
+    MF_TRY(q2_pa_setup(m, 0));
+    m->variant = variant;
+    return MF_OK;
+  }
   if (variant == MF_VARIANT_GENERAL || variant == MF_VARIANT_PARTIAL) {
     if (!m->gen) {
       mf_set_error("mf_set_apply_variant: the general and partial-assembly variants need a structured mesh that is "

@@ -42,10 +42,15 @@ MESHES = {
 
 
 @pytest.mark.parametrize("name", sorted(MESHES))
-def test_q2_apply_matches_oracle(name):
+@pytest.mark.parametrize("variant", [mf.MF_VARIANT_AUTO, mf.MF_VARIANT_REFERENCE])
+def test_q2_apply_matches_oracle(name, variant):
+    """AUTO is the sum-factorised partial-assembly kernel on Laplace and vector Laplace meshes and
+    the reference kernel on elasticity meshes."""
     p = MESHES[name]()
     mesh = mf.Mesh.from_problem(p)
     assert mesh.info["q2"] and not mesh.info["structured"]
+    assert mesh.info["partial_assembly"] == (p.physics != "elasticity")
+    mesh.set_variant(variant)
     for seed in (0, 1):
         x = p.x(seed)
         y = mesh.apply(gpu(x))
@@ -57,9 +62,25 @@ def test_q2_apply_matches_oracle(name):
     assert rel2(y32.double().cpu().numpy(), ref) < 2e-5
 
 
+def test_q2_partial_assembly_larger_mesh():
+    """10 x 9 x 11 curved Q2 Laplace mesh: the sum-factorised kernel against the oracle, and against
+    the reference kernel of the same library."""
+    p = inputs.q2_box("laplace", 10, ny=9, nz=11, jitter=0.1, curve=0.05, seed=90, sigma=1.0)
+    mesh = mf.Mesh.from_problem(p)
+    x = p.x(3)
+    y_pa = mesh.apply(gpu(x))
+    mesh.set_variant(mf.MF_VARIANT_REFERENCE)
+    y_ref = mesh.apply(gpu(x))
+    torch.cuda.synchronize()
+    ref = oracle_apply(p, x)
+    assert rel2(y_pa.cpu().numpy(), ref) <= TOL64
+    assert rel2(y_pa.cpu().numpy(), y_ref.cpu().numpy()) <= TOL64
+
+
 @pytest.mark.parametrize("nrhs", [1, 4])
-def test_q2_multi_rhs(nrhs):
-    p = inputs.q2_box("elasticity", 2, ny=2, nz=3, jitter=0.1, seed=86)
+@pytest.mark.parametrize("physics", ["elasticity", "vector_laplace"])
+def test_q2_multi_rhs(nrhs, physics):
+    p = inputs.q2_box(physics, 2, ny=2, nz=3, jitter=0.1, seed=86)
     mesh = mf.Mesh.from_problem(p)
     xs = [p.x(seed=s) for s in range(nrhs)]
     X = np.stack([x.reshape(-1, 3) for x in xs], axis=1).reshape(-1)
@@ -125,6 +146,11 @@ def test_q2_setup_checks():
         mf.Mesh("laplace", coords, mat, dirichlet, gpu(bad), element="hex27")
     assert "det" in mf.mf_last_error()
     mesh = mf.Mesh.from_problem(p)
-    for v in (mf.MF_VARIANT_GENERAL, mf.MF_VARIANT_PARTIAL):
-        with pytest.raises(mf.MfError):
-            mesh.set_variant(v)
+    with pytest.raises(mf.MfError):
+        mesh.set_variant(mf.MF_VARIANT_GENERAL)
+    mesh.set_variant(mf.MF_VARIANT_PARTIAL)  # Laplace: the sum-factorised partial assembly
+    pe = inputs.q2_box("elasticity", 1, seed=89)
+    me = mf.Mesh.from_problem(pe)
+    assert not me.info["partial_assembly"]
+    with pytest.raises(mf.MfError):
+        me.set_variant(mf.MF_VARIANT_PARTIAL)
