@@ -8,6 +8,8 @@
 // (2x2x2 parity classes on a structured box, a greedy colouring otherwise), one launch per colour,
 // so every addition is a plain read-modify-write in a fixed order: no atomics, bitwise
 // reproducible.
+#include <vector>
+
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
 #include "mf_q2.cuh"
@@ -284,15 +286,17 @@ __global__ void __launch_bounds__(64) q2pa_build(MeshView m, double *__restrict_
   }
 }
 
-// Q2 Laplace / vector Laplace apply from the partial assembly, one thread per element of a colour.
+// Q2 Laplace / vector Laplace apply from the partial assembly in two launches, without colours: every
+// element at once writes its 27 x ND results to its own slots of `buf` ([element][node][comp]); then
+// every DoF sums its slots in a fixed order (the node's slot list, sorted by element) and the
+// Dirichlet rows take y_d = x_d.  Deterministic, and all elements run in one launch (a colour of a
+// Q2 box mesh holds only 1/8 of them).
 template <int ND>
-__global__ void __launch_bounds__(64) q2pa_apply_colour(MeshView m, const double *__restrict__ D,
-                                                        const double *__restrict__ x, double *__restrict__ y, int nrhs,
-                                                        int64_t count, const int32_t *__restrict__ celems,
-                                                        const int *__restrict__ skip) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= count || (skip && *skip)) return;
-  const int64_t e = celems[t];
+__global__ void __launch_bounds__(64) q2pa_elements(MeshView m, const double *__restrict__ D,
+                                                    const double *__restrict__ x, int nrhs, int r,
+                                                    double *__restrict__ buf, const int *__restrict__ skip) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_cells || (skip && *skip)) return;
   const q2::SF tab = q2::sf_tables();
   int32_t nodes[27];
   bool dir[27];
@@ -301,16 +305,33 @@ __global__ void __launch_bounds__(64) q2pa_apply_colour(MeshView m, const double
     nodes[a] = __ldg(m.cells + 27 * e + a);
     dir[a] = m.dmask[nodes[a]] != 0;
   }
-  for (int r = 0; r < nrhs; ++r)
-    for (int k = 0; k < ND; ++k) {
-      double u[27], v[27];
+  for (int k = 0; k < ND; ++k) {
+    double u[27], v[27];
 #pragma unroll
-      for (int a = 0; a < 27; ++a) u[a] = dir[a] ? 0.0 : x[((int64_t)nodes[a] * nrhs + r) * ND + k];
-      q2::pa_laplace(tab, D + e, m.n_cells, u, v);
+    for (int a = 0; a < 27; ++a) u[a] = dir[a] ? 0.0 : x[((int64_t)nodes[a] * nrhs + r) * ND + k];
+    q2::pa_laplace(tab, D + e, m.n_cells, u, v);
 #pragma unroll
-      for (int a = 0; a < 27; ++a)
-        if (!dir[a]) y[((int64_t)nodes[a] * nrhs + r) * ND + k] += v[a];
-    }
+    for (int a = 0; a < 27; ++a) buf[(e * 27 + a) * ND + k] = v[a];
+  }
+}
+
+template <int ND>
+__global__ void q2pa_gather(int64_t n_nodes, const int64_t *__restrict__ off, const int32_t *__restrict__ slots,
+                            const uint8_t *__restrict__ dmask, const double *__restrict__ buf,
+                            const double *__restrict__ x, double *__restrict__ y, int nrhs, int r,
+                            const int *__restrict__ skip) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_nodes * ND || (skip && *skip)) return;
+  const int64_t n = i / ND;
+  const int k = (int)(i % ND);
+  const int64_t o = (n * nrhs + r) * ND + k;
+  if (dmask[n]) {
+    y[o] = x[o];
+    return;
+  }
+  double s = 0.0;
+  for (int64_t t = off[n]; t < off[n + 1]; ++t) s += buf[(int64_t)slots[t] * ND + k];
+  y[o] = s;
 }
 
 // Dirichlet rows: y_d = x_d.
@@ -326,8 +347,32 @@ __global__ void dirichlet_rows(const int32_t *__restrict__ dn, int64_t n, int nd
 
 // Apply for the elements other than Q1 (P1 tetrahedra, Q2 hexahedra): colour by colour, then the
 // Dirichlet rows.
+// Q2 Laplace / vector Laplace from the partial assembly: element launch and node gather per
+// right-hand side.
+mf_status q2pa_apply(const mf_mesh *m, const double *x, double *y, int nrhs, cudaStream_t s, const int *skip) {
+  const MeshView v = m->view();
+  const int nd = m->ndpn;
+  for (int r = 0; r < nrhs; ++r) {
+    mf_count_launches(2);
+    if (nd == 1) {
+      q2pa_elements<1><<<blocks_for(m->n_cells, 64), 64, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
+      q2pa_gather<1><<<blocks_for(m->n_nodes), kThreads, 0, s>>>(m->n_nodes, m->q2off, m->q2slots, m->dmask,
+                                                                   m->q2buf, x, y, nrhs, r, skip);
+    } else {
+      q2pa_elements<3><<<blocks_for(m->n_cells, 64), 64, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
+      q2pa_gather<3><<<blocks_for(m->n_nodes * 3), kThreads, 0, s>>>(m->n_nodes, m->q2off, m->q2slots, m->dmask,
+                                                                       m->q2buf, x, y, nrhs, r, skip);
+    }
+  }
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
+}
+
 template <typename R>
 mf_status explicit_apply(const mf_mesh *m, const R *x, R *y, int nrhs, cudaStream_t s, const int *skip) {
+  if constexpr (sizeof(R) == 8) {
+    if (m->npe == 27 && m->q2pa && m->variant != MF_VARIANT_REFERENCE) return q2pa_apply(m, x, y, nrhs, s, skip);
+  }
   MF_CUDA(cudaMemsetAsync(y, 0, m->n_dof * nrhs * sizeof(R), s));
   const MeshView v = m->view();
   for (int c = 0; c < m->n_colours; ++c) {
@@ -335,14 +380,7 @@ mf_status explicit_apply(const mf_mesh *m, const R *x, R *y, int nrhs, cudaStrea
     if (cnt == 0) continue;
     const int32_t *ce = m->colour_elems + m->colour_off[c];
     mf_count_launches(1);
-    if (m->npe == 27 && m->q2pa && m->variant != MF_VARIANT_REFERENCE && sizeof(R) == 8) {
-      const double *xd = reinterpret_cast<const double *>(x);
-      double *yd = reinterpret_cast<double *>(y);
-      if (m->physics == MF_LAPLACE)
-        q2pa_apply_colour<1><<<blocks_for(cnt, 64), 64, 0, s>>>(v, m->q2pa, xd, yd, nrhs, cnt, ce, skip);
-      else
-        q2pa_apply_colour<3><<<blocks_for(cnt, 64), 64, 0, s>>>(v, m->q2pa, xd, yd, nrhs, cnt, ce, skip);
-    } else if (m->npe == 27) {
+    if (m->npe == 27) {
       if (m->physics == MF_LAPLACE)
         q2_apply_colour<MF_LAPLACE, R><<<blocks_for(cnt, 64), 64, 0, s>>>(v, x, y, nrhs, cnt, ce, skip);
       else if (m->physics == MF_VECTOR_LAPLACE)
@@ -404,6 +442,26 @@ mf_status q2_pa_setup(mf_mesh *m, cudaStream_t s) {
     mf_set_error("Q2 partial assembly: allocation of %zu bytes failed", bytes);
     return MF_ERR_OOM;
   }
+  // node -> slot lists (slot = 27 e + a), each sorted by element: the order of the gather's sum
+  const int64_t N = m->n_nodes, E = m->n_cells;
+  std::vector<int64_t> off(N + 1, 0);
+  for (int64_t t = 0; t < 27 * E; ++t) off[m->h_cells[t] + 1]++;
+  for (int64_t n = 0; n < N; ++n) off[n + 1] += off[n];
+  std::vector<int64_t> pos(off.begin(), off.end() - 1);
+  std::vector<int32_t> slots(27 * E);
+  for (int64_t t = 0; t < 27 * E; ++t) slots[pos[m->h_cells[t]]++] = (int32_t)t;
+  const size_t buf_bytes = (size_t)E * 27 * m->ndpn * sizeof(double);
+  if ((e = cudaMalloc(&m->q2off, (N + 1) * sizeof(int64_t))) != cudaSuccess ||
+      (e = cudaMalloc(&m->q2slots, 27 * E * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&m->q2buf, buf_bytes)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(m->q2pa); cudaFree(m->q2off); cudaFree(m->q2slots); cudaFree(m->q2buf);
+    m->q2pa = nullptr; m->q2off = nullptr; m->q2slots = nullptr; m->q2buf = nullptr;
+    mf_set_error("Q2 partial assembly: allocation failed");
+    return MF_ERR_OOM;
+  }
+  MF_CUDA(cudaMemcpyAsync(m->q2off, off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  MF_CUDA(cudaMemcpyAsync(m->q2slots, slots.data(), 27 * E * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   mf_count_launches(1);
   q2pa_build<<<blocks_for(m->n_cells, 64), 64, 0, s>>>(m->view(), m->q2pa);
   MF_CUDA(cudaGetLastError());

@@ -142,6 +142,9 @@ struct mf_mesh {
   // partial assembly of Q2 Laplace meshes: the flux matrix (6 values) per Gauss point, FP64,
   // [q][k][cell]; used by the sum-factorised Q2 kernel
   double *q2pa = nullptr;
+  int64_t *q2off = nullptr;   // node -> slot lists of the element outputs (CSR form, N + 1)
+  int32_t *q2slots = nullptr; // slots 27 e + a, per node sorted by element
+  double *q2buf = nullptr;    // element outputs [E][27][ndpn]
 
   MeshView view() const {
     MeshView v;

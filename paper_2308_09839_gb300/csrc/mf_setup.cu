@@ -238,6 +238,9 @@ static void free_mesh(mf_mesh *m) {
   cudaFree(m->pa);
   cudaFree(m->pa32);
   cudaFree(m->q2pa);
+  cudaFree(m->q2off);
+  cudaFree(m->q2slots);
+  cudaFree(m->q2buf);
   delete m;
 }
 
