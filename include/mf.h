@@ -6,7 +6,8 @@
  * and isotropic linear-elasticity operators on trilinear hexahedra (Q1) with 2x2x2 Gauss
  * quadrature (Sec. 2, Eqs. 1, 3, 4, 6), matrix-free (Sec. 3, Eqs. 7 and 9, Algorithm 1) or through
  * an assembled CSR matrix (Sec. 3 and Table 1), and solves A x = b by conjugate gradient (the
- * operations of Table 4).
+ * operations of Table 4).  The same operators on linear tetrahedra (P1) and triquadratic
+ * hexahedra (Q2), the elements Sec. 7 names as future work, are set up by mf_setup_mesh_elem.
  *
  * Conventions shared by every call:
  *   - All array arguments are DEVICE pointers on the current CUDA device, owned by the caller,
