@@ -471,19 +471,16 @@ def main():
         torch.cuda.empty_cache()
 
     # ---- elements beyond Q1 (Sec. 7): P1 tetrahedra (Kuhn split of an n^3 box, 6 per box) and Q2
-    # hexahedra (27 nodes, 3x3x3 Gauss), jitter 0.1h: matrix-free apply (reference kernel, FP64 and
-    # FP32) against the CSR SpMV, and CG to 1e-8 both ways (tetrahedra, Laplace).  The FP64 kernels are bound by
-    # the FP64 pipe: FP64 operations per element of the formulations in csrc/mf_tet.cuh (geometry
-    # 47, Laplace 44 + 4 adds, elasticity 164 + 12 adds) and csrc/mf_q2.cuh (per Gauss point: J 648,
-    # adj J 32, gradient 324 / 648, flux 40 / stress 150, scatter 324 / 648; times 27) against the
-    # measured 1.20 TFLOP/s of FP64 FMA.
-    # Q2 Laplace from the partial assembly, per element: 16 one-dimensional contractions of 27 x 3
-    # multiply-adds and the 27 flux products of 9 (D read from memory): 2 x (1296 + 243) operations.
-    Q2_PA_FLOPS = 3078
+    # hexahedra (27 nodes, 3x3x3 Gauss), jitter 0.1h: matrix-free apply (FP64 and FP32) against the
+    # CSR SpMV, and CG to 1e-8 both ways (tetrahedra, Laplace).  The FP64 kernels are bound by the
+    # FP64 pipe: FP64 operations per element of their formulations (bytes_model.tet_apply_flops,
+    # q2_apply_flops) against the measured 1.20 TFLOP/s of FP64 FMA.
+    Q2_PA_FLOPS = bm.q2_apply_flops("laplace", partial_assembly=True)["total"]
     if not args.no_tet:
-        cases = (("tetrahedra", inputs.tet_box, args.n_tet, {"laplace": 95, "elasticity": 211}, "x 6 tetrahedra"),
-                 ("q2_hexahedra", inputs.q2_box, args.n_q2, {"laplace": 36936, "elasticity": 57402},
-                  "Q2 hexahedra"))
+        tf_ = {ph: bm.tet_apply_flops(ph)["total"] for ph in ("laplace", "elasticity")}
+        qf_ = {ph: bm.q2_apply_flops(ph)["total"] for ph in ("laplace", "elasticity")}
+        cases = (("tetrahedra", inputs.tet_box, args.n_tet, tf_, "x 6 tetrahedra"),
+                 ("q2_hexahedra", inputs.q2_box, args.n_q2, qf_, "Q2 hexahedra"))
         for key, make, nb, flops, what in cases:
             res = {}
             for phys in ("laplace", "elasticity"):

@@ -115,3 +115,42 @@ def kernel_apply_ops(physics: str) -> dict:
 def fp32_lane_peak(sms: int = 152, lanes: int = 128, clock_hz: float = 2.07e9) -> float:
     """FP32-pipe lane operations per second: SMs x FP32 lanes per SM x maximum SM clock."""
     return sms * lanes * clock_hz
+
+
+# ------------------------------------------------ FP64 arithmetic of the P1 and Q2 kernels ----
+
+def tet_apply_flops(physics: str) -> dict:
+    """FP64 operations per P1 tetrahedron of the reference apply (csrc/mf_tet.cuh), a multiply-add
+    counted as 2.  Geometry: 9 edge differences, 3 cross products (6 mul + 3 add), n_0 (6 adds),
+    D (3 mul + 2 add).  Laplace: 3 differences u_k - u_0, t (3 x (3 mul + 2 add)), c = kappa / (6 D)
+    (2), v (4 x (3 mul + 2 add + 1 mul)), 4 scatter adds.  Elasticity: 9 differences, H (9 x (3 mul
+    + 2 add)), tr (2), S (9 x 2 + 4), c (2), v (12 x 6), 12 scatter adds."""
+    geometry = 9 + 3 * 9 + 6 + 5
+    if physics == "elasticity":
+        parts = {"geometry": geometry, "gradient": 9 + 9 * 5, "stress": 2 + 9 * 2 + 4 + 2, "scatter": 12 * 6 + 12}
+    else:
+        parts = {"geometry": geometry, "gradient": 3 + 3 * 5, "flux": 2, "scatter": 4 * 6 + 4}
+    return dict(parts=parts, total=sum(parts.values()))
+
+
+def q2_apply_flops(physics: str, partial_assembly: bool = False) -> dict:
+    """FP64 operations per Q2 hexahedron (27 nodes, 27 Gauss points; csrc/mf_q2.cuh), a
+    multiply-add counted as 2.
+
+    Reference kernel, per Gauss point: reference gradients of the 27 nodes from the 1D tables (6
+    mul each) and J (27 x 9 multiply-adds) = 648; adj J and det J 32; the gradient of u (27 x 3
+    multiply-adds per component, 324 or 648 with the gradients reused); the flux (Laplace, 40) or
+    the stress (elasticity, 150); the scatter (27 x 3 multiply-adds per component, 324 or 648).
+    Partial assembly with sum factorisation (Laplace): 16 one-dimensional contractions of 27 x 3
+    multiply-adds and 27 flux products D_q g_q of 9 multiply-adds."""
+    if partial_assembly:
+        if physics == "elasticity":
+            raise ValueError("the Q2 partial assembly is built for Laplace and vector Laplace")
+        parts = {"contractions": 2 * 16 * 81, "flux": 2 * 27 * 9}
+    elif physics == "elasticity":
+        parts = {"jacobian": 27 * 648, "adjugate": 27 * 32, "gradient": 27 * 648, "stress": 27 * 150,
+                 "scatter": 27 * 648}
+    else:
+        parts = {"jacobian": 27 * 648, "adjugate": 27 * 32, "gradient": 27 * 324, "flux": 27 * 40,
+                 "scatter": 27 * 324}
+    return dict(parts=parts, total=sum(parts.values()))

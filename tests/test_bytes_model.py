@@ -79,3 +79,18 @@ def test_kernel_bytes_tensor_product():
     n = 256
     b = bm.kernel_apply_bytes("laplace", n ** 3, (n + 1) ** 3, structured=True, tensor_product=True)
     assert b == (n + 1) ** 3 * (1 + 16) + n ** 3 * 8
+
+
+def test_p1_q2_operation_counts():
+    """The FP64 operation counts the bench divides by for the P1 and Q2 kernels: totals of their
+    parts, and the partial assembly's count below the reference kernel's by the expected factor."""
+    from paper_2308_09839_gb300 import bytes_model as bm
+    assert bm.tet_apply_flops("laplace")["total"] == 95
+    assert bm.tet_apply_flops("elasticity")["total"] == 211
+    ref = bm.q2_apply_flops("laplace")["total"]
+    pa = bm.q2_apply_flops("laplace", partial_assembly=True)["total"]
+    assert ref == 36936 and pa == 3078 and 11 < ref / pa < 13
+    assert bm.q2_apply_flops("elasticity")["total"] == 57402
+    import pytest
+    with pytest.raises(ValueError):
+        bm.q2_apply_flops("elasticity", partial_assembly=True)
