@@ -9,7 +9,8 @@ future work in Sec. 7, against facts that do not come from the oracle's own form
   M = (h/30)[[4,2,-1],[2,16,2],[-1,2,4]];
 * the patch test on a jittered mesh with straight edges (interior rows of A u vanish for linear u);
 * the energy of a linear field u = F x on curved elements (kappa |grad u|^2 V, lam tr(eps)^2 +
-  2 mu eps:eps times V), and the null spaces (constants, six rigid-body modes).
+  2 mu eps:eps times V), and the null spaces (constants, six rigid-body modes);
+* the convergence rates of a manufactured solution: O(h^3) in L2 and O(h^2) in the H1 seminorm.
 """
 import math
 
@@ -101,3 +102,46 @@ def test_q2_linear_field_energy_and_null_spaces_on_curved_elements():
             assert np.allclose(AE[e] @ (X[e] @ W.T).reshape(-1), 0, atol=1e-11)
         assert np.allclose(AE[e] @ np.tile([1.0, -2.0, 0.5], 27), 0, atol=1e-11)
         assert np.linalg.matrix_rank(AE[e], tol=1e-9 * np.abs(AE[e]).max()) == 81 - 6
+
+
+def _q2_mms_errors(n, jitter):
+    """Q2 solution of -lap u = f for u = cos(pi x) cos(pi y) sin(pi z / 2) (u = 0 on z = 0, natural
+    conditions elsewhere) on the n^3 box: L2 and H1-seminorm errors.  The load vector and the error
+    integrals use the 3x3x3 Gauss rule and the oracle's Q2 shape functions (pinned above)."""
+    p = inputs.q2_box("laplace", n, jitter=jitter, seed=7)
+    pi = math.pi
+    u = lambda X: np.cos(pi * X[..., 0]) * np.cos(pi * X[..., 1]) * np.sin(pi * X[..., 2] / 2)
+    gu = lambda X: np.stack([-pi * np.sin(pi * X[..., 0]) * np.cos(pi * X[..., 1]) * np.sin(pi * X[..., 2] / 2),
+                             -pi * np.cos(pi * X[..., 0]) * np.sin(pi * X[..., 1]) * np.sin(pi * X[..., 2] / 2),
+                             pi / 2 * np.cos(pi * X[..., 0]) * np.cos(pi * X[..., 1]) * np.cos(pi * X[..., 2] / 2)], -1)
+    pts, w = fem.gauss3_points()
+    N = fem.q2_shape_values(pts)                       # (27 q, 27 a)
+    dN = fem.q2_shape_ref_grads(pts)                   # (27 q, 27 a, 3)
+    Xe = p.coords[p.cells]                             # (E, 27, 3)
+    Xq = np.einsum("qa,eai->eqi", N, Xe)
+    J = fem.jacobians(Xe, dN)
+    det = np.linalg.det(J)
+    f = 2.25 * pi * pi * u(Xq)
+    be = np.einsum("q,eq,qa,eq->ea", w, det, N, f)
+    b = np.bincount(p.cells.reshape(-1), weights=be.reshape(-1), minlength=p.n_nodes)
+    b[p.dirichlet.astype(bool)] = 0.0
+    A = fem.assemble_csr("laplace", p.coords, p.cells, np.ones(p.n_cells), p.dirichlet, p.n_nodes)
+    import scipy.sparse.linalg as spl
+    uh = spl.spsolve(A.tocsc(), b)
+    ue = uh[p.cells]                                   # (E, 27)
+    uq = np.einsum("qa,ea->eq", N, ue)
+    g_ref = np.einsum("qaj,ea->eqj", dN, ue)
+    gq = np.einsum("eqji,eqj->eqi", np.linalg.inv(J), g_ref)  # J^{-T} grad_ref
+    e0 = math.sqrt(np.einsum("q,eq,eq->", w, det, (uq - u(Xq)) ** 2))
+    e1 = math.sqrt(np.einsum("q,eq,eqi->", w, det, (gq - gu(Xq)) ** 2))
+    return e0, e1
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.15])
+def test_q2_manufactured_solution_convergence(jitter):
+    """Q2: O(h^3) in L2 and O(h^2) in the H1 seminorm (straight-edged jittered meshes included)."""
+    e = [_q2_mms_errors(n, jitter) for n in (2, 4, 8)]
+    r0 = [math.log2(e[i][0] / e[i + 1][0]) for i in range(2)]
+    r1 = [math.log2(e[i][1] / e[i + 1][1]) for i in range(2)]
+    assert r0[-1] > 2.8, r0
+    assert 1.8 < r1[-1] < 2.3, r1

@@ -10,8 +10,11 @@ against facts that do not come from the oracle's own formulas:
 * the null space: constants (Laplace) and the six rigid-body modes (elasticity);
 * the patch test on a jittered mesh: A u = 0 on interior rows for a linear u and uniform material;
 * the tetrahedralisation: orientation, conformity (every interior face shared by two elements),
-  total volume 1.
+  total volume 1;
+* the convergence rates of a manufactured solution: O(h^2) in L2 and O(h) in the H1 seminorm.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -154,3 +157,43 @@ def test_energy_pin_catches_planted_slips(monkeypatch):
     monkeypatch.setattr(fem, "reference_rule", rule)
     monkeypatch.setattr(fem, "tet_ref_grads", lambda: np.array([[1.0, 1, 1], [1, 0, 0], [0, 1, 0], [0, 0, 1]]))
     assert _energy_error() > 1e-3  # sign of grad phi_0
+
+
+def _tet_mms_errors(n):
+    """P1 solution of -lap u = f for u = cos(pi x) cos(pi y) sin(pi z / 2) (u = 0 on z = 0, natural
+    conditions elsewhere) on the Kuhn-split n^3 box: L2 and H1-seminorm errors.  The load vector and
+    the L2 error use the 4-point rule of degree 2 (barycentric (a, b, b, b) and permutations,
+    a = (5 + 3 sqrt 5) / 20, b = (5 - sqrt 5) / 20, weights |T| / 4)."""
+    p = inputs.tet_box("laplace", n, jitter=0.1, seed=9)
+    pi = math.pi
+    u = lambda X: np.cos(pi * X[..., 0]) * np.cos(pi * X[..., 1]) * np.sin(pi * X[..., 2] / 2)
+    gu = lambda X: np.stack([-pi * np.sin(pi * X[..., 0]) * np.cos(pi * X[..., 1]) * np.sin(pi * X[..., 2] / 2),
+                             -pi * np.cos(pi * X[..., 0]) * np.sin(pi * X[..., 1]) * np.sin(pi * X[..., 2] / 2),
+                             pi / 2 * np.cos(pi * X[..., 0]) * np.cos(pi * X[..., 1]) * np.cos(pi * X[..., 2] / 2)], -1)
+    a, b = (5 + 3 * math.sqrt(5)) / 20, (5 - math.sqrt(5)) / 20
+    L = np.full((4, 4), b) + np.eye(4) * (a - b)      # barycentric coordinates of the 4 points
+    X = p.coords[p.cells]
+    vol = _volume(X)
+    Xq = np.einsum("qa,eai->eqi", L, X)
+    be = np.einsum("e,qa,eq->ea", vol / 4, L, 2.25 * pi * pi * u(Xq))
+    bvec = np.bincount(p.cells.reshape(-1), weights=be.reshape(-1), minlength=p.n_nodes)
+    bvec[p.dirichlet.astype(bool)] = 0.0
+    A = fem.assemble_csr("laplace", p.coords, p.cells, np.ones(p.n_cells), p.dirichlet, p.n_nodes)
+    import scipy.sparse.linalg as spl
+    uh = spl.spsolve(A.tocsc(), bvec)
+    ue = uh[p.cells]
+    w, dN = fem.reference_rule(4)
+    J = fem.jacobians(X, dN)[:, 0]
+    g = np.einsum("eji,aj,ea->ei", np.linalg.inv(J), dN[0], ue)   # constant gradient per element
+    e0 = math.sqrt(np.einsum("e,eq->", vol / 4, (np.einsum("qa,ea->eq", L, ue) - u(Xq)) ** 2))
+    e1 = math.sqrt(np.einsum("e,eqi->", vol / 4, (g[:, None, :] - gu(Xq)) ** 2))
+    return e0, e1
+
+
+def test_tet_manufactured_solution_convergence():
+    """P1 on the Kuhn meshes: O(h^2) in L2 and O(h) in the H1 seminorm."""
+    e = [_tet_mms_errors(n) for n in (4, 8, 16)]
+    r0 = [math.log2(e[i][0] / e[i + 1][0]) for i in range(2)]
+    r1 = [math.log2(e[i][1] / e[i + 1][1]) for i in range(2)]
+    assert r0[-1] > 1.8, r0
+    assert 0.85 < r1[-1] < 1.2, r1
