@@ -144,6 +144,8 @@ def mf_setup_mesh(physics, n_nodes, n_cells, coords, cells, nx, ny, nz, mat, dir
 
 
 def mf_setup_mesh_elem(element, physics, n_nodes, n_cells, coords, cells, mat, dirichlet, stream=None) -> int:
+    """Mesh of an explicit connectivity of element type MF_ELEM_HEX8 ([E][8]), MF_ELEM_TET4 ([E][4],
+    positively oriented) or MF_ELEM_HEX27 ([E][27], node i + 3j + 9k at reference (i-1, j-1, k-1))."""
     h = vp()
     check(lib.mf_setup_mesh_elem(element, physics, n_nodes, n_cells, _ptr(coords), _ptr(cells), _ptr(mat),
                                  _ptr(dirichlet), _stream(stream), C.byref(h)), "mf_setup_mesh_elem")
@@ -398,7 +400,9 @@ def mf_version() -> str:
 # ----------------------------------------------------------------------------- handle owners ----
 
 class Mesh:
-    """Owner of an ``mf_mesh`` handle.  Arrays are torch tensors on the current CUDA device."""
+    """Owner of an ``mf_mesh`` handle.  Arrays are torch tensors on the current CUDA device.
+    ``element`` is "hex8" (Q1; ``cells`` None for a structured box of ``dims``), "tet4" (P1) or
+    "hex27" (Q2); the last two need ``cells``."""
 
     def __init__(self, physics: str, coords, mat, dirichlet=None, cells=None, dims=None, stream=None,
                  element: str = "hex8"):
