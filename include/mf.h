@@ -106,7 +106,9 @@ mf_status mf_destroy_mesh(mf_mesh *mesh);
 /* Host outputs (any may be NULL): node, cell and DoF counts, free (unconstrained) DoFs, number of
  * element colours of the scatter, and flags (bit 0: structured, bit 1: every cell affine, bit 2:
  * tensor-product grid of axis-aligned cells, which enables the FP64-accurate tile kernels, bit 3:
- * partial-assembly data built, bit 4: tetrahedral mesh, bit 5: Q2 mesh). */
+ * partial-assembly data built, bit 4: tetrahedral mesh, bit 5: Q2 mesh, bit 6: structured mesh whose
+ * cell constants or cell sizes span more than the double-word kernels cover, so that every apply
+ * runs the FP64 reference kernel; see "Range" below). */
 mf_status mf_mesh_query(const mf_mesh *mesh, int64_t *n_nodes, int64_t *n_cells, int64_t *n_dof,
                         int64_t *n_free, int32_t *n_colours, int32_t *flags);
 
@@ -115,8 +117,11 @@ mf_status mf_mesh_query(const mf_mesh *mesh, int64_t *n_nodes, int64_t *n_cells,
  *   MF_VARIANT_AUTO       fastest variant that meets FP64 accuracy for this mesh (default): on a
  *                         structured tensor-product grid the face-marching kernel (Walsh-Hadamard
  *                         form of the 2x2x2 Gauss sums, double-word FP32 arithmetic); on another
- *                         structured box the partial-assembly kernel when its data fit (flag bit 3
- *                         of mf_mesh_query), else the general kernel; otherwise the reference kernel
+ *                         structured box the partial-assembly kernel when its data take at most
+ *                         a quarter of the device's total memory (flag bit 3 of mf_mesh_query;
+ *                         the choice depends on the mesh and the device model only), else the
+ *                         general kernel; otherwise the reference kernel.  Results are bitwise
+ *                         reproducible for a given variant
  *   MF_VARIANT_REFERENCE  Algorithm 1 as printed: one thread per element, FP64 arithmetic,
  *                         Jacobian at every quadrature point, colour-by-colour scatter
  *   MF_VARIANT_GENERAL    structured boxes that are not tensor-product grids: Jacobian, adjugate
@@ -127,6 +132,25 @@ mf_status mf_mesh_query(const mf_mesh *mesh, int64_t *n_nodes, int64_t *n_cells,
  *                         Laplace, 10 for elasticity); built on first selection (MF_ERR_OOM if it
  *                         does not fit; synchronises the device)
  */
+/*
+ * Range of the double-word kernels (face-marching, general and partial-assembly; FP64 applies and
+ * the FP64 CG on them).  Their arithmetic is pairs of floats: 48 significand bits, and FP32's
+ * exponent range.  The library keeps FP64 accuracy (<= 1e-12 relative in the 2-norm against an FP64
+ * evaluation) for every finite input as follows; all scalings are by powers of two, hence exact:
+ *   - cell constants: when max |kappa| (or max(|lam|, mu)) is outside [2^-8, 2^9), the double-word
+ *     data are built from constants scaled into that window; coordinates likewise when the largest
+ *     det J at a Gauss point (~(h/2)^3) is outside [2^-40, 2^25); y is scaled back in the kernel;
+ *   - x: every CTA records the largest |x| it reads; if that lies outside [2^-72, 2^41) the CTA
+ *     computes its tile again with its inputs scaled into [1, 2) and y scaled back (the tile's
+ *     inputs below 2^-74 of its largest one are then treated as zero).  The result does not depend
+ *     on the scaling decision beyond rounding, and 2^k x gives exactly 2^k y.  Such applies take
+ *     about twice the time of in-range ones;
+ *   - meshes whose cell constants span a ratio above 2^80, or whose det J spans a ratio above 2^60
+ *     (cell sizes over 2^20), do not build double-word data at all (mf_mesh_query flag bit 6): the
+ *     auto variant runs the FP64 reference kernel and MF_VARIANT_GENERAL / MF_VARIANT_PARTIAL return
+ *     MF_ERR_UNSUPPORTED.
+ * The FP32 applies (mf_apply_f32, the inner solves of MF_PREC_MIXED_IR) have FP32's range.
+ */
 enum { MF_VARIANT_AUTO = 0, MF_VARIANT_REFERENCE = 1, MF_VARIANT_GENERAL = 2, MF_VARIANT_PARTIAL = 3 };
 mf_status mf_set_apply_variant(mf_mesh *mesh, int variant);
 
@@ -136,7 +160,8 @@ mf_status mf_set_apply_variant(mf_mesh *mesh, int variant);
  *   x  device double[N], input; entries on Dirichlet nodes are ignored except that y_d = x_d.
  *   y  device double[N], output, overwritten.  Must not overlap x.
  * Asynchronous on `stream`, allocates nothing, deterministic (bitwise-reproducible: the scatter
- * uses no atomics).  Errors: MF_ERR_ARG (null, aliasing, mesh is not Laplace), MF_ERR_CUDA.
+ * uses no atomics).  FP64-accurate for every finite x (see "Range" above).  Errors: MF_ERR_ARG
+ * (null, aliasing, mesh is not Laplace), MF_ERR_CUDA.
  */
 mf_status mf_apply_laplace(const mf_mesh *mesh, const double *x, double *y, mf_stream stream);
 
@@ -374,6 +399,23 @@ mf_status mf_grid_restrict(const void *in, int32_t nfx, int32_t nfy, int32_t nfz
                            float scale, mf_stream stream);
 mf_status mf_grid_prolong(const void *in, int32_t ncx, int32_t ncy, int32_t ncz, int32_t c, void *out,
                           float scale, mf_stream stream);
+
+/*
+ * mf_training_pair - one (input, target) pair for training the learned preconditioner (the network's
+ * workload; the paper has none).  Given b = A x* for an exact solution x* and an iterate x_k of a
+ * solve of A x = b (device double[n_dof] each), forms in FP64 the residual r = b - A x_k and the
+ * error e = x* - x_k (so that A e = r) in the variables of the symmetrically scaled system with
+ * D = diag(A) (Eqs. 4/6, the Jacobi diagonal of mf_operator_diagonal): r~ = D^-1/2 r and
+ * e~ = D^1/2 e, Dirichlet entries 0.
+ *   r64, e64   device double[n_dof] outputs r~ and e~, or NULL.
+ *   r32, e32   device float[n_dof] outputs r~ / s and e~ / s with s = RMS(r~) (network input and
+ *              unscaled target).
+ *   sums       host double[2] or NULL: sum of r~^2 and of e~^2.
+ * Uses the mesh's solver workspace (allocated on first use, like mf_cg_solve).  Synchronises
+ * `stream`.  Errors: MF_ERR_ARG, MF_ERR_OOM, MF_ERR_CUDA.
+ */
+mf_status mf_training_pair(mf_mesh *mesh, const double *b, const double *xs, const double *xk, double *r64,
+                           double *e64, float *r32, float *e32, double *sums, mf_stream stream);
 
 /* Message describing the last failure in the calling thread ("" if none).  Valid until the next
  * failing call in the same thread. */

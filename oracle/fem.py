@@ -381,16 +381,3 @@ def volumes(coords, cells) -> np.ndarray:
         el = np.arange(s, min(s + ch, cells.shape[0]))
         out[el] = np.linalg.det(jacobians(coords[cells[el]], dN)) @ w
     return out
-
-
-def min_det(coords, cells) -> float:
-    """Smallest det J over all Gauss points and corners (mesh validity)."""
-    pts, _ = gauss_points()
-    allp = np.concatenate([pts, corner_signs()])
-    dN = shape_ref_grads(allp)
-    m = math.inf
-    ch = _chunk(cells.shape[1])
-    for s in range(0, cells.shape[0], ch):
-        el = np.arange(s, min(s + ch, cells.shape[0]))
-        m = min(m, float(np.linalg.det(jacobians(coords[cells[el]], dN)).min()))
-    return m

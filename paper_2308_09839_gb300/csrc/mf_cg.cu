@@ -314,6 +314,41 @@ __global__ void add_f32(int64_t n, double *__restrict__ x, const float *__restri
   GRID_STRIDE(i, n) x[i] += (double)d[i];
 }
 
+// Training pair of the learned preconditioner: r~ = D^-1/2 (b - A x_k), e~ = D^1/2 (x* - x_k) with
+// D = diag(A) (invdiag holds 1/D), Dirichlet entries 0; sums of r~^2 and e~^2 into sc->res2, sc->bb.
+__global__ void __launch_bounds__(kRedThreads)
+    pair_kernel(int64_t n, int ndpn, const double *__restrict__ b, const double *__restrict__ Axk,
+                const double *__restrict__ xs, const double *__restrict__ xk, const double *__restrict__ invdiag,
+                const uint8_t *__restrict__ dmask, double *__restrict__ r, double *__restrict__ e, double *partials,
+                CgScalars *sc) {
+  double v[2] = {0.0, 0.0};
+  GRID_STRIDE(i, n) {
+    const bool dir = dmask[i / ndpn] != 0;
+    const double sq = sqrt(invdiag[i]);  // D^-1/2
+    const double ri = dir ? 0.0 : (b[i] - Axk[i]) * sq;
+    const double ei = dir ? 0.0 : (xs[i] - xk[i]) / sq;
+    r[i] = ri;
+    e[i] = ei;
+    v[0] += ri * ri;
+    v[1] += ei * ei;
+  }
+  double out[2];
+  if (grid_reduce<2>(v, partials, &sc->ticket, out) && threadIdx.x == 0) {
+    sc->res2 = out[0];
+    sc->bb = out[1];
+  }
+}
+
+// r32 = r~ / s, e32 = e~ / s with s = RMS(r~) = sqrt(sc->res2 / n) (1 when r~ = 0).
+__global__ void pair_scale(int64_t n, const double *__restrict__ r, const double *__restrict__ e,
+                           const CgScalars *__restrict__ sc, float *__restrict__ r32, float *__restrict__ e32) {
+  const double ss = sc->res2 > 0.0 ? sqrt(sc->res2 / (double)n) : 1.0;
+  GRID_STRIDE(i, n) {
+    r32[i] = (float)(r[i] / ss);
+    e32[i] = (float)(e[i] / ss);
+  }
+}
+
 using OpFn = std::function<mf_status(const void *in, void *out, cudaStream_t s, const int *skip)>;
 // operator with in . out fused: writes the dot product to *dot (null function when not available)
 using OpDotFn = std::function<mf_status(const void *in, void *out, cudaStream_t s, const int *skip, double *dot)>;
@@ -331,9 +366,22 @@ struct CgWorkspace {
   CgScalars *sc = nullptr, *sc32 = nullptr;
   CgScalars *h_sc = nullptr;
   cudaStream_t cap = nullptr;
+  // What a captured graph depends on besides the workspace: the operator (matrix-free, or which
+  // assembled matrix: its device arrays and sizes are baked into the graph), the mesh's apply
+  // variant, the preconditioner, the recurrence and the iterations per launch.  A CSR matrix is
+  // identified by its process-unique id, so a matrix assembled after another was destroyed never
+  // matches a graph captured for the old one, even at the same host address.
+  struct Key {
+    int op = -1, precond = -1, variant = -1, check_every = -1, recurrence = -1, precision = -1;
+    uint64_t csr_id = 0;
+    bool operator==(const Key &o) const {
+      return op == o.op && precond == o.precond && variant == o.variant && check_every == o.check_every &&
+             recurrence == o.recurrence && precision == o.precision && csr_id == o.csr_id;
+    }
+  };
   struct Graph {
     cudaGraphExec_t exec = nullptr;
-    long long key = -1;
+    Key key;
     int64_t kernels = 0;  // kernel nodes per replay
   } g[2];
   bool invdiag_ready = false;  // invdiag holds 1 / diag(A) of this mesh
@@ -444,7 +492,7 @@ mf_status cgp_iteration(const OpFn &op, const OpDotFn &opdot, int64_t n, double 
 using IterFn = std::function<mf_status(cudaStream_t)>;
 
 template <typename R>
-mf_status cg_loop(CgWorkspace *w, int slot, long long key, const OpFn &op, const OpDotFn &opdot, int64_t n, R *x,
+mf_status cg_loop(CgWorkspace *w, int slot, const CgWorkspace::Key &key, const OpFn &op, const OpDotFn &opdot, int64_t n, R *x,
                   R *r, R *p, R *Ap,
                   const double *invdiag, CgScalars *sc, int k, bool use_graph, double deadline_s,
                   std::chrono::steady_clock::time_point t0, cudaStream_t s, CgScalars *host,
@@ -457,7 +505,7 @@ mf_status cg_loop(CgWorkspace *w, int slot, long long key, const OpFn &op, const
     return MF_OK;
   };
   CgWorkspace::Graph &g = w->g[slot];
-  if (use_graph && (g.exec == nullptr || g.key != key)) {
+  if (use_graph && (g.exec == nullptr || !(g.key == key))) {
     if (g.exec) {
       cudaGraphExecDestroy(g.exec);
       g.exec = nullptr;
@@ -929,10 +977,21 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
     opdot32 = [m, w](const void *in, void *out, cudaStream_t st, const int *skip, double *dot) -> mf_status {
       return tile_apply_dot_fp32(m, (const float *)in, (float *)out, st, skip, w->dotp, w->dticket, dot);
     };
-  const long long key64 = ((long long)o->op << 40) ^ ((long long)o->precond << 36) ^ ((long long)m->variant << 32) ^
-                          ((long long)(intptr_t)A & 0xffffffffll) ^ ((long long)o->check_every << 44) ^
-                          ((long long)o->recurrence << 60);
-  const long long key32 = ((long long)m->variant << 32) ^ ((long long)o->check_every << 44) ^ 0x5a5a;
+  CgWorkspace::Key key64;
+  key64.op = o->op;
+  key64.precond = o->precond;
+  key64.variant = m->variant;
+  key64.check_every = o->check_every;
+  key64.recurrence = o->recurrence;
+  key64.precision = MF_PREC_FP64;
+  key64.csr_id = o->op == MF_OP_CSR ? A->id : 0;
+  CgWorkspace::Key key32;
+  key32.op = MF_OP_MATFREE;
+  key32.precond = MF_PC_NONE;
+  key32.variant = m->variant;
+  key32.check_every = o->check_every;
+  key32.recurrence = MF_CG_CLASSIC;
+  key32.precision = MF_PREC_MIXED_IR;
   mf_status st = MF_OK;
   int iters = 0, outer = 0;
   double rel_rec = 0.0;
@@ -1063,7 +1122,7 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
 // ------------------------------------------------------------------------------------------------
 namespace {
 
-constexpr int64_t kNoAllocMaxDof = 262144;  // MF_NOALLOC_MAX_DOF in mf.h
+constexpr int64_t kNoAllocMaxDof = MF_NOALLOC_MAX_DOF;
 constexpr int64_t kNoAllocScalarsDoubles = (sizeof(CgScalars) + sizeof(double) - 1) / sizeof(double);
 constexpr int64_t kNoAllocDoubles = 3 * kNoAllocMaxDof + 4 * kRedBlocks + kNoAllocScalarsDoubles;
 
@@ -1162,6 +1221,31 @@ extern "C" mf_status mf_cg_solve_noalloc(const mf_mesh *m, const mf_solve_opts *
   if (st == MF_ERR_BREAKDOWN) mf_set_error("mf_cg_solve_noalloc: breakdown (p^T A p <= 0 or non-finite scalar)");
   if (st == MF_NOT_CONVERGED) mf_set_error("mf_cg_solve_noalloc: not converged within the iteration limit");
   return st;
+}
+
+extern "C" mf_status mf_training_pair(mf_mesh *m, const double *b, const double *xs, const double *xk, double *r64,
+                                      double *e64, float *r32, float *e32, double *sums, mf_stream stream) {
+  mf_clear_error();
+  MF_ARG(m && b && xs && xk && r32 && e32, "mf_training_pair: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  MF_TRY(ensure_invdiag(m, s));
+  CgWorkspace *w = m->cg;
+  const int64_t n = m->n_dof;
+  double *r = r64 ? r64 : w->r, *e = e64 ? e64 : w->p;
+  MF_TRY(apply_fp64(m, xk, w->Ap, s));
+  mf_count_launches(2);
+  pair_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, m->ndpn, b, w->Ap, xs, xk, w->invdiag, m->dmask, r, e, w->partials,
+                                                 w->sc);
+  pair_scale<<<kRedBlocks, kRedThreads, 0, s>>>(n, r, e, w->sc, r32, e32);
+  MF_CUDA(cudaGetLastError());
+  CgScalars h;
+  MF_CUDA(cudaMemcpyAsync(&h, w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  if (sums) {
+    sums[0] = h.res2;
+    sums[1] = h.bb;
+  }
+  return MF_OK;
 }
 
 extern "C" mf_status mf_operator_diagonal(const mf_mesh *m, double *diag, mf_stream stream) {

@@ -7,6 +7,7 @@
 // read-modify-write: elements are processed colour by colour (elements of one colour share no
 // node, hence no row), which keeps the fill deterministic.
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "mf_element.cuh"
@@ -536,6 +537,8 @@ extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr 
   MF_ARG(nnz < (int64_t)INT32_MAX * 4, "mf_assemble_csr: matrix too large");
 
   mf_csr *A = new mf_csr();
+  static std::atomic<uint64_t> next_id{1};
+  A->id = next_id.fetch_add(1);
   A->n_rows = n_rows;
   A->nnz = nnz;
   int64_t maxrow = 0;

@@ -131,6 +131,80 @@ __device__ __forceinline__ double f2d(float f) {
 // (hi, lo) -> nearest double: one FP64 add.
 __device__ __forceinline__ double to_double(dw x) { return __dadd_rn(f2d(x.h), f2d(x.l)); }
 
+// ------------------------------------------------------------ power-of-two range scaling ----
+// The double-word kernels work in FP32's exponent range.  Inputs outside it are brought in by an
+// exact power-of-two scaling (x * 2^-s before the split, y * 2^s after the final add); these helpers
+// do that scaling and record the magnitude of the inputs a CTA has read.
+
+// 2^k as a double, k in [-1022, 1023].
+__device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// v * 2^k exactly (up to FP64's own underflow and overflow), |k| <= 2044.  Normal values whose
+// result stays normal take two integer operations on the exponent field; zeros, subnormals,
+// non-finite values and results leaving the normal range take two FP64 multiplies.
+__device__ __forceinline__ double ldexp_exact(double v, int k) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e != 0 && e != 0x7ff && e + k >= 1 && e + k <= 2046) return __longlong_as_double(b + ((long long)k << 52));
+  const int k1 = k / 2, k2 = k - k1;
+  return __dmul_rn(__dmul_rn(v, pow2d(k1)), pow2d(k2));
+}
+
+// float v * 2^k, |k| <= 252 (FP32 results keep FP32's range).
+__device__ __forceinline__ float ldexpf_exact(float v, int k) {
+  const int k1 = k / 2, k2 = k - k1;
+  return __fmul_rn(__fmul_rn(v, __uint_as_float((unsigned)(k1 + 127) << 23)), __uint_as_float((unsigned)(k2 + 127) << 23));
+}
+
+// split(x * 2^-s): the scaled value as a pair.  Values that are below 2^-74 after the scaling
+// (negligible next to the CTA's largest input, which the scaling brings to [1, 2)) become zero.
+__device__ __forceinline__ dw split_scaled(double x, int s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const int es = e - s;
+  if (e == 0 || e == 0x7ff || es < 949 || es > 1150) {
+    const double xs = ldexp_exact(x, -s);
+    if (!(fabs(xs) >= 0x1p-74)) {  // also zeros; NaN stays NaN through the FP32 conversion below
+      if (xs == xs) return dw{__uint_as_float((unsigned)(b >> 32) & 0x80000000u), 0.0f};
+    }
+    const float h = __double2float_rz(xs);
+    return dw{h, __double2float_rn(xs - (double)h)};
+  }
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  const unsigned sign = bh & 0x80000000u;
+  const unsigned mhi = ((bh & 0x000fffffu) << 3) | (bl >> 29);
+  const unsigned hb = sign | ((unsigned)(es - 1023 + 127) << 23) | mhi;
+  const unsigned rem = bl & 0x1fffffffu;
+  const float lo = __fmul_rn(__uint2float_rn(rem), __uint_as_float((unsigned)(es - 1075 + 127) << 23));
+  return dw{__uint_as_float(hb), __uint_as_float(__float_as_uint(lo) | sign)};
+}
+
+// Magnitude record of the inputs a thread has read, in one register: the largest high word of |x|
+// (exponent and leading mantissa bits, ordered like |x|), with bit 0 also set for any input whose
+// low word is non-zero (so that inputs below 2^-1042, whose high word is zero, still count).
+struct MagRec {
+  unsigned key = 0u;
+  __device__ __forceinline__ void add(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    key = max(key, ((unsigned)(b >> 32) & 0x7fffffffu) | ((unsigned)b != 0u ? 1u : 0u));
+  }
+};
+
+// Exponent s with max |x| < 2^(s+1) and, for normal inputs, 2^s <= max |x| (inputs below 2^-1042 are
+// given s = -1043); false when every input was zero or one of them was not finite.
+__device__ __forceinline__ bool mag_exponent(unsigned key, int &s) {
+  const int e = (int)(key >> 20);
+  if (e == 0x7ff || key == 0u) return false;
+  if (e != 0) s = e - 1023;
+  else if (key > 1u) s = -1042 + (31 - __clz(key & 0xfffffu));
+  else s = -1043;
+  return true;
+}
+
+// Window of input magnitudes (exponent of the CTA's largest |x|) in which the double-word kernels
+// keep FP64 accuracy without rescaling, given cell constants and spacings normalised at setup.
+constexpr int kMagLo = -72, kMagHi = 40;
+
 // Host/device-agnostic split of a double constant (setup and constants, not hot paths).
 __host__ __device__ inline dw from_double_slow(double x) {
   const float h = (float)x;

@@ -41,6 +41,7 @@ struct GenArgs {
   const uint8_t *dmask;
   const void *pa;       // partial-assembly data (float2 or float, see PaView), or null
   int64_t n_cells;
+  int oscale;           // y = 2^oscale (operator of the normalised cell constants and coordinates) x
 };
 
 // v or -v (negation of a float pair is exact: both parts change sign)
@@ -401,25 +402,39 @@ struct GenSmem {
   typename N::S acc[2][NACC];
   typename N::S ash[PHYS == MF_LAPLACE ? 1 : 36 * EX * EY];
   typename N::S pbuf[std::is_same<N, NumDW>::value ? 20 * EX * EY : 1];  // partial-assembly prefetch slots
+  unsigned red[32];  // per-warp input magnitude records
 };
 
 // Owner-computes tile traversal marching up in z (output-plane accumulators in shared memory,
-// summed in a fixed order), with the node offsets staged next to the input values.
-template <int PHYS, class N, int EX, int EY, bool PA>
-__global__ void __launch_bounds__(EX *EY, (PA && std::is_same<N, NumF32>::value) ? 2 : 1)
-    gen_apply(GenArgs g, const typename N::IO *__restrict__ x,
-                                                       typename N::IO *__restrict__ y, const int *__restrict__ skip) {
+// summed in a fixed order), with the node offsets staged next to the input values.  One pass over
+// this CTA's work item; SC: x * 2^-sc in and y * 2^so out (normalised meshes and the rescaled pass
+// for inputs outside the double-word range).  Double-word passes record the magnitude of the inputs
+// read in `mag` (Dirichlet entries excluded).
+template <int PHYS, class N, int EX, int EY, bool PA, bool SC>
+__device__ __forceinline__ void gen_pass(const GenArgs &g, const typename N::IO *__restrict__ x,
+                                         typename N::IO *__restrict__ y, GenSmem<PHYS, N, EX, EY> &sm, int sc, int so,
+                                         dwa::MagRec &mag) {
   using T = typename N::T;
   using S = typename N::S;
   using IO = typename N::IO;
+  constexpr bool IS_DW = std::is_same<N, NumDW>::value;
   constexpr int ND = phys_ndpn(PHYS);
   constexpr int NT = EX * EY, TX = EX - 1, TY = EY - 1, PX = EX + 1, PY = EY + 1, NP = PX * PY;
   constexpr int LOADS = (NP + NT - 1) / NT;
   constexpr int NACC = TX * TY * ND;
-  extern __shared__ __align__(16) unsigned char gen_smem_raw[];
-  auto &sm = *reinterpret_cast<GenSmem<PHYS, N, EX, EY> *>(gen_smem_raw);
   (void)PY;
-  if (skip && *skip) return;
+  auto conv_in = [&](IO v) -> T {
+    if constexpr (IS_DW && SC) return dwa::split_scaled(v, sc);
+    else return N::in(v);
+  };
+  auto conv_out = [&](T v) -> IO {
+    if constexpr (!SC) return N::out(v);
+    else if constexpr (IS_DW) return dwa::ldexp_exact(N::out(v), so);
+    else return dwa::ldexpf_exact(N::out(v), so);
+  };
+  (void)sc;
+  (void)so;
+  __syncthreads();  // a previous pass over the item may still be reading sm
   const int tid = threadIdx.x;
   const int bx = blockIdx.x % g.tiles_x;
   const int by = (blockIdx.x / g.tiles_x) % g.tiles_y;
@@ -463,7 +478,11 @@ __global__ void __launch_bounds__(EX *EY, (PA && std::is_same<N, NumF32>::value)
       const int p = tid + l * NT;
       if (p < NP) {
 #pragma unroll
-        for (int c = 0; c < ND; ++c) N::st(sm.up[k & 1][p * ND + c], dr[l] ? N::zero() : N::in(xr[l][c]));
+        for (int c = 0; c < ND; ++c) {
+          N::st(sm.up[k & 1][p * ND + c], dr[l] ? N::zero() : conv_in(xr[l][c]));
+          if constexpr (IS_DW)
+            if (!dr[l]) mag.add(xr[l][c]);
+        }
         if constexpr (!PA) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) N::st(sm.dp[k & 1][p * 3 + c], N::from2(dl[l][c]));
@@ -478,7 +497,7 @@ __global__ void __launch_bounds__(EX *EY, (PA && std::is_same<N, NumF32>::value)
       const int lx = idx % TX, ly = idx / TX;
       if (lx < ownx && ly < owny) {
         const int64_t node = (i0 + lx) + (int64_t)NXP * ((j0 + ly) + (int64_t)NYP * k);
-        y[node * ND + c] = __ldg(g.dmask + node) ? x[node * ND + c] : N::out(N::ld(a[t]));
+        y[node * ND + c] = __ldg(g.dmask + node) ? x[node * ND + c] : conv_out(N::ld(a[t]));
       }
       N::st(a[t], N::zero());
     }
@@ -540,9 +559,37 @@ __global__ void __launch_bounds__(EX *EY, (PA && std::is_same<N, NumF32>::value)
   if (s_hi + 1 == g.nz && g.nz >= k0 && g.nz < k1) write_plane(g.nz);
 }
 
+// One CTA per work item.  Double-word arithmetic: if the largest input the CTA read lies outside
+// [2^kMagLo, 2^kMagHi], the item is computed again with x scaled by the power of two that brings
+// that input to [1, 2) and y scaled back (FP64 accuracy over FP64's whole range; the decision
+// depends on the item's own inputs only, and the second pass rewrites every value of the first).
+template <int PHYS, class N, int EX, int EY, bool PA>
+__global__ void __launch_bounds__(EX *EY, (PA && std::is_same<N, NumF32>::value) ? 2 : 1)
+    gen_apply(GenArgs g, const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
+              const int *__restrict__ skip) {
+  extern __shared__ __align__(16) unsigned char gen_smem_raw[];
+  auto &sm = *reinterpret_cast<GenSmem<PHYS, N, EX, EY> *>(gen_smem_raw);
+  if (skip && *skip) return;
+  dwa::MagRec mag;
+  if (g.oscale == 0) gen_pass<PHYS, N, EX, EY, PA, false>(g, x, y, sm, 0, 0, mag);
+  else gen_pass<PHYS, N, EX, EY, PA, true>(g, x, y, sm, 0, g.oscale, mag);
+  if constexpr (std::is_same<N, NumDW>::value) {
+    const unsigned t = __reduce_max_sync(0xffffffffu, mag.key);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    unsigned T = 0u;
+#pragma unroll
+    for (int i = 0; i < EX * EY / 32; ++i) T = max(T, sm.red[i]);
+    int s = 0;
+    if (dwa::mag_exponent(T, s) && (s < dwa::kMagLo || s > dwa::kMagHi))
+      gen_pass<PHYS, N, EX, EY, PA, true>(g, x, y, sm, s, g.oscale + s, mag);
+  }
+}
+
 // ------------------------------------------------------------------------------------ setup ----
 // Half spacings of the base grid from the axis node lines, and node offsets from the base grid.
-__global__ void gen_axes(const double *X, int nx, int ny, int nz, float2 *hh) {
+__global__ void gen_axes(const double *X, int nx, int ny, int nz, double geo, float2 *hh) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nx + ny + nz) return;
   double a, b;
@@ -558,11 +605,11 @@ __global__ void gen_axes(const double *X, int nx, int ny, int nz, float2 *hh) {
     a = X[3 * (int64_t)(nx + 1) * (ny + 1) * k + 2];
     b = X[3 * (int64_t)(nx + 1) * (ny + 1) * (k + 1) + 2];
   }
-  const dw v = dwa::from_double_slow(0.5 * (b - a));
+  const dw v = dwa::from_double_slow(0.5 * (b - a) * geo);  // normalised (geo: power of two)
   hh[t] = make_float2(v.h, v.l);
 }
 
-__global__ void gen_delta(const double *X, int nx, int ny, int nz, float2 *delta) {
+__global__ void gen_delta(const double *X, int nx, int ny, int nz, double geo, float2 *delta) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t Nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   if (n >= Nn) return;
@@ -570,15 +617,15 @@ __global__ void gen_delta(const double *X, int nx, int ny, int nz, float2 *delta
   const double base[3] = {X[3 * (int64_t)i], X[3 * (int64_t)(nx + 1) * j + 1],
                           X[3 * (int64_t)(nx + 1) * (ny + 1) * k + 2]};
   for (int c = 0; c < 3; ++c) {
-    const dw v = dwa::from_double_slow(X[3 * n + c] - base[c]);
+    const dw v = dwa::from_double_slow((X[3 * n + c] - base[c]) * geo);
     delta[3 * n + c] = make_float2(v.h, v.l);
   }
 }
 
-__global__ void gen_mat_pairs(const double *m, int64_t n, float2 *out) {
+__global__ void gen_mat_pairs(const double *m, int64_t n, double scale, float2 *out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const dw v = dwa::from_double_slow(m[i]);
+  const dw v = dwa::from_double_slow(m[i] * scale);
   out[i] = make_float2(v.h, v.l);
 }
 
@@ -597,7 +644,7 @@ mf_status gen_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *
   g.tiles_x = (m->nx + 1 + EX - 2) / (EX - 1);
   g.tiles_y = (m->ny + 1 + EY - 2) / (EY - 1);
   const int cols = g.tiles_x * g.tiles_y;
-  const int nseg = std::max(1, std::min(m->nz + 1, (152 * 4 + cols - 1) / cols));
+  const int nseg = std::max(1, std::min(m->nz + 1, (device_sm_count() * 4 + cols - 1) / cols));
   g.seg = (m->nz + 1 + nseg - 1) / nseg;
   g.hh = m->gen_axis;
   g.delta = m->gen_delta;
@@ -605,6 +652,7 @@ mf_status gen_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *
   g.dmask = m->dmask;
   g.pa = std::is_same<N, NumDW>::value ? (const void *)m->pa : (const void *)m->pa32;
   g.n_cells = m->n_cells;
+  g.oscale = m->dw_oscale;
   const int smem = (int)sizeof(GenSmem<PHYS, N, EX, EY>);
   auto kern = gen_apply<PHYS, N, EX, EY, PA>;
   static bool set = false;
@@ -629,20 +677,27 @@ mf_status gen_setup(mf_mesh *m, cudaStream_t s) {
   const int n = m->nx + m->ny + m->nz;
   MF_CUDA(cudaMalloc(&m->gen_axis, n * sizeof(float2)));
   MF_CUDA(cudaMalloc(&m->gen_delta, 3 * m->n_nodes * sizeof(float2)));
-  gen_axes<<<blocks_for(n), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->gen_axis);
-  gen_delta<<<blocks_for(m->n_nodes), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->gen_delta);
+  gen_axes<<<blocks_for(n), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->dw_geo, m->gen_axis);
+  gen_delta<<<blocks_for(m->n_nodes), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->dw_geo, m->gen_delta);
   if (!m->mat_pairs) {
     const int64_t nm = m->n_cells * phys_nmat(m->physics);
     MF_CUDA(cudaMalloc(&m->mat_pairs, nm * sizeof(float2)));
-    gen_mat_pairs<<<blocks_for(nm), kThreads, 0, s>>>(m->mat, nm, m->mat_pairs);
+    gen_mat_pairs<<<blocks_for(nm), kThreads, 0, s>>>(m->mat, nm, m->dw_mat, m->mat_pairs);
   }
   MF_CUDA(cudaGetLastError());
   MF_CUDA(cudaStreamSynchronize(s));
   m->gen = true;
-  // the auto variant uses partial assembly when its data take at most a quarter of the free memory
+  // The auto variant uses partial assembly when its data take at most a quarter of the device's
+  // total memory: a function of the mesh and the device model, not of what else is allocated.  If
+  // the allocation fails all the same, the mesh keeps the general kernel (flag bit 3 of
+  // mf_mesh_query reports which one the auto variant runs).
   size_t free_b = 0, total_b = 0;
   MF_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  if ((double)pa_values(m) * (sizeof(float2) + sizeof(float)) <= 0.25 * (double)free_b) MF_TRY(pa_setup(m, s));
+  if ((double)pa_values(m) * (sizeof(float2) + sizeof(float)) <= 0.25 * (double)total_b) {
+    const mf_status st = pa_setup(m, s);
+    if (st != MF_OK && st != MF_ERR_OOM) return st;
+    mf_clear_error();
+  }
   return MF_OK;
 }
 
@@ -652,7 +707,7 @@ namespace {
 // det J at the 2x2x2 Gauss points, Algorithm 1) and stored as pairs and floats: one thread per cell.
 template <int PHYS>
 __global__ void pa_build(const double *__restrict__ X, int nx, int ny, int nz, const double *__restrict__ mat,
-                         float2 *__restrict__ pa, float *__restrict__ pa32) {
+                         double geo, double matscale, float2 *__restrict__ pa, float *__restrict__ pa32) {
   constexpr int K = PHYS == MF_ELASTICITY ? 10 : 6;
   const int64_t E = (int64_t)nx * ny * nz;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -661,7 +716,7 @@ __global__ void pa_build(const double *__restrict__ X, int nx, int ny, int nz, c
   double Xe[8][3];
   for (int a = 0; a < 8; ++a) {
     const int64_t node = (i + (a & 1)) + (int64_t)(nx + 1) * ((j + ((a >> 1) & 1)) + (int64_t)(ny + 1) * (k + (a >> 2)));
-    for (int c = 0; c < 3; ++c) Xe[a][c] = X[3 * node + c];
+    for (int c = 0; c < 3; ++c) Xe[a][c] = X[3 * node + c] * geo;  // normalised coordinates
   }
   for (int q = 0; q < 8; ++q) {
     double xi[3];
@@ -681,7 +736,7 @@ __global__ void pa_build(const double *__restrict__ X, int nx, int ny, int nz, c
     } else {
       const int r[6] = {0, 0, 0, 1, 1, 2}, c[6] = {0, 1, 2, 1, 2, 2};
       for (int t = 0; t < 6; ++t)
-        v[t] = mat[e] * (C[r[t]][0] * C[c[t]][0] + C[r[t]][1] * C[c[t]][1] + C[r[t]][2] * C[c[t]][2]) / det;
+        v[t] = mat[e] * matscale * (C[r[t]][0] * C[c[t]][0] + C[r[t]][1] * C[c[t]][1] + C[r[t]][2] * C[c[t]][2]) / det;
     }
     for (int t = 0; t < K; ++t) {
       const dw d = dwa::from_double_slow(v[t]);
@@ -726,11 +781,11 @@ mf_status pa_setup(mf_mesh *m, cudaStream_t s) {
     return MF_ERR_OOM;
   }
   if (m->physics == MF_ELASTICITY)
-    pa_build<MF_ELASTICITY><<<blocks_for(m->n_cells), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->mat, m->pa,
-                                                                          m->pa32);
+    pa_build<MF_ELASTICITY><<<blocks_for(m->n_cells), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->mat, m->dw_geo,
+                                                                          m->dw_mat, m->pa, m->pa32);
   else
-    pa_build<MF_LAPLACE><<<blocks_for(m->n_cells), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->mat, m->pa,
-                                                                       m->pa32);
+    pa_build<MF_LAPLACE><<<blocks_for(m->n_cells), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->mat, m->dw_geo,
+                                                                       m->dw_mat, m->pa, m->pa32);
   MF_CUDA(cudaGetLastError());
   MF_CUDA(cudaStreamSynchronize(s));
   return MF_OK;

@@ -125,6 +125,15 @@ struct mf_mesh {
   // inverses as (hi, lo) float pairs [hx | hy | hz | 1/hx | 1/hy | 1/hz], and the cell constants
   // as pairs; enables the FP64-accurate tile kernels of mf_tile.cu
   bool tp = false;
+  // Range of the double-word kernels (tensor-product, general and partial-assembly).  At setup the
+  // cell constants are scaled by dw_mat = 2^-s_k and the coordinates by dw_geo = 2^-s_h (powers of
+  // two, exact) when their magnitudes lie outside the window the double-word arithmetic covers; the
+  // kernels then evaluate 2^-(s_k + s_h) A and scale y by 2^dw_oscale.  dw_ok is false when the
+  // constants or the cell sizes span more than that arithmetic covers: the double-word data are not
+  // built and every apply runs the FP64 reference kernel.
+  bool dw_ok = true;
+  int dw_oscale = 0;
+  double dw_mat = 1.0, dw_geo = 1.0;
   int tile_seg = 0;  // z-segment length of the tile kernels (0: heuristic; set by the autotuner)
   // general structured geometry (structured boxes that are not tensor-product grids): half
   // spacings of the base grid [hx/2 | hy/2 | hz/2] and node offsets from it, as float pairs;
@@ -155,6 +164,7 @@ struct mf_mesh {
 };
 
 struct mf_csr {
+  uint64_t id = 0;  // unique per assembled matrix in the process (never reused): keys cached solver graphs
   int64_t n_rows = 0, nnz = 0;
   int64_t *rowptr = nullptr;
   int32_t *col = nullptr;
@@ -191,6 +201,11 @@ mf_status gen_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_
 // diag(A) of the matrix-free operator (Jacobi), FP64, Dirichlet rows 1.
 mf_status operator_diagonal(const mf_mesh *m, double *diag, cudaStream_t s);
 void cg_workspace_free(CgWorkspace *w);
+
+// Number of SMs of the current device (cached per device; 152 on GB300).  Sizes persistent grids
+// and the wave model of the tile kernels; the reductions whose order must not depend on the GPU use
+// fixed grids instead.
+int device_sm_count();
 
 // number of element colours and the launch grid for one colour
 int64_t colour_count(const mf_mesh *m, int c);

@@ -47,7 +47,22 @@ template <int NC, class N, int EX, int EY>
 struct MarchSmem {
   typename N::S up[2][(EX + 1) * (EY + 1) * NC];  // staged node planes (double buffered)
   typename N::S xrow[2][NC * EX * EY];            // partial sums of the top node row of each face
+  unsigned red[32];                               // per-warp input magnitude records
 };
+
+// Largest input magnitude of the work item over the whole CTA (all threads call it): true and the
+// exponent s (2^s <= max |x| < 2^(s+1)) when some input was non-zero and finite.
+template <int NT>
+__device__ __forceinline__ bool cta_mag_exponent(const dwa::MagRec &m, unsigned (&red)[32], int &s) {
+  const unsigned t = __reduce_max_sync(0xffffffffu, m.key);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  unsigned T = 0u;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) T = max(T, red[i]);
+  return dwa::mag_exponent(T, s);
+}
 
 // PHYS = MF_LAPLACE (Eq. 7), MF_VECTOR_LAPLACE (Eq. 5) or MF_ELASTICITY (Eq. 9, Algorithm 1);
 // vectors hold NC values per node (x, y, z components interleaved for the vector operators).
@@ -56,10 +71,27 @@ struct MarchSmem {
 // same persistent kernel, so the read-only and L1 paths may hold stale lines).
 // DOT: also return this thread's part of x . y over the nodes it writes (the dot product a CG
 // iteration needs next, p . Ap, formed while the result is written; FP64 products and sums).
-template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT = false>
-__device__ __forceinline__ double march_item(const TileArgs &g, int item, int64_t rr,
+// SC: power-of-two scaling, x * 2^-sc in and y * 2^so out (the cell constants and spacings of a
+// normalised mesh, and the rescaled pass for inputs outside the double-word range); without SC
+// neither is applied (so must be 0).  Double-word passes record the magnitude of the inputs read in
+// `mag` (Dirichlet entries excluded).
+template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT, bool SC>
+__device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_t rr,
                                              const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
-                                             MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm) {
+                                             MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm, int sc, int so,
+                                             dwa::MagRec &mag) {
+  constexpr bool IS_DW = std::is_same<N, tile::NumDW>::value;
+  auto conv_in = [&](typename N::IO v) -> typename N::T {
+    if constexpr (IS_DW && SC) return dwa::split_scaled(v, sc);
+    else return N::in(v);
+  };
+  auto conv_out = [&](typename N::T v) -> typename N::IO {
+    if constexpr (!SC) return N::out(v);
+    else if constexpr (IS_DW) return dwa::ldexp_exact(N::out(v), so);
+    else return dwa::ldexpf_exact(N::out(v), so);
+  };
+  (void)sc;
+  (void)so;
   double dacc = 0.0;
   static_assert(EX == 32, "a warp is one row of element columns");
   using T = typename N::T;
@@ -127,9 +159,14 @@ __device__ __forceinline__ double march_item(const TileArgs &g, int item, int64_
 #pragma unroll
     for (int l = 0; l < LOADS; ++l) {
       const int p = tid + l * NT;
-      if (p < NP)
+      if (p < NP) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) N::st(u[p * NC + c], dr[l] ? N::zero() : N::in(xr[l][c]));
+        for (int c = 0; c < NC; ++c) {
+          N::st(u[p * NC + c], dr[l] ? N::zero() : conv_in(xr[l][c]));
+          if constexpr (IS_DW)
+            if (!dr[l]) mag.add(xr[l][c]);
+        }
+      }
     }
   };
   // 2D forward transform of this thread's face in plane k (modes: bit 0 x, bit 1 y)
@@ -281,11 +318,11 @@ __device__ __forceinline__ double march_item(const TileArgs &g, int item, int64_
         const int64_t vi = (node * g.nrhs + rr) * NC + l;
         if constexpr (DOT) {
           const IO xv = ldx(x + vi);
-          const IO yv = dir ? xv : N::out(tot);
+          const IO yv = dir ? xv : conv_out(tot);
           y[vi] = yv;
           dacc += (double)xv * (double)yv;
         } else {
-          y[vi] = dir ? ldx(x + vi) : N::out(tot);
+          y[vi] = dir ? ldx(x + vi) : conv_out(tot);
         }
       }
     }
@@ -295,6 +332,38 @@ __device__ __forceinline__ double march_item(const TileArgs &g, int item, int64_
       for (int m = 0; m < 4; ++m) Fb[c][m] = Ft[c][m];
   }
   return dacc;
+}
+
+// The scaled pass as a separate (not inlined) function: it runs for normalised meshes and for the
+// rare work items whose inputs lie outside the double-word range, and keeping its code out of the
+// unscaled pass leaves that pass its registers.
+template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT>
+__device__ __noinline__ double march_pass_scaled(const TileArgs &g, int item, int64_t rr,
+                                                 const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
+                                                 MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm, int sc, int so,
+                                                 dwa::MagRec &mag) {
+  return march_pass<PHYS, N, EX, EY, COHERENT, DOT, true>(g, item, rr, x, y, sm, sc, so, mag);
+}
+
+// One work item with the output scaling of the mesh; for double-word arithmetic, if the largest input
+// the CTA read lies outside [2^kMagLo, 2^kMagHi] the item is computed again with x scaled by the power
+// of two that brings that input to [1, 2) (and y scaled back), so results keep FP64 accuracy over
+// FP64's whole range.  The decision depends on the item's own inputs only (deterministic); the
+// second pass overwrites every value the first one wrote.
+template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT = false>
+__device__ __forceinline__ double march_item(const TileArgs &g, int item, int64_t rr,
+                                             const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
+                                             MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm) {
+  dwa::MagRec mag;
+  double d = g.oscale == 0
+                 ? march_pass<PHYS, N, EX, EY, COHERENT, DOT, false>(g, item, rr, x, y, sm, 0, 0, mag)
+                 : march_pass_scaled<PHYS, N, EX, EY, COHERENT, DOT>(g, item, rr, x, y, sm, 0, g.oscale, mag);
+  if constexpr (std::is_same<N, tile::NumDW>::value) {
+    int s = 0;
+    if (cta_mag_exponent<EX * EY>(mag, sm.red, s) && (s < dwa::kMagLo || s > dwa::kMagHi))
+      d = march_pass_scaled<PHYS, N, EX, EY, COHERENT, DOT>(g, item, rr, x, y, sm, s, g.oscale + s, mag);
+  }
+  return d;
 }
 
 template <int PHYS, class N, int EX, int EY, int MINB>

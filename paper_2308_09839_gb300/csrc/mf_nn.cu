@@ -221,7 +221,7 @@ mf_status launch_conv_t(ConvArgs a, cudaStream_t s) {
     resident.store(std::max(r, 1));
   }
   a.tiles = a.tiles_x * a.tiles_y * ((a.nz + TZc - 1) / TZc);
-  const int grid = std::min(a.tiles, 152 * resident.load());
+  const int grid = std::min(a.tiles, device_sm_count() * resident.load());
   mf_count_launches(1);
   conv_mma<CKP, CN, MODE><<<grid, kConvThreads, smem, s>>>(a);
   MF_CUDA(cudaGetLastError());

@@ -32,6 +32,18 @@ void mf_count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_re
 int64_t mf_launches_now() { return g_launches.load(std::memory_order_relaxed); }
 extern "C" int64_t mf_kernel_launches(void) { return mf_launches_now(); }
 
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int n = cache[dev].load();
+  if (n == 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cache[dev].store(n);
+  }
+  return n;
+}
+
 // ------------------------------------------------------------------------- setup kernels ----
 enum : int { BAD_DET = 1, BAD_NODE = 2, BAD_COORD = 4, BAD_MAT = 8 };
 
@@ -39,6 +51,7 @@ struct ValidateOut {
   int flags;
   int not_affine;     // set if any cell is not a parallelepiped
   long long first_bad;  // smallest element index with a problem
+  unsigned long long det_max, det_min;  // bit patterns of the largest and smallest det J (positive)
 };
 
 // det J at the 8 Gauss points and the 8 corners must be positive and finite; node ids in range;
@@ -78,6 +91,11 @@ __global__ void validate_kernel(MeshView m, int physics, ValidateOut *out) {
           }
         double det = q1::adjugate(J, C);
         if (!(det > 0.0) || !isfinite(det)) flags |= BAD_DET;
+        if (p < 8 && det > 0.0 && isfinite(det)) {
+          const unsigned long long bits = (unsigned long long)__double_as_longlong(det);
+          atomicMax(&out->det_max, bits);
+          atomicMin(&out->det_min, bits);
+        }
       }
       // monomial coefficients of xi*eta, eta*zeta, xi*zeta, xi*eta*zeta in x(xi)
       double scale = 0;
@@ -201,6 +219,22 @@ __global__ void material_kernel(const double *in, double *out, float *out32, int
   }
 }
 
+// Largest |cell constant| and smallest positive one (kappa, or mu of (lam, mu)), as bit patterns
+// of positive doubles (their integer order is their numeric order).
+__global__ void mat_range_kernel(const double *mat, int64_t n_cells, int physics, unsigned long long *out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n_cells) return;
+  double big, small;
+  if (phys_is_laplace(physics)) {
+    big = small = fabs(mat[e]);
+  } else {
+    small = fabs(mat[2 * e + 1]);
+    big = fmax(fabs(mat[2 * e]), small);
+  }
+  atomicMax(out, (unsigned long long)__double_as_longlong(big));
+  if (small > 0.0) atomicMin(out + 1, (unsigned long long)__double_as_longlong(small));
+}
+
 __global__ void to_f32_kernel(const double *in, float *out, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -296,6 +330,44 @@ int64_t colour_count(const mf_mesh *m, int c) {
   return (int64_t)((m->nx - px + 1) / 2) * ((m->ny - py + 1) / 2) * ((m->nz - pz + 1) / 2);
 }
 
+// Window of the double-word kernels.  A structured mesh's cell constants (kappa, or lam and mu) and
+// cell sizes (det J at the Gauss points ~ (h/2)^3) are checked here: when the largest of them lies
+// outside the window, the double-word data are built from values scaled by a power of two (exact)
+// and the kernels scale y back; when they span more than the double-word arithmetic covers (cell
+// constants over a ratio of 2^80, det J over 2^60, i.e. cell sizes over 2^20), the double-word
+// kernels are switched off and the mesh runs the FP64 reference kernel.
+static mf_status dw_range_setup(mf_mesh *m, unsigned long long det_max_bits, unsigned long long det_min_bits,
+                                cudaStream_t s) {
+  unsigned long long *d = nullptr;
+  MF_TRY(dmalloc(&d, 2));
+  unsigned long long h[2] = {0ull, ~0ull};
+  MF_CUDA(cudaMemcpyAsync(d, h, sizeof(h), cudaMemcpyHostToDevice, s));
+  mat_range_kernel<<<blocks_for(m->n_cells), kThreads, 0, s>>>(m->mat, m->n_cells, m->physics, d);
+  MF_CUDA(cudaGetLastError());
+  MF_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  cudaFree(d);
+  double mat_max, mat_min, det_max, det_min;
+  memcpy(&mat_max, &h[0], 8);
+  memcpy(&mat_min, &h[1], 8);
+  memcpy(&det_max, &det_max_bits, 8);
+  memcpy(&det_min, &det_min_bits, 8);
+  m->dw_ok = mat_max > 0.0 && mat_min > 0.0 && det_max > 0.0 && det_min > 0.0 && std::isfinite(mat_max) &&
+             std::isfinite(det_max) && std::ilogb(mat_max) - std::ilogb(mat_min) <= 80 &&
+             std::ilogb(det_max) - std::ilogb(det_min) <= 60;
+  m->dw_oscale = 0;
+  m->dw_mat = m->dw_geo = 1.0;
+  if (!m->dw_ok) return MF_OK;
+  const int ek = std::ilogb(mat_max), ed = std::ilogb(det_max);
+  const int sk = (ek < -8 || ek > 8) ? ek : 0;
+  // det J = (h/2)^3 on a box cell: the length scale is 2^(ed/3)
+  const int sh = (ed < -40 || ed > 24) ? (ed >= 0 ? ed / 3 : -((-ed + 2) / 3)) : 0;
+  m->dw_mat = std::ldexp(1.0, -sk);
+  m->dw_geo = std::ldexp(1.0, -sh);
+  m->dw_oscale = sk + sh;
+  return MF_OK;
+}
+
 // ----------------------------------------------------------------------------- entry points ----
 static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cells, const double *coords,
                             const int32_t *cells, int32_t nx, int32_t ny, int32_t nz, const double *mat,
@@ -364,7 +436,7 @@ static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cel
     // validation (uses the caller's material array before conversion)
     ValidateOut *dv = nullptr;
     SETUP_TRY(dmalloc(&dv, 1));
-    ValidateOut hv = {0, 0, (long long)n_cells};
+    ValidateOut hv = {0, 0, (long long)n_cells, 0ull, ~0ull};
     SETUP_CUDA(cudaMemcpyAsync(dv, &hv, sizeof(hv), cudaMemcpyHostToDevice, s));
     MeshView v = m->view();
     v.mat = mat;
@@ -406,15 +478,24 @@ static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cel
       SETUP_TRY(colour_elements(m, s));
       if (npe == 27 && phys_is_laplace(physics)) {
         // the auto variant uses the Q2 partial assembly when it takes at most a quarter of the
-        // free memory
+        // device's total memory (a function of the mesh and the device model); if the allocation
+        // fails all the same, the mesh keeps the reference kernel (flag bit 3 reports it)
         size_t free_b = 0, total_b = 0;
         SETUP_CUDA(cudaMemGetInfo(&free_b, &total_b));
-        if ((double)n_cells * 27 * 6 * sizeof(double) <= 0.25 * (double)free_b) SETUP_TRY(q2_pa_setup(m, s));
+        if ((double)n_cells * 27 * 6 * sizeof(double) <= 0.25 * (double)total_b) {
+          st = q2_pa_setup(m, s);
+          if (st != MF_OK && st != MF_ERR_OOM) goto fail;
+          st = MF_OK;
+          mf_clear_error();
+        }
       }
     } else {
       m->n_colours = 8;  // parity colouring of the box
-      SETUP_TRY(tile_setup(m, s));
-      SETUP_TRY(gen_setup(m, s));
+      SETUP_TRY(dw_range_setup(m, hv.det_max, hv.det_min, s));
+      if (m->dw_ok) {
+        SETUP_TRY(tile_setup(m, s));
+        SETUP_TRY(gen_setup(m, s));
+      }
     }
     SETUP_CUDA(cudaStreamSynchronize(s));
   }
@@ -463,7 +544,7 @@ extern "C" mf_status mf_mesh_query(const mf_mesh *m, int64_t *n_nodes, int64_t *
   if (n_colours) *n_colours = m->n_colours;
   if (flags)
     *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0) | (m->pa || m->q2pa ? 8 : 0) |
-             (m->npe == 4 ? 16 : 0) | (m->npe == 27 ? 32 : 0);
+             (m->npe == 4 ? 16 : 0) | (m->npe == 27 ? 32 : 0) | (m->structured && !m->dw_ok ? 64 : 0);
   return MF_OK;
 }
 
@@ -480,7 +561,8 @@ extern "C" mf_status mf_set_apply_variant(mf_mesh *m, int variant) {
   if (variant == MF_VARIANT_GENERAL || variant == MF_VARIANT_PARTIAL) {
     if (!m->gen) {
       mf_set_error("mf_set_apply_variant: the general and partial-assembly variants need a structured mesh that is "
-                   "not a tensor-product grid");
+                   "not a tensor-product grid, with cell constants and cell sizes within the double-word range "
+                   "(flag bit 6 of mf_mesh_query set means they are not)");
       return MF_ERR_UNSUPPORTED;
     }
   }

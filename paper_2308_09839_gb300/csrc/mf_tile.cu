@@ -27,7 +27,7 @@ __global__ void tp_check(const double *X, int nx, int ny, int nz, int *not_tp) {
 }
 
 // Spacing h and 1/h of every cell along each axis, as (hi, lo) pairs.
-__global__ void tp_axes(const double *X, int nx, int ny, int nz, float2 *out) {
+__global__ void tp_axes(const double *X, int nx, int ny, int nz, double geo, float2 *out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = nx + ny + nz;
   if (t >= n) return;
@@ -44,16 +44,16 @@ __global__ void tp_axes(const double *X, int nx, int ny, int nz, float2 *out) {
     a = X[3 * (int64_t)(nx + 1) * (ny + 1) * k + 2];
     b = X[3 * (int64_t)(nx + 1) * (ny + 1) * (k + 1) + 2];
   }
-  const double h = b - a;
+  const double h = (b - a) * geo;  // normalised spacing (geo is a power of two)
   const dw hh = dwa::from_double_slow(h), ih = dwa::from_double_slow(1.0 / h);
   out[t] = make_float2(hh.h, hh.l);
   out[n + t] = make_float2(ih.h, ih.l);
 }
 
-__global__ void mat_pairs(const double *m, int64_t n, float2 *out) {
+__global__ void mat_pairs(const double *m, int64_t n, double scale, float2 *out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const dw v = dwa::from_double_slow(m[i]);
+  const dw v = dwa::from_double_slow(m[i] * scale);  // normalised cell constant (scale: power of two)
   out[i] = make_float2(v.h, v.l);
 }
 
@@ -73,10 +73,10 @@ mf_status tile_setup(mf_mesh *m, cudaStream_t s) {
   if (h) return MF_OK;
   const int n = m->nx + m->ny + m->nz;
   MF_CUDA(cudaMalloc(&m->tp_axis, 2 * n * sizeof(float2)));
-  tp_axes<<<blocks_for(n), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->tp_axis);
+  tp_axes<<<blocks_for(n), kThreads, 0, s>>>(m->X, m->nx, m->ny, m->nz, m->dw_geo, m->tp_axis);
   const int64_t nm = m->n_cells * phys_nmat(m->physics);
   MF_CUDA(cudaMalloc(&m->mat_pairs, nm * sizeof(float2)));
-  mat_pairs<<<blocks_for(nm), kThreads, 0, s>>>(m->mat, nm, m->mat_pairs);
+  mat_pairs<<<blocks_for(nm), kThreads, 0, s>>>(m->mat, nm, m->dw_mat, m->mat_pairs);
   MF_CUDA(cudaGetLastError());
   MF_CUDA(cudaStreamSynchronize(s));
   m->tp = true;

@@ -204,6 +204,7 @@ struct TileArgs {
   const float2 *hx, *hy, *hz, *ihx, *ihy, *ihz;  // per-axis spacings and inverses (pairs)
   const float2 *mat;                             // kappa[E] or (lam, mu)[E] as pairs
   const uint8_t *dmask;
+  int oscale;  // y = 2^oscale x (operator of the normalised cell constants and spacings) x
 };
 
 // Segment length from a wave model: with R CTAs resident at a time, nseg segments of seg = ceil((nz
@@ -226,7 +227,7 @@ inline int wave_segment(int cols, int nzp1, int resident_total) {
 }
 
 // Grid decomposition of a structured mesh into tile columns and z-segments of `seg` node planes
-// (seg <= 0: by the wave model for `resident` CTAs per SM on 152 SMs and `batch` launches' worth
+// (seg <= 0: by the wave model for `resident` CTAs per SM on the device's SMs and `batch` launches' worth
 // of columns (right-hand sides), or, without an occupancy figure, enough segments for about four
 // CTAs per SM).
 inline TileArgs make_tile_args(const mf_mesh *m, int EX, int EY, int seg, int resident = 0, int batch = 1) {
@@ -240,9 +241,9 @@ inline TileArgs make_tile_args(const mf_mesh *m, int EX, int EY, int seg, int re
   if (seg <= 0) {
     const int cols = g.tiles_x * g.tiles_y;
     if (resident > 0) {
-      seg = wave_segment(cols * batch, m->nz + 1, 152 * resident);
+      seg = wave_segment(cols * batch, m->nz + 1, device_sm_count() * resident);
     } else {
-      const int target = 152 * 4;
+      const int target = device_sm_count() * 4;
       const int nseg = std::max(1, std::min(m->nz + 1, (target + cols - 1) / cols));
       seg = (m->nz + 1 + nseg - 1) / nseg;
     }
@@ -257,6 +258,7 @@ inline TileArgs make_tile_args(const mf_mesh *m, int EX, int EY, int seg, int re
   g.ihz = m->tp_axis + n + m->nx + m->ny;
   g.mat = m->mat_pairs;
   g.dmask = m->dmask;
+  g.oscale = m->dw_oscale;
   g.nrhs = 1;
   g.r0 = 0;
   return g;

@@ -38,25 +38,26 @@ def node_logk(p) -> np.ndarray:
     return (s / c).reshape(-1).astype(np.float32)
 
 
-def generate_pairs(mesh: mf.Mesh, p, n_pairs: int, seed: int = 0, k_range=(2, 150), smooth: int = 2):
+def generate_pairs(mesh: mf.Mesh, p, n_pairs: int, seed: int = 0, k_range=(2, 150), smooth: int = 2,
+                   keep_states: bool = False):
     """Training pairs on the device (float32 [n_pairs][n_nodes] each) and the output scale c.
 
     For a seeded random exact solution x* (white noise from a seeded device generator, smoothed 0 to
-    `smooth` times by a 7-point average), b = A x* and the FP64 Jacobi-preconditioned CG solver
-    runs k iterations (k log-uniform in k_range); with r = b - A x_k, e = x* - x_k and D = diag(A) the
-    pair is input D^{-1/2} r / s and target D^{1/2} e c / s, s = RMS(D^{-1/2} r) (the symmetrically
-    scaled system's residual and error).  c makes the targets O(1)."""
+    `smooth` times by a periodic 7-point average: a random input field, not part of the method),
+    b = A x* and the FP64 Jacobi-preconditioned CG solver runs k iterations (k log-uniform in
+    k_range).  The library then forms (mf_training_pair) r = b - A x_k and e = x* - x_k in FP64 and,
+    with D = diag(A), the pair D^-1/2 r / s -> D^1/2 e / s, s = RMS(D^-1/2 r) (the symmetrically
+    scaled system's residual and error).  The targets are finally multiplied by c, the median of
+    RMS(D^-1/2 r) / RMS(D^1/2 e) over the pairs, which makes them O(1).  keep_states: also return the
+    (x*, x_k) of every pair (for tests)."""
     rng = np.random.default_rng(seed)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
     n = p.n_dof
     dmask = torch.from_numpy(p.dirichlet.astype(bool)).cuda()
-    diag = torch.empty(n, dtype=torch.float64, device="cuda")
-    mf.mf_operator_diagonal(mesh, diag)
-    sq = torch.sqrt(diag)
     R = torch.empty(n_pairs, n, dtype=torch.float32, device="cuda")
     T = torch.empty(n_pairs, n, dtype=torch.float32, device="cuda")
-    ratios = []
+    ratios, states = [], []
     nzyx = (p.nz + 1, p.ny + 1, p.nx + 1)
     for i in range(n_pairs):
         xs = torch.randn(nzyx, dtype=torch.float64, device="cuda", generator=gen)
@@ -70,16 +71,14 @@ def generate_pairs(mesh: mf.Mesh, p, n_pairs: int, seed: int = 0, k_range=(2, 15
         # a fixed graph block of 16 iterations (the device-side iteration limit stops at k), so one
         # captured graph serves every pair
         xk, _ = mesh.cg(b, max_iter=k, rtol=1e-14, check_every=16, precond=mf.MF_PC_JACOBI)
-        r = (b - mesh.apply(xk)) / sq
-        e = (xs - xk) * sq
-        r[dmask] = 0.0
-        e[dmask] = 0.0
-        s = torch.sqrt(torch.mean(r * r)).item()
-        ratios.append(s / max(torch.sqrt(torch.mean(e * e)).item(), 1e-300))
-        R[i] = (r / s).float()
-        T[i] = (e / s).float()
+        rr, ee = mf.mf_training_pair(mesh, b, xs, xk, R[i], T[i])
+        ratios.append(math.sqrt(rr) / max(math.sqrt(ee), 1e-300))
+        if keep_states:
+            states.append((xs.clone(), xk.clone()))
     c = float(np.median(ratios))
     T *= c
+    if keep_states:
+        return R, T, c, states
     return R, T, c
 
 

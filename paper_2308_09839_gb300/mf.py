@@ -91,6 +91,7 @@ _SIGS = {
     "mf_grid_restrict": (C.c_int, [vp, i32, i32, i32, i32, vp, C.c_float, vp]),
     "mf_grid_prolong": (C.c_int, [vp, i32, i32, i32, i32, vp, C.c_float, vp]),
     "mf_operator_diagonal": (C.c_int, [vp, vp, vp]),
+    "mf_training_pair": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp]),
     "mf_kernel_launches": (i64, []),
     "mf_last_error": (C.c_char_p, []),
     "mf_version": (C.c_char_p, []),
@@ -383,6 +384,14 @@ class Net:
 
 def mf_operator_diagonal(h, diag, stream=None) -> None:
     check(lib.mf_operator_diagonal(h.h if isinstance(h, Mesh) else h, _ptr(diag), _stream(stream)), "mf_operator_diagonal")
+
+
+def mf_training_pair(h, b, xs, xk, r32, e32, r64=None, e64=None, stream=None):
+    """One training pair (see mf.h); returns (sum r~^2, sum e~^2)."""
+    sums = (C.c_double * 2)()
+    check(lib.mf_training_pair(h.h if isinstance(h, Mesh) else h, _ptr(b), _ptr(xs), _ptr(xk), _ptr(r64), _ptr(e64),
+                               _ptr(r32), _ptr(e32), sums, _stream(stream)), "mf_training_pair")
+    return float(sums[0]), float(sums[1])
 
 
 def mf_kernel_launches() -> int:

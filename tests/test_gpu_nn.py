@@ -22,8 +22,15 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
 
 
-SHAPES = [((5, 7, 9), 2, 16), ((4, 4, 8), 16, 16), ((9, 6, 11), 16, 32), ((5, 5, 5), 32, 64),
-          ((3, 9, 10), 64, 64), ((6, 5, 7), 64, 32), ((7, 7, 7), 32, 16), ((9, 9, 9), 16, 1), ((4, 5, 3), 3, 5)]
+SMALL = [((5, 7, 9), 2, 16), ((4, 4, 8), 16, 16), ((9, 6, 11), 16, 32), ((5, 5, 5), 32, 64),
+         ((3, 9, 10), 64, 64), ((6, 5, 7), 64, 32), ((7, 7, 7), 32, 16), ((9, 9, 9), 16, 1), ((4, 5, 3), 3, 5)]
+# Node grids of the network's levels at sizes where the convolution kernels' persistent CTAs each
+# loop over several work items (more output tiles than CTAs resident on the GPU), so that resident
+# weights, re-staged halos and the per-item barriers are compared with the oracle too; 41^3 x 64 -> 64
+# takes the path that stages the weights in groups of taps.
+LARGE = [((65, 65, 65), 2, 16), ((65, 65, 65), 16, 16), ((65, 65, 65), 16, 1), ((33, 33, 33), 16, 32),
+         ((33, 33, 33), 32, 64), ((41, 41, 41), 64, 64), ((33, 33, 33), 64, 32), ((49, 49, 49), 32, 16)]
+SHAPES = SMALL + LARGE
 
 
 @pytest.mark.parametrize("dims,cin,cout", SHAPES)
@@ -188,3 +195,44 @@ def test_fcg_with_zero_network_matches_oracle_fcg_m():
     assert info.rel_res_true <= 1.05e-8 and h_o[-1] <= 1e-8
     assert rel(x.cpu().numpy(), xo) <= 1e-6
     net.close()
+
+
+def test_training_pairs_match_oracle():
+    """The training pairs of the learned preconditioner against the oracle: in FP64 before any
+    scaling the pair satisfies A e = r with the oracle's A; r~ = D^-1/2 (b - A x_k) and
+    e~ = D^1/2 (x* - x_k) with the oracle's diagonal; the FP32 pairs the workflow stores are r~/s and
+    c e~/s with s = RMS(r~) and c the median ratio RMS(r~)/RMS(e~), to FP32 rounding."""
+    from oracle import fem
+    from paper_2308_09839_gb300 import inputs, learned
+    p = inputs.laplace_box(16, ny=12, nz=9, sigma=1.0, layered=True, seed=2)
+    mesh = mf.Mesh.from_problem(p)
+    R, T, c, states = learned.generate_pairs(mesh, p, 5, seed=3, k_range=(2, 40), keep_states=True)
+    torch.cuda.synchronize()
+    A = fem.assemble_csr(p.physics, p.coords, p.cell_array(), p.mat, p.dirichlet, p.n_nodes)
+    D = fem.diagonal(p.physics, p.coords, p.cell_array(), p.mat, p.dirichlet, p.n_nodes)
+    free = p.dirichlet == 0
+    ratios = []
+    for i, (xs_d, xk_d) in enumerate(states):
+        xs, xk = xs_d.cpu().numpy(), xk_d.cpu().numpy()
+        b_d = mesh.apply(xs_d)
+        r64 = torch.empty_like(xs_d)
+        e64 = torch.empty_like(xs_d)
+        r32 = torch.empty(p.n_dof, dtype=torch.float32, device="cuda")
+        e32 = torch.empty_like(r32)
+        sr, se = mf.mf_training_pair(mesh, b_d, xs_d, xk_d, r32, e32, r64=r64, e64=e64)
+        r64, e64 = r64.cpu().numpy(), e64.cpu().numpy()
+        # the defining identity, unscaled: A e = r on the free DoFs
+        r_un, e_un = r64 * np.sqrt(D), e64 / np.sqrt(D)
+        assert rel(r_un[free], (A @ e_un)[free]) <= 1e-12
+        r_ref = np.where(free, (A @ xs - A @ xk) / np.sqrt(D), 0.0)
+        e_ref = np.where(free, (xs - xk) * np.sqrt(D), 0.0)
+        assert rel(r64, r_ref) <= 1e-12 and rel(e64, e_ref) <= 1e-14
+        assert abs(sr - (r_ref ** 2).sum()) <= 1e-12 * sr and abs(se - (e_ref ** 2).sum()) <= 1e-12 * se
+        s = np.sqrt(np.mean(r_ref ** 2))
+        ratios.append(s / np.sqrt(np.mean(e_ref ** 2)))
+        tol = lambda v: 2.0 ** -23 * np.abs(v) + 1e-30
+        assert np.all(np.abs(r32.cpu().numpy() - r_ref / s) <= tol(r_ref / s))
+        assert np.all(np.abs(R[i].cpu().numpy() - r_ref / s) <= tol(r_ref / s))
+        ti = e_ref / s
+        assert np.all(np.abs(T[i].cpu().numpy() / c - ti) <= 2 * tol(ti))
+    assert abs(c - float(np.median(ratios))) <= 1e-10 * c

@@ -178,6 +178,29 @@ def test_cg_small_laplace_matches_oracle(op):
     assert rel2(x, xo) <= 1e-5
 
 
+def test_cg_csr_graph_after_destroy_and_reassemble():
+    """A CG graph captured for one assembled matrix must never be replayed for another.  Solve with a
+    CSR, destroy it (its handle's host address may then be reused by the next one), fill the freed
+    device memory with NaN through another allocation, assemble a new matrix and solve again: the
+    second solve must use the new matrix and match the oracle."""
+    p = inputs.small_laplace_16(seed=0)
+    A, b, xo, it_o = _oracle_cg(p)
+    mesh = mf.Mesh.from_problem(p)
+    fillers = []
+    for _ in range(3):
+        csr = mesh.assemble_csr()
+        x, info = mesh.cg(gpu(b), csr=csr, check_every=8)
+        torch.cuda.synchronize()
+        assert info.status == mf.MF_OK
+        assert abs(info.iters - it_o) <= max(2, math.ceil(0.01 * it_o)), (info.iters, it_o)
+        assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.05e-8 * np.linalg.norm(b)
+        assert rel2(x.cpu().numpy(), xo) <= 1e-5
+        nbytes = csr.info["nnz"] * 12 + (csr.info["n_rows"] + 1) * 8
+        csr.close()
+        fillers.append(torch.full((2 * nbytes // 8,), float("nan"), dtype=torch.float64, device=DEV))
+        torch.cuda.synchronize()
+
+
 def test_cg_elasticity_matches_oracle():
     p = inputs.elasticity_box(8, jitter=0.2, seed=13)
     A, b, xo, it_o = _oracle_cg(p)
