@@ -179,6 +179,29 @@ __device__ __forceinline__ dw split_scaled(double x, int s) {
   return dw{__uint_as_float(hb), __uint_as_float(__float_as_uint(lo) | sign)};
 }
 
+// split(x * 2^-s) for any s, one code path: s = 0 gives exactly split(x).  With s != 0, values
+// below 2^-74 after the scaling become zero (see split_scaled).
+__device__ __forceinline__ dw split_shift(double x, int s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const int es = e - s;
+  if ((e != 0 && (es < 949 || es > 1150)) || (e == 0 && s != 0)) {
+    const double xs = s == 0 ? x : ldexp_exact(x, -s);
+    if (s != 0 && !(fabs(xs) >= 0x1p-74) && xs == xs)
+      return dw{__uint_as_float((unsigned)(b >> 32) & 0x80000000u), 0.0f};
+    const float h = __double2float_rz(xs);
+    return dw{h, __double2float_rn(xs - (double)h)};
+  }
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  const unsigned sign = bh & 0x80000000u;
+  const unsigned mhi = ((bh & 0x000fffffu) << 3) | (bl >> 29);
+  const unsigned hb = sign | ((unsigned)(es - 1023 + 127) << 23) | mhi;
+  const unsigned rem = bl & 0x1fffffffu;
+  const float lo = __fmul_rn(__uint2float_rn(rem), __uint_as_float((unsigned)(es - 1075 + 127) << 23));
+  const unsigned lb = __float_as_uint(lo) | sign;
+  return dw{__uint_as_float(e == 0 ? sign : hb), __uint_as_float(e == 0 ? sign : lb)};
+}
+
 // Magnitude record of the inputs a thread has read, in one register: the largest high word of |x|
 // (exponent and leading mantissa bits, ordered like |x|), with bit 0 also set for any input whose
 // low word is non-zero (so that inputs below 2^-1042, whose high word is zero, still count).

@@ -22,16 +22,19 @@
 //    voxels, ldmatrix.trans fragments, FP32 accumulation), partial sums per CTA reduced in fixed
 //    order (deterministic).
 //  * restrict / prolong (and their adjoints as scaled prolong / restrict), relu masks, loss, Adam.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <random>
 #include <vector>
 
 #include "mf_internal.cuh"
+#include "mf_umma.cuh"
 
 typedef __nv_bfloat16 bf16;
 
@@ -228,8 +231,616 @@ mf_status launch_conv_t(ConvArgs a, cudaStream_t s) {
   return MF_OK;
 }
 
+// ------------------------------------------------------------ tcgen05 implicit-GEMM convolution ----
+// The same convolution on the 5th-generation tensor cores, for 16, 32 or 64 input channels.
+//
+// Work item: 8 (x) x 16 (y) x TZ (z) output voxels.  The item's input halo of 10 x 18 x (TZ + 2)
+// voxels arrives by one TMA tensor load, in the shared-memory order [z][channel chunk][y][x][8
+// channels] (a 5-D tensor map over the channels-last input whose chunk dimension has a 16-byte
+// stride), with zeros outside the grid.  In that order the 8 voxels of an x-row of the tile form a
+// 128-byte core matrix of the no-swizzle K-major layout for every channel chunk, so the A operand of
+// tap (dx, dy, dz) for output plane z is the halo itself at a byte offset: MMA row m = x + 8 y reads
+// halo voxel (x + dx, y + dy, z + dz), with rows grouped in eights 160 bytes apart (one halo y-row)
+// and channel chunks 2880 bytes apart.  No im2col copy is made.  The weights of all taps (or of 9 at a
+// time when they do not fit) are stored by the threads in the same canonical layout ([tap][channel
+// chunk][output channel][8]).  One thread issues tcgen05.mma M = 128, N = output channels, K = 16
+// for every (plane, tap, channel pair), accumulating in tensor memory (one 128 x N FP32 accumulator
+// per output plane); tcgen05.commit signals an mbarrier, and the four warps read the accumulators
+// back (warp w: tile rows 32 w .. 32 w + 31) and apply bias, skip, ReLU and the BF16/FP32 stores.
+// Waits are bounded: on a timeout the kernel records an error in tc_status and stops.
+constexpr int kTcThreads = 128;
+
+// The tcgen05 path is the default; MF_CONV_MMA_SYNC=1 in the environment selects the mma.sync
+// kernel instead (for comparisons).
+static bool conv_tc_enabled() {
+  static const bool on = [] {
+    const char *e = getenv("MF_CONV_MMA_SYNC");
+    return !(e && e[0] == '1');
+  }();
+  return on;
+}
+constexpr int TXt = 8, TYt = 16, HXt = TXt + 2, HYt = TYt + 2;
+constexpr int kTcYS = HXt * 16, kTcKCS = HYt * kTcYS;  // halo byte strides: y-row, channel chunk
+constexpr long long kTcBudget = 1ll << 31;             // clock cycles per wait (about one second)
+
+__device__ int tc_status;  // nonzero after a timed-out wait (read by the network's synchronous calls)
+
+template <int CKP, int CN>
+struct TcCfg {
+  static constexpr int KC = CKP / 8;                 // channel chunks
+  static constexpr int TZ = CKP == 64 ? 2 : 4;        // output planes per item
+  static constexpr int HZ = TZ + 2;
+  static constexpr int ZS = KC * kTcKCS;              // halo byte stride of a z-plane
+  static constexpr int HALO = HZ * ZS;                // halo bytes
+  static constexpr int TAPB = CKP * CN * 2;           // weight bytes per tap
+  static constexpr int G = (HALO + 27 * TAPB <= 200 * 1024) ? 27 : 9;  // taps staged at once
+  static constexpr int SMEM = 1024 + HALO + G * TAPB; // + alignment slack
+  static constexpr int COLS = TZ * CN <= 32 ? 32 : TZ * CN <= 64 ? 64 : TZ * CN <= 128 ? 128 : 256;
+};
+
+struct TcArgs {
+  int nx, ny, nz, ck, cn, relu;
+  const bf16 *w;
+  const float *bias;
+  const bf16 *skip;
+  bf16 *out_bf;
+  float *out_f;
+  int tiles_x, tiles_y, tiles;
+  int vec_out;  // cn == CN and 16-byte aligned output / skip: vector epilogue
+};
+
+template <int CKP, int CN, int MODE>
+__global__ void __launch_bounds__(kTcThreads) conv_tc(TcArgs a, const __grid_constant__ CUtensorMap tmap) {
+  using Cfg = TcCfg<CKP, CN>;
+  constexpr int KC = Cfg::KC, TZ = Cfg::TZ, G = Cfg::G, NG = 27 / G, KS = CKP / 16;
+  constexpr uint32_t IDESC = umma::idesc_bf16(128, CN);
+  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+  __shared__ __align__(8) uint64_t halo_bar, mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  // 1024-byte aligned halo, weights after it
+  unsigned char *base = tc_smem_raw + ((1024 - (umma::smem_u32(tc_smem_raw) & 1023)) & 1023);
+  unsigned char *halo = base;
+  unsigned char *wsm = base + Cfg::HALO;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    umma::mbar_init(&halo_bar, 1);
+    umma::mbar_init(&mma_bar, 1);
+    umma::mbar_init_fence();
+    abort_flag = 0;
+  }
+  if (warp == 0) umma::tmem_alloc(&tmem_slot, Cfg::COLS);
+  // weights of taps [t0, t0 + G) in the canonical K-major layout: 16 bytes = 8 input channels of one
+  // output channel; zero beyond the real channel counts
+  auto stage_w = [&](int t0) {
+    for (int idx = tid; idx < G * KC * CN; idx += kTcThreads) {
+      const int n = idx % CN, kc = (idx / CN) % KC, tl = idx / (CN * KC), tap = t0 + tl;
+      __align__(16) bf16 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k = kc * 8 + j;
+        bf16 e = __float2bfloat16(0.0f);
+        if (k < a.ck && n < a.cn) {
+          if (MODE == 0) e = a.w[((int64_t)tap * a.ck + k) * a.cn + n];
+          else e = a.w[((int64_t)(26 - tap) * a.cn + n) * a.ck + k];
+        }
+        v[j] = e;
+      }
+      *reinterpret_cast<uint4 *>(wsm + (size_t)tl * Cfg::TAPB + ((size_t)kc * CN + n) * 16) =
+          *reinterpret_cast<const uint4 *>(v);
+    }
+  };
+  if (G == 27) stage_w(0);
+  umma::fence_proxy_async_smem();
+  umma::tc_fence_before_sync();
+  __syncthreads();
+  umma::tc_fence_after_sync();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t halo_a = umma::smem_u32(halo), w_a = umma::smem_u32(wsm);
+  uint32_t halo_phase = 0, mma_phase = 0;
+
+  auto wait_all = [&](uint64_t *bar, uint32_t &phase) {  // every thread waits; a timeout aborts the CTA
+    if (!umma::mbar_wait(bar, phase, kTcBudget)) {
+      abort_flag = 1;
+      atomicExch(&tc_status, 1);
+    }
+    phase ^= 1u;
+  };
+
+  for (int item = blockIdx.x; item < a.tiles; item += gridDim.x) {
+    const int bx = item % a.tiles_x, by = (item / a.tiles_x) % a.tiles_y, bz = item / (a.tiles_x * a.tiles_y);
+    const int x0 = bx * TXt, y0 = by * TYt, z0 = bz * TZ;
+    if (tid == 0) {
+      umma::mbar_arrive_expect_tx(&halo_bar, Cfg::HALO);
+      umma::tma_load_5d(halo, &tmap, &halo_bar, 0, x0 - 1, y0 - 1, 0, z0 - 1);
+    }
+    for (int gi = 0; gi < NG; ++gi) {
+      if (NG > 1) {
+        if (gi > 0) wait_all(&mma_bar, mma_phase);  // the previous group's MMAs no longer read wsm
+        __syncthreads();
+        if (abort_flag) break;
+        stage_w(gi * G);
+        umma::fence_proxy_async_smem();
+        __syncthreads();
+      }
+      if (gi == 0) wait_all(&halo_bar, halo_phase);
+      __syncthreads();
+      if (abort_flag) break;
+      if (tid == 0) {
+        umma::tc_fence_after_sync();
+#pragma unroll 1
+        for (int tl = 0; tl < G; ++tl) {
+          const int tap = gi * G + tl, dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+#pragma unroll 1
+          for (int zi = 0; zi < TZ; ++zi)
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+              const uint32_t aa = halo_a + (uint32_t)((zi + dz) * Cfg::ZS + 2 * ks * kTcKCS + dy * kTcYS + dx * 16);
+              const uint32_t ba = w_a + (uint32_t)(tl * Cfg::TAPB + 2 * ks * CN * 16);
+              umma::mma_bf16(tmem + (uint32_t)(zi * CN), umma::sdesc(aa, kTcKCS, kTcYS), umma::sdesc(ba, CN * 16, 128),
+                             IDESC, (tap > 0 || ks > 0) ? 1u : 0u);
+            }
+        }
+        umma::mma_commit(&mma_bar);
+      }
+    }
+    if (abort_flag) break;
+    wait_all(&mma_bar, mma_phase);  // every MMA of the item is complete
+    __syncthreads();
+    if (abort_flag) break;
+    umma::tc_fence_after_sync();
+    // epilogue: warp w holds tile rows m = 32 w + lane, i.e. x = m % 8, y = m / 8
+    const int m = 32 * warp + lane, gx = x0 + (m & 7), gy = y0 + (m >> 3);
+#pragma unroll 1
+    for (int zi = 0; zi < TZ; ++zi) {
+      const int gz = z0 + zi;
+      const bool in = gx < a.nx && gy < a.ny && gz < a.nz;
+      const int64_t vox = ((int64_t)gz * a.ny + gy) * a.nx + gx;
+#pragma unroll
+      for (int c0 = 0; c0 < CN; c0 += 16) {
+        float v[16];
+        umma::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(zi * CN + c0), v);
+        if (!in) continue;
+        if (MODE == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = c0 + j;
+            if (n < a.cn) {
+              if (a.bias) v[j] += __ldg(a.bias + n);
+              if (a.skip && !a.vec_out) v[j] += __bfloat162float(a.skip[vox * a.cn + n]);
+            }
+          }
+          if (a.skip && a.vec_out) {
+            const uint4 *sp = reinterpret_cast<const uint4 *>(a.skip + vox * CN + c0);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint4 u = __ldg(sp + h);
+              const __nv_bfloat162 *q = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const float2 f = __bfloat1622float2(q[j]);
+                v[8 * h + 2 * j] += f.x;
+                v[8 * h + 2 * j + 1] += f.y;
+              }
+            }
+          }
+          if (a.relu)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
+        }
+        if (a.vec_out) {
+          if (a.out_bf) {
+            __align__(16) __nv_bfloat162 q[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) q[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            uint4 *op = reinterpret_cast<uint4 *>(a.out_bf + vox * CN + c0);
+            op[0] = reinterpret_cast<const uint4 *>(q)[0];
+            op[1] = reinterpret_cast<const uint4 *>(q)[1];
+          }
+          if (a.out_f) {
+            float4 *op = reinterpret_cast<float4 *>(a.out_f + vox * CN + c0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) op[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = c0 + j;
+            if (n < a.cn) {
+              if (a.out_bf) a.out_bf[vox * a.cn + n] = __float2bfloat16(v[j]);
+              if (a.out_f) a.out_f[vox * a.cn + n] = v[j];
+            }
+          }
+        }
+      }
+    }
+    umma::tc_fence_before_sync();
+    __syncthreads();  // accumulators read before the next item's MMAs overwrite them
+  }
+  // a CTA that gave up still owns the copies and MMAs it issued: wait for them (bounded) so that
+  // nothing writes this CTA's shared or tensor memory after it exits
+  if (abort_flag && tid == 0) {
+    umma::mbar_wait(&halo_bar, halo_phase, kTcBudget);
+    umma::mbar_wait(&mma_bar, mma_phase, kTcBudget);
+  }
+  umma::tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, Cfg::COLS);
+}
+
+// Pipelined form of conv_tc for the shapes whose 27 taps of weights fit in shared memory next to one
+// or two halo buffers.  Warp-specialised: warp 0 loads the halos of the CTA's items by TMA into a
+// ring of NS buffers; warp 1 issues the MMAs of an item into one of two accumulator sets in tensor
+// memory, as soon as its halo has arrived and the epilogue has released that set, and commits to
+// the halo's "empty" and the set's "full" barrier; warps 2-5 drain the accumulators (warp w: tile
+// rows 32 (w % 4) .. + 31, its tensor-memory lane quarter) while the next item's loads and MMAs run.
+// Per item the planes TZ and the stages NS are the largest that fit.
+constexpr int kTcpThreads = 192;
+
+template <int CKP, int CN>
+struct TcpCfg {
+  static constexpr int KC = CKP / 8;
+  static constexpr int TAPB = CKP * CN * 2;
+  static constexpr int W = 27 * TAPB;
+  static constexpr int LIMIT = 220 * 1024;
+  static constexpr int halo(int tz) { return (tz + 2) * KC * kTcKCS; }
+  static constexpr int TZ = (2 * halo(4) + W <= LIMIT)   ? 4
+                            : (2 * halo(2) + W <= LIMIT) ? 2
+                            : (2 * halo(1) + W <= LIMIT) ? 1
+                            : (halo(2) + W <= LIMIT)     ? 2
+                                                         : 1;
+  static constexpr int NS = (2 * halo(TZ) + W <= LIMIT) ? 2 : 1;
+  static constexpr int HALO = halo(TZ);
+  static constexpr bool FITS = NS * HALO + W <= LIMIT;
+  static constexpr int ZS = KC * kTcKCS;
+  static constexpr int SMEM = 1024 + NS * HALO + W;
+  static constexpr int ACC = TZ * CN;  // columns of one accumulator set
+  static constexpr int COLS = 2 * ACC <= 32 ? 32 : 2 * ACC <= 64 ? 64 : 2 * ACC <= 128 ? 128 : 2 * ACC <= 256 ? 256 : 512;
+};
+
+template <int CKP, int CN, int MODE>
+__global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_constant__ CUtensorMap tmap) {
+  using Cfg = TcpCfg<CKP, CN>;
+  constexpr int KC = Cfg::KC, TZ = Cfg::TZ, NS = Cfg::NS, KS = CKP / 16, ACC = Cfg::ACC;
+  constexpr uint32_t IDESC = umma::idesc_bf16(128, CN);
+  extern __shared__ __align__(16) unsigned char tcp_smem_raw[];
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  unsigned char *base = tcp_smem_raw + ((1024 - (umma::smem_u32(tcp_smem_raw) & 1023)) & 1023);
+  unsigned char *wsm = base + NS * Cfg::HALO;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  volatile int *abort_v = &abort_flag;
+
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) {
+      umma::mbar_init(&full[i], 1);
+      umma::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      umma::mbar_init(&accf[i], 1);
+      umma::mbar_init(&acce[i], 4);
+    }
+    umma::mbar_init_fence();
+    abort_flag = 0;
+  }
+  if (warp == 1) umma::tmem_alloc(&tmem_slot, Cfg::COLS);
+  for (int idx = tid; idx < 27 * KC * CN; idx += kTcpThreads) {  // all weights, canonical K-major
+    const int n = idx % CN, kc = (idx / CN) % KC, tap = idx / (CN * KC);
+    __align__(16) bf16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = kc * 8 + j;
+      bf16 e = __float2bfloat16(0.0f);
+      if (k < a.ck && n < a.cn) {
+        if (MODE == 0) e = a.w[((int64_t)tap * a.ck + k) * a.cn + n];
+        else e = a.w[((int64_t)(26 - tap) * a.cn + n) * a.ck + k];
+      }
+      v[j] = e;
+    }
+    *reinterpret_cast<uint4 *>(wsm + (size_t)tap * Cfg::TAPB + ((size_t)kc * CN + n) * 16) =
+        *reinterpret_cast<const uint4 *>(v);
+  }
+  umma::fence_proxy_async_smem();
+  umma::tc_fence_before_sync();
+  __syncthreads();
+  umma::tc_fence_after_sync();
+  const uint32_t tmem = tmem_slot;
+  const int nloc = (int)blockIdx.x < a.tiles ? (a.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  auto fail = [&]() {
+    *abort_v = 1;
+    atomicExch(&tc_status, 1);
+  };
+  auto coords = [&](int i, int &x0, int &y0, int &z0) {
+    const int item = blockIdx.x + i * gridDim.x;
+    const int bx = item % a.tiles_x, by = (item / a.tiles_x) % a.tiles_y, bz = item / (a.tiles_x * a.tiles_y);
+    x0 = bx * TXt;
+    y0 = by * TYt;
+    z0 = bz * TZ;
+  };
+
+  if (warp == 0) {  // ------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nloc && !*abort_v; ++i) {
+        const int s = i % NS;
+        if (i >= NS && !umma::mbar_wait(&empty[s], (uint32_t)((i / NS - 1) & 1), kTcBudget)) {
+          fail();
+          break;
+        }
+        int x0, y0, z0;
+        coords(i, x0, y0, z0);
+        umma::mbar_arrive_expect_tx(&full[s], Cfg::HALO);
+        umma::tma_load_5d(base + s * Cfg::HALO, &tmap, &full[s], 0, x0 - 1, y0 - 1, 0, z0 - 1);
+        ++issued;
+      }
+      if (*abort_v)  // bounded drain of the copies this CTA still has in flight
+        for (int j = issued - 1; j >= 0 && j >= issued - NS; --j)
+          umma::mbar_wait(&full[j % NS], (uint32_t)((j / NS) & 1), kTcBudget);
+    }
+  } else if (warp == 1) {  // --------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t w_a = umma::smem_u32(wsm);
+      int done = 0;
+      for (int i = 0; i < nloc && !*abort_v; ++i) {
+        const int s = i % NS, ac = i & 1;
+        if (!umma::mbar_wait(&full[s], (uint32_t)((i / NS) & 1), kTcBudget)) {
+          fail();
+          break;
+        }
+        if (i >= 2 && !umma::mbar_wait(&acce[ac], (uint32_t)(((i >> 1) - 1) & 1), kTcBudget)) {
+          fail();
+          break;
+        }
+        umma::tc_fence_after_sync();
+        const uint32_t halo_a = umma::smem_u32(base + s * Cfg::HALO);
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+#pragma unroll
+          for (int zi = 0; zi < TZ; ++zi)
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+              const uint32_t aa = halo_a + (uint32_t)((zi + dz) * Cfg::ZS + 2 * ks * kTcKCS + dy * kTcYS + dx * 16);
+              const uint32_t ba = w_a + (uint32_t)(tap * Cfg::TAPB + 2 * ks * CN * 16);
+              umma::mma_bf16(tmem + (uint32_t)(ac * ACC + zi * CN), umma::sdesc(aa, kTcKCS, kTcYS),
+                             umma::sdesc(ba, CN * 16, 128), IDESC, (tap > 0 || ks > 0) ? 1u : 0u);
+            }
+        }
+        umma::mma_commit(&empty[s]);
+        umma::mma_commit(&accf[ac]);
+        done = i + 1;
+      }
+      if (*abort_v && done > 0)  // bounded drain of the MMAs still in flight
+        umma::mbar_wait(&accf[(done - 1) & 1], (uint32_t)(((done - 1) >> 1) & 1), kTcBudget);
+    }
+  } else {  // ----------------------------------------------------------------------- epilogue
+    const int q = warp & 3, m = 32 * q + lane;
+    for (int i = 0; i < nloc; ++i) {
+      const int ac = i & 1;
+      const bool ok = umma::mbar_wait(&accf[ac], (uint32_t)((i >> 1) & 1), kTcBudget);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) fail();
+        break;
+      }
+      if (*abort_v) break;
+      umma::tc_fence_after_sync();
+      int x0, y0, z0;
+      coords(i, x0, y0, z0);
+      const int gx = x0 + (m & 7), gy = y0 + (m >> 3);
+#pragma unroll 1
+      for (int zi = 0; zi < TZ; ++zi) {
+        const int gz = z0 + zi;
+        const bool in = gx < a.nx && gy < a.ny && gz < a.nz;
+        const int64_t vox = ((int64_t)gz * a.ny + gy) * a.nx + gx;
+#pragma unroll
+        for (int c0 = 0; c0 < CN; c0 += 16) {
+          float v[16];
+          umma::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * ACC + zi * CN + c0), v);
+          if (!in) continue;
+          if (MODE == 0) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = c0 + j;
+              if (n < a.cn) {
+                if (a.bias) v[j] += __ldg(a.bias + n);
+                if (a.skip && !a.vec_out) v[j] += __bfloat162float(a.skip[vox * a.cn + n]);
+              }
+            }
+            if (a.skip && a.vec_out) {
+              const uint4 *sp = reinterpret_cast<const uint4 *>(a.skip + vox * CN + c0);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const uint4 u = __ldg(sp + h);
+                const __nv_bfloat162 *qq = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const float2 f = __bfloat1622float2(qq[j]);
+                  v[8 * h + 2 * j] += f.x;
+                  v[8 * h + 2 * j + 1] += f.y;
+                }
+              }
+            }
+            if (a.relu)
+#pragma unroll
+              for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
+          }
+          if (a.vec_out) {
+            if (a.out_bf) {
+              __align__(16) __nv_bfloat162 qq[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) qq[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+              uint4 *op = reinterpret_cast<uint4 *>(a.out_bf + vox * CN + c0);
+              op[0] = reinterpret_cast<const uint4 *>(qq)[0];
+              op[1] = reinterpret_cast<const uint4 *>(qq)[1];
+            }
+            if (a.out_f) {
+              float4 *op = reinterpret_cast<float4 *>(a.out_f + vox * CN + c0);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) op[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = c0 + j;
+              if (n < a.cn) {
+                if (a.out_bf) a.out_bf[vox * a.cn + n] = __float2bfloat16(v[j]);
+                if (a.out_f) a.out_f[vox * a.cn + n] = v[j];
+              }
+            }
+          }
+        }
+      }
+      umma::tc_fence_before_sync();
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&acce[ac]);  // this warp's lanes of the set are free again
+    }
+  }
+  umma::tc_fence_before_sync();
+  __syncthreads();
+  umma::tc_fence_after_sync();
+  if (warp == 1) umma::tmem_dealloc(tmem, Cfg::COLS);
+}
+
+// 5-D tensor map of a channels-last BF16 tensor [nz][ny][nx][C] (C = 16, 32 or 64) for conv_tc:
+// dims (innermost first) 8 channels, x, y, channel chunk, z; strides 2C, 2C nx, 16, 2C nx ny bytes; box
+// 8 x 10 x 18 x C/8 x (TZ + 2); zeros outside.  False if the driver rejects it.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+static bool make_halo_map(CUtensorMap *map, const bf16 *in, int nx, int ny, int nz, int C, int hz) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || ((uintptr_t)in & 15) != 0) return false;
+  const cuuint64_t dims[5] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)(C / 8), (cuuint64_t)nz};
+  const cuuint64_t strides[4] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * nx, 16, (cuuint64_t)C * 2 * nx * ny};
+  const cuuint32_t box[5] = {8, (cuuint32_t)HXt, (cuuint32_t)HYt, (cuuint32_t)(C / 8), (cuuint32_t)hz};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(in), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launch the tcgen05 convolution; false (nothing launched) when the tensor map cannot be made.
+template <int CKP, int CN, int MODE>
+static bool launch_conv_tcp_t(const ConvArgs &c, cudaStream_t s, mf_status *st) {
+  using Cfg = TcpCfg<CKP, CN>;
+  CUtensorMap map;
+  if (!make_halo_map(&map, c.in, c.nx, c.ny, c.nz, CKP, Cfg::TZ + 2)) return false;
+  static std::atomic<int> resident{0};
+  auto kern = conv_tcp<CKP, CN, MODE>;
+  if (resident.load() == 0) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    int r = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, kTcpThreads, Cfg::SMEM) != cudaSuccess || r < 1) {
+      cudaGetLastError();
+      return false;
+    }
+    resident.store(std::max(1, std::min(r, 512 / Cfg::COLS)));
+  }
+  TcArgs a;
+  a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.ck = c.ck; a.cn = c.cn; a.relu = c.relu;
+  a.w = c.w; a.bias = c.bias; a.skip = c.skip; a.out_bf = c.out_bf; a.out_f = c.out_f;
+  a.tiles_x = (c.nx + TXt - 1) / TXt;
+  a.tiles_y = (c.ny + TYt - 1) / TYt;
+  a.tiles = a.tiles_x * a.tiles_y * ((c.nz + Cfg::TZ - 1) / Cfg::TZ);
+  auto al = [](const void *p) { return p == nullptr || ((uintptr_t)p & 15) == 0; };
+  a.vec_out = c.cn == CN && al(c.out_bf) && al(c.out_f) && al(c.skip);
+  const int grid = std::min(a.tiles, device_sm_count() * resident.load());
+  mf_count_launches(1);
+  kern<<<grid, kTcpThreads, Cfg::SMEM, s>>>(a, map);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mf_set_error("conv_tcp launch failed: %s", cudaGetErrorString(e));
+    *st = MF_ERR_CUDA;
+  } else {
+    *st = MF_OK;
+  }
+  return true;
+}
+
+template <int CKP, int CN, int MODE>
+static bool launch_conv_tc_t(const ConvArgs &c, cudaStream_t s, mf_status *st) {
+  if constexpr (TcpCfg<CKP, CN>::FITS) return launch_conv_tcp_t<CKP, CN, MODE>(c, s, st);
+  using Cfg = TcCfg<CKP, CN>;
+  CUtensorMap map;
+  if (!make_halo_map(&map, c.in, c.nx, c.ny, c.nz, CKP, Cfg::HZ)) return false;
+  static std::atomic<int> resident{0};
+  auto kern = conv_tc<CKP, CN, MODE>;
+  if (resident.load() == 0) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    int r = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, kTcThreads, Cfg::SMEM) != cudaSuccess || r < 1) {
+      cudaGetLastError();
+      return false;
+    }
+    // tensor memory: resident CTAs x columns must fit the 512 columns of an SM
+    resident.store(std::max(1, std::min(r, 512 / Cfg::COLS)));
+  }
+  TcArgs a;
+  a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.ck = c.ck; a.cn = c.cn; a.relu = c.relu;
+  a.w = c.w; a.bias = c.bias; a.skip = c.skip; a.out_bf = c.out_bf; a.out_f = c.out_f;
+  a.tiles_x = (c.nx + TXt - 1) / TXt;
+  a.tiles_y = (c.ny + TYt - 1) / TYt;
+  a.tiles = a.tiles_x * a.tiles_y * ((c.nz + Cfg::TZ - 1) / Cfg::TZ);
+  auto al = [](const void *p) { return p == nullptr || ((uintptr_t)p & 15) == 0; };
+  a.vec_out = c.cn == CN && al(c.out_bf) && al(c.out_f) && al(c.skip);
+  const int grid = std::min(a.tiles, device_sm_count() * resident.load());
+  mf_count_launches(1);
+  kern<<<grid, kTcThreads, Cfg::SMEM, s>>>(a, map);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mf_set_error("conv_tc launch failed: %s", cudaGetErrorString(e));
+    *st = MF_ERR_CUDA;
+  } else {
+    *st = MF_OK;
+  }
+  return true;
+}
+
+// The tcgen05 path when the input has 16, 32 or 64 channels (the tensor map's 16-byte chunks) and
+// at most 64 outputs; false otherwise (the caller then runs conv_mma).
+template <int MODE>
+static bool launch_conv_tc(const ConvArgs &c, cudaStream_t s, mf_status *st) {
+  if (!(c.ck == 16 || c.ck == 32 || c.ck == 64) || c.cn < 1 || c.cn > 64) return false;
+  const int cnp = c.cn <= 16 ? 16 : c.cn <= 32 ? 32 : 64;
+#define TCCASE(K, N) \
+  if (c.ck == K && cnp == N) return launch_conv_tc_t<K, N, MODE>(c, s, st);
+  TCCASE(16, 16) TCCASE(16, 32) TCCASE(16, 64)
+  TCCASE(32, 16) TCCASE(32, 32) TCCASE(32, 64)
+  TCCASE(64, 16) TCCASE(64, 32) TCCASE(64, 64)
+#undef TCCASE
+  return false;
+}
+
 template <int MODE>
 mf_status launch_conv(ConvArgs a, cudaStream_t s) {
+  if (conv_tc_enabled()) {
+    mf_status st = MF_OK;
+    if (launch_conv_tc<MODE>(a, s, &st)) return st;
+    if (getenv("MF_DEBUG")) fprintf(stderr, "conv: mma.sync path (mode %d, cin %d, cout %d)\n", MODE, a.ck, a.cn);
+  }
   a.tiles_x = (a.nx + TXc - 1) / TXc;
   a.tiles_y = (a.ny + TYc - 1) / TYc;
   const int ckp = a.ck <= 16 ? 16 : a.ck <= 32 ? 32 : 64;

@@ -89,17 +89,18 @@ template <int PHYS, class N>
 static mf_status march_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
                               const int *skip, int nrhs = 1) {
   using MS = march::MarchShape<PHYS, N>;
-  auto kern = march::march_apply<PHYS, N, MS::EX, MS::EY, MS::MINB>;
+  constexpr int NT = MS::EX * MS::EY / MS::RY;
+  auto kern = march::march_apply<PHYS, N, MS::EX, MS::EY, MS::RY, MS::MINB>;
   static std::atomic<int> resident{0};  // CTAs per SM: a property of the kernel, same for every caller
   if (resident.load() == 0) {
     int r = 0;
-    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, MS::EX * MS::EY, 0));
+    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, NT, 0));
     resident.store(std::max(r, 1));
   }
   TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident.load(), nrhs);
   g.nrhs = nrhs;
   g.r0 = 0;
-  kern<<<tile_items(g) * nrhs, MS::EX * MS::EY, 0, s>>>(g, x, y, skip);
+  kern<<<tile_items(g) * nrhs, NT, 0, s>>>(g, x, y, skip);
   return MF_OK;
 }
 
@@ -119,16 +120,17 @@ template <int PHYS, class N>
 static mf_status march_dot_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
                                   const int *skip, double *partials, unsigned int *ticket, double *out) {
   using MS = march::MarchShape<PHYS, N>;
-  auto kern = march::march_apply_dot<PHYS, N, MS::EX, MS::EY, MS::MINB>;
+  constexpr int NT = MS::EX * MS::EY / MS::RY;
+  auto kern = march::march_apply_dot<PHYS, N, MS::EX, MS::EY, MS::RY, MS::MINB>;
   static std::atomic<int> resident{0};
   if (resident.load() == 0) {
     int r = 0;
-    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, MS::EX * MS::EY, 0));
+    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, NT, 0));
     resident.store(std::max(r, 1));
   }
   TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident.load());
   mf_count_launches(1);
-  kern<<<tile_items(g), MS::EX * MS::EY, 0, s>>>(g, x, y, skip, partials, ticket, out);
+  kern<<<tile_items(g), NT, 0, s>>>(g, x, y, skip, partials, ticket, out);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }

@@ -163,7 +163,8 @@ def mf_mesh_query(h) -> dict:
     check(lib.mf_mesh_query(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e), C.byref(f)), "mf_mesh_query")
     return dict(n_nodes=a.value, n_cells=b.value, n_dof=c.value, n_free=d.value, n_colours=e.value,
                 structured=bool(f.value & 1), all_affine=bool(f.value & 2), tensor_product=bool(f.value & 4),
-                partial_assembly=bool(f.value & 8), tetrahedral=bool(f.value & 16), q2=bool(f.value & 32))
+                partial_assembly=bool(f.value & 8), tetrahedral=bool(f.value & 16), q2=bool(f.value & 32),
+                dw_range_exceeded=bool(f.value & 64), flags=f.value)
 
 
 def mf_set_apply_variant(h, variant: int) -> None:
