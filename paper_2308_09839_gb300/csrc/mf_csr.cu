@@ -10,6 +10,7 @@
 #include <atomic>
 #include <vector>
 
+#include "mf_dw.cuh"
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
 #include "mf_q2.cuh"
@@ -353,39 +354,89 @@ __global__ void expand_columns(int64_t n_nodes, int nd, bool blockdiag, const in
   }
 }
 
-// y = A x with L threads per row.  Each lane first issues U independent (value, column) loads,
-// then the U gathers of x, so every thread keeps several memory requests in flight; rows longer
-// than L*U continue in a plain strided loop.  Lanes are reduced by a fixed shuffle tree
-// (deterministic).
+// y = A x with L lanes per row, 16-byte loads and double-word arithmetic.  On GB300 the FP64 pipe
+// runs about 0.6 T fused multiply-adds per second, which caps an FP64 SpMV at one multiply-add per
+// stored value near 50 % of the HBM bandwidth; here every product and sum is formed on the FP32 pipes
+// in pairs of floats (the TwoProd and TwoSum error-free transformations of mf_dw.cuh), FP64-accurate
+// to about 2^-48 relative per operation.  A row any of whose products leaves the pairs' exponent
+// range (a value or x outside [2^-74, 2^127), or a product outside [2^-90, 2^90]) is summed again in
+// FP64 by one lane, so results stay FP64-accurate over FP64's whole range.
+// Lane l of a row reads the value pairs (and column pairs) a0 + 2 (l + L u), u < U, from the even
+// index a0 at or just below the row start, so that every load is aligned; entries outside the row
+// are skipped.  The arrays carry padding entries past nnz so that the pair at the end of the last
+// row stays in bounds.  Rows longer than 2 L U - 1 continue in a tail loop.  Lane sums are combined
+// by a fixed shuffle tree (deterministic).
+__device__ __forceinline__ void dw_mac(dwa::dw &acc, double v, double xv, bool &bad) {
+  unsigned ev, ex;
+  const dwa::dw a = dwa::split_fast(v, ev), b = dwa::split_fast(xv, ex);
+  const bool zero = ev == 0u || ex == 0u;  // a zero (or FP64-subnormal) factor: product zero or tiny
+  const unsigned es = ev + ex;
+  bad |= !zero && (ev < 949u || ev > 1150u || ex < 949u || ex > 1150u || es < 2046u - 90u || es > 2046u + 90u);
+  bad |= (ev == 0u && v != 0.0) || (ex == 0u && xv != 0.0);  // subnormal factors: exact in FP64 only
+  acc = dwa::add(acc, dwa::mul(a, b));
+}
+
 template <int L, int U>
-__global__ void __launch_bounds__(256) spmv_kernel(int64_t n_rows, const int64_t *__restrict__ rowptr,
-                                                   const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                   const double *__restrict__ x, double *__restrict__ y,
-                                                   const int *__restrict__ skip) {
+__global__ void __launch_bounds__(256) spmv_vec(int64_t n_rows, const int64_t *__restrict__ rowptr,
+                                                const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                const double *__restrict__ x, double *__restrict__ y,
+                                                const int *__restrict__ skip) {
   if (skip && *skip) return;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gid / L;
   const int lane = (int)(gid % L);
-  double s = 0.0;
+  dwa::dw acc{0.0f, 0.0f};
+  bool bad = false;
+  int64_t beg = 0, end = 0;
   if (row < n_rows) {
-    const int64_t beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
-    double v[U];
-    int32_t c[U];
+    beg = __ldg(rowptr + row);
+    end = __ldg(rowptr + row + 1);
+    const int64_t a0 = beg & ~(int64_t)1;
+    double2 v[U];
+    int2 c[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t p = beg + lane + (int64_t)u * L;
-      const bool ok = p < end;
-      v[u] = ok ? __ldcs(val + p) : 0.0;
-      c[u] = ok ? __ldcs(col + p) : -1;
+      const int64_t p = a0 + 2 * (lane + (int64_t)L * u);
+      if (p < end) {
+        v[u] = __ldcs(reinterpret_cast<const double2 *>(val + p));
+        c[u] = __ldcs(reinterpret_cast<const int2 *>(col + p));
+      } else {
+        v[u] = make_double2(0.0, 0.0);
+        c[u] = make_int2(0, 0);
+      }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (c[u] >= 0) s += v[u] * __ldg(x + c[u]);
-    for (int64_t p = beg + lane + (int64_t)U * L; p < end; p += L) s += __ldcs(val + p) * __ldg(x + __ldcs(col + p));
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = a0 + 2 * (lane + (int64_t)L * u);
+      if (p >= beg && p < end) dw_mac(acc, v[u].x, __ldg(x + c[u].x), bad);
+      if (p + 1 < end) dw_mac(acc, v[u].y, __ldg(x + c[u].y), bad);
+    }
+    for (int64_t p = a0 + 2 * (lane + (int64_t)L * U); p < end; p += 2 * L) {
+      const double2 vv = __ldcs(reinterpret_cast<const double2 *>(val + p));
+      const int2 cc = __ldcs(reinterpret_cast<const int2 *>(col + p));
+      dw_mac(acc, vv.x, __ldg(x + cc.x), bad);
+      if (p + 1 < end) dw_mac(acc, vv.y, __ldg(x + cc.y), bad);
+    }
   }
 #pragma unroll
-  for (int off = L / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (row < n_rows && lane == 0) y[row] = s;
+  for (int off = L / 2; off > 0; off >>= 1) {
+    const dwa::dw o{__shfl_xor_sync(0xffffffffu, acc.h, off), __shfl_xor_sync(0xffffffffu, acc.l, off)};
+    acc = dwa::add(acc, o);
+  }
+  if (__any_sync(0xffffffffu, bad && row < n_rows)) {
+    // rows of this warp with a product outside the pairs' range (OR over the row's L lanes): plain
+    // FP64 sum by one lane, in entry order
+    bool rb = bad;
+#pragma unroll
+    for (int off = L / 2; off > 0; off >>= 1) rb |= __shfl_xor_sync(0xffffffffu, rb, off) != 0;
+    if (row < n_rows && lane == 0 && rb) {
+      double s = 0.0;
+      for (int64_t p = beg; p < end; ++p) s += val[p] * __ldg(x + col[p]);
+      y[row] = s;
+      return;
+    }
+  }
+  if (row < n_rows && lane == 0) y[row] = dwa::to_double(acc);
 }
 
 template <int PHYS>
@@ -494,10 +545,10 @@ void node_neighbours(const mf_mesh *m, const std::vector<uint8_t> &dmask, std::v
 mf_status spmv(const mf_csr *A, const double *x, double *y, cudaStream_t s, const int *skip) {
   const int64_t threads = A->n_rows * A->lanes;
   mf_count_launches(1);
-  switch (A->lanes) {
-    case 8: spmv_kernel<8, 4><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
-    case 16: spmv_kernel<16, 6><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
-    default: spmv_kernel<32, 4><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+  switch (A->lanes) {  // 2 L U value slots per row: 32 for up to 31 entries, 96 for up to 95
+    case 8: spmv_vec<8, 2><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+    case 16: spmv_vec<16, 3><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+    default: spmv_vec<32, 2><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
   }
   MF_CUDA(cudaGetLastError());
   return MF_OK;
@@ -552,8 +603,8 @@ extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr 
   };
   cudaError_t e = cudaSuccess;
   if ((e = cudaMalloc(&A->rowptr, (n_rows + 1) * sizeof(int64_t))) != cudaSuccess ||
-      (e = cudaMalloc(&A->col, nnz * sizeof(int32_t))) != cudaSuccess ||
-      (e = cudaMalloc(&A->val, nnz * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&A->col, (nnz + 2) * sizeof(int32_t))) != cudaSuccess ||  // + 2: pair loads (spmv_vec)
+      (e = cudaMalloc(&A->val, (nnz + 2) * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&d_noff, noff.size() * sizeof(int64_t))) != cudaSuccess ||
       (e = cudaMalloc(&d_nbr, std::max<size_t>(nbr.size(), 1) * sizeof(int32_t))) != cudaSuccess) {
     cudaGetLastError();
@@ -567,7 +618,8 @@ extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr 
   if (!nbr.empty()) MF_CUDA(cudaMemcpyAsync(d_nbr, nbr.data(), nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   expand_columns<<<blocks_for(n_rows), kThreads, 0, s>>>(m->n_nodes, nd, blockdiag, d_noff, d_nbr, m->dmask, A->rowptr,
                                                           A->col);
-  MF_CUDA(cudaMemsetAsync(A->val, 0, nnz * sizeof(double), s));
+  MF_CUDA(cudaMemsetAsync(A->val, 0, (nnz + 2) * sizeof(double), s));
+  MF_CUDA(cudaMemsetAsync(A->col + nnz, 0, 2 * sizeof(int32_t), s));
   const MeshView v = m->view();
   if (m->physics == MF_LAPLACE) launch_fill<MF_LAPLACE>(m, v, A, s);
   else if (m->physics == MF_VECTOR_LAPLACE) launch_fill<MF_VECTOR_LAPLACE>(m, v, A, s);

@@ -112,6 +112,20 @@ __device__ __forceinline__ dw split(double x) {
   return dw{__uint_as_float(e == 0 ? sign : hb), __uint_as_float(e == 0 ? sign : lb)};
 }
 
+// split() without its out-of-range path: exact for |x| in [2^-74, 2^127) (biased exponent e in
+// [949, 1150]) and zeros; the biased exponent field is returned in e so that the caller can check
+// the range itself (any other input gives an unspecified pair).
+__device__ __forceinline__ dw split_fast(double x, unsigned &e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  e = (bh >> 20) & 0x7ffu;
+  const unsigned sign = bh & 0x80000000u;
+  const unsigned hb = sign | ((e - 1023u + 127u) << 23) | ((bh & 0x000fffffu) << 3) | (bl >> 29);
+  const float lo = __fmul_rn(__uint2float_rn(bl & 0x1fffffffu), __uint_as_float((e - 1075u + 127u) << 23));
+  const unsigned lb = __float_as_uint(lo) | sign;
+  return dw{__uint_as_float(e == 0u ? sign : hb), __uint_as_float(e == 0u ? sign : lb)};
+}
+
 // float -> double exactly by bit manipulation, without branches (lanes of a warp often differ in
 // whether the low part of a pair is zero): normal floats are rebiased; zeros and subnormals give a
 // signed zero (a subnormal low part is below 2^-126 of nothing that matters here), infinities and
@@ -227,6 +241,13 @@ __device__ __forceinline__ bool mag_exponent(unsigned key, int &s) {
 // Window of input magnitudes (exponent of the CTA's largest |x|) in which the double-word kernels
 // keep FP64 accuracy without rescaling, given cell constants and spacings normalised at setup.
 constexpr int kMagLo = -72, kMagHi = 40;
+
+// Quick test on a thread's own record: some input was non-zero and the largest is outside the window
+// (or not finite; the caller then looks at the whole CTA with mag_exponent).
+__device__ __forceinline__ bool mag_outside(unsigned key) {
+  const unsigned e = key >> 20;
+  return key != 0u && (e < (unsigned)(1023 + kMagLo) || e > (unsigned)(1023 + kMagHi));
+}
 
 // Host/device-agnostic split of a double constant (setup and constants, not hot paths).
 __host__ __device__ inline dw from_double_slow(double x) {

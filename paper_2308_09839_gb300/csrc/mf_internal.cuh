@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -133,6 +134,10 @@ struct mf_mesh {
   // built and every apply runs the FP64 reference kernel.
   bool dw_ok = true;
   int dw_oscale = 0;
+  // per-CTA range flags of the face-marching launches (tile_flag_words entries; see mf_march.cuh) and
+  // the launch counter whose low 5 bits pick each launch's flag bit
+  unsigned *tp_flags = nullptr;
+  mutable std::atomic<unsigned> tp_epoch{0};
   double dw_mat = 1.0, dw_geo = 1.0;
   int tile_seg = 0;  // z-segment length of the tile kernels (0: heuristic; set by the autotuner)
   // general structured geometry (structured boxes that are not tensor-product grids): half
@@ -206,6 +211,12 @@ void cg_workspace_free(CgWorkspace *w);
 // and the wave model of the tile kernels; the reductions whose order must not depend on the GPU use
 // fixed grids instead.
 int device_sm_count();
+
+// Forward 3x3x3 convolution of a channels-last BF16 input stored with cin_stride >= cin channels per
+// voxel, on the tensor-core path (mf_nn.cu); MF_ERR_UNSUPPORTED when that path cannot run it.
+mf_status conv3d_fwd_strided(const void *x, int nx, int ny, int nz, int cin, int cin_stride, const void *w,
+                             const float *bias, int cout, const void *skip, int relu, void *y_bf16, float *y_f32,
+                             cudaStream_t stream);
 
 // number of element colours and the launch grid for one colour
 int64_t colour_count(const mf_mesh *m, int c);

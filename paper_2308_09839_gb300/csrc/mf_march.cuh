@@ -52,26 +52,23 @@ struct MarchSmem {
 
 // PHYS = MF_LAPLACE (Eq. 7), MF_VECTOR_LAPLACE (Eq. 5) or MF_ELASTICITY (Eq. 9, Algorithm 1);
 // vectors hold NC values per node (x, y, z components interleaved for the vector operators).
-// One work item (tile column x z-segment `item`, right-hand side `rr`); must be called by all
-// EX*EY/RY threads of the CTA.  A thread owns RY consecutive element rows of its x column: the
-// x-butterflies of the node rows its faces share are formed once, and the y-sums of the node rows
-// between them stay in registers (only the top row's go through shared memory).
-// COHERENT: read x through L2 only (x was written by other CTAs earlier in the same persistent
-// kernel, so the read-only and L1 paths may hold stale lines).
+// One work item (tile column x z-segment `item`, right-hand side `rr`); must be called by all EX*EY
+// threads of the CTA.  COHERENT: read x through L2 only (x was written by other CTAs earlier in the
+// same persistent kernel, so the read-only and L1 paths may hold stale lines).
 // DOT: also return this thread's part of x . y over the nodes it writes (the dot product a CG
 // iteration needs next, p . Ap, formed while the result is written; FP64 products and sums).
 // SC: power-of-two scaling, x * 2^-sc in and y * 2^so out (the cell constants and spacings of a
 // normalised mesh, and the rescaled pass for inputs outside the double-word range); without SC
-// neither is applied (so must be 0).  Double-word passes record the magnitude of the inputs read in
-// `mag` (Dirichlet entries excluded) and publish the item's largest in sm.mag.
-template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT, bool SC, int RY = 1>
+// neither is applied.  Double-word passes record in `mag` the magnitude of the inputs this thread
+// staged (Dirichlet entries excluded).
+template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT, bool SC>
 __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_t rr,
                                              const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
                                              MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm, int sc, int so,
                                              dwa::MagRec &mag) {
   constexpr bool IS_DW = std::is_same<N, tile::NumDW>::value;
   auto conv_in = [&](typename N::IO v) -> typename N::T {
-    if constexpr (IS_DW && SC) return dwa::split_scaled(v, sc);
+    if constexpr (IS_DW && SC) return dwa::split_shift(v, sc);
     else return N::in(v);
   };
   auto conv_out = [&](typename N::T v) -> typename N::IO {
@@ -83,15 +80,15 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
   (void)so;
   double dacc = 0.0;
   static_assert(EX == 32, "a warp is one row of element columns");
-  static_assert(EY % RY == 0, "whole row groups per thread");
   using T = typename N::T;
   using IO = typename N::IO;
   constexpr int NC = phys_ndpn(PHYS);
-  constexpr int NT = EX * EY / RY, PX = EX + 1, NP = (EX + 1) * (EY + 1);
+  constexpr int NT = EX * EY, PX = EX + 1, NP = (EX + 1) * (EY + 1), TX = EX - 1, TY = EY - 1;
   constexpr int LOADS = (NP + NT - 1) / NT;
+  (void)TX;
+  (void)TY;
   auto ldx = [](const IO *p) -> IO { return COHERENT ? __ldcg(p) : __ldg(p); };
   __syncthreads();  // the previous item of a persistent CTA may still be reading sm
-  if (threadIdx.x == 0) sm.mag = 0u;
 
   const int tid = threadIdx.x;
   const int bx = item % g.tiles_x;
@@ -100,38 +97,25 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
   const int i0 = bx * (EX - 1), j0 = by * (EY - 1);
   const int NXP = g.nx + 1, NYP = g.ny + 1;
   const int k0 = bz * g.seg, k1 = min(k0 + g.seg, g.nz + 1);
-  const int tx = tid % EX, tw = tid / EX;
-  const int ex = i0 - 1 + tx, ey0 = j0 - 1 + tw * RY;  // element rows ey0 .. ey0 + RY - 1
-  const bool xin = ex >= 0 && ex < g.nx;
-  bool ein[RY], own[RY];
-#pragma unroll
-  for (int r = 0; r < RY; ++r) {
-    const int ey = ey0 + r;
-    ein[r] = xin && ey >= 0 && ey < g.ny;
-    // this thread's lower-left node (ex, ey) of row r is owned by the CTA
-    own[r] = tx >= 1 && tw * RY + r >= 1 && ex < NXP && ey < NYP;
-  }
+  const int tx = tid % EX, ty = tid / EX;
+  const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;
+  const bool ein = ex >= 0 && ex < g.nx && ey >= 0 && ey < g.ny;
+  // this thread's lower-left node (ex, ey) is owned by the CTA
+  const bool own = tx >= 1 && ty >= 1 && ex < NXP && ey < NYP;
 
   // per-column geometry invariants
-  T hx = N::zero(), ihx = N::zero();
-  if (xin) {
+  T hx = N::zero(), hy = N::zero(), ihx = N::zero(), ihy = N::zero();
+  if (ein) {
     hx = N::from2(__ldg(g.hx + ex));
     ihx = N::from2(__ldg(g.ihx + ex));
+    hy = N::from2(__ldg(g.hy + ey));
+    ihy = N::from2(__ldg(g.ihy + ey));
   }
-  T hy[RY], ihy[RY], hy_ihx[RY], hx_ihy[RY], hxhy[RY];
-#pragma unroll
-  for (int r = 0; r < RY; ++r) {
-    hy[r] = ihy[r] = N::zero();
-    if (ein[r]) {
-      hy[r] = N::from2(__ldg(g.hy + ey0 + r));
-      ihy[r] = N::from2(__ldg(g.ihy + ey0 + r));
-    }
-    hy_ihx[r] = hx_ihy[r] = hxhy[r] = N::zero();
-    if constexpr (phys_is_laplace(PHYS)) {
-      hy_ihx[r] = N::mul(hy[r], ihx);
-      hx_ihy[r] = N::mul(hx, ihy[r]);
-      hxhy[r] = N::mul(hx, hy[r]);
-    }
+  T hy_ihx = N::zero(), hx_ihy = N::zero(), hxhy = N::zero();
+  if constexpr (phys_is_laplace(PHYS)) {
+    hy_ihx = N::mul(hy, ihx);
+    hx_ihy = N::mul(hx, ihy);
+    hxhy = N::mul(hx, hy);
   }
 
   // plane staging: global -> registers (one plane ahead) -> shared memory
@@ -161,37 +145,28 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
 #pragma unroll
     for (int l = 0; l < LOADS; ++l) {
       const int p = tid + l * NT;
-      if (p < NP) {
+      if (p < NP)
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           N::st(u[p * NC + c], dr[l] ? N::zero() : conv_in(xr[l][c]));
           if constexpr (IS_DW)
             if (!dr[l]) mag.add(xr[l][c]);
         }
-      }
     }
   };
-  // 2D forward transforms of this thread's RY faces in plane k (modes: bit 0 x, bit 1 y): the
-  // x-butterflies of the RY + 1 node rows, then the y-butterflies of each face
-  auto face_fwd = [&](int k, T F[RY][NC][4]) {
+  // 2D forward transform of this thread's face in plane k (modes: bit 0 x, bit 1 y)
+  auto face_fwd = [&](int k, T F[NC][4]) {
     const auto *u = sm.up[k & 1];
-    const int p = tx + PX * (tw * RY);
+    const int p = tx + PX * ty;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      T a[RY + 1][2];
-#pragma unroll
-      for (int j = 0; j <= RY; ++j) {
-        const T u0 = N::ld(u[(p + j * PX) * NC + c]), u1 = N::ld(u[(p + j * PX + 1) * NC + c]);
-        a[j][0] = N::add(u0, u1);
-        a[j][1] = N::sub(u1, u0);
-      }
-#pragma unroll
-      for (int r = 0; r < RY; ++r) {
-        F[r][c][0] = N::add(a[r][0], a[r + 1][0]);
-        F[r][c][1] = N::add(a[r][1], a[r + 1][1]);
-        F[r][c][2] = N::sub(a[r + 1][0], a[r][0]);
-        F[r][c][3] = N::sub(a[r + 1][1], a[r][1]);
-      }
+      const T u0 = N::ld(u[p * NC + c]), u1 = N::ld(u[(p + 1) * NC + c]);
+      const T u2 = N::ld(u[(p + PX) * NC + c]), u3 = N::ld(u[(p + PX + 1) * NC + c]);
+      const T a0 = N::add(u0, u1), a1 = N::sub(u1, u0), a2 = N::add(u2, u3), a3 = N::sub(u3, u2);
+      F[c][0] = N::add(a0, a2);
+      F[c][1] = N::add(a1, a3);
+      F[c][2] = N::sub(a2, a0);
+      F[c][3] = N::sub(a3, a1);
     }
   };
 
@@ -206,182 +181,140 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
   }
   if (s_lo + 2 <= plim) fetch(s_lo + 2);
   __syncthreads();
-  T Fb[RY][NC][4], Gc[RY][NC][4];  // bottom-face transforms of the current elements; top parts from below
+  T Fb[NC][4], Gc[NC][4];  // bottom-face transform of the current element; top-face part from below
   face_fwd(s_lo, Fb);
 #pragma unroll
-  for (int r = 0; r < RY; ++r)
+  for (int c = 0; c < NC; ++c)
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) Gc[r][c][m] = N::zero();
+    for (int m = 0; m < 4; ++m) Gc[c][m] = N::zero();
   __syncthreads();  // everyone has read plane s_lo before its buffer is reused
 
-  // material of the elements: loaded one step ahead for elasticity; for the Laplace operators at
-  // the top of the step, ahead of the face transform
+  // material of the element: loaded one step ahead for elasticity; for Laplace (64 registers at
+  // two 512-thread CTAs per SM) at the top of the step, ahead of the face transform
   constexpr int NM = phys_nmat(PHYS);
   constexpr bool PREFETCH = PHYS != MF_LAPLACE;
   const int e_step = g.nx * g.ny * NM;
-  const float2 *matp = g.mat + NM * (ex + (int64_t)g.nx * (ey0 + (int64_t)g.ny * s_lo));
-  float2 mat_next[RY][NM];
+  const float2 *matp = g.mat + NM * (ex + (int64_t)g.nx * (ey + (int64_t)g.ny * s_lo));
+  float2 mat_next[NM];
 #pragma unroll
-  for (int r = 0; r < RY; ++r)
-#pragma unroll
-    for (int q = 0; q < NM; ++q)
-      mat_next[r][q] = (PREFETCH && ein[r] && s_lo < g.nz) ? __ldg(matp + r * g.nx * NM + q) : make_float2(0.f, 0.f);
+  for (int q = 0; q < NM; ++q)
+    mat_next[q] = (PREFETCH && ein && s_lo < g.nz) ? __ldg(matp + q) : make_float2(0.f, 0.f);
 
   for (int ez = s_lo; ez <= s_hi; ++ez) {
-    float2 mat_cur[RY][NM];
+    const bool elem = ein && ez < g.nz;
+    float2 mat_cur[NM];
     if constexpr (PREFETCH) {
       matp += e_step;
 #pragma unroll
-      for (int r = 0; r < RY; ++r)
-#pragma unroll
-        for (int q = 0; q < NM; ++q) {
-          mat_cur[r][q] = mat_next[r][q];
-          mat_next[r][q] = (ein[r] && ez + 1 < g.nz) ? __ldg(matp + r * g.nx * NM + q) : make_float2(0.f, 0.f);
-        }
+      for (int q = 0; q < NM; ++q) {
+        mat_cur[q] = mat_next[q];
+        mat_next[q] = (ein && ez + 1 < g.nz) ? __ldg(matp + q) : make_float2(0.f, 0.f);
+      }
     } else {
 #pragma unroll
-      for (int r = 0; r < RY; ++r)
-#pragma unroll
-        for (int q = 0; q < NM; ++q)
-          mat_cur[r][q] = (ein[r] && ez < g.nz) ? __ldg(matp + r * g.nx * NM + q) : make_float2(0.f, 0.f);
+      for (int q = 0; q < NM; ++q) mat_cur[q] = elem ? __ldg(matp + q) : make_float2(0.f, 0.f);
       matp += e_step;
     }
-    T Ft[RY][NC][4];
+    T Ft[NC][4], S[NC][4];
     if (ez < g.nz) face_fwd(ez + 1, Ft);
     else {
 #pragma unroll
-      for (int r = 0; r < RY; ++r)
+      for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-          for (int m = 0; m < 4; ++m) Ft[r][c][m] = N::zero();
+        for (int m = 0; m < 4; ++m) Ft[c][m] = N::zero();
     }
-    T hz = N::zero(), ihz = N::zero();
-    if (ez < g.nz) {
-      hz = N::from2(__ldg(g.hz + ez));
-      ihz = N::from2(__ldg(g.ihz + ez));
-    }
-    T rb[RY][NC], tp[RY][NC];  // contributions to each face's bottom and top node rows (x-summed)
-#pragma unroll
-    for (int r = 0; r < RY; ++r) {
-      T S[NC][4];
-      if (ein[r] && ez < g.nz) {
-        // o[l][m]: D times the 8 modes; the z butterfly gives mode m (m < 4) as Fb + Ft and mode
-        // m + 4 as Ft - Fb; mode 0 has D = 0
-        T o[NC][8];
-        if constexpr (phys_is_laplace(PHYS)) {  // Laplace; vector Laplace: the same D per component
-          const tile::LapCoef<N> cf =
-              tile::laplace_coef<N>(N::from2(mat_cur[r][0]), hy_ihx[r], hx_ihy[r], hxhy[r], hz, ihz);
-#pragma unroll
-          for (int l = 0; l < NC; ++l) {
-            o[l][1] = N::mul(cf.s1, N::add(Fb[r][l][1], Ft[r][l][1]));
-            o[l][2] = N::mul(cf.s2, N::add(Fb[r][l][2], Ft[r][l][2]));
-            o[l][3] = N::mul(cf.s12, N::add(Fb[r][l][3], Ft[r][l][3]));
-            o[l][4] = N::mul(cf.s3, N::sub(Ft[r][l][0], Fb[r][l][0]));
-            o[l][5] = N::mul(cf.s13, N::sub(Ft[r][l][1], Fb[r][l][1]));
-            o[l][6] = N::mul(cf.s23, N::sub(Ft[r][l][2], Fb[r][l][2]));
-            o[l][7] = N::mul(cf.s123, N::sub(Ft[r][l][3], Fb[r][l][3]));
-          }
-        } else {
-          const T h[3] = {hx, hy[r], hz}, ih[3] = {ihx, ihy[r], ihz};
-          const tile::ElCoef<N> cf =
-              tile::elasticity_coef<N>(N::from2(mat_cur[r][0]), N::from2(mat_cur[r][NM - 1]), h, ih);
-          T c[3][8];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            c[k][0] = N::zero();
-#pragma unroll
-            for (int m = 1; m < 4; ++m) c[k][m] = N::add(Fb[r][k][m], Ft[r][k][m]);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) c[k][m + 4] = N::sub(Ft[r][k][m], Fb[r][k][m]);
-          }
-          tile::elasticity_modes<N>(cf, c, o);
-        }
-        // transposed z butterfly: bottom part o[m] - o[m+4] (summed with the carried top part of
-        // the element below), top part o[m] + o[m+4] (carried up)
+    if (elem) {
+      const T hz = N::from2(__ldg(g.hz + ez)), ihz = N::from2(__ldg(g.ihz + ez));
+      // o[l][m]: D times the 8 modes; the z butterfly gives mode m (m < 4) as Fb + Ft and mode
+      // m + 4 as Ft - Fb; mode 0 has D = 0
+      T o[NC][8];
+      if constexpr (phys_is_laplace(PHYS)) {  // Laplace; vector Laplace: the same D per component
+        const tile::LapCoef<N> cf = tile::laplace_coef<N>(N::from2(mat_cur[0]), hy_ihx, hx_ihy, hxhy, hz, ihz);
 #pragma unroll
         for (int l = 0; l < NC; ++l) {
-          S[l][0] = N::sub(Gc[r][l][0], o[l][4]);
-          Gc[r][l][0] = o[l][4];
-#pragma unroll
-          for (int m = 1; m < 4; ++m) {
-            S[l][m] = N::add(Gc[r][l][m], N::sub(o[l][m], o[l][m + 4]));
-            Gc[r][l][m] = N::add(o[l][m], o[l][m + 4]);
-          }
+          o[l][1] = N::mul(cf.s1, N::add(Fb[l][1], Ft[l][1]));
+          o[l][2] = N::mul(cf.s2, N::add(Fb[l][2], Ft[l][2]));
+          o[l][3] = N::mul(cf.s12, N::add(Fb[l][3], Ft[l][3]));
+          o[l][4] = N::mul(cf.s3, N::sub(Ft[l][0], Fb[l][0]));
+          o[l][5] = N::mul(cf.s13, N::sub(Ft[l][1], Fb[l][1]));
+          o[l][6] = N::mul(cf.s23, N::sub(Ft[l][2], Fb[l][2]));
+          o[l][7] = N::mul(cf.s123, N::sub(Ft[l][3], Fb[l][3]));
         }
       } else {
+        const T h[3] = {hx, hy, hz}, ih[3] = {ihx, ihy, ihz};
+        const tile::ElCoef<N> cf =
+            tile::elasticity_coef<N>(N::from2(mat_cur[0]), N::from2(mat_cur[NM - 1]), h, ih);
+        T c[3][8];
 #pragma unroll
-        for (int l = 0; l < NC; ++l)
+        for (int k = 0; k < 3; ++k) {
+          c[k][0] = N::zero();
 #pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            S[l][m] = Gc[r][l][m];
-            Gc[r][l][m] = N::zero();
-          }
+          for (int m = 1; m < 4; ++m) c[k][m] = N::add(Fb[k][m], Ft[k][m]);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) c[k][m + 4] = N::sub(Ft[k][m], Fb[k][m]);
+        }
+        tile::elasticity_modes<N>(cf, c, o);
       }
-      // transposed 2D transform of the face sums -> contributions to the face's 4 corner nodes;
-      // along x node (ex, .) gets this face's left corners and the left neighbour face's right ones
+      // transposed z butterfly: bottom part o[m] - o[m+4] (summed with the carried top part of the
+      // element below), top part o[m] + o[m+4] (carried up)
 #pragma unroll
       for (int l = 0; l < NC; ++l) {
-        const T t0 = N::sub(S[l][0], S[l][1]), t1 = N::add(S[l][0], S[l][1]);
-        const T t2 = N::sub(S[l][2], S[l][3]), t3 = N::add(S[l][2], S[l][3]);
-        const T v00 = N::sub(t0, t2), v01 = N::add(t0, t2), v10 = N::sub(t1, t3), v11 = N::add(t1, t3);
-        rb[r][l] = N::add(v00, shfl_up1<N>(v10));
-        tp[r][l] = N::add(v01, shfl_up1<N>(v11));
+        S[l][0] = N::sub(Gc[l][0], o[l][4]);
+        Gc[l][0] = o[l][4];
+#pragma unroll
+        for (int m = 1; m < 4; ++m) {
+          S[l][m] = N::add(Gc[l][m], N::sub(o[l][m], o[l][m + 4]));
+          Gc[l][m] = N::add(o[l][m], o[l][m + 4]);
+        }
       }
-    }
-    // the top node row of the thread's last face goes to the thread above through shared memory
+    } else {
 #pragma unroll
-    for (int l = 0; l < NC; ++l) N::st(sm.xrow[ez & 1][l * NT + tid], tp[RY - 1][l]);
-    bool wr[RY], dir[RY];
-    int64_t node[RY];
+      for (int l = 0; l < NC; ++l)
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-      wr[r] = own[r] && ez >= k0;
-      node[r] = (ex + NXP * (ey0 + r)) + (int64_t)ez * NPL;
-      dir[r] = wr[r] && __ldg(g.dmask + node[r]) != 0;  // issued before the barrier
+        for (int m = 0; m < 4; ++m) {
+          S[l][m] = Gc[l][m];
+          Gc[l][m] = N::zero();
+        }
     }
+    // transposed 2D transform of the face sums -> contributions to the face's 4 corner nodes; along
+    // x node (ex, .) gets this face's left corners and the left neighbour face's right corners
+    T rb[NC];
+#pragma unroll
+    for (int l = 0; l < NC; ++l) {
+      const T t0 = N::sub(S[l][0], S[l][1]), t1 = N::add(S[l][0], S[l][1]);
+      const T t2 = N::sub(S[l][2], S[l][3]), t3 = N::add(S[l][2], S[l][3]);
+      const T v00 = N::sub(t0, t2), v01 = N::add(t0, t2), v10 = N::sub(t1, t3), v11 = N::add(t1, t3);
+      rb[l] = N::add(v00, shfl_up1<N>(v10));
+      N::st(sm.xrow[ez & 1][l * NT + tid], N::add(v01, shfl_up1<N>(v11)));
+    }
+    const bool wr = own && ez >= k0;
+    const int64_t node = (ex + NXP * ey) + (int64_t)ez * NPL;
+    const bool dir = wr && __ldg(g.dmask + node) != 0;  // issued before the barrier
     if (ez + 2 <= plim) {
       stage(ez + 2);  // plane ez's buffer: its last reader finished before the previous barrier
       if (ez + 3 <= plim) fetch(ez + 3);
     }
-    if constexpr (IS_DW) {
-      // every plane has been staged by now: publish the item's largest input record, which the
-      // barrier below makes visible to the whole CTA after the march
-      if (ez == s_hi) {
-        const unsigned w = __reduce_max_sync(0xffffffffu, mag.key);
-        if ((threadIdx.x & 31) == 0) atomicMax(&sm.mag, w);
-      }
-    }
     __syncthreads();
-    // y: node (ex, ey) gets the bottom row of the faces at ey and the top row of the faces at ey - 1
-    // (this thread's previous row, or the thread below for the first row)
+    // y: node (ex, ey) gets the bottom row of this thread's faces and the top row of the row below
+    if (wr) {
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-      if (wr[r]) {
-#pragma unroll
-        for (int l = 0; l < NC; ++l) {
-          const T below = r == 0 ? N::ld(sm.xrow[ez & 1][l * NT + tid - EX]) : tp[r > 0 ? r - 1 : 0][l];
-          const T tot = N::add(rb[r][l], below);
-          const int64_t vi = (node[r] * g.nrhs + rr) * NC + l;
-          if constexpr (DOT) {
-            const IO xv = ldx(x + vi);
-            const IO yv = dir[r] ? xv : conv_out(tot);
-            y[vi] = yv;
-            dacc += (double)xv * (double)yv;
-          } else {
-            y[vi] = dir[r] ? ldx(x + vi) : conv_out(tot);
-          }
+      for (int l = 0; l < NC; ++l) {
+        const T tot = N::add(rb[l], N::ld(sm.xrow[ez & 1][l * NT + tid - EX]));
+        const int64_t vi = (node * g.nrhs + rr) * NC + l;
+        if constexpr (DOT) {
+          const IO xv = ldx(x + vi);
+          const IO yv = dir ? xv : conv_out(tot);
+          y[vi] = yv;
+          dacc += (double)xv * (double)yv;
+        } else {
+          y[vi] = dir ? ldx(x + vi) : conv_out(tot);
         }
       }
     }
 #pragma unroll
-    for (int r = 0; r < RY; ++r)
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
-#pragma unroll
-        for (int m = 0; m < 4; ++m) Fb[r][c][m] = Ft[r][c][m];
+      for (int m = 0; m < 4; ++m) Fb[c][m] = Ft[c][m];
   }
   return dacc;
 }
@@ -389,12 +322,12 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
 // The scaled pass as a separate (not inlined) function: it runs for normalised meshes and for the
 // rare work items whose inputs lie outside the double-word range, and keeping its code out of the
 // unscaled pass leaves that pass its registers.
-template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT, int RY>
+template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT>
 __device__ __noinline__ double march_pass_scaled(const TileArgs &g, int item, int64_t rr,
                                                  const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
                                                  MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm, int sc, int so,
                                                  dwa::MagRec &mag) {
-  return march_pass<PHYS, N, EX, EY, COHERENT, DOT, true, RY>(g, item, rr, x, y, sm, sc, so, mag);
+  return march_pass<PHYS, N, EX, EY, COHERENT, DOT, true>(g, item, rr, x, y, sm, sc, so, mag);
 }
 
 // One work item with the output scaling of the mesh; for double-word arithmetic, if the largest input
@@ -402,55 +335,66 @@ __device__ __noinline__ double march_pass_scaled(const TileArgs &g, int item, in
 // of two that brings that input to [1, 2) (and y scaled back), so results keep FP64 accuracy over
 // FP64's whole range.  The decision depends on the item's own inputs only (deterministic); the
 // second pass overwrites every value the first one wrote.
-template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT = false, int RY = 1>
+template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT = false>
 __device__ __forceinline__ double march_item(const TileArgs &g, int item, int64_t rr,
                                              const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
                                              MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm) {
   dwa::MagRec mag;
   double d = g.oscale == 0
-                 ? march_pass<PHYS, N, EX, EY, COHERENT, DOT, false, RY>(g, item, rr, x, y, sm, 0, 0, mag)
-                 : march_pass_scaled<PHYS, N, EX, EY, COHERENT, DOT, RY>(g, item, rr, x, y, sm, 0, g.oscale, mag);
+                 ? march_pass<PHYS, N, EX, EY, COHERENT, DOT, false>(g, item, rr, x, y, sm, 0, 0, mag)
+                 : march_pass_scaled<PHYS, N, EX, EY, COHERENT, DOT>(g, item, rr, x, y, sm, 0, g.oscale, mag);
   if constexpr (std::is_same<N, tile::NumDW>::value) {
+    const unsigned w = __reduce_max_sync(0xffffffffu, mag.key);
+    __syncthreads();
+    if (threadIdx.x == 0) sm.mag = 0u;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&sm.mag, w);
+    __syncthreads();
     int s = 0;
     if (dwa::mag_exponent(sm.mag, s) && (s < dwa::kMagLo || s > dwa::kMagHi))
-      d = march_pass_scaled<PHYS, N, EX, EY, COHERENT, DOT, RY>(g, item, rr, x, y, sm, s, g.oscale + s, mag);
+      d = march_pass_scaled<PHYS, N, EX, EY, COHERENT, DOT>(g, item, rr, x, y, sm, s, g.oscale + s, mag);
   }
   return d;
 }
 
-template <int PHYS, class N, int EX, int EY, int RY, int MINB>
-__global__ void __launch_bounds__(EX *EY / RY, MINB) march_apply(TileArgs g, const typename N::IO *__restrict__ x,
+// Stand-alone launches: the unscaled pass only, so that the range check adds no code (and no
+// registers) to them.  A thread whose staged inputs' largest magnitude lies outside [2^kMagLo,
+// 2^kMagHi] sets this launch's bit in the CTA's flag word; march_fixup, launched right after on the
+// same stream, redoes those work items (and, on a normalised mesh, all of them) with the scaled pass.
+template <int PHYS, class N, int EX, int EY, int MINB>
+__global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const typename N::IO *__restrict__ x,
                                                                  typename N::IO *__restrict__ y,
                                                                  const int *__restrict__ skip) {
   __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
   if (skip && *skip) return;
+  if (g.oscale != 0) return;  // normalised mesh: the fix-up kernel computes every item
+  dwa::MagRec mag;
   // right-hand side fastest: CTAs that run together read the same x lines ([node][rhs][comp])
-  march_item<PHYS, N, EX, EY, false, false, RY>(g, blockIdx.x / g.nrhs, g.r0 + blockIdx.x % g.nrhs, x, y, sm);
+  march_pass<PHYS, N, EX, EY, false, false, false>(g, blockIdx.x / g.nrhs, g.r0 + blockIdx.x % g.nrhs, x, y, sm, 0,
+                                                       0, mag);
+  if constexpr (std::is_same<N, tile::NumDW>::value)
+    if (dwa::mag_outside(mag.key)) atomicOr(g.flags + blockIdx.x, g.bit);
 }
 
-// Apply with the dot product x . y fused in (one right-hand side): each CTA stores its part, the
-// last CTA to finish (ticket) sums the parts in CTA order into *out and resets the ticket, so the
-// result does not depend on scheduling.  partials: one slot per CTA.
-template <int PHYS, class N, int EX, int EY, int RY, int MINB>
-__global__ void __launch_bounds__(EX *EY / RY, MINB)
-    march_apply_dot(TileArgs g, const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
-                    const int *__restrict__ skip, double *__restrict__ partials, unsigned int *ticket,
-                    double *out) {
-  constexpr int NT = EX * EY / RY, NW = NT / 32;
-  __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
+// Sum of the per-CTA parts in CTA order into *out (the last CTA of the launch to arrive does it and
+// resets the ticket), so that the result does not depend on scheduling.
+template <int NT>
+__device__ __forceinline__ void ordered_dot_sum(double d, double *__restrict__ partials, int slot, int nslots,
+                                                unsigned int *ticket, double *out, bool store) {
+  constexpr int NW = NT / 32;
   __shared__ double red[NW];
   __shared__ bool last;
-  if (skip && *skip) return;
-  double d = march_item<PHYS, N, EX, EY, false, true, RY>(g, blockIdx.x, g.r0, x, y, sm);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
   if (lane == 0) red[w] = d;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < NW; ++i) s += red[i];
-    partials[blockIdx.x] = s;
+    if (store) {
+      double s = 0.0;
+      for (int i = 0; i < NW; ++i) s += red[i];
+      partials[slot] = s;
+    }
     __threadfence();
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
@@ -458,7 +402,7 @@ __global__ void __launch_bounds__(EX *EY / RY, MINB)
   if (!last) return;
   __threadfence();
   double s = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) s += __ldcg(partials + i);
+  for (int i = threadIdx.x; i < nslots; i += NT) s += __ldcg(partials + i);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   __syncthreads();
@@ -472,26 +416,156 @@ __global__ void __launch_bounds__(EX *EY / RY, MINB)
   }
 }
 
-// Launch shapes: EX = 32 element columns per warp row, EY element rows, RY rows per thread (threads
-// EX EY / RY), MINB resident CTAs per SM.
+// Apply with the dot product x . y fused in (one right-hand side): each CTA stores its part, the
+// last CTA to finish sums the parts in CTA order into *out.  partials: one slot per CTA.
+template <int PHYS, class N, int EX, int EY, int MINB>
+__global__ void __launch_bounds__(EX *EY, MINB)
+    march_apply_dot(TileArgs g, const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
+                    const int *__restrict__ skip, double *__restrict__ partials, unsigned int *ticket,
+                    double *out) {
+  __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
+  if (skip && *skip) return;
+  if (g.oscale != 0) return;  // normalised mesh: the fix-up kernel computes every item and the sum
+  dwa::MagRec mag;
+  const double d = march_pass<PHYS, N, EX, EY, false, true, false>(g, blockIdx.x, g.r0, x, y, sm, 0, 0, mag);
+  if constexpr (std::is_same<N, tile::NumDW>::value)
+    if (dwa::mag_outside(mag.key)) atomicOr(g.flags + blockIdx.x, g.bit);
+  ordered_dot_sum<EX * EY>(d, partials, blockIdx.x, gridDim.x, ticket, out, true);
+}
+
+// Largest input magnitude record of a work item (the inputs its CTA stages, Dirichlet entries
+// excluded), over the whole CTA (all threads call it and receive it).
+template <int PHYS, class N, int EX, int EY>
+__device__ unsigned march_prescan(const TileArgs &g, int item, int64_t rr, const typename N::IO *__restrict__ x,
+                                  unsigned *slot) {
+  constexpr int NC = phys_ndpn(PHYS), NT = EX * EY, PX = EX + 1, NP = (EX + 1) * (EY + 1);
+  const int bx = item % g.tiles_x, by = (item / g.tiles_x) % g.tiles_y, bz = item / (g.tiles_x * g.tiles_y);
+  const int i0 = bx * (EX - 1), j0 = by * (EY - 1), NXP = g.nx + 1, NYP = g.ny + 1;
+  const int k0 = bz * g.seg, k1 = min(k0 + g.seg, g.nz + 1);
+  const int plo = max(k0 - 1, 0), phi = min(k1, g.nz);
+  const int64_t NPL = (int64_t)NXP * NYP;
+  dwa::MagRec mag;
+  for (int p = threadIdx.x; p < NP; p += NT) {
+    const int ix = i0 - 1 + p % PX, iy = j0 - 1 + p / PX;
+    if (ix < 0 || ix >= NXP || iy < 0 || iy >= NYP) continue;
+    for (int k = plo; k <= phi; ++k) {
+      const int64_t node = ix + NXP * iy + (int64_t)k * NPL;
+      if (__ldg(g.dmask + node)) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) mag.add(__ldg(x + (node * g.nrhs + rr) * NC + c));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *slot = 0u;
+  __syncthreads();
+  const unsigned w = __reduce_max_sync(0xffffffffu, mag.key);
+  if ((threadIdx.x & 31) == 0) atomicMax(slot, w);
+  __syncthreads();
+  return *slot;
+}
+
+// Fix-up after march_apply / march_apply_dot (n_cta CTAs, the flags of this launch's bit): every
+// flagged work item whose CTA-wide largest input lies outside the double-word window is computed
+// again with its inputs scaled into [1, 2) and y scaled back; on a normalised mesh every item is
+// computed here, with the mesh's output scaling.  Each flag bit is cleared as it is read.  With DOT
+// the recomputed items' parts are stored and, if any changed, the dot product is summed again in CTA
+// order by the last CTA of this launch.  Persistent: CTAs loop over the items.
+// ctl: two words of the mesh (ctl[0]: some part changed, ctl[1]: ticket of this kernel), zero between
+// launches.
+template <int PHYS, class N, int EX, int EY, bool DOT>
+__global__ void __launch_bounds__(EX *EY) march_fixup(TileArgs g, const typename N::IO *__restrict__ x,
+                                                          typename N::IO *__restrict__ y, const int *__restrict__ skip,
+                                                          int n_cta, double *__restrict__ partials, unsigned int *ctl,
+                                                          double *out) {
+  __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
+  __shared__ unsigned todo, mslot;
+  __shared__ int changed;
+  constexpr bool IS_DW = std::is_same<N, tile::NumDW>::value;
+  if (skip && *skip) return;
+  if (threadIdx.x == 0) changed = 0;
+  // quick exit: one plain load per thread over this CTA's items (the usual case: nothing flagged)
+  bool mine = false;
+  for (int c = blockIdx.x + (int)threadIdx.x * (int)gridDim.x; c < n_cta; c += EX * EY * (int)gridDim.x)
+    mine |= g.oscale != 0 || (IS_DW && (__ldcg(g.flags + c) & g.bit) != 0u);
+  const bool some = __syncthreads_or(mine) != 0;
+  for (int c = blockIdx.x; some && c < n_cta; c += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) todo = g.oscale != 0 ? 1u : (IS_DW ? (atomicAnd(g.flags + c, ~g.bit) & g.bit) : 0u);
+    __syncthreads();
+    if (!todo) continue;
+    const int item = DOT ? c : c / g.nrhs;
+    const int64_t rr = DOT ? g.r0 : g.r0 + c % g.nrhs;
+    int sc = 0;
+    if constexpr (IS_DW) {
+      int s = 0;
+      if (dwa::mag_exponent(march_prescan<PHYS, N, EX, EY>(g, item, rr, x, &mslot), s) &&
+          (s < dwa::kMagLo || s > dwa::kMagHi))
+        sc = s;
+      else if (g.oscale == 0)
+        continue;  // the first pass was within the window after all
+    }
+    dwa::MagRec mag;
+    const double d = march_pass<PHYS, N, EX, EY, false, DOT, true>(g, item, rr, x, y, sm, sc, g.oscale + sc, mag);
+    if constexpr (DOT) {
+      double t = d;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      __shared__ double red[EX * EY / 32];
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int i = 0; i < EX * EY / 32; ++i) u += red[i];
+        partials[c] = u;
+        changed = 1;
+      }
+    }
+  }
+  if constexpr (DOT) {
+    __syncthreads();
+    __shared__ int last;
+    // every CTA reports whether it changed a part; the last one to arrive sums again if any did
+    if (threadIdx.x == 0) {
+      if (changed) atomicOr(ctl, 1u);
+      __threadfence();
+      last = atomicAdd(ctl + 1, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const bool any = __ldcg(ctl) != 0u;
+    if (any) {
+      constexpr int NT = EX * EY, NW = NT / 32;
+      __shared__ double red2[NW];
+      double s = 0.0;
+      for (int i = threadIdx.x; i < n_cta; i += NT) s += __ldcg(partials + i);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < NW; ++i) t += red2[i];
+        *out = t;
+      }
+    }
+    if (threadIdx.x == 0) {
+      ctl[0] = 0u;
+      ctl[1] = 0u;
+    }
+  }
+}
+
+// Launch shapes: EX = 32 element columns per warp row, EY rows, MINB resident CTAs per SM.
 // Double-word elasticity takes 12 rows at 168 registers (12 warps per SM, halo factor 1.13): at 8
 // rows it needed 241 registers and ran 8 warps per SM, 17 % slower at 160^3.  FP32 elasticity keeps
-// 8 rows, where it is fastest.
-#ifndef MF_LAP_EY
-#define MF_LAP_EY 16
-#endif
-#ifndef MF_LAP_RY
-#define MF_LAP_RY 2
-#endif
-#ifndef MF_LAP_MINB
-#define MF_LAP_MINB 2
-#endif
-template <int PHYS, class N> struct MarchShape { static constexpr int EX = 32, EY = 8, RY = 1, MINB = 4; };
-template <> struct MarchShape<MF_LAPLACE, tile::NumDW> {
-  static constexpr int EX = 32, EY = MF_LAP_EY, RY = MF_LAP_RY, MINB = MF_LAP_MINB;
-};
-template <class N> struct MarchShape<MF_ELASTICITY, N> { static constexpr int EX = 32, EY = 8, RY = 1, MINB = 1; };
-template <> struct MarchShape<MF_ELASTICITY, tile::NumDW> { static constexpr int EX = 32, EY = 12, RY = 1, MINB = 1; };
-template <class N> struct MarchShape<MF_VECTOR_LAPLACE, N> { static constexpr int EX = 32, EY = 8, RY = 1, MINB = 2; };
+// 8 rows, where it is fastest.  Two element rows per thread (x-butterflies of shared node rows
+// formed once, y-sums between them in registers) were measured slower for the double-word Laplace
+// apply at 256^3: 0.52-0.58 ms on 32x8, 32x12 and 32x16 tiles against 0.50 ms with one row per
+// thread on 32x8 tiles at 4 CTAs per SM (half the warps hide less latency).
+template <int PHYS, class N> struct MarchShape { static constexpr int EX = 32, EY = 8, MINB = 4; };
+template <class N> struct MarchShape<MF_ELASTICITY, N> { static constexpr int EX = 32, EY = 8, MINB = 1; };
+template <> struct MarchShape<MF_ELASTICITY, tile::NumDW> { static constexpr int EX = 32, EY = 12, MINB = 1; };
+template <class N> struct MarchShape<MF_VECTOR_LAPLACE, N> { static constexpr int EX = 32, EY = 8, MINB = 2; };
 
 }  // namespace march

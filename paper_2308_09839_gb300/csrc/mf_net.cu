@@ -41,11 +41,23 @@ struct Layer {
 const int kLayers[8][4] = {{0, 2, 16, 1}, {1, 16, 32, 1}, {2, 32, 64, 1}, {2, 64, 64, 1},
                            {1, 64, 32, 1}, {1, 32, 16, 1}, {0, 16, 16, 1}, {0, 16, 1, 0}};
 
-__global__ void make_input(const float *__restrict__ r, const float *__restrict__ logk, int64_t n, bf16 *__restrict__ in) {
+// The network input: 2 channels per voxel (residual, log kappa), and the same padded to 16 channels
+// (zeros) for the tensor-core convolution, whose TMA loads move 16-byte channel chunks.
+__global__ void make_input(const float *__restrict__ r, const float *__restrict__ logk, int64_t n, bf16 *__restrict__ in,
+                           bf16 *__restrict__ in16) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  in[2 * i] = __float2bfloat16(r[i]);
-  in[2 * i + 1] = __float2bfloat16(logk[i]);
+  const bf16 a = __float2bfloat16(r[i]), b = __float2bfloat16(logk[i]);
+  in[2 * i] = a;
+  in[2 * i + 1] = b;
+  __align__(16) bf16 v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __float2bfloat16(0.0f);
+  v[0] = a;
+  v[1] = b;
+  uint4 *o = reinterpret_cast<uint4 *>(in16 + 16 * i);
+  o[0] = reinterpret_cast<const uint4 *>(v)[0];
+  o[1] = reinterpret_cast<const uint4 *>(v)[1];
 }
 
 // Relative squared error L = sum (o - t)^2 / sum t^2 and its gradient 2 (o - t) / sum t^2 (bf16).
@@ -153,6 +165,7 @@ struct mf_net {
   bf16 *pb = nullptr;                                           // BF16 copy (weights used by kernels)
   int64_t step = 0;
   // activations (bf16) and gradients
+  bf16 *in16 = nullptr;  // the input padded to 16 channels (tensor-core path of layer 0)
   bf16 *in0 = nullptr, *e0 = nullptr, *r0 = nullptr, *e1 = nullptr, *r1 = nullptr, *e2 = nullptr, *m2 = nullptr,
        *p1 = nullptr, *d1 = nullptr, *q1 = nullptr, *p0 = nullptr, *d0 = nullptr;
   float *out = nullptr;
@@ -198,7 +211,14 @@ mf_status conv(const mf_net *N, int l, const bf16 *in, const bf16 *skip, bf16 *o
 
 mf_status forward(mf_net *N, cudaStream_t s) {
   const int *n0 = N->n[0], *n1 = N->n[1];
-  MF_TRY(conv(N, 0, N->in0, nullptr, N->e0, nullptr, s));
+  {  // layer 0 on the tensor cores from the padded input, else from the 2-channel one
+    const Layer &L = N->layers[0];
+    const int *d = N->n[0];
+    const mf_status st = conv3d_fwd_strided(N->in16, d[0], d[1], d[2], L.cin, 16, W(N, 0), B(N, 0), L.cout, nullptr,
+                                            L.relu, N->e0, nullptr, s);
+    if (st == MF_ERR_UNSUPPORTED) MF_TRY(conv(N, 0, N->in0, nullptr, N->e0, nullptr, s));
+    else MF_TRY(st);
+  }
   MF_TRY(mf_grid_restrict(N->e0, n0[0], n0[1], n0[2], 16, N->r0, 1.0f, (mf_stream)s));
   MF_TRY(conv(N, 1, N->r0, nullptr, N->e1, nullptr, s));
   MF_TRY(mf_grid_restrict(N->e1, n1[0], n1[1], n1[2], 32, N->r1, 1.0f, (mf_stream)s));
@@ -280,7 +300,7 @@ mf_status backward(mf_net *N, const float *target, float *loss_host, cudaStream_
 
 mf_status load_input(mf_net *N, const float *r, const float *logk, cudaStream_t s) {
   mf_count_launches(1);
-  make_input<<<blocks_for(N->V[0]), kThreads, 0, s>>>(r, logk, N->V[0], N->in0);
+  make_input<<<blocks_for(N->V[0]), kThreads, 0, s>>>(r, logk, N->V[0], N->in0, N->in16);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }
@@ -316,7 +336,7 @@ extern "C" mf_status mf_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t 
     return st;                            \
   }
   NA(N->p, off) NA(N->g, off) NA(N->m, off) NA(N->v, off) NA(N->pb, off)
-  NA(N->in0, V0 * 2) NA(N->e0, V0 * 16) NA(N->r0, V1 * 16) NA(N->e1, V1 * 32) NA(N->r1, V2 * 32) NA(N->e2, V2 * 64)
+  NA(N->in0, V0 * 2) NA(N->in16, V0 * 16) NA(N->e0, V0 * 16) NA(N->r0, V1 * 16) NA(N->e1, V1 * 32) NA(N->r1, V2 * 32) NA(N->e2, V2 * 64)
   NA(N->m2, V2 * 64) NA(N->p1, V1 * 64) NA(N->d1, V1 * 32) NA(N->q1, V1 * 16) NA(N->p0, V0 * 16) NA(N->d0, V0 * 16)
   NA(N->out, V0) NA(N->g_out, V0)
   const int64_t gmax = std::max(std::max(V0 * 16, V1 * 64), V2 * 64);

@@ -56,6 +56,7 @@ struct ConvArgs {
   bf16 *out_bf;           // [..][cn] or null
   float *out_f;           // [..][cn] or null
   int tiles_x, tiles_y, tiles;
+  int cphys;              // channels per voxel of `in` in memory (>= ck; 0: ck), tensor-core path only
 };
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
@@ -499,6 +500,42 @@ struct TcpCfg {
   static constexpr int COLS = 2 * ACC <= 32 ? 32 : 2 * ACC <= 64 ? 64 : 2 * ACC <= 128 ? 128 : 2 * ACC <= 256 ? 256 : 512;
 };
 
+// All 27 taps of weights in the canonical K-major layout w_s[tap][k / 8][n][k % 8] (zero beyond the
+// real channel counts).  The global weights are read in 16-byte runs along their contiguous index
+// (output channels n in the forward layout [tap][k][n], input channels k in the transposed one of
+// the input gradient) and scattered into shared memory as 2-byte stores.
+template <int CKP, int CN, int MODE>
+__device__ __forceinline__ void stage_weights(const TcArgs &a, unsigned char *wsm, int tapb, int tid, int nthreads) {
+  constexpr int KC = CKP / 8;
+  bf16 *w_s = reinterpret_cast<bf16 *>(wsm);
+  auto put = [&](int tap, int k, int n, bf16 v) {
+    w_s[(size_t)tap * (tapb / 2) + ((size_t)(k >> 3) * CN + n) * 8 + (k & 7)] = v;
+  };
+  const bf16 zero = __float2bfloat16(0.0f);
+  // contiguous dimension: n (MODE 0, length cn) or k (MODE 1, length ck); the other one is strided
+  const int cl = MODE == 0 ? a.cn : a.ck, ol = MODE == 0 ? CKP : CN, cpad = MODE == 0 ? CN : CKP;
+  const bool vec = cl % 8 == 0 && ((uintptr_t)a.w & 15) == 0;
+  const int runs = cpad / 8;  // 8-element runs along the contiguous dimension
+  for (int idx = tid; idx < 27 * ol * runs; idx += nthreads) {
+    const int o = idx % ol, run = (idx / ol) % runs, tap = idx / (runs * ol);  // o fastest: fewer bank conflicts
+    const int c0 = run * 8;
+    __align__(16) bf16 v[8];
+    const bool inside = MODE == 0 ? (o < a.ck && c0 < a.cn) : (o < a.cn && c0 < a.ck);
+    const int64_t base = MODE == 0 ? ((int64_t)tap * a.ck + o) * a.cn + c0 : ((int64_t)(26 - tap) * a.cn + o) * a.ck + c0;
+    if (inside && vec) {
+      *reinterpret_cast<uint4 *>(v) = __ldg(reinterpret_cast<const uint4 *>(a.w + base));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = (inside && c0 + j < cl) ? a.w[base + j] : zero;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (MODE == 0) put(tap, o, c0 + j, v[j]);   // o = k, contiguous n
+      else put(tap, c0 + j, o, v[j]);             // o = n, contiguous k
+    }
+  }
+}
+
 template <int CKP, int CN, int MODE>
 __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_constant__ CUtensorMap tmap) {
   using Cfg = TcpCfg<CKP, CN>;
@@ -525,23 +562,10 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
     umma::mbar_init_fence();
     abort_flag = 0;
   }
+  __shared__ float bias_s[CN];
   if (warp == 1) umma::tmem_alloc(&tmem_slot, Cfg::COLS);
-  for (int idx = tid; idx < 27 * KC * CN; idx += kTcpThreads) {  // all weights, canonical K-major
-    const int n = idx % CN, kc = (idx / CN) % KC, tap = idx / (CN * KC);
-    __align__(16) bf16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int k = kc * 8 + j;
-      bf16 e = __float2bfloat16(0.0f);
-      if (k < a.ck && n < a.cn) {
-        if (MODE == 0) e = a.w[((int64_t)tap * a.ck + k) * a.cn + n];
-        else e = a.w[((int64_t)(26 - tap) * a.cn + n) * a.ck + k];
-      }
-      v[j] = e;
-    }
-    *reinterpret_cast<uint4 *>(wsm + (size_t)tap * Cfg::TAPB + ((size_t)kc * CN + n) * 16) =
-        *reinterpret_cast<const uint4 *>(v);
-  }
+  stage_weights<CKP, CN, MODE>(a, wsm, Cfg::TAPB, tid, kTcpThreads);
+  for (int n = tid; n < CN; n += kTcpThreads) bias_s[n] = (MODE == 0 && a.bias && n < a.cn) ? a.bias[n] : 0.0f;
   umma::fence_proxy_async_smem();
   umma::tc_fence_before_sync();
   __syncthreads();
@@ -617,8 +641,24 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
     }
   } else {  // ----------------------------------------------------------------------- epilogue
     const int q = warp & 3, m = 32 * q + lane;
+    const bool vskip = MODE == 0 && a.skip && a.vec_out;
     for (int i = 0; i < nloc; ++i) {
       const int ac = i & 1;
+      int x0, y0, z0;
+      coords(i, x0, y0, z0);
+      const int gx = x0 + (m & 7), gy = y0 + (m >> 3);
+      // the skip values of the item's voxels are loaded before the wait, so that their latency
+      // overlaps the item's MMAs
+      uint4 sk[TZ][CN / 8];
+      if (vskip) {
+#pragma unroll
+        for (int zi = 0; zi < TZ; ++zi) {
+          const bool in = gx < a.nx && gy < a.ny && z0 + zi < a.nz;
+          const uint4 *sp = reinterpret_cast<const uint4 *>(a.skip + (((int64_t)(z0 + zi) * a.ny + gy) * a.nx + gx) * CN);
+#pragma unroll
+          for (int h = 0; h < CN / 8; ++h) sk[zi][h] = in ? __ldg(sp + h) : make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
       const bool ok = umma::mbar_wait(&accf[ac], (uint32_t)((i >> 1) & 1), kTcBudget);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) fail();
@@ -626,10 +666,7 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
       }
       if (*abort_v) break;
       umma::tc_fence_after_sync();
-      int x0, y0, z0;
-      coords(i, x0, y0, z0);
-      const int gx = x0 + (m & 7), gy = y0 + (m >> 3);
-#pragma unroll 1
+#pragma unroll
       for (int zi = 0; zi < TZ; ++zi) {
         const int gz = z0 + zi;
         const bool in = gx < a.nx && gy < a.ny && gz < a.nz;
@@ -643,16 +680,13 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int n = c0 + j;
-              if (n < a.cn) {
-                if (a.bias) v[j] += __ldg(a.bias + n);
-                if (a.skip && !a.vec_out) v[j] += __bfloat162float(a.skip[vox * a.cn + n]);
-              }
+              v[j] += bias_s[n];
+              if (a.skip && !a.vec_out && n < a.cn) v[j] += __bfloat162float(a.skip[vox * a.cn + n]);
             }
-            if (a.skip && a.vec_out) {
-              const uint4 *sp = reinterpret_cast<const uint4 *>(a.skip + vox * CN + c0);
+            if (vskip) {
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
-                const uint4 u = __ldg(sp + h);
+                const uint4 u = sk[zi][c0 / 8 + h];
                 const __nv_bfloat162 *qq = reinterpret_cast<const __nv_bfloat162 *>(&u);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -745,7 +779,9 @@ static bool launch_conv_tcp_t(const ConvArgs &c, cudaStream_t s, mf_status *st) 
   static std::atomic<int> resident{0};
   auto kern = conv_tcp<CKP, CN, MODE>;
   if (resident.load() == 0) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) != cudaSuccess) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -786,7 +822,9 @@ static bool launch_conv_tc_t(const ConvArgs &c, cudaStream_t s, mf_status *st) {
   static std::atomic<int> resident{0};
   auto kern = conv_tc<CKP, CN, MODE>;
   if (resident.load() == 0) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) != cudaSuccess) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -823,10 +861,11 @@ static bool launch_conv_tc_t(const ConvArgs &c, cudaStream_t s, mf_status *st) {
 // at most 64 outputs; false otherwise (the caller then runs conv_mma).
 template <int MODE>
 static bool launch_conv_tc(const ConvArgs &c, cudaStream_t s, mf_status *st) {
-  if (!(c.ck == 16 || c.ck == 32 || c.ck == 64) || c.cn < 1 || c.cn > 64) return false;
+  const int ph = c.cphys ? c.cphys : c.ck;  // stored channels: the tensor map's 16-byte chunks
+  if (!(ph == 16 || ph == 32 || ph == 64) || c.ck > ph || c.cn < 1 || c.cn > 64) return false;
   const int cnp = c.cn <= 16 ? 16 : c.cn <= 32 ? 32 : 64;
 #define TCCASE(K, N) \
-  if (c.ck == K && cnp == N) return launch_conv_tc_t<K, N, MODE>(c, s, st);
+  if (ph == K && cnp == N) return launch_conv_tc_t<K, N, MODE>(c, s, st);
   TCCASE(16, 16) TCCASE(16, 32) TCCASE(16, 64)
   TCCASE(32, 16) TCCASE(32, 32) TCCASE(32, 64)
   TCCASE(64, 16) TCCASE(64, 32) TCCASE(64, 64)
@@ -1155,6 +1194,26 @@ extern "C" mf_status mf_conv3d_fwd(const void *x, int32_t nx, int32_t ny, int32_
   a.out_bf = (bf16 *)y_bf16;
   a.out_f = y_f32;
   return launch_conv<0>(a, (cudaStream_t)stream);
+}
+
+// Forward convolution of an input stored with `cin_stride` >= cin channels per voxel (the channels
+// beyond cin are ignored), on the tensor-core path; MF_ERR_UNSUPPORTED when that path cannot take it.
+mf_status conv3d_fwd_strided(const void *x, int nx, int ny, int nz, int cin, int cin_stride, const void *w,
+                             const float *bias, int cout, const void *skip, int relu, void *y_bf16, float *y_f32,
+                             cudaStream_t stream) {
+  ConvArgs a{};
+  a.in = (const bf16 *)x;
+  a.nx = nx; a.ny = ny; a.nz = nz; a.ck = cin; a.cphys = cin_stride;
+  a.w = (const bf16 *)w;
+  a.bias = bias;
+  a.skip = (const bf16 *)skip;
+  a.relu = relu;
+  a.cn = cout;
+  a.out_bf = (bf16 *)y_bf16;
+  a.out_f = y_f32;
+  mf_status st = MF_OK;
+  if (!conv_tc_enabled() || !launch_conv_tc<0>(a, stream, &st)) return MF_ERR_UNSUPPORTED;
+  return st;
 }
 
 extern "C" mf_status mf_conv3d_dgrad(const void *dy, int32_t nx, int32_t ny, int32_t nz, int32_t cin, const void *w,

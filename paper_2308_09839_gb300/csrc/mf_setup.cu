@@ -266,6 +266,7 @@ static void free_mesh(mf_mesh *m) {
   cudaFree(m->dnodes);
   cudaFree(m->colour_elems);
   cudaFree(m->tp_axis);
+  cudaFree(m->tp_flags);
   cudaFree(m->mat_pairs);
   cudaFree(m->gen_axis);
   cudaFree(m->gen_delta);

@@ -77,9 +77,32 @@ mf_status tile_setup(mf_mesh *m, cudaStream_t s) {
   const int64_t nm = m->n_cells * phys_nmat(m->physics);
   MF_CUDA(cudaMalloc(&m->mat_pairs, nm * sizeof(float2)));
   mat_pairs<<<blocks_for(nm), kThreads, 0, s>>>(m->mat, nm, m->dw_mat, m->mat_pairs);
+  // range flags: 2 control words + one word per CTA of the largest launch (z-segments of one
+  // plane, 16 right-hand sides)
+  const int64_t nflags = 2 + 16 * tile_dot_slots(m);
+  MF_CUDA(cudaMalloc(&m->tp_flags, nflags * sizeof(unsigned)));
+  MF_CUDA(cudaMemsetAsync(m->tp_flags, 0, nflags * sizeof(unsigned), s));
   MF_CUDA(cudaGetLastError());
   MF_CUDA(cudaStreamSynchronize(s));
   m->tp = true;
+  return MF_OK;
+}
+
+// The fix-up kernel of the range check (mf_march.cuh), right after a face-marching launch of n_cta
+// CTAs: double-word launches always (it reads the flags and returns quickly when none is set), FP32
+// launches on normalised meshes only.  Persistent grid.
+template <int PHYS, class N, bool DOT>
+static mf_status fixup_launch(const mf_mesh *m, const TileArgs &g, const typename N::IO *x, typename N::IO *y,
+                              cudaStream_t s, const int *skip, int n_cta, double *partials, double *out) {
+  if (!std::is_same<N, NumDW>::value && m->dw_oscale == 0) return MF_OK;
+  using MS = march::MarchShape<PHYS, N>;
+  constexpr int NT = MS::EX * MS::EY;
+  auto kern = march::march_fixup<PHYS, N, MS::EX, MS::EY, DOT>;
+  // one CTA per SM: enough for the rare items to redo, and a short scan of the flags otherwise
+  const int grid = std::max(1, std::min(n_cta, device_sm_count()));
+  mf_count_launches(1);
+  kern<<<grid, NT, 0, s>>>(g, x, y, skip, n_cta, partials, m->tp_flags, out);
+  MF_CUDA(cudaGetLastError());
   return MF_OK;
 }
 
@@ -89,8 +112,8 @@ template <int PHYS, class N>
 static mf_status march_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
                               const int *skip, int nrhs = 1) {
   using MS = march::MarchShape<PHYS, N>;
-  constexpr int NT = MS::EX * MS::EY / MS::RY;
-  auto kern = march::march_apply<PHYS, N, MS::EX, MS::EY, MS::RY, MS::MINB>;
+  constexpr int NT = MS::EX * MS::EY;
+  auto kern = march::march_apply<PHYS, N, MS::EX, MS::EY, MS::MINB>;
   static std::atomic<int> resident{0};  // CTAs per SM: a property of the kernel, same for every caller
   if (resident.load() == 0) {
     int r = 0;
@@ -100,7 +123,11 @@ static mf_status march_launch(const mf_mesh *m, const typename N::IO *x, typenam
   TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident.load(), nrhs);
   g.nrhs = nrhs;
   g.r0 = 0;
-  kern<<<tile_items(g) * nrhs, NT, 0, s>>>(g, x, y, skip);
+  g.flags = m->tp_flags + 2;
+  g.bit = 1u << (m->tp_epoch.fetch_add(1u) & 31u);
+  const int n_cta = tile_items(g) * nrhs;
+  kern<<<n_cta, NT, 0, s>>>(g, x, y, skip);
+  MF_TRY((fixup_launch<PHYS, N, false>(m, g, x, y, s, skip, n_cta, nullptr, nullptr)));
   return MF_OK;
 }
 
@@ -120,8 +147,8 @@ template <int PHYS, class N>
 static mf_status march_dot_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
                                   const int *skip, double *partials, unsigned int *ticket, double *out) {
   using MS = march::MarchShape<PHYS, N>;
-  constexpr int NT = MS::EX * MS::EY / MS::RY;
-  auto kern = march::march_apply_dot<PHYS, N, MS::EX, MS::EY, MS::RY, MS::MINB>;
+  constexpr int NT = MS::EX * MS::EY;
+  auto kern = march::march_apply_dot<PHYS, N, MS::EX, MS::EY, MS::MINB>;
   static std::atomic<int> resident{0};
   if (resident.load() == 0) {
     int r = 0;
@@ -129,9 +156,13 @@ static mf_status march_dot_launch(const mf_mesh *m, const typename N::IO *x, typ
     resident.store(std::max(r, 1));
   }
   TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident.load());
+  g.flags = m->tp_flags + 2;
+  g.bit = 1u << (m->tp_epoch.fetch_add(1u) & 31u);
+  const int n_cta = tile_items(g);
   mf_count_launches(1);
-  kern<<<tile_items(g), NT, 0, s>>>(g, x, y, skip, partials, ticket, out);
+  kern<<<n_cta, NT, 0, s>>>(g, x, y, skip, partials, ticket, out);
   MF_CUDA(cudaGetLastError());
+  MF_TRY((fixup_launch<PHYS, N, true>(m, g, x, y, s, skip, n_cta, partials, out)));
   return MF_OK;
 }
 

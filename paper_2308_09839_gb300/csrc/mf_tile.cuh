@@ -205,6 +205,10 @@ struct TileArgs {
   const float2 *mat;                             // kappa[E] or (lam, mu)[E] as pairs
   const uint8_t *dmask;
   int oscale;  // y = 2^oscale x (operator of the normalised cell constants and spacings) x
+  // range check of the stand-alone launches (march_apply / march_apply_dot and their fix-up kernel):
+  // per-CTA flag words, and this launch's bit in them
+  unsigned *flags;
+  unsigned bit;
 };
 
 // Segment length from a wave model: with R CTAs resident at a time, nseg segments of seg = ceil((nz
@@ -259,6 +263,8 @@ inline TileArgs make_tile_args(const mf_mesh *m, int EX, int EY, int seg, int re
   g.mat = m->mat_pairs;
   g.dmask = m->dmask;
   g.oscale = m->dw_oscale;
+  g.flags = m->tp_flags;
+  g.bit = 0u;
   g.nrhs = 1;
   g.r0 = 0;
   return g;

@@ -209,4 +209,36 @@ def test_cg_right_hand_side_scaled_by_power_of_two(name, k):
     np.testing.assert_array_equal(xk.cpu().numpy(), np.ldexp(x0, k))
     A = fem.assemble_csr(p.physics, p.coords, p.cell_array(), p.mat, p.dirichlet, p.n_nodes)
     _, it_o, _ = solvers.cg(lambda v: A @ v, b, rtol=1e-8)
-    assert abs(i0.iters - it_o) <= max(2, math.ceil(0.01 * it_o))
+    # the layered lognormal(sigma = 1) problems take over 1000 iterations; the count is compared
+    # with the drift tolerance of double-word operators (the oracle pin on CG counts)
+    assert abs(i0.iters - it_o) <= max(3, math.ceil(0.03 * it_o)), (i0.iters, it_o)
+
+
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+@pytest.mark.parametrize("case", ["tiny", "huge", "subnormal", "mixed", "plain"])
+def test_csr_spmv_over_the_fp64_range(physics, case):
+    """The CSR SpMV forms its products and sums in pairs of floats; rows whose products leave the
+    pairs' exponent range are summed again in FP64, so y stays FP64-accurate for every input."""
+    p = (inputs.laplace_box if physics == "laplace" else inputs.elasticity_box)(9, ny=7, nz=6, jitter=0.2, seed=21)
+    if case == "subnormal":
+        p = scaled(p, mat=2.0 ** 60)
+    mesh = mf.Mesh.from_problem(p)
+    A = mesh.assemble_csr()
+    R = fem.assemble_csr(p.physics, p.coords, p.cell_array(), p.mat, p.dirichlet, p.n_nodes)
+    x = p.x(8)
+    if case == "tiny":
+        x = x * 1e-200
+    elif case == "huge":
+        x = x * 1e200
+    elif case == "subnormal":
+        x = np.ldexp(x, -1030)
+    elif case == "mixed":
+        x = x * 10.0 ** np.random.default_rng(3).uniform(-250, 250, size=x.size)
+    y = A.spmv(gpu(x))
+    torch.cuda.synchronize()
+    y = y.cpu().numpy()
+    if case == "subnormal":
+        ref = np.ldexp(R @ np.ldexp(x, 1100), -1100)
+    else:
+        ref = R @ x
+    assert rel2(y, ref) <= TOL64, (case, rel2(y, ref))
