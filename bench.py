@@ -523,9 +523,17 @@ def main():
         for (p, m, x, y) in meshes:
             b = torch.from_numpy(p.b()).cuda()
             xs, info = m.cg(b, timeout_s=args.cg_timeout, ok=CG_OK)
+            xs = xs.clone()
             cg[p.physics] = {"seconds": info.seconds, "iters": info.iters, "status": info.status,
                              "rel_res_true": info.rel_res_true,
-                             "cg_gdofs": p.n_free * info.iters / info.seconds / 1e9}
+                             "cg_gdofs": p.n_free * info.iters / info.seconds / 1e9,
+                             "ms_per_iter": 1e3 * info.seconds / max(info.iters, 1)}
+            # the same recurrence with separate vector kernels: same iterates, bitwise
+            xsp, isp = m.cg(b, timeout_s=args.cg_timeout, ok=CG_OK, recurrence=mf.MF_CG_CLASSIC_SPLIT)
+            cg[p.physics]["split_kernels"] = {"seconds": isp.seconds, "iters": isp.iters,
+                                              "ms_per_iter": 1e3 * isp.seconds / max(isp.iters, 1),
+                                              "bitwise_equal_solution": bool(torch.equal(xs, xsp))}
+            del xsp
             # single-synchronisation recurrence (Chronopoulos-Gear): one kernel fewer per iteration
             _, ip = m.cg(b, timeout_s=args.cg_timeout, ok=CG_OK, recurrence=mf.MF_CG_PIPELINED)
             cg[p.physics]["pipelined"] = {"seconds": ip.seconds, "iters": ip.iters, "status": ip.status,
@@ -575,7 +583,7 @@ def main():
     # CSR SpMV, and CG to 1e-8 both ways (tetrahedra, Laplace).  The FP64 kernels are bound by the
     # FP64 pipe: FP64 operations per element of their formulations (bytes_model.tet_apply_flops,
     # q2_apply_flops) against the measured 1.20 TFLOP/s of FP64 FMA.
-    Q2_PA_FLOPS = bm.q2_apply_flops("laplace", partial_assembly=True)["total"]
+    Q2_PA_FLOPS = {ph: bm.q2_apply_flops(ph, partial_assembly=True)["total"] for ph in ("laplace", "elasticity")}
     if not args.no_tet:
         tf_ = {ph: bm.tet_apply_flops(ph)["total"] for ph in ("laplace", "elasticity")}
         qf_ = {ph: bm.q2_apply_flops(ph)["total"] for ph in ("laplace", "elasticity")}
@@ -605,11 +613,11 @@ def main():
                 ta = timed_t(lambda: mt.apply(xt, yt), reps)
                 t32 = timed_t(lambda: mt.apply(x32, y32), reps)
                 pa = bool(mt.info["partial_assembly"])
-                if pa:  # Q2 Laplace: AUTO is the sum-factorised partial assembly; time the reference too
+                if pa:  # Q2: AUTO is the sum-factorised partial assembly; time the reference too
                     mt.set_variant(mf.MF_VARIANT_REFERENCE)
                     tref = timed_t(lambda: mt.apply(xt, yt), reps)
                     mt.set_variant(mf.MF_VARIANT_AUTO)
-                tf = (Q2_PA_FLOPS if pa else flops[phys]) * pt.n_cells / ta / 1e12
+                tf = (Q2_PA_FLOPS[phys] if pa else flops[phys]) * pt.n_cells / ta / 1e12
                 r = {"mesh": f"{nb}^3 boxes, {what}, jitter 0.1h", "cells": pt.n_cells, "free_dof": pt.n_free,
                      "colours": mt.info["n_colours"], "ms_apply": 1e3 * ta, "gdofs_apply": pt.n_free / ta / 1e9,
                      "ms_apply_f32": 1e3 * t32, "fp64_tflops": tf, "fp64_frac": tf / 1.20,

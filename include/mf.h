@@ -25,6 +25,7 @@
 #ifndef MF_H_
 #define MF_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -108,7 +109,9 @@ mf_status mf_destroy_mesh(mf_mesh *mesh);
  * tensor-product grid of axis-aligned cells, which enables the FP64-accurate tile kernels, bit 3:
  * partial-assembly data built, bit 4: tetrahedral mesh, bit 5: Q2 mesh, bit 6: structured mesh whose
  * cell constants or cell sizes span more than the double-word kernels cover, so that every apply
- * runs the FP64 reference kernel; see "Range" below). */
+ * runs the FP64 reference kernel; bit 7: double-word data built from cell constants or coordinates
+ * normalised by a power of two, which the kernels undo exactly on their results; see "Range"
+ * below). */
 mf_status mf_mesh_query(const mf_mesh *mesh, int64_t *n_nodes, int64_t *n_cells, int64_t *n_dof,
                         int64_t *n_free, int32_t *n_colours, int32_t *flags);
 
@@ -229,14 +232,22 @@ enum { MF_OP_MATFREE = 0, MF_OP_CSR = 1 };
 enum { MF_PREC_FP64 = 0, MF_PREC_MIXED_IR = 1 };
 enum { MF_PC_NONE = 0, MF_PC_JACOBI = 1, MF_PC_LEARNED = 2 };
 /* CG recurrence (FP64 solves with MF_PC_NONE or MF_PC_JACOBI):
- *   MF_CG_CLASSIC    Hestenes-Stiefel as in Table 4: per iteration the apply (with p^T A p fused on
- *                    tensor-product meshes), the x/r update with r^T z, and the p update
+ *   MF_CG_CLASSIC    Hestenes-Stiefel as in Table 4.  On scalar Laplace tensor-product meshes with the
+ *                    auto variant (without normalisation: mf_mesh_query flag bit 7 clear) the vector
+ *                    updates are fused into the apply: its kernel forms p_k = z_k + beta p_{k-1} at
+ *                    the nodes it stages, stores p_k and the deferred x += alpha p_{k-1} at the nodes
+ *                    it owns, and returns A p_k with p_k^T A p_k; one vector kernel then updates r and
+ *                    forms r^T z.  Elsewhere: the apply (p^T A p fused on tensor-product meshes), the
+ *                    x/r update with r^T z, and the p update.
  *   MF_CG_PIPELINED  single-synchronisation recurrence of Chronopoulos and Gear (1989): w = A u
  *                    (u = M^-1 r) with u^T w fused into the apply, then one pass that updates p, s = A p,
- *                    x, r and u and forms r^T u; one kernel fewer per iteration, the same iterates
- *                    in exact arithmetic.  Not available for MIXED_IR, the learned preconditioner,
- *                    mf_cg_solve_noalloc or the batched solver (MF_ERR_ARG). */
-enum { MF_CG_CLASSIC = 0, MF_CG_PIPELINED = 1 };
+ *                    x, r and u and forms r^T u; the same iterates in exact arithmetic.
+ *   MF_CG_CLASSIC_SPLIT  the classic recurrence with the separate vector kernels everywhere.  Its
+ *                    iterates, iteration count and solution are bitwise those of MF_CG_CLASSIC (the
+ *                    fused kernels evaluate the same FP64 formulas on the same values).
+ * PIPELINED and CLASSIC_SPLIT are not available for MIXED_IR, the learned preconditioner,
+ * mf_cg_solve_noalloc or the batched solver (MF_ERR_ARG). */
+enum { MF_CG_CLASSIC = 0, MF_CG_PIPELINED = 1, MF_CG_CLASSIC_SPLIT = 2 };
 typedef struct mf_net mf_net;
 
 typedef struct {
@@ -257,7 +268,7 @@ typedef struct {
   int32_t max_outer;     /* MIXED_IR: refinement steps */
   const mf_csr *csr;     /* operator when op == MF_OP_CSR */
   const mf_net *net;     /* network when precond == MF_PC_LEARNED (flexible CG, see mf_net_create) */
-  int32_t recurrence;    /* MF_CG_CLASSIC (default) or MF_CG_PIPELINED */
+  int32_t recurrence;    /* MF_CG_CLASSIC (default), MF_CG_PIPELINED or MF_CG_CLASSIC_SPLIT */
 } mf_solve_opts;
 
 typedef struct {
@@ -294,6 +305,32 @@ void mf_solve_opts_default(mf_solve_opts *opts);
  */
 mf_status mf_cg_solve(mf_mesh *mesh, const mf_solve_opts *opts, const double *b, double *x,
                       mf_solve_info *info, mf_stream stream);
+
+/*
+ * CG checkpoint and resume.  The paper has no counterpart; this lets a long solve stop (iteration
+ * limit, wall-clock budget, the process's own schedule) and continue later, in another process or
+ * after the device was handed to other work.
+ *
+ * mf_cg_state_save copies the state of the last mf_cg_solve (or mf_cg_resume) on this mesh to host
+ * memory: the iteration count k, the scalars of the recurrence (r.z, ||r||^2, ||b||^2, the
+ * tolerance, beta) and the vectors x_k, r_k and the last search direction.  Only a solve that
+ * stopped with MF_NOT_CONVERGED or MF_ERR_TIMEOUT in FP64 with MF_PC_NONE or MF_PC_JACOBI and the
+ * classic recurrence (fused or MF_CG_CLASSIC_SPLIT) leaves a state; otherwise MF_ERR_ARG.  The call
+ * synchronises the stream.
+ *   host_state: mf_cg_state_bytes(mesh) bytes of host memory (caller-owned); bytes: its size.
+ *
+ * mf_cg_resume continues that solve: opts must name the same operator, preconditioner and
+ * recurrence, and b must be the same right-hand side; opts->max_iter and rtol apply to the whole
+ * solve (iterations count from the original start).  Then iterations, residual records and the
+ * solution are bitwise those of a solve that was never interrupted (a state saved on one GPU resumes
+ * on another of the same kind).  The state's vector length must equal the mesh's n_dof.
+ *   Arguments and returns as for mf_cg_solve; MF_ERR_ARG for a state of another mesh size,
+ *   preconditioner or recurrence, or a corrupt header.
+ */
+size_t mf_cg_state_bytes(const mf_mesh *mesh);
+mf_status mf_cg_state_save(mf_mesh *mesh, void *host_state, size_t bytes, mf_stream stream);
+mf_status mf_cg_resume(mf_mesh *mesh, const mf_solve_opts *opts, const void *host_state, size_t bytes, const double *b,
+                       double *x, mf_solve_info *info, mf_stream stream);
 
 /*
  * mf_cg_solve_noalloc - the unpreconditioned FP64 CG of mf_cg_solve for callers that cannot

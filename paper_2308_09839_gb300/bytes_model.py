@@ -141,12 +141,16 @@ def q2_apply_flops(physics: str, partial_assembly: bool = False) -> dict:
     mul each) and J (27 x 9 multiply-adds) = 648; adj J and det J 32; the gradient of u (27 x 3
     multiply-adds per component, 324 or 648 with the gradients reused); the flux (Laplace, 40) or
     the stress (elasticity, 150); the scatter (27 x 3 multiply-adds per component, 324 or 648).
-    Partial assembly with sum factorisation (Laplace): 16 one-dimensional contractions of 27 x 3
-    multiply-adds and 27 flux products D_q g_q of 9 multiply-adds."""
+    Partial assembly with sum factorisation: 16 one-dimensional contractions of 27 x 3 multiply-adds
+    per component; per Gauss point the flux D_q g_q (Laplace, 9 multiply-adds), or for elasticity
+    grad u = H K and P = S K^T (27 multiply-adds each) and the stress S (9 multiply-adds for the
+    symmetric part, 2 adds and a multiply for the trace, 3 adds on the diagonal)."""
     if partial_assembly:
         if physics == "elasticity":
-            raise ValueError("the Q2 partial assembly is built for Laplace and vector Laplace")
-        parts = {"contractions": 2 * 16 * 81, "flux": 2 * 27 * 9}
+            parts = {"contractions": 3 * 2 * 16 * 81, "gradient": 27 * 2 * 27, "stress": 27 * (2 * 9 + 3 + 3),
+                     "back": 27 * 2 * 27}
+        else:
+            parts = {"contractions": 2 * 16 * 81, "flux": 2 * 27 * 9}
     elif physics == "elasticity":
         parts = {"jacobian": 27 * 648, "adjugate": 27 * 32, "gradient": 27 * 648, "stress": 27 * 150,
                  "scatter": 27 * 648}

@@ -286,6 +286,166 @@ __global__ void __launch_bounds__(64) q2pa_build(MeshView m, double *__restrict_
   }
 }
 
+// Q2 elasticity partial assembly (Eq. 6 with the Q2 map): per Gauss point K = J^-1 (9 values, K[c][l] =
+// dxi_c/dx_l) and w det J lambda, w det J mu, stored [element][11][32] (points q < 27 used) so that the
+// apply's warp reads each value of its element's 27 points with one coalesced load.
+constexpr int kQ2ElVals = 11;
+__global__ void __launch_bounds__(64) q2pa_el_build(MeshView m, double *__restrict__ D) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_cells) return;
+  double X[27][3];
+  for (int a = 0; a < 27; ++a) {
+    const int64_t n = m.cells[27 * e + a];
+    for (int i = 0; i < 3; ++i) X[a][i] = m.X[3 * n + i];
+  }
+  const double lam = m.mat[2 * e], mu = m.mat[2 * e + 1];
+  double *De = D + e * kQ2ElVals * 32;
+  for (int q = 0; q < 27; ++q) {
+    double xi[3];
+    q2::point_q(q, xi);
+    q2::Tab<double> t;
+    q2::tables_at<double>(xi, t);
+    double J[3][3], C[3][3];
+    q2::jacobian(X, t, J);
+    const double det = q1::adjugate(J, C);
+    for (int c = 0; c < 3; ++c)
+      for (int l = 0; l < 3; ++l) De[(3 * c + l) * 32 + q] = C[c][l] / det;
+    const double wd = q2::weight_q(q) * det;
+    De[9 * 32 + q] = wd * lam;
+    De[10 * 32 + q] = wd * mu;
+  }
+}
+
+namespace q2w {
+
+// One-dimensional contraction of a warp's element array along axis AX (0 x, 1 y, 2 z) for the three
+// components: out[k] at this lane's index o = sum_i M[q][i] in[k][base + i st] (TRANS: M[i][q]), q the
+// index of o along AX.  M is a 3 x 3 table in shared memory, in[k] a 32-entry row (27 used).
+template <int AX, bool TRANS>
+__device__ __forceinline__ void contract3(const double (*M)[3], const double (*in)[32], int o, double out[3]) {
+  constexpr int st = AX == 0 ? 1 : AX == 1 ? 3 : 9;
+  const int q = (o / st) % 3, base = o - q * st;
+  const double m0 = TRANS ? M[0][q] : M[q][0], m1 = TRANS ? M[1][q] : M[q][1], m2 = TRANS ? M[2][q] : M[q][2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    out[k] = __fma_rn(m2, in[k][base + 2 * st], __fma_rn(m1, in[k][base + st], m0 * in[k][base]));
+}
+
+__device__ __forceinline__ void put3(double (*dst)[32], int o, const double v[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dst[k][o] = v[k];
+}
+
+}  // namespace q2w
+
+// Q2 elasticity apply from the partial assembly: one warp per element, lane o < 27 is node o for the
+// gather and the results and Gauss point o for the stress.  The reference gradients of the three
+// components at the 27 points are formed by one-dimensional contractions with the 1D value and
+// derivative tables B and G (the sum factorisation of the Q2 Laplace kernel: 8 passes of 3 multiply-adds
+// per entry instead of 27 x 3), the stress P = S K^T with S = w det J (mu (grad u + grad u^T) + lambda
+// tr(grad u) I), grad u = H K per point, and the transposed contractions take P back to the nodes.  The
+// element's 27 x 3 results go to its own slots (as q2pa_elements); q2pa_gather sums them per node.
+__global__ void __launch_bounds__(128) q2pa_el_elements(MeshView m, const double *__restrict__ D,
+                                                       const double *__restrict__ x, int nrhs, int r,
+                                                       double *__restrict__ buf, const int *__restrict__ skip) {
+  constexpr int W = 4;  // elements (warps) per block
+  __shared__ double tB[3][3], tG[3][3];
+  __shared__ double sU[W][3][32], sA[W][3][32], sB[W][3][32];
+  if (skip && *skip) return;
+  if (threadIdx.x < 9) {
+    const q2::SF t = q2::sf_tables();
+    tB[threadIdx.x / 3][threadIdx.x % 3] = t.B[threadIdx.x / 3][threadIdx.x % 3];
+    tG[threadIdx.x / 3][threadIdx.x % 3] = t.G[threadIdx.x / 3][threadIdx.x % 3];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, o = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * W + w;
+  if (e >= m.n_cells) return;  // whole warps; no block barrier follows
+  const bool lv = o < 27;
+  double (*U)[32] = sU[w], (*A)[32] = sA[w], (*B)[32] = sB[w];
+  if (lv) {
+    const int64_t node = __ldg(m.cells + 27 * e + o);
+    const bool dir = m.dmask[node] != 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) U[k][o] = dir ? 0.0 : x[(node * nrhs + r) * 3 + k];
+  }
+  __syncwarp();
+  double t[3], gx[3], gy[3], gz[3];
+  // reference gradients: gx = Gx By Bz u, gy = Bx Gy Bz u, gz = Bx By Gz u
+  if (lv) { q2w::contract3<2, false>(tB, U, o, t); q2w::put3(A, o, t); }
+  __syncwarp();
+  if (lv) { q2w::contract3<1, false>(tB, A, o, t); q2w::put3(B, o, t); }
+  __syncwarp();
+  if (lv) q2w::contract3<0, false>(tG, B, o, gx);
+  __syncwarp();
+  if (lv) { q2w::contract3<1, false>(tG, A, o, t); q2w::put3(B, o, t); }
+  __syncwarp();
+  if (lv) {
+    q2w::contract3<0, false>(tB, B, o, gy);
+    q2w::contract3<2, false>(tG, U, o, t);
+    q2w::put3(A, o, t);
+  }
+  __syncwarp();
+  if (lv) { q2w::contract3<1, false>(tB, A, o, t); q2w::put3(B, o, t); }
+  __syncwarp();
+  double fx[3], fy[3], fz[3];
+  if (lv) {
+    q2w::contract3<0, false>(tB, B, o, gz);
+    const double *De = D + e * kQ2ElVals * 32 + o;
+    double K[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) K[c][l] = __ldg(De + (3 * c + l) * 32);
+    const double slam = __ldg(De + 9 * 32), smu = __ldg(De + 10 * 32);
+    double G[3][3];  // grad u: G[k][l] = sum_c H[k][c] K[c][l], H[k] = (gx, gy, gz)[k]
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) G[k][l] = gx[k] * K[0][l] + gy[k] * K[1][l] + gz[k] * K[2][l];
+    const double tr = slam * (G[0][0] + G[1][1] + G[2][2]);
+    double S[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) S[k][l] = smu * (G[k][l] + G[l][k]) + (k == l ? tr : 0.0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // P[k][c] = sum_l S[k][l] K[c][l]
+      fx[k] = S[k][0] * K[0][0] + S[k][1] * K[0][1] + S[k][2] * K[0][2];
+      fy[k] = S[k][0] * K[1][0] + S[k][1] * K[1][1] + S[k][2] * K[1][2];
+      fz[k] = S[k][0] * K[2][0] + S[k][1] * K[2][1] + S[k][2] * K[2][2];
+    }
+    q2w::put3(A, o, fx);
+  }
+  __syncwarp();
+  // v = Bz^T (By^T Gx^T fx + Gy^T Bx^T fy) + Gz^T By^T Bx^T fz
+  double bb[3], v[3];
+  if (lv) { q2w::contract3<0, true>(tG, A, o, t); q2w::put3(B, o, t); }
+  __syncwarp();
+  if (lv) { q2w::contract3<1, true>(tB, B, o, bb); q2w::put3(A, o, fy); }
+  __syncwarp();
+  if (lv) { q2w::contract3<0, true>(tB, A, o, t); q2w::put3(B, o, t); }
+  __syncwarp();
+  if (lv) {
+    q2w::contract3<1, true>(tG, B, o, t);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bb[k] += t[k];
+    q2w::put3(A, o, bb);
+  }
+  __syncwarp();
+  if (lv) { q2w::contract3<2, true>(tB, A, o, v); q2w::put3(B, o, fz); }
+  __syncwarp();
+  if (lv) { q2w::contract3<0, true>(tB, B, o, t); q2w::put3(A, o, t); }
+  __syncwarp();
+  if (lv) { q2w::contract3<1, true>(tB, A, o, t); q2w::put3(B, o, t); }
+  __syncwarp();
+  if (lv) {
+    q2w::contract3<2, true>(tG, B, o, t);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) buf[(e * 27 + o) * 3 + k] = v[k] + t[k];
+  }
+}
+
 // Q2 Laplace / vector Laplace apply from the partial assembly in two launches, without colours: every
 // element at once writes its 27 x ND results to its own slots of `buf` ([element][node][comp]); then
 // every DoF sums its slots in a fixed order (the node's slot list, sorted by element) and the
@@ -358,6 +518,10 @@ mf_status q2pa_apply(const mf_mesh *m, const double *x, double *y, int nrhs, cud
       q2pa_elements<1><<<blocks_for(m->n_cells, 64), 64, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
       q2pa_gather<1><<<blocks_for(m->n_nodes), kThreads, 0, s>>>(m->n_nodes, m->q2off, m->q2slots, m->dmask,
                                                                    m->q2buf, x, y, nrhs, r, skip);
+    } else if (m->physics == MF_ELASTICITY) {
+      q2pa_el_elements<<<(unsigned)((m->n_cells + 3) / 4), 128, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
+      q2pa_gather<3><<<blocks_for(m->n_nodes * 3), kThreads, 0, s>>>(m->n_nodes, m->q2off, m->q2slots, m->dmask,
+                                                                       m->q2buf, x, y, nrhs, r, skip);
     } else {
       q2pa_elements<3><<<blocks_for(m->n_cells, 64), 64, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
       q2pa_gather<3><<<blocks_for(m->n_nodes * 3), kThreads, 0, s>>>(m->n_nodes, m->q2off, m->q2slots, m->dmask,
@@ -428,13 +592,18 @@ mf_status apply_reference(const mf_mesh *m, const R *x, R *y, cudaStream_t s, co
 
 }  // namespace
 
+size_t q2_pa_bytes(int physics, int64_t n_cells) {
+  return physics == MF_ELASTICITY ? (size_t)n_cells * kQ2ElVals * 32 * sizeof(double)
+                                  : (size_t)n_cells * 27 * 6 * sizeof(double);
+}
+
 mf_status q2_pa_setup(mf_mesh *m, cudaStream_t s) {
   if (m->q2pa) return MF_OK;
-  if (m->npe != 27 || !phys_is_laplace(m->physics)) {
-    mf_set_error("partial assembly of Q2 meshes is built for Laplace and vector Laplace");
+  if (m->npe != 27) {
+    mf_set_error("the sum-factorised partial assembly is built for Q2 meshes");
     return MF_ERR_UNSUPPORTED;
   }
-  const size_t bytes = (size_t)m->n_cells * 27 * 6 * sizeof(double);
+  const size_t bytes = q2_pa_bytes(m->physics, m->n_cells);
   cudaError_t e = cudaMalloc(&m->q2pa, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -463,7 +632,12 @@ mf_status q2_pa_setup(mf_mesh *m, cudaStream_t s) {
   MF_CUDA(cudaMemcpyAsync(m->q2off, off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   MF_CUDA(cudaMemcpyAsync(m->q2slots, slots.data(), 27 * E * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   mf_count_launches(1);
-  q2pa_build<<<blocks_for(m->n_cells, 64), 64, 0, s>>>(m->view(), m->q2pa);
+  if (m->physics == MF_ELASTICITY) {
+    MF_CUDA(cudaMemsetAsync(m->q2pa, 0, bytes, s));  // the unused point slots 27..31
+    q2pa_el_build<<<blocks_for(m->n_cells, 64), 64, 0, s>>>(m->view(), m->q2pa);
+  } else {
+    q2pa_build<<<blocks_for(m->n_cells, 64), 64, 0, s>>>(m->view(), m->q2pa);
+  }
   MF_CUDA(cudaGetLastError());
   MF_CUDA(cudaStreamSynchronize(s));
   return MF_OK;
@@ -515,6 +689,7 @@ static mf_status check_apply_args(const mf_mesh *m, const void *x, void *y, size
 }
 
 extern "C" mf_status mf_apply_laplace(const mf_mesh *m, const double *x, double *y, mf_stream stream) {
+  MF_RANGE("mf_apply_laplace");
   mf_clear_error();
   MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(double) : 0));
   MF_ARG(m->physics == MF_LAPLACE, "mf_apply_laplace: mesh was set up for another physics");
@@ -522,6 +697,7 @@ extern "C" mf_status mf_apply_laplace(const mf_mesh *m, const double *x, double 
 }
 
 extern "C" mf_status mf_apply_vector_laplace(const mf_mesh *m, const double *x, double *y, mf_stream stream) {
+  MF_RANGE("mf_apply_vector_laplace");
   mf_clear_error();
   MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(double) : 0));
   MF_ARG(m->physics == MF_VECTOR_LAPLACE, "mf_apply_vector_laplace: mesh was set up for another physics");
@@ -529,6 +705,7 @@ extern "C" mf_status mf_apply_vector_laplace(const mf_mesh *m, const double *x, 
 }
 
 extern "C" mf_status mf_apply_elasticity(const mf_mesh *m, const double *x, double *y, mf_stream stream) {
+  MF_RANGE("mf_apply_elasticity");
   mf_clear_error();
   MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(double) : 0));
   MF_ARG(m->physics == MF_ELASTICITY, "mf_apply_elasticity: mesh was set up for another physics");
@@ -536,12 +713,14 @@ extern "C" mf_status mf_apply_elasticity(const mf_mesh *m, const double *x, doub
 }
 
 extern "C" mf_status mf_apply_f32(const mf_mesh *m, const float *x, float *y, mf_stream stream) {
+  MF_RANGE("mf_apply_f32");
   mf_clear_error();
   MF_TRY(check_apply_args(m, x, y, m ? m->n_dof * sizeof(float) : 0));
   return apply_fp32(m, x, y, (cudaStream_t)stream);
 }
 
 extern "C" mf_status mf_apply_multi(const mf_mesh *m, int32_t nrhs, const double *X, double *Y, mf_stream stream) {
+  MF_RANGE("mf_apply_multi");
   mf_clear_error();
   MF_ARG(nrhs >= 1 && nrhs <= 16, "mf_apply_multi: nrhs must be in [1, 16]");
   MF_TRY(check_apply_args(m, X, Y, m ? m->n_dof * nrhs * sizeof(double) : 0));

@@ -293,6 +293,7 @@ extern "C" mf_status mf_set_tile_segment(mf_mesh *m, int32_t seg) {
 }
 
 extern "C" mf_status mf_batch_create(mf_mesh *const *meshes, int32_t n, const mf_solve_opts *o, mf_batch **out) {
+  MF_RANGE("mf_batch_create");
   mf_clear_error();
   MF_ARG(meshes && o && out && n > 0, "mf_batch_create: bad argument");
   *out = nullptr;
@@ -420,6 +421,7 @@ extern "C" mf_status mf_batch_create(mf_mesh *const *meshes, int32_t n, const mf
 
 extern "C" mf_status mf_batch_solve(mf_batch *B, const double *const *b, double *const *x, mf_solve_info *infos,
                                     mf_stream stream) {
+  MF_RANGE("mf_batch_solve");
   mf_clear_error();
   MF_ARG(B && b && x, "mf_batch_solve: null argument");
   const auto t0 = std::chrono::steady_clock::now();

@@ -16,6 +16,7 @@
 //   p = r + beta p                       read r, p; write p
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <functional>
 #include <mutex>
 
@@ -30,7 +31,7 @@ struct CgScalars {
   double bb, rr, rz, pAp, alpha, beta, tol2, res2;
   int iter, max_iter, done, status;
   unsigned int ticket;
-  int pad;
+  int xpend;  // the last x/r update ran: alpha p of that iteration is still owed to x (fused CG)
 };
 
 // Sum NV per-thread values over the whole grid.  Returns true in the last block to arrive, whose
@@ -107,6 +108,9 @@ __global__ void __launch_bounds__(kRedThreads) cg_init(int64_t n, const R *__res
     sc->bb = out[0];
     sc->rr = out[0];
     sc->rz = out[1];
+    sc->alpha = 0.0;  // the fused iteration's first apply: p_0 = z_0 + 0 p and x += 0 p
+    sc->beta = 0.0;
+    sc->xpend = 0;
     sc->tol2 = rtol * rtol * out[0];
     sc->iter = 0;
     sc->max_iter = max_iter;
@@ -131,6 +135,7 @@ __global__ void __launch_bounds__(kRedThreads) cg_pap(int64_t n, const R *__rest
 }
 
 // x += alpha p; r -= alpha Ap; rho' = r.z (z = M r), ||r||^2; beta = rho'/rho; convergence test.
+// x null: r only (the fused iteration adds alpha p to x in the next apply, or cg_flush_x at the end).
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) cg_update_xr(int64_t n, R *__restrict__ x, R *__restrict__ r,
                                                             const R *__restrict__ p, const R *__restrict__ Ap,
@@ -143,15 +148,19 @@ __global__ void __launch_bounds__(kRedThreads) cg_update_xr(int64_t n, R *__rest
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       sc->status = MF_ERR_BREAKDOWN;
       sc->done = 1;
+      sc->xpend = 0;
     }
     return;
   }
   const double alpha = sc->rz / pap;
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc->alpha = alpha;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->alpha = alpha;
+    sc->xpend = 1;
+  }
   double v[2] = {0.0, 0.0};
   GRID_STRIDE(i, n) {
-    x[i] = (R)((double)x[i] + alpha * (double)p[i]);
-    const R ri = (R)((double)r[i] - alpha * (double)Ap[i]);
+    if (x) x[i] = (R)__fma_rn(alpha, (double)p[i], (double)x[i]);
+    const R ri = (R)__fma_rn(-alpha, (double)Ap[i], (double)r[i]);
     r[i] = ri;
     const double rd = (double)ri;
     v[0] += rd * rd;
@@ -183,9 +192,21 @@ __global__ void __launch_bounds__(kRedThreads) cg_update_p(int64_t n, const R *_
   if (sc->done) return;
   const double beta = sc->beta;
   GRID_STRIDE(i, n) {
-    const double z = invdiag ? (double)r[i] * invdiag[i] : (double)r[i];
-    p[i] = (R)(z + beta * (double)p[i]);
+    const double z = invdiag ? __dmul_rn((double)r[i], invdiag[i]) : (double)r[i];
+    p[i] = (R)__fma_rn(beta, (double)p[i], z);
   }
+}
+
+// End of a fused CG solve that started at iteration iter0: the last iteration's x += alpha p, if its
+// x/r update ran (p_k is in p0 when k - iter0 is even, in p1 when it is odd; k = iter - 1).
+__global__ void __launch_bounds__(kRedThreads) cg_flush_x(int64_t n, double *__restrict__ x,
+                                                          const double *__restrict__ p0,
+                                                          const double *__restrict__ p1, const CgScalars *sc,
+                                                          int iter0) {
+  if (!sc->xpend) return;
+  const double alpha = sc->alpha;
+  const double *p = ((sc->iter - 1 - iter0) & 1) ? p1 : p0;
+  GRID_STRIDE(i, n) x[i] = __fma_rn(alpha, p[i], x[i]);
 }
 
 // ---- single-synchronisation CG (Chronopoulos and Gear 1989), the pipelined recurrence.  With
@@ -359,6 +380,7 @@ struct CgWorkspace {
   int64_t n = 0;
   double *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *invdiag = nullptr, *bb = nullptr;
   double *s = nullptr, *u = nullptr;  // pipelined recurrence: s = A p, u = M^-1 r (Jacobi only)
+  double *p2 = nullptr;               // fused classic iteration: p of odd iterations (p: even)
   float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr;
   double *partials = nullptr;
   double *dotp = nullptr;       // per-CTA parts of the dot product fused into the apply
@@ -385,6 +407,12 @@ struct CgWorkspace {
     int64_t kernels = 0;  // kernel nodes per replay
   } g[2];
   bool invdiag_ready = false;  // invdiag holds 1 / diag(A) of this mesh
+  // What the last classic FP64 solve left for mf_cg_state_save: fused (1) or split (0) iteration, -1
+  // for no state; its status and preconditioner; where its last search direction is and whether the
+  // split kernels had already formed p_k from it.
+  int last_fused = -1, last_status = 0, last_precond = 0;
+  const double *last_p = nullptr;
+  bool last_p_new = false;
 };
 
 void cg_workspace_free(CgWorkspace *w) {
@@ -392,7 +420,7 @@ void cg_workspace_free(CgWorkspace *w) {
   for (auto &g : w->g)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   cudaFree(w->x); cudaFree(w->r); cudaFree(w->p); cudaFree(w->Ap); cudaFree(w->invdiag); cudaFree(w->bb);
-  cudaFree(w->s); cudaFree(w->u);
+  cudaFree(w->s); cudaFree(w->u); cudaFree(w->p2);
   cudaFree(w->x32); cudaFree(w->r32); cudaFree(w->p32); cudaFree(w->Ap32);
   cudaFree(w->partials); cudaFree(w->sc); cudaFree(w->sc32); cudaFree(w->dotp); cudaFree(w->dticket);
   if (w->h_sc) cudaFreeHost(w->h_sc);
@@ -532,6 +560,7 @@ mf_status cg_loop(CgWorkspace *w, int slot, const CgWorkspace::Key &key, const O
     g.key = key;
   }
   for (;;) {
+    MF_RANGE("mf_cg_block");
     if (use_graph) {
       MF_CUDA(cudaGraphLaunch(g.exec, s));
       mf_count_launches(g.kernels);
@@ -928,9 +957,118 @@ extern "C" void mf_solve_opts_default(mf_solve_opts *o) {
   o->recurrence = MF_CG_CLASSIC;
 }
 
+namespace {
+
+// Host layout of a CG checkpoint: this header, then x, r and the search direction (n doubles each).
+struct CgStateHeader {
+  uint64_t magic;
+  int64_t n;
+  int32_t fused;     // 1: fused classic iteration (direction p_{k-1}); 0: split kernels
+  int32_t precond;   // MF_PC_NONE or MF_PC_JACOBI
+  int32_t iter;      // k
+  int32_t p_is_new;  // split kernels: the direction is already p_k
+  double rz, rr, bb, beta;
+};
+constexpr uint64_t kStateMagic = 0x3174537447436d66ull;  // "mfCGtSt1"
+
+// Puts a checkpoint's vectors and scalars into the workspace in place of cg_init: x, r, the direction
+// (into `p`), and the device scalars (alpha = 0: the state's x already holds every update).
+mf_status restore_state(CgWorkspace *w, const CgStateHeader &h, const double *vecs, double *p, double rtol,
+                        int max_iter, cudaStream_t s) {
+  const size_t nb = (size_t)h.n * sizeof(double);
+  MF_CUDA(cudaMemcpyAsync(w->x, vecs, nb, cudaMemcpyHostToDevice, s));
+  MF_CUDA(cudaMemcpyAsync(w->r, vecs + h.n, nb, cudaMemcpyHostToDevice, s));
+  MF_CUDA(cudaMemcpyAsync(p, vecs + 2 * h.n, nb, cudaMemcpyHostToDevice, s));
+  CgScalars c{};
+  c.bb = h.bb;
+  c.rr = h.rr;
+  c.rz = h.rz;
+  c.beta = h.beta;
+  c.tol2 = rtol * rtol * h.bb;  // as cg_init forms it
+  c.iter = h.iter;
+  c.max_iter = max_iter;
+  c.done = h.iter >= max_iter ? 1 : 0;
+  c.status = c.done ? MF_NOT_CONVERGED : 0;
+  MF_CUDA(cudaStreamSynchronize(s));  // h_sc may still be read by an earlier copy on this stream
+  w->h_sc[0] = c;
+  MF_CUDA(cudaMemcpyAsync(w->sc, w->h_sc, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
+  return MF_OK;
+}
+
+// rs: a checkpoint's header to resume from (null: a new solve), rv: its vectors x, r, direction.
+mf_status cg_solve_impl(mf_mesh *m, const mf_solve_opts *o, const double *b, double *x, mf_solve_info *info,
+                        cudaStream_t stream, const CgStateHeader *rs, const double *rv);
+
+}  // namespace
+
 extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const double *b, double *x, mf_solve_info *info,
                                  mf_stream stream) {
+  MF_RANGE("mf_cg_solve");
   mf_clear_error();
+  return cg_solve_impl(m, o, b, x, info, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+extern "C" size_t mf_cg_state_bytes(const mf_mesh *m) {
+  return m ? sizeof(CgStateHeader) + 3 * (size_t)m->n_dof * sizeof(double) : 0;
+}
+
+extern "C" mf_status mf_cg_state_save(mf_mesh *m, void *host_state, size_t bytes, mf_stream stream) {
+  MF_RANGE("mf_cg_state_save");
+  mf_clear_error();
+  MF_ARG(m && host_state, "mf_cg_state_save: null argument");
+  MF_ARG(bytes >= mf_cg_state_bytes(m), "mf_cg_state_save: %zu bytes given, %zu needed", bytes, mf_cg_state_bytes(m));
+  CgWorkspace *w = m->cg;
+  MF_ARG(w && w->last_fused >= 0 && (w->last_status == MF_NOT_CONVERGED || w->last_status == MF_ERR_TIMEOUT),
+         "mf_cg_state_save: no stopped classic FP64 CG solve on this mesh to save");
+  cudaStream_t s = (cudaStream_t)stream;
+  CgScalars c;
+  MF_CUDA(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  c = w->h_sc[0];
+  CgStateHeader h{};
+  h.magic = kStateMagic;
+  h.n = m->n_dof;
+  h.fused = w->last_fused;
+  h.precond = w->last_precond;
+  h.iter = c.iter;
+  h.p_is_new = w->last_p_new ? 1 : 0;
+  h.rz = c.rz;
+  h.rr = c.rr;
+  h.bb = c.bb;
+  h.beta = c.beta;
+  std::memcpy(host_state, &h, sizeof h);
+  double *v = reinterpret_cast<double *>(static_cast<char *>(host_state) + sizeof h);
+  const size_t nb = (size_t)m->n_dof * sizeof(double);
+  MF_CUDA(cudaMemcpyAsync(v, w->x, nb, cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaMemcpyAsync(v + m->n_dof, w->r, nb, cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaMemcpyAsync(v + 2 * m->n_dof, w->last_p, nb, cudaMemcpyDeviceToHost, s));
+  MF_CUDA(cudaStreamSynchronize(s));
+  return MF_OK;
+}
+
+extern "C" mf_status mf_cg_resume(mf_mesh *m, const mf_solve_opts *o, const void *host_state, size_t bytes,
+                                  const double *b, double *x, mf_solve_info *info, mf_stream stream) {
+  MF_RANGE("mf_cg_resume");
+  mf_clear_error();
+  MF_ARG(m && o && host_state && b && x, "mf_cg_resume: null argument");
+  MF_ARG(bytes >= sizeof(CgStateHeader), "mf_cg_resume: state too small");
+  CgStateHeader h;
+  std::memcpy(&h, host_state, sizeof h);
+  MF_ARG(h.magic == kStateMagic && h.n == m->n_dof && bytes >= mf_cg_state_bytes(m) && h.iter >= 0 &&
+             (h.fused == 0 || h.fused == 1),
+         "mf_cg_resume: the state does not belong to this mesh (or is corrupt)");
+  MF_ARG(o->precision == MF_PREC_FP64, "mf_cg_resume: FP64 solves only");
+  MF_ARG(o->precond == h.precond, "mf_cg_resume: the state was written with preconditioner %d", h.precond);
+  MF_ARG(o->recurrence == MF_CG_CLASSIC || o->recurrence == MF_CG_CLASSIC_SPLIT,
+         "mf_cg_resume: the classic recurrence only");
+  const double *vecs = reinterpret_cast<const double *>(static_cast<const char *>(host_state) + sizeof h);
+  return cg_solve_impl(m, o, b, x, info, (cudaStream_t)stream, &h, vecs);
+}
+
+namespace {
+
+mf_status cg_solve_impl(mf_mesh *m, const mf_solve_opts *o, const double *b, double *x, mf_solve_info *info,
+                        cudaStream_t stream, const CgStateHeader *rs, const double *rv) {
   const auto t0 = std::chrono::steady_clock::now();
   MF_ARG(m && o && b && x, "mf_cg_solve: null argument");
   MF_ARG(o->op == MF_OP_MATFREE || o->op == MF_OP_CSR, "mf_cg_solve: unknown op %d", o->op);
@@ -944,10 +1082,10 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
     MF_ARG(o->recurrence == MF_CG_CLASSIC, "mf_cg_solve: MF_PC_LEARNED runs flexible CG (classic recurrence only)");
     return fcg_solve(m, o, b, x, info, (cudaStream_t)stream, t0);
   }
-  MF_ARG(o->recurrence == MF_CG_CLASSIC || o->recurrence == MF_CG_PIPELINED, "mf_cg_solve: unknown recurrence %d",
-         o->recurrence);
+  MF_ARG(o->recurrence == MF_CG_CLASSIC || o->recurrence == MF_CG_PIPELINED || o->recurrence == MF_CG_CLASSIC_SPLIT,
+         "mf_cg_solve: unknown recurrence %d", o->recurrence);
   MF_ARG(o->recurrence == MF_CG_CLASSIC || o->precision == MF_PREC_FP64,
-         "mf_cg_solve: the pipelined recurrence is FP64 (MIXED_IR uses the classic one)");
+         "mf_cg_solve: the pipelined and split recurrences are FP64 (MIXED_IR uses the classic one)");
   MF_ARG(o->precision == MF_PREC_FP64 || o->precond == MF_PC_NONE, "mf_cg_solve: MIXED_IR takes no preconditioner");
   MF_ARG(o->precision == MF_PREC_FP64 || o->op == MF_OP_MATFREE, "mf_cg_solve: MIXED_IR needs the matrix-free operator");
   MF_ARG(o->max_iter > 0 && o->rtol > 0 && o->check_every > 0, "mf_cg_solve: bad max_iter/rtol/check_every");
@@ -956,6 +1094,7 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
   const bool jac = o->precond == MF_PC_JACOBI;
   MF_TRY(ensure_workspace(m, mixed, jac));
   CgWorkspace *w = m->cg;
+  w->last_fused = -1;  // until this solve stops with a state to save
   const int64_t n = m->n_dof;
   if (jac) MF_TRY(ensure_invdiag(m, s));
   const mf_csr *A = o->csr;
@@ -1014,17 +1153,86 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
     if (st == MF_OK) st = (mf_status)h->status;
     iters = h->iter;
     rel_rec = h->bb > 0 ? std::sqrt(h->rr / h->bb) : 0.0;
-  } else if (!mixed) {
+  } else if (!mixed && o->recurrence == MF_CG_CLASSIC && fuse && o->op == MF_OP_MATFREE && m->dw_oscale == 0 &&
+             m->physics == MF_LAPLACE) {
+    // scalar Laplace only: with three components per node (elasticity, vector Laplace) the fused
+    // kernel's extra staging cost more than the vector kernels it saves (elasticity 160^3: 0.652
+    // against 0.635 ms per iteration, with Jacobi 0.719 against 0.666 ms)
+    MF_ARG(!rs || rs->fused == 1, "mf_cg_resume: the state was written by the split kernels (MF_CG_CLASSIC_SPLIT)");
+    // classic recurrence with the p and x updates in the apply: per iteration the fused apply (and its
+    // range fix-up) and the r update.  p_k alternates between w->p (even k) and w->p2 (odd k); a graph
+    // holds an even number of iterations, so that each replay starts on an even k.
+    if (!w->p2) MF_CUDA(cudaMalloc(&w->p2, n * sizeof(double)));
+    const double *idg = jac ? w->invdiag : nullptr;
+    if (rs) {
+      // the state's p_{k-1} and beta_{k-1} with alpha = 0 (x_k is complete): the first apply forms p_k
+      MF_TRY(restore_state(w, *rs, rv, w->p2, o->rtol, o->max_iter, s));
+    } else {
+      mf_count_launches(1);
+      // p_{-1} = z_0 with beta_{-1} = 0 and alpha_{-1} = 0: the first apply forms p_0 = z_0, leaves x = 0
+      cg_init<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->x, w->r, w->p2, idg, w->partials, w->sc, o->rtol,
+                                                        o->max_iter);
+      MF_CUDA(cudaGetLastError());
+    }
+    const int iter0 = rs ? rs->iter : 0;
+    int pos = 0;
+    IterFn iter = [&](cudaStream_t st) -> mf_status {
+      double *pn = (pos & 1) ? w->p2 : w->p, *po = (pos & 1) ? w->p : w->p2;
+      ++pos;
+      MF_TRY(tile_apply_cg_fp64(m, w->r, po, idg, pn, w->x, w->Ap, &w->sc->alpha, st, &w->sc->done, w->dotp,
+                                w->dticket, &w->sc->pAp));
+      mf_count_launches(1);
+      cg_update_xr<double><<<kRedBlocks, kRedThreads, 0, st>>>(n, nullptr, w->r, nullptr, w->Ap, idg, w->partials,
+                                                               w->sc);
+      MF_CUDA(cudaGetLastError());
+      return MF_OK;
+    };
+    const int kb = o->check_every % 2 ? 2 * o->check_every : o->check_every;
+    st = cg_loop<double>(w, 0, key64, op64, opdot64, n, w->x, w->r, w->p, w->Ap, idg, w->sc, kb, o->use_graph != 0,
+                         o->timeout_s, t0, s, h, iter);
+    if (st != MF_OK && st != MF_ERR_TIMEOUT) return st;
     mf_count_launches(1);
-    cg_init<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->x, w->r, w->p, jac ? w->invdiag : nullptr, w->partials,
-                                                      w->sc, o->rtol, o->max_iter);
+    cg_flush_x<<<kRedBlocks, kRedThreads, 0, s>>>(n, w->x, w->p, w->p2, w->sc, iter0);
     MF_CUDA(cudaGetLastError());
+    if (st == MF_OK) st = (mf_status)h->status;
+    iters = h->iter;
+    rel_rec = h->bb > 0 ? std::sqrt(h->rr / h->bb) : 0.0;
+    // the last direction: written by the apply of position iters - iter0 - 1 (the old buffer of
+    // position 0 when no iteration ran)
+    const int npos = iters - iter0;
+    w->last_p = npos <= 0 ? w->p2 : (((npos - 1) & 1) ? w->p2 : w->p);
+    w->last_p_new = false;
+    w->last_fused = 1;
+    w->last_status = st;
+    w->last_precond = o->precond;
+  } else if (!mixed) {
+    MF_ARG(!rs || rs->fused == 0, "mf_cg_resume: the state was written by the fused iteration (MF_CG_CLASSIC)");
+    if (rs) {
+      MF_TRY(restore_state(w, *rs, rv, w->p, o->rtol, o->max_iter, s));
+      if (!rs->p_is_new) {  // the solve stopped before its p update: p_k = z_k + beta_{k-1} p_{k-1}
+        mf_count_launches(1);
+        cg_update_p<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, w->r, w->p, jac ? w->invdiag : nullptr, w->sc);
+        MF_CUDA(cudaGetLastError());
+      }
+    } else {
+      mf_count_launches(1);
+      cg_init<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, b, w->x, w->r, w->p, jac ? w->invdiag : nullptr,
+                                                        w->partials, w->sc, o->rtol, o->max_iter);
+      MF_CUDA(cudaGetLastError());
+    }
     st = cg_loop<double>(w, 0, key64, op64, opdot64, n, w->x, w->r, w->p, w->Ap, jac ? w->invdiag : nullptr, w->sc,
                          o->check_every, o->use_graph != 0, o->timeout_s, t0, s, h);
     if (st != MF_OK && st != MF_ERR_TIMEOUT) return st;
     if (st == MF_OK) st = (mf_status)h->status;
     iters = h->iter;
     rel_rec = h->bb > 0 ? std::sqrt(h->rr / h->bb) : 0.0;
+    // a solve stopped by its iteration limit skipped its last p update (done was set); one stopped by
+    // the wall clock ended a whole graph block, p update included
+    w->last_p = w->p;
+    w->last_p_new = !h->done;
+    w->last_fused = 0;
+    w->last_status = st;
+    w->last_precond = o->precond;
   } else {
     // FP64 iterative refinement around an FP32 inner CG: x_{m+1} = x_m + A32^{-1}(b - A64 x_m).
     MF_CUDA(cudaMemsetAsync(w->x, 0, n * sizeof(double), s));
@@ -1110,6 +1318,8 @@ extern "C" mf_status mf_cg_solve(mf_mesh *m, const mf_solve_opts *o, const doubl
   return st;
 }
 
+}  // namespace
+
 // ------------------------------------------------------------------------------------------------
 // Allocation-free CG (mf_cg_solve_noalloc).
 //
@@ -1156,6 +1366,7 @@ mf_status noalloc_scratch(double **out) {
 
 extern "C" mf_status mf_cg_solve_noalloc(const mf_mesh *m, const mf_solve_opts *o, const double *b, double *x,
                                          mf_solve_info *info, mf_stream stream) {
+  MF_RANGE("mf_cg_solve_noalloc");
   mf_clear_error();
   const auto t0 = std::chrono::steady_clock::now();
   MF_ARG(m && o && b && x, "mf_cg_solve_noalloc: null argument");
@@ -1225,6 +1436,7 @@ extern "C" mf_status mf_cg_solve_noalloc(const mf_mesh *m, const mf_solve_opts *
 
 extern "C" mf_status mf_training_pair(mf_mesh *m, const double *b, const double *xs, const double *xk, double *r64,
                                       double *e64, float *r32, float *e32, double *sums, mf_stream stream) {
+  MF_RANGE("mf_training_pair");
   mf_clear_error();
   MF_ARG(m && b && xs && xk && r32 && e32, "mf_training_pair: null argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1249,6 +1461,7 @@ extern "C" mf_status mf_training_pair(mf_mesh *m, const double *b, const double 
 }
 
 extern "C" mf_status mf_operator_diagonal(const mf_mesh *m, double *diag, mf_stream stream) {
+  MF_RANGE("mf_operator_diagonal");
   mf_clear_error();
   MF_ARG(m && diag, "mf_operator_diagonal: null argument");
   return operator_diagonal(m, diag, (cudaStream_t)stream);

@@ -10,7 +10,6 @@
 #include <atomic>
 #include <vector>
 
-#include "mf_dw.cuh"
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
 #include "mf_q2.cuh"
@@ -354,43 +353,30 @@ __global__ void expand_columns(int64_t n_nodes, int nd, bool blockdiag, const in
   }
 }
 
-// y = A x with L lanes per row, 16-byte loads and double-word arithmetic.  On GB300 the FP64 pipe
-// runs about 0.6 T fused multiply-adds per second, which caps an FP64 SpMV at one multiply-add per
-// stored value near 50 % of the HBM bandwidth; here every product and sum is formed on the FP32 pipes
-// in pairs of floats (the TwoProd and TwoSum error-free transformations of mf_dw.cuh), FP64-accurate
-// to about 2^-48 relative per operation.  A row any of whose products leaves the pairs' exponent
-// range (a value or x outside [2^-74, 2^127), or a product outside [2^-90, 2^90]) is summed again in
-// FP64 by one lane, so results stay FP64-accurate over FP64's whole range.
-// Lane l of a row reads the value pairs (and column pairs) a0 + 2 (l + L u), u < U, from the even
-// index a0 at or just below the row start, so that every load is aligned; entries outside the row
-// are skipped.  The arrays carry padding entries past nnz so that the pair at the end of the last
-// row stays in bounds.  Rows longer than 2 L U - 1 continue in a tail loop.  Lane sums are combined
-// by a fixed shuffle tree (deterministic).
-__device__ __forceinline__ void dw_mac(dwa::dw &acc, double v, double xv, bool &bad) {
-  unsigned ev, ex;
-  const dwa::dw a = dwa::split_fast(v, ev), b = dwa::split_fast(xv, ex);
-  const bool zero = ev == 0u || ex == 0u;  // a zero (or FP64-subnormal) factor: product zero or tiny
-  const unsigned es = ev + ex;
-  bad |= !zero && (ev < 949u || ev > 1150u || ex < 949u || ex > 1150u || es < 2046u - 90u || es > 2046u + 90u);
-  bad |= (ev == 0u && v != 0.0) || (ex == 0u && xv != 0.0);  // subnormal factors: exact in FP64 only
-  acc = dwa::add(acc, dwa::mul(a, b));
-}
+// y = A x in FP64 with L lanes per row and 16-byte loads.  On GB300 the FP64 pipe runs about 0.6 T
+// fused multiply-adds per second, about as fast as HBM delivers the 12-byte entries, so the kernel is
+// shaped to spend as few FP64 instructions as possible beside the one multiply-add per entry: few lanes
+// per row (2 for up to 27 entries, 4 for up to 87), so that the shuffle tree that combines them is
+// short.  Lane l of a row reads the value pairs (and column pairs) a0 + 2 (l + L u), u < U, from the even
+// index a0 at or just below the row start, so that every load is aligned; entries outside the row are
+// skipped.  The arrays carry padding entries past nnz so that the pair at the end of the last row stays
+// in bounds.  Rows longer than 2 L U - 1 continue in a tail loop.  Each lane sums its entries in
+// order; the lane sums are combined by a fixed shuffle tree (deterministic).
+// lanes per row for rows of up to 31 entries (27-point stencils, tetrahedra)
+constexpr int kShortRowLanes = 4;
 
 template <int L, int U>
-__global__ void __launch_bounds__(256) spmv_vec(int64_t n_rows, const int64_t *__restrict__ rowptr,
-                                                const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                const double *__restrict__ x, double *__restrict__ y,
-                                                const int *__restrict__ skip) {
+__global__ void __launch_bounds__(256) spmv_pairs(int64_t n_rows, const int64_t *__restrict__ rowptr,
+                                                  const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                  const double *__restrict__ x, double *__restrict__ y,
+                                                  const int *__restrict__ skip) {
   if (skip && *skip) return;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gid / L;
   const int lane = (int)(gid % L);
-  dwa::dw acc{0.0f, 0.0f};
-  bool bad = false;
-  int64_t beg = 0, end = 0;
+  double acc = 0.0;
   if (row < n_rows) {
-    beg = __ldg(rowptr + row);
-    end = __ldg(rowptr + row + 1);
+    const int64_t beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
     const int64_t a0 = beg & ~(int64_t)1;
     double2 v[U];
     int2 c[U];
@@ -408,35 +394,19 @@ __global__ void __launch_bounds__(256) spmv_vec(int64_t n_rows, const int64_t *_
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t p = a0 + 2 * (lane + (int64_t)L * u);
-      if (p >= beg && p < end) dw_mac(acc, v[u].x, __ldg(x + c[u].x), bad);
-      if (p + 1 < end) dw_mac(acc, v[u].y, __ldg(x + c[u].y), bad);
+      if (p >= beg && p < end) acc = __fma_rn(v[u].x, __ldg(x + c[u].x), acc);
+      if (p + 1 < end) acc = __fma_rn(v[u].y, __ldg(x + c[u].y), acc);
     }
     for (int64_t p = a0 + 2 * (lane + (int64_t)L * U); p < end; p += 2 * L) {
       const double2 vv = __ldcs(reinterpret_cast<const double2 *>(val + p));
       const int2 cc = __ldcs(reinterpret_cast<const int2 *>(col + p));
-      dw_mac(acc, vv.x, __ldg(x + cc.x), bad);
-      if (p + 1 < end) dw_mac(acc, vv.y, __ldg(x + cc.y), bad);
+      acc = __fma_rn(vv.x, __ldg(x + cc.x), acc);
+      if (p + 1 < end) acc = __fma_rn(vv.y, __ldg(x + cc.y), acc);
     }
   }
 #pragma unroll
-  for (int off = L / 2; off > 0; off >>= 1) {
-    const dwa::dw o{__shfl_xor_sync(0xffffffffu, acc.h, off), __shfl_xor_sync(0xffffffffu, acc.l, off)};
-    acc = dwa::add(acc, o);
-  }
-  if (__any_sync(0xffffffffu, bad && row < n_rows)) {
-    // rows of this warp with a product outside the pairs' range (OR over the row's L lanes): plain
-    // FP64 sum by one lane, in entry order
-    bool rb = bad;
-#pragma unroll
-    for (int off = L / 2; off > 0; off >>= 1) rb |= __shfl_xor_sync(0xffffffffu, rb, off) != 0;
-    if (row < n_rows && lane == 0 && rb) {
-      double s = 0.0;
-      for (int64_t p = beg; p < end; ++p) s += val[p] * __ldg(x + col[p]);
-      y[row] = s;
-      return;
-    }
-  }
-  if (row < n_rows && lane == 0) y[row] = dwa::to_double(acc);
+  for (int off = L / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (row < n_rows && lane == 0) y[row] = acc;
 }
 
 template <int PHYS>
@@ -543,12 +513,17 @@ void node_neighbours(const mf_mesh *m, const std::vector<uint8_t> &dmask, std::v
 }  // namespace
 
 mf_status spmv(const mf_csr *A, const double *x, double *y, cudaStream_t s, const int *skip) {
-  const int64_t threads = A->n_rows * A->lanes;
   mf_count_launches(1);
-  switch (A->lanes) {  // 2 L U value slots per row: 32 for up to 31 entries, 96 for up to 95
-    case 8: spmv_vec<8, 2><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
-    case 16: spmv_vec<16, 3><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
-    default: spmv_vec<32, 2><<<blocks_for(threads), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip); break;
+  // 2 L U value slots per row: 32 for rows of up to 31 entries, 88 for up to 87, 128 (and the tail
+  // loop) beyond
+  const int64_t maxrow = A->max_row;
+  if (maxrow <= 31) {
+    constexpr int L = kShortRowLanes, U = 32 / (2 * kShortRowLanes);
+    spmv_pairs<L, U><<<blocks_for(A->n_rows * L), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip);
+  } else if (maxrow <= 87) {
+    spmv_pairs<4, 11><<<blocks_for(A->n_rows * 4), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip);
+  } else {
+    spmv_pairs<8, 8><<<blocks_for(A->n_rows * 8), kThreads, 0, s>>>(A->n_rows, A->rowptr, A->col, A->val, x, y, skip);
   }
   MF_CUDA(cudaGetLastError());
   return MF_OK;
@@ -566,6 +541,7 @@ mf_status operator_diagonal(const mf_mesh *m, double *diag, cudaStream_t s) {
 }
 
 extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr **out) {
+  MF_RANGE("mf_assemble_csr");
   mf_clear_error();
   MF_ARG(m && out, "mf_assemble_csr: null argument");
   *out = nullptr;
@@ -594,7 +570,7 @@ extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr 
   A->nnz = nnz;
   int64_t maxrow = 0;
   for (int64_t r = 0; r < n_rows; ++r) maxrow = std::max(maxrow, rowptr[r + 1] - rowptr[r]);
-  A->lanes = maxrow <= 32 ? 8 : maxrow <= 96 ? 16 : 32;
+  A->max_row = maxrow;
   int64_t *d_noff = nullptr;
   int32_t *d_nbr = nullptr;
   auto cleanup = [&]() {
@@ -603,7 +579,7 @@ extern "C" mf_status mf_assemble_csr(const mf_mesh *m, mf_stream stream, mf_csr 
   };
   cudaError_t e = cudaSuccess;
   if ((e = cudaMalloc(&A->rowptr, (n_rows + 1) * sizeof(int64_t))) != cudaSuccess ||
-      (e = cudaMalloc(&A->col, (nnz + 2) * sizeof(int32_t))) != cudaSuccess ||  // + 2: pair loads (spmv_vec)
+      (e = cudaMalloc(&A->col, (nnz + 2) * sizeof(int32_t))) != cudaSuccess ||  // + 2: pair loads (spmv_pairs)
       (e = cudaMalloc(&A->val, (nnz + 2) * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&d_noff, noff.size() * sizeof(int64_t))) != cudaSuccess ||
       (e = cudaMalloc(&d_nbr, std::max<size_t>(nbr.size(), 1) * sizeof(int32_t))) != cudaSuccess) {
@@ -654,6 +630,7 @@ extern "C" mf_status mf_csr_export(const mf_csr *A, int64_t *rowptr, int32_t *co
 }
 
 extern "C" mf_status mf_spmv_csr(const mf_csr *A, const double *x, double *y, mf_stream stream) {
+  MF_RANGE("mf_spmv_csr");
   mf_clear_error();
   MF_ARG(A && x && y, "mf_spmv_csr: null argument");
   const size_t bytes = A->n_rows * sizeof(double);

@@ -8,7 +8,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mf.h"
+
+// NVTX range around a library call: Nsight tools show the C-ABI calls (setup, apply, CSR, CG and its
+// graph blocks, network calls) on the timeline.  Without a tool attached a push or pop is a check of
+// a null function pointer.
+struct MfRange {
+  explicit MfRange(const char *name) { nvtxRangePushA(name); }
+  ~MfRange() { nvtxRangePop(); }
+  MfRange(const MfRange &) = delete;
+  MfRange &operator=(const MfRange &) = delete;
+};
+#define MF_RANGE(name) MfRange mf_range_scope_(name)
 
 // Physics traits: DoFs per node, cell constants per cell, and whether the element arithmetic is the
 // scalar Laplace one (applied to each component for the vector Laplacian of Eq. 5).
@@ -174,7 +187,7 @@ struct mf_csr {
   int64_t *rowptr = nullptr;
   int32_t *col = nullptr;
   double *val = nullptr;
-  int lanes = 8;  // threads per row in the SpMV kernel
+  int64_t max_row = 0;  // longest row (entries): chooses the SpMV kernel shape
 };
 
 // --------------------------------------------------------------------- internal entry points ----
@@ -196,11 +209,17 @@ mf_status tile_apply_dot_fp64(const mf_mesh *m, const double *x, double *y, cuda
                               double *partials, unsigned int *ticket, double *out);
 mf_status tile_apply_dot_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip,
                               double *partials, unsigned int *ticket, double *out);
+// One classic CG iteration's apply with the updates of p (from r and p_{k-1}) and x fused in; y = A p_k
+// and p_k . A p_k in *out (tensor-product meshes with the auto variant, unscaled).
+mf_status tile_apply_cg_fp64(const mf_mesh *m, const double *r, const double *pold, const double *invd, double *pnew,
+                             double *x, double *y, const double *alpha_beta, cudaStream_t s, const int *skip,
+                             double *partials, unsigned int *ticket, double *out);
 mf_status tile_apply_multi_fp64(const mf_mesh *m, int nrhs, const double *x, double *y, cudaStream_t s);
 // general structured kernels (mf_general.cu)
 mf_status gen_setup(mf_mesh *m, cudaStream_t s);
 mf_status pa_setup(mf_mesh *m, cudaStream_t s);
 mf_status q2_pa_setup(mf_mesh *m, cudaStream_t s);  // mf_apply.cu
+size_t q2_pa_bytes(int physics, int64_t n_cells);  // mf_apply.cu: bytes of the Q2 partial assembly
 mf_status gen_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStream_t s, const int *skip);
 mf_status gen_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip);
 // diag(A) of the matrix-free operator (Jacobi), FP64, Dirichlet rows 1.

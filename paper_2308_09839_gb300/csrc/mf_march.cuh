@@ -50,6 +50,30 @@ struct MarchSmem {
   unsigned mag;                                   // largest input magnitude record of the item
 };
 
+// Operands of the CG iteration fused into the apply (classic Hestenes-Stiefel recurrence, FP64
+// vectors, one right-hand side).  The apply of iteration k forms its input
+//   p_k = z_k + beta_{k-1} p_{k-1},   z_k = r_k (or D^-1 r_k with Jacobi),
+// node by node while it stages the node planes (every CTA recomputes its halo nodes), stores p_k
+// and the deferred solution update x_k = x_{k-1} + alpha_{k-1} p_{k-1} for the nodes it owns, and
+// returns A p_k and p_k . A p_k.  p_{k-1} and p_k live in two buffers: neighbouring CTAs still read
+// p_{k-1} at their halo nodes while this one writes p_k.  The FP64 formulas are those of the
+// separate vector kernels (same operations, same rounding), so the iterates are bitwise the same.
+struct CgFuse {
+  const double *r, *pold;  // r_k, p_{k-1}
+  const double *invd;      // 1 / diag(A) (Jacobi) or null
+  double *pnew, *x;        // p_k (written), x (updated in place)
+  const double *ab;        // alpha_{k-1}, beta_{k-1} (device scalars)
+};
+
+// 8-byte asynchronous copy global -> shared (zero-filled when !valid: nothing is read)
+__device__ __forceinline__ void cpa8(void *dst, const void *src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // PHYS = MF_LAPLACE (Eq. 7), MF_VECTOR_LAPLACE (Eq. 5) or MF_ELASTICITY (Eq. 9, Algorithm 1);
 // vectors hold NC values per node (x, y, z components interleaved for the vector operators).
 // One work item (tile column x z-segment `item`, right-hand side `rr`); must be called by all EX*EY
@@ -61,15 +85,33 @@ struct MarchSmem {
 // normalised mesh, and the rescaled pass for inputs outside the double-word range); without SC
 // neither is applied.  Double-word passes record in `mag` the magnitude of the inputs this thread
 // staged (Dirichlet entries excluded).
-template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT, bool SC>
+// CGU (with DOT, FP64 vectors): the CG iteration of CgFuse fused in; x is then p_k's buffer (cg.pnew),
+// the staged values are formed from cg's vectors copied asynchronously into `raw` (two buffers of
+// 3 or 4 arrays of the plane's NP x NC values, then a ring of 4 planes of the owned nodes' p_k in FP64
+// for the write phase), and sab holds alpha_{k-1}, beta_{k-1}.
+template <int PHYS, class N, int EX, int EY, bool COHERENT, bool DOT, bool SC, bool CGU = false>
 __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_t rr,
                                              const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
                                              MarchSmem<phys_ndpn(PHYS), N, EX, EY> &sm, int sc, int so,
-                                             dwa::MagRec &mag) {
+                                             dwa::MagRec &mag, const CgFuse *cg = nullptr, double *raw = nullptr,
+                                             const double *sab = nullptr) {
+  static_assert(!CGU || (DOT && std::is_same<typename N::IO, double>::value), "CG fusion: FP64 vectors with the dot");
+  (void)cg;
+  (void)raw;
+  (void)sab;
   constexpr bool IS_DW = std::is_same<N, tile::NumDW>::value;
+  // Unscaled double-word passes split without split()'s path for magnitudes outside [2^-74, 2^127):
+  // such inputs lie outside the range window, so the magnitude record sends their work item to the
+  // scaled pass, which overwrites everything this pass wrote.
   auto conv_in = [&](typename N::IO v) -> typename N::T {
-    if constexpr (IS_DW && SC) return dwa::split_shift(v, sc);
-    else return N::in(v);
+    if constexpr (IS_DW && SC) {
+      return dwa::split_shift(v, sc);
+    } else if constexpr (IS_DW) {
+      unsigned e;
+      return dwa::split_fast(v, e);
+    } else {
+      return N::in(v);
+    }
   };
   auto conv_out = [&](typename N::T v) -> typename N::IO {
     if constexpr (!SC) return N::out(v);
@@ -130,27 +172,72 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
     const int ix = i0 - 1 + p % PX, iy = j0 - 1 + p / PX;
     nib[l] = (p < NP && ix >= 0 && ix < NXP && iy >= 0 && iy < NYP) ? ix + NXP * iy : -1;
   }
+  // CGU: slots whose node this CTA owns (written once: p_k and x), and the raw array layout
+  unsigned own_slot = 0u;
+  const int na = CGU && cg->invd ? 4 : 3;  // r, p_{k-1}, x [, 1/diag]
+  if constexpr (CGU) {
+#pragma unroll
+    for (int l = 0; l < LOADS; ++l) {
+      const int p = tid + l * NT, px = p % PX, py = p / PX;
+      if (nib[l] >= 0 && px >= 1 && px <= EX - 1 && py >= 1 && py <= EY - 1) own_slot |= 1u << l;
+    }
+  }
+  auto rawp = [&](int k, int a, int idx) -> double * { return raw + ((k & 1) * na + a) * (NP * NC) + idx; };
+  // p_k of the owned nodes by owner thread, planes k mod 4: written at staging, read two steps later in
+  // the write phase; the next write to the same plane slot comes two barriers after that read
+  auto pown = [&](int k, int idx) -> double * { return raw + 2 * na * (NP * NC) + (k & 3) * (NT * NC) + idx; };
   auto fetch = [&](int k) {
 #pragma unroll
     for (int l = 0; l < LOADS; ++l) {
       const bool ok = nib[l] >= 0;
       const int64_t node = nib[l] + (int64_t)k * NPL;
       dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
+      if constexpr (CGU) {
+        const int p = tid + l * NT;
+        const bool ownk = (own_slot >> l & 1u) && k >= k0 && k < k1;
+        if (p < NP)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) xr[l][c] = ok ? ldx(x + (node * g.nrhs + rr) * NC + c) : (IO)0;
+          for (int c = 0; c < NC; ++c) {
+            const int64_t gi = node * NC + c;
+            cpa8(rawp(k, 0, p * NC + c), cg->r + (ok ? gi : 0), ok);
+            cpa8(rawp(k, 1, p * NC + c), cg->pold + (ok ? gi : 0), ok);
+            cpa8(rawp(k, 2, p * NC + c), cg->x + (ownk ? gi : 0), ownk);
+            if (na == 4) cpa8(rawp(k, 3, p * NC + c), cg->invd + (ok ? gi : 0), ok);
+          }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xr[l][c] = ok ? ldx(x + (node * g.nrhs + rr) * NC + c) : (IO)0;
+      }
     }
+    if constexpr (CGU) cpa_commit();
   };
   auto stage = [&](int k) {
     auto *u = sm.up[k & 1];
+    if constexpr (CGU) cpa_wait_all();  // this thread's copies of plane k (issued one step earlier)
 #pragma unroll
     for (int l = 0; l < LOADS; ++l) {
       const int p = tid + l * NT;
       if (p < NP)
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          N::st(u[p * NC + c], dr[l] ? N::zero() : conv_in(xr[l][c]));
+          IO v;
+          if constexpr (CGU) {
+            const int i = p * NC + c;
+            const double rv = *rawp(k, 0, i), po = *rawp(k, 1, i);
+            const double z = na == 4 ? __dmul_rn(rv, *rawp(k, 3, i)) : rv;
+            v = __fma_rn(sab[1], po, z);  // p_k
+            if ((own_slot >> l & 1u) && k >= k0 && k < k1) {
+              const int64_t gi = (nib[l] + (int64_t)k * NPL) * NC + c;
+              cg->pnew[gi] = v;
+              cg->x[gi] = __fma_rn(sab[0], po, *rawp(k, 2, i));
+              *pown(k, ((p % PX) + EX * (p / PX)) * NC + c) = v;  // owner thread (p % PX, p / PX)
+            }
+          } else {
+            v = xr[l][c];
+          }
+          N::st(u[p * NC + c], dr[l] ? N::zero() : conv_in(v));
           if constexpr (IS_DW)
-            if (!dr[l]) mag.add(xr[l][c]);
+            if (!dr[l]) mag.add(v);
         }
     }
   };
@@ -302,7 +389,9 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
         const T tot = N::add(rb[l], N::ld(sm.xrow[ez & 1][l * NT + tid - EX]));
         const int64_t vi = (node * g.nrhs + rr) * NC + l;
         if constexpr (DOT) {
-          const IO xv = ldx(x + vi);
+          IO xv;
+          if constexpr (CGU) xv = *pown(ez, tid * NC + l);  // p_k, staged two steps earlier
+          else xv = ldx(x + vi);
           const IO yv = dir ? xv : conv_out(tot);
           y[vi] = yv;
           dacc += (double)xv * (double)yv;
@@ -357,21 +446,21 @@ __device__ __forceinline__ double march_item(const TileArgs &g, int item, int64_
   return d;
 }
 
-// Stand-alone launches: the unscaled pass only, so that the range check adds no code (and no
-// registers) to them.  A thread whose staged inputs' largest magnitude lies outside [2^kMagLo,
-// 2^kMagHi] sets this launch's bit in the CTA's flag word; march_fixup, launched right after on the
-// same stream, redoes those work items (and, on a normalised mesh, all of them) with the scaled pass.
-template <int PHYS, class N, int EX, int EY, int MINB>
+// Stand-alone launches: one pass per work item, without the range check's second pass, so that the
+// check adds no code (and no registers) to them.  A thread whose staged inputs' largest magnitude lies
+// outside [2^kMagLo, 2^kMagHi] sets this launch's bit in the CTA's flag word; march_fixup, launched
+// right after on the same stream, redoes those work items with the scaled pass.  SCALED: the
+// instantiation for normalised meshes (y scaled by 2^oscale; the host picks it by the mesh).
+template <int PHYS, class N, int EX, int EY, int MINB, bool SCALED = false>
 __global__ void __launch_bounds__(EX *EY, MINB) march_apply(TileArgs g, const typename N::IO *__restrict__ x,
                                                                  typename N::IO *__restrict__ y,
                                                                  const int *__restrict__ skip) {
   __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
   if (skip && *skip) return;
-  if (g.oscale != 0) return;  // normalised mesh: the fix-up kernel computes every item
   dwa::MagRec mag;
   // right-hand side fastest: CTAs that run together read the same x lines ([node][rhs][comp])
-  march_pass<PHYS, N, EX, EY, false, false, false>(g, blockIdx.x / g.nrhs, g.r0 + blockIdx.x % g.nrhs, x, y, sm, 0,
-                                                       0, mag);
+  march_pass<PHYS, N, EX, EY, false, false, SCALED>(g, blockIdx.x / g.nrhs, g.r0 + blockIdx.x % g.nrhs, x, y, sm, 0,
+                                                        SCALED ? g.oscale : 0, mag);
   if constexpr (std::is_same<N, tile::NumDW>::value)
     if (dwa::mag_outside(mag.key)) atomicOr(g.flags + blockIdx.x, g.bit);
 }
@@ -417,20 +506,49 @@ __device__ __forceinline__ void ordered_dot_sum(double d, double *__restrict__ p
 }
 
 // Apply with the dot product x . y fused in (one right-hand side): each CTA stores its part, the
-// last CTA to finish sums the parts in CTA order into *out.  partials: one slot per CTA.
-template <int PHYS, class N, int EX, int EY, int MINB>
+// last CTA to finish sums the parts in CTA order into *out.  partials: one slot per CTA.  SCALED as
+// for march_apply.
+template <int PHYS, class N, int EX, int EY, int MINB, bool SCALED = false>
 __global__ void __launch_bounds__(EX *EY, MINB)
     march_apply_dot(TileArgs g, const typename N::IO *__restrict__ x, typename N::IO *__restrict__ y,
                     const int *__restrict__ skip, double *__restrict__ partials, unsigned int *ticket,
                     double *out) {
   __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
   if (skip && *skip) return;
-  if (g.oscale != 0) return;  // normalised mesh: the fix-up kernel computes every item and the sum
   dwa::MagRec mag;
-  const double d = march_pass<PHYS, N, EX, EY, false, true, false>(g, blockIdx.x, g.r0, x, y, sm, 0, 0, mag);
+  const double d = march_pass<PHYS, N, EX, EY, false, true, SCALED>(g, blockIdx.x, g.r0, x, y, sm, 0,
+                                                                     SCALED ? g.oscale : 0, mag);
   if constexpr (std::is_same<N, tile::NumDW>::value)
     if (dwa::mag_outside(mag.key)) atomicOr(g.flags + blockIdx.x, g.bit);
   ordered_dot_sum<EX * EY>(d, partials, blockIdx.x, gridDim.x, ticket, out, true);
+}
+
+// One CG iteration's apply with the vector updates of CgFuse fused in: stores p_k and x for the owned
+// nodes, y = A p_k, and p_k . A p_k summed in CTA order into *out (as march_apply_dot).  Dynamic shared
+// memory: cg_raw_bytes.  Unscaled meshes only (the caller keeps the separate kernels on a normalised
+// mesh); inputs outside the double-word window flag the CTA for march_fixup, which reads p_k back
+// from cg.pnew.
+template <int PHYS, class N, int EX, int EY, int MINB>
+__global__ void __launch_bounds__(EX *EY, MINB)
+    march_apply_cg(TileArgs g, CgFuse cg, typename N::IO *__restrict__ y, const int *__restrict__ skip,
+                   double *__restrict__ partials, unsigned int *ticket, double *out) {
+  __shared__ MarchSmem<phys_ndpn(PHYS), N, EX, EY> sm;
+  __shared__ double sab[2];
+  extern __shared__ __align__(16) double cg_raw[];
+  if (skip && *skip) return;
+  if (threadIdx.x < 2) sab[threadIdx.x] = cg.ab[threadIdx.x];  // visible after march_pass's first barrier
+  dwa::MagRec mag;
+  const double d = march_pass<PHYS, N, EX, EY, true, true, false, true>(g, blockIdx.x, 0, cg.pnew, y, sm, 0, 0, mag,
+                                                                         &cg, cg_raw, sab);
+  if (dwa::mag_outside(mag.key)) atomicOr(g.flags + blockIdx.x, g.bit);
+  ordered_dot_sum<EX * EY>(d, partials, blockIdx.x, gridDim.x, ticket, out, true);
+}
+
+// Dynamic shared memory of march_apply_cg: two buffers of (3 or 4) arrays of a plane's values, and
+// the ring of 4 planes of owned p_k.
+template <int PHYS, int EX, int EY>
+constexpr size_t cg_raw_bytes(bool jacobi) {
+  return sizeof(double) * (2 * (jacobi ? 4 : 3) * (EX + 1) * (EY + 1) + 4 * EX * EY) * phys_ndpn(PHYS);
 }
 
 // Largest input magnitude record of a work item (the inputs its CTA stages, Dirichlet entries
@@ -466,8 +584,8 @@ __device__ unsigned march_prescan(const TileArgs &g, int item, int64_t rr, const
 
 // Fix-up after march_apply / march_apply_dot (n_cta CTAs, the flags of this launch's bit): every
 // flagged work item whose CTA-wide largest input lies outside the double-word window is computed
-// again with its inputs scaled into [1, 2) and y scaled back; on a normalised mesh every item is
-// computed here, with the mesh's output scaling.  Each flag bit is cleared as it is read.  With DOT
+// again with its inputs scaled into [1, 2) and y scaled back (with the mesh's output scaling on a
+// normalised mesh).  Each flag bit is cleared as it is read.  With DOT
 // the recomputed items' parts are stored and, if any changed, the dot product is summed again in CTA
 // order by the last CTA of this launch.  Persistent: CTAs loop over the items.
 // ctl: two words of the mesh (ctl[0]: some part changed, ctl[1]: ticket of this kernel), zero between
@@ -486,11 +604,11 @@ __global__ void __launch_bounds__(EX *EY) march_fixup(TileArgs g, const typename
   // quick exit: one plain load per thread over this CTA's items (the usual case: nothing flagged)
   bool mine = false;
   for (int c = blockIdx.x + (int)threadIdx.x * (int)gridDim.x; c < n_cta; c += EX * EY * (int)gridDim.x)
-    mine |= g.oscale != 0 || (IS_DW && (__ldcg(g.flags + c) & g.bit) != 0u);
+    mine |= IS_DW && (__ldcg(g.flags + c) & g.bit) != 0u;
   const bool some = __syncthreads_or(mine) != 0;
   for (int c = blockIdx.x; some && c < n_cta; c += gridDim.x) {
     __syncthreads();
-    if (threadIdx.x == 0) todo = g.oscale != 0 ? 1u : (IS_DW ? (atomicAnd(g.flags + c, ~g.bit) & g.bit) : 0u);
+    if (threadIdx.x == 0) todo = IS_DW ? (atomicAnd(g.flags + c, ~g.bit) & g.bit) : 0u;
     __syncthreads();
     if (!todo) continue;
     const int item = DOT ? c : c / g.nrhs;
@@ -501,7 +619,7 @@ __global__ void __launch_bounds__(EX *EY) march_fixup(TileArgs g, const typename
       if (dwa::mag_exponent(march_prescan<PHYS, N, EX, EY>(g, item, rr, x, &mslot), s) &&
           (s < dwa::kMagLo || s > dwa::kMagHi))
         sc = s;
-      else if (g.oscale == 0)
+      else
         continue;  // the first pass was within the window after all
     }
     dwa::MagRec mag;

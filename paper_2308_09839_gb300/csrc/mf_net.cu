@@ -308,6 +308,7 @@ mf_status load_input(mf_net *N, const float *r, const float *logk, cudaStream_t 
 }  // namespace
 
 extern "C" mf_status mf_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t seed, mf_net **out) {
+  MF_RANGE("mf_net_create");
   mf_clear_error();
   MF_ARG(out != nullptr, "mf_net_create: out is NULL");
   *out = nullptr;
@@ -406,6 +407,7 @@ extern "C" mf_status mf_net_set_output_scale(mf_net *N, float scale) {
 }
 
 extern "C" mf_status mf_net_forward(mf_net *N, const float *r, const float *logk, float *out, mf_stream stream) {
+  MF_RANGE("mf_net_forward");
   mf_clear_error();
   MF_ARG(N && r && logk && out, "mf_net_forward: null argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -417,6 +419,7 @@ extern "C" mf_status mf_net_forward(mf_net *N, const float *r, const float *logk
 
 extern "C" mf_status mf_net_gradients(mf_net *N, const float *r, const float *logk, const float *target, float *grads_host,
                                       float *loss_host, mf_stream stream) {
+  MF_RANGE("mf_net_gradients");
   mf_clear_error();
   MF_ARG(N && r && logk && target, "mf_net_gradients: null argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -432,6 +435,7 @@ extern "C" mf_status mf_net_gradients(mf_net *N, const float *r, const float *lo
 
 extern "C" mf_status mf_net_train_step(mf_net *N, const float *r, const float *logk, const float *target, float lr,
                                        float *loss_host, mf_stream stream) {
+  MF_RANGE("mf_net_train_step");
   mf_clear_error();
   MF_ARG(N && r && logk && target && lr > 0, "mf_net_train_step: bad argument");
   cudaStream_t s = (cudaStream_t)stream;

@@ -214,6 +214,34 @@ __global__ void __launch_bounds__(kConvThreads) conv_mma(ConvArgs a) {
   }
 }
 
+// Resident CTAs per SM of a persistent kernel: the occupancy calculator's figure, or the bound from
+// the device's shared-memory, register and thread limits if that is higher (the calculator can
+// assume a smaller shared-memory carveout than the one the kernel requested), capped by the tensor
+// memory: resident CTAs x `cols` columns must fit the 512 columns of an SM.  0 on a CUDA error.
+static int persistent_resident(const void *kern, int threads, int dyn_smem, int cols) {
+  int r = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, threads, dyn_smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaFuncAttributes fa;
+  int dev = 0, smem_sm = 0, resv = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaFuncGetAttributes(&fa, kern) == cudaSuccess &&
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
+    const int per_cta = dyn_smem + (int)fa.sharedSizeBytes + resv;
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;  // allocation unit: 256 per warp
+    const int by_smem = smem_sm / std::max(per_cta, 1);
+    const int by_regs = 65536 / (regs_warp * warps);
+    const int by_warps = 64 / warps;
+    r = std::max(r, std::min(std::min(by_smem, by_regs), std::min(by_warps, 32)));
+  } else {
+    cudaGetLastError();
+  }
+  return std::max(1, std::min(r, 512 / std::max(cols, 1)));
+}
+
 template <int CKP, int CN, int MODE>
 mf_status launch_conv_t(ConvArgs a, cudaStream_t s) {
   constexpr int smem = ConvCfg<CKP, CN>::SMEM;
@@ -370,18 +398,19 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc(TcArgs a, const __grid_con
       if (abort_flag) break;
       if (tid == 0) {
         umma::tc_fence_after_sync();
+        const uint64_t ad0 = umma::sdesc(halo_a, kTcKCS, kTcYS), bd0 = umma::sdesc(w_a, CN * 16, 128);
 #pragma unroll 1
         for (int tl = 0; tl < G; ++tl) {
           const int tap = gi * G + tl, dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
-#pragma unroll 1
+          const uint32_t ta = (uint32_t)(dz * Cfg::ZS + dy * kTcYS + dx * 16), tb = (uint32_t)(tl * Cfg::TAPB);
+#pragma unroll
           for (int zi = 0; zi < TZ; ++zi)
 #pragma unroll
-            for (int ks = 0; ks < KS; ++ks) {
-              const uint32_t aa = halo_a + (uint32_t)((zi + dz) * Cfg::ZS + 2 * ks * kTcKCS + dy * kTcYS + dx * 16);
-              const uint32_t ba = w_a + (uint32_t)(tl * Cfg::TAPB + 2 * ks * CN * 16);
-              umma::mma_bf16(tmem + (uint32_t)(zi * CN), umma::sdesc(aa, kTcKCS, kTcYS), umma::sdesc(ba, CN * 16, 128),
-                             IDESC, (tap > 0 || ks > 0) ? 1u : 0u);
-            }
+            for (int ks = 0; ks < KS; ++ks)
+              umma::mma_bf16(tmem + (uint32_t)(zi * CN),
+                             umma::sdesc_add(ad0, ta + (uint32_t)(zi * Cfg::ZS + 2 * ks * kTcKCS)),
+                             umma::sdesc_add(bd0, tb + (uint32_t)(2 * ks * CN * 16)), IDESC,
+                             (tap > 0 || ks > 0) ? 1u : 0u);
         }
         umma::mma_commit(&mma_bar);
       }
@@ -605,7 +634,7 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
     }
   } else if (warp == 1) {  // --------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t w_a = umma::smem_u32(wsm);
+      const uint64_t bd0 = umma::sdesc(umma::smem_u32(wsm), CN * 16, 128);
       int done = 0;
       for (int i = 0; i < nloc && !*abort_v; ++i) {
         const int s = i % NS, ac = i & 1;
@@ -618,19 +647,21 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
           break;
         }
         umma::tc_fence_after_sync();
-        const uint32_t halo_a = umma::smem_u32(base + s * Cfg::HALO);
-#pragma unroll 1
+        // all 27 x TZ x KS MMAs unrolled: operand descriptors are the item's base descriptors plus
+        // compile-time offsets, so the issuing thread spends about two instructions per MMA
+        const uint64_t ad0 = umma::sdesc(umma::smem_u32(base + s * Cfg::HALO), kTcKCS, kTcYS);
+        const uint32_t d0 = tmem + (uint32_t)(ac * ACC);
+#pragma unroll
         for (int tap = 0; tap < 27; ++tap) {
           const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
 #pragma unroll
           for (int zi = 0; zi < TZ; ++zi)
 #pragma unroll
-            for (int ks = 0; ks < KS; ++ks) {
-              const uint32_t aa = halo_a + (uint32_t)((zi + dz) * Cfg::ZS + 2 * ks * kTcKCS + dy * kTcYS + dx * 16);
-              const uint32_t ba = w_a + (uint32_t)(tap * Cfg::TAPB + 2 * ks * CN * 16);
-              umma::mma_bf16(tmem + (uint32_t)(ac * ACC + zi * CN), umma::sdesc(aa, kTcKCS, kTcYS),
-                             umma::sdesc(ba, CN * 16, 128), IDESC, (tap > 0 || ks > 0) ? 1u : 0u);
-            }
+            for (int ks = 0; ks < KS; ++ks)
+              umma::mma_bf16(d0 + (uint32_t)(zi * CN),
+                             umma::sdesc_add(ad0, (uint32_t)((zi + dz) * Cfg::ZS + 2 * ks * kTcKCS + dy * kTcYS + dx * 16)),
+                             umma::sdesc_add(bd0, (uint32_t)(tap * Cfg::TAPB + 2 * ks * CN * 16)), IDESC,
+                             (tap > 0 || ks > 0) ? 1u : 0u);
         }
         umma::mma_commit(&empty[s]);
         umma::mma_commit(&accf[ac]);
@@ -785,12 +816,9 @@ static bool launch_conv_tcp_t(const ConvArgs &c, cudaStream_t s, mf_status *st) 
       cudaGetLastError();
       return false;
     }
-    int r = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, kTcpThreads, Cfg::SMEM) != cudaSuccess || r < 1) {
-      cudaGetLastError();
-      return false;
-    }
-    resident.store(std::max(1, std::min(r, 512 / Cfg::COLS)));
+    const int r = persistent_resident((const void *)kern, kTcpThreads, Cfg::SMEM, Cfg::COLS);
+    if (r < 1) return false;
+    resident.store(r);
   }
   TcArgs a;
   a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.ck = c.ck; a.cn = c.cn; a.relu = c.relu;
@@ -828,13 +856,9 @@ static bool launch_conv_tc_t(const ConvArgs &c, cudaStream_t s, mf_status *st) {
       cudaGetLastError();
       return false;
     }
-    int r = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, kTcThreads, Cfg::SMEM) != cudaSuccess || r < 1) {
-      cudaGetLastError();
-      return false;
-    }
-    // tensor memory: resident CTAs x columns must fit the 512 columns of an SM
-    resident.store(std::max(1, std::min(r, 512 / Cfg::COLS)));
+    const int r = persistent_resident((const void *)kern, kTcThreads, Cfg::SMEM, Cfg::COLS);
+    if (r < 1) return false;
+    resident.store(r);
   }
   TcArgs a;
   a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.ck = c.ck; a.cn = c.cn; a.relu = c.relu;
@@ -1181,6 +1205,7 @@ __global__ void f32_to_bf16(const float *__restrict__ a, bf16 *__restrict__ b, i
 extern "C" mf_status mf_conv3d_fwd(const void *x, int32_t nx, int32_t ny, int32_t nz, int32_t cin, const void *w,
                                    const float *bias, int32_t cout, const void *skip, int32_t relu, void *y_bf16,
                                    float *y_f32, mf_stream stream) {
+  MF_RANGE("mf_conv3d_fwd");
   mf_clear_error();
   MF_ARG(x && w && (y_bf16 || y_f32) && nx > 0 && ny > 0 && nz > 0, "mf_conv3d_fwd: bad argument");
   ConvArgs a{};
@@ -1218,6 +1243,7 @@ mf_status conv3d_fwd_strided(const void *x, int nx, int ny, int nz, int cin, int
 
 extern "C" mf_status mf_conv3d_dgrad(const void *dy, int32_t nx, int32_t ny, int32_t nz, int32_t cin, const void *w,
                                      int32_t cout, void *dx_bf16, float *dx_f32, mf_stream stream) {
+  MF_RANGE("mf_conv3d_dgrad");
   mf_clear_error();
   MF_ARG(dy && w && (dx_bf16 || dx_f32) && nx > 0 && ny > 0 && nz > 0, "mf_conv3d_dgrad: bad argument");
   ConvArgs a{};
@@ -1264,6 +1290,7 @@ static mf_status launch_wgrad_t(const bf16 *x, const bf16 *dy, int nx, int ny, i
 extern "C" mf_status mf_conv3d_wgrad(const void *x, const void *dy, int32_t nx, int32_t ny, int32_t nz, int32_t cin,
                                      int32_t cout, float *dw, float *db, float *workspace, int64_t ws_bytes,
                                      mf_stream stream) {
+  MF_RANGE("mf_conv3d_wgrad");
   mf_clear_error();
   MF_ARG(x && dy && dw && workspace && cin > 0 && cout > 0 && cin <= 64 && cout <= 64 && nx > 0 && ny > 0 && nz > 0,
          "mf_conv3d_wgrad: bad argument");
@@ -1298,6 +1325,7 @@ static bool vec8(const void *in, const void *out, int c) {
 
 extern "C" mf_status mf_grid_restrict(const void *in, int32_t nfx, int32_t nfy, int32_t nfz, int32_t c, void *out,
                                       float scale, mf_stream stream) {
+  MF_RANGE("mf_grid_restrict");
   mf_clear_error();
   MF_ARG(in && out && nfx % 2 == 1 && nfy % 2 == 1 && nfz % 2 == 1 && c > 0, "mf_grid_restrict: bad argument");
   const int64_t n = (int64_t)((nfx + 1) / 2) * ((nfy + 1) / 2) * ((nfz + 1) / 2) * c;
@@ -1314,6 +1342,7 @@ extern "C" mf_status mf_grid_restrict(const void *in, int32_t nfx, int32_t nfy, 
 
 extern "C" mf_status mf_grid_prolong(const void *in, int32_t ncx, int32_t ncy, int32_t ncz, int32_t c, void *out,
                                      float scale, mf_stream stream) {
+  MF_RANGE("mf_grid_prolong");
   mf_clear_error();
   MF_ARG(in && out && ncx > 0 && ncy > 0 && ncz > 0 && c > 0, "mf_grid_prolong: bad argument");
   const int64_t n = (int64_t)(2 * ncx - 1) * (2 * ncy - 1) * (2 * ncz - 1) * c;

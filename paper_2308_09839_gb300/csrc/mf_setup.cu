@@ -477,13 +477,13 @@ static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cel
       SETUP_CUDA(cudaMemcpyAsync(m->h_cells.data(), cells, npe * n_cells * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       SETUP_CUDA(cudaStreamSynchronize(s));
       SETUP_TRY(colour_elements(m, s));
-      if (npe == 27 && phys_is_laplace(physics)) {
+      if (npe == 27) {
         // the auto variant uses the Q2 partial assembly when it takes at most a quarter of the
         // device's total memory (a function of the mesh and the device model); if the allocation
         // fails all the same, the mesh keeps the reference kernel (flag bit 3 reports it)
         size_t free_b = 0, total_b = 0;
         SETUP_CUDA(cudaMemGetInfo(&free_b, &total_b));
-        if ((double)n_cells * 27 * 6 * sizeof(double) <= 0.25 * (double)total_b) {
+        if ((double)q2_pa_bytes(physics, n_cells) <= 0.25 * (double)total_b) {
           st = q2_pa_setup(m, s);
           if (st != MF_OK && st != MF_ERR_OOM) goto fail;
           st = MF_OK;
@@ -513,12 +513,14 @@ fail:
 extern "C" mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells, const double *coords,
                                    const int32_t *cells, int32_t nx, int32_t ny, int32_t nz, const double *mat,
                                    const uint8_t *dirichlet, mf_stream stream, mf_mesh **out) {
+  MF_RANGE("mf_setup_mesh");
   return setup_mesh(8, physics, n_nodes, n_cells, coords, cells, nx, ny, nz, mat, dirichlet, stream, out);
 }
 
 extern "C" mf_status mf_setup_mesh_elem(int element, int physics, int64_t n_nodes, int64_t n_cells,
                                         const double *coords, const int32_t *cells, const double *mat,
                                         const uint8_t *dirichlet, mf_stream stream, mf_mesh **out) {
+  MF_RANGE("mf_setup_mesh_elem");
   mf_clear_error();
   MF_ARG(element == MF_ELEM_HEX8 || element == MF_ELEM_TET4 || element == MF_ELEM_HEX27,
          "mf_setup_mesh_elem: unknown element %d", element);
@@ -528,6 +530,7 @@ extern "C" mf_status mf_setup_mesh_elem(int element, int physics, int64_t n_node
 }
 
 extern "C" mf_status mf_destroy_mesh(mf_mesh *mesh) {
+  MF_RANGE("mf_destroy_mesh");
   mf_clear_error();
   if (!mesh) return MF_OK;
   MF_CUDA(cudaDeviceSynchronize());
@@ -545,7 +548,8 @@ extern "C" mf_status mf_mesh_query(const mf_mesh *m, int64_t *n_nodes, int64_t *
   if (n_colours) *n_colours = m->n_colours;
   if (flags)
     *flags = (m->structured ? 1 : 0) | (m->all_affine ? 2 : 0) | (m->tp ? 4 : 0) | (m->pa || m->q2pa ? 8 : 0) |
-             (m->npe == 4 ? 16 : 0) | (m->npe == 27 ? 32 : 0) | (m->structured && !m->dw_ok ? 64 : 0);
+             (m->npe == 4 ? 16 : 0) | (m->npe == 27 ? 32 : 0) | (m->structured && !m->dw_ok ? 64 : 0) |
+             (m->dw_ok && m->dw_oscale != 0 ? 128 : 0);
   return MF_OK;
 }
 

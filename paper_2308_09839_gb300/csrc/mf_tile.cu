@@ -88,13 +88,13 @@ mf_status tile_setup(mf_mesh *m, cudaStream_t s) {
   return MF_OK;
 }
 
-// The fix-up kernel of the range check (mf_march.cuh), right after a face-marching launch of n_cta
-// CTAs: double-word launches always (it reads the flags and returns quickly when none is set), FP32
-// launches on normalised meshes only.  Persistent grid.
+// The fix-up kernel of the range check (mf_march.cuh), right after a double-word face-marching
+// launch of n_cta CTAs (it reads the flags and returns quickly when none is set; FP32 launches have no
+// range check).  Persistent grid.
 template <int PHYS, class N, bool DOT>
 static mf_status fixup_launch(const mf_mesh *m, const TileArgs &g, const typename N::IO *x, typename N::IO *y,
                               cudaStream_t s, const int *skip, int n_cta, double *partials, double *out) {
-  if (!std::is_same<N, NumDW>::value && m->dw_oscale == 0) return MF_OK;
+  if (!std::is_same<N, NumDW>::value) return MF_OK;
   using MS = march::MarchShape<PHYS, N>;
   constexpr int NT = MS::EX * MS::EY;
   auto kern = march::march_fixup<PHYS, N, MS::EX, MS::EY, DOT>;
@@ -113,11 +113,12 @@ static mf_status march_launch(const mf_mesh *m, const typename N::IO *x, typenam
                               const int *skip, int nrhs = 1) {
   using MS = march::MarchShape<PHYS, N>;
   constexpr int NT = MS::EX * MS::EY;
-  auto kern = march::march_apply<PHYS, N, MS::EX, MS::EY, MS::MINB>;
+  auto kern0 = march::march_apply<PHYS, N, MS::EX, MS::EY, MS::MINB, false>;
+  auto kern = m->dw_oscale != 0 ? march::march_apply<PHYS, N, MS::EX, MS::EY, MS::MINB, true> : kern0;
   static std::atomic<int> resident{0};  // CTAs per SM: a property of the kernel, same for every caller
   if (resident.load() == 0) {
     int r = 0;
-    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, NT, 0));
+    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern0, NT, 0));
     resident.store(std::max(r, 1));
   }
   TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident.load(), nrhs);
@@ -142,20 +143,34 @@ static mf_status tile_launch(const mf_mesh *m, const typename N::IO *x, typename
   return MF_OK;
 }
 
+// Resident CTAs per SM of the fused-dot apply.  Its work decomposition (z-segments from the wave
+// model) is also that of the fused CG apply, so that both sum p . Ap over the same CTAs in the same
+// order.
+template <int PHYS, class N>
+static mf_status dot_resident(int *out) {
+  using MS = march::MarchShape<PHYS, N>;
+  static std::atomic<int> resident{0};
+  if (resident.load() == 0) {
+    int r = 0;
+    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &r, march::march_apply_dot<PHYS, N, MS::EX, MS::EY, MS::MINB>, MS::EX * MS::EY, 0));
+    resident.store(std::max(r, 1));
+  }
+  *out = resident.load();
+  return MF_OK;
+}
+
 // Apply with x . y fused (CG: p . Ap); partials needs one slot per CTA (tile_dot_slots).
 template <int PHYS, class N>
 static mf_status march_dot_launch(const mf_mesh *m, const typename N::IO *x, typename N::IO *y, cudaStream_t s,
                                   const int *skip, double *partials, unsigned int *ticket, double *out) {
   using MS = march::MarchShape<PHYS, N>;
   constexpr int NT = MS::EX * MS::EY;
-  auto kern = march::march_apply_dot<PHYS, N, MS::EX, MS::EY, MS::MINB>;
-  static std::atomic<int> resident{0};
-  if (resident.load() == 0) {
-    int r = 0;
-    MF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, NT, 0));
-    resident.store(std::max(r, 1));
-  }
-  TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident.load());
+  auto kern = m->dw_oscale != 0 ? march::march_apply_dot<PHYS, N, MS::EX, MS::EY, MS::MINB, true>
+                                 : march::march_apply_dot<PHYS, N, MS::EX, MS::EY, MS::MINB, false>;
+  int resident = 0;
+  MF_TRY((dot_resident<PHYS, N>(&resident)));
+  TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident);
   g.flags = m->tp_flags + 2;
   g.bit = 1u << (m->tp_epoch.fetch_add(1u) & 31u);
   const int n_cta = tile_items(g);
@@ -201,6 +216,48 @@ mf_status tile_apply_dot_fp64(const mf_mesh *m, const double *x, double *y, cuda
 mf_status tile_apply_dot_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip,
                               double *partials, unsigned int *ticket, double *out) {
   return tile_apply_dot<NumF32>(m, x, y, s, skip, partials, ticket, out);
+}
+
+// One classic CG iteration's apply with the p and x updates fused in (march_apply_cg), then the
+// fix-up kernel of the range check on p_k's buffer.
+template <int PHYS>
+static mf_status march_cg_launch(const mf_mesh *m, const march::CgFuse &cg, double *y, cudaStream_t s, const int *skip,
+                                 double *partials, unsigned int *ticket, double *out) {
+  using MS = march::MarchShape<PHYS, NumDW>;
+  constexpr int NT = MS::EX * MS::EY;
+  auto kern = march::march_apply_cg<PHYS, NumDW, MS::EX, MS::EY, MS::MINB>;
+  const size_t dyn = march::cg_raw_bytes<PHYS, MS::EX, MS::EY>(cg.invd != nullptr);
+  static std::atomic<bool> ready{false};
+  if (!ready.load()) {
+    MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)march::cg_raw_bytes<PHYS, MS::EX, MS::EY>(true)));
+    ready.store(true);  // the shared-memory carveout is left to the driver: L1 keeps the rest
+  }
+  int resident = 0;
+  MF_TRY((dot_resident<PHYS, NumDW>(&resident)));
+  TileArgs g = make_tile_args(m, MS::EX, MS::EY, m->tile_seg, resident);
+  g.flags = m->tp_flags + 2;
+  g.bit = 1u << (m->tp_epoch.fetch_add(1u) & 31u);
+  const int n_cta = tile_items(g);
+  mf_count_launches(1);
+  kern<<<n_cta, NT, dyn, s>>>(g, cg, y, skip, partials, ticket, out);
+  MF_CUDA(cudaGetLastError());
+  MF_TRY((fixup_launch<PHYS, NumDW, true>(m, g, cg.pnew, y, s, skip, n_cta, partials, out)));
+  return MF_OK;
+}
+
+mf_status tile_apply_cg_fp64(const mf_mesh *m, const double *r, const double *pold, const double *invd, double *pnew,
+                             double *x, double *y, const double *alpha_beta, cudaStream_t s, const int *skip,
+                             double *partials, unsigned int *ticket, double *out) {
+  if (m->dw_oscale != 0) {
+    mf_set_error("internal: the fused CG apply needs an unscaled mesh");
+    return MF_ERR_UNSUPPORTED;
+  }
+  const march::CgFuse cg{r, pold, invd, pnew, x, alpha_beta};
+  if (m->physics == MF_LAPLACE) return march_cg_launch<MF_LAPLACE>(m, cg, y, s, skip, partials, ticket, out);
+  if (m->physics == MF_VECTOR_LAPLACE)
+    return march_cg_launch<MF_VECTOR_LAPLACE>(m, cg, y, s, skip, partials, ticket, out);
+  return march_cg_launch<MF_ELASTICITY>(m, cg, y, s, skip, partials, ticket, out);
 }
 
 // Multi right-hand-side apply on [node][rhs][comp] vectors: one face-marching launch over all

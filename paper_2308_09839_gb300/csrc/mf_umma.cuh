@@ -93,6 +93,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// The descriptor of the operand `byte_off` bytes further on (a multiple of 16; the start address
+// field holds addr / 16 in 14 bits, and shared-memory addresses stay below 256 KB, so the sum does
+// not carry into the next field).
+__device__ __forceinline__ uint64_t sdesc_add(uint64_t d, uint32_t byte_off) { return d + (byte_off >> 4); }
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);

@@ -26,7 +26,7 @@ PHYSICS = {"laplace": MF_LAPLACE, "elasticity": MF_ELASTICITY, "vector_laplace":
 MF_VARIANT_AUTO, MF_VARIANT_REFERENCE, MF_VARIANT_GENERAL, MF_VARIANT_PARTIAL = 0, 1, 2, 3
 MF_ELEM_HEX8, MF_ELEM_TET4, MF_ELEM_HEX27 = 0, 1, 2
 ELEMENTS = {"hex8": MF_ELEM_HEX8, "tet4": MF_ELEM_TET4, "hex27": MF_ELEM_HEX27}
-MF_CG_CLASSIC, MF_CG_PIPELINED = 0, 1
+MF_CG_CLASSIC, MF_CG_PIPELINED, MF_CG_CLASSIC_SPLIT = 0, 1, 2
 MF_OP_MATFREE, MF_OP_CSR = 0, 1
 MF_PREC_FP64, MF_PREC_MIXED_IR = 0, 1
 MF_PC_NONE, MF_PC_JACOBI, MF_PC_LEARNED = 0, 1, 2
@@ -69,6 +69,9 @@ _SIGS = {
     "mf_solve_opts_default": (None, [C.POINTER(mf_solve_opts)]),
     "mf_cg_solve": (C.c_int, [vp, C.POINTER(mf_solve_opts), vp, vp, C.POINTER(mf_solve_info), vp]),
     "mf_cg_solve_noalloc": (C.c_int, [vp, C.POINTER(mf_solve_opts), vp, vp, C.POINTER(mf_solve_info), vp]),
+    "mf_cg_state_bytes": (C.c_size_t, [vp]),
+    "mf_cg_state_save": (C.c_int, [vp, vp, C.c_size_t, vp]),
+    "mf_cg_resume": (C.c_int, [vp, C.POINTER(mf_solve_opts), vp, C.c_size_t, vp, vp, C.POINTER(mf_solve_info), vp]),
     "mf_batch_create": (C.c_int, [C.POINTER(vp), i32, C.POINTER(mf_solve_opts), C.POINTER(vp)]),
     "mf_batch_solve": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(mf_solve_info), vp]),
     "mf_batch_destroy": (C.c_int, [vp]),
@@ -164,7 +167,7 @@ def mf_mesh_query(h) -> dict:
     return dict(n_nodes=a.value, n_cells=b.value, n_dof=c.value, n_free=d.value, n_colours=e.value,
                 structured=bool(f.value & 1), all_affine=bool(f.value & 2), tensor_product=bool(f.value & 4),
                 partial_assembly=bool(f.value & 8), tetrahedral=bool(f.value & 16), q2=bool(f.value & 32),
-                dw_range_exceeded=bool(f.value & 64), flags=f.value)
+                dw_range_exceeded=bool(f.value & 64), dw_normalised=bool(f.value & 128), flags=f.value)
 
 
 def mf_set_apply_variant(h, variant: int) -> None:
@@ -239,6 +242,26 @@ def mf_cg_solve_noalloc(h, opts: mf_solve_opts, b, x, stream=None, ok=(MF_OK, MF
 
 
 MF_NOALLOC_MAX_DOF = 262144
+
+
+def mf_cg_state_bytes(h) -> int:
+    return int(lib.mf_cg_state_bytes(h))
+
+
+def mf_cg_state_save(h, stream=None) -> bytes:
+    """The checkpoint of the last stopped classic FP64 CG solve on this mesh, as bytes."""
+    n = mf_cg_state_bytes(h)
+    buf = C.create_string_buffer(n)
+    check(lib.mf_cg_state_save(h, buf, n, _stream(stream)), "mf_cg_state_save")
+    return buf.raw
+
+
+def mf_cg_resume(h, opts: mf_solve_opts, state: bytes, b, x, stream=None, ok=(MF_OK, MF_NOT_CONVERGED)) -> mf_solve_info:
+    info = mf_solve_info()
+    buf = C.create_string_buffer(state, len(state))
+    st = lib.mf_cg_resume(h, C.byref(opts), buf, len(state), _ptr(b), _ptr(x), C.byref(info), _stream(stream))
+    check(st, "mf_cg_resume", ok)
+    return info
 
 
 def _ptr_array(ts):
@@ -486,6 +509,18 @@ class Mesh:
         if x is None:
             x = torch.empty_like(b)
         info = mf_cg_solve(self.h, o, b, x, stream, ok=ok)
+        return x, info
+
+    def cg_state(self, stream=None) -> bytes:
+        return mf_cg_state_save(self.h, stream)
+
+    def cg_resume(self, state: bytes, b, x=None, stream=None, ok=(MF_OK, MF_NOT_CONVERGED), **kw):
+        o = mf_solve_opts_default()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        if x is None:
+            x = torch.empty_like(b)
+        info = mf_cg_resume(self.h, o, state, b, x, stream, ok=ok)
         return x, info
 
     def close(self):

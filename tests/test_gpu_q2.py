@@ -44,12 +44,12 @@ MESHES = {
 @pytest.mark.parametrize("name", sorted(MESHES))
 @pytest.mark.parametrize("variant", [mf.MF_VARIANT_AUTO, mf.MF_VARIANT_REFERENCE])
 def test_q2_apply_matches_oracle(name, variant):
-    """AUTO is the sum-factorised partial-assembly kernel on Laplace and vector Laplace meshes and
-    the reference kernel on elasticity meshes."""
+    """AUTO is the sum-factorised partial-assembly kernel (one thread per element for Laplace and
+    vector Laplace, one warp per element for elasticity)."""
     p = MESHES[name]()
     mesh = mf.Mesh.from_problem(p)
     assert mesh.info["q2"] and not mesh.info["structured"]
-    assert mesh.info["partial_assembly"] == (p.physics != "elasticity")
+    assert mesh.info["partial_assembly"]
     mesh.set_variant(variant)
     for seed in (0, 1):
         x = p.x(seed)
@@ -62,10 +62,11 @@ def test_q2_apply_matches_oracle(name, variant):
     assert rel2(y32.double().cpu().numpy(), ref) < 2e-5
 
 
-def test_q2_partial_assembly_larger_mesh():
-    """10 x 9 x 11 curved Q2 Laplace mesh: the sum-factorised kernel against the oracle, and against
-    the reference kernel of the same library."""
-    p = inputs.q2_box("laplace", 10, ny=9, nz=11, jitter=0.1, curve=0.05, seed=90, sigma=1.0)
+@pytest.mark.parametrize("physics", ["laplace", "elasticity"])
+def test_q2_partial_assembly_larger_mesh(physics):
+    """10 x 9 x 11 curved Q2 mesh: the sum-factorised kernel against the oracle, and against the
+    reference kernel of the same library."""
+    p = inputs.q2_box(physics, 10, ny=9, nz=11, jitter=0.1, curve=0.05, seed=90, sigma=1.0)
     mesh = mf.Mesh.from_problem(p)
     x = p.x(3)
     y_pa = mesh.apply(gpu(x))
@@ -151,6 +152,7 @@ def test_q2_setup_checks():
     mesh.set_variant(mf.MF_VARIANT_PARTIAL)  # Laplace: the sum-factorised partial assembly
     pe = inputs.q2_box("elasticity", 1, seed=89)
     me = mf.Mesh.from_problem(pe)
-    assert not me.info["partial_assembly"]
+    assert me.info["partial_assembly"]
+    me.set_variant(mf.MF_VARIANT_PARTIAL)  # elasticity: the warp-per-element partial assembly
     with pytest.raises(mf.MfError):
-        me.set_variant(mf.MF_VARIANT_PARTIAL)
+        me.set_variant(mf.MF_VARIANT_GENERAL)

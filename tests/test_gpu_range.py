@@ -140,6 +140,7 @@ def test_scaled_cell_constants_and_coordinates_match_oracle(name, variant, what,
     """kappa or Young's modulus at 1e+-30, domains of size 1e-20 and 1e15: normalised at setup."""
     p = scaled(MESHES[name][0](), **{what: factor})
     mesh = _mesh(p, variant)
+    assert mesh.info["dw_normalised"] and not mesh.info["dw_range_exceeded"]
     x = p.x(5)
     y = gpu_apply(mesh, x)
     ref = oracle_apply(p, x)
