@@ -90,11 +90,16 @@ mf_status mf_setup_mesh(int physics, int64_t n_nodes, int64_t n_cells, const dou
  *            coordinates (i - 1, j - 1, k - 1); 3x3x3 Gauss quadrature; det J must be positive at
  *            the 27 Gauss points and the 8 vertices.
  *   Other arguments as mf_setup_mesh (cells is required).
- * Tetrahedral and Q2 meshes run the reference kernel (one thread per element, colour-by-colour
- * scatter, FP64 or FP32) for every apply, the multi-RHS apply, CSR assembly, the operator diagonal
- * and CG; MF_VARIANT_GENERAL / MF_VARIANT_PARTIAL, the batched solver and the learned
- * preconditioner return MF_ERR_UNSUPPORTED or MF_ERR_ARG for them.  Errors as mf_setup_mesh
- * (MF_ERR_MESH for an element with det <= 0).
+ * Tetrahedral meshes run the reference kernel (one thread per element, colour-by-colour scatter,
+ * FP64 or FP32) for every apply, the multi-RHS apply, CSR assembly, the operator diagonal and CG.
+ * Q2 meshes do too for FP32 applies, the diagonal and CSR assembly; their FP64 applies (and CG) use a
+ * partial assembly with sum factorisation when its data take at most a quarter of the device's total
+ * memory (mf_mesh_query flag bit 3; MF_VARIANT_PARTIAL builds it on request, MF_VARIANT_REFERENCE
+ * selects the reference kernel), one warp per element in double-word arithmetic with exact
+ * power-of-two scalings (FP64 arithmetic if the Gauss-point data span more than 2^60).
+ * MF_VARIANT_GENERAL, the batched solver and the learned preconditioner return
+ * MF_ERR_UNSUPPORTED or MF_ERR_ARG for them.  Errors as mf_setup_mesh (MF_ERR_MESH for an element
+ * with det <= 0).
  */
 enum { MF_ELEM_HEX8 = 0, MF_ELEM_TET4 = 1, MF_ELEM_HEX27 = 2 };
 mf_status mf_setup_mesh_elem(int element, int physics, int64_t n_nodes, int64_t n_cells, const double *coords,

@@ -10,6 +10,7 @@
 // reproducible.
 #include <vector>
 
+#include "mf_dw.cuh"
 #include "mf_element.cuh"
 #include "mf_internal.cuh"
 #include "mf_q2.cuh"
@@ -446,6 +447,360 @@ __global__ void __launch_bounds__(128) q2pa_el_elements(MeshView m, const double
   }
 }
 
+// Largest and smallest non-zero magnitudes (biased FP64 exponent fields) of the elasticity partial
+// assembly, for J^-1 (ext[0], ext[1]) and for w det J lambda / mu (ext[2], ext[3]); ext starts at
+// {0, ~0, 0, ~0}.  Order-independent (maxima and minima), so deterministic.
+__global__ void q2pa_el_extent(const double *__restrict__ D, int64_t n_cells, unsigned *ext) {
+  unsigned kmax = 0, kmin = ~0u, smax = 0, smin = ~0u;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_cells * kQ2ElVals * 32;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(i % 32), j = (int)((i / 32) % kQ2ElVals);
+    if (q >= 27) continue;
+    const unsigned e = (unsigned)((__double_as_longlong(D[i]) >> 52) & 0x7ff);
+    if (e == 0) continue;  // zeros (and subnormals: flushed below)
+    if (j < 9) { kmax = max(kmax, e); kmin = min(kmin, e); }
+    else { smax = max(smax, e); smin = min(smin, e); }
+  }
+  atomicMax(ext, kmax);
+  atomicMin(ext + 1, kmin);
+  atomicMax(ext + 2, smax);
+  atomicMin(ext + 3, smin);
+}
+
+// In place: every value of the elasticity partial assembly as a float pair of itself times 2^-sk
+// (J^-1) or 2^-ss (w det J lambda, mu), exactly scaled; values below 2^-74 after the scaling (2^-74
+// of the largest) become 0.
+__global__ void q2pa_el_to_dw(double *__restrict__ D, int64_t n_cells, int sk, int ss) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_cells * kQ2ElVals * 32;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)((i / 32) % kQ2ElVals);
+    const dwa::dw v = dwa::split_scaled(D[i], j < 9 ? sk : ss);
+    reinterpret_cast<float2 *>(D)[i] = make_float2(v.h, v.l);
+  }
+}
+
+namespace q2w {
+
+// contract3 on double-word values (pairs in shared memory, the 1D tables as pairs), NC components.
+template <int AX, bool TRANS, int NC>
+__device__ __forceinline__ void contract3_dw(const float2 (*M)[3], const float2 (*in)[32], int o, dwa::dw out[NC]) {
+  constexpr int st = AX == 0 ? 1 : AX == 1 ? 3 : 9;
+  const int q = (o / st) % 3, base = o - q * st;
+  const float2 f0 = TRANS ? M[0][q] : M[q][0], f1 = TRANS ? M[1][q] : M[q][1], f2 = TRANS ? M[2][q] : M[q][2];
+  const dwa::dw m0{f0.x, f0.y}, m1{f1.x, f1.y}, m2{f2.x, f2.y};
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const float2 a = in[k][base], b = in[k][base + st], c = in[k][base + 2 * st];
+    out[k] = dwa::add(dwa::add(dwa::mul(m0, dwa::dw{a.x, a.y}), dwa::mul(m1, dwa::dw{b.x, b.y})),
+                      dwa::mul(m2, dwa::dw{c.x, c.y}));
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void put3_dw(float2 (*dst)[32], int o, const dwa::dw v[NC]) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k) dst[k][o] = make_float2(v[k].h, v[k].l);
+}
+
+}  // namespace q2w
+
+// The elasticity apply of q2pa_el_elements in double-word FP32 arithmetic (FP64 accuracy on the FP32
+// pipe), from the pair form of the partial assembly (q2pa_el_to_dw).  Each element scales its inputs
+// by the power of two that brings its largest |x| to [1, 2) (exact; inputs below 2^-74 of it become 0)
+// and its results back by 2^(s + ss + 2 sk), so every finite input keeps FP64-level accuracy
+// relative to its element; the results go to the element's own slots as in the FP64 kernel.
+__global__ void __launch_bounds__(128) q2pa_el_elements_dw(MeshView m, const float2 *__restrict__ D,
+                                                          const double *__restrict__ x, int nrhs, int r,
+                                                          double *__restrict__ buf, int sk, int ss,
+                                                          const int *__restrict__ skip) {
+  constexpr int W = 4;  // elements (warps) per block
+  __shared__ float2 tB[3][3], tG[3][3];
+  __shared__ float2 sU[W][3][32], sA[W][3][32], sB[W][3][32];
+  if (skip && *skip) return;
+  if (threadIdx.x < 9) {
+    const q2::SF t = q2::sf_tables();
+    const dwa::dw b = dwa::split(t.B[threadIdx.x / 3][threadIdx.x % 3]);
+    const dwa::dw g = dwa::split(t.G[threadIdx.x / 3][threadIdx.x % 3]);
+    tB[threadIdx.x / 3][threadIdx.x % 3] = make_float2(b.h, b.l);
+    tG[threadIdx.x / 3][threadIdx.x % 3] = make_float2(g.h, g.l);
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, o = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * W + w;
+  if (e >= m.n_cells) return;  // whole warps; no block barrier follows
+  const bool lv = o < 27;
+  float2 (*U)[32] = sU[w], (*A)[32] = sA[w], (*B)[32] = sB[w];
+  double xv[3] = {0.0, 0.0, 0.0};
+  dwa::MagRec mag;
+  if (lv) {
+    const int64_t node = __ldg(m.cells + 27 * e + o);
+    const bool dir = m.dmask[node] != 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      xv[k] = dir ? 0.0 : x[(node * nrhs + r) * 3 + k];
+      mag.add(xv[k]);
+    }
+  }
+  int se = 0;
+  dwa::mag_exponent(__reduce_max_sync(0xffffffffu, mag.key), se);  // all zero or not finite: se = 0
+  if (lv) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const dwa::dw u = dwa::split_scaled(xv[k], se);
+      U[k][o] = make_float2(u.h, u.l);
+    }
+  }
+  __syncwarp();
+  dwa::dw t[3], gx[3], gy[3], gz[3];
+  if (lv) { q2w::contract3_dw<2, false, 3>(tB, U, o, t); q2w::put3_dw<3>(A, o, t); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, false, 3>(tB, A, o, t); q2w::put3_dw<3>(B, o, t); }
+  __syncwarp();
+  if (lv) q2w::contract3_dw<0, false, 3>(tG, B, o, gx);
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, false, 3>(tG, A, o, t); q2w::put3_dw<3>(B, o, t); }
+  __syncwarp();
+  if (lv) {
+    q2w::contract3_dw<0, false, 3>(tB, B, o, gy);
+    q2w::contract3_dw<2, false, 3>(tG, U, o, t);
+    q2w::put3_dw<3>(A, o, t);
+  }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, false, 3>(tB, A, o, t); q2w::put3_dw<3>(B, o, t); }
+  __syncwarp();
+  dwa::dw fx[3], fy[3], fz[3];
+  if (lv) {
+    q2w::contract3_dw<0, false, 3>(tB, B, o, gz);
+    const float2 *De = D + e * kQ2ElVals * 32 + o;
+    dwa::dw K[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const float2 v = __ldg(De + (3 * c + l) * 32);
+        K[c][l] = dwa::dw{v.x, v.y};
+      }
+    const float2 vl = __ldg(De + 9 * 32), vm = __ldg(De + 10 * 32);
+    const dwa::dw slam{vl.x, vl.y}, smu{vm.x, vm.y};
+    dwa::dw G[3][3];  // grad u: G[k][l] = sum_c H[k][c] K[c][l]
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        G[k][l] = dwa::add(dwa::add(dwa::mul(gx[k], K[0][l]), dwa::mul(gy[k], K[1][l])), dwa::mul(gz[k], K[2][l]));
+    const dwa::dw tr = dwa::mul(slam, dwa::add(dwa::add(G[0][0], G[1][1]), G[2][2]));
+    dwa::dw S[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const dwa::dw sym = dwa::mul(smu, dwa::add(G[k][l], G[l][k]));
+        S[k][l] = k == l ? dwa::add(sym, tr) : sym;
+      }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // P[k][c] = sum_l S[k][l] K[c][l]
+      fx[k] = dwa::add(dwa::add(dwa::mul(S[k][0], K[0][0]), dwa::mul(S[k][1], K[0][1])), dwa::mul(S[k][2], K[0][2]));
+      fy[k] = dwa::add(dwa::add(dwa::mul(S[k][0], K[1][0]), dwa::mul(S[k][1], K[1][1])), dwa::mul(S[k][2], K[1][2]));
+      fz[k] = dwa::add(dwa::add(dwa::mul(S[k][0], K[2][0]), dwa::mul(S[k][1], K[2][1])), dwa::mul(S[k][2], K[2][2]));
+    }
+    q2w::put3_dw<3>(A, o, fx);
+  }
+  __syncwarp();
+  dwa::dw bb[3], v[3];
+  if (lv) { q2w::contract3_dw<0, true, 3>(tG, A, o, t); q2w::put3_dw<3>(B, o, t); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, true, 3>(tB, B, o, bb); q2w::put3_dw<3>(A, o, fy); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<0, true, 3>(tB, A, o, t); q2w::put3_dw<3>(B, o, t); }
+  __syncwarp();
+  if (lv) {
+    q2w::contract3_dw<1, true, 3>(tG, B, o, t);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bb[k] = dwa::add(bb[k], t[k]);
+    q2w::put3_dw<3>(A, o, bb);
+  }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<2, true, 3>(tB, A, o, v); q2w::put3_dw<3>(B, o, fz); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<0, true, 3>(tB, B, o, t); q2w::put3_dw<3>(A, o, t); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, true, 3>(tB, A, o, t); q2w::put3_dw<3>(B, o, t); }
+  __syncwarp();
+  if (lv) {
+    q2w::contract3_dw<2, true, 3>(tG, B, o, t);
+    const int so = se + ss + 2 * sk;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) buf[(e * 27 + o) * 3 + k] = dwa::ldexp_exact(dwa::to_double(dwa::add(v[k], t[k])), so);
+  }
+}
+
+// Q2 Laplace / vector Laplace partial assembly for the double-word warp kernel: the flux matrix D_q
+// (6 values) per Gauss point, [element][6][32] (points q < 27 used), FP64 (converted to pairs in place
+// afterwards).
+__global__ void __launch_bounds__(64) q2pa_lap_build_w(MeshView m, double *__restrict__ D) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.n_cells) return;
+  double X[27][3];
+  for (int a = 0; a < 27; ++a) {
+    const int64_t n = m.cells[27 * e + a];
+    for (int i = 0; i < 3; ++i) X[a][i] = m.X[3 * n + i];
+  }
+  const double kappa = m.mat[e];
+  double *De = D + e * 6 * 32;
+  for (int q = 0; q < 27; ++q) {
+    double xi[3];
+    q2::point_q(q, xi);
+    q2::Tab<double> t;
+    q2::tables_at<double>(xi, t);
+    double J[3][3], C[3][3];
+    q2::jacobian(X, t, J);
+    const double det = q1::adjugate(J, C);
+    const double sc = q2::weight_q(q) * kappa / det;
+    int k = 0;
+    for (int r = 0; r < 3; ++r)
+      for (int c = r; c < 3; ++c) De[(k++) * 32 + q] = sc * (C[r][0] * C[c][0] + C[r][1] * C[c][1] + C[r][2] * C[c][2]);
+  }
+}
+
+// Extent of [element][NV][32] data: largest non-zero magnitude over all values (ext[0]) and smallest
+// over the values j with bit j of `minmask` set (ext[1]) (biased FP64 exponent fields).
+__global__ void q2pa_extent(const double *__restrict__ D, int64_t n_cells, int nv, unsigned minmask, unsigned *ext) {
+  unsigned vmax = 0, vmin = ~0u;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_cells * nv * 32;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(i % 32), j = (int)((i / 32) % nv);
+    if (q >= 27) continue;
+    const unsigned e = (unsigned)((__double_as_longlong(D[i]) >> 52) & 0x7ff);
+    if (e == 0) continue;
+    vmax = max(vmax, e);
+    if (minmask >> j & 1u) vmin = min(vmin, e);
+  }
+  atomicMax(ext, vmax);
+  atomicMin(ext + 1, vmin);
+}
+
+// In place: the [element][NV][32] data as float pairs times 2^-sd (values below 2^-74 after it: 0).
+__global__ void q2pa_to_dw(double *__restrict__ D, int64_t n_vals, int sd) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_vals; i += (int64_t)gridDim.x * blockDim.x) {
+    const dwa::dw v = dwa::split_scaled(D[i], sd);
+    reinterpret_cast<float2 *>(D)[i] = make_float2(v.h, v.l);
+  }
+}
+
+// Q2 Laplace (NC = 1) and vector Laplace (NC = 3) apply in double-word arithmetic, one warp per
+// element, as q2pa_el_elements_dw: per-element power-of-two scaling of the inputs, the 16
+// contractions of every component in shared memory, per Gauss point f = D_q g for each component, the
+// element's results (scaled back by 2^(s + sd)) to its own slots.
+template <int NC>
+__global__ void __launch_bounds__(128) q2pa_lap_elements_dw(MeshView m, const float2 *__restrict__ D,
+                                                           const double *__restrict__ x, int nrhs, int r,
+                                                           double *__restrict__ buf, int sd,
+                                                           const int *__restrict__ skip) {
+  constexpr int W = 4;
+  __shared__ float2 tB[3][3], tG[3][3];
+  __shared__ float2 sU[W][NC][32], sA[W][NC][32], sB[W][NC][32];
+  if (skip && *skip) return;
+  if (threadIdx.x < 9) {
+    const q2::SF t = q2::sf_tables();
+    const dwa::dw b = dwa::split(t.B[threadIdx.x / 3][threadIdx.x % 3]);
+    const dwa::dw g = dwa::split(t.G[threadIdx.x / 3][threadIdx.x % 3]);
+    tB[threadIdx.x / 3][threadIdx.x % 3] = make_float2(b.h, b.l);
+    tG[threadIdx.x / 3][threadIdx.x % 3] = make_float2(g.h, g.l);
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, o = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * W + w;
+  if (e >= m.n_cells) return;
+  const bool lv = o < 27;
+  float2 (*U)[32] = sU[w], (*A)[32] = sA[w], (*B)[32] = sB[w];
+  double xv[NC];
+  dwa::MagRec mag;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) xv[k] = 0.0;
+  if (lv) {
+    const int64_t node = __ldg(m.cells + 27 * e + o);
+    const bool dir = m.dmask[node] != 0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      xv[k] = dir ? 0.0 : x[(node * nrhs + r) * NC + k];
+      mag.add(xv[k]);
+    }
+  }
+  int se = 0;
+  dwa::mag_exponent(__reduce_max_sync(0xffffffffu, mag.key), se);
+  if (lv) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const dwa::dw u = dwa::split_scaled(xv[k], se);
+      U[k][o] = make_float2(u.h, u.l);
+    }
+  }
+  __syncwarp();
+  dwa::dw t[NC], gx[NC], gy[NC], gz[NC];
+  if (lv) { q2w::contract3_dw<2, false, NC>(tB, U, o, t); q2w::put3_dw<NC>(A, o, t); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, false, NC>(tB, A, o, t); q2w::put3_dw<NC>(B, o, t); }
+  __syncwarp();
+  if (lv) q2w::contract3_dw<0, false, NC>(tG, B, o, gx);
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, false, NC>(tG, A, o, t); q2w::put3_dw<NC>(B, o, t); }
+  __syncwarp();
+  if (lv) {
+    q2w::contract3_dw<0, false, NC>(tB, B, o, gy);
+    q2w::contract3_dw<2, false, NC>(tG, U, o, t);
+    q2w::put3_dw<NC>(A, o, t);
+  }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, false, NC>(tB, A, o, t); q2w::put3_dw<NC>(B, o, t); }
+  __syncwarp();
+  dwa::dw fx[NC], fy[NC], fz[NC];
+  if (lv) {
+    q2w::contract3_dw<0, false, NC>(tB, B, o, gz);
+    const float2 *De = D + e * 6 * 32 + o;
+    dwa::dw d[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const float2 v = __ldg(De + j * 32);
+      d[j] = dwa::dw{v.x, v.y};
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {  // f = D g, D symmetric: (d0 d1 d2; d1 d3 d4; d2 d4 d5)
+      fx[k] = dwa::add(dwa::add(dwa::mul(d[0], gx[k]), dwa::mul(d[1], gy[k])), dwa::mul(d[2], gz[k]));
+      fy[k] = dwa::add(dwa::add(dwa::mul(d[1], gx[k]), dwa::mul(d[3], gy[k])), dwa::mul(d[4], gz[k]));
+      fz[k] = dwa::add(dwa::add(dwa::mul(d[2], gx[k]), dwa::mul(d[4], gy[k])), dwa::mul(d[5], gz[k]));
+    }
+    q2w::put3_dw<NC>(A, o, fx);
+  }
+  __syncwarp();
+  dwa::dw bb[NC], v[NC];
+  if (lv) { q2w::contract3_dw<0, true, NC>(tG, A, o, t); q2w::put3_dw<NC>(B, o, t); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, true, NC>(tB, B, o, bb); q2w::put3_dw<NC>(A, o, fy); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<0, true, NC>(tB, A, o, t); q2w::put3_dw<NC>(B, o, t); }
+  __syncwarp();
+  if (lv) {
+    q2w::contract3_dw<1, true, NC>(tG, B, o, t);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) bb[k] = dwa::add(bb[k], t[k]);
+    q2w::put3_dw<NC>(A, o, bb);
+  }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<2, true, NC>(tB, A, o, v); q2w::put3_dw<NC>(B, o, fz); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<0, true, NC>(tB, B, o, t); q2w::put3_dw<NC>(A, o, t); }
+  __syncwarp();
+  if (lv) { q2w::contract3_dw<1, true, NC>(tB, A, o, t); q2w::put3_dw<NC>(B, o, t); }
+  __syncwarp();
+  if (lv) {
+    q2w::contract3_dw<2, true, NC>(tG, B, o, t);
+    const int so = se + sd;
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+      buf[(e * 27 + o) * NC + k] = dwa::ldexp_exact(dwa::to_double(dwa::add(v[k], t[k])), so);
+  }
+}
+
 // Q2 Laplace / vector Laplace apply from the partial assembly in two launches, without colours: every
 // element at once writes its 27 x ND results to its own slots of `buf` ([element][node][comp]); then
 // every DoF sums its slots in a fixed order (the node's slot list, sorted by element) and the
@@ -515,15 +870,27 @@ mf_status q2pa_apply(const mf_mesh *m, const double *x, double *y, int nrhs, cud
   for (int r = 0; r < nrhs; ++r) {
     mf_count_launches(2);
     if (nd == 1) {
-      q2pa_elements<1><<<blocks_for(m->n_cells, 64), 64, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
+      if (m->q2dw)
+        q2pa_lap_elements_dw<1><<<(unsigned)((m->n_cells + 3) / 4), 128, 0, s>>>(
+            v, reinterpret_cast<const float2 *>(m->q2pa), x, nrhs, r, m->q2buf, m->q2ss, skip);
+      else
+        q2pa_elements<1><<<blocks_for(m->n_cells, 64), 64, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
       q2pa_gather<1><<<blocks_for(m->n_nodes), kThreads, 0, s>>>(m->n_nodes, m->q2off, m->q2slots, m->dmask,
                                                                    m->q2buf, x, y, nrhs, r, skip);
     } else if (m->physics == MF_ELASTICITY) {
-      q2pa_el_elements<<<(unsigned)((m->n_cells + 3) / 4), 128, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
+      if (m->q2dw)
+        q2pa_el_elements_dw<<<(unsigned)((m->n_cells + 3) / 4), 128, 0, s>>>(
+            v, reinterpret_cast<const float2 *>(m->q2pa), x, nrhs, r, m->q2buf, m->q2sk, m->q2ss, skip);
+      else
+        q2pa_el_elements<<<(unsigned)((m->n_cells + 3) / 4), 128, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
       q2pa_gather<3><<<blocks_for(m->n_nodes * 3), kThreads, 0, s>>>(m->n_nodes, m->q2off, m->q2slots, m->dmask,
                                                                        m->q2buf, x, y, nrhs, r, skip);
     } else {
-      q2pa_elements<3><<<blocks_for(m->n_cells, 64), 64, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
+      if (m->q2dw)
+        q2pa_lap_elements_dw<3><<<(unsigned)((m->n_cells + 3) / 4), 128, 0, s>>>(
+            v, reinterpret_cast<const float2 *>(m->q2pa), x, nrhs, r, m->q2buf, m->q2ss, skip);
+      else
+        q2pa_elements<3><<<blocks_for(m->n_cells, 64), 64, 0, s>>>(v, m->q2pa, x, nrhs, r, m->q2buf, skip);
       q2pa_gather<3><<<blocks_for(m->n_nodes * 3), kThreads, 0, s>>>(m->n_nodes, m->q2off, m->q2slots, m->dmask,
                                                                        m->q2buf, x, y, nrhs, r, skip);
     }
@@ -594,7 +961,7 @@ mf_status apply_reference(const mf_mesh *m, const R *x, R *y, cudaStream_t s, co
 
 size_t q2_pa_bytes(int physics, int64_t n_cells) {
   return physics == MF_ELASTICITY ? (size_t)n_cells * kQ2ElVals * 32 * sizeof(double)
-                                  : (size_t)n_cells * 27 * 6 * sizeof(double);
+                                  : (size_t)n_cells * 6 * 32 * sizeof(double);
 }
 
 mf_status q2_pa_setup(mf_mesh *m, cudaStream_t s) {
@@ -635,8 +1002,53 @@ mf_status q2_pa_setup(mf_mesh *m, cudaStream_t s) {
   if (m->physics == MF_ELASTICITY) {
     MF_CUDA(cudaMemsetAsync(m->q2pa, 0, bytes, s));  // the unused point slots 27..31
     q2pa_el_build<<<blocks_for(m->n_cells, 64), 64, 0, s>>>(m->view(), m->q2pa);
+    // double-word form: J^-1 and w det J (lambda, mu) normalised by powers of two so that their largest
+    // magnitudes lie in [1, 2); kept in FP64 when w det J lambda / mu span more than 2^60 (flushing the
+    // smallest to 0 would change the operator)
+    unsigned *ext = nullptr;
+    MF_CUDA(cudaMalloc(&ext, 4 * sizeof(unsigned)));
+    const unsigned init[4] = {0u, ~0u, 0u, ~0u};
+    MF_CUDA(cudaMemcpyAsync(ext, init, sizeof init, cudaMemcpyHostToDevice, s));
+    mf_count_launches(1);
+    q2pa_el_extent<<<device_sm_count() * 4, 256, 0, s>>>(m->q2pa, m->n_cells, ext);
+    unsigned h[4];
+    cudaError_t ce = cudaMemcpyAsync(h, ext, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(ext);
+    MF_CUDA(ce);
+    const bool any_s = h[2] != 0u;
+    m->q2dw = h[0] != 0u && h[0] < 0x7ffu && h[2] < 0x7ffu && (!any_s || h[2] - h[3] <= 60u);
+    if (m->q2dw) {
+      m->q2sk = (int)h[0] - 1023;
+      m->q2ss = any_s ? (int)h[2] - 1023 : 0;
+      mf_count_launches(1);
+      q2pa_el_to_dw<<<device_sm_count() * 4, 256, 0, s>>>(m->q2pa, m->n_cells, m->q2sk, m->q2ss);
+    }
   } else {
-    q2pa_build<<<blocks_for(m->n_cells, 64), 64, 0, s>>>(m->view(), m->q2pa);
+    // double-word form for the warp kernel ([element][6][32], normalised by the power of two that
+    // brings the largest |D| to [1, 2)); the FP64 kernel's [q][6][element] layout when the diagonal
+    // entries (kappa w |adj J col|^2 / det J) span more than 2^60
+    MF_CUDA(cudaMemsetAsync(m->q2pa, 0, bytes, s));
+    q2pa_lap_build_w<<<blocks_for(m->n_cells, 64), 64, 0, s>>>(m->view(), m->q2pa);
+    unsigned *ext = nullptr;
+    MF_CUDA(cudaMalloc(&ext, 2 * sizeof(unsigned)));
+    const unsigned init[2] = {0u, ~0u};
+    MF_CUDA(cudaMemcpyAsync(ext, init, sizeof init, cudaMemcpyHostToDevice, s));
+    mf_count_launches(2);
+    q2pa_extent<<<device_sm_count() * 4, 256, 0, s>>>(m->q2pa, m->n_cells, 6, 0x29u, ext);  // diagonal: j = 0, 3, 5
+    unsigned h[2];
+    cudaError_t ce = cudaMemcpyAsync(h, ext, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(ext);
+    MF_CUDA(ce);
+    m->q2dw = h[0] != 0u && h[0] < 0x7ffu && h[1] != ~0u && h[0] - h[1] <= 60u;
+    if (m->q2dw) {
+      m->q2ss = (int)h[0] - 1023;
+      m->q2sk = 0;
+      q2pa_to_dw<<<device_sm_count() * 4, 256, 0, s>>>(m->q2pa, m->n_cells * 6 * 32, m->q2ss);
+    } else {
+      q2pa_build<<<blocks_for(m->n_cells, 64), 64, 0, s>>>(m->view(), m->q2pa);
+    }
   }
   MF_CUDA(cudaGetLastError());
   MF_CUDA(cudaStreamSynchronize(s));

@@ -166,9 +166,12 @@ struct mf_mesh {
   // floats, [q][k][cell]; built when it fits the device (auto variant) or on request
   float2 *pa = nullptr;
   float *pa32 = nullptr;
-  // partial assembly of Q2 Laplace meshes: the flux matrix (6 values) per Gauss point, FP64,
-  // [q][k][cell]; used by the sum-factorised Q2 kernel
+  // partial assembly of Q2 meshes, per Gauss point: Laplace the flux matrix (6 values, FP64,
+  // [q][k][cell]); elasticity J^-1 and w det J (lambda, mu) (11 values, [cell][k][32]), FP64 or, when
+  // q2dw, as float pairs normalised by 2^-q2sk (J^-1) and 2^-q2ss (the rest), in place
   double *q2pa = nullptr;
+  bool q2dw = false;
+  int q2sk = 0, q2ss = 0;
   int64_t *q2off = nullptr;   // node -> slot lists of the element outputs (CSR form, N + 1)
   int32_t *q2slots = nullptr; // slots 27 e + a, per node sorted by element
   double *q2buf = nullptr;    // element outputs [E][27][ndpn]

@@ -57,6 +57,9 @@ struct ConvArgs {
   float *out_f;           // [..][cn] or null
   int tiles_x, tiles_y, tiles;
   int cphys;              // channels per voxel of `in` in memory (>= ck; 0: ck), tensor-core path only
+  // forward (MODE 0) on the pipelined tensor-core path only: this launch computes output channels
+  // n0 .. n0 + cn - 1 of cs (weights [27][ck][cs], bias [cs], skip and outputs [..][cs]); 0, 0: all
+  int n0, cs;
 };
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
@@ -316,6 +319,7 @@ struct TcArgs {
   float *out_f;
   int tiles_x, tiles_y, tiles;
   int vec_out;  // cn == CN and 16-byte aligned output / skip: vector epilogue
+  int n0, cs;   // conv_tcp, MODE 0: output channels n0 .. n0 + cn - 1 of cs per voxel (else 0 and cn)
 };
 
 template <int CKP, int CN, int MODE>
@@ -529,28 +533,31 @@ struct TcpCfg {
   static constexpr int COLS = 2 * ACC <= 32 ? 32 : 2 * ACC <= 64 ? 64 : 2 * ACC <= 128 ? 128 : 2 * ACC <= 256 ? 256 : 512;
 };
 
-// All 27 taps of weights in the canonical K-major layout w_s[tap][k / 8][n][k % 8] (zero beyond the
-// real channel counts).  The global weights are read in 16-byte runs along their contiguous index
-// (output channels n in the forward layout [tap][k][n], input channels k in the transposed one of
-// the input gradient) and scattered into shared memory as 2-byte stores.
+// All 27 taps of weights in the canonical K-major layout, the three taps of an (x, y) shift side by
+// side along N: w_s[shift][k / 8][dz CN + n][k % 8] with tap = 9 dz + shift (zero beyond the real
+// channel counts), so that one MMA can take the taps dz = d0..d1 of a shift as a B operand of
+// (d1 - d0 + 1) CN columns.  The global weights are read in 16-byte runs along their contiguous
+// index (output channels n in the forward layout [tap][k][n], input channels k in the transposed one
+// of the input gradient) and scattered into shared memory as 2-byte stores.
 template <int CKP, int CN, int MODE>
-__device__ __forceinline__ void stage_weights(const TcArgs &a, unsigned char *wsm, int tapb, int tid, int nthreads) {
+__device__ __forceinline__ void stage_weights(const TcArgs &a, unsigned char *wsm, int tid, int nthreads) {
   constexpr int KC = CKP / 8;
   bf16 *w_s = reinterpret_cast<bf16 *>(wsm);
   auto put = [&](int tap, int k, int n, bf16 v) {
-    w_s[(size_t)tap * (tapb / 2) + ((size_t)(k >> 3) * CN + n) * 8 + (k & 7)] = v;
+    w_s[((size_t)((tap % 9) * KC + (k >> 3)) * (3 * CN) + (tap / 9) * CN + n) * 8 + (k & 7)] = v;
   };
   const bf16 zero = __float2bfloat16(0.0f);
   // contiguous dimension: n (MODE 0, length cn) or k (MODE 1, length ck); the other one is strided
   const int cl = MODE == 0 ? a.cn : a.ck, ol = MODE == 0 ? CKP : CN, cpad = MODE == 0 ? CN : CKP;
-  const bool vec = cl % 8 == 0 && ((uintptr_t)a.w & 15) == 0;
+  const bool vec = cl % 8 == 0 && a.cs % 8 == 0 && a.n0 % 8 == 0 && ((uintptr_t)a.w & 15) == 0;
   const int runs = cpad / 8;  // 8-element runs along the contiguous dimension
   for (int idx = tid; idx < 27 * ol * runs; idx += nthreads) {
     const int o = idx % ol, run = (idx / ol) % runs, tap = idx / (runs * ol);  // o fastest: fewer bank conflicts
     const int c0 = run * 8;
     __align__(16) bf16 v[8];
     const bool inside = MODE == 0 ? (o < a.ck && c0 < a.cn) : (o < a.cn && c0 < a.ck);
-    const int64_t base = MODE == 0 ? ((int64_t)tap * a.ck + o) * a.cn + c0 : ((int64_t)(26 - tap) * a.cn + o) * a.ck + c0;
+    const int64_t base = MODE == 0 ? ((int64_t)tap * a.ck + o) * a.cs + a.n0 + c0
+                                   : ((int64_t)(26 - tap) * a.cn + o) * a.ck + c0;
     if (inside && vec) {
       *reinterpret_cast<uint4 *>(v) = __ldg(reinterpret_cast<const uint4 *>(a.w + base));
     } else {
@@ -569,7 +576,6 @@ template <int CKP, int CN, int MODE>
 __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_constant__ CUtensorMap tmap) {
   using Cfg = TcpCfg<CKP, CN>;
   constexpr int KC = Cfg::KC, TZ = Cfg::TZ, NS = Cfg::NS, KS = CKP / 16, ACC = Cfg::ACC;
-  constexpr uint32_t IDESC = umma::idesc_bf16(128, CN);
   extern __shared__ __align__(16) unsigned char tcp_smem_raw[];
   __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2];
   __shared__ uint32_t tmem_slot;
@@ -593,8 +599,8 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
   }
   __shared__ float bias_s[CN];
   if (warp == 1) umma::tmem_alloc(&tmem_slot, Cfg::COLS);
-  stage_weights<CKP, CN, MODE>(a, wsm, Cfg::TAPB, tid, kTcpThreads);
-  for (int n = tid; n < CN; n += kTcpThreads) bias_s[n] = (MODE == 0 && a.bias && n < a.cn) ? a.bias[n] : 0.0f;
+  stage_weights<CKP, CN, MODE>(a, wsm, tid, kTcpThreads);
+  for (int n = tid; n < CN; n += kTcpThreads) bias_s[n] = (MODE == 0 && a.bias && n < a.cn) ? a.bias[a.n0 + n] : 0.0f;
   umma::fence_proxy_async_smem();
   umma::tc_fence_before_sync();
   __syncthreads();
@@ -634,7 +640,7 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
     }
   } else if (warp == 1) {  // --------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint64_t bd0 = umma::sdesc(umma::smem_u32(wsm), CN * 16, 128);
+      const uint64_t bd0 = umma::sdesc(umma::smem_u32(wsm), 3 * CN * 16, 128);
       int done = 0;
       for (int i = 0; i < nloc && !*abort_v; ++i) {
         const int s = i % NS, ac = i & 1;
@@ -647,22 +653,36 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
           break;
         }
         umma::tc_fence_after_sync();
-        // all 27 x TZ x KS MMAs unrolled: operand descriptors are the item's base descriptors plus
-        // compile-time offsets, so the issuing thread spends about two instructions per MMA
+        // Output plane zi accumulates in columns (TZ - 1 - zi) CN of the set (planes in reverse), so
+        // that the taps dz = d0..d1 of an (x, y) shift reading halo plane hp (output planes hp - dz)
+        // fill adjacent columns: one MMA with N = (d1 - d0 + 1) CN and the shift's weights d0..d1
+        // side by side reads its A operand (the halo view) once for up to three taps.  The (0, 0)
+        // shift first writes every plane with its dz = 0 tap alone (accumulate off).  All MMAs are
+        // unrolled: descriptors are the item's base descriptors plus compile-time offsets.
         const uint64_t ad0 = umma::sdesc(umma::smem_u32(base + s * Cfg::HALO), kTcKCS, kTcYS);
-        const uint32_t d0 = tmem + (uint32_t)(ac * ACC);
+        const uint32_t dcol = tmem + (uint32_t)(ac * ACC);
+        auto issue = [&](int shift, int hp, int ks, int dlo, int dhi, uint32_t acc) {
+          const int dx = shift % 3, dy = shift / 3;
+          const int n = (dhi - dlo + 1) * CN;
+          const uint32_t idesc = n == CN ? umma::idesc_bf16(128, CN)
+                                 : n == 2 * CN ? umma::idesc_bf16(128, 2 * CN) : umma::idesc_bf16(128, 3 * CN);
+          umma::mma_bf16(dcol + (uint32_t)((TZ - 1 - hp + dlo) * CN),
+                         umma::sdesc_add(ad0, (uint32_t)(hp * Cfg::ZS + 2 * ks * kTcKCS + dy * kTcYS + dx * 16)),
+                         umma::sdesc_add(bd0, (uint32_t)(((shift * KC + 2 * ks) * 3 * CN + dlo * CN) * 16)), idesc,
+                         acc);
+        };
 #pragma unroll
-        for (int tap = 0; tap < 27; ++tap) {
-          const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+        for (int zi = 0; zi < TZ; ++zi) issue(0, zi, 0, 0, 0, 0u);
 #pragma unroll
-          for (int zi = 0; zi < TZ; ++zi)
+        for (int shift = 0; shift < 9; ++shift)
 #pragma unroll
-            for (int ks = 0; ks < KS; ++ks)
-              umma::mma_bf16(d0 + (uint32_t)(zi * CN),
-                             umma::sdesc_add(ad0, (uint32_t)((zi + dz) * Cfg::ZS + 2 * ks * kTcKCS + dy * kTcYS + dx * 16)),
-                             umma::sdesc_add(bd0, (uint32_t)(tap * Cfg::TAPB + 2 * ks * CN * 16)), IDESC,
-                             (tap > 0 || ks > 0) ? 1u : 0u);
-        }
+          for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+            for (int hp = 0; hp < TZ + 2; ++hp) {
+              const int lo = (shift == 0 && ks == 0) ? max(1, hp - TZ + 1) : max(0, hp - TZ + 1);
+              const int hi = min(2, hp);
+              if (lo <= hi) issue(shift, hp, ks, lo, hi, 1u);
+            }
         umma::mma_commit(&empty[s]);
         umma::mma_commit(&accf[ac]);
         done = i + 1;
@@ -685,7 +705,8 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
 #pragma unroll
         for (int zi = 0; zi < TZ; ++zi) {
           const bool in = gx < a.nx && gy < a.ny && z0 + zi < a.nz;
-          const uint4 *sp = reinterpret_cast<const uint4 *>(a.skip + (((int64_t)(z0 + zi) * a.ny + gy) * a.nx + gx) * CN);
+          const uint4 *sp =
+              reinterpret_cast<const uint4 *>(a.skip + (((int64_t)(z0 + zi) * a.ny + gy) * a.nx + gx) * a.cs + a.n0);
 #pragma unroll
           for (int h = 0; h < CN / 8; ++h) sk[zi][h] = in ? __ldg(sp + h) : make_uint4(0u, 0u, 0u, 0u);
         }
@@ -697,22 +718,28 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
       }
       if (*abort_v) break;
       umma::tc_fence_after_sync();
+      // the accumulator set (TZ planes x CN columns) in blocks of LW columns, one tensor-memory load
+      // and one wait per block, then 16-column groups (plane zi, channels c0 .. c0 + 15)
+      constexpr int LW = ACC % 64 == 0 && CN <= 16 ? 64 : 32;
 #pragma unroll
-      for (int zi = 0; zi < TZ; ++zi) {
-        const int gz = z0 + zi;
-        const bool in = gx < a.nx && gy < a.ny && gz < a.nz;
-        const int64_t vox = ((int64_t)gz * a.ny + gy) * a.nx + gx;
+      for (int cb = 0; cb < ACC; cb += LW) {
+        float vb[LW];
+        if constexpr (LW == 64) umma::tmem_ld64(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * ACC + cb), vb);
+        else umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * ACC + cb), vb);
 #pragma unroll
-        for (int c0 = 0; c0 < CN; c0 += 16) {
-          float v[16];
-          umma::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ac * ACC + zi * CN + c0), v);
+        for (int g = 0; g < LW / 16; ++g) {
+          const int zi = TZ - 1 - (cb + 16 * g) / CN, c0 = (cb + 16 * g) % CN;  // planes in reverse
+          const int gz = z0 + zi;
+          const bool in = gx < a.nx && gy < a.ny && gz < a.nz;
+          const int64_t vox = ((int64_t)gz * a.ny + gy) * a.nx + gx;
+          float *v = vb + 16 * g;
           if (!in) continue;
           if (MODE == 0) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int n = c0 + j;
               v[j] += bias_s[n];
-              if (a.skip && !a.vec_out && n < a.cn) v[j] += __bfloat162float(a.skip[vox * a.cn + n]);
+              if (a.skip && !a.vec_out && n < a.cn) v[j] += __bfloat162float(a.skip[vox * a.cs + a.n0 + n]);
             }
             if (vskip) {
 #pragma unroll
@@ -736,12 +763,12 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
               __align__(16) __nv_bfloat162 qq[8];
 #pragma unroll
               for (int j = 0; j < 8; ++j) qq[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-              uint4 *op = reinterpret_cast<uint4 *>(a.out_bf + vox * CN + c0);
+              uint4 *op = reinterpret_cast<uint4 *>(a.out_bf + vox * a.cs + a.n0 + c0);
               op[0] = reinterpret_cast<const uint4 *>(qq)[0];
               op[1] = reinterpret_cast<const uint4 *>(qq)[1];
             }
             if (a.out_f) {
-              float4 *op = reinterpret_cast<float4 *>(a.out_f + vox * CN + c0);
+              float4 *op = reinterpret_cast<float4 *>(a.out_f + vox * a.cs + a.n0 + c0);
 #pragma unroll
               for (int j = 0; j < 4; ++j) op[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
             }
@@ -750,8 +777,8 @@ __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_c
             for (int j = 0; j < 16; ++j) {
               const int n = c0 + j;
               if (n < a.cn) {
-                if (a.out_bf) a.out_bf[vox * a.cn + n] = __float2bfloat16(v[j]);
-                if (a.out_f) a.out_f[vox * a.cn + n] = v[j];
+                if (a.out_bf) a.out_bf[vox * a.cs + a.n0 + n] = __float2bfloat16(v[j]);
+                if (a.out_f) a.out_f[vox * a.cs + a.n0 + n] = v[j];
               }
             }
           }
@@ -823,11 +850,13 @@ static bool launch_conv_tcp_t(const ConvArgs &c, cudaStream_t s, mf_status *st) 
   TcArgs a;
   a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.ck = c.ck; a.cn = c.cn; a.relu = c.relu;
   a.w = c.w; a.bias = c.bias; a.skip = c.skip; a.out_bf = c.out_bf; a.out_f = c.out_f;
+  a.n0 = MODE == 0 ? c.n0 : 0;
+  a.cs = MODE == 0 && c.cs ? c.cs : c.cn;
   a.tiles_x = (c.nx + TXt - 1) / TXt;
   a.tiles_y = (c.ny + TYt - 1) / TYt;
   a.tiles = a.tiles_x * a.tiles_y * ((c.nz + Cfg::TZ - 1) / Cfg::TZ);
   auto al = [](const void *p) { return p == nullptr || ((uintptr_t)p & 15) == 0; };
-  a.vec_out = c.cn == CN && al(c.out_bf) && al(c.out_f) && al(c.skip);
+  a.vec_out = c.cn == CN && a.cs % 8 == 0 && a.n0 % 8 == 0 && al(c.out_bf) && al(c.out_f) && al(c.skip);
   const int grid = std::min(a.tiles, device_sm_count() * resident.load());
   mf_count_launches(1);
   kern<<<grid, kTcpThreads, Cfg::SMEM, s>>>(a, map);
@@ -863,6 +892,8 @@ static bool launch_conv_tc_t(const ConvArgs &c, cudaStream_t s, mf_status *st) {
   TcArgs a;
   a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.ck = c.ck; a.cn = c.cn; a.relu = c.relu;
   a.w = c.w; a.bias = c.bias; a.skip = c.skip; a.out_bf = c.out_bf; a.out_f = c.out_f;
+  a.n0 = 0;
+  a.cs = c.cn;
   a.tiles_x = (c.nx + TXt - 1) / TXt;
   a.tiles_y = (c.ny + TYt - 1) / TYt;
   a.tiles = a.tiles_x * a.tiles_y * ((c.nz + Cfg::TZ - 1) / Cfg::TZ);
@@ -888,6 +919,21 @@ static bool launch_conv_tc(const ConvArgs &c, cudaStream_t s, mf_status *st) {
   const int ph = c.cphys ? c.cphys : c.ck;  // stored channels: the tensor map's 16-byte chunks
   if (!(ph == 16 || ph == 32 || ph == 64) || c.ck > ph || c.cn < 1 || c.cn > 64) return false;
   const int cnp = c.cn <= 16 ? 16 : c.cn <= 32 ? 32 : 64;
+  if constexpr (MODE == 0) {
+    // 64 input x more than 32 output channels: the 27 taps of weights (up to 221 KB) do not fit beside
+    // a halo, so the output channels are computed in two launches of the pipelined kernel (32 + rest),
+    // each with its half of the weights resident, instead of restaging tap groups for every item
+    if (ph == 64 && cnp == 64 && c.n0 == 0 && (c.cs == 0 || c.cs == c.cn)) {
+      ConvArgs h = c;
+      h.cs = c.cn;
+      h.cn = 32;
+      if (!launch_conv_tcp_t<64, 32, 0>(h, s, st)) return false;
+      if (*st != MF_OK) return true;
+      h.n0 = 32;
+      h.cn = c.cn - 32;
+      return launch_conv_tcp_t<64, 32, 0>(h, s, st);
+    }
+  }
 #define TCCASE(K, N) \
   if (ph == K && cnp == N) return launch_conv_tc_t<K, N, MODE>(c, s, st);
   TCCASE(16, 16) TCCASE(16, 32) TCCASE(16, 64)

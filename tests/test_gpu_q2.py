@@ -121,7 +121,12 @@ def test_q2_csr_and_diagonal(physics):
 
 @pytest.mark.parametrize("physics", ["laplace", "elasticity"])
 def test_q2_cg_and_jacobi_match_oracle(physics):
+    """Iteration counts within 5 % of the oracle's: the operators are the double-word partial-assembly
+    kernels, and under double-word-sized rounding of its operator the oracle's own CG moves by more than
+    1 % (Laplace) and 3 % (elasticity) on these problems (test_q2_cg_counts_drift_under_double_word_
+    rounding in the oracle pins)."""
     p = inputs.q2_box(physics, 3, ny=2, nz=3, jitter=0.1, seed=88)
+    frac = 0.05
     A = fem.assemble_csr(p.physics, p.coords, p.cells, p.mat, p.dirichlet, p.n_nodes)
     b = p.b()
     _, it_o, _ = solvers.cg(lambda v: A @ v, b, rtol=1e-8)
@@ -131,11 +136,11 @@ def test_q2_cg_and_jacobi_match_oracle(physics):
     x, info = mesh.cg(gpu(b))
     torch.cuda.synchronize()
     assert info.status == mf.MF_OK
-    assert abs(info.iters - it_o) <= max(2, math.ceil(0.01 * it_o)), (info.iters, it_o)
+    assert abs(info.iters - it_o) <= max(2, math.ceil(frac * it_o)), (info.iters, it_o)
     assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.05e-8 * np.linalg.norm(b)
     _, ij = mesh.cg(gpu(b), precond=mf.MF_PC_JACOBI)
     assert ij.status == mf.MF_OK
-    assert abs(ij.iters - it_j) <= max(2, math.ceil(0.01 * it_j)), (ij.iters, it_j)
+    assert abs(ij.iters - it_j) <= max(2, math.ceil(frac * it_j)), (ij.iters, it_j)
 
 
 def test_q2_setup_checks():
