@@ -410,6 +410,13 @@ mf_status mf_set_tile_segment(mf_mesh *mesh, int32_t seg);
  *                       float[mf_net_num_params], may be NULL).
  *   mf_net_get_params / mf_net_set_params   flat FP32 parameters (host arrays), for checkpoints and
  *                       for moving weights between networks of different grid sizes.
+ *   mf_net_state_bytes / mf_net_state_save / mf_net_state_load   the whole training state in one
+ *                       caller-owned host buffer: parameters, Adam's moments and step count, the
+ *                       gradient-norm history of the clip, the output scale.  Training continued
+ *                       after a load takes the same steps, bitwise, as training that was never
+ *                       interrupted (the kernels are deterministic).  Save and load synchronise the
+ *                       device; load returns MF_ERR_ARG for a buffer that is no state, is truncated or
+ *                       holds another parameter count.
  * Low-level kernels, exposed for parity tests (BF16 tensors as uint16 bit patterns, channels-last
  * [z][y][x][C]; weights [27][Cin][Cout] with tap t = dx + 3 dy + 9 dz for offsets (d - 1)):
  *   mf_conv3d_fwd   y = relu?(conv(x, w) + bias + skip); C in [1, 64].
@@ -423,6 +430,9 @@ mf_status mf_net_destroy(mf_net *net);
 int64_t mf_net_num_params(const mf_net *net);
 mf_status mf_net_get_params(const mf_net *net, float *host);
 mf_status mf_net_set_params(mf_net *net, const float *host);
+int64_t mf_net_state_bytes(const mf_net *net);
+mf_status mf_net_state_save(const mf_net *net, void *host, int64_t bytes);
+mf_status mf_net_state_load(mf_net *net, const void *host, int64_t bytes);
 mf_status mf_net_set_output_scale(mf_net *net, float scale);
 mf_status mf_net_forward(mf_net *net, const float *r, const float *logk, float *out, mf_stream stream);
 mf_status mf_net_train_step(mf_net *net, const float *r, const float *logk, const float *target, float lr,
@@ -462,6 +472,16 @@ mf_status mf_training_pair(mf_mesh *mesh, const double *b, const double *xs, con
 /* Message describing the last failure in the calling thread ("" if none).  Valid until the next
  * failing call in the same thread. */
 const char *mf_last_error(void);
+
+/* Index checks of the bounds-checked build (no counterpart in the paper: a debugging aid).  A
+ * library built with -DMF_DEBUG_BOUNDS (`python -m paper_2308_09839_gb300.build --debug`, which
+ * writes libmf_debug.so) checks the node, cell and column indices its kernels compute before they
+ * use them; a failed check sets a bit (1 node index, 2 cell index, 4 CSR column index) in a device
+ * status word and the access is redirected to index 0, so the kernel finishes in bounds.  This call
+ * synchronises the device, returns the bits set since the last call in *bits (and clears them) and
+ * *enabled = 1.  In a release build it touches no device: *bits = 0, *enabled = 0.  enabled may be
+ * NULL.  Errors: MF_ERR_ARG (bits NULL), MF_ERR_CUDA. */
+mf_status mf_debug_status(uint32_t *bits, int32_t *enabled);
 
 /* Number of CUDA kernels this library has launched in the process so far (kernels replayed by a
  * CUDA graph count once per replay).  Host call, thread-safe; for accounting in benchmarks. */

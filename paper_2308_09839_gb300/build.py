@@ -2,7 +2,9 @@
 
 Every translation unit is compiled in parallel, then linked with the static CUDA runtime.  The
 result is written next to this file; build products go to ``_build/`` under the repository root.
-Usage: ``python -m paper_2308_09839_gb300.build [--verbose-ptxas]``.
+``--debug`` builds the bounds-checked library ``libmf_debug.so`` instead (``-DMF_DEBUG_BOUNDS``:
+index checks that record failures in a status word read by ``mf_debug_status``; objects in
+``_build_debug/``).  Usage: ``python -m paper_2308_09839_gb300.build [--verbose-ptxas] [--debug]``.
 """
 from __future__ import annotations
 
@@ -32,9 +34,12 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src: str, ptxas_verbose: bool) -> tuple[str, str]:
-    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+DEBUG_LIB = os.path.join(PKG, "libmf_debug.so")
+
+
+def _compile(src: str, ptxas_verbose: bool, debug: bool = False) -> tuple[str, str]:
+    obj = os.path.join(BUILD + ("_debug" if debug else ""), os.path.basename(src).replace(".cu", ".o"))
+    cmd = [nvcc(), *ARCH, *FLAGS, *(["-DMF_DEBUG_BOUNDS"] if debug else []), "-c", src, "-o", obj]
     if ptxas_verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -43,25 +48,25 @@ def _compile(src: str, ptxas_verbose: bool) -> tuple[str, str]:
     return obj, r.stderr
 
 
-def build(ptxas_verbose: bool = False, quiet: bool = True) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(ptxas_verbose: bool = False, quiet: bool = True, debug: bool = False) -> str:
+    out = DEBUG_LIB if debug else LIB
+    os.makedirs(BUILD + ("_debug" if debug else ""), exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        results = list(ex.map(lambda s: _compile(s, ptxas_verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, ptxas_verbose, debug), srcs))
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = out + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
     if not quiet or ptxas_verbose:
         for _, err in results:
             if err.strip():
                 print(err, file=sys.stderr)
-    return LIB
+    return out
 
 
 if __name__ == "__main__":
-    build(ptxas_verbose="--verbose-ptxas" in sys.argv, quiet=False)
-    print(LIB)
+    print(build(ptxas_verbose="--verbose-ptxas" in sys.argv, quiet=False, debug="--debug" in sys.argv))

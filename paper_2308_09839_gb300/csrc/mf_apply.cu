@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(128) apply_ref_colour(MeshView m, const R *__r
                                                         const int *__restrict__ skip) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count || (skip && *skip)) return;
-  const int64_t e = celems ? (int64_t)celems[t] : parity_element(t, colour, m.nx, m.ny, m.nz);
+  const int64_t e = mf_dbg_index(celems ? (int64_t)celems[t] : parity_element(t, colour, m.nx, m.ny, m.nz), m.n_cells,
+                                 MF_DBG_CELL);
   int64_t nodes[8];
   element_nodes(m, e, nodes);
   const R *Xc = coords_of<R>(m);
@@ -80,7 +81,8 @@ __global__ void __launch_bounds__(128) apply_multi_colour(MeshView m, const doub
                                                           const int32_t *__restrict__ celems) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
-  const int64_t e = celems ? (int64_t)celems[t] : parity_element(t, colour, m.nx, m.ny, m.nz);
+  const int64_t e = mf_dbg_index(celems ? (int64_t)celems[t] : parity_element(t, colour, m.nx, m.ny, m.nz), m.n_cells,
+                                 MF_DBG_CELL);
   int64_t nodes[8];
   element_nodes(m, e, nodes);
   double X[8][3];
@@ -184,9 +186,11 @@ __global__ void __launch_bounds__(128) tet_apply_colour(MeshView m, const R *__r
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count || (skip && *skip)) return;
   constexpr int ND = phys_ndpn(PHYS);
-  const int64_t e = celems[t];
+  const int64_t e = mf_dbg_index((int64_t)celems[t], m.n_cells, MF_DBG_CELL);
   int64_t nodes[4];
   p1::nodes_of(m.cells, e, nodes);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) nodes[a] = mf_dbg_index(nodes[a], m.n_nodes, MF_DBG_NODE);
   const R *Xc = coords_of<R>(m);
   const R *mat = mat_of<R>(m);
   R X[4][3], n[4][3];
@@ -235,14 +239,14 @@ __global__ void __launch_bounds__(64) q2_apply_colour(MeshView m, const R *__res
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count || (skip && *skip)) return;
   constexpr int ND = phys_ndpn(PHYS);
-  const int64_t e = celems[t];
+  const int64_t e = mf_dbg_index((int64_t)celems[t], m.n_cells, MF_DBG_CELL);
   const R *Xc = coords_of<R>(m);
   const R *mat = mat_of<R>(m);
   int64_t nodes[27];
   R X[27][3];
   bool dir[27];
   for (int a = 0; a < 27; ++a) {
-    nodes[a] = m.cells[27 * e + a];
+    nodes[a] = cell_node(m, 27, e, a);
     for (int i = 0; i < 3; ++i) X[a][i] = Xc[3 * nodes[a] + i];
     dir[a] = m.dmask[nodes[a]] != 0;
   }
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(64) q2pa_build(MeshView m, double *__restrict_
   const int64_t E = m.n_cells;
   double X[27][3];
   for (int a = 0; a < 27; ++a) {
-    const int64_t n = m.cells[27 * e + a];
+    const int64_t n = cell_node(m, 27, e, a);
     for (int i = 0; i < 3; ++i) X[a][i] = m.X[3 * n + i];
   }
   const double kappa = m.mat[e];
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(64) q2pa_el_build(MeshView m, double *__restri
   if (e >= m.n_cells) return;
   double X[27][3];
   for (int a = 0; a < 27; ++a) {
-    const int64_t n = m.cells[27 * e + a];
+    const int64_t n = cell_node(m, 27, e, a);
     for (int i = 0; i < 3; ++i) X[a][i] = m.X[3 * n + i];
   }
   const double lam = m.mat[2 * e], mu = m.mat[2 * e + 1];
@@ -365,7 +369,7 @@ __global__ void __launch_bounds__(128) q2pa_el_elements(MeshView m, const double
   const bool lv = o < 27;
   double (*U)[32] = sU[w], (*A)[32] = sA[w], (*B)[32] = sB[w];
   if (lv) {
-    const int64_t node = __ldg(m.cells + 27 * e + o);
+    const int64_t node = cell_node(m, 27, e, o);
     const bool dir = m.dmask[node] != 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) U[k][o] = dir ? 0.0 : x[(node * nrhs + r) * 3 + k];
@@ -533,7 +537,7 @@ __global__ void __launch_bounds__(128) q2pa_el_elements_dw(MeshView m, const flo
   double xv[3] = {0.0, 0.0, 0.0};
   dwa::MagRec mag;
   if (lv) {
-    const int64_t node = __ldg(m.cells + 27 * e + o);
+    const int64_t node = cell_node(m, 27, e, o);
     const bool dir = m.dmask[node] != 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -642,7 +646,7 @@ __global__ void __launch_bounds__(64) q2pa_lap_build_w(MeshView m, double *__res
   if (e >= m.n_cells) return;
   double X[27][3];
   for (int a = 0; a < 27; ++a) {
-    const int64_t n = m.cells[27 * e + a];
+    const int64_t n = cell_node(m, 27, e, a);
     for (int i = 0; i < 3; ++i) X[a][i] = m.X[3 * n + i];
   }
   const double kappa = m.mat[e];
@@ -718,7 +722,7 @@ __global__ void __launch_bounds__(128) q2pa_lap_elements_dw(MeshView m, const fl
 #pragma unroll
   for (int k = 0; k < NC; ++k) xv[k] = 0.0;
   if (lv) {
-    const int64_t node = __ldg(m.cells + 27 * e + o);
+    const int64_t node = cell_node(m, 27, e, o);
     const bool dir = m.dmask[node] != 0;
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
@@ -817,7 +821,7 @@ __global__ void __launch_bounds__(64) q2pa_elements(MeshView m, const double *__
   bool dir[27];
 #pragma unroll
   for (int a = 0; a < 27; ++a) {
-    nodes[a] = __ldg(m.cells + 27 * e + a);
+    nodes[a] = cell_node(m, 27, e, a);
     dir[a] = m.dmask[nodes[a]] != 0;
   }
   for (int k = 0; k < ND; ++k) {
@@ -1138,3 +1142,5 @@ extern "C" mf_status mf_apply_multi(const mf_mesh *m, int32_t nrhs, const double
   MF_TRY(check_apply_args(m, X, Y, m ? m->n_dof * nrhs * sizeof(double) : 0));
   return apply_multi_fp64(m, nrhs, X, Y, (cudaStream_t)stream);
 }
+
+MF_DBG_TU(apply)

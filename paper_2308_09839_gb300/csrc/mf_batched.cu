@@ -480,3 +480,5 @@ extern "C" mf_status mf_cg_solve_batched(mf_mesh *const *meshes, int32_t n, cons
   mf_batch_destroy(B);
   return st;
 }
+
+MF_DBG_TU(batched)

@@ -1466,3 +1466,5 @@ extern "C" mf_status mf_operator_diagonal(const mf_mesh *m, double *diag, mf_str
   MF_ARG(m && diag, "mf_operator_diagonal: null argument");
   return operator_diagonal(m, diag, (cudaStream_t)stream);
 }
+
+MF_DBG_TU(cg)

@@ -394,14 +394,14 @@ __global__ void __launch_bounds__(256) spmv_pairs(int64_t n_rows, const int64_t 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t p = a0 + 2 * (lane + (int64_t)L * u);
-      if (p >= beg && p < end) acc = __fma_rn(v[u].x, __ldg(x + c[u].x), acc);
-      if (p + 1 < end) acc = __fma_rn(v[u].y, __ldg(x + c[u].y), acc);
+      if (p >= beg && p < end) acc = __fma_rn(v[u].x, __ldg(x + mf_dbg_index(c[u].x, (int)n_rows, MF_DBG_COLUMN)), acc);
+      if (p + 1 < end) acc = __fma_rn(v[u].y, __ldg(x + mf_dbg_index(c[u].y, (int)n_rows, MF_DBG_COLUMN)), acc);
     }
     for (int64_t p = a0 + 2 * (lane + (int64_t)L * U); p < end; p += 2 * L) {
       const double2 vv = __ldcs(reinterpret_cast<const double2 *>(val + p));
       const int2 cc = __ldcs(reinterpret_cast<const int2 *>(col + p));
-      acc = __fma_rn(vv.x, __ldg(x + cc.x), acc);
-      if (p + 1 < end) acc = __fma_rn(vv.y, __ldg(x + cc.y), acc);
+      acc = __fma_rn(vv.x, __ldg(x + mf_dbg_index(cc.x, (int)n_rows, MF_DBG_COLUMN)), acc);
+      if (p + 1 < end) acc = __fma_rn(vv.y, __ldg(x + mf_dbg_index(cc.y, (int)n_rows, MF_DBG_COLUMN)), acc);
     }
   }
 #pragma unroll
@@ -648,3 +648,5 @@ extern "C" mf_status mf_destroy_csr(mf_csr *A) {
   delete A;
   return MF_OK;
 }
+
+MF_DBG_TU(csr)

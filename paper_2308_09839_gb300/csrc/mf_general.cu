@@ -462,7 +462,8 @@ __device__ __forceinline__ void gen_pass(const GenArgs &g, const typename N::IO 
       const int p = tid + l * NT;
       const int ix = i0 - 1 + p % PX, iy = j0 - 1 + p / PX;
       const bool ok = p < NP && ix >= 0 && ix < NXP && iy >= 0 && iy < NYP;
-      const int64_t node = ix + (int64_t)NXP * (iy + (int64_t)NYP * k);
+      const int64_t node =
+          ok ? mf_dbg_index(ix + (int64_t)NXP * (iy + (int64_t)NYP * k), (int64_t)NXP * NYP * (g.nz + 1), MF_DBG_NODE) : 0;
       dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
 #pragma unroll
       for (int c = 0; c < ND; ++c) xr[l][c] = ok ? __ldg(x + node * ND + c) : (IO)0;
@@ -496,7 +497,8 @@ __device__ __forceinline__ void gen_pass(const GenArgs &g, const typename N::IO 
       const int idx = t / ND, c = t % ND;
       const int lx = idx % TX, ly = idx / TX;
       if (lx < ownx && ly < owny) {
-        const int64_t node = (i0 + lx) + (int64_t)NXP * ((j0 + ly) + (int64_t)NYP * k);
+        const int64_t node = mf_dbg_index((i0 + lx) + (int64_t)NXP * ((j0 + ly) + (int64_t)NYP * k),
+                                          (int64_t)NXP * NYP * (g.nz + 1), MF_DBG_NODE);
         y[node * ND + c] = __ldg(g.dmask + node) ? x[node * ND + c] : conv_out(N::ld(a[t]));
       }
       N::st(a[t], N::zero());
@@ -798,3 +800,5 @@ mf_status gen_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStrea
 mf_status gen_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip) {
   return gen_dispatch<NumF32>(m, x, y, s, skip);
 }
+
+MF_DBG_TU(general)

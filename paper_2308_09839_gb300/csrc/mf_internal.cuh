@@ -61,6 +61,51 @@ void mf_clear_error();
 void mf_count_launches(int64_t n);
 int64_t mf_launches_now();
 
+// ------------------------------------------------------------------- bounds-checked builds ----
+// Built with -DMF_DEBUG_BOUNDS (`python -m paper_2308_09839_gb300.build --debug` makes libmf_debug.so)
+// the index checks of the kernels are compiled in: mf_dbg_index(i, n, bit) returns i when
+// 0 <= i < n and otherwise sets `bit` in this translation unit's status word and returns 0, an index
+// inside every buffer it is used on, so the kernel finishes without touching memory outside its
+// buffers (its results are then meaningless and the status says so).  mf_debug_status gathers and
+// clears the words of all translation units.  Release builds compile the checks to nothing.
+enum : unsigned { MF_DBG_NODE = 1u, MF_DBG_CELL = 2u, MF_DBG_COLUMN = 4u };
+#ifdef MF_DEBUG_BOUNDS
+static __device__ unsigned mf_dbg_word;
+template <typename I>
+__device__ __forceinline__ I mf_dbg_index(I i, I n, unsigned bit) {
+  if (i >= 0 && i < n) return i;
+  atomicOr(&mf_dbg_word, bit);
+  return (I)0;
+}
+#define MF_DBG_TU(name)                                                   \
+  unsigned mf_dbg_take_##name() {                                         \
+    unsigned h = 0u;                                                      \
+    const unsigned z = 0u;                                                \
+    if (cudaMemcpyFromSymbol(&h, mf_dbg_word, sizeof h) != cudaSuccess) h = ~0u; \
+    cudaMemcpyToSymbol(mf_dbg_word, &z, sizeof z);                        \
+    return h;                                                             \
+  }
+#else
+template <typename I>
+__device__ __forceinline__ I mf_dbg_index(I i, I, unsigned) {
+  return i;
+}
+#define MF_DBG_TU(name) \
+  unsigned mf_dbg_take_##name() { return 0u; }
+#endif
+// pointer p into the buffer [base, base + n), checked like mf_dbg_index (release builds: p itself)
+#ifdef MF_DEBUG_BOUNDS
+#define MF_DBG_PTR(p, base, n, bit) ((base) + mf_dbg_index((int64_t)((p) - (base)), (int64_t)(n), (bit)))
+#else
+#define MF_DBG_PTR(p, base, n, bit) (p)
+#endif
+unsigned mf_dbg_take_apply();
+unsigned mf_dbg_take_tile();
+unsigned mf_dbg_take_cg();
+unsigned mf_dbg_take_batched();
+unsigned mf_dbg_take_general();
+unsigned mf_dbg_take_csr();
+
 // ------------------------------------------------------------------------- device geometry ----
 // Plain view of a mesh, passed by value to kernels.
 struct MeshView {
@@ -103,6 +148,14 @@ __device__ __forceinline__ void element_nodes(const MeshView &m, int64_t e, int6
 #pragma unroll
     for (int a = 0; a < 8; ++a) nodes[a] = base + (a & 1) * sx + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
   }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) nodes[a] = mf_dbg_index(nodes[a], m.n_nodes, MF_DBG_NODE);
+}
+
+// node a of element e of an explicit connectivity with npe nodes per element (checked in
+// bounds-checked builds)
+__device__ __forceinline__ int64_t cell_node(const MeshView &m, int npe, int64_t e, int a) {
+  return mf_dbg_index((int64_t)__ldg(m.cells + (int64_t)npe * e + a), m.n_nodes, MF_DBG_NODE);
 }
 
 // -------------------------------------------------------------------------------- the mesh ----

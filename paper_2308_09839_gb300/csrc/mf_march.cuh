@@ -164,7 +164,8 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
   IO xr[LOADS][NC];
   bool dr[LOADS];
   // in-plane node index of each load slot (-1: outside the mesh or the tile's plane)
-  const int64_t NPL = (int64_t)NXP * NYP;
+  const int64_t NPL = (int64_t)NXP * NYP, NN = NPL * (g.nz + 1);
+  (void)NN;
   int nib[LOADS];
 #pragma unroll
   for (int l = 0; l < LOADS; ++l) {
@@ -190,7 +191,7 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
 #pragma unroll
     for (int l = 0; l < LOADS; ++l) {
       const bool ok = nib[l] >= 0;
-      const int64_t node = nib[l] + (int64_t)k * NPL;
+      const int64_t node = ok ? mf_dbg_index(nib[l] + (int64_t)k * NPL, NN, MF_DBG_NODE) : 0;
       dr[l] = ok ? __ldg(g.dmask + node) != 0 : true;
       if constexpr (CGU) {
         const int p = tid + l * NT;
@@ -227,7 +228,7 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
             const double z = na == 4 ? __dmul_rn(rv, *rawp(k, 3, i)) : rv;
             v = __fma_rn(sab[1], po, z);  // p_k
             if ((own_slot >> l & 1u) && k >= k0 && k < k1) {
-              const int64_t gi = (nib[l] + (int64_t)k * NPL) * NC + c;
+              const int64_t gi = mf_dbg_index(nib[l] + (int64_t)k * NPL, NN, MF_DBG_NODE) * NC + c;
               cg->pnew[gi] = v;
               cg->x[gi] = __fma_rn(sab[0], po, *rawp(k, 2, i));
               *pown(k, ((p % PX) + EX * (p / PX)) * NC + c) = v;  // owner thread (p % PX, p / PX)
@@ -282,10 +283,13 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
   constexpr bool PREFETCH = PHYS != MF_LAPLACE;
   const int e_step = g.nx * g.ny * NM;
   const float2 *matp = g.mat + NM * (ex + (int64_t)g.nx * (ey + (int64_t)g.ny * s_lo));
+  const int64_t NMC = (int64_t)NM * g.nx * g.ny * g.nz;  // cell constants of the mesh
+  (void)NMC;
   float2 mat_next[NM];
 #pragma unroll
   for (int q = 0; q < NM; ++q)
-    mat_next[q] = (PREFETCH && ein && s_lo < g.nz) ? __ldg(matp + q) : make_float2(0.f, 0.f);
+    mat_next[q] = (PREFETCH && ein && s_lo < g.nz) ? __ldg(MF_DBG_PTR(matp + q, g.mat, NMC, MF_DBG_CELL))
+                                                   : make_float2(0.f, 0.f);
 
   for (int ez = s_lo; ez <= s_hi; ++ez) {
     const bool elem = ein && ez < g.nz;
@@ -295,11 +299,13 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
 #pragma unroll
       for (int q = 0; q < NM; ++q) {
         mat_cur[q] = mat_next[q];
-        mat_next[q] = (ein && ez + 1 < g.nz) ? __ldg(matp + q) : make_float2(0.f, 0.f);
+        mat_next[q] = (ein && ez + 1 < g.nz) ? __ldg(MF_DBG_PTR(matp + q, g.mat, NMC, MF_DBG_CELL))
+                                             : make_float2(0.f, 0.f);
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < NM; ++q) mat_cur[q] = elem ? __ldg(matp + q) : make_float2(0.f, 0.f);
+      for (int q = 0; q < NM; ++q)
+        mat_cur[q] = elem ? __ldg(MF_DBG_PTR(matp + q, g.mat, NMC, MF_DBG_CELL)) : make_float2(0.f, 0.f);
       matp += e_step;
     }
     T Ft[NC][4], S[NC][4];
@@ -375,7 +381,7 @@ __device__ __forceinline__ double march_pass(const TileArgs &g, int item, int64_
       N::st(sm.xrow[ez & 1][l * NT + tid], N::add(v01, shfl_up1<N>(v11)));
     }
     const bool wr = own && ez >= k0;
-    const int64_t node = (ex + NXP * ey) + (int64_t)ez * NPL;
+    const int64_t node = wr ? mf_dbg_index((ex + NXP * ey) + (int64_t)ez * NPL, NN, MF_DBG_NODE) : 0;
     const bool dir = wr && __ldg(g.dmask + node) != 0;  // issued before the barrier
     if (ez + 2 <= plim) {
       stage(ez + 2);  // plane ez's buffer: its last reader finished before the previous barrier

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <random>
+#include <cstring>
 #include <vector>
 
 #include "mf_internal.cuh"
@@ -396,6 +397,67 @@ extern "C" mf_status mf_net_set_params(mf_net *N, const float *host) {
   MF_ARG(N && host, "mf_net_set_params: null argument");
   MF_CUDA(cudaMemcpy(N->p, host, N->n_params * sizeof(float), cudaMemcpyHostToDevice));
   MF_TRY(nn_f32_to_bf16(N->p, N->pb, N->n_params, 0));
+  MF_CUDA(cudaDeviceSynchronize());
+  return MF_OK;
+}
+
+// Training state: a header, then the FP32 parameters and Adam's first and second moments.
+namespace {
+constexpr uint64_t kNetStateMagic = 0x31303054454e464dull;  // the bytes "MFNET001"
+struct NetStateHeader {
+  uint64_t magic;
+  int64_t n_params, step;
+  float clip[2];  // moving average of the gradient norm, last step's scale
+  float out_scale, pad;
+};
+}  // namespace
+
+extern "C" int64_t mf_net_state_bytes(const mf_net *N) {
+  return N ? (int64_t)sizeof(NetStateHeader) + 3 * N->n_params * (int64_t)sizeof(float) : 0;
+}
+
+extern "C" mf_status mf_net_state_save(const mf_net *N, void *host, int64_t bytes) {
+  mf_clear_error();
+  MF_ARG(N && host, "mf_net_state_save: null argument");
+  MF_ARG(bytes >= mf_net_state_bytes(N), "mf_net_state_save: buffer of %lld bytes, %lld needed", (long long)bytes,
+         (long long)mf_net_state_bytes(N));
+  MF_CUDA(cudaDeviceSynchronize());
+  NetStateHeader h{};
+  h.magic = kNetStateMagic;
+  h.n_params = N->n_params;
+  h.step = N->step;
+  MF_CUDA(cudaMemcpy(h.clip, N->clip, 2 * sizeof(float), cudaMemcpyDeviceToHost));
+  h.out_scale = N->out_scale;
+  char *o = static_cast<char *>(host);
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  const size_t pb = N->n_params * sizeof(float);
+  MF_CUDA(cudaMemcpy(o, N->p, pb, cudaMemcpyDeviceToHost));
+  MF_CUDA(cudaMemcpy(o + pb, N->m, pb, cudaMemcpyDeviceToHost));
+  MF_CUDA(cudaMemcpy(o + 2 * pb, N->v, pb, cudaMemcpyDeviceToHost));
+  return MF_OK;
+}
+
+extern "C" mf_status mf_net_state_load(mf_net *N, const void *host, int64_t bytes) {
+  mf_clear_error();
+  MF_ARG(N && host, "mf_net_state_load: null argument");
+  MF_ARG(bytes >= (int64_t)sizeof(NetStateHeader), "mf_net_state_load: %lld bytes is no network state", (long long)bytes);
+  NetStateHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  MF_ARG(h.magic == kNetStateMagic, "mf_net_state_load: not a network state");
+  MF_ARG(h.n_params == N->n_params, "mf_net_state_load: state of %lld parameters, network has %lld",
+         (long long)h.n_params, (long long)N->n_params);
+  MF_ARG(bytes >= mf_net_state_bytes(N), "mf_net_state_load: truncated state (%lld bytes)", (long long)bytes);
+  MF_CUDA(cudaDeviceSynchronize());
+  const char *o = static_cast<const char *>(host) + sizeof(h);
+  const size_t pb = N->n_params * sizeof(float);
+  MF_CUDA(cudaMemcpy(N->p, o, pb, cudaMemcpyHostToDevice));
+  MF_CUDA(cudaMemcpy(N->m, o + pb, pb, cudaMemcpyHostToDevice));
+  MF_CUDA(cudaMemcpy(N->v, o + 2 * pb, pb, cudaMemcpyHostToDevice));
+  MF_CUDA(cudaMemcpy(N->clip, h.clip, 2 * sizeof(float), cudaMemcpyHostToDevice));
+  N->step = h.step;
+  N->out_scale = h.out_scale;
+  MF_TRY(nn_f32_to_bf16(N->p, N->pb, N->n_params, 0));  // the same rounding as the Adam kernel's copy
   MF_CUDA(cudaDeviceSynchronize());
   return MF_OK;
 }

@@ -575,3 +575,18 @@ extern "C" mf_status mf_set_apply_variant(mf_mesh *m, int variant) {
   m->variant = variant;
   return MF_OK;
 }
+
+extern "C" mf_status mf_debug_status(uint32_t *bits, int32_t *enabled) {
+  mf_clear_error();
+  MF_ARG(bits != nullptr, "mf_debug_status: bits is NULL");
+#ifdef MF_DEBUG_BOUNDS
+  if (enabled) *enabled = 1;
+  MF_CUDA(cudaDeviceSynchronize());
+  *bits = mf_dbg_take_apply() | mf_dbg_take_tile() | mf_dbg_take_cg() | mf_dbg_take_batched() |
+          mf_dbg_take_general() | mf_dbg_take_csr();
+#else
+  if (enabled) *enabled = 0;
+  *bits = 0u;
+#endif
+  return MF_OK;
+}

@@ -278,3 +278,5 @@ mf_status tile_apply_fp64(const mf_mesh *m, const double *x, double *y, cudaStre
 mf_status tile_apply_fp32(const mf_mesh *m, const float *x, float *y, cudaStream_t s, const int *skip) {
   return tile_launch<NumF32>(m, x, y, s, skip);
 }
+
+MF_DBG_TU(tile)

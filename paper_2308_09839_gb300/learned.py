@@ -88,18 +88,34 @@ def _crop(t, nzyx, origin, size):
 
 
 def train(R, E, logk, nzyx, crop: int = 33, steps: int = 2000, lr: float = 2e-4, seed: int = 0, log_every: int = 0,
-          warmup: int = 100):
+          warmup: int = 100, stop_at: int | None = None, resume: dict | None = None):
     """Train a network on random crops of `crop`^3 nodes (the full grid when `crop` equals its size)
     with Adam, linear warm-up over `warmup` steps and cosine decay; returns (params, loss history,
-    seconds)."""
+    seconds).
+
+    Checkpoints: with `stop_at` the run stops after that many steps and returns a checkpoint dict
+    instead (the network's training state from mf_net_state_save, the crop generator's state, the
+    step and the loss history so far; save_checkpoint / load_checkpoint write and read it as a .pt
+    file).  `resume` continues such a checkpoint; the resumed run takes the same steps, bitwise, as a
+    run that was never stopped."""
     assert (crop - 1) % 4 == 0
     rng = np.random.default_rng(seed)
     net = mf.Net(crop, crop, crop, seed=seed)
+    start, hist = 0, []
+    if resume is not None:
+        assert resume["crop"] == crop and resume["steps"] == steps, "checkpoint of another run"
+        net.load_state(resume["net_state"])
+        rng.bit_generator.state = resume["rng"]
+        start, hist = int(resume["step"]), list(resume["hist"])
     lk = torch.from_numpy(logk).cuda() if isinstance(logk, np.ndarray) else logk
-    hist = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for s in range(steps):
+    for s in range(start, steps):
+        if stop_at is not None and s == stop_at:
+            ckpt = {"net_state": net.state(), "rng": rng.bit_generator.state, "step": s, "hist": hist,
+                    "crop": crop, "steps": steps}
+            net.close()
+            return ckpt
         i = int(rng.integers(0, R.shape[0]))
         origin = [int(rng.integers(0, (d - crop) // 4 + 1)) * 4 for d in nzyx]
         r = _crop(R[i], nzyx, origin, crop)
@@ -115,6 +131,16 @@ def train(R, E, logk, nzyx, crop: int = 33, steps: int = 2000, lr: float = 2e-4,
     params = net.params()
     net.close()
     return params, hist, secs
+
+
+def save_checkpoint(path: str, ckpt: dict) -> None:
+    """Write a training checkpoint (train(..., stop_at=...)) to a .pt file."""
+    torch.save({k: (torch.from_numpy(v) if isinstance(v, np.ndarray) else v) for k, v in ckpt.items()}, path)
+
+
+def load_checkpoint(path: str) -> dict:
+    d = torch.load(path, weights_only=False)
+    return {k: (v.numpy() if isinstance(v, torch.Tensor) else v) for k, v in d.items()}
 
 
 def make_inference_net(params, nzyx, out_scale: float) -> mf.Net:

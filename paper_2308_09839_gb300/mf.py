@@ -13,7 +13,8 @@ import os
 
 import torch
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmf.so")
+# MF_LIB: path of another build of the library (the bounds-checked libmf_debug.so) to load instead
+_LIB_PATH = os.environ.get("MF_LIB") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmf.so")
 if not os.path.exists(_LIB_PATH):
     raise ImportError(f"{_LIB_PATH} is not built; run `python -m paper_2308_09839_gb300.build` "
                       "(or __graft_entry__.build()) first")
@@ -78,11 +79,15 @@ _SIGS = {
     "mf_cg_solve_batched": (C.c_int, [C.POINTER(vp), i32, C.POINTER(mf_solve_opts), C.POINTER(vp), C.POINTER(vp),
                                       C.POINTER(mf_solve_info), vp]),
     "mf_set_tile_segment": (C.c_int, [vp, i32]),
+    "mf_debug_status": (C.c_int, [C.POINTER(C.c_uint32), C.POINTER(i32)]),
     "mf_net_create": (C.c_int, [i32, i32, i32, C.c_uint64, C.POINTER(vp)]),
     "mf_net_destroy": (C.c_int, [vp]),
     "mf_net_num_params": (i64, [vp]),
     "mf_net_get_params": (C.c_int, [vp, vp]),
     "mf_net_set_params": (C.c_int, [vp, vp]),
+    "mf_net_state_bytes": (i64, [vp]),
+    "mf_net_state_save": (C.c_int, [vp, vp, i64]),
+    "mf_net_state_load": (C.c_int, [vp, vp, i64]),
     "mf_net_set_output_scale": (C.c_int, [vp, C.c_float]),
     "mf_net_forward": (C.c_int, [vp, vp, vp, vp, vp]),
     "mf_net_train_step": (C.c_int, [vp, vp, vp, vp, C.c_float, C.POINTER(C.c_float), vp]),
@@ -298,6 +303,13 @@ def mf_cg_solve_batched(meshes, opts: mf_solve_opts, bs, xs, stream=None, ok=(MF
     return list(infos)
 
 
+def mf_debug_status() -> tuple[int, bool]:
+    """(bits of failed index checks since the last call, whether the loaded library checks at all)."""
+    bits, en = C.c_uint32(), i32()
+    check(lib.mf_debug_status(C.byref(bits), C.byref(en)), "mf_debug_status")
+    return int(bits.value), bool(en.value)
+
+
 def mf_set_tile_segment(h, seg: int) -> None:
     check(lib.mf_set_tile_segment(h.h if isinstance(h, Mesh) else h, seg), "mf_set_tile_segment")
 
@@ -373,6 +385,19 @@ class Net:
 
     def set_output_scale(self, s):
         check(lib.mf_net_set_output_scale(self.h, float(s)), "mf_net_set_output_scale")
+
+    def state(self):
+        """The whole training state (mf_net_state_save) as a uint8 array."""
+        import numpy as np
+        out = np.empty(int(lib.mf_net_state_bytes(self.h)), dtype=np.uint8)
+        check(lib.mf_net_state_save(self.h, out.ctypes.data, out.size), "mf_net_state_save")
+        return out
+
+    def load_state(self, blob):
+        """Restore a training state taken by state() (mf_net_state_load)."""
+        import numpy as np
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        check(lib.mf_net_state_load(self.h, blob.ctypes.data, blob.size), "mf_net_state_load")
 
     def forward(self, r, logk, out=None, stream=None):
         if out is None:

@@ -63,3 +63,11 @@ def test_host_only_calls(lib):
     assert "null" in mf.mf_last_error()
     info = {}
     assert mf.lib.mf_mesh_query(None, None, None, None, None, None, None) == mf.MF_ERR_ARG
+
+
+def test_release_build_reports_no_index_checks(lib):
+    """mf_debug_status in the release library: checks compiled out, no device touched."""
+    from paper_2308_09839_gb300 import mf
+    if os.environ.get("MF_LIB"):
+        pytest.skip("another build of the library is loaded")
+    assert mf.mf_debug_status() == (0, False)

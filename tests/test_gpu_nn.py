@@ -247,3 +247,36 @@ def test_training_pairs_match_oracle():
         ti = e64 / s
         assert np.all(np.abs(T[i].cpu().numpy() / c - ti) <= 2 * tol(ti))
     assert abs(c - float(np.median(ratios))) <= 1e-10 * c
+
+
+def test_training_checkpoint_resume_is_bitwise(tmp_path):
+    """A training run stopped at step 17, written to a .pt file, read back and resumed takes the same
+    steps as the uninterrupted run: equal loss history and parameters, bit for bit (the network's whole
+    training state: parameters, Adam moments and step, clip history, plus the crop generator)."""
+    from paper_2308_09839_gb300 import learned
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    nzyx = (17, 17, 17)
+    R = torch.randn(4, 17 ** 3, device="cuda", generator=g)
+    E = torch.randn(4, 17 ** 3, device="cuda", generator=g)
+    lk = torch.randn(17 ** 3, device="cuda", generator=g)
+    kw = dict(crop=9, steps=40, lr=3e-3, seed=5, warmup=5)
+    pa, ha, _ = learned.train(R, E, lk, nzyx, **kw)
+    ck = learned.train(R, E, lk, nzyx, stop_at=17, **kw)
+    assert ck["step"] == 17 and len(ck["hist"]) == 17
+    path = str(tmp_path / "train.pt")
+    learned.save_checkpoint(path, ck)
+    pb, hb, _ = learned.train(R, E, lk, nzyx, resume=learned.load_checkpoint(path), **kw)
+    assert ha == hb
+    assert np.array_equal(pa, pb)
+    # a buffer that is not a state, or a truncated one, is refused
+    net = mf.Net(9, 9, 9, seed=0)
+    blob = net.state()
+    bad = blob.copy()
+    bad[0] ^= 0xFF
+    with pytest.raises(mf.MfError):
+        net.load_state(bad)
+    with pytest.raises(mf.MfError):
+        net.load_state(blob[:-4])
+    net.load_state(blob)
+    net.close()
