@@ -104,7 +104,8 @@ __global__ void csr_fill_colour(MeshView m, int colour, int64_t count, const int
   if (gid >= count * 8) return;
   const int64_t t = gid >> 3;
   const int a = (int)(gid & 7);
-  const int64_t e = celems ? (int64_t)celems[t] : parity_element_c(t, colour, m.nx, m.ny, m.nz);
+  const int64_t e =
+      mf_dbg_index(celems ? (int64_t)celems[t] : parity_element_c(t, colour, m.nx, m.ny, m.nz), m.n_cells, MF_DBG_CELL);
   int64_t nodes[8];
   element_nodes(m, e, nodes);
   if (m.dmask[nodes[a]]) return;  // Dirichlet row: identity, set separately
@@ -157,7 +158,8 @@ __global__ void diag_colour(MeshView m, int colour, int64_t count, const int32_t
   constexpr int NE = phys_ndpn(EP);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // one element per thread
   if (t >= count) return;
-  const int64_t e = celems ? (int64_t)celems[t] : parity_element_c(t, colour, m.nx, m.ny, m.nz);
+  const int64_t e =
+      mf_dbg_index(celems ? (int64_t)celems[t] : parity_element_c(t, colour, m.nx, m.ny, m.nz), m.n_cells, MF_DBG_CELL);
   int64_t nodes[8];
   element_nodes(m, e, nodes);
   double X[8][3];
@@ -185,10 +187,12 @@ __global__ void tet_fill_colour(MeshView m, int64_t count, const int32_t *__rest
   constexpr int NE = phys_ndpn(EP);
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= count * 4) return;
-  const int64_t e = celems[gid >> 2];
+  const int64_t e = mf_dbg_index((int64_t)celems[gid >> 2], m.n_cells, MF_DBG_CELL);
   const int a = (int)(gid & 3);
   int64_t nodes[4];
   p1::nodes_of(m.cells, e, nodes);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) nodes[a] = mf_dbg_index(nodes[a], m.n_nodes, MF_DBG_NODE);
   if (m.dmask[nodes[a]]) return;  // Dirichlet row: identity, set separately
   double X[4][3], n[4][3];
   for (int c = 0; c < 4; ++c)
@@ -232,10 +236,10 @@ __global__ void __launch_bounds__(64) q2_fill_colour(MeshView m, int64_t count, 
   constexpr int NE = phys_ndpn(EP);
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= count * 27) return;
-  const int64_t e = celems[gid / 27];
+  const int64_t e = mf_dbg_index((int64_t)celems[gid / 27], m.n_cells, MF_DBG_CELL);
   const int a = (int)(gid % 27);
   int64_t nodes[27];
-  for (int c = 0; c < 27; ++c) nodes[c] = m.cells[27 * e + c];
+  for (int c = 0; c < 27; ++c) nodes[c] = cell_node(m, 27, e, c);
   if (m.dmask[nodes[a]]) return;  // Dirichlet row: identity, set separately
   double X[27][3];
   for (int c = 0; c < 27; ++c)
@@ -276,11 +280,11 @@ __global__ void __launch_bounds__(64) q2_diag_colour(MeshView m, int64_t count, 
   constexpr int NE = phys_ndpn(EP);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
-  const int64_t e = celems[t];
+  const int64_t e = mf_dbg_index((int64_t)celems[t], m.n_cells, MF_DBG_CELL);
   int64_t nodes[27];
   double X[27][3];
   for (int c = 0; c < 27; ++c) {
-    nodes[c] = m.cells[27 * e + c];
+    nodes[c] = cell_node(m, 27, e, c);
     for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
   }
   const double c0 = phys_is_laplace(PHYS) ? m.mat[e] : m.mat[2 * e];
@@ -299,9 +303,11 @@ __global__ void tet_diag_colour(MeshView m, int64_t count, const int32_t *__rest
   constexpr int ND = phys_ndpn(PHYS);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
-  const int64_t e = celems[t];
+  const int64_t e = mf_dbg_index((int64_t)celems[t], m.n_cells, MF_DBG_CELL);
   int64_t nodes[4];
   p1::nodes_of(m.cells, e, nodes);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) nodes[a] = mf_dbg_index(nodes[a], m.n_nodes, MF_DBG_NODE);
   double X[4][3], n[4][3];
   for (int c = 0; c < 4; ++c)
     for (int i = 0; i < 3; ++i) X[c][i] = m.X[3 * nodes[c] + i];
