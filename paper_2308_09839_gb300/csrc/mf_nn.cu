@@ -1164,14 +1164,16 @@ __device__ __forceinline__ void st_ch(bf16 *p, const float (&f)[V]) {
 template <int V>
 __global__ void restrict_k(const bf16 *__restrict__ in, int nfx, int nfy, int nfz, int c, bf16 *__restrict__ out,
                            float scale) {
-  const int ncx = (nfx + 1) / 2, ncy = (nfy + 1) / 2, ncz = (nfz + 1) / 2;
-  const int cg = c / V;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t n = (int64_t)ncx * ncy * ncz * cg;
-  if (i >= n) return;
-  const int ch = (int)(i % cg) * V;
-  const int64_t v = i / cg;
-  const int cx = (int)(v % ncx), cy = (int)((v / ncx) % ncy), cz = (int)(v / ((int64_t)ncx * ncy));
+  // grid: x over the (coarse y, coarse x, channel group) items of one plane, y over the planes
+  // (32-bit index arithmetic)
+  const int ncx = (nfx + 1) / 2, ncy = (nfy + 1) / 2;
+  const int cg = c / V, row = ncx * cg;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncy * row) return;
+  const int cy = i / row, r = i - cy * row;
+  const int cx = r / cg, ch = (r - cx * cg) * V;
+  const int cz = blockIdx.y;
+  const int64_t v = ((int64_t)cz * ncy + cy) * ncx + cx;
   float s[V], t[V];
 #pragma unroll
   for (int q = 0; q < V; ++q) s[q] = 0.0f;
@@ -1202,14 +1204,15 @@ __global__ void restrict_k(const bf16 *__restrict__ in, int nfx, int nfy, int nf
 template <int V>
 __global__ void prolong_k(const bf16 *__restrict__ in, int ncx, int ncy, int ncz, int c, bf16 *__restrict__ out,
                           float scale) {
-  const int nfx = 2 * ncx - 1, nfy = 2 * ncy - 1, nfz = 2 * ncz - 1;
-  const int cg = c / V;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t n = (int64_t)nfx * nfy * nfz * cg;
-  if (i >= n) return;
-  const int ch = (int)(i % cg) * V;
-  const int64_t v = i / cg;
-  const int fx = (int)(v % nfx), fy = (int)((v / nfx) % nfy), fz = (int)(v / ((int64_t)nfx * nfy));
+  // grid: x over the (fine y, fine x, channel group) items of one plane, y over the planes
+  const int nfx = 2 * ncx - 1, nfy = 2 * ncy - 1;
+  const int cg = c / V, row = nfx * cg;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nfy * row) return;
+  const int fy = i / row, r = i - fy * row;
+  const int fx = r / cg, ch = (r - fx * cg) * V;
+  const int fz = blockIdx.y;
+  const int64_t v = ((int64_t)fz * nfy + fy) * nfx + fx;
   const int xs[2] = {fx / 2, (fx + 1) / 2}, ys[2] = {fy / 2, (fy + 1) / 2}, zs[2] = {fz / 2, (fz + 1) / 2};
   const int nxp = (fx & 1) ? 2 : 1, nyp = (fy & 1) ? 2 : 1, nzp = (fz & 1) ? 2 : 1;
   const float w = scale / (float)(nxp * nyp * nzp);
@@ -1374,14 +1377,16 @@ extern "C" mf_status mf_grid_restrict(const void *in, int32_t nfx, int32_t nfy, 
   MF_RANGE("mf_grid_restrict");
   mf_clear_error();
   MF_ARG(in && out && nfx % 2 == 1 && nfy % 2 == 1 && nfz % 2 == 1 && c > 0, "mf_grid_restrict: bad argument");
-  const int64_t n = (int64_t)((nfx + 1) / 2) * ((nfy + 1) / 2) * ((nfz + 1) / 2) * c;
+  const int ncx = (nfx + 1) / 2, ncy = (nfy + 1) / 2, ncz = (nfz + 1) / 2;
+  MF_ARG(ncz <= 65535 && (int64_t)ncx * ncy * c < INT32_MAX, "mf_grid_restrict: grid too large");
   mf_count_launches(1);
+  constexpr int T = 256;
   if (vec8(in, out, c))
-    restrict_k<8><<<blocks_for(n / 8), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, nfx, nfy, nfz, c,
-                                                                             (bf16 *)out, scale);
+    restrict_k<8><<<dim3((ncx * ncy * (c / 8) + T - 1) / T, ncz), T, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)in, nfx, nfy, nfz, c, (bf16 *)out, scale);
   else
-    restrict_k<1><<<blocks_for(n), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, nfx, nfy, nfz, c,
-                                                                        (bf16 *)out, scale);
+    restrict_k<1><<<dim3((ncx * ncy * c + T - 1) / T, ncz), T, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)in, nfx, nfy, nfz, c, (bf16 *)out, scale);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }
@@ -1391,14 +1396,16 @@ extern "C" mf_status mf_grid_prolong(const void *in, int32_t ncx, int32_t ncy, i
   MF_RANGE("mf_grid_prolong");
   mf_clear_error();
   MF_ARG(in && out && ncx > 0 && ncy > 0 && ncz > 0 && c > 0, "mf_grid_prolong: bad argument");
-  const int64_t n = (int64_t)(2 * ncx - 1) * (2 * ncy - 1) * (2 * ncz - 1) * c;
+  const int nfx = 2 * ncx - 1, nfy = 2 * ncy - 1, nfz = 2 * ncz - 1;
+  MF_ARG(nfz <= 65535 && (int64_t)nfx * nfy * c < INT32_MAX, "mf_grid_prolong: grid too large");
   mf_count_launches(1);
+  constexpr int T = 256;
   if (vec8(in, out, c))
-    prolong_k<8><<<blocks_for(n / 8), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, ncx, ncy, ncz, c,
-                                                                            (bf16 *)out, scale);
+    prolong_k<8><<<dim3((nfx * nfy * (c / 8) + T - 1) / T, nfz), T, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)in, ncx, ncy, ncz, c, (bf16 *)out, scale);
   else
-    prolong_k<1><<<blocks_for(n), kThreads, 0, (cudaStream_t)stream>>>((const bf16 *)in, ncx, ncy, ncz, c,
-                                                                       (bf16 *)out, scale);
+    prolong_k<1><<<dim3((nfx * nfy * c + T - 1) / T, nfz), T, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)in, ncx, ncy, ncz, c, (bf16 *)out, scale);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
 }
