@@ -39,7 +39,7 @@ UNIT = "GDoF/s"
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 192^3 Laplace and 128^3
 # elasticity meshes, scaled by the node count (the traffic is proportional to it).  Part of y is
 # still dirty in L2 when a launch ends, so the write share is below the bytes written.
-TRAFFIC = {"laplace": round(153668096 * 16974593 / 7189057), "elasticity": round(105907200 * 4173281 / 2146689)}
+TRAFFIC = {"laplace": round(153548544 * 16974593 / 7189057), "elasticity": round(101496576 * 4173281 / 2146689)}
 
 
 def parse():
