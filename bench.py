@@ -743,7 +743,7 @@ def main():
         Rp, Tp, cs = learned.generate_pairs(m5, p5, args.pairs, seed=1, k_range=(2, 150))
         torch.cuda.synchronize()
         t_pairs = time.perf_counter() - t0
-        params, hist, t_train = learned.train(Rp, Tp, learned.node_logk(p5), nzyx, crop=nzyx[0],
+        params, hist, t_train = learned.train(Rp, Tp, learned.node_logk(m5), nzyx, crop=nzyx[0],
                                               steps=args.train_steps, lr=args.lr)
         del Rp, Tp
         net5 = learned.make_inference_net(params, nzyx, cs)

@@ -435,6 +435,11 @@ mf_status mf_net_state_save(const mf_net *net, void *host, int64_t bytes);
 mf_status mf_net_state_load(mf_net *net, const void *host, int64_t bytes);
 mf_status mf_net_set_output_scale(mf_net *net, float scale);
 mf_status mf_net_forward(mf_net *net, const float *r, const float *logk, float *out, mf_stream stream);
+/* The network's second input for a scalar Laplace mesh on a structured box: out[node] (device
+ * float[n_nodes]) = the mean of log kappa over the cells that touch the node (1 to 8 cells), computed
+ * in FP64 and rounded to FP32; the flexible CG forms the same field.  Asynchronous.  Errors:
+ * MF_ERR_ARG, MF_ERR_UNSUPPORTED (other meshes), MF_ERR_CUDA. */
+mf_status mf_node_logk(const mf_mesh *mesh, float *out, mf_stream stream);
 mf_status mf_net_train_step(mf_net *net, const float *r, const float *logk, const float *target, float lr,
                             float *loss, mf_stream stream);
 mf_status mf_net_gradients(mf_net *net, const float *r, const float *logk, const float *target, float *grads,

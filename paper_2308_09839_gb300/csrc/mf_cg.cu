@@ -629,8 +629,10 @@ __global__ void __launch_bounds__(kRedThreads) scaled_norm2(int64_t n, const dou
 
 // rhat = D^{-1/2} r / s (FP32), s = RMS of D^{-1/2} r from ss = ||D^{-1/2} r||^2
 __global__ void scale_to_f32(int64_t n, const double *r, const double *isd, const double *ss, float *out) {
-  const double s = sqrt(fmax(*ss, 1e-300) / (double)n);
-  GRID_STRIDE(i, n) out[i] = (float)(r[i] * isd[i] / s);
+  // one FP64 division per thread, not per node: GB300's FP64 divide is a long sequence on its narrow
+  // FP64 pipe (the output is rounded to FP32, far coarser than the reciprocal's rounding)
+  const double is = 1.0 / sqrt(fmax(*ss, 1e-300) / (double)n);
+  GRID_STRIDE(i, n) out[i] = (float)(r[i] * isd[i] * is);
 }
 
 // z = beta z + omega D^{-1} r (damped Jacobi step; beta = 0 starts z), zero on Dirichlet nodes
@@ -1465,6 +1467,20 @@ extern "C" mf_status mf_operator_diagonal(const mf_mesh *m, double *diag, mf_str
   mf_clear_error();
   MF_ARG(m && diag, "mf_operator_diagonal: null argument");
   return operator_diagonal(m, diag, (cudaStream_t)stream);
+}
+
+extern "C" mf_status mf_node_logk(const mf_mesh *m, float *out, mf_stream stream) {
+  MF_RANGE("mf_node_logk");
+  mf_clear_error();
+  MF_ARG(m && out, "mf_node_logk: null argument");
+  if (!m->structured || m->physics != MF_LAPLACE || m->npe != 8) {
+    mf_set_error("mf_node_logk: scalar Laplace on a structured box only");
+    return MF_ERR_UNSUPPORTED;
+  }
+  mf_count_launches(1);
+  node_logk<<<blocks_for(m->n_nodes), kThreads, 0, (cudaStream_t)stream>>>(m->mat, m->nx, m->ny, m->nz, out);
+  MF_CUDA(cudaGetLastError());
+  return MF_OK;
 }
 
 MF_DBG_TU(cg)

@@ -22,20 +22,10 @@ import torch
 from . import mf
 
 
-def node_logk(p) -> np.ndarray:
-    """Mean of log kappa over the cells touching each node (structured box)."""
-    nx, ny, nz = p.nx, p.ny, p.nz
-    lk = np.log(p.mat).reshape(nz, ny, nx)
-    pad = np.pad(lk, 1, mode="constant")
-    cnt = np.pad(np.ones_like(lk), 1, mode="constant")
-    s = np.zeros((nz + 1, ny + 1, nx + 1))
-    c = np.zeros_like(s)
-    for dz in (0, 1):
-        for dy in (0, 1):
-            for dx in (0, 1):
-                s += pad[dz:dz + nz + 1, dy:dy + ny + 1, dx:dx + nx + 1]
-                c += cnt[dz:dz + nz + 1, dy:dy + ny + 1, dx:dx + nx + 1]
-    return (s / c).reshape(-1).astype(np.float32)
+def node_logk(mesh: mf.Mesh) -> torch.Tensor:
+    """The network's second input channel: the node mean of log kappa (mf_node_logk, on the device;
+    the flexible CG forms the same field)."""
+    return mf.mf_node_logk(mesh)
 
 
 def generate_pairs(mesh: mf.Mesh, p, n_pairs: int, seed: int = 0, k_range=(2, 150), smooth: int = 2,

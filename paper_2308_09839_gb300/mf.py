@@ -90,6 +90,7 @@ _SIGS = {
     "mf_net_state_load": (C.c_int, [vp, vp, i64]),
     "mf_net_set_output_scale": (C.c_int, [vp, C.c_float]),
     "mf_net_forward": (C.c_int, [vp, vp, vp, vp, vp]),
+    "mf_node_logk": (C.c_int, [vp, vp, vp]),
     "mf_net_train_step": (C.c_int, [vp, vp, vp, vp, C.c_float, C.POINTER(C.c_float), vp]),
     "mf_net_gradients": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(C.c_float), vp]),
     "mf_conv3d_fwd": (C.c_int, [vp, i32, i32, i32, i32, vp, vp, i32, vp, i32, vp, vp, vp]),
@@ -301,6 +302,14 @@ def mf_cg_solve_batched(meshes, opts: mf_solve_opts, bs, xs, stream=None, ok=(MF
                                  _stream(stream))
     check(st, "mf_cg_solve_batched", ok)
     return list(infos)
+
+
+def mf_node_logk(mesh, out=None, stream=None):
+    """Node mean of log kappa of a scalar Laplace structured box (device float32[n_nodes])."""
+    if out is None:
+        out = torch.empty(mesh.info["n_nodes"], dtype=torch.float32, device=mesh.device)
+    check(lib.mf_node_logk(mesh.h, _ptr(out), _stream(stream)), "mf_node_logk")
+    return out
 
 
 def mf_debug_status() -> tuple[int, bool]:

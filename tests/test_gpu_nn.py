@@ -157,7 +157,7 @@ def test_learned_preconditioner_gains_over_jacobi_pcg():
     mesh = mf.Mesh.from_problem(p)
     nzyx = (p.nz + 1, p.ny + 1, p.nx + 1)
     R, E, c = learned.generate_pairs(mesh, p, 64, seed=1, k_range=(2, 60))
-    lk = learned.node_logk(p)
+    lk = learned.node_logk(mesh)
     params, hist, secs = learned.train(R, E, lk, nzyx, crop=33, steps=1500, lr=2e-4)
     assert np.mean(hist[-50:]) < 0.7 * np.mean(hist[:20])
     net = learned.make_inference_net(params, nzyx, c)
@@ -280,3 +280,24 @@ def test_training_checkpoint_resume_is_bitwise(tmp_path):
         net.load_state(blob[:-4])
     net.load_state(blob)
     net.close()
+
+
+def test_node_logk_is_the_mean_over_adjacent_cells():
+    """The network's second input channel (mf_node_logk): log kappa averaged over the cells that touch
+    each node, checked by brute force on a small ragged box (corner nodes touch 1 cell, interior 8)."""
+    from paper_2308_09839_gb300 import inputs
+    p = inputs.laplace_box(4, ny=3, nz=2, sigma=1.0, seed=4)
+    mesh = mf.Mesh.from_problem(p)
+    got = mf.mf_node_logk(mesh).cpu().numpy()
+    lk = np.log(p.mat).reshape(p.nz, p.ny, p.nx)
+    for k in range(p.nz + 1):
+        for j in range(p.ny + 1):
+            for i in range(p.nx + 1):
+                vals = [lk[ez, ey, ex] for ez in (k - 1, k) for ey in (j - 1, j) for ex in (i - 1, i)
+                        if 0 <= ez < p.nz and 0 <= ey < p.ny and 0 <= ex < p.nx]
+                n = inputs.node_id(i, j, k, p.nx, p.ny)
+                assert abs(got[n] - np.mean(vals)) <= 1e-6 * max(1.0, abs(np.mean(vals)))
+    # a mesh it does not serve is refused
+    pe = inputs.elasticity_box(2, seed=1)
+    with pytest.raises(mf.MfError):
+        mf.mf_node_logk(mf.Mesh.from_problem(pe), out=torch.empty(pe.n_nodes, device="cuda"))

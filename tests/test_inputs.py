@@ -60,19 +60,3 @@ def test_renumber_is_a_relabelling():
     assert np.array_equal(np.sort(node_perm), np.arange(p.n_nodes))
     assert np.array_equal(coords[new_cells], p.coords[cells[elem_perm]])
     assert np.array_equal(dirichlet[node_perm], p.dirichlet)
-
-
-def test_node_logk_is_the_mean_over_adjacent_cells():
-    """The network's second input channel: log kappa averaged over the cells that touch each node,
-    checked by brute force on a small box (corner nodes touch 1 cell, interior nodes 8)."""
-    from paper_2308_09839_gb300 import learned
-    p = inputs.laplace_box(4, ny=3, nz=2, sigma=1.0, seed=4)
-    got = learned.node_logk(p)
-    lk = np.log(p.mat).reshape(p.nz, p.ny, p.nx)
-    for k in range(p.nz + 1):
-        for j in range(p.ny + 1):
-            for i in range(p.nx + 1):
-                vals = [lk[ez, ey, ex] for ez in (k - 1, k) for ey in (j - 1, j) for ex in (i - 1, i)
-                        if 0 <= ez < p.nz and 0 <= ey < p.ny and 0 <= ex < p.nx]
-                n = inputs.node_id(i, j, k, p.nx, p.ny)
-                assert abs(got[n] - np.mean(vals)) <= 1e-6 * max(1.0, abs(np.mean(vals)))
