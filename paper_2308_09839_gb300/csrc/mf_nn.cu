@@ -519,11 +519,13 @@ struct TcpCfg {
   static constexpr int W = 27 * TAPB;
   static constexpr int LIMIT = 220 * 1024;
   static constexpr int halo(int tz) { return (tz + 2) * KC * kTcKCS; }
-  static constexpr int TZ = (2 * halo(4) + W <= LIMIT)   ? 4
-                            : (2 * halo(2) + W <= LIMIT) ? 2
-                            : (2 * halo(1) + W <= LIMIT) ? 1
-                            : (halo(2) + W <= LIMIT)     ? 2
-                                                         : 1;
+  // one plane per item only when an accumulator set still spans 32 columns (the epilogue reads the
+  // sets in blocks of 32): with 16 output channels the single-buffered two-plane form is taken instead
+  static constexpr int TZ = (2 * halo(4) + W <= LIMIT)               ? 4
+                            : (2 * halo(2) + W <= LIMIT)             ? 2
+                            : (2 * halo(1) + W <= LIMIT && CN >= 32) ? 1
+                            : (halo(2) + W <= LIMIT)                 ? 2
+                                                                     : 1;
   static constexpr int NS = (2 * halo(TZ) + W <= LIMIT) ? 2 : 1;
   static constexpr int HALO = halo(TZ);
   static constexpr bool FITS = NS * HALO + W <= LIMIT;
@@ -576,6 +578,7 @@ template <int CKP, int CN, int MODE>
 __global__ void __launch_bounds__(kTcpThreads) conv_tcp(TcArgs a, const __grid_constant__ CUtensorMap tmap) {
   using Cfg = TcpCfg<CKP, CN>;
   constexpr int KC = Cfg::KC, TZ = Cfg::TZ, NS = Cfg::NS, KS = CKP / 16, ACC = Cfg::ACC;
+  static_assert(ACC % 32 == 0, "the epilogue reads an accumulator set in blocks of 32 columns");
   extern __shared__ __align__(16) unsigned char tcp_smem_raw[];
   __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2];
   __shared__ uint32_t tmem_slot;

@@ -24,14 +24,18 @@ def rel(a, b):
 
 SMALL = [((5, 7, 9), 2, 16), ((4, 4, 8), 16, 16), ((9, 6, 11), 16, 32), ((5, 5, 5), 32, 64),
          ((3, 9, 10), 64, 64), ((6, 5, 7), 64, 32), ((7, 7, 7), 32, 16), ((9, 9, 9), 16, 1), ((4, 5, 3), 3, 5),
-         ((7, 6, 5), 64, 48), ((5, 6, 7), 64, 40)]
+         ((7, 6, 5), 64, 48), ((5, 6, 7), 64, 40),
+         # 64 inputs to at most 16 outputs (forward) and 16 to 64 (its input gradient reads 64 channels
+         # into 16): the configuration whose accumulator sets must span two planes
+         ((6, 7, 5), 64, 16), ((5, 5, 6), 64, 8), ((5, 6, 6), 16, 64)]
 # Node grids of the network's levels at sizes where the convolution kernels' persistent CTAs each
 # loop over several work items (more output tiles than CTAs resident on the GPU), so that resident
 # weights, re-staged halos and the per-item barriers are compared with the oracle too.  64 -> 64 (and
 # 64 -> 48, 64 -> 40) forward runs as two launches over halves of the output channels; its input
 # gradient takes the path that stages the weights in groups of taps.
 LARGE = [((65, 65, 65), 2, 16), ((65, 65, 65), 16, 16), ((65, 65, 65), 16, 1), ((33, 33, 33), 16, 32),
-         ((33, 33, 33), 32, 64), ((41, 41, 41), 64, 64), ((33, 33, 33), 64, 32), ((49, 49, 49), 32, 16)]
+         ((33, 33, 33), 32, 64), ((41, 41, 41), 64, 64), ((33, 33, 33), 64, 32), ((49, 49, 49), 32, 16),
+         ((33, 33, 33), 64, 16)]
 SHAPES = SMALL + LARGE
 
 
