@@ -71,3 +71,43 @@ def test_release_build_reports_no_index_checks(lib):
     if os.environ.get("MF_LIB"):
         pytest.skip("another build of the library is loaded")
     assert mf.mf_debug_status() == (0, False)
+
+
+C_PROGRAM = r"""
+#include "mf.h"
+#include <stdio.h>
+int main(void) {
+  mf_solve_opts o;
+  uint32_t bits = 1;
+  int32_t enabled = 1;
+  mf_status s;
+  mf_solve_opts_default(&o);
+  s = mf_debug_status(&bits, &enabled);
+  printf("%s %g\n", mf_version(), o.rtol);
+  /* argument checks happen before any device call */
+  if (mf_apply_laplace(NULL, NULL, NULL, NULL) != MF_ERR_ARG) return 2;
+  if (mf_spmv_csr(NULL, NULL, NULL, NULL) != MF_ERR_ARG) return 3;
+  return s != MF_OK || bits != 0u || enabled != 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/mf.h compiles as strict C99 (no C++ in the boundary) and a C program links libmf.so
+    and runs its host-only calls."""
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("gcc unavailable")
+    if os.environ.get("MF_LIB"):
+        pytest.skip("another build of the library is loaded")
+    src = tmp_path / "use_mf.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use_mf"
+    pkg = os.path.dirname(LIB)
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", pkg, "-l:libmf.so", f"-Wl,-rpath,{pkg}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
+    assert run.stdout.startswith("mf-gb300")
