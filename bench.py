@@ -784,7 +784,8 @@ def main():
         "config": {"workload": f"Q1 matrix-free apply, Laplace {pL.nx}^3 Cartesian (F={F[0]}) + elasticity "
                                f"{pE.nx}^3 Cartesian (F={F[1]}), 8 z-layers x lognormal(0,0.5)",
                    "n_dof_total": [pL.n_dof, pE.n_dof], "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (no flush)", "variant": args.variant,
+                   "l2": f"no flush: the FP64 x and y of one apply alone exceed the 129 MB L2 "
+                         f"({16 * pL.n_dof / 1e9:.2f} GB Laplace, {16 * pE.n_dof / 1e9:.2f} GB elasticity)", "variant": args.variant,
                    "tile_segments": segs or None},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
         "extras": extras,
