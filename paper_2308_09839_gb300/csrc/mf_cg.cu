@@ -26,6 +26,13 @@ namespace {
 
 constexpr int kRedBlocks = 608;  // 4 per SM on 152 SMs; fixed so the reduction tree is fixed
 constexpr int kRedThreads = 256;
+// The per-iteration vector kernels take kVecUnroll strided elements per step of their grid-stride
+// loop and issue all of the step's loads before its arithmetic, so that each thread has kVecUnroll
+// times the loads of a plain grid-stride loop in flight (HBM needs far more bytes in flight per SM
+// than 32 warps with one 8-byte load each).  A thread still visits i, i + S, i + 2S, ... in that
+// order, so every sum is formed in the order of the plain loop.  Their launch bounds keep all
+// kRedBlocks blocks resident at once (at most 64 registers a thread).
+constexpr int kVecUnroll = 4;
 
 struct CgScalars {
   double bb, rr, rz, pAp, alpha, beta, tol2, res2;
@@ -125,19 +132,33 @@ __global__ void __launch_bounds__(kRedThreads) cg_init(int64_t n, const R *__res
 
 // pAp = p.Ap (when the operator does not fuse it into its own write phase).
 template <typename R>
-__global__ void __launch_bounds__(kRedThreads) cg_pap(int64_t n, const R *__restrict__ p, const R *__restrict__ Ap,
+__global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) cg_pap(int64_t n, const R *__restrict__ p, const R *__restrict__ Ap,
                                                       double *partials, CgScalars *sc) {
   if (sc->done) return;
   double v[1] = {0.0};
-  GRID_STRIDE(i, n) v[0] += (double)p[i] * (double)Ap[i];
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kVecUnroll - 1) * S < n; i += kVecUnroll * S) {
+    R pu[kVecUnroll], au[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      pu[u] = p[i + u * S];
+      au[u] = Ap[i + u * S];
+    }
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) v[0] += (double)pu[u] * (double)au[u];
+  }
+  for (; i < n; i += S) v[0] += (double)p[i] * (double)Ap[i];
   double out[1];
   if (grid_reduce<1>(v, partials, &sc->ticket, out) && threadIdx.x == 0) sc->pAp = out[0];
 }
 
 // x += alpha p; r -= alpha Ap; rho' = r.z (z = M r), ||r||^2; beta = rho'/rho; convergence test.
-// x null: r only (the fused iteration adds alpha p to x in the next apply, or cg_flush_x at the end).
-template <typename R>
-__global__ void __launch_bounds__(kRedThreads) cg_update_xr(int64_t n, R *__restrict__ x, R *__restrict__ r,
+// X false: r only, x and p are not read (the fused iteration adds alpha p to x in the next apply, or
+// cg_flush_x at the end).  A step takes kVecUnroll elements for r alone and half as many for x and r,
+// about eight loads in flight per thread either way.
+template <typename R, bool X>
+__global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) cg_update_xr(int64_t n, R *__restrict__ x, R *__restrict__ r,
                                                             const R *__restrict__ p, const R *__restrict__ Ap,
                                                             const double *__restrict__ invdiag, double *partials,
                                                             CgScalars *sc) {
@@ -158,14 +179,35 @@ __global__ void __launch_bounds__(kRedThreads) cg_update_xr(int64_t n, R *__rest
     sc->xpend = 1;
   }
   double v[2] = {0.0, 0.0};
-  GRID_STRIDE(i, n) {
-    if (x) x[i] = (R)__fma_rn(alpha, (double)p[i], (double)x[i]);
-    const R ri = (R)__fma_rn(-alpha, (double)Ap[i], (double)r[i]);
-    r[i] = ri;
+  // one element: x_j and r_j updated from the loaded values, then the two sums
+  auto elem = [&](int64_t j, R pj, R xj, R aj, R rj, double dj) {
+    if constexpr (X) x[j] = (R)__fma_rn(alpha, (double)pj, (double)xj);
+    const R ri = (R)__fma_rn(-alpha, (double)aj, (double)rj);
+    r[j] = ri;
     const double rd = (double)ri;
     v[0] += rd * rd;
-    v[1] += invdiag ? rd * rd * invdiag[i] : rd * rd;
+    v[1] += invdiag ? rd * rd * dj : rd * rd;
+  };
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  constexpr int U = X ? kVecUnroll / 2 : kVecUnroll;
+  for (; i + (U - 1) * S < n; i += U * S) {
+    R pu[U], xu[U], au[U], ru[U];
+    double du[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t j = i + u * S;
+      pu[u] = X ? p[j] : (R)0;
+      xu[u] = X ? x[j] : (R)0;
+      au[u] = Ap[j];
+      ru[u] = r[j];
+      du[u] = invdiag ? invdiag[j] : 1.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) elem(i + u * S, pu[u], xu[u], au[u], ru[u], du[u]);
   }
+  for (; i < n; i += S)
+    elem(i, X ? p[i] : (R)0, X ? x[i] : (R)0, Ap[i], r[i], invdiag ? invdiag[i] : 1.0);
   double out[2];
   if (grid_reduce<2>(v, partials, &sc->ticket, out) && threadIdx.x == 0) {
     const double rr = out[0], rz = out[1];
@@ -187,14 +229,30 @@ __global__ void __launch_bounds__(kRedThreads) cg_update_xr(int64_t n, R *__rest
 
 // p = z + beta p.
 template <typename R>
-__global__ void __launch_bounds__(kRedThreads) cg_update_p(int64_t n, const R *__restrict__ r, R *__restrict__ p,
+__global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) cg_update_p(int64_t n, const R *__restrict__ r, R *__restrict__ p,
                                                            const double *__restrict__ invdiag, const CgScalars *sc) {
   if (sc->done) return;
   const double beta = sc->beta;
-  GRID_STRIDE(i, n) {
-    const double z = invdiag ? __dmul_rn((double)r[i], invdiag[i]) : (double)r[i];
-    p[i] = (R)__fma_rn(beta, (double)p[i], z);
+  auto elem = [&](int64_t j, R rj, R pj, double dj) {
+    const double z = invdiag ? __dmul_rn((double)rj, dj) : (double)rj;
+    p[j] = (R)__fma_rn(beta, (double)pj, z);
+  };
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kVecUnroll - 1) * S < n; i += kVecUnroll * S) {
+    R ru[kVecUnroll], pu[kVecUnroll];
+    double du[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      const int64_t j = i + u * S;
+      ru[u] = r[j];
+      pu[u] = p[j];
+      du[u] = invdiag ? invdiag[j] : 1.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) elem(i + u * S, ru[u], pu[u], du[u]);
   }
+  for (; i < n; i += S) elem(i, r[i], p[i], invdiag ? invdiag[i] : 1.0);
 }
 
 // End of a fused CG solve that started at iteration iter0: the last iteration's x += alpha p, if its
@@ -491,7 +549,7 @@ mf_status cg_iteration(const OpFn &op, const OpDotFn &opdot, int64_t n, R *x, R 
     mf_count_launches(3);
     cg_pap<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, p, Ap, partials, sc);
   }
-  cg_update_xr<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, Ap, invdiag, partials, sc);
+  cg_update_xr<R, true><<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, Ap, invdiag, partials, sc);
   cg_update_p<R><<<kRedBlocks, kRedThreads, 0, s>>>(n, r, p, invdiag, sc);
   MF_CUDA(cudaGetLastError());
   return MF_OK;
@@ -1184,7 +1242,7 @@ mf_status cg_solve_impl(mf_mesh *m, const mf_solve_opts *o, const double *b, dou
       MF_TRY(tile_apply_cg_fp64(m, w->r, po, idg, pn, w->x, w->Ap, &w->sc->alpha, st, &w->sc->done, w->dotp,
                                 w->dticket, &w->sc->pAp));
       mf_count_launches(1);
-      cg_update_xr<double><<<kRedBlocks, kRedThreads, 0, st>>>(n, nullptr, w->r, nullptr, w->Ap, idg, w->partials,
+      cg_update_xr<double, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, nullptr, w->r, nullptr, w->Ap, idg, w->partials,
                                                                w->sc);
       MF_CUDA(cudaGetLastError());
       return MF_OK;
