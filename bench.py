@@ -247,6 +247,12 @@ def oracle_sample_rate(problems, nz_slabs, repeats=1):
     return dof_equiv / secs, secs, "; ".join(desc)
 
 
+def workload_name(pL, pE):
+    """The benchmarked workload, named the same way by both arms."""
+    return (f"Q1 matrix-free apply, Laplace {pL.nx}^3 Cartesian (F={pL.n_free}) + elasticity "
+            f"{pE.nx}^3 Cartesian (F={pE.n_free}), 8 z-layers x lognormal(0,0.5)")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -266,8 +272,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"Q1 matrix-free apply, Laplace {args.n_laplace}^3 + elasticity {args.n_elasticity}^3 "
-                               "Cartesian, layered lognormal coefficients", "l2": "inputs larger than L2"},
+        "config": {"workload": workload_name(pL, pE), "n_dof_total": [pL.n_dof, pE.n_dof],
+                   "parallelism": "host cores", "l2": "not applicable: the oracle runs on the host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "cpu_model": cpu_model(),
                          "sample": "per step: " + desc + " (one-cell-thick slabs of both workloads, one per "
                                    "process, all at once)"},
@@ -781,8 +787,7 @@ def main():
         "dtype_note": ("double-word FP32 arithmetic (pairs of floats), FP64 inputs and outputs, parity <= 1e-12 "
                        "relative 2-norm against the FP64 oracle" if args.variant == 0 else "FP64 arithmetic"),
         "data": "synthetic",
-        "config": {"workload": f"Q1 matrix-free apply, Laplace {pL.nx}^3 Cartesian (F={F[0]}) + elasticity "
-                               f"{pE.nx}^3 Cartesian (F={F[1]}), 8 z-layers x lognormal(0,0.5)",
+        "config": {"workload": workload_name(pL, pE),
                    "n_dof_total": [pL.n_dof, pE.n_dof], "parallelism": f"replicas{world}",
                    "l2": f"no flush: the FP64 x and y of one apply alone exceed the 129 MB L2 "
                          f"({16 * pL.n_dof / 1e9:.2f} GB Laplace, {16 * pE.n_dof / 1e9:.2f} GB elasticity)", "variant": args.variant,
