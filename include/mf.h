@@ -415,8 +415,10 @@ mf_status mf_set_tile_segment(mf_mesh *mesh, int32_t seg);
  *                       gradient-norm history of the clip, the output scale.  Training continued
  *                       after a load takes the same steps, bitwise, as training that was never
  *                       interrupted (the kernels are deterministic).  Save and load synchronise the
- *                       device; load returns MF_ERR_ARG for a buffer that is no state, is truncated or
- *                       holds another parameter count.
+ *                       device; load returns MF_ERR_ARG for a buffer that is no state, is truncated,
+ *                       holds another parameter count or a header out of range (negative step,
+ *                       output scale not positive, clip values not finite), before it changes the
+ *                       network.
  * Low-level kernels, exposed for parity tests (BF16 tensors as uint16 bit patterns, channels-last
  * [z][y][x][C]; weights [27][Cin][Cout] with tap t = dx + 3 dy + 9 dz for offsets (d - 1)):
  *   mf_conv3d_fwd   y = relu?(conv(x, w) + bias + skip); C in [1, 64].

@@ -448,6 +448,9 @@ extern "C" mf_status mf_net_state_load(mf_net *N, const void *host, int64_t byte
   MF_ARG(h.n_params == N->n_params, "mf_net_state_load: state of %lld parameters, network has %lld",
          (long long)h.n_params, (long long)N->n_params);
   MF_ARG(bytes >= mf_net_state_bytes(N), "mf_net_state_load: truncated state (%lld bytes)", (long long)bytes);
+  MF_ARG(h.step >= 0 && std::isfinite(h.out_scale) && h.out_scale > 0.0f && std::isfinite(h.clip[0]) &&
+             h.clip[0] >= 0.0f && std::isfinite(h.clip[1]),
+         "mf_net_state_load: corrupt header (step %lld, output scale %g)", (long long)h.step, (double)h.out_scale);
   MF_CUDA(cudaDeviceSynchronize());
   const char *o = static_cast<const char *>(host) + sizeof(h);
   const size_t pb = N->n_params * sizeof(float);
