@@ -282,6 +282,15 @@ def test_training_checkpoint_resume_is_bitwise(tmp_path):
         net.load_state(bad)
     with pytest.raises(mf.MfError):
         net.load_state(blob[:-4])
+    # header fields out of range (header: magic, n_params, step as 8-byte integers, two clip
+    # floats, the output scale): a negative step, a zero output scale, a NaN clip average
+    for off, val in ((16, np.int64(-1)), (32, np.float32(0.0)), (24, np.float32(np.nan))):
+        bad = blob.copy()
+        raw = np.array([val]).view(np.uint8)
+        bad[off:off + raw.size] = raw
+        with pytest.raises(mf.MfError):
+            net.load_state(bad)
+    assert np.array_equal(net.state(), blob)  # refused loads left the network as it was
     net.load_state(blob)
     net.close()
 
