@@ -261,7 +261,8 @@ def run_reference(args):
     pL = inputs.cartesian_laplace_256(n=args.n_laplace)
     pE = inputs.cartesian_elasticity_160(n=args.n_elasticity)
     workers = os.cpu_count() or 1
-    oracle_all_core_rate([pL, pE], [1, 1], workers)  # warm-up (the pool is created inside)
+    for _ in range(max(1, args.warmup)):  # untimed warm-up steps (each step creates its own pool)
+        oracle_all_core_rate([pL, pE], [1, 1], workers)
     rates, tot = [], 0.0
     for _ in range(args.steps):
         r, s, desc = oracle_all_core_rate([pL, pE], [1, 1], workers)
