@@ -129,7 +129,9 @@ def save_checkpoint(path: str, ckpt: dict) -> None:
 
 
 def load_checkpoint(path: str) -> dict:
-    d = torch.load(path, weights_only=False)
+    """Read a checkpoint written by save_checkpoint.  It holds tensors and plain values only, so it is
+    read with torch's weights-only loader: a file holding any other object is refused, not unpickled."""
+    d = torch.load(path, weights_only=True)
     return {k: (v.numpy() if isinstance(v, torch.Tensor) else v) for k, v in d.items()}
 
 
