@@ -41,21 +41,35 @@ def _device_key() -> str:
 
 
 def _load() -> dict:
+    """The cache as a dict; a missing, unreadable or malformed file reads as empty."""
     try:
-        return json.load(open(cache_path()))
+        with open(cache_path()) as f:
+            d = json.load(f)
     except (OSError, ValueError):
         return {}
+    return d if isinstance(d, dict) else {}
 
 
 def _store(d: dict) -> None:
+    """Replace the cache file atomically.  Each process writes its own temporary file, so processes
+    that tune at once (one per GPU) never interleave their writes; the last replacement wins."""
     path = cache_path()
+    tmp = f"{path}.{os.getpid()}.tmp"
     try:
-        os.makedirs(os.path.dirname(path), exist_ok=True)
-        with open(path + ".tmp", "w") as f:
+        os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+        with open(tmp, "w") as f:
             json.dump(d, f, indent=1, sort_keys=True)
-        os.replace(path + ".tmp", path)
+        os.replace(tmp, path)
     except OSError:
         pass
+
+
+def _cached(cache: dict, key: str, candidates) -> int | None:
+    """The cached choice under `key` if it is one of `candidates`, else None (the entry is tuned again)."""
+    v = cache.get(key)
+    if isinstance(v, int) and not isinstance(v, bool) and v in candidates:
+        return v
+    return None
 
 
 def _time_batch(meshes, bs, xs, iters: int, reps: int = 2) -> float:
@@ -84,7 +98,7 @@ def tune(meshes, dims, bs, xs, iters: int = 20, use_cache: bool = True) -> dict:
     cache = _load() if use_cache else {}
     buckets = sorted({_bucket(d) for d in dims})
     choice = {b: 16 for b in buckets}
-    cached = {b: cache.get(f"{key}|bucket{b}") for b in buckets}
+    cached = {b: _cached(cache, f"{key}|bucket{b}", CANDIDATES) for b in buckets}
     if use_cache and all(v is not None for v in cached.values()):
         choice = {b: int(v) for b, v in cached.items()}
     else:
@@ -119,8 +133,8 @@ def tune_apply(mesh, reps: int = 20, use_cache: bool = True) -> int:
     GPU, physics and mesh dimensions.  The choice never changes the result bits."""
     key = f"{_device_key()}|apply|{mesh.physics}|{mesh.dims}"
     cache = _load() if use_cache else {}
-    if use_cache and key in cache:
-        seg = int(cache[key])
+    seg = _cached(cache, key, APPLY_CANDIDATES) if use_cache else None
+    if seg is not None:
         mf.mf_set_tile_segment(mesh, seg)
         return seg
     n = mesh.info["n_dof"]
