@@ -111,3 +111,37 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
     run = subprocess.run([str(exe)], capture_output=True, text=True)
     assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
     assert run.stdout.startswith("mf-gb300")
+
+
+def test_ctypes_structs_and_constants_match_the_header(lib, tmp_path):
+    """The binding's view of the boundary equals the C compiler's: every field offset and the size of
+    mf_solve_opts and mf_solve_info, and the value of every MF_* integer constant mf.py defines (a
+    name the header lacks fails to compile)."""
+    import ctypes
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("gcc unavailable")
+    from paper_2308_09839_gb300 import mf
+    lines = ['#include "mf.h"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
+    expect = []
+    for st in (mf.mf_solve_opts, mf.mf_solve_info):
+        name = st.__name__
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        expect.append(ctypes.sizeof(st))
+        for field, _ in st._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {field}));')
+            expect.append(getattr(st, field).offset)
+    consts = sorted(k for k, v in vars(mf).items() if k.startswith("MF_") and isinstance(v, int))
+    assert len(consts) > 20
+    for k in consts:
+        lines.append(f'  printf("%lld\\n", (long long)({k}));')
+        expect.append(getattr(mf, k))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == expect
