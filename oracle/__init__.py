@@ -15,4 +15,6 @@ Modules:
            error norms (Eqs. 1-6, Algorithm 1, Sec. 3)
   solvers  textbook CG (the operations of Table 4), Jacobi-PCG, flexible CG, iterative refinement
   conv     plain 3D convolution forward/backward for the learned preconditioner's network
+  net      the network's forward and backward composed from ``conv``
+  optim    its training step: Adam (Kingma & Ba 2015) and the library's gradient-norm clip
 """

@@ -1,5 +1,6 @@
-"""Pins of the network oracle (oracle/conv.py) against definitions it does not use itself."""
+"""Pins of the network oracle (oracle/conv.py, oracle/net.py, oracle/optim.py) against definitions it does not use itself."""
 import numpy as np
+import pytest
 
 from oracle import conv
 
@@ -100,3 +101,46 @@ def test_network_oracle_gradient_matches_finite_differences():
         lm = net.loss_and_grad(p - dp, inp, tgt, bf16=False)[0]
         fd = (lp - lm) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
+
+
+def test_adam_closed_forms():
+    """Adam (oracle/optim.py) against what its definition fixes: the first step from zero moments
+    moves every parameter by lr g / (|g| + eps) (the bias corrections make m_hat = g, v_hat = g^2);
+    a constant gradient keeps that step size at every later step; a zero gradient component never
+    moves; and the moments follow their geometric sums."""
+    from oracle import optim
+    rng = np.random.default_rng(3)
+    p0 = rng.standard_normal(50)
+    g = rng.standard_normal(50) * np.logspace(-6, 2, 50)
+    g[7] = 0.0
+    lr, eps = 1e-3, 1e-8
+    p1, m1, v1 = optim.adam_step(p0, g, np.zeros(50), np.zeros(50), 1, lr)
+    np.testing.assert_allclose(p0 - p1, lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-18)
+    p, m, v = p0, np.zeros(50), np.zeros(50)
+    for t in range(1, 13):
+        p, m, v = optim.adam_step(p, g, m, v, t, lr)
+    np.testing.assert_allclose(p0 - p, 12 * lr * g / (np.abs(g) + eps), rtol=1e-10, atol=1e-16)
+    assert p[7] == p0[7]
+    np.testing.assert_allclose(m, (1 - 0.9 ** 12) * g, rtol=1e-12)
+    np.testing.assert_allclose(v, (1 - 0.999 ** 12) * g * g, rtol=1e-12)
+    # a gradient that flips sign at the second step: m = 0.9 (0.1 g) - 0.1 g and
+    # v = (0.999 * 0.001 + 0.001) g^2, corrected by 1 - 0.9^2 and 1 - 0.999^2 (the difference of two
+    # parameters of size up to 3 is exact to a few of their ulps, hence the absolute tolerance)
+    p2, _, _ = optim.adam_step(p1, -g, m1, v1, 2, lr)
+    m_hat = (0.9 * 0.1 * g - 0.1 * g) / (1 - 0.81)
+    v_hat = (0.999 * 0.001 + 0.001) * g * g / (1 - 0.999 ** 2)
+    np.testing.assert_allclose(p1 - p2, lr * m_hat / (np.sqrt(v_hat) + eps), rtol=1e-12, atol=4e-15)
+
+
+def test_gradient_clip_special_cases():
+    """The clip rule (oracle/optim.py): the first step keeps its gradient and sets the average; a
+    norm up to 5x the average is kept; 10x is halved and the average moves by a tenth of the clipped
+    norm; a non-finite norm skips the step and keeps the average."""
+    from oracle import optim
+    assert optim.clip_scale(3.0, 0.0) == (1.0, 3.0)
+    s, e = optim.clip_scale(10.0, 2.0)
+    assert s == 1.0 and e == pytest.approx(0.9 * 2.0 + 0.1 * 10.0)
+    s, e = optim.clip_scale(20.0, 2.0)
+    assert s == pytest.approx(0.5) and e == pytest.approx(0.9 * 2.0 + 0.1 * 10.0)
+    assert optim.clip_scale(float("nan"), 2.0) == (0.0, 2.0)
+    assert optim.clip_scale(float("inf"), 2.0) == (0.0, 2.0)
