@@ -152,6 +152,41 @@ def test_network_training_reduces_loss_and_is_deterministic():
     assert np.array_equal(p0, params)
 
 
+def test_training_step_is_adam_on_the_clipped_gradient():
+    """mf_net_train_step against oracle/optim.py, one step at a time: with the gradient g_t that
+    mf_net_gradients returns at the current weights (the same forward and backward), the new FP32
+    weights equal the oracle's FP64 Adam step on scale_t g_t, scale_t from the oracle's clip rule on
+    ||g_t||.  The second step's target is scaled by 1e-3, which makes its gradient far larger than
+    5x the first one's, so that step is clipped; the third is not.  Tolerance: 1e-4 lr plus 2.5e-7 of
+    the weight, from the FP32 bias corrections 1 - b^t (their relative error reaches 3e-5 at t = 2)
+    and the rounding of the weight (an FP32 emulation of the step stays below 0.15 of it)."""
+    from oracle import optim
+    dims = (9, 9, 9)
+    inp, tgt = _net_case(dims, seed=2)
+    r = torch.from_numpy(np.ascontiguousarray(inp[..., 0]).reshape(-1)).cuda()
+    k = torch.from_numpy(np.ascontiguousarray(inp[..., 1]).reshape(-1)).cuda()
+    t1 = torch.from_numpy(tgt.reshape(-1)).cuda()
+    t2 = t1 * 1e-3
+    nt = mf.Net(*dims, seed=4)
+    p = nt.params().astype(np.float64)
+    m, v, ema, lr, scales = np.zeros_like(p), np.zeros_like(p), 0.0, 1e-3, []
+    for step, t in enumerate((t1, t2, t1), start=1):
+        _, g = nt.gradients(r, k, t)
+        g = g.astype(np.float64)
+        assert np.all(np.isfinite(g)) and np.any(g != 0)
+        scale, ema = optim.clip_scale(float(np.linalg.norm(g)), ema)
+        scales.append(scale)
+        p_exp, m, v = optim.adam_step(p, scale * g, m, v, step, lr)
+        nt.train_step(r, k, t, lr)
+        p_gpu = nt.params().astype(np.float64)
+        err = np.abs(p_gpu - p_exp)
+        tol = 1e-4 * lr + 2.5e-7 * np.abs(p_exp)
+        assert np.all(err <= tol), (step, float((err / tol).max()))
+        p = p_gpu
+    nt.close()
+    assert scales[0] == 1.0 and scales[1] < 0.1 and scales[2] == 1.0, scales
+
+
 def test_learned_preconditioner_gains_over_jacobi_pcg():
     """Train on CG-generated pairs of a 32^3-cell GRF Laplace problem and use the network in
     flexible CG: it must reach the FP64 tolerance (true residual) and take fewer iterations than
