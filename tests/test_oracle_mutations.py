@@ -105,3 +105,57 @@ def test_catches_missing_dirichlet_column_drop(monkeypatch):
     x = inputs.uniform_vector(p.n_dof, 1)
     z = inputs.uniform_vector(p.n_dof, 2)
     assert abs(x @ wrong_apply(z) - z @ wrong_apply(x)) > 1e-6
+
+
+# ---- the training step (oracle/optim.py): each slip must trip a pin in tests/test_oracle_conv.py
+
+def _adam(correct_m=True, correct_v=True, eps_inside=False, swap=False, t_shift=0):
+    def step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+        if swap:
+            b1, b2 = b2, b1
+        p, g, m, v = (np.asarray(a, dtype=np.float64) for a in (p, g, m, v))
+        m1 = b1 * m + (1.0 - b1) * g
+        v1 = b2 * v + (1.0 - b2) * g * g
+        m_hat = m1 / (1.0 - b1 ** (t + t_shift)) if correct_m else m1
+        v_hat = v1 / (1.0 - b2 ** (t + t_shift)) if correct_v else v1
+        den = np.sqrt(v_hat + eps) if eps_inside else np.sqrt(v_hat) + eps
+        return p - lr * m_hat / den, m1, v1
+    return step
+
+
+@pytest.mark.parametrize("slip", [dict(correct_m=False), dict(correct_v=False), dict(eps_inside=True),
+                                  dict(swap=True), dict(t_shift=1)],
+                         ids=["no-m-correction", "no-v-correction", "eps-inside-sqrt", "swapped-betas",
+                              "step-off-by-one"])
+def test_adam_pins_catch(monkeypatch, slip):
+    from oracle import optim
+    from tests import test_oracle_conv
+    monkeypatch.setattr(optim, "adam_step", _adam(**slip))
+    with pytest.raises(AssertionError):
+        test_oracle_conv.test_adam_closed_forms()
+
+
+def test_adam_pins_pass_unmutated(monkeypatch):
+    from oracle import optim
+    from tests import test_oracle_conv
+    monkeypatch.setattr(optim, "adam_step", _adam())
+    test_oracle_conv.test_adam_closed_forms()
+
+
+@pytest.mark.parametrize("slip", ["weights-swapped", "threshold-absolute", "nan-resets"])
+def test_clip_pins_catch(monkeypatch, slip):
+    from oracle import optim
+    from tests import test_oracle_conv
+
+    def clip(norm, ema, ratio=5.0):
+        if not np.isfinite(norm):
+            return (0.0, 0.0) if slip == "nan-resets" else (0.0, ema)
+        limit = ratio if slip == "threshold-absolute" else ratio * ema
+        scale = limit / norm if (ema > 0.0 and norm > limit) else 1.0
+        used = norm * scale
+        if ema <= 0.0:
+            return scale, used
+        return scale, (0.1 * ema + 0.9 * used if slip == "weights-swapped" else 0.9 * ema + 0.1 * used)
+    monkeypatch.setattr(optim, "clip_scale", clip)
+    with pytest.raises(AssertionError):
+        test_oracle_conv.test_gradient_clip_special_cases()
