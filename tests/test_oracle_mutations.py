@@ -159,3 +159,146 @@ def test_clip_pins_catch(monkeypatch, slip):
     monkeypatch.setattr(optim, "clip_scale", clip)
     with pytest.raises(AssertionError):
         test_oracle_conv.test_gradient_clip_special_cases()
+
+
+# ---- the Krylov solvers (oracle/solvers.py): each slip must trip a pin in tests/test_oracle_pins.py
+
+def _cg(slip):
+    def cg(apply, b, rtol=1e-8, max_iter=2000, x0=None, dot=None):
+        dot = dot or (lambda u, v: float(np.dot(u, v)))
+        x = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        bn = np.sqrt(dot(b, b))
+        rr = dot(r, r)
+        hist, k = [np.sqrt(rr) / bn], 0
+        while k < max_iter and np.isfinite(rr) and np.sqrt(rr) > rtol * bn:
+            Ap = apply(p)
+            alpha = rr / (dot(p, p) if slip == "alpha-without-A" else dot(p, Ap))
+            x += alpha * p
+            r_old = r.copy()
+            r -= alpha * Ap
+            rr_new = dot(r, r)
+            beta = rr / rr_new if slip == "beta-inverted" else rr_new / rr
+            p = (r_old if slip == "p-from-old-r" else r) + beta * p
+            rr = rr_new
+            k += 1
+            hist.append(np.sqrt(rr) / bn)
+        return x, k, hist
+    return cg
+
+
+@pytest.mark.parametrize("slip", ["alpha-without-A", "beta-inverted", "p-from-old-r"])
+def test_cg_pins_catch(monkeypatch, slip):
+    from oracle import solvers
+    from tests import test_oracle_pins
+    monkeypatch.setattr(solvers, "cg", _cg(slip))
+    with pytest.raises(AssertionError):
+        test_oracle_pins.test_cg_finite_termination_small_spd()
+    with pytest.raises(AssertionError):
+        test_oracle_pins.test_cg_matches_direct_solve_and_residual()
+
+
+def test_cg_pins_pass_unmutated(monkeypatch):
+    from oracle import solvers
+    from tests import test_oracle_pins
+    monkeypatch.setattr(solvers, "cg", _cg(None))
+    test_oracle_pins.test_cg_finite_termination_small_spd()
+    test_oracle_pins.test_cg_matches_direct_solve_and_residual()
+
+
+def _fcg_m(slip):
+    def fcg_m(apply, b, precond, m=8, rtol=1e-8, max_iter=2000, keep_directions=False):
+        x = np.zeros_like(b)
+        r = b.copy()
+        bn = float(np.linalg.norm(b))
+        stored, allpairs, hist, k = [], [], [1.0], 0
+        while k < max_iter and np.linalg.norm(r) > rtol * bn:
+            z = precond(r)
+            p = z.copy()
+            window = stored[-1:] if slip == "last-direction-only" else stored
+            for pj, apj, dj in window:
+                c = float(np.dot(z, apj)) / dj
+                p = p + c * pj if slip == "sign" else p - c * pj
+            Ap = apply(p)
+            pAp = float(np.dot(p, Ap))
+            alpha = float(np.dot(p, r)) / pAp
+            x += alpha * p
+            r -= alpha * Ap
+            stored.append((p, Ap, pAp))
+            if len(stored) > m:
+                stored.pop(0)
+            if keep_directions:
+                allpairs.append((p, Ap))
+            k += 1
+            hist.append(float(np.linalg.norm(r)) / bn)
+        return (x, k, hist, allpairs) if keep_directions else (x, k, hist)
+    return fcg_m
+
+
+@pytest.mark.parametrize("slip", ["last-direction-only", "sign"])
+def test_fcg_m_pins_catch(monkeypatch, slip):
+    from oracle import solvers
+    from tests import test_oracle_pins
+    monkeypatch.setattr(solvers, "fcg_m", _fcg_m(slip))
+    with pytest.raises(AssertionError):
+        test_oracle_pins.test_fcg_m_special_cases_and_orthogonality()
+
+
+def test_pcg_with_r_dot_r_is_caught(monkeypatch):
+    """PCG whose beta uses r.r instead of r.z: FCG(1) with the same fixed preconditioner no longer
+    reproduces it."""
+    from oracle import solvers
+    from tests import test_oracle_pins
+
+    def pcg(apply, b, precond, rtol=1e-8, max_iter=2000):
+        x, r = np.zeros_like(b), b.copy()
+        z = precond(r)
+        p, bn, rz, rr = z.copy(), float(np.linalg.norm(b)), float(np.dot(r, z)), float(np.dot(r, r))
+        hist, k = [1.0], 0
+        while k < max_iter and np.linalg.norm(r) > rtol * bn:
+            Ap = apply(p)
+            alpha = rz / float(np.dot(p, Ap))
+            x += alpha * p
+            r -= alpha * Ap
+            z = precond(r)
+            rr_new = float(np.dot(r, r))
+            p = z + (rr_new / rr) * p
+            rz, rr = float(np.dot(r, z)), rr_new
+            k += 1
+            hist.append(float(np.linalg.norm(r)) / bn)
+        return x, k, hist
+    monkeypatch.setattr(solvers, "pcg", pcg)
+    with pytest.raises(AssertionError):
+        test_oracle_pins.test_fcg_m_special_cases_and_orthogonality()
+
+
+def test_single_sync_without_alpha_correction_is_caught(monkeypatch):
+    """Chronopoulos-Gear with alpha = gamma / delta at every step (the beta term of the denominator
+    dropped)."""
+    from oracle import solvers
+    from tests import test_oracle_pins
+
+    def css(apply, b, precond=None, rtol=1e-8, max_iter=2000):
+        M = precond or (lambda v: v.copy())
+        x, r = np.zeros_like(b), b.copy()
+        p, s = np.zeros_like(b), np.zeros_like(b)
+        bn = float(np.linalg.norm(b))
+        u, gamma_prev, hist, k = M(r), None, [1.0], 0
+        while k < max_iter and np.isfinite(np.linalg.norm(r)) and np.linalg.norm(r) > rtol * bn:
+            w = apply(u)
+            gamma, delta = float(np.dot(r, u)), float(np.dot(w, u))
+            beta = 0.0 if k == 0 else gamma / gamma_prev
+            alpha = gamma / delta
+            p = u + beta * p
+            s = w + beta * s
+            x += alpha * p
+            r -= alpha * s
+            u = M(r)
+            gamma_prev = gamma
+            k += 1
+            hist.append(float(np.linalg.norm(r)) / bn)
+        return x, k, hist
+    monkeypatch.setattr(solvers, "cg_single_sync", css)
+    with pytest.raises(AssertionError):
+        test_oracle_pins.test_single_sync_cg_pins()
