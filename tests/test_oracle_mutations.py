@@ -302,3 +302,74 @@ def test_single_sync_without_alpha_correction_is_caught(monkeypatch):
     monkeypatch.setattr(solvers, "cg_single_sync", css)
     with pytest.raises(AssertionError):
         test_oracle_pins.test_single_sync_cg_pins()
+
+
+# ---- the network's operations (oracle/conv.py): each slip must trip a pin in tests/test_oracle_conv.py
+
+def _conv_flipped(x, w, b=None):
+    """conv3d with the tap offsets mirrored (correlation with the flipped kernel)."""
+    nz, ny, nx, _ = x.shape
+    xp = np.pad(np.asarray(x, dtype=np.float64), ((1, 1), (1, 1), (1, 1), (0, 0)))
+    y = np.zeros((nz, ny, nx, w.shape[2]))
+    for t in range(27):
+        ox, oy, oz = 2 - t % 3, 2 - (t // 3) % 3, 2 - t // 9
+        y += xp[oz:oz + nz, oy:oy + ny, ox:ox + nx, :] @ np.asarray(w[t], dtype=np.float64)
+    return y + b if b is not None else y
+
+
+def _dgrad_unflipped(dy, w):
+    """dgrad taking dy at v + off instead of v - off."""
+    nz, ny, nx, _ = dy.shape
+    dyp = np.pad(np.asarray(dy, dtype=np.float64), ((1, 1), (1, 1), (1, 1), (0, 0)))
+    dx = np.zeros((nz, ny, nx, w.shape[1]))
+    for t in range(27):
+        ox, oy, oz = t % 3, (t // 3) % 3, t // 9
+        dx += dyp[oz:oz + nz, oy:oy + ny, ox:ox + nx, :] @ np.asarray(w[t], dtype=np.float64).T
+    return dx
+
+
+def _wgrad_flipped(x, dy):
+    """wgrad with x taken at v - off."""
+    nz, ny, nx, ci = x.shape
+    xp = np.pad(np.asarray(x, dtype=np.float64), ((1, 1), (1, 1), (1, 1), (0, 0)))
+    d = np.asarray(dy, dtype=np.float64).reshape(-1, dy.shape[3])
+    dw = np.zeros((27, ci, dy.shape[3]))
+    for t in range(27):
+        ox, oy, oz = 2 - t % 3, 2 - (t // 3) % 3, 2 - t // 9
+        dw[t] = xp[oz:oz + nz, oy:oy + ny, ox:ox + nx, :].reshape(-1, ci).T @ d
+    return dw, d.sum(axis=0)
+
+
+def _restrict_injection(x):
+    return np.asarray(x, dtype=np.float64)[::2, ::2, ::2]
+
+
+def _bf16_truncate(a):
+    f = np.asarray(a, dtype=np.float32)
+    return (f.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32)
+
+
+@pytest.mark.parametrize("name,fn,pin", [
+    ("conv3d", _conv_flipped, "test_conv_brute_force_tiny"),
+    ("conv3d_dgrad", _dgrad_unflipped, "test_dgrad_is_the_adjoint"),
+    ("conv3d_wgrad", _wgrad_flipped, "test_wgrad_matches_directional_derivative"),
+    ("restrict", _restrict_injection, "test_restriction_prolongation_pair"),
+    ("bf16_round", _bf16_truncate, "test_bf16_rounding"),
+], ids=["conv-taps-mirrored", "dgrad-not-mirrored", "wgrad-mirrored", "restrict-by-injection",
+        "bf16-truncation"])
+def test_conv_pins_catch(monkeypatch, name, fn, pin):
+    from oracle import conv
+    from tests import test_oracle_conv
+    monkeypatch.setattr(conv, name, fn)
+    with pytest.raises(AssertionError):
+        getattr(test_oracle_conv, pin)()
+
+
+def test_prolongation_weight_slip_is_caught(monkeypatch):
+    """Trilinear interpolation without the factor 2 (plain transpose of full weighting)."""
+    from oracle import conv
+    from tests import test_oracle_conv
+    orig = conv.prolong
+    monkeypatch.setattr(conv, "prolong", lambda x: 0.5 * orig(x))
+    with pytest.raises(AssertionError):
+        test_oracle_conv.test_restriction_prolongation_pair()
