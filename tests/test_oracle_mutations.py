@@ -373,3 +373,38 @@ def test_prolongation_weight_slip_is_caught(monkeypatch):
     monkeypatch.setattr(conv, "prolong", lambda x: 0.5 * orig(x))
     with pytest.raises(AssertionError):
         test_oracle_conv.test_restriction_prolongation_pair()
+
+
+# ---- the Q2 hexahedron (oracle/fem.py): each slip must trip a pin in tests/test_oracle_q2.py
+
+def _gauss2_tensor():
+    g = np.array([-1.0, 1.0]) / np.sqrt(3.0)
+    q = np.arange(8)
+    idx = np.stack([q % 2, (q // 2) % 2, q // 4], axis=1)
+    return g[idx], np.ones(8)
+
+
+def _gauss3_weights_misplaced():
+    g1 = np.array([-np.sqrt(0.6), 0.0, np.sqrt(0.6)])
+    w1 = np.array([8.0, 5.0, 5.0]) / 9.0
+    q = np.arange(27)
+    idx = np.stack([q % 3, (q // 3) % 3, q // 9], axis=1)
+    return g1[idx], w1[idx[:, 0]] * w1[idx[:, 1]] * w1[idx[:, 2]]
+
+
+def _lagrange2_derivative_sign(t):
+    L = np.stack([0.5 * t * (t - 1.0), 1.0 - t * t, 0.5 * t * (t + 1.0)], axis=-1)
+    dL = np.stack([t + 0.5, -2.0 * t, t + 0.5], axis=-1)
+    return L, dL
+
+
+@pytest.mark.parametrize("name,fn,pin", [
+    ("gauss3_points", _gauss2_tensor, "test_q2_box_element_is_kronecker_sum"),
+    ("gauss3_points", _gauss3_weights_misplaced, "test_q2_box_element_is_kronecker_sum"),
+    ("_lagrange2", _lagrange2_derivative_sign, "test_q2_shape_functions")],
+    ids=["two-point-rule", "weights-misplaced", "derivative-sign"])
+def test_q2_pins_catch(monkeypatch, name, fn, pin):
+    from tests import test_oracle_q2
+    monkeypatch.setattr(fem, name, fn)
+    with pytest.raises(AssertionError):
+        getattr(test_oracle_q2, pin)()
