@@ -105,26 +105,34 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        with open(self.path) as f:
+            text = f.read()
         os.unlink(self.path)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            r = [c.strip() for c in r]
-            if len(r) < 9:
-                continue
-            try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, r[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarise_clocks(text)
+
+
+def summarise_clocks(text: str):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in `nvidia-smi --query-gpu=
+    ClockSampler.FIELDS --format=csv,noheader,nounits` output; rows that are short or hold no number
+    (a partial last line, "[N/A]") are skipped.  None when no row parses."""
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in text.strip().splitlines():
+        r = [c.strip() for c in line.split(",")]
+        if len(r) < 9:
+            continue
+        try:
+            sm.append(float(r[1]))
+            smax.append(float(r[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, r[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 # ----------------------------------------------------------------------- multi-rank timing ----
