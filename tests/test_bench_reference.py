@@ -38,3 +38,16 @@ def test_reference_arm_other_ranks_do_nothing():
     out = _run({"RANK": "1"})
     assert out.returncode == 0, out.stderr[-2000:]
     assert out.stdout.strip() == ""
+
+
+def test_one_core_oracle_sample():
+    """The one-core leg of cpu_baseline: the oracle's apply on bottom slabs of both workloads, its
+    rate scaled by the full problems' free DoF per cell."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2308_09839_gb300 import inputs
+    pL = inputs.cartesian_laplace_256(n=12)
+    pE = inputs.cartesian_elasticity_160(n=6)
+    rate, secs, desc = bench.oracle_sample_rate([pL, pE], [2, 1])
+    assert rate > 0 and secs > 0
+    assert "laplace 12x12x2 cells x1" in desc and "elasticity 6x6x1 cells x1" in desc
