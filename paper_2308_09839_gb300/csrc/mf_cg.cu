@@ -24,7 +24,10 @@
 
 namespace {
 
-constexpr int kRedBlocks = 608;  // 4 per SM on 152 SMs; fixed so the reduction tree is fixed
+// Reduction grids: a fixed number of blocks (4 per SM of a 152-SM GB300), so that the reduction
+// tree, and with it every dot product's rounding, is the same on every run and every GPU.
+constexpr int kRedBlocksPerSm = 4;
+constexpr int kRedBlocks = 152 * kRedBlocksPerSm;
 constexpr int kRedThreads = 256;
 // The per-iteration vector kernels take kVecUnroll strided elements per step of their grid-stride
 // loop and issue all of the step's loads before its arithmetic, so that each thread has kVecUnroll
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(kRedThreads) cg_init(int64_t n, const R *__res
 
 // pAp = p.Ap (when the operator does not fuse it into its own write phase).
 template <typename R>
-__global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) cg_pap(int64_t n, const R *__restrict__ p, const R *__restrict__ Ap,
+__global__ void __launch_bounds__(kRedThreads, kRedBlocksPerSm) cg_pap(int64_t n, const R *__restrict__ p, const R *__restrict__ Ap,
                                                       double *partials, CgScalars *sc) {
   if (sc->done) return;
   double v[1] = {0.0};
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) cg_pap(int64_t 
 // cg_flush_x at the end).  A step takes kVecUnroll elements for r alone and half as many for x and r,
 // about eight loads in flight per thread either way.
 template <typename R, bool X>
-__global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) cg_update_xr(int64_t n, R *__restrict__ x, R *__restrict__ r,
+__global__ void __launch_bounds__(kRedThreads, kRedBlocksPerSm) cg_update_xr(int64_t n, R *__restrict__ x, R *__restrict__ r,
                                                             const R *__restrict__ p, const R *__restrict__ Ap,
                                                             const double *__restrict__ invdiag, double *partials,
                                                             CgScalars *sc) {
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) cg_update_xr(in
 
 // p = z + beta p.
 template <typename R>
-__global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152) cg_update_p(int64_t n, const R *__restrict__ r, R *__restrict__ p,
+__global__ void __launch_bounds__(kRedThreads, kRedBlocksPerSm) cg_update_p(int64_t n, const R *__restrict__ r, R *__restrict__ p,
                                                            const double *__restrict__ invdiag, const CgScalars *sc) {
   if (sc->done) return;
   const double beta = sc->beta;
