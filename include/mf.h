@@ -58,7 +58,9 @@ typedef struct mf_csr mf_csr;
  *   physics    MF_LAPLACE (1 DoF per node), MF_ELASTICITY (3 DoFs per node) or MF_VECTOR_LAPLACE
  *              (3 DoFs per node: the vector Laplacian of Eqs. 2 and 5, the scalar operator acting
  *              on each component).
- *   n_nodes    N >= 8; n_cells E >= 1.
+ *   n_nodes    N >= 8; n_cells E >= 1.  Indices are 32-bit: 3 N and 8 E (npe E for the element
+ *              types of mf_setup_mesh_elem) must not exceed 2^31 - 1, about 715 M nodes and 268 M
+ *              hexahedra (a 640^3 box); larger meshes are refused with MF_ERR_ARG.
  *   coords     device double[N][3], node coordinates.
  *   cells      device int32[E][8] element -> node map in the corner order above, or NULL for a
  *              structured nx x ny x nz box numbered as above (then E must equal nx*ny*nz and N

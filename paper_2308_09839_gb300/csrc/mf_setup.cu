@@ -381,7 +381,12 @@ static mf_status setup_mesh(int npe, int physics, int64_t n_nodes, int64_t n_cel
   MF_ARG(coords && mat, "mf_setup_mesh: coords and mat are required");
   MF_ARG(npe == 8 || cells != nullptr, "mf_setup_mesh: tetrahedral and Q2 meshes need an explicit connectivity");
   MF_ARG(n_nodes >= npe && n_cells >= 1, "mf_setup_mesh: need n_nodes >= %d and n_cells >= 1", npe);
-  MF_ARG(n_nodes < (int64_t)INT32_MAX, "mf_setup_mesh: n_nodes must fit int32");
+  // the kernels index coordinates and DoFs (3 per node) and the connectivity (npe per cell) with
+  // 32-bit integers: larger meshes are refused here rather than indexed past 2^31 - 1
+  MF_ARG(3 * n_nodes <= (int64_t)INT32_MAX, "mf_setup_mesh: %lld nodes: 3 n_nodes must fit int32",
+         (long long)n_nodes);
+  MF_ARG((int64_t)npe * n_cells <= (int64_t)INT32_MAX,
+         "mf_setup_mesh: %lld cells of %d nodes: the connectivity's size must fit int32", (long long)n_cells, npe);
   if (!cells) {
     MF_ARG(nx > 0 && ny > 0 && nz > 0, "mf_setup_mesh: structured mesh needs nx, ny, nz > 0");
     MF_ARG((int64_t)nx * ny * nz == n_cells, "mf_setup_mesh: n_cells != nx*ny*nz");

@@ -65,6 +65,28 @@ def test_host_only_calls(lib):
     assert mf.lib.mf_mesh_query(None, None, None, None, None, None, None) == mf.MF_ERR_ARG
 
 
+def test_setup_refuses_meshes_beyond_32_bit_indices(lib):
+    """3 N and npe E must fit int32 (the kernels' index type): the setup refuses larger meshes with
+    MF_ERR_ARG before it touches a pointer or the device (the dummy pointers are never read)."""
+    import ctypes as C
+    from paper_2308_09839_gb300 import mf
+    fake = C.c_void_p(16)
+    out = C.c_void_p()
+    big_nodes = (2 ** 31) // 3 + 1
+    assert mf.lib.mf_setup_mesh(mf.MF_LAPLACE, big_nodes, 1000, fake, fake, 0, 0, 0, fake, None, None,
+                                C.byref(out)) == mf.MF_ERR_ARG
+    assert "3 n_nodes must fit int32" in mf.mf_last_error() and not out.value
+    big_cells = (2 ** 31) // 8 + 1
+    assert mf.lib.mf_setup_mesh(mf.MF_LAPLACE, 1000, big_cells, fake, fake, 0, 0, 0, fake, None, None,
+                                C.byref(out)) == mf.MF_ERR_ARG
+    assert "connectivity" in mf.mf_last_error() and not out.value
+    # 27-node cells reach the limit 27/8 times sooner
+    q2_cells = (2 ** 31) // 27 + 1
+    assert mf.lib.mf_setup_mesh_elem(mf.MF_ELEM_HEX27, mf.MF_LAPLACE, 1000, q2_cells, fake, fake, fake, None, None,
+                                     C.byref(out)) == mf.MF_ERR_ARG
+    assert "27 nodes" in mf.mf_last_error() and not out.value
+
+
 def test_release_build_reports_no_index_checks(lib):
     """mf_debug_status in the release library: checks compiled out, no device touched."""
     from paper_2308_09839_gb300 import mf
