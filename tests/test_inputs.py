@@ -1,6 +1,7 @@
 """The seeded input generators shared by the CUDA path's tests and benchmark and by the oracle: the
 same seed gives the same arrays, the element maps are consistent with the node lattice, and the
-derived meshes (tetrahedra, Q2) sit on the Q1 box they are built from."""
+derived meshes (tetrahedra, Q2) sit on the Q1 box they are built from, and the coefficient fields
+follow their stated recipes."""
 import numpy as np
 import pytest
 
@@ -60,3 +61,23 @@ def test_renumber_is_a_relabelling():
     assert np.array_equal(np.sort(node_perm), np.arange(p.n_nodes))
     assert np.array_equal(coords[new_cells], p.coords[cells[elem_perm]])
     assert np.array_equal(dirichlet[node_perm], p.dirichlet)
+
+
+def test_coefficient_recipes():
+    """The coefficient fields follow their stated recipes: lognormal cells with log-sd sigma; eight
+    equal z-slabs, each with one multiplier 10^s, s in [-1, 1]; the Gaussian random field has mean 0,
+    standard deviation sigma, and the correlation of white noise smoothed by a Gaussian of c cells,
+    exp(-d^2 / (4 c^2)) at lag d (estimated on a periodic 64^3 box, which biases it slightly low)."""
+    import math
+    lk = np.log(inputs.lognormal_cells(200000, 0.5, seed=3))
+    assert abs(lk.mean()) < 0.01 and abs(lk.std() - 0.5) < 0.01
+    m = inputs.layer_multiplier(6, 5, 16, 8, seed=4).reshape(16, 5, 6)
+    s = np.log10(m[:, 0, 0])
+    assert np.all(np.abs(s) <= 1.0)
+    assert np.all(m == m[:, :1, :1])  # constant within each z-plane
+    assert np.all(s[0::2] == s[1::2]) and len(set(s[0::2])) == 8  # 8 slabs of 2 planes
+    f = inputs.gaussian_random_field(64, 64, 64, 4.0, 1.5, seed=0).reshape(64, 64, 64)
+    assert abs(f.mean()) < 1e-12 and abs(f.std() - 1.5) < 1e-12
+    for d, tol in ((2, 0.02), (4, 0.05), (8, 0.1)):
+        c = np.mean([np.mean(f * np.roll(f, d, axis=a)) for a in range(3)]) / f.var()
+        assert abs(c - math.exp(-d * d / (4 * 16.0))) < tol, (d, c)
