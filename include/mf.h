@@ -232,6 +232,9 @@ mf_status mf_csr_export(const mf_csr *csr, int64_t *rowptr, int32_t *col, double
  * allocates nothing, deterministic. */
 mf_status mf_spmv_csr(const mf_csr *csr, const double *x, double *y, mf_stream stream);
 
+/* Frees the matrix's device arrays (synchronises the device first).  NULL is a no-op.  CG graphs
+ * captured for this matrix are never replayed for another one (they are keyed by a process-unique
+ * matrix id). */
 mf_status mf_destroy_csr(mf_csr *csr);
 
 /* Solver options (mf_cg_solve). */
@@ -378,6 +381,7 @@ mf_status mf_cg_solve_noalloc(const mf_mesh *mesh, const mf_solve_opts *opts, co
  *   mf_batch_create   allocates the batch workspace and captures the graph (synchronous).
  *   mf_batch_solve    b, x: HOST arrays of n DEVICE pointers (double[n_dof_i]); infos: host
  *                     array of n (rel_res_true is not recomputed: -1).  Synchronises `stream`.
+ *   mf_batch_destroy  frees the workspace and the graph (synchronises the device); NULL is a no-op.
  *   mf_cg_solve_batched  create + solve + destroy in one call.
  */
 typedef struct mf_batch mf_batch;
@@ -404,6 +408,9 @@ mf_status mf_set_tile_segment(mf_mesh *mesh, int32_t seg);
  * log kappa) with s = RMS(D^-1/2 r1); z2 = z1 + theta cn with the energy-norm step
  * theta = max(0, cn.r1 / cn.A cn); z = z2 + w D^-1 (r - A z2); w = 2/3, c the output scale.
  *   mf_net_create       node grid nx x ny x nz (each 4m+1 >= 5), seeded He initialisation.
+ *   mf_net_destroy      frees the network (synchronises the device); NULL is a no-op.
+ *   mf_net_set_output_scale  the factor c applied to the network's output (c > 0, else MF_ERR_ARG;
+ *                       1 after mf_net_create); mf_cg_solve reads it once, when a solve starts.
  *   mf_net_forward      r, logk, out: device float[nx ny nz] (x fastest).  Asynchronous.
  *   mf_net_train_step   one Adam step on the relative squared error |out - target|^2 / |target|^2
  *                       (gradient norm clipped to 5x its moving average over earlier steps);
