@@ -35,6 +35,26 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_every_declaration_is_documented():
+    """Each function of the boundary has a comment: directly above its declaration, or in the block
+    comment of its group that names it."""
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        lines = open(os.path.join(ROOT, "include", fn)).read().splitlines()
+        decl = re.compile(r"^\s*(?:mf_status|void|int64_t|size_t|const char \*)\s*\*?\s*(mf_\w+)\s*\(")
+        comments = []
+        for i, line in enumerate(lines):
+            m = decl.match(line)
+            if not m:
+                continue
+            above = lines[i - 1].strip()
+            block = "\n".join(ln for ln in lines[max(0, i - 80):i] if ln.lstrip().startswith(("/*", "*")))
+            if not (above.endswith("*/") or m.group(1) in block):
+                comments.append(m.group(1))
+        assert not comments, (fn, comments)
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
