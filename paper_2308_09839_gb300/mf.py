@@ -270,6 +270,15 @@ def mf_cg_resume(h, opts: mf_solve_opts, state: bytes, b, x, stream=None, ok=(MF
     return info
 
 
+def _vec(t, n: int, dtypes, what: str) -> None:
+    """Refuse a vector that the kernels would read or write out of bounds: a dtype other than the
+    ones the call takes, or fewer than n elements."""
+    if t.dtype not in dtypes:
+        raise ValueError(f"{what}: dtype {t.dtype}; expected {' or '.join(str(d) for d in dtypes)}")
+    if t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements; {n} needed")
+
+
 def _ptr_array(ts):
     arr = (vp * len(ts))()
     for i, t in enumerate(ts):
@@ -507,8 +516,11 @@ class Mesh:
         mf_set_apply_variant(self.h, variant)
 
     def apply(self, x, y=None, stream=None):
+        n = self.info["n_dof"]
+        _vec(x, n, (torch.float64, torch.float32), "Mesh.apply x")
         if y is None:
             y = torch.empty_like(x)
+        _vec(y, n, (x.dtype,), "Mesh.apply y")
         if x.dtype == torch.float32:
             mf_apply_f32(self.h, x, y, stream)
         elif self.physics == MF_LAPLACE:
@@ -520,8 +532,11 @@ class Mesh:
         return y
 
     def apply_multi(self, X, nrhs, Y=None, stream=None):
+        n = self.info["n_dof"] * int(nrhs)
+        _vec(X, n, (torch.float64,), "Mesh.apply_multi X")
         if Y is None:
             Y = torch.empty_like(X)
+        _vec(Y, n, (torch.float64,), "Mesh.apply_multi Y")
         mf_apply_multi(self.h, nrhs, X, Y, stream)
         return Y
 
@@ -540,8 +555,11 @@ class Mesh:
         if csr is not None:
             o.csr = csr.h
             o.op = MF_OP_CSR
+        n = self.info["n_dof"]
+        _vec(b, n, (torch.float64,), "Mesh.cg b")
         if x is None:
             x = torch.empty_like(b)
+        _vec(x, n, (torch.float64,), "Mesh.cg x")
         info = mf_cg_solve(self.h, o, b, x, stream, ok=ok)
         return x, info
 
@@ -552,8 +570,11 @@ class Mesh:
         o = mf_solve_opts_default()
         for k, v in kw.items():
             setattr(o, k, v)
+        n = self.info["n_dof"]
+        _vec(b, n, (torch.float64,), "Mesh.cg_resume b")
         if x is None:
             x = torch.empty_like(b)
+        _vec(x, n, (torch.float64,), "Mesh.cg_resume x")
         info = mf_cg_resume(self.h, o, state, b, x, stream, ok=ok)
         return x, info
 
@@ -576,8 +597,11 @@ class Csr:
         self.info = mf_csr_query(h)
 
     def spmv(self, x, y=None, stream=None):
+        n = self.info["n_rows"]
+        _vec(x, n, (torch.float64,), "Csr.spmv x")
         if y is None:
             y = torch.empty_like(x)
+        _vec(y, n, (torch.float64,), "Csr.spmv y")
         mf_spmv_csr(self.h, x, y, stream)
         return y
 

@@ -187,3 +187,35 @@ def test_ctypes_structs_and_constants_match_the_header(lib, tmp_path):
     assert r.returncode == 0, r.stderr
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert got == expect
+
+
+def test_vector_arguments_are_checked_before_the_library(lib):
+    """Mesh and Csr methods refuse vectors that the kernels would read or write out of bounds (another
+    dtype, too few elements, y of another precision than x) before any call into the library; valid
+    host tensors get past these checks and stop at the CUDA-tensor check."""
+    import torch
+    from paper_2308_09839_gb300 import mf
+    m = mf.Mesh.__new__(mf.Mesh)
+    m.h, m.physics, m.info = None, mf.MF_ELASTICITY, {"n_dof": 24}
+    f64, f32 = torch.float64, torch.float32
+    cases = [
+        (lambda: m.apply(torch.zeros(24, dtype=torch.float16)), "dtype"),
+        (lambda: m.apply(torch.zeros(23, dtype=f64)), "23 elements; 24 needed"),
+        (lambda: m.apply(torch.zeros(24, dtype=f64), torch.zeros(24, dtype=f32)), "Mesh.apply y: dtype"),
+        (lambda: m.apply_multi(torch.zeros(24 * 3 - 1, dtype=f64), 3), "71 elements; 72 needed"),
+        (lambda: m.cg(torch.zeros(24, dtype=f32)), "Mesh.cg b: dtype"),
+        (lambda: m.cg(torch.zeros(24, dtype=f64), torch.zeros(20, dtype=f64)), "Mesh.cg x: 20 elements"),
+        (lambda: m.cg_resume(b"", torch.zeros(10, dtype=f64)), "Mesh.cg_resume b: 10 elements"),
+        (lambda: m.apply(torch.zeros(24, dtype=f64)), "expected a CUDA tensor"),
+        (lambda: m.apply(torch.zeros(24, dtype=f32)), "expected a CUDA tensor"),
+        (lambda: m.apply_multi(torch.zeros(72, dtype=f64), 3), "expected a CUDA tensor"),
+        (lambda: m.cg(torch.zeros(24, dtype=f64)), "expected a CUDA tensor"),
+    ]
+    a = mf.Csr.__new__(mf.Csr)
+    a.h, a.info = None, {"n_rows": 24}
+    cases += [(lambda: a.spmv(torch.zeros(24, dtype=f32)), "Csr.spmv x: dtype"),
+              (lambda: a.spmv(torch.zeros(24, dtype=f64), torch.zeros(2, dtype=f64)), "Csr.spmv y: 2 elements"),
+              (lambda: a.spmv(torch.zeros(24, dtype=f64)), "expected a CUDA tensor")]
+    for call, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            call()
