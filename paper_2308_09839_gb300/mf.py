@@ -417,13 +417,22 @@ class Net:
         blob = np.ascontiguousarray(blob, dtype=np.uint8)
         check(lib.mf_net_state_load(self.h, blob.ctypes.data, blob.size), "mf_net_state_load")
 
+    def _fields(self, what, *ts):
+        """Node fields of the network's grid: float32, nx ny nz elements each."""
+        n = self.dims[0] * self.dims[1] * self.dims[2]
+        for name, t in ts:
+            _vec(t, n, (torch.float32,), f"Net.{what} {name}")
+
     def forward(self, r, logk, out=None, stream=None):
+        self._fields("forward", ("r", r), ("logk", logk))
         if out is None:
             out = torch.empty_like(r)
+        self._fields("forward", ("out", out))
         check(lib.mf_net_forward(self.h, _ptr(r), _ptr(logk), _ptr(out), _stream(stream)), "mf_net_forward")
         return out
 
     def train_step(self, r, logk, target, lr, stream=None):
+        self._fields("train_step", ("r", r), ("logk", logk), ("target", target))
         loss = C.c_float()
         check(lib.mf_net_train_step(self.h, _ptr(r), _ptr(logk), _ptr(target), float(lr), C.byref(loss),
                                     _stream(stream)), "mf_net_train_step")
@@ -431,6 +440,7 @@ class Net:
 
     def gradients(self, r, logk, target, stream=None):
         import numpy as np
+        self._fields("gradients", ("r", r), ("logk", logk), ("target", target))
         g = np.empty(self.n_params, dtype=np.float32)
         loss = C.c_float()
         check(lib.mf_net_gradients(self.h, _ptr(r), _ptr(logk), _ptr(target), g.ctypes.data, C.byref(loss),

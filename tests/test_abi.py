@@ -216,6 +216,15 @@ def test_vector_arguments_are_checked_before_the_library(lib):
     cases += [(lambda: a.spmv(torch.zeros(24, dtype=f32)), "Csr.spmv x: dtype"),
               (lambda: a.spmv(torch.zeros(24, dtype=f64), torch.zeros(2, dtype=f64)), "Csr.spmv y: 2 elements"),
               (lambda: a.spmv(torch.zeros(24, dtype=f64)), "expected a CUDA tensor")]
+    nt = mf.Net.__new__(mf.Net)
+    nt.h, nt.dims = None, (5, 5, 9)
+    v = torch.zeros(225, dtype=f32)
+    cases += [(lambda: nt.forward(torch.zeros(225, dtype=torch.float16), v), "Net.forward r: dtype"),
+              (lambda: nt.forward(v, torch.zeros(224, dtype=f32)), "Net.forward logk: 224 elements"),
+              (lambda: nt.train_step(v, v, torch.zeros(225, dtype=f64), 1e-3), "Net.train_step target: dtype"),
+              (lambda: nt.gradients(v, v, v[:100]), "Net.gradients target: 100 elements"),
+              (lambda: nt.forward(v, v), "expected a CUDA tensor"),
+              (lambda: nt.train_step(v, v, v, 1e-3), "expected a CUDA tensor")]
     for call, msg in cases:
         with pytest.raises(ValueError, match=msg):
             call()
